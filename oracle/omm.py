@@ -1,0 +1,363 @@
+"""FP64 CPU oracle for orbital-minimization (OMM) conjugate-gradient solves.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product library imports, links or
+calls this module; it exists so that tests, the smoke check and the CPU
+baseline arm of the benchmark can compare the CUDA path with a plain,
+slow, obviously correct implementation written from the paper
+(arXiv 2209.05934, "Modular implementation of the linear and cubic-scaling
+orbital minimization methods ...").
+
+Notation follows the paper with the coefficient matrix C written as W (m x n,
+one column per orbital):  H_W = W^T H W,  S_W = W^T S W.
+
+Every function works on dense numpy arrays and, for the linear-scaling form,
+on scipy.sparse matrices: the paper states that the sparse and dense forms
+run the same equations, with sparse matrices instead of dense ones and the
+gradient restricted to the sparsity pattern of W (section "Solver library").
+Library primitives used as single steps: matrix products (numpy / scipy.sparse),
+polynomial roots (numpy.roots), Cholesky and triangular solves (scipy.linalg).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+# status codes shared by name (not by code) with the library's C header
+OK = 0
+ERR_LINESEARCH = -5
+ERR_MAXITER = -6
+
+
+# ----------------------------------------------------------------------------
+# small helpers: Frobenius inner product and trace for dense or sparse operands
+# ----------------------------------------------------------------------------
+def frob(A, B) -> float:
+    """<A, B> = sum_ij A_ij B_ij."""
+    if sp.issparse(A) or sp.issparse(B):
+        A = sp.csr_matrix(A)
+        return float(A.multiply(B).sum())
+    return float(np.sum(np.asarray(A) * np.asarray(B)))
+
+
+def trace(A) -> float:
+    if sp.issparse(A):
+        return float(A.diagonal().sum())
+    return float(np.trace(A))
+
+
+def _dense(A):
+    return A.toarray() if sp.issparse(A) else np.asarray(A)
+
+
+# ----------------------------------------------------------------------------
+# Kim shift and its automatic choice
+# ----------------------------------------------------------------------------
+def shift(H, S, eta: float):
+    """H' = H - eta S: the eigenspectrum shift of the Kim functional (section
+    "Overview of OMM approaches", step (1) of the Kim construction)."""
+    return H - eta * S
+
+
+def gershgorin_eta(H, S) -> float:
+    """An upper bound of the generalised eigenvalues of (H, S) from Gershgorin discs.
+
+    lambda_max(H, S) = max_x x^T H x / x^T S x <= g_H / s_lo when g_H >= 0,
+    where g_H = max_i (H_ii + sum_{j!=i} |H_ij|) bounds lambda_max(H) and
+    s_lo = min_i (S_ii - sum_{j!=i} |S_ij|) bounds lambda_min(S) from below
+    (must be > 0).  When g_H < 0 the bound is g_H / s_hi with
+    s_hi = max_i (S_ii + sum_{j!=i} |S_ij|).  With eta >= lambda_max the shifted
+    H' is negative semidefinite, so the line-search quartic has a non-negative
+    leading coefficient.
+    """
+    Hd = _dense(H)
+    Sd = _dense(S)
+    dH = np.diag(Hd)
+    dS = np.diag(Sd)
+    offH = np.abs(Hd).sum(axis=1) - np.abs(dH)
+    offS = np.abs(Sd).sum(axis=1) - np.abs(dS)
+    g_H = float(np.max(dH + offH))
+    s_lo = float(np.min(dS - offS))
+    s_hi = float(np.max(dS + offS))
+    if s_lo <= 0.0:
+        raise ValueError("S is not strictly diagonally dominant; no Gershgorin bound")
+    return g_H / s_lo if g_H >= 0.0 else g_H / s_hi
+
+
+# ----------------------------------------------------------------------------
+# the functional, its gradient, the charge and the density matrix
+# ----------------------------------------------------------------------------
+def functional(W, H, S) -> float:
+    """E~ = 2 Tr[(2 I - W^T S W) W^T H W]  (Eq. 5, the Ordejon-Mauri functional,
+    spin factor 2 included)."""
+    HW_ = W.T @ (H @ W)
+    SW_ = W.T @ (S @ W)
+    n = W.shape[1]
+    two_I = 2.0 * (sp.identity(n, format="csr") if sp.issparse(SW_) else np.eye(n))
+    return 2.0 * trace((two_I - SW_) @ HW_)
+
+
+def gradient(W, H, S, mask=None):
+    """G = dE~/dW* = 2 (2 H W - S W H_W - H W S_W), the libOMM gradient
+    (section "Solver library"); for real W this is (1/2) dE~/dW.
+
+    In the linear-scaling form the gradient is kept only on the sparsity
+    pattern of the initial W (same section): `mask` is that pattern (a 0/1
+    array or sparse matrix of W's shape), applied elementwise.
+    """
+    HW = H @ W
+    SW = S @ W
+    H_W = W.T @ HW
+    S_W = W.T @ SW
+    G = 2.0 * (2.0 * HW - SW @ H_W - HW @ S_W)
+    return apply_mask(G, mask)
+
+
+def apply_mask(A, mask):
+    if mask is None:
+        return A
+    if sp.issparse(A) or sp.issparse(mask):
+        return sp.csr_matrix(sp.csr_matrix(A).multiply(mask))
+    return A * mask
+
+
+def charge(W, S) -> float:
+    """n_e = 2 Tr[(2 I - S_W) S_W]  (Listing 1, total charge)."""
+    S_W = _dense(W.T @ (S @ W))
+    n = S_W.shape[0]
+    return 2.0 * float(np.trace((2.0 * np.eye(n) - S_W) @ S_W))
+
+
+def density_matrix(W, S):
+    """rho = 2 W (2 I - S_W) W^T  (Eq. 6)."""
+    S_W = _dense(W.T @ (S @ W))
+    n = S_W.shape[0]
+    Wd = _dense(W)
+    return 2.0 * Wd @ (2.0 * np.eye(n) - S_W) @ Wd.T
+
+
+def energy_density_matrix(W, H, S, eta: float = 0.0):
+    """rho_E = 2 W H_W W^T, plus eta*rho for the Kim functional (Eq. 7 and the
+    Kim construction, step (3)); H is the unshifted Hamiltonian."""
+    Wd = _dense(W)
+    H_W = Wd.T @ (_dense(H) @ Wd)
+    rho_E = 2.0 * Wd @ H_W @ Wd.T
+    if eta != 0.0:
+        rho_E = rho_E + eta * density_matrix(W, S)
+    return rho_E
+
+
+# ----------------------------------------------------------------------------
+# exact line search: the quartic and its minimum
+# ----------------------------------------------------------------------------
+def quartic_coeffs(W, D, H, S) -> np.ndarray:
+    """Coefficients c_0..c_4 of E~(W + x D) as a polynomial in x.
+
+    The functional is quartic along a line (section "Introduction": the
+    quartic's parameters are computed analytically).  Written out from the
+    definition: H_W(x) = A0 + x A1 + x^2 A2 and S_W(x) = B0 + x B1 + x^2 B2 with
+    A0 = W^T H W, A1 = W^T H D + D^T H W, A2 = D^T H D (same for S), and
+    E~(x) = 2 (2 tr H_W(x) - <S_W(x), H_W(x)>), a product of two quadratics.
+    """
+    HW, HD = H @ W, H @ D
+    SW, SD = S @ W, S @ D
+    A = [W.T @ HW, W.T @ HD + D.T @ HW, D.T @ HD]
+    B = [W.T @ SW, W.T @ SD + D.T @ SW, D.T @ SD]
+    c = np.zeros(5)
+    for k in range(3):
+        c[k] += 2.0 * 2.0 * trace(A[k])
+    for i in range(3):
+        for j in range(3):
+            c[i + j] -= 2.0 * frob(B[i], A[j])
+    return c
+
+
+def quartic(c, x):
+    return c[0] + x * (c[1] + x * (c[2] + x * (c[3] + x * c[4])))
+
+
+def line_min(c) -> tuple[float, int]:
+    """Minimiser of the quartic c0 + c1 x + ... + c4 x^4.
+
+    Candidates are the real roots of its derivative with a positive second
+    derivative; the lowest quartic value wins, ties go to the smaller |x| and
+    then to x > 0.  With c4 = c3 = 0 and c2 > 0 the parabola's vertex is taken.
+    Returns (x, status); status is ERR_LINESEARCH when no minimum exists (the
+    paper warns that the line minimisation can have none, section
+    "Recommendations for OMM solver use").
+    """
+    c = np.asarray(c, dtype=np.float64)
+    if c[4] == 0.0 and c[3] == 0.0:
+        if c[2] > 0.0:
+            return -c[1] / (2.0 * c[2]), OK
+        return 0.0, ERR_LINESEARCH
+    if c[4] < 0.0:
+        return 0.0, ERR_LINESEARCH
+    deriv = [4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1]]
+    while deriv and deriv[0] == 0.0:
+        deriv = deriv[1:]
+    roots = np.roots(deriv)
+    scale = max(1.0, float(np.max(np.abs(roots)))) if roots.size else 1.0
+    real = [float(r.real) for r in roots if abs(r.imag) <= 1e-10 * scale]
+    cands = []
+    for x in real:
+        curv = 12.0 * c[4] * x * x + 6.0 * c[3] * x + 2.0 * c[2]
+        if curv > 0.0:
+            cands.append(x)
+    if not cands:
+        # a double root can have zero curvature; take the lowest real root value
+        if real and c[4] > 0.0:
+            cands = real
+        else:
+            return 0.0, ERR_LINESEARCH
+    best = min(cands, key=lambda x: (quartic(c, x), abs(x), -x))
+    return best, OK
+
+
+# ----------------------------------------------------------------------------
+# the CG minimisation
+# ----------------------------------------------------------------------------
+@dataclass
+class Result:
+    W: object
+    E: float                 # E~_eta + 2 eta n at the final W (the minimised quantity)
+    E_unshifted: float       # E~(W) with the unshifted H
+    iters: int
+    status: int
+    eta: float
+    history: list = field(default_factory=list)   # E_k per iteration
+    orth: float = float("nan")                     # ||S_W - I||_F at the final W
+
+
+def omm_cg(H, S, W0, tol: float = 1e-10, eta: float | None = None, max_iter: int = 10000,
+           orth_tol: float | None = None, mask=None) -> Result:
+    """Conjugate-gradient minimisation of the (shifted) Ordejon-Mauri functional.
+
+    Steps, in the paper's order (sections "Overview of OMM approaches" and
+    "Solver library", Table 1):
+      0. H' = H - eta S (Kim shift with n' = n; eta=None picks the Gershgorin
+         bound so the exact line search is always well posed).
+      each iteration k:
+      1. H_W = W^T H' W, S_W = W^T S W by definition; energy
+         E_k = 2 (2 tr H_W - <S_W, H_W>) + 2 eta n.
+      2. stop at k >= 1 when |2 (E_k - E_{k-1}) / (E_k + E_{k-1})| < tol
+         (OMM.RelTol) and, if orth_tol is given, ||S_W - I||_F < orth_tol.
+      3. G = 2 (2 H'W - S W H_W - H'W S_W), restricted to W's pattern.
+      4. D = -G at k = 0; otherwise Polak-Ribiere+ beta =
+         max(0, <G, G - G_prev> / <G_prev, G_prev>), D = -G + beta D, and D = -G
+         whenever <G, D> >= 0.  (The paper does not name its CG variant.)
+      5. exact line search: coefficients of E~(W + x D), the quartic's minimum x.
+      6. W <- W + x D.
+    """
+    if eta is None:
+        eta = gershgorin_eta(H, S)
+    Hs = shift(H, S, eta)
+    n = W0.shape[1]
+    W = apply_mask(W0.copy() if not sp.issparse(W0) else W0.copy(), mask)
+    if sp.issparse(W):
+        W = sp.csr_matrix(W)
+    history = []
+    E_prev = None
+    G_prev = None
+    D = None
+    k = 0
+    status = OK
+    while True:
+        HW = Hs @ W
+        SW = S @ W
+        H_W = W.T @ HW
+        S_W = W.T @ SW
+        E = 2.0 * (2.0 * trace(H_W) - frob(S_W, H_W)) + 2.0 * eta * n
+        history.append(E)
+        orth = float(np.linalg.norm(_dense(S_W) - np.eye(n)))
+        if k >= 1:
+            rel = abs(2.0 * (E - E_prev) / (E + E_prev))
+            if rel < tol and (orth_tol is None or orth < orth_tol):
+                break
+        if k >= max_iter:
+            status = ERR_MAXITER
+            break
+        G = apply_mask(2.0 * (2.0 * HW - SW @ H_W - HW @ S_W), mask)
+        if D is None:
+            D = -G
+        else:
+            beta = max(0.0, frob(G, G - G_prev) / frob(G_prev, G_prev))
+            D = -G + beta * D
+            if frob(G, D) >= 0.0:
+                D = -G
+        c = quartic_coeffs(W, D, Hs, S)
+        x, st = line_min(c)
+        if st != OK:
+            status = st
+            break
+        W = W + x * D
+        E_prev = E
+        G_prev = G
+        k += 1
+    E_unshifted = functional(W, H, S)
+    return Result(W=W, E=E, E_unshifted=E_unshifted, iters=k, status=status, eta=eta,
+                  history=history, orth=orth)
+
+
+def omm_cg_cholesky(H, S, W0, tol: float = 1e-10, eta: float | None = None,
+                    max_iter: int = 10000, orth_tol: float | None = None) -> Result:
+    """Cholesky-reduced variant (dense only; section "Overview of OMM approaches").
+
+    S = L L^T reduces H C = S C Lambda to the standard problem with
+    H~ = L^-1 H' L^-T and overlap I; the CG runs on W~ = L^T W and the result
+    is mapped back with W = L^-T W~.  Same eta as the plain form.
+    """
+    H = _dense(H)
+    S = _dense(S)
+    if eta is None:
+        eta = gershgorin_eta(H, S)
+    L = sla.cholesky(S, lower=True)
+    Hs = shift(H, S, eta)
+    Ht = sla.solve_triangular(L, sla.solve_triangular(L, Hs, lower=True).T, lower=True).T
+    Ht = 0.5 * (Ht + Ht.T)
+    m = H.shape[0]
+    Wt0 = L.T @ np.asarray(W0)
+    res = omm_cg(Ht, np.eye(m), Wt0, tol=tol, eta=0.0, max_iter=max_iter, orth_tol=orth_tol)
+    W = sla.solve_triangular(L.T, res.W, lower=False)
+    n = W.shape[1]
+    return Result(W=W, E=res.E + 2.0 * eta * n, E_unshifted=functional(W, H, S),
+                  iters=res.iters, status=res.status, eta=eta,
+                  history=[e + 2.0 * eta * n for e in res.history], orth=res.orth)
+
+
+# ----------------------------------------------------------------------------
+# sparse-form helpers
+# ----------------------------------------------------------------------------
+def bsr_to_csr(rowptr, col, vals, nbrows: int, nbcols: int):
+    """Assemble a scipy CSR matrix from block-CSR arrays (blocks row-major)."""
+    bm, bn = vals.shape[1], vals.shape[2]
+    A = sp.bsr_matrix((vals, np.asarray(col, dtype=np.int64), np.asarray(rowptr, dtype=np.int64)),
+                      shape=(nbrows * bm, nbcols * bn))
+    return A.tocsr()
+
+
+def filter_blocks(vals, eps: float) -> np.ndarray:
+    """Keep-mask of input blocks whose Frobenius norm is at least eps.
+
+    The squared norm is summed in row-major element order, one rounded product
+    and one rounded add per element, and compared strictly: ||B||^2 < eps^2
+    drops the block (DBCSR-style block filtering).
+    """
+    flat = np.asarray(vals).reshape(vals.shape[0], -1)
+    s = np.zeros(flat.shape[0])
+    for t in range(flat.shape[1]):
+        s = s + flat[:, t] * flat[:, t]
+    return ~(s < eps * eps)
+
+
+def structural_pattern_product(rowptr_a, col_a, rowptr_b, col_b, nb_cols):
+    """Boolean block pattern of A*B (block CSR in, block CSR out, sorted)."""
+    na = rowptr_a.shape[0] - 1
+    Pa = sp.csr_matrix((np.ones(col_a.shape[0]), col_a, rowptr_a), shape=(na, rowptr_b.shape[0] - 1))
+    Pb = sp.csr_matrix((np.ones(col_b.shape[0]), col_b, rowptr_b), shape=(rowptr_b.shape[0] - 1, nb_cols))
+    P = (Pa @ Pb).tocsr()
+    P.sort_indices()
+    return P.indptr.astype(np.int64), P.indices.astype(np.int32)

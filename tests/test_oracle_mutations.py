@@ -1,0 +1,96 @@
+"""Planted mistakes in the oracle (on the CPU) must trip its pins.
+
+Each case swaps one oracle routine for a plausibly wrong variant (a dropped
+term, a flipped sign, a lost factor, a wrong root) and checks that the pin
+guarding that routine rejects it.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import omm as O
+
+
+@pytest.fixture(scope="module")
+def prob(small_system):
+    H, S = small_system.dense_H(), small_system.dense_S()
+    Hs = O.shift(H, S, O.gershgorin_eta(H, S))
+    W = small_system.W0_dense() * 2.0
+    D = np.random.default_rng(4).standard_normal(W.shape) * 0.05
+    return H, S, Hs, W, D, small_system.n
+
+
+def _fd_gradient_ok(grad, W, H, S):
+    G = grad(W, H, S)
+    h = 1e-5
+    rng = np.random.default_rng(1)
+    D = rng.standard_normal(W.shape)
+    fd = (O.functional(W + h * D, H, S) - O.functional(W - h * D, H, S)) / (2 * h)
+    return abs(fd - 2.0 * np.sum(G * D)) <= 1e-7 * abs(fd)
+
+
+def _interp_ok(coeffs, W, D, H, S):
+    c = coeffs(W, D, H, S)
+    xs = np.array([-2.0, -1.0, 0.0, 1.0, 2.0])
+    vals = np.array([O.functional(W + x * D, H, S) for x in xs])
+    fit = np.linalg.solve(np.vander(xs, 5, increasing=True), vals)
+    return np.allclose(c, fit, rtol=1e-9, atol=1e-9 * np.abs(vals).max())
+
+
+def test_pins_accept_the_oracle(prob):
+    H, S, Hs, W, D, n = prob
+    assert _fd_gradient_ok(O.gradient, W, Hs, S)
+    assert _interp_ok(O.quartic_coeffs, W, D, Hs, S)
+
+
+def test_dropped_gradient_term_is_caught(prob):
+    H, S, Hs, W, D, n = prob
+
+    def bad(W, H, S):
+        HW, SW = H @ W, S @ W
+        return 2.0 * (2.0 * HW - SW @ (W.T @ HW))          # lost -H W S_W
+    assert not _fd_gradient_ok(bad, W, Hs, S)
+
+
+def test_gradient_sign_error_is_caught(prob):
+    H, S, Hs, W, D, n = prob
+
+    def bad(W, H, S):
+        HW, SW = H @ W, S @ W
+        return 2.0 * (2.0 * HW - SW @ (W.T @ HW) + HW @ (W.T @ SW))
+    assert not _fd_gradient_ok(bad, W, Hs, S)
+
+
+def test_quartic_cross_term_error_is_caught(prob):
+    H, S, Hs, W, D, n = prob
+
+    def bad(W, D, H, S):
+        c = O.quartic_coeffs(W, D, H, S)
+        # forget the transposed half of W^T H D + D^T H W in the linear term
+        X = W.T @ H @ D
+        c = c.copy()
+        c[1] -= 2.0 * 2.0 * np.trace(X)
+        return c
+    assert not _interp_ok(bad, W, D, Hs, S)
+
+
+def test_functional_missing_spin_factor_is_caught(small_system):
+    H, S, n = small_system.dense_H(), small_system.dense_S(), small_system.n
+    lam, V = sla.eigh(H, S)
+    W = 0.7 * V[:, :n]
+
+    def bad(W, H, S):
+        return O.functional(W, H, S) / 2.0
+    expect = 2.0 * (2.0 * 0.49 - 0.7 ** 4) * lam[:n].sum()
+    assert bad(W, H, S) != pytest.approx(expect, rel=1e-6)
+
+
+def test_wrong_root_choice_is_caught():
+    p = np.polynomial.polynomial.polymul([1, -2, 1], [4, 4, 1])
+    c = np.array(p) + np.array([0, 0.5, 0, 0, 0])
+    roots = np.roots([4 * c[4], 3 * c[3], 2 * c[2], c[1]]).real
+    bad_x = max(roots)               # right-hand well, the higher minimum
+    grid = np.linspace(-4, 3, 700001)
+    best = grid[np.argmin(O.quartic(c, grid))]
+    assert abs(bad_x - best) > 1e-2
+    assert abs(O.line_min(c)[0] - best) < 1e-5

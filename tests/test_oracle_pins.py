@@ -1,0 +1,274 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these checks re-calls the oracle routine it pins: each compares it with
+a closed form, an independent library routine, a hand-written Jacobi solver,
+finite differences, exact interpolation or brute force.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle import jacobi
+from oracle import omm as O
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def _sym(rng, m):
+    A = rng.standard_normal((m, m))
+    return 0.5 * (A + A.T)
+
+
+# --------------------------------------------------------------- Jacobi solver
+def test_jacobi_closed_form_2x2():
+    a, b, c = 1.7, -0.4, -2.3
+    ev = jacobi.jacobi_eigenvalues([[a, b], [b, c]])
+    mid, rad = 0.5 * (a + c), math.sqrt(0.25 * (a - c) ** 2 + b * b)
+    assert ev == pytest.approx([mid - rad, mid + rad], abs=1e-14)
+
+
+def test_jacobi_known_spectrum_householder():
+    rng = np.random.default_rng(11)
+    m = 9
+    v = rng.standard_normal(m)
+    Q = np.eye(m) - 2.0 * np.outer(v, v) / (v @ v)          # exact reflector
+    lam = np.sort(rng.uniform(-5, 5, m))
+    A = Q @ np.diag(lam) @ Q.T
+    ev = jacobi.jacobi_eigenvalues(A.tolist())
+    np.testing.assert_allclose(ev, lam, atol=1e-12)
+
+
+def test_jacobi_generalized_vs_library():
+    rng = np.random.default_rng(5)
+    m = 12
+    H = _sym(rng, m)
+    X = rng.standard_normal((m, m))
+    S = X @ X.T / m + np.eye(m)
+    ev = jacobi.generalized_eigenvalues(H.tolist(), S.tolist())
+    ref = sla.eigh(H, S, eigvals_only=True)
+    np.testing.assert_allclose(ev, ref, atol=1e-11)
+
+
+# --------------------------------------------------------------- functional
+def test_functional_on_scaled_eigenvectors(small_system):
+    """W = a V with V the S-orthonormal lowest-n eigenvectors: S_W = a^2 I and
+    H_W = a^2 Lambda, so E~ = 2 (2 a^2 - a^4) sum(lambda)."""
+    H, S, n = small_system.dense_H(), small_system.dense_S(), small_system.n
+    lam, V = sla.eigh(H, S)
+    for a in (1.0, 0.7, 1.3):
+        W = a * V[:, :n]
+        expect = 2.0 * (2.0 * a * a - a ** 4) * lam[:n].sum()
+        assert O.functional(W, H, S) == pytest.approx(expect, rel=1e-12)
+        assert O.charge(W, S) == pytest.approx(2.0 * (2.0 * a * a - a ** 4) * n, rel=1e-12)
+
+
+def test_gradient_finite_differences(small_system):
+    H, S = small_system.dense_H(), small_system.dense_S()
+    rng = np.random.default_rng(2)
+    W = np.asfortranarray(small_system.W0_dense() * 3.0)
+    G = O.gradient(W, H, S)
+    h = 1e-5
+    for _ in range(12):
+        i, j = rng.integers(W.shape[0]), rng.integers(W.shape[1])
+        Wp, Wm = W.copy(), W.copy()
+        Wp[i, j] += h
+        Wm[i, j] -= h
+        fd = (O.functional(Wp, H, S) - O.functional(Wm, H, S)) / (2 * h)
+        assert fd == pytest.approx(2.0 * G[i, j], rel=1e-6, abs=1e-8)
+    # directional derivative along a random direction
+    D = rng.standard_normal(W.shape)
+    fd = (O.functional(W + h * D, H, S) - O.functional(W - h * D, H, S)) / (2 * h)
+    assert fd == pytest.approx(2.0 * np.sum(G * D), rel=1e-7)
+
+
+def test_gradient_mask_matches_pattern(small_system):
+    H, S = small_system.dense_H(), small_system.dense_S()
+    mask = small_system.w_mask(4.0)
+    assert 0 < mask.sum() < mask.size
+    W = small_system.W0_local(4.0)
+    G = O.gradient(W, H, S, mask=mask)
+    assert np.all(G[~mask] == 0.0)
+    np.testing.assert_array_equal(G[mask], O.gradient(W, H, S)[mask])
+
+
+# --------------------------------------------------------------- line search
+def test_quartic_coeffs_exact_interpolation(small_system):
+    """E~(W + x D) is a quartic: five samples determine it exactly."""
+    H, S = small_system.dense_H(), small_system.dense_S()
+    eta = O.gershgorin_eta(H, S)
+    Hs = O.shift(H, S, eta)
+    rng = np.random.default_rng(4)
+    W = small_system.W0_dense() * 2.0
+    D = rng.standard_normal(W.shape) * 0.05
+    c = O.quartic_coeffs(W, D, Hs, S)
+    xs = np.array([-2.0, -1.0, 0.0, 1.0, 2.0])
+    vals = np.array([O.functional(W + x * D, Hs, S) for x in xs])
+    V = np.vander(xs, 5, increasing=True)
+    fit = np.linalg.solve(V, vals)
+    np.testing.assert_allclose(c, fit, rtol=1e-9, atol=1e-9 * np.abs(vals).max())
+    assert c[0] == pytest.approx(O.functional(W, Hs, S), rel=1e-13)
+    G = O.gradient(W, Hs, S)
+    assert c[1] == pytest.approx(2.0 * np.sum(G * D), rel=1e-12)
+    assert c[4] >= 0.0          # shifted H' is negative semidefinite
+
+
+def test_line_min_against_dense_sampling(small_system):
+    H, S = small_system.dense_H(), small_system.dense_S()
+    Hs = O.shift(H, S, O.gershgorin_eta(H, S))
+    rng = np.random.default_rng(8)
+    W = small_system.W0_dense()
+    for trial in range(5):
+        D = -O.gradient(W, Hs, S) + 0.1 * rng.standard_normal(W.shape) * trial
+        c = O.quartic_coeffs(W, D, Hs, S)
+        x, st = O.line_min(c)
+        assert st == O.OK
+        grid = np.linspace(x - 4 * abs(x) - 1, x + 4 * abs(x) + 1, 200001)
+        qg = O.quartic(c, grid)
+        assert O.quartic(c, x) <= qg.min() + 1e-9 * abs(qg.min())
+        assert abs(grid[np.argmin(qg)] - x) <= 2 * (grid[1] - grid[0]) + 1e-6 * abs(x)
+        # the quartic value at x equals the functional sampled at W + x D
+        assert O.functional(W + x * D, Hs, S) == pytest.approx(O.quartic(c, x), rel=1e-10)
+
+
+def test_line_min_closed_forms():
+    # (x-1)^2 (x+2)^2 + 0.5 x: two wells, the left one is lower
+    p = np.polynomial.polynomial.polymul([1, -2, 1], [4, 4, 1])
+    c = np.array(p) + np.array([0, 0.5, 0, 0, 0])
+    x, st = O.line_min(c)
+    grid = np.linspace(-4, 3, 700001)
+    assert st == O.OK and x == pytest.approx(grid[np.argmin(O.quartic(c, grid))], abs=1e-5)
+    # parabola
+    x, st = O.line_min([3.0, -4.0, 2.0, 0.0, 0.0])
+    assert st == O.OK and x == pytest.approx(1.0)
+    # unbounded below: no minimum
+    assert O.line_min([0.0, -1.0, 1.0, 0.0, -1.0])[1] == O.ERR_LINESEARCH
+    assert O.line_min([0.0, -1.0, -1.0, 0.0, 0.0])[1] == O.ERR_LINESEARCH
+
+
+def test_gershgorin_bounds_spectrum(c1_system):
+    H, S = c1_system.dense_H(), c1_system.dense_S()
+    eta = O.gershgorin_eta(H, S)
+    lam = sla.eigh(H, S, eigvals_only=True)
+    assert eta >= lam[-1]
+    assert np.linalg.eigvalsh(O.shift(H, S, eta)).max() <= 1e-12
+
+
+# --------------------------------------------------------------- CG minimum
+def test_cg_reaches_jacobi_ground_state(tiny_system):
+    H, S, n = tiny_system.dense_H(), tiny_system.dense_S(), tiny_system.n
+    res = O.omm_cg(H, S, tiny_system.W0_dense(), tol=1e-15, max_iter=5000)
+    assert res.status in (O.OK, O.ERR_MAXITER)
+    lam = jacobi.generalized_eigenvalues(H.tolist(), S.tolist())
+    e_min = 2.0 * sum(lam[:n])
+    assert res.E == pytest.approx(e_min, rel=1e-11)
+    assert res.E_unshifted == pytest.approx(e_min, rel=1e-9)
+    S_W = res.W.T @ S @ res.W
+    assert np.linalg.norm(S_W - np.eye(n)) < 1e-6
+    assert O.charge(res.W, S) == pytest.approx(2 * n, rel=1e-10)
+    rho = O.density_matrix(res.W, S)
+    # (rho/2) S (rho/2) = rho/2: projector onto the occupied subspace
+    np.testing.assert_allclose(0.25 * rho @ S @ rho, 0.5 * rho, atol=1e-7)
+
+
+def test_cg_c1_energy_and_monotone(c1_system):
+    H, S, n = c1_system.dense_H(), c1_system.dense_S(), c1_system.n
+    res = O.omm_cg(H, S, c1_system.W0_dense(), tol=1e-12)
+    assert res.status == O.OK
+    e_min = 2.0 * sla.eigh(H, S, eigvals_only=True)[:n].sum()
+    assert res.E == pytest.approx(e_min, rel=1e-10)
+    hist = np.array(res.history)
+    assert np.all(np.diff(hist) <= 1e-12 * np.abs(hist[1:]))
+
+
+def test_cholesky_variant_same_minimum(small_system):
+    H, S, n = small_system.dense_H(), small_system.dense_S(), small_system.n
+    a = O.omm_cg(H, S, small_system.W0_dense(), tol=1e-14)
+    b = O.omm_cg_cholesky(H, S, small_system.W0_dense(), tol=1e-14)
+    assert b.E == pytest.approx(a.E, rel=1e-11)
+    np.testing.assert_allclose(O.density_matrix(b.W, S), O.density_matrix(a.W, S), atol=1e-6)
+
+
+# --------------------------------------------------------------- linear-scaling form
+def _sparse_inputs(sysm, radius):
+    rp, col, Hv, Sv = sysm.bsr()
+    N = sysm.natoms
+    H = O.bsr_to_csr(rp, col, Hv, N, N)
+    S = O.bsr_to_csr(rp, col, Sv, N, N)
+    mask = sp.csr_matrix(sysm.w_mask(radius).astype(np.float64))
+    W0 = sp.csr_matrix(sysm.W0_local(radius))
+    return H, S, W0, mask
+
+
+def test_sparse_full_pattern_equals_dense(small_system):
+    H, S, _, _ = _sparse_inputs(small_system, 100.0)
+    W0 = small_system.W0_dense()
+    mask = sp.csr_matrix(np.ones(W0.shape))
+    a = O.omm_cg(H, S, sp.csr_matrix(W0), tol=1e-13, mask=mask)
+    b = O.omm_cg(small_system.dense_H(), small_system.dense_S(), W0, tol=1e-13)
+    assert a.iters == b.iters
+    assert a.E == pytest.approx(b.E, rel=1e-12)
+
+
+def test_sparse_types_match_dense_masked():
+    """The scipy.sparse path and the dense-with-mask path give the same iterates."""
+    import synth
+    sysm = synth.make_system(3, 3, 2, seed=2)
+    Hs, Ss, W0, mask = _sparse_inputs(sysm, 3.6)
+    a = O.omm_cg(Hs, Ss, W0, tol=0.0, max_iter=40, mask=mask)
+    b = O.omm_cg(sysm.dense_H(), sysm.dense_S(), sysm.W0_local(3.6), tol=0.0, max_iter=40,
+                 mask=sysm.w_mask(3.6))
+    assert a.iters == b.iters == 40
+    np.testing.assert_allclose(a.history, b.history, rtol=1e-12)
+    np.testing.assert_allclose(a.W.toarray(), b.W, atol=1e-12)
+
+
+def test_truncated_minimum_is_variational():
+    """The localised minimum lies above the dense one and drops as R_C grows
+    (cf. the truncation-error study, Fig. 10)."""
+    import synth
+    sysm = synth.make_system(3, 3, 2, seed=2)
+    H, S, n = sysm.dense_H(), sysm.dense_S(), sysm.n
+    e_dense = 2.0 * sla.eigh(H, S, eigvals_only=True)[:n].sum()
+    energies = []
+    for radius in (2.8, 3.6, 4.5):
+        mask = sysm.w_mask(radius)
+        res = O.omm_cg(H, S, sysm.W0_local(radius), tol=1e-10, mask=mask, max_iter=4000)
+        assert res.status == O.OK
+        assert np.all(res.W[~mask] == 0.0)
+        energies.append(res.E)
+    assert energies[0] > energies[1] > energies[2] > e_dense
+
+
+def test_truncated_minimum_stationary_brute_force():
+    """At the localised minimum the functional is flat along every allowed
+    entry (finite differences), and not along a forbidden one."""
+    import synth
+    sysm = synth.make_system(2, 2, 2, seed=1)
+    H, S = sysm.dense_H(), sysm.dense_S()
+    mask = sysm.w_mask(3.0)
+    assert 0 < mask.sum() < mask.size
+    res = O.omm_cg(H, S, sysm.W0_local(3.0), tol=1e-15, max_iter=6000, mask=mask)
+    Hsh = O.shift(H, S, res.eta)
+    W = res.W
+    rng = np.random.default_rng(0)
+    idx = np.argwhere(mask)
+    h = 1e-5
+    for i, j in idx[rng.choice(len(idx), 10, replace=False)]:
+        Wp, Wm = W.copy(), W.copy()
+        Wp[i, j] += h
+        Wm[i, j] -= h
+        fd = (O.functional(Wp, Hsh, S) - O.functional(Wm, Hsh, S)) / (2 * h)
+        assert abs(fd) < 1e-5
+    G_full = O.gradient(W, Hsh, S)
+    assert np.abs(G_full[~mask]).max() > 1e-2
+
+
+def test_block_filter_threshold():
+    vals = np.zeros((3, 2, 2))
+    vals[0, 0, 0] = 1e-9                     # ||B|| = 1e-9 < 1e-8: dropped
+    vals[1, 1, 1] = 1e-8                     # exactly eps: kept (strict comparison)
+    vals[2] = 0.3
+    assert list(O.filter_blocks(vals, 1e-8)) == [False, True, True]
