@@ -1,0 +1,220 @@
+/*
+ * omm.h -- C ABI of the GB300 orbital-minimization (OMM) library.
+ *
+ * The library minimises the Ordejon-Mauri energy functional
+ *     E~(W) = 2 Tr[(2 I - W^T S W) W^T H W]                  (Eq. 5)
+ * over the m x n coefficient matrix W (the paper's C) by conjugate gradients
+ * with an exact quartic line search (Introduction; section "Solver library").
+ * H is the m x m Hamiltonian, S the m x m overlap matrix (both symmetric, S
+ * positive definite), n the number of occupied orbitals.  Two forms exist:
+ * dense (cubic scaling) and block sparse with a localisation pattern fixed
+ * on W (linear scaling, section "Solver library": the gradient is kept on
+ * the sparsity pattern of the initial W).
+ *
+ * Conventions for every entry point:
+ *   - dense matrices are column-major; W is m x n with leading dimension m
+ *     (orbital j occupies W[j*m .. j*m+m-1], i.e. the paper's C^dagger in
+ *     row-major order);
+ *   - block-sparse values are stored block after block in the pattern's CSR
+ *     order, each block row-major;
+ *   - every function returns an int status: OMM_OK (0) or a negative OMM_ERR_*
+ *     code; no function aborts the process; on error, outputs are left
+ *     untouched unless the description says otherwise;
+ *   - the caller owns every pointer it passes; the library copies what it
+ *     keeps and never frees caller memory;
+ *   - "stream" arguments are cudaStream_t values passed as void*; NULL means
+ *     the legacy default stream for op-level calls and a library-owned stream
+ *     for handles.
+ * A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef OMM_GB300_H
+#define OMM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum {
+    OMM_OK = 0,
+    OMM_ERR_ARG = -1,          /* invalid argument (sizes, NULL pointer, layout) */
+    OMM_ERR_NOMEM = -2,        /* device or pinned host allocation failed */
+    OMM_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    OMM_ERR_NOT_SPD = -4,      /* S is not positive definite (Cholesky pivot <= 0,
+                                  or no Gershgorin lower bound for eta_auto) */
+    OMM_ERR_LINESEARCH = -5,   /* the quartic along the search line has no minimum
+                                  (section "Recommendations for OMM solver use") */
+    OMM_ERR_MAXITER = -6,      /* max_iter CG steps without meeting the tolerance;
+                                  W, E and iters still describe the last iterate */
+    OMM_ERR_PATTERN = -7,      /* sparsity pattern malformed or inconsistent */
+    OMM_ERR_NONFINITE = -8,    /* NaN or Inf in the energy or line-search data */
+    OMM_ERR_TIMEOUT = -9,      /* a bounded device-side wait gave up */
+    OMM_ERR_STATE = -10,       /* call out of order (e.g. solve before set_HS) */
+    OMM_ERR_UNSUPPORTED = -11  /* option combination not available */
+};
+
+/* arithmetic of the solve */
+enum {
+    OMM_PREC_FP64 = 0,   /* every product in FP64 */
+    OMM_PREC_MIXED = 1   /* BF16-split tensor-core products for the bulk of the
+                            CG, FP64 state, then an accurate refinement sweep */
+};
+
+typedef struct omm_handle omm_handle;
+
+/*
+ * Block-sparse pattern for the linear-scaling form.  H and S share one
+ * pattern of bm x bm blocks; W uses bm x bn blocks (basis atom x orbitals of
+ * one host atom).  Block rows index basis atoms; nbr = m / bm; W has nbc =
+ * n / bn block columns.  Column indices must be sorted and unique within
+ * each block row.  Arrays are host memory, read during omm_create only.
+ */
+typedef struct {
+    int32_t bm, bn;
+    int64_t nbr, nbc;
+    const int64_t *H_rowptr;   /* nbr + 1 */
+    const int32_t *H_col;      /* H_rowptr[nbr] */
+    const int64_t *W_rowptr;   /* nbr + 1 */
+    const int32_t *W_col;      /* W_rowptr[nbr], values in [0, nbc) */
+} omm_pattern;
+
+typedef struct {
+    double eta;            /* Kim shift H' = H - eta S (n' = n); used when eta_auto == 0 */
+    int32_t eta_auto;      /* 1 (default): eta = Gershgorin upper bound of the spectrum,
+                              which makes every line-search quartic bounded below */
+    int32_t precision;     /* OMM_PREC_FP64 (default) or OMM_PREC_MIXED (dense only) */
+    int32_t cholesky;      /* 1: Cholesky-reduced variant (dense only), S = L L^T */
+    int32_t max_iter;      /* CG step limit, default 10000 */
+    double orth_tol;       /* > 0: also require ||W^T S W - I||_F < orth_tol to stop */
+    double filter_eps;     /* block filtering threshold on Frobenius norms, default 1e-8:
+                              input blocks with ||B||_F < eps are dropped from the stored
+                              pattern; block products with ||A_ik|| ||B_kj|| < eps are
+                              skipped (screening never changes a stored pattern) */
+    void *stream;          /* cudaStream_t for all work of the handle, NULL = own stream */
+} omm_options;
+
+typedef struct {
+    double E;              /* energy of the final iterate: E~_eta + 2 eta n, where E~_eta
+                              is Eq. 5 with H' (equals E~ with H at the dense minimum) */
+    double E_rel_change;   /* last |2 (E_k - E_{k-1}) / (E_k + E_{k-1})| (Table 1, RelTol) */
+    double orth;           /* ||W^T S W - I||_F at the final iterate */
+    double charge;         /* 2 Tr[(2 I - S_W) S_W] (Listing 1) */
+    double eta;            /* shift actually used */
+    int32_t iters;         /* CG steps taken in the last solve */
+    int32_t status;        /* status of the last solve */
+    int32_t iters_mixed;   /* steps taken with split-precision products */
+    int32_t iters_refine;  /* steps taken in the accurate refinement sweep */
+    double t_setup_ms;     /* device time of the last omm_set_HS */
+    double t_solve_ms;     /* device time of the last omm_solve */
+    int64_t nnzb_H;        /* stored blocks of H/S after filtering (sparse) */
+    int64_t nnzb_W;        /* blocks of W's pattern (sparse) */
+    int64_t nnzb_HW;       /* blocks of the structural pattern of H W (sparse) */
+    int64_t nnzb_N;        /* blocks of the structural pattern of W^T H W (sparse) */
+} omm_diag;
+
+/* Fill *opt with the defaults listed above. */
+void omm_default_options(omm_options *opt);
+
+/*
+ * Create a solver for an m x n problem.  block_size is the basis block size
+ * bm (atom block of H and S); for the dense form it only has to divide
+ * nothing and may be 0.  pattern == NULL selects the dense form; otherwise
+ * the pattern is validated (OMM_ERR_PATTERN) and copied.  opt == NULL takes
+ * the defaults.  All device memory of the handle is allocated here
+ * (OMM_ERR_NOMEM on failure).  *out receives the handle on OMM_OK.
+ */
+int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *pattern,
+               const omm_options *opt, omm_handle **out);
+
+/*
+ * Load H and S (section "Solver input and output": H and S are the solver's
+ * input at every SCF step).  Dense: column-major m x m arrays (symmetric, so
+ * row-major is the same).  Sparse: block values in the pattern's order.
+ * on_device != 0: H and S are device pointers; else host pointers.
+ * Runs the per-(H,S) setup on the device: the shift H' = H - eta S (with the
+ * Gershgorin eta when eta_auto), block filtering (sparse), Cholesky reduction
+ * (when selected).  The previous solution W stays resident for warm starts.
+ */
+int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_device);
+
+/*
+ * Minimise from W0 (m x n column-major; sparse: 8x2-style block values in the
+ * W pattern's order) to the RelTol criterion of Table 1:
+ *     |2 (E_k - E_{k-1}) / (E_k + E_{k-1})| < tol   at k >= 1,
+ * plus ||S_W - I||_F < orth_tol when orth_tol > 0.  W0 == NULL warm-starts from
+ * the resident W of the previous solve (OMM_ERR_STATE if there is none).
+ * W_out (nullable) receives the final W in the layout of W0; E_out and
+ * iters_out (nullable) receive the energy and the number of CG steps.  On
+ * OMM_ERR_MAXITER the outputs describe the last iterate.
+ */
+int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
+              double *W_out, int32_t W_out_on_device, double *E_out, int32_t *iters_out);
+
+/* Diagnostics of the last set_HS / solve. */
+int omm_get_diag(omm_handle *h, omm_diag *d);
+
+/*
+ * Copy one internal m x n or n x n FP64 array of the handle (for inspection
+ * and tests).  which: 0 W, 1 H'W, 2 S W, 3 G, 4 D, 5 H_W (n x n), 6 S_W (n x n).
+ * Dense only; dst is host memory unless on_device.
+ */
+int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device);
+
+void omm_destroy(omm_handle *h);
+const char *omm_status_str(int status);
+
+/* ------------------------------------------------------------------------
+ * Op-level entry points: single steps of the hot path on caller-owned device
+ * memory, enqueued on `stream`, asynchronous.  They allocate nothing.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * FP64 GEMM  C = alpha op(A) op(B) + beta Cin  (the products H D, S D, W^T H D,
+ * S W H_W + H W S_W of the CG step, section "Solver library").  Column-major;
+ * op(X) = X or X^T (trans != 0); M, N, K >= 0; leading dimensions >= the
+ * stored row counts.  Cin may equal C; beta == 0 ignores Cin.
+ */
+int omm_op_dgemm(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K,
+                 double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
+                 double beta, const double *Cin, int64_t ldcin, double *C, int64_t ldc,
+                 void *stream);
+
+/*
+ * Coefficients c[0..4] of the line-search quartic E~_eta(W + x D) (Introduction:
+ * the quartic's parameters are computed analytically), from the n x n blocks
+ *   h0 = W^T H' W, s0 = W^T S W, X = W^T H' D, Y = W^T S D, h2 = D^T H' D, s2 = D^T S D:
+ *   c0 = 2 [2 tr h0 - <s0,h0>]
+ *   c1 = 2 [4 tr X - 2 <s0,X> - 2 <Y,h0>]
+ *   c2 = 2 [2 tr h2 - <s0,h2> - 2 <Y,X> - 2 <Y,X^T> - <s2,h0>]
+ *   c3 = 2 [-2 <Y,h2> - 2 <s2,X>]
+ *   c4 = -2 <s2,h2>
+ * (<A,B> = sum_ij A_ij B_ij; h0, s0, h2, s2 symmetric).  All six inputs are
+ * device n x n column-major arrays with leading dimensions ld_h (h0, s0) and
+ * ld_z (X, Y, h2, s2).  coeffs: 5 doubles of device memory.  scratch: device
+ * memory of at least omm_op_quartic_coeffs_scratch_bytes(n) bytes, 16-byte
+ * aligned, holding per-block partial sums and a completion counter that must
+ * be zero on entry (cudaMemset once; the kernel leaves it zero again).
+ * Reduction order is fixed: equal inputs give bitwise equal coefficients.
+ */
+int64_t omm_op_quartic_coeffs_scratch_bytes(int64_t n);
+int omm_op_quartic_coeffs(int64_t n, const double *h0, const double *s0, int64_t ld_h,
+                          const double *X, const double *Y, const double *h2,
+                          const double *s2, int64_t ld_z, double *coeffs, void *scratch,
+                          int64_t scratch_bytes, void *stream);
+
+/*
+ * Minimiser x of c0 + c1 x + ... + c4 x^4 (device coeffs, 5 doubles) into
+ * *x_out (device double) and a status (device int32: OMM_OK, OMM_ERR_LINESEARCH
+ * when the quartic has no minimum, OMM_ERR_NONFINITE).  Candidates are the
+ * real roots of the derivative with positive curvature; the lowest value
+ * wins, ties go to the smaller |x|, then to x > 0.
+ */
+int omm_op_line_min(const double *coeffs, double *x_out, int32_t *status_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OMM_GB300_H */

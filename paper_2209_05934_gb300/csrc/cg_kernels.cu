@@ -1,0 +1,630 @@
+// Reductions, line search and CG updates of the OMM step (FP64 state).
+//
+// Every reduction uses a fixed number of blocks for a given size, a fixed
+// per-thread traversal, warp-shuffle trees and a "last block" that sums the
+// per-block partials in block order, so equal inputs give bitwise equal
+// results (needed for the batched and serving forms, whose results must not
+// depend on what else runs).
+#include <math.h>
+
+#include "omm_internal.cuh"
+
+namespace omm {
+namespace {
+
+constexpr int NT = 256;
+constexpr int TILE = 32;
+
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *red /* smem NV*8 */) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = v[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        v[q] = s;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[warp * NV + q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += red[w * NV + q];
+            v[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Publish this block's NV partials; returns true in the last block to finish,
+// whose thread 0 then holds the block-ordered totals in `tot`.
+template <int NV>
+__device__ bool publish_and_collect(const double (&v)[NV], double *partials, unsigned int *counter,
+                                    double (&tot)[NV]) {
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) partials[blockIdx.x * NV + q] = v[q];
+        __threadfence();
+        const unsigned prev = atomicAdd(counter, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        volatile const double *p = partials;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) tot[q] = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) tot[q] += p[b * NV + q];
+        *counter = 0u;
+    }
+    return true;
+}
+
+__device__ inline bool finite(double x) { return isfinite(x); }
+
+__device__ inline double quartic_val(const double *c, double x) {
+    return c[0] + x * (c[1] + x * (c[2] + x * (c[3] + x * c[4])));
+}
+
+// Real roots of a x^3 + b x^2 + c x + d (a > 0): one root by safeguarded
+// Newton/bisection on the Cauchy bracket, deflation, a stable quadratic
+// formula for the rest, then Newton polishing of every root.
+__device__ int cubic_real_roots(double a, double b, double c, double d, double *r) {
+    auto f = [&](double x) { return ((a * x + b) * x + c) * x + d; };
+    auto fp = [&](double x) { return (3.0 * a * x + 2.0 * b) * x + c; };
+    const double R = 1.0 + fmax(fabs(b), fmax(fabs(c), fabs(d))) / a;
+    double lo = -R, hi = R;   // f(lo) < 0 < f(hi)
+    double x = 0.0;
+    for (int it = 0; it < 400; ++it) {
+        const double fx = f(x);
+        if (fx == 0.0) break;
+        if (fx < 0.0) lo = x; else hi = x;
+        const double dx = fp(x);
+        double xn = (dx != 0.0) ? x - fx / dx : 0.5 * (lo + hi);
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (xn == x || hi - lo <= 4e-16 * fmax(1.0, fabs(x))) { x = xn; break; }
+        x = xn;
+    }
+    int nr = 0;
+    r[nr++] = x;
+    // a x^3 + b x^2 + c x + d = (x - x1)(a x^2 + p x + q)
+    const double p = b + a * x;
+    const double q = c + p * x;
+    const double disc = p * p - 4.0 * a * q;
+    if (disc >= 0.0) {
+        const double sq = sqrt(disc);
+        const double t = -0.5 * (p + (p >= 0.0 ? sq : -sq));
+        if (t != 0.0) {
+            r[nr++] = t / a;
+            r[nr++] = q / t;
+        } else {
+            r[nr++] = 0.0;
+        }
+    }
+    for (int i = 0; i < nr; ++i) {
+        for (int it = 0; it < 3; ++it) {
+            const double dx = fp(r[i]);
+            if (dx == 0.0) break;
+            const double xn = r[i] - f(r[i]) / dx;
+            if (!isfinite(xn)) break;
+            if (fabs(f(xn)) <= fabs(f(r[i]))) r[i] = xn; else break;
+        }
+    }
+    return nr;
+}
+
+// Minimiser of the quartic c0 + c1 x + ... + c4 x^4; returns status.
+__device__ int quartic_min(const double *c, double *xout) {
+    for (int i = 0; i < 5; ++i)
+        if (!finite(c[i])) return OMM_ERR_NONFINITE;
+    if (c[4] == 0.0 && c[3] == 0.0) {
+        if (c[2] > 0.0) { *xout = -c[1] / (2.0 * c[2]); return OMM_OK; }
+        return OMM_ERR_LINESEARCH;
+    }
+    if (c[4] < 0.0) return OMM_ERR_LINESEARCH;
+    double r[3];
+    int nr;
+    if (c[4] > 0.0) {
+        nr = cubic_real_roots(4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1], r);
+    } else {
+        // c4 == 0, c3 != 0: derivative 3 c3 x^2 + 2 c2 x + c1
+        const double a = 3.0 * c[3], b = 2.0 * c[2], cc = c[1];
+        const double disc = b * b - 4.0 * a * cc;
+        nr = 0;
+        if (disc >= 0.0) {
+            const double sq = sqrt(disc);
+            const double t = -0.5 * (b + (b >= 0.0 ? sq : -sq));
+            if (t != 0.0) { r[nr++] = t / a; r[nr++] = cc / t; }
+        }
+    }
+    bool have = false;
+    double best = 0.0, bestv = 0.0;
+    for (int pass = 0; pass < 2 && !have; ++pass) {
+        for (int i = 0; i < nr; ++i) {
+            const double x = r[i];
+            if (!finite(x)) continue;
+            const double curv = 12.0 * c[4] * x * x + 6.0 * c[3] * x + 2.0 * c[2];
+            if (pass == 0 && !(curv > 0.0)) continue;
+            if (pass == 1 && !(c[4] > 0.0)) continue;
+            const double v = quartic_val(c, x);
+            bool better = !have || v < bestv ||
+                          (v == bestv && (fabs(x) < fabs(best) || (fabs(x) == fabs(best) && x > best)));
+            if (better) { have = true; best = x; bestv = v; }
+        }
+    }
+    if (!have) return OMM_ERR_LINESEARCH;
+    *xout = best;
+    return OMM_OK;
+}
+
+// ---------------------------------------------------------------- coefficients
+// partial sums: 0 tr h0, 1 <s0,h0>, 2 tr X, 3 <s0,X>, 4 <Y,h0>, 5 tr h2, 6 <s0,h2>,
+// 7 <Y,X>, 8 <Y,X^T>, 9 <s2,h0>, 10 <Y,h2>, 11 <s2,X>, 12 <s2,h2>
+constexpr int NC = 13;
+
+__global__ void __launch_bounds__(NT) coeffs_kernel(int n, const double *__restrict__ h0,
+                                                     const double *__restrict__ s0, int64_t ldh,
+                                                     const double *__restrict__ X,
+                                                     const double *__restrict__ Y,
+                                                     const double *__restrict__ h2,
+                                                     const double *__restrict__ s2, int64_t ldz,
+                                                     double *partials, unsigned int *counter,
+                                                     DevState *state, double *coeffs_out,
+                                                     int do_linemin) {
+    if (state != nullptr && *((volatile int *)&state->done)) return;
+    __shared__ double Xt[TILE][TILE + 1];
+    __shared__ double red[(NT / 32) * NC];
+    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int T = (n + TILE - 1) / TILE;
+    const int64_t ntiles = (int64_t)T * T;
+    double v[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) v[q] = 0.0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ti = (int)(t % T), tj = (int)(t / T);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int a = ly + 8 * r;
+            const int64_t gi = (int64_t)tj * TILE + lx, gj = (int64_t)ti * TILE + a;
+            Xt[a][lx] = (gi < n && gj < n) ? X[gi + gj * ldz] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t i = (int64_t)ti * TILE + lx, j = (int64_t)tj * TILE + ly + 8 * r;
+            if (i >= n || j >= n) continue;
+            const double vh0 = h0[i + j * ldh], vs0 = s0[i + j * ldh];
+            const double vx = X[i + j * ldz], vy = Y[i + j * ldz];
+            const double vh2 = h2[i + j * ldz], vs2 = s2[i + j * ldz];
+            const double vxt = Xt[lx][ly + 8 * r];
+            if (i == j) { v[0] += vh0; v[2] += vx; v[5] += vh2; }
+            v[1] = fma(vs0, vh0, v[1]);
+            v[3] = fma(vs0, vx, v[3]);
+            v[4] = fma(vy, vh0, v[4]);
+            v[6] = fma(vs0, vh2, v[6]);
+            v[7] = fma(vy, vx, v[7]);
+            v[8] = fma(vy, vxt, v[8]);
+            v[9] = fma(vs2, vh0, v[9]);
+            v[10] = fma(vy, vh2, v[10]);
+            v[11] = fma(vs2, vx, v[11]);
+            v[12] = fma(vs2, vh2, v[12]);
+        }
+    }
+    block_sum<NC>(v, red);
+    double tot[NC];
+    if (!publish_and_collect<NC>(v, partials, counter, tot)) return;
+    if (threadIdx.x != 0) return;
+    double c[5];
+    c[0] = 2.0 * (2.0 * tot[0] - tot[1]);
+    c[1] = 2.0 * (4.0 * tot[2] - 2.0 * tot[3] - 2.0 * tot[4]);
+    c[2] = 2.0 * (2.0 * tot[5] - tot[6] - 2.0 * (tot[7] + tot[8]) - tot[9]);
+    c[3] = 2.0 * (-2.0 * tot[10] - 2.0 * tot[11]);
+    c[4] = -2.0 * tot[12];
+    if (coeffs_out != nullptr)
+        for (int q = 0; q < 5; ++q) coeffs_out[q] = c[q];
+    if (state != nullptr) {
+        for (int q = 0; q < 5; ++q) state->c[q] = c[q];
+        if (do_linemin) {
+            double x = 0.0;
+            const int st = quartic_min(c, &x);
+            state->x = x;
+            if (st != OMM_OK) {
+                state->status = st;
+                state->done = 1;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- n x n update + energy
+// partials: 0 tr h0, 1 <s0,h0>, 2 ||s0 - I||^2
+constexpr int NE = 3;
+
+__global__ void __launch_bounds__(NT) nn_update_kernel(int n, double *h0, double *s0, int64_t ldh,
+                                                        const double *__restrict__ X,
+                                                        const double *__restrict__ Y,
+                                                        const double *__restrict__ h2,
+                                                        const double *__restrict__ s2,
+                                                        int64_t ldz, double *partials,
+                                                        unsigned int *counter, DevState *state,
+                                                        int mode) {
+    if (*((volatile int *)&state->done)) return;
+    __shared__ double Tt[4][TILE][TILE + 1];
+    __shared__ double red[(NT / 32) * NE];
+    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int T = (n + TILE - 1) / TILE;
+    const int64_t ntiles = (int64_t)T * T;
+    const double x = state->x;
+    double v[NE] = {0.0, 0.0, 0.0};
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ti = (int)(t % T), tj = (int)(t / T);
+        if (mode == 0) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int a = ly + 8 * r;
+                const int64_t gi = (int64_t)tj * TILE + lx, gj = (int64_t)ti * TILE + a;
+                const bool in = gi < n && gj < n;
+                Tt[0][a][lx] = in ? X[gi + gj * ldz] : 0.0;
+                Tt[1][a][lx] = in ? Y[gi + gj * ldz] : 0.0;
+                Tt[2][a][lx] = in ? h2[gi + gj * ldz] : 0.0;
+                Tt[3][a][lx] = in ? s2[gi + gj * ldz] : 0.0;
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t i = (int64_t)ti * TILE + lx, j = (int64_t)tj * TILE + ly + 8 * r;
+            if (i >= n || j >= n) continue;
+            double vh = h0[i + j * ldh], vs = s0[i + j * ldh];
+            if (mode == 0) {
+                const int b = ly + 8 * r;
+                const double xs = X[i + j * ldz] + Tt[0][lx][b];
+                const double ys = Y[i + j * ldz] + Tt[1][lx][b];
+                const double h2s = 0.5 * (h2[i + j * ldz] + Tt[2][lx][b]);
+                const double s2s = 0.5 * (s2[i + j * ldz] + Tt[3][lx][b]);
+                vh = vh + x * (xs + x * h2s);
+                vs = vs + x * (ys + x * s2s);
+                h0[i + j * ldh] = vh;
+                s0[i + j * ldh] = vs;
+            }
+            if (i == j) v[0] += vh;
+            v[1] = fma(vs, vh, v[1]);
+            const double e = vs - (i == j ? 1.0 : 0.0);
+            v[2] = fma(e, e, v[2]);
+        }
+    }
+    block_sum<NE>(v, red);
+    double tot[NE];
+    if (!publish_and_collect<NE>(v, partials, counter, tot)) return;
+    if (threadIdx.x != 0) return;
+    const double E = 2.0 * (2.0 * tot[0] - tot[1]) + 2.0 * state->eta * (double)n;
+    state->trh0 = tot[0];
+    state->sh = tot[1];
+    state->orth2 = tot[2];
+    if (!isfinite(E)) {
+        state->status = OMM_ERR_NONFINITE;
+        state->done = 1;
+        state->E = E;
+        return;
+    }
+    if (mode == 1) {
+        state->E = E;
+        state->E_prev = E;
+        state->rel = 0.0;
+        if (state->max_iter <= 0) {
+            state->status = OMM_ERR_MAXITER;
+            state->done = 1;
+        }
+        return;
+    }
+    const double Ep = state->E;
+    const double rel = fabs(2.0 * (E - Ep) / (E + Ep));
+    state->E_prev = Ep;
+    state->E = E;
+    state->rel = rel;
+    state->k += 1;
+    const bool orth_ok = !(state->orth_tol > 0.0) || sqrt(tot[2]) < state->orth_tol;
+    if (rel < state->tol && orth_ok) {
+        state->status = OMM_OK;
+        state->done = 1;
+    } else if (state->k >= state->max_iter) {
+        state->status = OMM_ERR_MAXITER;
+        state->done = 1;
+    }
+}
+
+// ---------------------------------------------------------------- m x n kernels
+__global__ void axpy3_kernel(int64_t mn, double *W, const double *__restrict__ D, double *HW,
+                             const double *__restrict__ HD, double *SW,
+                             const double *__restrict__ SD, const DevState *state) {
+    if (*((volatile const int *)&state->done)) return;
+    const double x = state->x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mn;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        W[i] = fma(x, D[i], W[i]);
+        HW[i] = fma(x, HD[i], HW[i]);
+        SW[i] = fma(x, SD[i], SW[i]);
+    }
+}
+
+constexpr int ND = 3;   // <G,G>, <G,Gp>, <G,D>
+
+__global__ void __launch_bounds__(NT) dots_kernel(int64_t mn, const double *__restrict__ G,
+                                                   const double *__restrict__ Gp,
+                                                   const double *__restrict__ D, double *partials,
+                                                   unsigned int *counter, DevState *state,
+                                                   int first) {
+    if (*((volatile int *)&state->done)) return;
+    __shared__ double red[(NT / 32) * ND];
+    double v[ND] = {0.0, 0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < mn; i += (int64_t)gridDim.x * NT) {
+        const double g = G[i];
+        v[0] = fma(g, g, v[0]);
+        if (!first) {
+            v[1] = fma(g, Gp[i], v[1]);
+            v[2] = fma(g, D[i], v[2]);
+        }
+    }
+    block_sum<ND>(v, red);
+    double tot[ND];
+    if (!publish_and_collect<ND>(v, partials, counter, tot)) return;
+    if (threadIdx.x != 0) return;
+    const double gg = tot[0];
+    double beta = 0.0;
+    int restart = 1;
+    if (!first) {
+        const double gpgp = state->gg_prev;
+        beta = (gpgp > 0.0) ? fmax(0.0, (gg - tot[1]) / gpgp) : 0.0;
+        // <G, -G + beta D> >= 0 means no descent: restart with -G
+        restart = (-gg + beta * tot[2] >= 0.0) ? 1 : 0;
+        if (restart) beta = 0.0;
+    }
+    if (!isfinite(gg) || !isfinite(beta)) {
+        state->status = OMM_ERR_NONFINITE;
+        state->done = 1;
+        return;
+    }
+    state->gg = gg;
+    state->ggp = tot[1];
+    state->gd = tot[2];
+    state->gg_prev = gg;
+    state->beta = beta;
+    state->restart = restart;
+}
+
+__global__ void direction_kernel(int64_t mn, const double *__restrict__ G, double *Gp, double *D,
+                                 const DevState *state) {
+    if (*((volatile const int *)&state->done)) return;
+    const double beta = state->beta;
+    const bool restart = state->restart != 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mn;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double g = G[i];
+        D[i] = restart ? -g : fma(beta, D[i], -g);
+        Gp[i] = g;
+    }
+}
+
+__global__ void shift_kernel(int64_t mm, const double *H, const double *__restrict__ S, double *Hs,
+                             const DevState *state) {
+    const double eta = state->eta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mm;
+         i += (int64_t)gridDim.x * blockDim.x)
+        Hs[i] = H[i] - eta * S[i];
+}
+
+// per column j (= row j, symmetric): g = H_jj + sum_{i!=j} |H_ij|,
+// lo = S_jj - sum_{i!=j} |S_ij|, hi = S_jj + sum_{i!=j} |S_ij|; then max/min.
+__global__ void __launch_bounds__(NT) gershgorin_kernel(int64_t m, const double *__restrict__ H,
+                                                         const double *__restrict__ S,
+                                                         double *partials, unsigned int *counter,
+                                                         DevState *state) {
+    __shared__ double red[(NT / 32) * 3];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+    double gmax = -INFINITY, lomin = INFINITY, himax = -INFINITY;
+    for (int64_t j = warp; j < m; j += nwarps) {
+        double sh = 0.0, ss = 0.0;
+        for (int64_t i = lane; i < m; i += 32) {
+            if (i == j) continue;
+            sh += fabs(H[i + j * m]);
+            ss += fabs(S[i + j * m]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sh += __shfl_down_sync(0xffffffffu, sh, off);
+            ss += __shfl_down_sync(0xffffffffu, ss, off);
+        }
+        if (lane == 0) {
+            gmax = fmax(gmax, H[j + j * m] + sh);
+            lomin = fmin(lomin, S[j + j * m] - ss);
+            himax = fmax(himax, S[j + j * m] + ss);
+        }
+    }
+    // max/min reduction across the block (order-independent)
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) { red[w * 3] = gmax; red[w * 3 + 1] = lomin; red[w * 3 + 2] = himax; }
+    __syncthreads();
+    double v[3];
+    if (threadIdx.x == 0) {
+        v[0] = -INFINITY; v[1] = INFINITY; v[2] = -INFINITY;
+        for (int q = 0; q < NT / 32; ++q) {
+            v[0] = fmax(v[0], red[q * 3]);
+            v[1] = fmin(v[1], red[q * 3 + 1]);
+            v[2] = fmax(v[2], red[q * 3 + 2]);
+        }
+    }
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 3; ++q) partials[blockIdx.x * 3 + q] = v[q];
+        __threadfence();
+        is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last || threadIdx.x != 0) return;
+    __threadfence();
+    volatile const double *p = partials;
+    double g = -INFINITY, lo = INFINITY, hi = -INFINITY;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+        g = fmax(g, p[b * 3]);
+        lo = fmin(lo, p[b * 3 + 1]);
+        hi = fmax(hi, p[b * 3 + 2]);
+    }
+    *counter = 0u;
+    if (!(lo > 0.0)) {
+        state->status = OMM_ERR_NOT_SPD;
+        state->eta = NAN;
+        return;
+    }
+    state->eta = (g >= 0.0) ? g / lo : g / hi;
+}
+
+int red_blocks_for_tiles(int n) {
+    const int64_t T = ceil_div(n, TILE);
+    int64_t nb = T * T;
+    if (nb > kRedBlocksMax) nb = kRedBlocksMax;
+    if (nb < 1) nb = 1;
+    return (int)nb;
+}
+
+int red_blocks_for_len(int64_t len) {
+    int64_t nb = ceil_div(len, (int64_t)NT * 8);
+    if (nb > kRedBlocksMax) nb = kRedBlocksMax;
+    if (nb < 1) nb = 1;
+    return (int)nb;
+}
+
+int ew_blocks(int64_t len) {
+    int64_t nb = ceil_div(len, (int64_t)NT * 4);
+    if (nb > 152 * 8) nb = 152 * 8;
+    if (nb < 1) nb = 1;
+    return (int)nb;
+}
+
+}  // namespace
+
+int64_t red_scratch_bytes() { return (int64_t)kRedBlocksMax * kRedSlots * sizeof(double); }
+
+int launch_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh, const double *Z,
+                          int64_t ldz, double *scratch, unsigned int *counter, DevState *state,
+                          double *coeffs_out, cudaStream_t st, bool do_linemin) {
+    const double *X = Z;
+    const double *Y = Z + (int64_t)n * ldz;
+    const double *h2 = Z + n;
+    const double *s2 = Z + n + (int64_t)n * ldz;
+    coeffs_kernel<<<red_blocks_for_tiles(n), NT, 0, st>>>(n, h0, s0, ldh, X, Y, h2, s2, ldz, scratch,
+                                                          counter, state, coeffs_out, do_linemin ? 1 : 0);
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int launch_axpy3(int64_t mn, double *W, const double *D, double *HW, const double *HD, double *SW,
+                 const double *SD, const DevState *state, cudaStream_t st) {
+    axpy3_kernel<<<ew_blocks(mn), NT, 0, st>>>(mn, W, D, HW, HD, SW, SD, state);
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int launch_nn_update_energy(int n, double *h0, double *s0, int64_t ldh, const double *Z,
+                            int64_t ldz, double *scratch, unsigned int *counter, DevState *state,
+                            int mode, cudaStream_t st) {
+    const double *X = Z;
+    const double *Y = Z + (int64_t)n * ldz;
+    const double *h2 = Z + n;
+    const double *s2 = Z + n + (int64_t)n * ldz;
+    nn_update_kernel<<<red_blocks_for_tiles(n), NT, 0, st>>>(n, h0, s0, ldh, X, Y, h2, s2, ldz,
+                                                             scratch, counter, state, mode);
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int launch_dots_beta(int64_t mn, const double *G, const double *Gp, const double *D,
+                     double *scratch, unsigned int *counter, DevState *state, int first,
+                     cudaStream_t st) {
+    dots_kernel<<<red_blocks_for_len(mn), NT, 0, st>>>(mn, G, Gp, D, scratch, counter, state, first);
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int launch_direction(int64_t mn, const double *G, double *Gp, double *D, const DevState *state,
+                     cudaStream_t st) {
+    direction_kernel<<<ew_blocks(mn), NT, 0, st>>>(mn, G, Gp, D, state);
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int launch_shift(int64_t mm, const double *H, const double *S, double *Hs, const DevState *state,
+                 cudaStream_t st) {
+    shift_kernel<<<ew_blocks(mm), NT, 0, st>>>(mm, H, S, Hs, state);
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int launch_gershgorin(int64_t m, const double *H, const double *S, double *scratch,
+                      unsigned int *counter, DevState *state, cudaStream_t st) {
+    int64_t nb = ceil_div(m, NT / 32);
+    if (nb > kRedBlocksMax) nb = kRedBlocksMax;
+    gershgorin_kernel<<<(unsigned)nb, NT, 0, st>>>(m, H, S, scratch, counter, state);
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+// ---------------------------------------------------------------- op-level entries
+namespace {
+__global__ void line_min_kernel(const double *c, double *x_out, int32_t *status_out) {
+    double cc[5];
+    for (int q = 0; q < 5; ++q) cc[q] = c[q];
+    double x = 0.0;
+    const int st = quartic_min(cc, &x);
+    *x_out = x;
+    *status_out = st;
+}
+}  // namespace
+
+}  // namespace omm
+
+extern "C" int64_t omm_op_quartic_coeffs_scratch_bytes(int64_t n) {
+    (void)n;
+    // per-block partials (<= kRedBlocksMax blocks x 13 doubles) + the counter
+    return (int64_t)omm::kRedBlocksMax * 13 * (int64_t)sizeof(double) + 256;
+}
+
+extern "C" int omm_op_quartic_coeffs(int64_t n, const double *h0, const double *s0, int64_t ld_h,
+                                     const double *X, const double *Y, const double *h2,
+                                     const double *s2, int64_t ld_z, double *coeffs, void *scratch,
+                                     int64_t scratch_bytes, void *stream) {
+    if (n < 0 || n > 2147483647) return OMM_ERR_ARG;
+    if (coeffs == nullptr || scratch == nullptr) return OMM_ERR_ARG;
+    if (scratch_bytes < omm_op_quartic_coeffs_scratch_bytes(n)) return OMM_ERR_ARG;
+    if (((uintptr_t)scratch) & 15u) return OMM_ERR_ARG;
+    if (n > 0 && (h0 == nullptr || s0 == nullptr || X == nullptr || Y == nullptr || h2 == nullptr ||
+                  s2 == nullptr || ld_h < n || ld_z < n))
+        return OMM_ERR_ARG;
+    double *partials = (double *)scratch;
+    unsigned int *counter =
+        (unsigned int *)((char *)scratch + (int64_t)omm::kRedBlocksMax * 13 * sizeof(double));
+    cudaStream_t st = (cudaStream_t)stream;
+    omm::coeffs_kernel<<<omm::red_blocks_for_tiles((int)n), omm::NT, 0, st>>>(
+        (int)n, h0, s0, ld_h, X, Y, h2, s2, ld_z, partials, counter, nullptr, coeffs, 0);
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+extern "C" int omm_op_line_min(const double *coeffs, double *x_out, int32_t *status_out,
+                               void *stream) {
+    if (coeffs == nullptr || x_out == nullptr || status_out == nullptr) return OMM_ERR_ARG;
+    omm::line_min_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(coeffs, x_out, status_out);
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}

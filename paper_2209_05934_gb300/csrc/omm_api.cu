@@ -1,0 +1,346 @@
+// Solver handle of the C ABI: device memory, the per-(H,S) setup and the
+// device-resident CG loop of the dense form.
+//
+// Layout in HBM (all column-major FP64, m basis functions, n orbitals):
+//   HS   m x 2m   [H' | S]         (shifted Hamiltonian next to the overlap)
+//   WD   m x 2n   [W  | D]         (iterate and search direction side by side)
+//   HDSD m x 2n   [H'D | S D]
+//   SWHW m x 2n   [S W | H'W]
+//   h0s0 2n x n   [H_W ; S_W]      (stacked, ld 2n)
+//   Z    2n x 2n  [W D]^T [H'D S D] = [[X, Y], [h2, s2]]
+//   G, Gp m x n
+// The side-by-side layouts turn each step into one GEMM: the two products
+// H'D and SD share D; the four n x n contractions are [W D]^T [H'D SD]; the
+// gradient is 4 H'W - 2 [SW H'W] [H_W ; S_W].
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "omm_internal.cuh"
+
+struct omm_handle {
+    int64_t m = 0, n = 0;
+    int32_t bm = 0;
+    bool sparse = false;
+    omm_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double *HS = nullptr, *WD = nullptr, *HDSD = nullptr, *SWHW = nullptr;
+    double *h0s0 = nullptr, *Z = nullptr, *G = nullptr, *Gp = nullptr;
+    double *scratch = nullptr;
+    unsigned int *counters = nullptr;
+    omm::DevState *dstate = nullptr;
+    omm::DevState *hstate = nullptr;   // pinned
+    bool have_HS = false, have_W = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    omm_diag diag{};
+    int chunk = 8;
+};
+
+namespace {
+
+template <class T>
+int dalloc(T **p, size_t count) {
+    if (count == 0) count = 1;
+    if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+        *p = nullptr;
+        return OMM_ERR_NOMEM;
+    }
+    return OMM_OK;
+}
+
+void free_handle(omm_handle *h) {
+    if (h == nullptr) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaFree(h->HS);
+    cudaFree(h->WD);
+    cudaFree(h->HDSD);
+    cudaFree(h->SWHW);
+    cudaFree(h->h0s0);
+    cudaFree(h->Z);
+    cudaFree(h->G);
+    cudaFree(h->Gp);
+    cudaFree(h->scratch);
+    cudaFree(h->counters);
+    cudaFree(h->dstate);
+    if (h->hstate) cudaFreeHost(h->hstate);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+#define TRY(expr)                       \
+    do {                                \
+        int rc_ = (expr);               \
+        if (rc_ != OMM_OK) return rc_;  \
+    } while (0)
+
+// counters: 0 coeffs, 1 nn update, 2 dots, 3 gershgorin
+unsigned int *ctr(omm_handle *h, int i) { return h->counters + 64 * i; }
+double *scr(omm_handle *h, int i) {
+    return h->scratch + (int64_t)i * omm::kRedBlocksMax * omm::kRedSlots;
+}
+
+// One CG step of the dense FP64 form (products, contractions, line search,
+// update, energy + convergence, gradient, direction).
+int dense_iteration(omm_handle *h) {
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    cudaStream_t st = h->stream;
+    omm::DevState *s = h->dstate;
+    omm::GemmBatch b{};
+    // H'D and S D
+    b.A[0] = h->HS;          b.B[0] = h->WD + mn; b.C[0] = h->HDSD;      b.Cin[0] = nullptr;
+    b.A[1] = h->HS + m * m;  b.B[1] = h->WD + mn; b.C[1] = h->HDSD + mn; b.Cin[1] = nullptr;
+    TRY(omm::dgemm_batched(false, false, m, n, m, 1.0, b, 2, m, m, 0.0, m, m, s, st));
+    // Z = [W D]^T [H'D SD]
+    omm::GemmBatch z{};
+    z.A[0] = h->WD; z.B[0] = h->HDSD; z.C[0] = h->Z;
+    TRY(omm::dgemm_batched(true, false, 2 * n, 2 * n, m, 1.0, z, 1, m, m, 0.0, 2 * n, 2 * n, s, st));
+    // quartic coefficients and its minimum
+    TRY(omm::launch_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 0),
+                                   ctr(h, 0), s, nullptr, st, true));
+    // W += x D, H'W += x H'D, SW += x SD
+    TRY(omm::launch_axpy3(mn, h->WD, h->WD + mn, h->SWHW + mn, h->HDSD, h->SWHW, h->HDSD + mn, s, st));
+    // H_W, S_W update, energy, RelTol test
+    TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
+                                     ctr(h, 1), s, 0, st));
+    // G = 4 H'W - 2 [SW H'W][H_W ; S_W]
+    omm::GemmBatch g{};
+    g.A[0] = h->SWHW; g.B[0] = h->h0s0; g.Cin[0] = h->SWHW + mn; g.C[0] = h->G;
+    TRY(omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, s, st));
+    TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 0, st));
+    TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st));
+    return OMM_OK;
+}
+
+int dense_start(omm_handle *h) {
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    cudaStream_t st = h->stream;
+    omm::DevState *s = h->dstate;
+    omm::GemmBatch b{};
+    // SW = S W, H'W = H' W
+    b.A[0] = h->HS + m * m; b.B[0] = h->WD; b.C[0] = h->SWHW;
+    b.A[1] = h->HS;         b.B[1] = h->WD; b.C[1] = h->SWHW + mn;
+    TRY(omm::dgemm_batched(false, false, m, n, m, 1.0, b, 2, m, m, 0.0, m, m, s, st));
+    // H_W = W^T H'W, S_W = W^T S W
+    omm::GemmBatch c{};
+    c.A[0] = h->WD; c.B[0] = h->SWHW + mn; c.C[0] = h->h0s0;
+    c.A[1] = h->WD; c.B[1] = h->SWHW;      c.C[1] = h->h0s0 + n;
+    TRY(omm::dgemm_batched(true, false, n, n, m, 1.0, c, 2, m, m, 0.0, 2 * n, 2 * n, s, st));
+    TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
+                                     ctr(h, 1), s, 1, st));
+    omm::GemmBatch g{};
+    g.A[0] = h->SWHW; g.B[0] = h->h0s0; g.Cin[0] = h->SWHW + mn; g.C[0] = h->G;
+    TRY(omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, s, st));
+    TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 1, st));
+    TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st));
+    return OMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void omm_default_options(omm_options *opt) {
+    if (opt == nullptr) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->eta = 0.0;
+    opt->eta_auto = 1;
+    opt->precision = OMM_PREC_FP64;
+    opt->cholesky = 0;
+    opt->max_iter = 10000;
+    opt->orth_tol = 0.0;
+    opt->filter_eps = 1e-8;
+    opt->stream = nullptr;
+}
+
+const char *omm_status_str(int status) {
+    switch (status) {
+        case OMM_OK: return "ok";
+        case OMM_ERR_ARG: return "invalid argument";
+        case OMM_ERR_NOMEM: return "out of memory";
+        case OMM_ERR_CUDA: return "CUDA error";
+        case OMM_ERR_NOT_SPD: return "overlap matrix not positive definite";
+        case OMM_ERR_LINESEARCH: return "line-search quartic has no minimum";
+        case OMM_ERR_MAXITER: return "maximum number of CG iterations reached";
+        case OMM_ERR_PATTERN: return "invalid or inconsistent sparsity pattern";
+        case OMM_ERR_NONFINITE: return "non-finite energy or line-search data";
+        case OMM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case OMM_ERR_STATE: return "call out of order";
+        case OMM_ERR_UNSUPPORTED: return "unsupported option combination";
+        default: return "unknown status";
+    }
+}
+
+int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *pattern,
+               const omm_options *opt, omm_handle **out) {
+    if (out == nullptr) return OMM_ERR_ARG;
+    *out = nullptr;
+    if (m <= 0 || n <= 0 || n > m) return OMM_ERR_ARG;
+    if (n > 2147483647 / 2 || m > ((int64_t)1 << 31)) return OMM_ERR_ARG;
+    if (block_size < 0) return OMM_ERR_ARG;
+    if (pattern != nullptr) return OMM_ERR_UNSUPPORTED;   // sparse form: separate handle type
+    omm_handle *h = new (std::nothrow) omm_handle();
+    if (h == nullptr) return OMM_ERR_NOMEM;
+    h->m = m;
+    h->n = n;
+    h->bm = block_size;
+    if (opt) h->opt = *opt; else omm_default_options(&h->opt);
+    if (h->opt.max_iter < 0) {
+        delete h;
+        return OMM_ERR_ARG;
+    }
+    if (h->opt.cholesky != 0 || h->opt.precision != OMM_PREC_FP64) {
+        delete h;
+        return OMM_ERR_UNSUPPORTED;
+    }
+    int rc = OMM_OK;
+    if (h->opt.stream) {
+        h->stream = (cudaStream_t)h->opt.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return OMM_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    const int64_t mn = m * n;
+    if ((rc = dalloc(&h->HS, (size_t)(2 * m * m))) ||
+        (rc = dalloc(&h->WD, (size_t)(2 * mn))) || (rc = dalloc(&h->HDSD, (size_t)(2 * mn))) ||
+        (rc = dalloc(&h->SWHW, (size_t)(2 * mn))) || (rc = dalloc(&h->h0s0, (size_t)(2 * n * n))) ||
+        (rc = dalloc(&h->Z, (size_t)(4 * n * n))) || (rc = dalloc(&h->G, (size_t)mn)) ||
+        (rc = dalloc(&h->Gp, (size_t)mn)) ||
+        (rc = dalloc(&h->scratch, (size_t)(4 * omm::kRedBlocksMax * omm::kRedSlots))) ||
+        (rc = dalloc(&h->counters, (size_t)(64 * 8))) || (rc = dalloc(&h->dstate, 1))) {
+        free_handle(h);
+        return rc;
+    }
+    if (cudaMallocHost((void **)&h->hstate, sizeof(omm::DevState)) != cudaSuccess) {
+        h->hstate = nullptr;
+        free_handle(h);
+        return OMM_ERR_NOMEM;
+    }
+    if (cudaMemsetAsync(h->counters, 0, 64 * 8 * sizeof(unsigned int), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->dstate, 0, sizeof(omm::DevState), h->stream) != cudaSuccess ||
+        cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        free_handle(h);
+        return OMM_ERR_CUDA;
+    }
+    *out = h;
+    return OMM_OK;
+}
+
+int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_device) {
+    if (h == nullptr || H == nullptr || S == nullptr) return OMM_ERR_ARG;
+    const int64_t m = h->m, mm = m * m;
+    cudaStream_t st = h->stream;
+    OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // S goes to its slot; H is staged in the H' slot and shifted in place
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->HS + mm, S, mm * sizeof(double), kind, st));
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->HS, H, mm * sizeof(double), kind, st));
+    omm::DevState init{};
+    init.eta = h->opt.eta;
+    *h->hstate = init;
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
+    if (h->opt.eta_auto)
+        TRY(omm::launch_gershgorin(m, h->HS, h->HS + mm, scr(h, 3), ctr(h, 3), h->dstate, st));
+    TRY(omm::launch_shift(mm, h->HS, h->HS + mm, h->HS, h->dstate, st));
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->hstate->status != OMM_OK) return h->hstate->status;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    h->diag.t_setup_ms = ms;
+    h->diag.eta = h->hstate->eta;
+    h->have_HS = true;
+    return OMM_OK;
+}
+
+int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol, double *W_out,
+              int32_t W_out_on_device, double *E_out, int32_t *iters_out) {
+    if (h == nullptr || !(tol >= 0.0)) return OMM_ERR_ARG;
+    if (!h->have_HS) return OMM_ERR_STATE;
+    if (W0 == nullptr && !h->have_W) return OMM_ERR_STATE;
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    cudaStream_t st = h->stream;
+    OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
+    if (W0 != nullptr)
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->WD, W0, mn * sizeof(double),
+                                     W0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    omm::DevState init{};
+    init.eta = h->diag.eta;
+    init.tol = tol;
+    init.orth_tol = h->opt.orth_tol;
+    init.max_iter = h->opt.max_iter;
+    init.n = (int)n;
+    *h->hstate = init;
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
+    TRY(dense_start(h));
+    h->have_W = true;
+    for (;;) {
+        for (int c = 0; c < h->chunk; ++c) TRY(dense_iteration(h));
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
+        OMM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h->hstate->done) break;
+    }
+    OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
+    if (W_out != nullptr)
+        OMM_CUDA_TRY(cudaMemcpyAsync(W_out, h->WD, mn * sizeof(double),
+                                     W_out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    const omm::DevState &s = *h->hstate;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    h->diag.t_solve_ms = ms;
+    h->diag.E = s.E;
+    h->diag.E_rel_change = s.rel;
+    h->diag.orth = sqrt(s.orth2 > 0.0 ? s.orth2 : 0.0);
+    // n_e = 2 Tr[(2I - S_W) S_W] = 2 (2 tr S_W - ||S_W||^2); from ||S_W - I||^2 =
+    // ||S_W||^2 - 2 tr S_W + n:  n_e = 2 (n - ||S_W - I||^2)
+    h->diag.charge = 2.0 * ((double)n - s.orth2);
+    h->diag.iters = s.k;
+    h->diag.status = s.status;
+    h->diag.iters_mixed = 0;
+    h->diag.iters_refine = s.k;
+    if (E_out) *E_out = s.E;
+    if (iters_out) *iters_out = s.k;
+    return s.status;
+}
+
+int omm_get_diag(omm_handle *h, omm_diag *d) {
+    if (h == nullptr || d == nullptr) return OMM_ERR_ARG;
+    *d = h->diag;
+    return OMM_OK;
+}
+
+int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device) {
+    if (h == nullptr || dst == nullptr) return OMM_ERR_ARG;
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaStream_t st = h->stream;
+    switch (which) {
+        case 0: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->WD, mn * 8, kind, st)); break;
+        case 1: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->SWHW + mn, mn * 8, kind, st)); break;
+        case 2: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->SWHW, mn * 8, kind, st)); break;
+        case 3: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->G, mn * 8, kind, st)); break;
+        case 4: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->WD + mn, mn * 8, kind, st)); break;
+        case 5:
+        case 6: {
+            const double *src = h->h0s0 + (which == 6 ? n : 0);
+            OMM_CUDA_TRY(cudaMemcpy2DAsync(dst, n * 8, src, 2 * n * 8, n * 8, n, kind, st));
+            break;
+        }
+        default: return OMM_ERR_ARG;
+    }
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return OMM_OK;
+}
+
+void omm_destroy(omm_handle *h) { free_handle(h); }
+
+}  // extern "C"

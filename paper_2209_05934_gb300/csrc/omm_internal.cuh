@@ -1,0 +1,91 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/omm.h"
+
+namespace omm {
+
+#define OMM_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return OMM_ERR_CUDA;          \
+    } while (0)
+
+// Device-resident CG state of one solve.  Kernels of an iteration read `done`
+// first and return at once when it is set, so a launched chunk of iterations
+// finishes as no-ops after convergence.
+struct DevState {
+    int k;              // CG steps taken
+    int done;           // 1 once converged or failed
+    int status;         // OMM_OK or OMM_ERR_*
+    int max_iter;
+    int n;
+    int restart;        // D = -G at the next direction update
+    double tol, orth_tol, eta;
+    double E, E_prev, rel;       // E_k, E_{k-1}, last relative change
+    double x;                    // current step length
+    double c[5];                 // quartic coefficients
+    double gg, gg_prev, ggp, gd; // <G,G>, <Gp,Gp>, <G,Gp>, <G,D_old>
+    double beta;
+    double trh0, sh, orth2;      // tr h0, <s0,h0>, ||s0 - I||_F^2
+    double charge;
+};
+
+// -------- FP64 GEMM (dense_fp64.cu)
+struct GemmBatch {
+    const double *A[4];
+    const double *B[4];
+    const double *Cin[4];
+    double *C[4];
+};
+
+// C_b = alpha op(A_b) op(B_b) + beta Cin_b for b < nbatch; column-major.
+// If `state` is non-null the kernel returns at once when state->done is set.
+int dgemm_batched(bool tA, bool tB, int64_t M, int64_t N, int64_t K, double alpha,
+                  const GemmBatch &bt, int nbatch, int64_t lda, int64_t ldb, double beta,
+                  int64_t ldcin, int64_t ldc, const DevState *state, cudaStream_t st);
+
+// -------- reductions and CG updates (cg_kernels.cu)
+constexpr int kRedBlocksMax = 512;
+constexpr int kRedSlots = 16;
+
+int64_t red_scratch_bytes();
+
+// coefficients + line minimum into state (x, c, status/done on failure)
+int launch_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh, const double *Z,
+                          int64_t ldz, double *scratch, unsigned int *counter, DevState *state,
+                          double *coeffs_out, cudaStream_t st, bool do_linemin);
+
+// W += x D, HW += x HD, SW += x SD  (three m x n arrays, ld = m)
+int launch_axpy3(int64_t mn, double *W, const double *D, double *HW, const double *HD, double *SW,
+                 const double *SD, const DevState *state, cudaStream_t st);
+
+// h0 += x (X + X^T) + x^2 sym(h2); s0 likewise; then energy, orthonormality,
+// convergence test (mode 0), or initial symmetrisation + energy (mode 1).
+int launch_nn_update_energy(int n, double *h0, double *s0, int64_t ldh, const double *Z,
+                            int64_t ldz, double *scratch, unsigned int *counter, DevState *state,
+                            int mode, cudaStream_t st);
+
+// <G,G>, <G,Gp>, <G,D> then beta (PR+) and the restart decision
+int launch_dots_beta(int64_t mn, const double *G, const double *Gp, const double *D,
+                     double *scratch, unsigned int *counter, DevState *state, int first,
+                     cudaStream_t st);
+
+// D = -G + beta D (or -G on restart); Gp = G
+int launch_direction(int64_t mn, const double *G, double *Gp, double *D, const DevState *state,
+                     cudaStream_t st);
+
+// H' = H - eta S (dense, m x m), eta read from state
+int launch_shift(int64_t mm, const double *H, const double *S, double *Hs, const DevState *state,
+                 cudaStream_t st);
+
+// Gershgorin bound into state->eta (dense, column-major m x m, symmetric)
+int launch_gershgorin(int64_t m, const double *H, const double *S, double *scratch,
+                      unsigned int *counter, DevState *state, cudaStream_t st);
+
+__device__ __host__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace omm

@@ -1,0 +1,232 @@
+"""Thin ctypes binding of libomm_gb300.so (argument marshalling only).
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+turns numpy arrays (host memory) and torch CUDA tensors (device memory) into
+the plain pointers and sizes of the C ABI declared in include/omm.h.  There
+is no fallback: if the library is missing, importing a function raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libomm_gb300.so")
+
+OK = 0
+ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_NOT_SPD, ERR_LINESEARCH = -1, -2, -3, -4, -5
+ERR_MAXITER, ERR_PATTERN, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = -6, -7, -8, -9, -10, -11
+PREC_FP64, PREC_MIXED = 0, 1
+
+ARRAY_W, ARRAY_HW, ARRAY_SW, ARRAY_G, ARRAY_D, ARRAY_HW_N, ARRAY_SW_N = range(7)
+
+
+class Options(C.Structure):
+    _fields_ = [("eta", C.c_double), ("eta_auto", C.c_int32), ("precision", C.c_int32),
+                ("cholesky", C.c_int32), ("max_iter", C.c_int32), ("orth_tol", C.c_double),
+                ("filter_eps", C.c_double), ("stream", C.c_void_p)]
+
+
+class Pattern(C.Structure):
+    _fields_ = [("bm", C.c_int32), ("bn", C.c_int32), ("nbr", C.c_int64), ("nbc", C.c_int64),
+                ("H_rowptr", C.c_void_p), ("H_col", C.c_void_p),
+                ("W_rowptr", C.c_void_p), ("W_col", C.c_void_p)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("E", C.c_double), ("E_rel_change", C.c_double), ("orth", C.c_double),
+                ("charge", C.c_double), ("eta", C.c_double), ("iters", C.c_int32),
+                ("status", C.c_int32), ("iters_mixed", C.c_int32), ("iters_refine", C.c_int32),
+                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("nnzb_H", C.c_int64),
+                ("nnzb_W", C.c_int64), ("nnzb_HW", C.c_int64), ("nnzb_N", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+_SIGS = {
+    "omm_default_options": (None, [C.POINTER(Options)]),
+    "omm_create": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_void_p, C.POINTER(Options),
+                             C.POINTER(C.c_void_p)]),
+    "omm_set_HS": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "omm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
+                            C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "omm_get_diag": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
+    "omm_get_array": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "omm_destroy": (None, [C.c_void_p]),
+    "omm_status_str": (C.c_char_p, [C.c_int]),
+    "omm_op_dgemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_double,
+                               C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
+                               C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]),
+    "omm_op_quartic_coeffs_scratch_bytes": (C.c_int64, [C.c_int64]),
+    "omm_op_quartic_coeffs": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                        C.c_void_p, C.c_int64, C.c_void_p]),
+    "omm_op_line_min": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+}
+
+
+def lib():
+    """Load libomm_gb300.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build(); "
+                               "there is no non-CUDA implementation")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class OmmError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = lib().omm_status_str(status).decode()
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+def check(status, what=""):
+    if status != OK:
+        raise OmmError(status, what)
+    return status
+
+
+def status_str(status: int) -> str:
+    return lib().omm_status_str(status).decode()
+
+
+# ---------------------------------------------------------------- marshalling
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array or a torch tensor; None -> (None, 0)."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        return C.c_void_p(x.data_ptr()), int(x.is_cuda)
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 and x.dtype not in (np.int64, np.int32):
+            raise TypeError("expected float64 arrays")
+        return C.c_void_p(x.ctypes.data), 0
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def colmajor(A: np.ndarray) -> np.ndarray:
+    return np.asfortranarray(np.asarray(A, dtype=np.float64))
+
+
+def _check_colmajor(x, rows, cols, name):
+    if _is_torch(x):
+        if tuple(x.shape) != (rows, cols):
+            raise ValueError(f"{name}: shape {tuple(x.shape)} != {(rows, cols)}")
+        if cols > 1 and rows > 1 and x.stride() != (1, rows):
+            raise ValueError(f"{name}: must be column-major contiguous (stride (1, {rows}))")
+        if str(x.dtype) != "torch.float64":
+            raise TypeError(f"{name}: float64 required")
+    else:
+        if x.shape != (rows, cols):
+            raise ValueError(f"{name}: shape {x.shape} != {(rows, cols)}")
+        if not x.flags["F_CONTIGUOUS"] or x.dtype != np.float64:
+            raise ValueError(f"{name}: must be a float64 Fortran-ordered array")
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().omm_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "stream":
+            v = C.c_void_p(v) if v is not None else None
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One omm_handle (dense form)."""
+
+    def __init__(self, m: int, n: int, block_size: int = 8, pattern=None, **options):
+        self.m, self.n = m, n
+        self._opts = default_options(**options)
+        h = C.c_void_p()
+        pat = None
+        if pattern is not None:
+            pat = C.byref(pattern)
+        check(lib().omm_create(m, n, block_size, pat, C.byref(self._opts), C.byref(h)), "omm_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().omm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_HS(self, H, S):
+        _check_colmajor(H, self.m, self.m, "H")
+        _check_colmajor(S, self.m, self.m, "S")
+        pH, dH = _ptr(H)
+        pS, dS = _ptr(S)
+        if dH != dS:
+            raise ValueError("H and S must both be host or both device arrays")
+        return check(lib().omm_set_HS(self._h, pH, pS, dH), "omm_set_HS")
+
+    def solve(self, W0=None, tol: float = 1e-10, W_out=None, raise_on_error=True):
+        if W0 is not None:
+            _check_colmajor(W0, self.m, self.n, "W0")
+        if W_out is not None:
+            _check_colmajor(W_out, self.m, self.n, "W_out")
+        p0, d0 = _ptr(W0)
+        po, do = _ptr(W_out)
+        E = C.c_double(0.0)
+        it = C.c_int32(0)
+        st = lib().omm_solve(self._h, p0, d0, float(tol), po, do, C.byref(E), C.byref(it))
+        if raise_on_error and st not in (OK,):
+            raise OmmError(st, "omm_solve")
+        return E.value, it.value, st
+
+    def diag(self) -> Diag:
+        d = Diag()
+        check(lib().omm_get_diag(self._h, C.byref(d)), "omm_get_diag")
+        return d
+
+    def get_array(self, which: int) -> np.ndarray:
+        rows = self.n if which in (ARRAY_HW_N, ARRAY_SW_N) else self.m
+        out = np.zeros((rows, self.n), order="F")
+        check(lib().omm_get_array(self._h, which, C.c_void_p(out.ctypes.data), 0), "omm_get_array")
+        return out
+
+
+# ---------------------------------------------------------------- op-level calls
+def op_dgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, Cout, ldc, stream=0):
+    return lib().omm_op_dgemm(int(transA), int(transB), M, N, K, float(alpha), _ptr(A)[0], lda,
+                              _ptr(B)[0], ldb, float(beta), _ptr(Cin)[0], ldcin, _ptr(Cout)[0], ldc,
+                              C.c_void_p(stream) if stream else None)
+
+
+def op_quartic_coeffs_scratch_bytes(n: int) -> int:
+    return lib().omm_op_quartic_coeffs_scratch_bytes(n)
+
+
+def op_quartic_coeffs(n, h0, s0, ld_h, X, Y, h2, s2, ld_z, coeffs, scratch, scratch_bytes, stream=0):
+    return lib().omm_op_quartic_coeffs(n, _ptr(h0)[0], _ptr(s0)[0], ld_h, _ptr(X)[0], _ptr(Y)[0],
+                                       _ptr(h2)[0], _ptr(s2)[0], ld_z, _ptr(coeffs)[0],
+                                       _ptr(scratch)[0], scratch_bytes,
+                                       C.c_void_p(stream) if stream else None)
+
+
+def op_line_min(coeffs, x_out, status_out, stream=0):
+    return lib().omm_op_line_min(_ptr(coeffs)[0], _ptr(x_out)[0], _ptr(status_out)[0],
+                                 C.c_void_p(stream) if stream else None)
