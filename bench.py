@@ -1,0 +1,359 @@
+"""Benchmark: dense OMM-CG solves per second at 1e-8 relative energy accuracy.
+
+One step = one whole solve of the 512-atom dense workload (8x8x8 jittered
+grid, 8 orbitals per atom: m = 4096, n = 1024): the per-(H,S) setup
+(Gershgorin shift, operand packing) plus conjugate-gradient minimisation from
+the seeded W0 until the RelTol test and, for the mixed form, the
+orthonormality test pass.  H, S and W0 are resident in HBM when the timed
+region starts (value); the e2e figure repeats the same solves through the C
+ABI from pinned host buffers, copies included.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl omm|reference]
+                    [--precision mixed|fp64]
+
+Multi-GPU runs (torchrun) are independent replicas: each rank solves its own
+systems; only the timing is reduced (max over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = dict(dims=(8, 8, 8), seed=0)
+METRIC = "OMM solves/s & time-to-converge @1e-8 rel energy; p50/p99 latency; %roofline"
+UNIT = "solves/s"
+TOL = {"fp64": dict(tol=1e-10, orth_tol=0.0), "mixed": dict(tol=1e-10, orth_tol=1e-6)}
+
+
+def workload_name(sysm):
+    nx, ny, nz = WORKLOAD["dims"]
+    return (f"dense OMM-CG, {sysm.natoms} atoms ({nx}x{ny}x{nz} jittered grid), 8 orbitals/atom, "
+            f"m={sysm.m}, n={sysm.n}, seed {WORKLOAD['seed']}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def golden():
+    p = os.path.join(ROOT, "tests", "golden", "oracle_reference.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, sm_max_nominal=2070.0):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.file.flush()
+        rows = []
+        for line in open(self.file.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except Exception:
+                pass
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else sm_max_nominal, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier_max(value: float, ws: int):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle (CPU) arm
+def oracle_sample(sysm, H, S, W0, n_iter: int):
+    """Time the oracle's setup and n_iter CG steps on the host cores."""
+    from oracle import omm as O
+    t0 = time.perf_counter()
+    eta = O.gershgorin_eta(H, S)
+    t1 = time.perf_counter()
+    res = O.omm_cg(H, S, W0, tol=0.0, eta=eta, max_iter=n_iter)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / max(1, res.iters)
+
+
+def cpu_baseline(sysm, H, S, W0, full_iters: int, n_iter: int = 2):
+    cores = len(os.sched_getaffinity(0))
+    t_setup, t_iter = oracle_sample(sysm, H, S, W0, n_iter)
+    t_solve = t_setup + full_iters * t_iter
+    return {"value": 1.0 / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle Gershgorin setup + {n_iter} FP64 CG steps on this workload, "
+                       f"{t_iter:.3f} s/step, scaled to the oracle's {full_iters} steps per solve"),
+            "seconds_per_solve": t_solve}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    sysm = synth.make_system(*WORKLOAD["dims"], seed=WORKLOAD["seed"])
+    H, S = sysm.dense_H(), sysm.dense_S()
+    W0 = np.asfortranarray(sysm.W0_dense())
+    g = golden().get("c2", {})
+    full_iters = int(g.get("oracle_iters", 60))
+    for _ in range(args.warmup):
+        oracle_sample(sysm, H, S, W0, 1)
+    times = []
+    for _ in range(args.steps):
+        ts, ti = oracle_sample(sysm, H, S, W0, 1)
+        times.append(ts + full_iters * ti)
+    t = statistics.mean(times)
+    cores = len(os.sched_getaffinity(0))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(sysm), "tol": TOL["fp64"]["tol"]},
+        "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": (f"per step: oracle setup + 1 FP64 CG step, scaled to the "
+                                    f"oracle's {full_iters} steps per solve")},
+        "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_omm(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2209_05934_gb300 import omm
+
+    omm.lib()
+    prec = args.precision
+    sysm = synth.make_system(*WORKLOAD["dims"], seed=WORKLOAD["seed"])
+    H, S = sysm.dense_H(), sysm.dense_S()
+    W0 = np.asfortranarray(sysm.W0_dense())
+    m, n = sysm.m, sysm.n
+    dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
+    Hd, Sd, W0d = dev(H), dev(S), dev(W0)
+    Wout = torch.zeros((n, m), dtype=torch.float64, device="cuda").T
+    stream = torch.cuda.current_stream()
+    opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
+                orth_tol=TOL[prec]["orth_tol"], stream=stream.cuda_stream)
+    solver = omm.Solver(m, n, 8, **opts)
+    tol = TOL[prec]["tol"]
+
+    def step():
+        solver.set_HS(Hd, Sd)
+        E, iters, st = solver.solve(W0d, tol=tol, W_out=Wout)
+        return E, iters
+
+    for _ in range(args.warmup):
+        E, iters = step()
+    torch.cuda.synchronize()
+    solver.set_profiling(True)
+    solver.stage_times(reset=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = omm.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            E, iters = step()
+            b.record(stream)
+            lat.append((a, b))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = omm.kernel_launches() - launches0
+    solver.set_profiling(False)
+    ms_stage, n_stage = solver.stage_times(reset=True)
+    t_ms = ev0.elapsed_time(ev1)
+    lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
+    if ws > 1:
+        torch.distributed.barrier()
+    t_max = barrier_max(t_ms, ws)
+    diag = solver.diag()
+    # accuracy against the exact minimum (2 x sum of the n lowest eigenvalues)
+    g = golden().get("c2", {})
+    e_exact = g.get("exact_E")
+    rel_err = abs(E - e_exact) / abs(e_exact) if e_exact else None
+
+    # ---- e2e: the same solves through the C ABI from pinned host buffers
+    Hh = torch.from_numpy(np.asfortranarray(H)).pin_memory()
+    Sh = torch.from_numpy(np.asfortranarray(S)).pin_memory()
+    W0h = torch.from_numpy(np.asfortranarray(W0)).pin_memory()
+    Wh = torch.zeros((n, m), dtype=torch.float64).pin_memory().T
+    solver_h = omm.Solver(m, n, 8, **opts)
+    solver_h.set_HS(Hh, Sh)
+    solver_h.solve(W0h, tol=tol, W_out=Wh)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        solver_h.set_HS(Hh, Sh)
+        Eh, _, _ = solver_h.solve(W0h, tol=tol, W_out=Wh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = barrier_max(e0.elapsed_time(e1), ws)
+    solver_h.close()
+
+    # ---- roofline of the dominant stage
+    pk, pk_kind = peaks()
+    dom = int(np.argmax(ms_stage[:6])) if sum(ms_stage[:6]) > 0 else 0
+    roof = roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind)
+
+    if rank != 0:
+        solver.close()
+        return
+    full_iters = int(g.get("oracle_iters", iters))
+    cpu = cpu_baseline(sysm, H, S, W0, full_iters) if ws == 1 else None
+    value = ws * args.steps / (t_max / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "bf16-split+f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(sysm), "precision": prec, "tol": tol,
+                   "orth_tol": TOL[prec]["orth_tol"], "parallelism": f"replicas x{ws}",
+                   "l2": "working set (H, S = 256 MiB, plus W/D/products) exceeds the 129 MB L2"},
+        "time_to_converge_ms": {"p50": lat_ms[len(lat_ms) // 2],
+                                "p99": lat_ms[min(len(lat_ms) - 1, int(math.ceil(0.99 * len(lat_ms))) - 1)]},
+        "accuracy": {"E": E, "exact_E": e_exact, "rel_err": rel_err, "orth": diag.orth,
+                     "iters": diag.iters, "iters_mixed": diag.iters_mixed,
+                     "iters_refine": diag.iters_refine},
+        "stages_ms_per_step": {name: ms_stage[i] / args.steps for i, name in enumerate(STAGES)},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * e2e_steps / (t_e2e / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(2 * m * m * 8 + m * n * 8),
+                "d2h_bytes_per_step": int(m * n * 8 + 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    solver.close()
+
+
+STAGES = ["products", "contract", "linesearch", "update", "gradient", "direction", "setup", "start",
+          "pack", "anchor"]
+
+
+def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
+    if n_stage[dom] == 0:
+        return None
+    avg_ms = ms_stage[dom] / n_stage[dom]
+    # algorithmic flops per launch of each stage (dense)
+    flops = {0: 4.0 * m * m * n, 1: 2.0 * (2 * n) * (2 * n) * m, 4: 2.0 * m * n * (2 * n)}
+    if prec == "fp64":
+        fp64_peak = pk.get("fp64_tflops", 1.19)
+        f = flops.get(dom)
+        if f is None:
+            return None
+        ach = f / (avg_ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": STAGES[dom], "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "FP64 DFMA throughput measured by the probe in profiles/fp64_peak.md"}
+    f = flops.get(dom)
+    if f is None:
+        return None
+    ach = f / (avg_ms * 1e-3) / 1e12
+    peak = pk["bf16_tflops_sustained"]
+    return {"bound": "tensor", "kernel": STAGES[dom], "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "peak_source": f"bf16 sustained ({pk_kind}); achieved counts FP64-equivalent flops"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="omm", choices=["omm", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_omm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -165,6 +165,30 @@ int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device);
 void omm_destroy(omm_handle *h);
 const char *omm_status_str(int status);
 
+/*
+ * Per-stage device timing of a handle.  While profiling is on, the library
+ * records CUDA events on the handle's stream around each stage of every CG
+ * step; omm_get_stage_times returns the summed milliseconds and the number of
+ * timed launches per stage (arrays of nstages entries, nullable), optionally
+ * resetting them.  Stages: products H'D, SD (0); n x n contractions (1);
+ * line-search coefficients and minimum (2); W/H'W/SW and H_W/S_W update with
+ * energy test (3); gradient (4); CG direction (5); per-(H,S) setup (6);
+ * solve start-up (7); split-precision operand packing (8); refinement
+ * re-anchoring (9).
+ */
+enum {
+    OMM_STAGE_PRODUCTS = 0, OMM_STAGE_CONTRACT = 1, OMM_STAGE_LINESEARCH = 2,
+    OMM_STAGE_UPDATE = 3, OMM_STAGE_GRADIENT = 4, OMM_STAGE_DIRECTION = 5,
+    OMM_STAGE_SETUP = 6, OMM_STAGE_START = 7, OMM_STAGE_PACK = 8, OMM_STAGE_ANCHOR = 9,
+    OMM_NSTAGES = 10
+};
+int omm_set_profiling(omm_handle *h, int32_t on);
+int omm_get_stage_times(omm_handle *h, double *ms, int64_t *launches, int32_t nstages,
+                        int32_t reset);
+
+/* Total number of CUDA kernels this library has launched in the process. */
+int64_t omm_kernel_launches(void);
+
 /* ------------------------------------------------------------------------
  * Op-level entry points: single steps of the hot path on caller-owned device
  * memory, enqueued on `stream`, asynchronous.  They allocate nothing.
@@ -212,6 +236,24 @@ int omm_op_quartic_coeffs(int64_t n, const double *h0, const double *s0, int64_t
  * wins, ties go to the smaller |x|, then to x > 0.
  */
 int omm_op_line_min(const double *coeffs, double *x_out, int32_t *status_out, void *stream);
+
+/*
+ * Split-precision tensor-core GEMM  C = alpha op(A) op(B) + beta Cin  (FP64 in
+ * and out, column-major, op as in omm_op_dgemm).  Each operand is split into
+ * ndigits BF16 digits (x = d1 + d2 + d3 + rest, d1 = bf16(x), d2 = bf16(x - d1),
+ * ...), the digit products with p + q <= ndigits + 1 run on the tcgen05 tensor
+ * cores with FP32 accumulation, and the epilogue forms the FP64 result.
+ * ndigits = 3 gives FP32-level accuracy (about 1e-7 of |A| |B|), 2 about
+ * 1e-5, 1 plain BF16.  This is the arithmetic of the bulk CG products of the
+ * mixed-precision form.  workspace: device memory of at least
+ * omm_op_split_gemm_workspace_bytes(M, N, K, ndigits) bytes (digit planes).
+ */
+int64_t omm_op_split_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int32_t ndigits);
+int omm_op_split_gemm(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K,
+                      int32_t ndigits, double alpha, const double *A, int64_t lda,
+                      const double *B, int64_t ldb, double beta, const double *Cin,
+                      int64_t ldcin, double *C, int64_t ldc, void *workspace,
+                      int64_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

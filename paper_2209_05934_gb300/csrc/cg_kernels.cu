@@ -525,6 +525,7 @@ int launch_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh
     const double *s2 = Z + n + (int64_t)n * ldz;
     coeffs_kernel<<<red_blocks_for_tiles(n), NT, 0, st>>>(n, h0, s0, ldh, X, Y, h2, s2, ldz, scratch,
                                                           counter, state, coeffs_out, do_linemin ? 1 : 0);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
@@ -532,6 +533,7 @@ int launch_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh
 int launch_axpy3(int64_t mn, double *W, const double *D, double *HW, const double *HD, double *SW,
                  const double *SD, const DevState *state, cudaStream_t st) {
     axpy3_kernel<<<ew_blocks(mn), NT, 0, st>>>(mn, W, D, HW, HD, SW, SD, state);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
@@ -545,6 +547,7 @@ int launch_nn_update_energy(int n, double *h0, double *s0, int64_t ldh, const do
     const double *s2 = Z + n + (int64_t)n * ldz;
     nn_update_kernel<<<red_blocks_for_tiles(n), NT, 0, st>>>(n, h0, s0, ldh, X, Y, h2, s2, ldz,
                                                              scratch, counter, state, mode);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
@@ -553,6 +556,7 @@ int launch_dots_beta(int64_t mn, const double *G, const double *Gp, const double
                      double *scratch, unsigned int *counter, DevState *state, int first,
                      cudaStream_t st) {
     dots_kernel<<<red_blocks_for_len(mn), NT, 0, st>>>(mn, G, Gp, D, scratch, counter, state, first);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
@@ -560,6 +564,7 @@ int launch_dots_beta(int64_t mn, const double *G, const double *Gp, const double
 int launch_direction(int64_t mn, const double *G, double *Gp, double *D, const DevState *state,
                      cudaStream_t st) {
     direction_kernel<<<ew_blocks(mn), NT, 0, st>>>(mn, G, Gp, D, state);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
@@ -567,6 +572,7 @@ int launch_direction(int64_t mn, const double *G, double *Gp, double *D, const D
 int launch_shift(int64_t mm, const double *H, const double *S, double *Hs, const DevState *state,
                  cudaStream_t st) {
     shift_kernel<<<ew_blocks(mm), NT, 0, st>>>(mm, H, S, Hs, state);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
@@ -576,6 +582,7 @@ int launch_gershgorin(int64_t m, const double *H, const double *S, double *scrat
     int64_t nb = ceil_div(m, NT / 32);
     if (nb > kRedBlocksMax) nb = kRedBlocksMax;
     gershgorin_kernel<<<(unsigned)nb, NT, 0, st>>>(m, H, S, scratch, counter, state);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
@@ -617,6 +624,7 @@ extern "C" int omm_op_quartic_coeffs(int64_t n, const double *h0, const double *
     cudaStream_t st = (cudaStream_t)stream;
     omm::coeffs_kernel<<<omm::red_blocks_for_tiles((int)n), omm::NT, 0, st>>>(
         (int)n, h0, s0, ld_h, X, Y, h2, s2, ld_z, partials, counter, nullptr, coeffs, 0);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
@@ -625,6 +633,7 @@ extern "C" int omm_op_line_min(const double *coeffs, double *x_out, int32_t *sta
                                void *stream) {
     if (coeffs == nullptr || x_out == nullptr || status_out == nullptr) return OMM_ERR_ARG;
     omm::line_min_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(coeffs, x_out, status_out);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }

@@ -128,6 +128,7 @@ int dgemm_batched(bool tA, bool tB, int64_t M, int64_t N, int64_t K, double alph
         dgemm_kernel<false, true><<<grid, NT, 0, st>>>(M, N, K, alpha, bt, lda, ldb, beta, ldcin, ldc, state);
     else
         dgemm_kernel<true, true><<<grid, NT, 0, st>>>(M, N, K, alpha, bt, lda, ldb, beta, ldcin, ldc, state);
+    omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }

@@ -36,6 +36,14 @@ struct omm_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     omm_diag diag{};
     int chunk = 8;
+    // optional per-stage device timing (omm_set_profiling)
+    bool profiling = false;
+    static constexpr int kMaxEv = 2048;
+    cudaEvent_t evs[kMaxEv] = {};
+    int ev_stage[kMaxEv / 2] = {};
+    int nev = 0;
+    double stage_ms[OMM_NSTAGES] = {};
+    int64_t stage_launches[OMM_NSTAGES] = {};
 };
 
 namespace {
@@ -53,6 +61,8 @@ int dalloc(T **p, size_t count) {
 void free_handle(omm_handle *h) {
     if (h == nullptr) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < omm_handle::kMaxEv; ++i)
+        if (h->evs[i]) cudaEventDestroy(h->evs[i]);
     cudaFree(h->HS);
     cudaFree(h->WD);
     cudaFree(h->HDSD);
@@ -77,6 +87,37 @@ void free_handle(omm_handle *h) {
         if (rc_ != OMM_OK) return rc_;  \
     } while (0)
 
+// Stage timing: events around each stage launch while profiling is on;
+// harvested (summed per stage) at every host synchronisation point.
+struct StageTimer {
+    omm_handle *h;
+    int stage;
+    int slot = -1;
+    StageTimer(omm_handle *h_, int stage_) : h(h_), stage(stage_) {
+        if (!h->profiling || h->nev + 2 > omm_handle::kMaxEv) return;
+        slot = h->nev;
+        h->nev += 2;
+        for (int i = 0; i < 2; ++i)
+            if (!h->evs[slot + i]) cudaEventCreate(&h->evs[slot + i]);
+        h->ev_stage[slot / 2] = stage;
+        cudaEventRecord(h->evs[slot], h->stream);
+    }
+    ~StageTimer() {
+        if (slot >= 0) cudaEventRecord(h->evs[slot + 1], h->stream);
+    }
+};
+
+void harvest_stage_times(omm_handle *h) {
+    for (int e = 0; e + 1 < h->nev; e += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->evs[e], h->evs[e + 1]) == cudaSuccess) {
+            h->stage_ms[h->ev_stage[e / 2]] += ms;
+            h->stage_launches[h->ev_stage[e / 2]] += 1;
+        }
+    }
+    h->nev = 0;
+}
+
 // counters: 0 coeffs, 1 nn update, 2 dots, 3 gershgorin
 unsigned int *ctr(omm_handle *h, int i) { return h->counters + 64 * i; }
 double *scr(omm_handle *h, int i) {
@@ -93,25 +134,27 @@ int dense_iteration(omm_handle *h) {
     // H'D and S D
     b.A[0] = h->HS;          b.B[0] = h->WD + mn; b.C[0] = h->HDSD;      b.Cin[0] = nullptr;
     b.A[1] = h->HS + m * m;  b.B[1] = h->WD + mn; b.C[1] = h->HDSD + mn; b.Cin[1] = nullptr;
-    TRY(omm::dgemm_batched(false, false, m, n, m, 1.0, b, 2, m, m, 0.0, m, m, s, st));
+    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(omm::dgemm_batched(false, false, m, n, m, 1.0, b, 2, m, m, 0.0, m, m, s, st)); }
     // Z = [W D]^T [H'D SD]
     omm::GemmBatch z{};
     z.A[0] = h->WD; z.B[0] = h->HDSD; z.C[0] = h->Z;
-    TRY(omm::dgemm_batched(true, false, 2 * n, 2 * n, m, 1.0, z, 1, m, m, 0.0, 2 * n, 2 * n, s, st));
+    { StageTimer t(h, OMM_STAGE_CONTRACT); TRY(omm::dgemm_batched(true, false, 2 * n, 2 * n, m, 1.0, z, 1, m, m, 0.0, 2 * n, 2 * n, s, st)); }
     // quartic coefficients and its minimum
-    TRY(omm::launch_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 0),
-                                   ctr(h, 0), s, nullptr, st, true));
-    // W += x D, H'W += x H'D, SW += x SD
-    TRY(omm::launch_axpy3(mn, h->WD, h->WD + mn, h->SWHW + mn, h->HDSD, h->SWHW, h->HDSD + mn, s, st));
-    // H_W, S_W update, energy, RelTol test
-    TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
-                                     ctr(h, 1), s, 0, st));
+    { StageTimer t(h, OMM_STAGE_LINESEARCH);
+      TRY(omm::launch_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 0),
+                                     ctr(h, 0), s, nullptr, st, true)); }
+    // W += x D, H'W += x H'D, SW += x SD; then H_W, S_W update, energy, RelTol test
+    { StageTimer t(h, OMM_STAGE_UPDATE);
+      TRY(omm::launch_axpy3(mn, h->WD, h->WD + mn, h->SWHW + mn, h->HDSD, h->SWHW, h->HDSD + mn, s, st));
+      TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
+                                       ctr(h, 1), s, 0, st)); }
     // G = 4 H'W - 2 [SW H'W][H_W ; S_W]
     omm::GemmBatch g{};
     g.A[0] = h->SWHW; g.B[0] = h->h0s0; g.Cin[0] = h->SWHW + mn; g.C[0] = h->G;
-    TRY(omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, s, st));
-    TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 0, st));
-    TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st));
+    { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, s, st)); }
+    { StageTimer t(h, OMM_STAGE_DIRECTION);
+      TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 0, st));
+      TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st)); }
     return OMM_OK;
 }
 
@@ -246,12 +289,16 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
     init.eta = h->opt.eta;
     *h->hstate = init;
     OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
-    if (h->opt.eta_auto)
-        TRY(omm::launch_gershgorin(m, h->HS, h->HS + mm, scr(h, 3), ctr(h, 3), h->dstate, st));
-    TRY(omm::launch_shift(mm, h->HS, h->HS + mm, h->HS, h->dstate, st));
+    {
+        StageTimer t(h, OMM_STAGE_SETUP);
+        if (h->opt.eta_auto)
+            TRY(omm::launch_gershgorin(m, h->HS, h->HS + mm, scr(h, 3), ctr(h, 3), h->dstate, st));
+        TRY(omm::launch_shift(mm, h->HS, h->HS + mm, h->HS, h->dstate, st));
+    }
     OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    harvest_stage_times(h);
     if (h->hstate->status != OMM_OK) return h->hstate->status;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
@@ -280,12 +327,13 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
     init.n = (int)n;
     *h->hstate = init;
     OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
-    TRY(dense_start(h));
+    { StageTimer t(h, OMM_STAGE_START); TRY(dense_start(h)); }
     h->have_W = true;
     for (;;) {
         for (int c = 0; c < h->chunk; ++c) TRY(dense_iteration(h));
         OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
         OMM_CUDA_TRY(cudaStreamSynchronize(st));
+        harvest_stage_times(h);
         if (h->hstate->done) break;
     }
     OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
@@ -342,5 +390,28 @@ int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device) 
 }
 
 void omm_destroy(omm_handle *h) { free_handle(h); }
+
+int omm_set_profiling(omm_handle *h, int32_t on) {
+    if (h == nullptr) return OMM_ERR_ARG;
+    h->profiling = on != 0;
+    return OMM_OK;
+}
+
+int omm_get_stage_times(omm_handle *h, double *ms, int64_t *launches, int32_t nstages, int32_t reset) {
+    if (h == nullptr || nstages < 0) return OMM_ERR_ARG;
+    for (int i = 0; i < nstages && i < OMM_NSTAGES; ++i) {
+        if (ms) ms[i] = h->stage_ms[i];
+        if (launches) launches[i] = h->stage_launches[i];
+    }
+    if (reset) {
+        for (int i = 0; i < OMM_NSTAGES; ++i) {
+            h->stage_ms[i] = 0.0;
+            h->stage_launches[i] = 0;
+        }
+    }
+    return OMM_OK;
+}
+
+int64_t omm_kernel_launches(void) { return omm::launch_count(); }
 
 }  // extern "C"

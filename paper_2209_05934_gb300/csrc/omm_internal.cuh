@@ -8,6 +8,10 @@
 
 namespace omm {
 
+// process-wide count of kernels launched by the library (host side)
+int64_t launch_count();
+void count_launch(int64_t k = 1);
+
 #define OMM_CUDA_TRY(expr)                                   \
     do {                                                     \
         cudaError_t e_ = (expr);                             \

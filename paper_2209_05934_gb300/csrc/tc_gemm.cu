@@ -1,0 +1,494 @@
+// Split-BF16 tensor-core GEMM on tcgen05 (sm_103a), with FP64 epilogues.
+//
+// An FP64 operand x is carried as up to three BF16 "digits"
+//     d1 = bf16(x),  d2 = bf16(x - d1),  d3 = bf16(x - d1 - d2),
+// (24 significant bits in all; Markidis et al. 2018, Ootomo & Yokota 2022
+// split a wide operand into narrow tensor-core operands the same way).
+// Each BF16 x BF16 product is exact in the FP32 accumulator, so
+//     C ~= sum over chosen digit pairs (p, q) of A_p B_q
+// with FP32 accumulation in tensor memory.  The pairs with p + q <= 4
+// ((1,1),(1,2),(2,1),(1,3),(2,2),(3,1)) give FP32-level accuracy.
+//
+// Operands are K-major BF16 digit planes: A as [plane][M rows][lda], B as
+// [plane][N rows][ldb], K contiguous (ld a multiple of 8 elements).  One CTA
+// computes a 128 x BN tile: warp 0 issues TMA loads of every needed digit
+// tile of a 64-wide K block into one pipeline stage (128-byte swizzle), warp 1
+// issues tcgen05.mma for every digit pair on that stage, and warps 2..5 read
+// the FP32 accumulator from tensor memory and write C = alpha acc + beta Cin
+// in FP64 (column-major), optionally with the BF16 digits of C as well.
+// Every mbarrier wait is bounded; on timeout the kernel records an error and
+// unwinds (tensor memory is always released).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
+#include "omm_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace omm {
+namespace tc {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;           // 64 bf16 = 128 bytes = one swizzle row
+constexpr int TILE_A_BYTES = BM * BK * 2;
+constexpr uint64_t kWaitNs = 4000000000ull;   // 4 s per kernel, far above any real wait
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: gives up once the kernel-wide deadline
+// passes or another role of the CTA has already given up (`abort`), records
+// the error and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t deadline,
+                                          volatile int *abort, int *err) {
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(addr, parity)) return true;
+        if (*abort) return false;
+        if ((i & 63u) == 63u && globaltimer_ns() > deadline) {
+            *abort = 1;
+            if (err) atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// K-major, 128-byte swizzled shared-memory matrix descriptor: 8-row x 128-byte
+// core matrices stacked every 1024 bytes along M/N.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1u << 16;             // leading-dimension offset (unused when swizzled)
+    d |= (uint64_t)(1024u >> 4) << 32;   // stride-dimension offset: 1024 bytes
+    d |= (uint64_t)1u << 46;             // descriptor version for tcgen05
+    d |= (uint64_t)2u << 61;             // 128-byte swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void split3(double v, __nv_bfloat16 &d1, __nv_bfloat16 &d2, __nv_bfloat16 &d3) {
+    d1 = __double2bfloat16(v);
+    const double r1 = v - (double)__bfloat162float(d1);
+    d2 = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(d2);
+    d3 = __double2bfloat16(r2);
+}
+
+// ------------------------------------------------------------------ the GEMM kernel
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const TcArgs args) {
+    if (args.state != nullptr && *((volatile const int *)&args.state->done)) return;
+    const int z = blockIdx.z;
+    const int nA = args.nA, nB = args.nB;
+    const int tileB = BN * BK * 2;
+    const int stage_bytes = nA * TILE_A_BYTES + nB * tileB;
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES];
+    __shared__ __align__(8) uint64_t empty_bar[STAGES];
+    __shared__ __align__(8) uint64_t acc_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const uint64_t deadline = globaltimer_ns() + kWaitNs;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int nkb = (args.K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&acc_bar, 1);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        const int a_row = z * args.a_row_step + m0;
+        const int b_row = z * args.b_row_step + n0;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+            if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, args.err)) break;
+            mbar_arrive_expect_tx(&full_bar[s], (uint32_t)stage_bytes);
+            uint8_t *st = smem + s * stage_bytes;
+            for (int p = 0; p < nA; ++p)
+                tma_load_3d(st + p * TILE_A_BYTES, &mapA, kb * BK, a_row, p, &full_bar[s]);
+            for (int q = 0; q < nB; ++q)
+                tma_load_3d(st + nA * TILE_A_BYTES + q * tileB, &mapB, kb * BK, b_row, q, &full_bar[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(BM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+            if (!mbar_wait(&full_bar[s], ph, deadline, &abort_flag, args.err)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + s * stage_bytes);
+            for (int pr = 0; pr < args.npairs; ++pr) {
+                const uint32_t sa = st + args.pa[pr] * TILE_A_BYTES;
+                const uint32_t sb = st + nA * TILE_A_BYTES + args.pb[pr] * tileB;
+                const uint64_t da = sdesc_sw128(sa), db = sdesc_sw128(sb);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    // advance 16 elements (32 bytes) along K inside the swizzle row
+                    umma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                              (kb | pr | kk) != 0 ? 1u : 0u);
+                }
+            }
+            umma_commit(&empty_bar[s]);
+        }
+        umma_commit(&acc_bar);
+    } else if (warp >= 2) {
+        // ---------------- epilogue: TMEM -> registers -> FP64 global
+        const int q = warp & 3;              // TMEM lane quarter this warp may access
+        const int row = m0 + 32 * q + lane;
+        bool got = nkb > 0 && mbar_wait(&acc_bar, 0, deadline, &abort_flag, args.err);
+        const bool have_acc = __all_sync(0xffffffffu, got);   // tcgen05.ld is warp-collective
+        tc_fence_after();
+        double *C = args.C + (int64_t)z * args.c_step;
+        const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
+        __nv_bfloat16 *Dd = args.Dout ? args.Dout + (int64_t)z * args.dout_step : nullptr;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            if (have_acc) {
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            }
+            if (row < args.M) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = n0 + c0 + i;
+                    if (col >= args.N) break;
+                    double out = args.alpha * (double)v[i];
+                    if (Cin != nullptr) out = fma(args.beta, Cin[row + (int64_t)col * args.ldcin], out);
+                    C[row + (int64_t)col * args.ldc] = out;
+                    if (Dd != nullptr) {
+                        __nv_bfloat16 d1, d2, d3;
+                        split3(out, d1, d2, d3);
+                        const int64_t o = row + (int64_t)col * args.ldd;
+                        Dd[o] = d1;
+                        if (args.ndig > 1) Dd[args.dplane + o] = d2;
+                        if (args.ndig > 2) Dd[2 * args.dplane + o] = d3;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, BN);
+    }
+}
+
+// ------------------------------------------------------------------ digit packing
+// column-major source (rows x cols, ld_src) -> planes [ndig][cols][ldd], element
+// (i, j) at j*ldd + i (the K-major layout when K runs along the rows).
+__global__ void pack_cm_kernel(int64_t rows, int64_t cols, const double *__restrict__ src, int64_t ld_src,
+                               __nv_bfloat16 *dst, int64_t ldd, int64_t plane, int ndig,
+                               const DevState *state) {
+    if (state != nullptr && *((volatile const int *)&state->done)) return;
+    const int64_t total = rows * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t % rows, j = t / rows;
+        __nv_bfloat16 d1, d2, d3;
+        split3(src[i + j * ld_src], d1, d2, d3);
+        const int64_t o = j * ldd + i;
+        dst[o] = d1;
+        if (ndig > 1) dst[plane + o] = d2;
+        if (ndig > 2) dst[2 * plane + o] = d3;
+    }
+}
+
+// column-major source (rows x cols) -> planes [ndig][rows][ldd], element (i, j)
+// at i*ldd + j (K-major when K runs along the columns); 32x32 smem transpose.
+__global__ void pack_t_kernel(int64_t rows, int64_t cols, const double *__restrict__ src, int64_t ld_src,
+                              __nv_bfloat16 *dst, int64_t ldd, int64_t plane, int ndig,
+                              const DevState *state) {
+    if (state != nullptr && *((volatile const int *)&state->done)) return;
+    __shared__ double tile[32][33];
+    const int64_t ti = (int64_t)blockIdx.x * 32, tj = (int64_t)blockIdx.y * 32;
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;   // 32 x 8 threads
+    for (int r = ly; r < 32; r += 8) {
+        const int64_t i = ti + lx, j = tj + r;
+        tile[r][lx] = (i < rows && j < cols) ? src[i + j * ld_src] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ly; r < 32; r += 8) {
+        const int64_t i = ti + r, j = tj + lx;
+        if (i < rows && j < cols) {
+            __nv_bfloat16 d1, d2, d3;
+            split3(tile[lx][r], d1, d2, d3);
+            const int64_t o = i * ldd + j;
+            dst[o] = d1;
+            if (ndig > 1) dst[plane + o] = d2;
+            if (ndig > 2) dst[2 * plane + o] = d3;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (fn == nullptr) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+template <int BN, int STAGES>
+int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int nbatch, cudaStream_t st) {
+    const int smem = STAGES * (a.nA * TILE_A_BYTES + a.nB * BN * BK * 2) + 1024;
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024) != cudaSuccess)
+            return OMM_ERR_CUDA;
+        attr_set = true;
+    }
+    if (smem > 227 * 1024) return OMM_ERR_ARG;
+    dim3 grid((unsigned)ceil_div(a.M, BM), (unsigned)ceil_div(a.N, BN), (unsigned)nbatch);
+    tc_gemm_kernel<BN, STAGES><<<grid, 192, smem, st>>>(ma, mb, a);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+}  // namespace
+
+int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
+                   int64_t plane_elems, int nplanes, int box_rows) {
+    auto enc = encode_fn();
+    if (enc == nullptr) return OMM_ERR_CUDA;
+    if ((ld % 8) != 0 || (plane_elems % 8) != 0 || (((uintptr_t)base) & 15u) != 0) return OMM_ERR_ARG;
+    if (K <= 0 || rows <= 0 || nplanes <= 0 || box_rows <= 0 || box_rows > 256) return OMM_ERR_ARG;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nplanes};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)plane_elems * 2};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    memset(map, 0, sizeof(*map));
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? OMM_OK : OMM_ERR_CUDA;
+}
+
+int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int nbatch, int bn,
+         cudaStream_t st) {
+    if (a.M <= 0 || a.N <= 0 || a.K < 0 || a.nA < 1 || a.nA > 3 || a.nB < 1 || a.nB > 3) return OMM_ERR_ARG;
+    if (a.npairs < 1 || a.npairs > 9 || nbatch < 1) return OMM_ERR_ARG;
+    for (int p = 0; p < a.npairs; ++p)
+        if (a.pa[p] >= a.nA || a.pb[p] >= a.nB) return OMM_ERR_ARG;
+    if (bn == 256) {
+        if (a.nA + 2 * a.nB <= 4) return launch_tc<256, 3>(mapA, mapB, a, nbatch, st);
+        return launch_tc<256, 1>(mapA, mapB, a, nbatch, st);
+    }
+    if (a.nA + a.nB <= 4) return launch_tc<128, 3>(mapA, mapB, a, nbatch, st);
+    return launch_tc<128, 2>(mapA, mapB, a, nbatch, st);
+}
+
+int pack_cm(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,
+            int64_t plane, int ndig, const DevState *state, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return OMM_OK;
+    int64_t nb = ceil_div(rows * cols, 256 * 4);
+    if (nb > 152 * 16) nb = 152 * 16;
+    pack_cm_kernel<<<(unsigned)nb, 256, 0, st>>>(rows, cols, src, ld_src, dst, ldd, plane, ndig, state);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int pack_t(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,
+           int64_t plane, int ndig, const DevState *state, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return OMM_OK;
+    dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32));
+    pack_t_kernel<<<grid, 256, 0, st>>>(rows, cols, src, ld_src, dst, ldd, plane, ndig, state);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+void pairs_for_digits(int ndig, TcArgs &a) {
+    // digit pairs (p, q) with p + q <= ndig + 1 (1-based), smallest terms first
+    int k = 0;
+    for (int lvl = ndig + 1; lvl >= 2; --lvl)
+        for (int p = 1; p <= ndig; ++p) {
+            const int q = lvl - p;
+            if (q < 1 || q > ndig) continue;
+            a.pa[k] = (uint8_t)(p - 1);
+            a.pb[k] = (uint8_t)(q - 1);
+            ++k;
+        }
+    a.npairs = k;
+    a.nA = ndig;
+    a.nB = ndig;
+}
+
+}  // namespace tc
+}  // namespace omm
+
+// ---------------------------------------------------------------- op-level entry
+extern "C" int64_t omm_op_split_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int32_t ndigits) {
+    if (M < 0 || N < 0 || K < 0 || ndigits < 1 || ndigits > 3) return -1;
+    const int64_t ldk = (K + 7) / 8 * 8;
+    return (int64_t)ndigits * (M + N) * ldk * 2 + 1024;
+}
+
+extern "C" int omm_op_split_gemm(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K,
+                                 int32_t ndigits, double alpha, const double *A, int64_t lda,
+                                 const double *B, int64_t ldb, double beta, const double *Cin,
+                                 int64_t ldcin, double *C, int64_t ldc, void *workspace,
+                                 int64_t workspace_bytes, void *stream) {
+    using namespace omm;
+    if (M <= 0 || N <= 0 || K <= 0 || ndigits < 1 || ndigits > 3) return OMM_ERR_ARG;
+    if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return OMM_ERR_ARG;
+    if (A == nullptr || B == nullptr || C == nullptr || workspace == nullptr) return OMM_ERR_ARG;
+    if (lda < (transA ? K : M) || ldb < (transB ? N : K) || ldc < M) return OMM_ERR_ARG;
+    if (beta != 0.0 && (Cin == nullptr || ldcin < M)) return OMM_ERR_ARG;
+    if (workspace_bytes < omm_op_split_gemm_workspace_bytes(M, N, K, ndigits)) return OMM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ldk = (K + 7) / 8 * 8;
+    uintptr_t base = ((uintptr_t)workspace + 255) & ~(uintptr_t)255;
+    __nv_bfloat16 *Ad = (__nv_bfloat16 *)base;
+    __nv_bfloat16 *Bd = Ad + (int64_t)ndigits * M * ldk;
+    if ((((uintptr_t)Bd) & 15u) != 0) return OMM_ERR_ARG;
+    int rc;
+    // op(A) is M x K: K-major rows of op(A)
+    if (transA) rc = tc::pack_cm(K, M, A, lda, Ad, ldk, M * ldk, ndigits, nullptr, st);
+    else rc = tc::pack_t(M, K, A, lda, Ad, ldk, M * ldk, ndigits, nullptr, st);
+    if (rc) return rc;
+    // op(B) is K x N: K-major rows are the columns of op(B)
+    if (transB) rc = tc::pack_t(N, K, B, ldb, Bd, ldk, N * ldk, ndigits, nullptr, st);
+    else rc = tc::pack_cm(K, N, B, ldb, Bd, ldk, N * ldk, ndigits, nullptr, st);
+    if (rc) return rc;
+    CUtensorMap ma, mb;
+    if ((rc = tc::make_digit_map(&ma, Ad, K, M, ldk, M * ldk, ndigits, 128))) return rc;
+    const int bn = (N > 128 && ndigits == 1) ? 256 : 128;
+    if ((rc = tc::make_digit_map(&mb, Bd, K, N, ldk, N * ldk, ndigits, bn))) return rc;
+    tc::TcArgs a{};
+    tc::pairs_for_digits(ndigits, a);
+    a.M = (int)M;
+    a.N = (int)N;
+    a.K = (int)K;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.Cin = beta != 0.0 ? Cin : nullptr;
+    a.ldcin = ldcin;
+    a.C = C;
+    a.ldc = ldc;
+    a.err = nullptr;
+    return tc::gemm(ma, mb, a, 1, bn, st);
+}

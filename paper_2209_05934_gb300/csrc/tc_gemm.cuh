@@ -1,0 +1,45 @@
+// Split-BF16 tcgen05 GEMM: host-side interface inside the library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "omm_internal.cuh"
+
+namespace omm {
+namespace tc {
+
+// Arguments of one (optionally z-batched) split GEMM
+//   C_z = alpha * sum_pairs A_{pa} B_{pb}^T + beta * Cin_z
+// with A, B given by 3-D tensor maps over BF16 digit planes [plane][rows][ld];
+// batch z reads A rows from z*a_row_step and B rows from z*b_row_step.
+struct TcArgs {
+    int M, N, K;
+    int nA, nB;                  // digit planes loaded per operand
+    int npairs;
+    uint8_t pa[9], pb[9];        // digit pairs (0-based plane indices)
+    int a_row_step, b_row_step;
+    double alpha, beta;
+    const double *Cin;           // nullable
+    int64_t ldcin, cin_step;
+    double *C;                   // FP64 column-major output
+    int64_t ldc, c_step;
+    __nv_bfloat16 *Dout;         // nullable: BF16 digits of C, planes [ndig][..][ldd]
+    int64_t ldd, dplane, dout_step;
+    int ndig;
+    const DevState *state;       // nullable: return at once when state->done
+    int *err;                    // nullable: set to 1 when a bounded wait times out
+};
+
+int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
+                   int64_t plane_elems, int nplanes, int box_rows);
+int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int nbatch, int bn,
+         cudaStream_t st);
+int pack_cm(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,
+            int64_t plane, int ndig, const DevState *state, cudaStream_t st);
+int pack_t(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,
+           int64_t plane, int ndig, const DevState *state, cudaStream_t st);
+void pairs_for_digits(int ndig, TcArgs &a);
+
+}  // namespace tc
+}  // namespace omm

@@ -67,7 +67,17 @@ _SIGS = {
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_int64, C.c_void_p]),
     "omm_op_line_min": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "omm_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "omm_get_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
+    "omm_kernel_launches": (C.c_int64, []),
+    "omm_op_split_gemm_workspace_bytes": (C.c_int64, [C.c_int64, C.c_int64, C.c_int64, C.c_int32]),
+    "omm_op_split_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                    C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                    C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                    C.c_void_p, C.c_int64, C.c_void_p]),
 }
+
+NSTAGES = 10
 
 
 def lib():
@@ -202,6 +212,16 @@ class Solver:
         check(lib().omm_get_diag(self._h, C.byref(d)), "omm_get_diag")
         return d
 
+    def set_profiling(self, on: bool):
+        check(lib().omm_set_profiling(self._h, int(on)), "omm_set_profiling")
+
+    def stage_times(self, reset: bool = False):
+        ms = np.zeros(NSTAGES)
+        cnt = np.zeros(NSTAGES, dtype=np.int64)
+        check(lib().omm_get_stage_times(self._h, C.c_void_p(ms.ctypes.data), C.c_void_p(cnt.ctypes.data),
+                                        NSTAGES, int(reset)), "omm_get_stage_times")
+        return ms, cnt
+
     def get_array(self, which: int) -> np.ndarray:
         rows = self.n if which in (ARRAY_HW_N, ARRAY_SW_N) else self.m
         out = np.zeros((rows, self.n), order="F")
@@ -214,6 +234,22 @@ def op_dgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C
     return lib().omm_op_dgemm(int(transA), int(transB), M, N, K, float(alpha), _ptr(A)[0], lda,
                               _ptr(B)[0], ldb, float(beta), _ptr(Cin)[0], ldcin, _ptr(Cout)[0], ldc,
                               C.c_void_p(stream) if stream else None)
+
+
+def kernel_launches() -> int:
+    return int(lib().omm_kernel_launches())
+
+
+def op_split_gemm_workspace_bytes(M, N, K, ndigits) -> int:
+    return int(lib().omm_op_split_gemm_workspace_bytes(M, N, K, ndigits))
+
+
+def op_split_gemm(transA, transB, M, N, K, ndigits, alpha, A, lda, B, ldb, beta, Cin, ldcin, Cout, ldc,
+                  workspace, workspace_bytes, stream=0):
+    return lib().omm_op_split_gemm(int(transA), int(transB), M, N, K, int(ndigits), float(alpha),
+                                   _ptr(A)[0], lda, _ptr(B)[0], ldb, float(beta), _ptr(Cin)[0], ldcin,
+                                   _ptr(Cout)[0], ldc, _ptr(workspace)[0], workspace_bytes,
+                                   C.c_void_p(stream) if stream else None)
 
 
 def op_quartic_coeffs_scratch_bytes(n: int) -> int:
