@@ -165,6 +165,10 @@ int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device);
 void omm_destroy(omm_handle *h);
 const char *omm_status_str(int status);
 
+/* Human-readable detail of the last failure on the calling thread (which
+ * CUDA call failed and why); empty when none.  Owned by the library. */
+const char *omm_last_error(void);
+
 /*
  * Per-stage device timing of a handle.  While profiling is on, the library
  * records CUDA events on the handle's stream around each stage of every CG

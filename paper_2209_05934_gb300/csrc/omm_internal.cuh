@@ -12,10 +12,17 @@ namespace omm {
 int64_t launch_count();
 void count_launch(int64_t k = 1);
 
-#define OMM_CUDA_TRY(expr)                                   \
-    do {                                                     \
-        cudaError_t e_ = (expr);                             \
-        if (e_ != cudaSuccess) return OMM_ERR_CUDA;          \
+// thread-local description of the last failure (omm_last_error)
+void set_error(const char *fmt, ...);
+
+#define OMM_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            ::omm::set_error("%s:%d: %s -> %s", __FILE__, __LINE__, #expr,              \
+                             cudaGetErrorString(e_));                                   \
+            return OMM_ERR_CUDA;                                                        \
+        }                                                                               \
     } while (0)
 
 // Device-resident CG state of one solve.  Kernels of an iteration read `done`

@@ -342,8 +342,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
         void *p = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
+            q != cudaDriverEntryPointSuccess) {
+            set_error("cuTensorMapEncodeTiled entry point unavailable");
             return nullptr;
+        }
         fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
     }
     return fn;
@@ -352,14 +354,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 template <int BN, int STAGES>
 int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int nbatch, cudaStream_t st) {
     const int smem = STAGES * (a.nA * TILE_A_BYTES + a.nB * BN * BK * 2) + 1024;
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024) != cudaSuccess)
-            return OMM_ERR_CUDA;
-        attr_set = true;
+    static int attr_bytes = 0;
+    if (smem > attr_bytes) {
+        OMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_bytes = smem;
     }
-    if (smem > 227 * 1024) return OMM_ERR_ARG;
     dim3 grid((unsigned)ceil_div(a.M, BM), (unsigned)ceil_div(a.N, BN), (unsigned)nbatch);
     tc_gemm_kernel<BN, STAGES><<<grid, 192, smem, st>>>(ma, mb, a);
     count_launch();
@@ -383,7 +383,12 @@ int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? OMM_OK : OMM_ERR_CUDA;
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d): K=%lld rows=%lld ld=%lld planes=%d box_rows=%d",
+                  (int)r, (long long)K, (long long)rows, (long long)ld, nplanes, box_rows);
+        return OMM_ERR_CUDA;
+    }
+    return OMM_OK;
 }
 
 int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int nbatch, int bn,

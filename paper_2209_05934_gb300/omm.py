@@ -70,6 +70,7 @@ _SIGS = {
     "omm_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "omm_get_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "omm_kernel_launches": (C.c_int64, []),
+    "omm_last_error": (C.c_char_p, []),
     "omm_op_split_gemm_workspace_bytes": (C.c_int64, [C.c_int64, C.c_int64, C.c_int64, C.c_int32]),
     "omm_op_split_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                     C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
@@ -100,7 +101,9 @@ class OmmError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
         msg = lib().omm_status_str(status).decode()
-        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+        detail = lib().omm_last_error().decode()
+        msg = f"{msg} ({status})" + (f" [{detail}]" if detail else "")
+        super().__init__(f"{what}: {msg}" if what else msg)
 
 
 def check(status, what=""):

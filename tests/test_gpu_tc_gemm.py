@@ -27,7 +27,7 @@ def run_split(omm, tA, tB, M, N, K, nd, A, B, alpha=1.0, beta=0.0, Cin=None):
     ws = torch.zeros(nb // 8 + 64, dtype=torch.float64, device="cuda")
     st = omm.op_split_gemm(tA, tB, M, N, K, nd, alpha, dev(A), A.shape[0], dev(B), B.shape[0], beta,
                            dev(Cin) if Cin is not None else None, M, out, M, ws, nb)
-    assert st == omm.OK
+    assert st == omm.OK, omm.lib().omm_last_error()
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
