@@ -18,6 +18,20 @@
 #include <new>
 
 #include "omm_internal.cuh"
+#include "tc_gemm.cuh"
+
+// Mixed-precision buffers: BF16 digit planes (three digits, K-major) of the
+// operands of the split tensor-core products, and their TMA descriptors.
+//   HSd   [3][2m][ldm]   columns of [H' | S] (= rows, symmetric)   A of H'D, SD
+//   WDd   [3][2n][ldm]   columns of [W | D]                         A of Z; B of H'D, SD
+//   HDSDd [3][2n][ldm]   columns of [H'D | SD]                      B of Z
+//   SWHWd [3][m][ld2n]   rows of [SW | H'W]                         A of the gradient
+//   HSWd  [3][n][ld2n]   columns of [H_W ; S_W]                     B of the gradient
+struct MixedBufs {
+    int64_t ldm = 0, ld2n = 0;
+    __nv_bfloat16 *HSd = nullptr, *WDd = nullptr, *HDSDd = nullptr, *SWHWd = nullptr, *HSWd = nullptr;
+    CUtensorMap mapHS_A, mapWD_A, mapWD_B, mapHDSD_B, mapSWHW_A, mapHSW_B;
+};
 
 struct omm_handle {
     int64_t m = 0, n = 0;
@@ -36,6 +50,7 @@ struct omm_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     omm_diag diag{};
     int chunk = 8;
+    MixedBufs mx;
     // optional per-stage device timing (omm_set_profiling)
     bool profiling = false;
     static constexpr int kMaxEv = 2048;
@@ -74,6 +89,11 @@ void free_handle(omm_handle *h) {
     cudaFree(h->scratch);
     cudaFree(h->counters);
     cudaFree(h->dstate);
+    cudaFree(h->mx.HSd);
+    cudaFree(h->mx.WDd);
+    cudaFree(h->mx.HDSDd);
+    cudaFree(h->mx.SWHWd);
+    cudaFree(h->mx.HSWd);
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -182,6 +202,192 @@ int dense_start(omm_handle *h) {
     return OMM_OK;
 }
 
+// ---------------------------------------------------------------- mixed precision
+constexpr int kDig = 3;
+
+omm::tc::TcArgs tc_args(omm_handle *h, int M, int N, int K) {
+    omm::tc::TcArgs a{};
+    omm::tc::pairs_for_digits(kDig, a);
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.alpha = 1.0;
+    a.beta = 0.0;
+    a.state = h->dstate;
+    a.err = &h->dstate->wait_timeout;
+    return a;
+}
+
+int mixed_alloc(omm_handle *h) {
+    const int64_t m = h->m, n = h->n;
+    MixedBufs &x = h->mx;
+    x.ldm = (m + 7) / 8 * 8;
+    x.ld2n = (2 * n + 7) / 8 * 8;
+    TRY(dalloc(&x.HSd, (size_t)(kDig * 2 * m * x.ldm)));
+    TRY(dalloc(&x.WDd, (size_t)(kDig * 2 * n * x.ldm)));
+    TRY(dalloc(&x.HDSDd, (size_t)(kDig * 2 * n * x.ldm)));
+    TRY(dalloc(&x.SWHWd, (size_t)(kDig * m * x.ld2n)));
+    TRY(dalloc(&x.HSWd, (size_t)(kDig * n * x.ld2n)));
+    TRY(omm::tc::make_digit_map(&x.mapHS_A, x.HSd, m, 2 * m, x.ldm, 2 * m * x.ldm, kDig, 128));
+    TRY(omm::tc::make_digit_map(&x.mapWD_A, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128));
+    TRY(omm::tc::make_digit_map(&x.mapWD_B, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128));
+    TRY(omm::tc::make_digit_map(&x.mapHDSD_B, x.HDSDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128));
+    TRY(omm::tc::make_digit_map(&x.mapSWHW_A, x.SWHWd, 2 * n, m, x.ld2n, m * x.ld2n, kDig, 128));
+    TRY(omm::tc::make_digit_map(&x.mapHSW_B, x.HSWd, 2 * n, n, x.ld2n, n * x.ld2n, kDig, 128));
+    return OMM_OK;
+}
+
+int pack_W(omm_handle *h) {
+    const MixedBufs &x = h->mx;
+    return omm::tc::pack_cm(h->m, h->n, h->WD, h->m, x.WDd, x.ldm, 2 * h->n * x.ldm, kDig, h->dstate,
+                            h->stream);
+}
+int pack_D(omm_handle *h) {
+    const MixedBufs &x = h->mx;
+    return omm::tc::pack_cm(h->m, h->n, h->WD + h->m * h->n, h->m, x.WDd + h->n * x.ldm, x.ldm,
+                            2 * h->n * x.ldm, kDig, h->dstate, h->stream);
+}
+int pack_SWHW(omm_handle *h) {
+    const MixedBufs &x = h->mx;
+    return omm::tc::pack_t(h->m, 2 * h->n, h->SWHW, h->m, x.SWHWd, x.ld2n, h->m * x.ld2n, kDig, h->dstate,
+                           h->stream);
+}
+int pack_HSW(omm_handle *h) {
+    const MixedBufs &x = h->mx;
+    return omm::tc::pack_cm(2 * h->n, h->n, h->h0s0, 2 * h->n, x.HSWd, x.ld2n, h->n * x.ld2n, kDig,
+                            h->dstate, h->stream);
+}
+
+// [H'; S] times the digits of W (rows b_row0 = 0) or D (b_row0 = n) of WDd:
+// FP64 results to C (H' part) and C + c_step (S part), digits to HDSDd.
+int split_products(omm_handle *h, int b_row0, double *C, int64_t c_step, int64_t dout_row0,
+                   int64_t dout_step) {
+    const int64_t m = h->m, n = h->n;
+    MixedBufs &x = h->mx;
+    omm::tc::TcArgs a = tc_args(h, (int)m, (int)n, (int)m);
+    a.a_row0 = 0;
+    a.a_row_step = (int)m;
+    a.b_row0 = b_row0;
+    a.b_row_step = 0;
+    a.C = C;
+    a.ldc = m;
+    a.c_step = c_step;
+    a.Dout = x.HDSDd + dout_row0 * x.ldm;
+    a.ldd = x.ldm;
+    a.dplane = 2 * n * x.ldm;
+    a.dout_step = dout_step * x.ldm;
+    a.ndig = kDig;
+    return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, 128, h->stream);
+}
+
+// Z = [W D]^T [H'D SD]
+int split_contract(omm_handle *h) {
+    const int64_t m = h->m, n = h->n;
+    MixedBufs &x = h->mx;
+    omm::tc::TcArgs a = tc_args(h, (int)(2 * n), (int)(2 * n), (int)m);
+    a.C = h->Z;
+    a.ldc = 2 * n;
+    return omm::tc::gemm(x.mapWD_A, x.mapHDSD_B, a, 1, 128, h->stream);
+}
+
+// G = 4 H'W - 2 [SW H'W][H_W ; S_W]
+int split_gradient(omm_handle *h) {
+    const int64_t m = h->m, n = h->n;
+    MixedBufs &x = h->mx;
+    omm::tc::TcArgs a = tc_args(h, (int)m, (int)n, (int)(2 * n));
+    a.alpha = -2.0;
+    a.beta = 4.0;
+    a.Cin = h->SWHW + m * n;
+    a.ldcin = m;
+    a.C = h->G;
+    a.ldc = m;
+    return omm::tc::gemm(x.mapSWHW_A, x.mapHSW_B, a, 1, 128, h->stream);
+}
+
+int fp64_gradient(omm_handle *h) {
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    omm::GemmBatch g{};
+    g.A[0] = h->SWHW; g.B[0] = h->h0s0; g.Cin[0] = h->SWHW + mn; g.C[0] = h->G;
+    return omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, h->dstate, h->stream);
+}
+
+// Start of the split-precision phase: H'W, SW, H_W, S_W, energy, G, D from W.
+int mixed_start(omm_handle *h) {
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    cudaStream_t st = h->stream;
+    omm::DevState *s = h->dstate;
+    { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
+    // H'W -> SWHW + mn, SW -> SWHW; their digits to HDSDd rows [0, n) and [n, 2n)
+    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(split_products(h, 0, h->SWHW + mn, -mn, 0, n)); }
+    {
+        StageTimer t(h, OMM_STAGE_CONTRACT);
+        omm::tc::TcArgs a = tc_args(h, (int)n, (int)n, (int)m);
+        a.b_row_step = (int)n;    // z = 0: H'W digits, z = 1: SW digits
+        a.C = h->h0s0;
+        a.ldc = 2 * n;
+        a.c_step = n;             // H_W in rows [0, n), S_W in rows [n, 2n)
+        TRY(omm::tc::gemm(h->mx.mapWD_A, h->mx.mapHDSD_B, a, 2, 128, st));
+    }
+    TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
+                                     ctr(h, 1), s, 1, st));
+    { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_SWHW(h)); TRY(pack_HSW(h)); }
+    { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(split_gradient(h)); }
+    {
+        StageTimer t(h, OMM_STAGE_DIRECTION);
+        TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 1, st));
+        TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st));
+    }
+    { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_D(h)); }
+    return OMM_OK;
+}
+
+// One CG step with split-precision products; accurate_gradient selects the
+// FP64 gradient of the refinement sweep.
+int mixed_iteration(omm_handle *h, bool accurate_gradient) {
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    cudaStream_t st = h->stream;
+    omm::DevState *s = h->dstate;
+    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(split_products(h, (int)n, h->HDSD, mn, 0, n)); }
+    { StageTimer t(h, OMM_STAGE_CONTRACT); TRY(split_contract(h)); }
+    { StageTimer t(h, OMM_STAGE_LINESEARCH);
+      TRY(omm::launch_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 0),
+                                     ctr(h, 0), s, nullptr, st, true)); }
+    { StageTimer t(h, OMM_STAGE_UPDATE);
+      TRY(omm::launch_axpy3(mn, h->WD, h->WD + mn, h->SWHW + mn, h->HDSD, h->SWHW, h->HDSD + mn, s, st));
+      TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
+                                       ctr(h, 1), s, 0, st)); }
+    if (accurate_gradient) {
+        { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
+        { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(fp64_gradient(h)); }
+    } else {
+        { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); TRY(pack_SWHW(h)); TRY(pack_HSW(h)); }
+        { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(split_gradient(h)); }
+    }
+    { StageTimer t(h, OMM_STAGE_DIRECTION);
+      TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 0, st));
+      TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st)); }
+    { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_D(h)); }
+    return OMM_OK;
+}
+
+// Run chunks of iterations until the device state says done; checks the
+// bounded-wait error word after every chunk.
+template <class F>
+int run_until_done(omm_handle *h, F iteration) {
+    for (;;) {
+        for (int c = 0; c < h->chunk; ++c) TRY(iteration());
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost,
+                                     h->stream));
+        OMM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        harvest_stage_times(h);
+        if (h->hstate->wait_timeout) {
+            omm::set_error("a bounded mbarrier wait in the tensor-core GEMM timed out");
+            return OMM_ERR_TIMEOUT;
+        }
+        if (h->hstate->done) return OMM_OK;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -235,7 +441,7 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         delete h;
         return OMM_ERR_ARG;
     }
-    if (h->opt.cholesky != 0 || h->opt.precision != OMM_PREC_FP64) {
+    if (h->opt.cholesky != 0 || (h->opt.precision != OMM_PREC_FP64 && h->opt.precision != OMM_PREC_MIXED)) {
         delete h;
         return OMM_ERR_UNSUPPORTED;
     }
@@ -257,6 +463,10 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         (rc = dalloc(&h->Gp, (size_t)mn)) ||
         (rc = dalloc(&h->scratch, (size_t)(4 * omm::kRedBlocksMax * omm::kRedSlots))) ||
         (rc = dalloc(&h->counters, (size_t)(64 * 8))) || (rc = dalloc(&h->dstate, 1))) {
+        free_handle(h);
+        return rc;
+    }
+    if (h->opt.precision == OMM_PREC_MIXED && (rc = mixed_alloc(h))) {
         free_handle(h);
         return rc;
     }
@@ -295,6 +505,11 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
             TRY(omm::launch_gershgorin(m, h->HS, h->HS + mm, scr(h, 3), ctr(h, 3), h->dstate, st));
         TRY(omm::launch_shift(mm, h->HS, h->HS + mm, h->HS, h->dstate, st));
     }
+    if (h->opt.precision == OMM_PREC_MIXED) {
+        // columns of [H' | S] become the K-major rows of the A operand (symmetric)
+        StageTimer t(h, OMM_STAGE_PACK);
+        TRY(omm::tc::pack_cm(m, 2 * m, h->HS, m, h->mx.HSd, h->mx.ldm, 2 * m * h->mx.ldm, kDig, nullptr, st));
+    }
     OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -327,14 +542,33 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
     init.n = (int)n;
     *h->hstate = init;
     OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
-    { StageTimer t(h, OMM_STAGE_START); TRY(dense_start(h)); }
-    h->have_W = true;
-    for (;;) {
-        for (int c = 0; c < h->chunk; ++c) TRY(dense_iteration(h));
-        OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
-        OMM_CUDA_TRY(cudaStreamSynchronize(st));
-        harvest_stage_times(h);
-        if (h->hstate->done) break;
+    int k_mixed = 0;
+    if (h->opt.precision == OMM_PREC_MIXED) {
+        // phase 1: split-precision CG to a tolerance a decade below the target
+        omm::DevState ph = init;
+        ph.tol = fmax(0.1 * tol, 1e-12);
+        ph.orth_tol = 0.0;
+        *h->hstate = ph;
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
+        { StageTimer t(h, OMM_STAGE_START); TRY(mixed_start(h)); }
+        h->have_W = true;
+        TRY(run_until_done(h, [&] { return mixed_iteration(h, false); }));
+        k_mixed = h->hstate->k;
+        if (h->hstate->status == OMM_OK) {
+            // phase 2: refinement sweep -- FP64 re-anchoring of H'W, SW, H_W,
+            // S_W and G, then CG steps with an FP64 gradient
+            omm::DevState rf = init;
+            rf.k = k_mixed;
+            *h->hstate = rf;
+            OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
+            { StageTimer t(h, OMM_STAGE_ANCHOR); TRY(dense_start(h)); }
+            { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); TRY(pack_D(h)); }
+            TRY(run_until_done(h, [&] { return mixed_iteration(h, true); }));
+        }
+    } else {
+        { StageTimer t(h, OMM_STAGE_START); TRY(dense_start(h)); }
+        h->have_W = true;
+        TRY(run_until_done(h, [&] { return dense_iteration(h); }));
     }
     OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
     if (W_out != nullptr)
@@ -353,8 +587,8 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
     h->diag.charge = 2.0 * ((double)n - s.orth2);
     h->diag.iters = s.k;
     h->diag.status = s.status;
-    h->diag.iters_mixed = 0;
-    h->diag.iters_refine = s.k;
+    h->diag.iters_mixed = k_mixed;
+    h->diag.iters_refine = s.k - k_mixed;
     if (E_out) *E_out = s.E;
     if (iters_out) *iters_out = s.k;
     return s.status;

@@ -43,6 +43,7 @@ struct DevState {
     double beta;
     double trh0, sh, orth2;      // tr h0, <s0,h0>, ||s0 - I||_F^2
     double charge;
+    int wait_timeout;            // set by a tensor-core kernel whose bounded wait gave up
 };
 
 // -------- FP64 GEMM (dense_fp64.cu)

