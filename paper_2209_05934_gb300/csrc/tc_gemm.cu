@@ -7,7 +7,11 @@
 // Each BF16 x BF16 product is exact in the FP32 accumulator, so
 //     C ~= sum over chosen digit pairs (p, q) of A_p B_q
 // with FP32 accumulation in tensor memory.  The pairs with p + q <= 4
-// ((1,1),(1,2),(2,1),(1,3),(2,2),(3,1)) give FP32-level accuracy.
+// ((1,1),(1,2),(2,1),(1,3),(2,2),(3,1)) keep FP32-level operands.  The tensor
+// cores' FP32 accumulation loses accuracy with the number of accumulation
+// steps, so the K range is cut into up to 512/BN contiguous pieces, each
+// accumulated in its own tensor-memory columns, and the epilogue adds the
+// pieces in FP64.
 //
 // Operands are K-major BF16 digit planes: A as [plane][M rows][lda], B as
 // [plane][N rows][ldb], K contiguous (ld a multiple of 8 elements).  One CTA
@@ -195,7 +199,8 @@ __global__ void __launch_bounds__(192, 1)
         abort_flag = 0;
         mbar_fence_init();
     }
-    if (warp == 1) tmem_alloc(&tmem_base, BN);
+    const int kacc = args.kacc;   // accumulators in tensor memory, each owning a contiguous K range
+    if (warp == 1) tmem_alloc(&tmem_base, (uint32_t)(BN * kacc));
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -226,6 +231,10 @@ __global__ void __launch_bounds__(192, 1)
             if (!mbar_wait(&full_bar[s], ph, deadline, &abort_flag, args.err)) { ok = false; break; }
             tc_fence_after();
             const uint32_t st = smem_u32(smem + s * stage_bytes);
+            // k-block kb feeds accumulator (kb * kacc) / nkb; its first k-block overwrites
+            const int acc = (kb * kacc) / nkb;
+            const bool first_kb = kb == 0 || ((kb - 1) * kacc) / nkb != acc;
+            const uint32_t tacc = tmem + (uint32_t)(acc * BN);
             for (int pr = 0; pr < args.npairs; ++pr) {
                 const uint32_t sa = st + args.pa[pr] * TILE_A_BYTES;
                 const uint32_t sb = st + nA * TILE_A_BYTES + args.pb[pr] * tileB;
@@ -233,8 +242,8 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
                     // advance 16 elements (32 bytes) along K inside the swizzle row
-                    umma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                              (kb | pr | kk) != 0 ? 1u : 0u);
+                    umma_bf16(tacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                              (!first_kb || pr != 0 || kk != 0) ? 1u : 0u);
                 }
             }
             umma_commit(&empty_bar[s]);
@@ -250,20 +259,25 @@ __global__ void __launch_bounds__(192, 1)
         double *C = args.C + (int64_t)z * args.c_step;
         const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
         __nv_bfloat16 *Dd = args.Dout ? args.Dout + (int64_t)z * args.dout_step : nullptr;
+        const int nacc = nkb < kacc ? nkb : kacc;
         for (int c0 = 0; c0 < BN; c0 += 16) {
-            float v[16];
-            if (have_acc) {
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-            } else {
+            double v[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            for (int i = 0; i < 16; ++i) v[i] = 0.0;
+            if (have_acc) {
+                for (int ac = 0; ac < nacc; ++ac) {
+                    float f[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * BN + c0), f);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += (double)f[i];
+                }
             }
             if (row < args.M) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int col = n0 + c0 + i;
                     if (col >= args.N) break;
-                    double out = args.alpha * (double)v[i];
+                    double out = args.alpha * v[i];
                     if (Cin != nullptr) out = fma(args.beta, Cin[row + (int64_t)col * args.ldcin], out);
                     C[row + (int64_t)col * args.ldc] = out;
                     if (Dd != nullptr) {
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem, BN);
+        tmem_dealloc(tmem, (uint32_t)(BN * kacc));
     }
 }
 
@@ -360,8 +374,13 @@ int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_bytes = smem;
     }
+    TcArgs b = a;
+    const int nkb = (a.K + BK - 1) / BK;
+    int kacc = 512 / BN;
+    while (kacc > 1 && kacc > nkb) kacc >>= 1;
+    b.kacc = kacc;
     dim3 grid((unsigned)ceil_div(a.M, BM), (unsigned)ceil_div(a.N, BN), (unsigned)nbatch);
-    tc_gemm_kernel<BN, STAGES><<<grid, 192, smem, st>>>(ma, mb, a);
+    tc_gemm_kernel<BN, STAGES><<<grid, 192, smem, st>>>(ma, mb, b);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

@@ -30,6 +30,7 @@ struct TcArgs {
     int ndig;
     const DevState *state;       // nullable: return at once when state->done
     int *err;                    // nullable: set to 1 when a bounded wait times out
+    int kacc;                    // set by the launcher: K-range accumulators in tensor memory
 };
 
 int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
