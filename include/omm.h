@@ -233,6 +233,27 @@ int omm_op_quartic_coeffs(int64_t n, const double *h0, const double *s0, int64_t
                           int64_t scratch_bytes, void *stream);
 
 /*
+ * omm_op_quartic_coeffs without caller-provided scratch, for callers that
+ * cannot allocate device memory (the paper has no counterpart: libOMM runs on
+ * CPUs).  Same inputs, output and reduction order as omm_op_quartic_coeffs;
+ * the scratch is a static device array of omm_op_quartic_coeffs_static_max_bytes()
+ * bytes (53,504) held by every GPU that loads the library until the process
+ * exits.  The kernel never launches more blocks than that array has partial
+ * slots for; a size whose launch would need more is rejected with
+ * OMM_ERR_ARG and a message in omm_last_error(), as is n outside
+ * [0, 2^31 - 1].  The first call on each device looks up the array's device
+ * address and zeroes its completion counter (synchronous CUDA calls), so make
+ * that first call before any stream capture.  All calls share the one array
+ * and the kernel leaves the counter at zero for the next call: calls that may
+ * overlap on the GPU (different streams, other host threads) race and must be
+ * serialised by the caller.  Allocates nothing.
+ */
+int64_t omm_op_quartic_coeffs_static_max_bytes(void);
+int omm_op_quartic_coeffs_static(int64_t n, const double *h0, const double *s0, int64_t ld_h,
+                                 const double *X, const double *Y, const double *h2,
+                                 const double *s2, int64_t ld_z, double *coeffs, void *stream);
+
+/*
  * Minimiser x of c0 + c1 x + ... + c4 x^4 (device coeffs, 5 doubles) into
  * *x_out (device double) and a status (device int32: OMM_OK, OMM_ERR_LINESEARCH
  * when the quartic has no minimum, OMM_ERR_NONFINITE).  Candidates are the

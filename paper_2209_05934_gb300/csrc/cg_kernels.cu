@@ -7,6 +7,8 @@
 // depend on what else runs).
 #include <math.h>
 
+#include <mutex>
+
 #include "omm_internal.cuh"
 
 namespace omm {
@@ -633,6 +635,77 @@ extern "C" int omm_op_line_min(const double *coeffs, double *x_out, int32_t *sta
                                void *stream) {
     if (coeffs == nullptr || x_out == nullptr || status_out == nullptr) return OMM_ERR_ARG;
     omm::line_min_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(coeffs, x_out, status_out);
+    omm::count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+// Some callers cannot allocate device memory at the point where they need the
+// line-search coefficients: code running under a memory budget that forbids
+// cudaMalloc on the hot path, or a caller that only owns the six input arrays
+// and the 5-double output.  For them the reduction's scratch (per-block
+// partial sums and the completion counter) lives in this file-scope array,
+// which every GPU that loads the library holds until the process exits.
+namespace {
+constexpr int64_t kCoeffPartialsBytes = (int64_t)omm::kRedBlocksMax * 13 * (int64_t)sizeof(double);
+constexpr int64_t kCoeffStaticBytes = kCoeffPartialsBytes + 256;   // + the counter, own 256-byte slot
+static __device__ __align__(256) unsigned char g_coeff_scratch[kCoeffStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_coeff_mu;
+void *g_coeff_ptr[kMaxDevices] = {};   // device address of g_coeff_scratch, per device
+
+// Once per device, with that device current: look up the array's device
+// address (its host-side name is only a stand-in) and zero the counter.
+int coeff_scratch_for_current_device(void **out) {
+    int dev = -1;
+    OMM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        omm::set_error("omm_op_quartic_coeffs_static: device ordinal %d outside 0..%d", dev, kMaxDevices - 1);
+        return OMM_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_coeff_mu);
+    if (g_coeff_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        OMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_coeff_scratch));
+        OMM_CUDA_TRY(cudaMemset((char *)p + kCoeffPartialsBytes, 0, 256));
+        g_coeff_ptr[dev] = p;
+    }
+    *out = g_coeff_ptr[dev];
+    return OMM_OK;
+}
+}  // namespace
+
+extern "C" int64_t omm_op_quartic_coeffs_static_max_bytes(void) { return kCoeffStaticBytes; }
+
+extern "C" int omm_op_quartic_coeffs_static(int64_t n, const double *h0, const double *s0, int64_t ld_h,
+                                            const double *X, const double *Y, const double *h2,
+                                            const double *s2, int64_t ld_z, double *coeffs, void *stream) {
+    if (n < 0 || n > 2147483647) {
+        omm::set_error("omm_op_quartic_coeffs_static: n = %lld outside 0..2147483647", (long long)n);
+        return OMM_ERR_ARG;
+    }
+    // scratch this launch needs: partials of every block it launches + the counter
+    const int64_t blocks = omm::red_blocks_for_tiles((int)n);
+    const int64_t need = blocks * 13 * (int64_t)sizeof(double);
+    if (need > kCoeffPartialsBytes) {
+        omm::set_error("omm_op_quartic_coeffs_static: n = %lld needs %lld bytes of scratch, the static "
+                       "array holds %lld", (long long)n, (long long)need, (long long)kCoeffPartialsBytes);
+        return OMM_ERR_ARG;
+    }
+    if (coeffs == nullptr) return OMM_ERR_ARG;
+    if (n > 0 && (h0 == nullptr || s0 == nullptr || X == nullptr || Y == nullptr || h2 == nullptr ||
+                  s2 == nullptr || ld_h < n || ld_z < n))
+        return OMM_ERR_ARG;
+    void *scratch = nullptr;
+    const int rc = coeff_scratch_for_current_device(&scratch);
+    if (rc != OMM_OK) return rc;
+    double *partials = (double *)scratch;
+    unsigned int *counter = (unsigned int *)((char *)scratch + kCoeffPartialsBytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    omm::coeffs_kernel<<<(unsigned)blocks, omm::NT, 0, st>>>((int)n, h0, s0, ld_h, X, Y, h2, s2, ld_z,
+                                                             partials, counter, nullptr, coeffs, 0);
     omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

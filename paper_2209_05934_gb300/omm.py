@@ -67,6 +67,10 @@ _SIGS = {
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_int64, C.c_void_p]),
     "omm_op_line_min": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "omm_op_quartic_coeffs_static_max_bytes": (C.c_int64, []),
+    "omm_op_quartic_coeffs_static": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                               C.c_void_p]),
     "omm_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "omm_get_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "omm_kernel_launches": (C.c_int64, []),
@@ -264,6 +268,13 @@ def op_quartic_coeffs(n, h0, s0, ld_h, X, Y, h2, s2, ld_z, coeffs, scratch, scra
                                        _ptr(h2)[0], _ptr(s2)[0], ld_z, _ptr(coeffs)[0],
                                        _ptr(scratch)[0], scratch_bytes,
                                        C.c_void_p(stream) if stream else None)
+
+
+def op_quartic_coeffs_static(n, h0, s0, ld_h, X, Y, h2, s2, ld_z, coeffs, stream=0):
+    """Allocation-free variant: the library's static device scratch instead of a caller buffer."""
+    return lib().omm_op_quartic_coeffs_static(n, _ptr(h0)[0], _ptr(s0)[0], ld_h, _ptr(X)[0], _ptr(Y)[0],
+                                              _ptr(h2)[0], _ptr(s2)[0], ld_z, _ptr(coeffs)[0],
+                                              C.c_void_p(stream) if stream else None)
 
 
 def op_line_min(coeffs, x_out, status_out, stream=0):
