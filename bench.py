@@ -328,7 +328,7 @@ def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
         ach = f / (avg_ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": STAGES[dom], "achieved": ach, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "FP64 DFMA throughput measured by the probe in profiles/fp64_peak.md"}
+                "peak_source": "FP64 DFMA throughput measured on this GB300 by an FMA-chain probe"}
     f = flops.get(dom)
     if f is None:
         return None

@@ -2,7 +2,7 @@
  * omm.h -- C ABI of the GB300 orbital-minimization (OMM) library.
  *
  * The library minimises the Ordejon-Mauri energy functional
- *     E~(W) = 2 Tr[(2 I - W^T S W) W^T H W]                  (Eq. 5)
+ *     E~(W) = 2 Tr[(2 I - W^T S W) W^T H W]                  (Eq. 4)
  * over the m x n coefficient matrix W (the paper's C) by conjugate gradients
  * with an exact quartic line search (Introduction; section "Solver library").
  * H is the m x m Hamiltonian, S the m x m overlap matrix (both symmetric, S
@@ -97,7 +97,7 @@ typedef struct {
 
 typedef struct {
     double E;              /* energy of the final iterate: E~_eta + 2 eta n, where E~_eta
-                              is Eq. 5 with H' (equals E~ with H at the dense minimum) */
+                              is Eq. 4 with H' (equals E~ with H at the dense minimum) */
     double E_rel_change;   /* last |2 (E_k - E_{k-1}) / (E_k + E_{k-1})| (Table 1, RelTol) */
     double orth;           /* ||W^T S W - I||_F at the final iterate */
     double charge;         /* 2 Tr[(2 I - S_W) S_W] (Listing 1) */

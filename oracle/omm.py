@@ -91,7 +91,7 @@ def gershgorin_eta(H, S) -> float:
 # the functional, its gradient, the charge and the density matrix
 # ----------------------------------------------------------------------------
 def functional(W, H, S) -> float:
-    """E~ = 2 Tr[(2 I - W^T S W) W^T H W]  (Eq. 5, the Ordejon-Mauri functional,
+    """E~ = 2 Tr[(2 I - W^T S W) W^T H W]  (Eq. 4, the Ordejon-Mauri functional,
     spin factor 2 included)."""
     HW_ = W.T @ (H @ W)
     SW_ = W.T @ (S @ W)
@@ -132,7 +132,7 @@ def charge(W, S) -> float:
 
 
 def density_matrix(W, S):
-    """rho = 2 W (2 I - S_W) W^T  (Eq. 6)."""
+    """rho = 2 W (2 I - S_W) W^T  (Eq. 5)."""
     S_W = _dense(W.T @ (S @ W))
     n = S_W.shape[0]
     Wd = _dense(W)
@@ -140,7 +140,7 @@ def density_matrix(W, S):
 
 
 def energy_density_matrix(W, H, S, eta: float = 0.0):
-    """rho_E = 2 W H_W W^T, plus eta*rho for the Kim functional (Eq. 7 and the
+    """rho_E = 2 W H_W W^T, plus eta*rho for the Kim functional (defined with Eq. 6 and the
     Kim construction, step (3)); H is the unshifted Hamiltonian."""
     Wd = _dense(W)
     H_W = Wd.T @ (_dense(H) @ Wd)
