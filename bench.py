@@ -290,6 +290,7 @@ def run_omm(args):
         "dtype": "f64" if prec == "fp64" else "bf16-split+f64",
         "data": "synthetic",
         "config": {"workload": workload_name(sysm), "precision": prec, "tol": tol,
+                   "refine": "exact-digit tensor cores" if prec == "mixed" else None,
                    "orth_tol": TOL[prec]["orth_tol"], "parallelism": f"replicas x{ws}",
                    "l2": "working set (H, S = 256 MiB, plus W/D/products) exceeds the 129 MB L2"},
         "time_to_converge_ms": {"p50": lat_ms[len(lat_ms) // 2],
@@ -345,7 +346,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="omm", choices=["omm", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -93,7 +93,15 @@ typedef struct {
                               pattern; block products with ||A_ik|| ||B_kj|| < eps are
                               skipped (screening never changes a stored pattern) */
     void *stream;          /* cudaStream_t for all work of the handle, NULL = own stream */
+    int32_t refine;        /* arithmetic of the mixed form's refinement sweep (re-anchoring
+                              and gradient): OMM_REFINE_EXACT (default) or OMM_REFINE_FP64 */
+    int32_t exact_digits;  /* digits per operand of the exact-digit products, 1..8, default 7 */
 } omm_options;
+
+enum {
+    OMM_REFINE_EXACT = 0,  /* exact-digit BF16 tensor-core products (omm_op_exact_gemm) */
+    OMM_REFINE_FP64 = 1    /* FP64 CUDA-core products (omm_op_dgemm) */
+};
 
 typedef struct {
     double E;              /* energy of the final iterate: E~_eta + 2 eta n, where E~_eta
@@ -275,6 +283,26 @@ int omm_op_line_min(const double *coeffs, double *x_out, int32_t *status_out, vo
  */
 int64_t omm_op_split_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int32_t ndigits);
 int omm_op_split_gemm(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K,
+                      int32_t ndigits, double alpha, const double *A, int64_t lda,
+                      const double *B, int64_t ldb, double beta, const double *Cin,
+                      int64_t ldcin, double *C, int64_t ldc, void *workspace,
+                      int64_t workspace_bytes, void *stream);
+
+/*
+ * Exact-digit tensor-core GEMM  C = alpha op(A) op(B) + beta Cin  (FP64 in and
+ * out, column-major, op as in omm_op_dgemm), accurate to about 2^-(7 ndigits - 6)
+ * of (max_k |op(A)_ik|)(max_k |op(B)_kj|) sqrt(K).  Each row of op(A) and column of
+ * op(B) is scaled by a power of two into (-1, 1) and cut into ndigits
+ * fixed-point digits of at most 64 in magnitude (error-free splitting after
+ * Ozaki, Ogita, Oishi & Rump 2012); every digit-pair product is accumulated
+ * exactly in FP32 on the tcgen05 tensor cores over K chunks of <= 4096, summed
+ * exactly in integers per weight level and combined in FP64.  It gives the
+ * mixed-precision form its accurate re-anchoring and refinement gradient.
+ * ndigits 1..8 (7 in the solver: 28 digit pairs).  workspace: device memory of
+ * at least omm_op_exact_gemm_workspace_bytes(M, N, K, ndigits) bytes.
+ */
+int64_t omm_op_exact_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int32_t ndigits);
+int omm_op_exact_gemm(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K,
                       int32_t ndigits, double alpha, const double *A, int64_t lda,
                       const double *B, int64_t ldb, double beta, const double *Cin,
                       int64_t ldcin, double *C, int64_t ldc, void *workspace,

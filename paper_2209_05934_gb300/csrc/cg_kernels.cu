@@ -43,10 +43,13 @@ __device__ void block_sum(double (&v)[NV], double *red /* smem NV*8 */) {
 }
 
 // Publish this block's NV partials; returns true in the last block to finish,
-// whose thread 0 then holds the block-ordered totals in `tot`.
+// whose thread 0 then holds the totals in `tot`.  The last block reads the
+// partials with all its threads (thread t takes blocks t, t + NT, ... in order)
+// and combines them with the same fixed tree as block_sum, so the result does
+// not depend on which block finished last.
 template <int NV>
 __device__ bool publish_and_collect(const double (&v)[NV], double *partials, unsigned int *counter,
-                                    double (&tot)[NV]) {
+                                    double (&tot)[NV], double *red) {
     __shared__ bool is_last;
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -57,14 +60,17 @@ __device__ bool publish_and_collect(const double (&v)[NV], double *partials, uns
     }
     __syncthreads();
     if (!is_last) return false;
+    __threadfence();
+    double w[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) w[q] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += NT)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) w[q] += __ldcg(&partials[b * NV + q]);
+    block_sum<NV>(w, red);
     if (threadIdx.x == 0) {
-        __threadfence();
-        volatile const double *p = partials;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) tot[q] = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) tot[q] += p[b * NV + q];
+        for (int q = 0; q < NV; ++q) tot[q] = w[q];
         *counter = 0u;
     }
     return true;
@@ -223,7 +229,7 @@ __global__ void __launch_bounds__(NT) coeffs_kernel(int n, const double *__restr
     }
     block_sum<NC>(v, red);
     double tot[NC];
-    if (!publish_and_collect<NC>(v, partials, counter, tot)) return;
+    if (!publish_and_collect<NC>(v, partials, counter, tot, red)) return;
     if (threadIdx.x != 0) return;
     double c[5];
     c[0] = 2.0 * (2.0 * tot[0] - tot[1]);
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(NT) nn_update_kernel(int n, double *h0, double
     }
     block_sum<NE>(v, red);
     double tot[NE];
-    if (!publish_and_collect<NE>(v, partials, counter, tot)) return;
+    if (!publish_and_collect<NE>(v, partials, counter, tot, red)) return;
     if (threadIdx.x != 0) return;
     const double E = 2.0 * (2.0 * tot[0] - tot[1]) + 2.0 * state->eta * (double)n;
     state->trh0 = tot[0];
@@ -379,7 +385,7 @@ __global__ void __launch_bounds__(NT) dots_kernel(int64_t mn, const double *__re
     }
     block_sum<ND>(v, red);
     double tot[ND];
-    if (!publish_and_collect<ND>(v, partials, counter, tot)) return;
+    if (!publish_and_collect<ND>(v, partials, counter, tot, red)) return;
     if (threadIdx.x != 0) return;
     const double gg = tot[0];
     double beta = 0.0;

@@ -18,6 +18,7 @@
 #include <new>
 
 #include "omm_internal.cuh"
+#include "tc_exact.cuh"
 #include "tc_gemm.cuh"
 
 // Mixed-precision buffers: BF16 digit planes (three digits, K-major) of the
@@ -31,6 +32,21 @@ struct MixedBufs {
     int64_t ldm = 0, ld2n = 0;
     __nv_bfloat16 *HSd = nullptr, *WDd = nullptr, *HDSDd = nullptr, *SWHWd = nullptr, *HSWd = nullptr;
     CUtensorMap mapHS_A, mapWD_A, mapWD_B, mapHDSD_B, mapSWHW_A, mapHSW_B;
+};
+
+// Exact-digit operands of the refinement sweep (s digits, row-scaled), each
+// with its per-row exponents:
+//   HSx   [s][2m][ldm]  columns of [H' | S]     A of the anchor H'W, SW
+//   Wx    [s][n][ldm]   columns of W            B of the anchor; A of H_W, S_W
+//   HWSWx [s][2n][ldm]  columns of [H'W | SW]   B of H_W, S_W
+//   SWHWx [s][m][ld2n]  rows of [SW | H'W]      A of the gradient
+//   HSWx  [s][n][ld2n]  columns of [H_W ; S_W]  B of the gradient
+struct ExactBufs {
+    int s = 0;
+    __nv_bfloat16 *HSx = nullptr, *Wx = nullptr, *HWSWx = nullptr, *SWHWx = nullptr, *HSWx = nullptr;
+    int *e = nullptr;   // exponents: [2m HS | n W | 2n HWSW | m SWHW | n HSW]
+    int *eHS = nullptr, *eW = nullptr, *eHWSW = nullptr, *eSWHW = nullptr, *eHSW = nullptr;
+    CUtensorMap mapHS_A, mapW, mapHWSW_B, mapSWHW_A, mapHSW_B;
 };
 
 struct omm_handle {
@@ -51,6 +67,7 @@ struct omm_handle {
     omm_diag diag{};
     int chunk = 8;
     MixedBufs mx;
+    ExactBufs ex;
     // optional per-stage device timing (omm_set_profiling)
     bool profiling = false;
     static constexpr int kMaxEv = 2048;
@@ -94,6 +111,12 @@ void free_handle(omm_handle *h) {
     cudaFree(h->mx.HDSDd);
     cudaFree(h->mx.SWHWd);
     cudaFree(h->mx.HSWd);
+    cudaFree(h->ex.HSx);
+    cudaFree(h->ex.Wx);
+    cudaFree(h->ex.HWSWx);
+    cudaFree(h->ex.SWHWx);
+    cudaFree(h->ex.HSWx);
+    cudaFree(h->ex.e);
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -311,6 +334,113 @@ int fp64_gradient(omm_handle *h) {
     return omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, h->dstate, h->stream);
 }
 
+int exact_alloc(omm_handle *h) {
+    const int64_t m = h->m, n = h->n;
+    const MixedBufs &x = h->mx;
+    ExactBufs &e = h->ex;
+    e.s = h->opt.exact_digits;
+    const int s = e.s;
+    TRY(dalloc(&e.HSx, (size_t)(s * 2 * m * x.ldm)));
+    TRY(dalloc(&e.Wx, (size_t)(s * n * x.ldm)));
+    TRY(dalloc(&e.HWSWx, (size_t)(s * 2 * n * x.ldm)));
+    TRY(dalloc(&e.SWHWx, (size_t)(s * m * x.ld2n)));
+    TRY(dalloc(&e.HSWx, (size_t)(s * n * x.ld2n)));
+    TRY(dalloc(&e.e, (size_t)(2 * m + n + 2 * n + m + n)));
+    e.eHS = e.e;
+    e.eW = e.eHS + 2 * m;
+    e.eHWSW = e.eW + n;
+    e.eSWHW = e.eHWSW + 2 * n;
+    e.eHSW = e.eSWHW + m;
+    TRY(omm::tc::make_digit_map(&e.mapHS_A, e.HSx, m, 2 * m, x.ldm, 2 * m * x.ldm, s, 128));
+    TRY(omm::tc::make_digit_map(&e.mapW, e.Wx, m, n, x.ldm, n * x.ldm, s, 128));
+    TRY(omm::tc::make_digit_map(&e.mapHWSW_B, e.HWSWx, m, 2 * n, x.ldm, 2 * n * x.ldm, s, 128));
+    TRY(omm::tc::make_digit_map(&e.mapSWHW_A, e.SWHWx, 2 * n, m, x.ld2n, m * x.ld2n, s, 128));
+    TRY(omm::tc::make_digit_map(&e.mapHSW_B, e.HSWx, 2 * n, n, x.ld2n, n * x.ld2n, s, 128));
+    return OMM_OK;
+}
+
+omm::tc::ExactArgs exact_args(omm_handle *h, int M, int N, int K) {
+    omm::tc::ExactArgs a{};
+    omm::tc::exact_pairs(h->ex.s, a);
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.alpha = 1.0;
+    a.beta = 0.0;
+    a.state = h->dstate;
+    a.err = &h->dstate->wait_timeout;
+    return a;
+}
+
+// G = 4 H'W - 2 [SW H'W][H_W ; S_W] with exact-digit products
+int exact_gradient(omm_handle *h) {
+    const int64_t m = h->m, n = h->n;
+    const MixedBufs &x = h->mx;
+    ExactBufs &e = h->ex;
+    cudaStream_t st = h->stream;
+    {
+        StageTimer t(h, OMM_STAGE_PACK);
+        TRY(omm::tc::exact_pack(false, m, 2 * n, h->SWHW, m, e.eSWHW, e.SWHWx, x.ld2n, m * x.ld2n, e.s, h->dstate, st));
+        TRY(omm::tc::exact_pack(true, 2 * n, n, h->h0s0, 2 * n, e.eHSW, e.HSWx, x.ld2n, n * x.ld2n, e.s, h->dstate, st));
+    }
+    StageTimer t(h, OMM_STAGE_GRADIENT);
+    omm::tc::ExactArgs a = exact_args(h, (int)m, (int)n, (int)(2 * n));
+    a.alpha = -2.0;
+    a.beta = 4.0;
+    a.Cin = h->SWHW + m * n;
+    a.ldcin = m;
+    a.C = h->G;
+    a.ldc = m;
+    a.eA = e.eSWHW;
+    a.eB = e.eHSW;
+    return omm::tc::exact_gemm(e.mapSWHW_A, e.mapHSW_B, a, 1, st);
+}
+
+// Refinement start with exact-digit products: H'W, SW, H_W, S_W, energy, G, D.
+int exact_anchor(omm_handle *h) {
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    const MixedBufs &x = h->mx;
+    ExactBufs &e = h->ex;
+    cudaStream_t st = h->stream;
+    omm::DevState *s = h->dstate;
+    {
+        StageTimer t(h, OMM_STAGE_ANCHOR);
+        TRY(omm::tc::exact_pack(true, m, n, h->WD, m, e.eW, e.Wx, x.ldm, n * x.ldm, e.s, s, st));
+        // z = 0: H'W -> SWHW + mn;  z = 1: SW -> SWHW
+        omm::tc::ExactArgs a = exact_args(h, (int)m, (int)n, (int)m);
+        a.a_row_step = (int)m;
+        a.C = h->SWHW + mn;
+        a.ldc = m;
+        a.c_step = -mn;
+        a.eA = e.eHS;
+        a.eA_step = m;
+        a.eB = e.eW;
+        TRY(omm::tc::exact_gemm(e.mapHS_A, e.mapW, a, 2, st));
+        TRY(omm::tc::exact_pack(true, m, n, h->SWHW + mn, m, e.eHWSW, e.HWSWx, x.ldm, 2 * n * x.ldm, e.s, s, st));
+        TRY(omm::tc::exact_pack(true, m, n, h->SWHW, m, e.eHWSW + n, e.HWSWx + n * x.ldm, x.ldm, 2 * n * x.ldm, e.s,
+                                s, st));
+        // z = 0: H_W = W^T H'W -> rows [0, n) of h0s0;  z = 1: S_W -> rows [n, 2n)
+        omm::tc::ExactArgs b = exact_args(h, (int)n, (int)n, (int)m);
+        b.b_row_step = (int)n;
+        b.C = h->h0s0;
+        b.ldc = 2 * n;
+        b.c_step = n;
+        b.eA = e.eW;
+        b.eB = e.eHWSW;
+        b.eB_step = n;
+        TRY(omm::tc::exact_gemm(e.mapW, e.mapHWSW_B, b, 2, st));
+    }
+    TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
+                                     ctr(h, 1), s, 1, st));
+    TRY(exact_gradient(h));
+    {
+        StageTimer t(h, OMM_STAGE_DIRECTION);
+        TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 1, st));
+        TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st));
+    }
+    return OMM_OK;
+}
+
 // Start of the split-precision phase: H'W, SW, H_W, S_W, energy, G, D from W.
 int mixed_start(omm_handle *h) {
     const int64_t m = h->m, n = h->n, mn = m * n;
@@ -358,7 +488,12 @@ int mixed_iteration(omm_handle *h, bool accurate_gradient) {
                                        ctr(h, 1), s, 0, st)); }
     if (accurate_gradient) {
         { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
-        { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(fp64_gradient(h)); }
+        if (h->opt.refine == OMM_REFINE_EXACT) {
+            TRY(exact_gradient(h));
+        } else {
+            StageTimer t(h, OMM_STAGE_GRADIENT);
+            TRY(fp64_gradient(h));
+        }
     } else {
         { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); TRY(pack_SWHW(h)); TRY(pack_HSW(h)); }
         { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(split_gradient(h)); }
@@ -403,6 +538,8 @@ void omm_default_options(omm_options *opt) {
     opt->orth_tol = 0.0;
     opt->filter_eps = 1e-8;
     opt->stream = nullptr;
+    opt->refine = OMM_REFINE_EXACT;
+    opt->exact_digits = 7;
 }
 
 const char *omm_status_str(int status) {
@@ -437,7 +574,8 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
     h->n = n;
     h->bm = block_size;
     if (opt) h->opt = *opt; else omm_default_options(&h->opt);
-    if (h->opt.max_iter < 0) {
+    if (h->opt.max_iter < 0 || (h->opt.refine != OMM_REFINE_EXACT && h->opt.refine != OMM_REFINE_FP64) ||
+        h->opt.exact_digits < 1 || h->opt.exact_digits > omm::tc::kExactMaxDigits) {
         delete h;
         return OMM_ERR_ARG;
     }
@@ -467,6 +605,10 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         return rc;
     }
     if (h->opt.precision == OMM_PREC_MIXED && (rc = mixed_alloc(h))) {
+        free_handle(h);
+        return rc;
+    }
+    if (h->opt.precision == OMM_PREC_MIXED && h->opt.refine == OMM_REFINE_EXACT && (rc = exact_alloc(h))) {
         free_handle(h);
         return rc;
     }
@@ -509,6 +651,9 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
         // columns of [H' | S] become the K-major rows of the A operand (symmetric)
         StageTimer t(h, OMM_STAGE_PACK);
         TRY(omm::tc::pack_cm(m, 2 * m, h->HS, m, h->mx.HSd, h->mx.ldm, 2 * m * h->mx.ldm, kDig, nullptr, st));
+        if (h->opt.refine == OMM_REFINE_EXACT)
+            TRY(omm::tc::exact_pack(true, m, 2 * m, h->HS, m, h->ex.eHS, h->ex.HSx, h->mx.ldm, 2 * m * h->mx.ldm,
+                                    h->ex.s, nullptr, st));
     }
     OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
@@ -561,7 +706,12 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
             rf.k = k_mixed;
             *h->hstate = rf;
             OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
-            { StageTimer t(h, OMM_STAGE_ANCHOR); TRY(dense_start(h)); }
+            if (h->opt.refine == OMM_REFINE_EXACT) {
+                TRY(exact_anchor(h));
+            } else {
+                StageTimer t(h, OMM_STAGE_ANCHOR);
+                TRY(dense_start(h));
+            }
             { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); TRY(pack_D(h)); }
             TRY(run_until_done(h, [&] { return mixed_iteration(h, true); }));
         }

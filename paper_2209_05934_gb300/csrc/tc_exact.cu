@@ -1,0 +1,419 @@
+// Exact-digit BF16 tensor-core GEMM: near-FP64 products on tcgen05 (sm_103a).
+//
+// Error-free splitting in the manner of Ozaki, Ogita, Oishi & Rump (2012),
+// applied to BF16 tensor cores as in Mukunoki et al. (2020): every K-major
+// row r of an operand is scaled by 2^-e_r so its entries lie in (-1, 1), then
+// cut into fixed-point digits
+//     d_1 = rint(a * 64),  a_1 = a * 64 - d_1,
+//     d_t = rint(a_{t-1} * 128),  a_t = a_{t-1} * 128 - d_t,
+// so a = sum_t d_t 2^-(7t-1) + O(2^-(7s)), each |d_t| <= 64 (exact in BF16).
+// A product of two digits is at most 2^12 in magnitude, so a sum of up to
+// 4096 of them is an integer below 2^24: the tensor cores accumulate every
+// digit pair (t, u) over a K chunk of <= 4096 exactly in FP32.  Pairs with
+// t + u <= s + 1 are kept; pairs of one level L = t + u share the weight
+// 2^-(7L-2).
+//
+// One CTA computes a 128 x 128 tile.  Warp 0 streams (A_t, B_u) digit tiles of
+// each pair through a 6-stage TMA ring; warp 1 accumulates each (pair, chunk)
+// unit in one of two tensor-memory buffers; warps 2..5 read a finished unit,
+// convert its exact integers to int32 and add them to the level's integer
+// sum (registers), and at the end of each level fold that sum into an FP64
+// running sum kept in tensor memory.  The final epilogue scales by
+// 2^(e_i + f_j) and writes C = alpha * A B + beta * Cin in FP64.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "omm_internal.cuh"
+#include "tc_exact.cuh"
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+namespace omm {
+namespace tc {
+namespace {
+
+using namespace ptx;
+
+constexpr int XBN = 128;
+constexpr int XSTAGES = 6;
+constexpr int XTILE_B_BYTES = XBN * BK * 2;
+constexpr int XSTAGE_BYTES = TILE_A_BYTES + XTILE_B_BYTES;
+constexpr int kChunkMax = 4096;     // 4096 * 64 * 64 = 2^24: exact FP32 integer sums
+constexpr int kRunCol = 2 * XBN;    // tensor-memory column of the FP64 running sum
+
+__global__ void __launch_bounds__(192, 1)
+    tc_exact_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                    const ExactArgs args) {
+    if (args.state != nullptr && *((volatile const int *)&args.state->done)) return;
+    const int z = blockIdx.z;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[XSTAGES];
+    __shared__ __align__(8) uint64_t empty_bar[XSTAGES];
+    __shared__ __align__(8) uint64_t tfull_bar[2];
+    __shared__ __align__(8) uint64_t tempty_bar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const uint64_t deadline = globaltimer_ns() + kWaitNs;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM;
+    const int n0 = blockIdx.y * XBN;
+    const int nkb_total = (args.K + BK - 1) / BK;
+    const int kb_per_chunk = kChunkMax / BK;
+    const int nchunks = (nkb_total + kb_per_chunk - 1) / kb_per_chunk;
+    const int nunits = args.npairs * nchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < XSTAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull_bar[b], 1);
+            mbar_init(&tempty_bar[b], 128);
+        }
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer: every unit's k-blocks, in unit order
+        const int a_row = args.a_row0 + z * args.a_row_step + m0;
+        const int b_row = args.b_row0 + z * args.b_row_step + n0;
+        int it = 0;
+        for (int u = 0; u < nunits && !abort_flag; ++u) {
+            const int p = u / nchunks, c = u % nchunks;
+            const int kb0 = c * kb_per_chunk;
+            const int kb1 = min(nkb_total, kb0 + kb_per_chunk);
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const int s = it % XSTAGES;
+                const uint32_t ph = (uint32_t)((it / XSTAGES) & 1);
+                if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, args.err)) break;
+                mbar_arrive_expect_tx(&full_bar[s], (uint32_t)XSTAGE_BYTES);
+                uint8_t *st = smem + s * XSTAGE_BYTES;
+                tma_load_3d(st, &mapA, kb * BK, a_row, args.pa[p], &full_bar[s]);
+                tma_load_3d(st + TILE_A_BYTES, &mapB, kb * BK, b_row, args.pb[p], &full_bar[s]);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer: unit u accumulates into buffer u & 1
+        constexpr uint32_t idesc = idesc_bf16(BM, XBN);
+        int it = 0;
+        for (int u = 0; u < nunits; ++u) {
+            const int c = u % nchunks;
+            const int b = u & 1;
+            if (!mbar_wait(&tempty_bar[b], (uint32_t)(((u >> 1) & 1) ^ 1), deadline, &abort_flag, args.err)) break;
+            tc_fence_after();
+            const uint32_t tacc = tmem + (uint32_t)(b * XBN);
+            const int kb0 = c * kb_per_chunk;
+            const int kb1 = min(nkb_total, kb0 + kb_per_chunk);
+            bool ok = true;
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const int s = it % XSTAGES;
+                const uint32_t ph = (uint32_t)((it / XSTAGES) & 1);
+                if (!mbar_wait(&full_bar[s], ph, deadline, &abort_flag, args.err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + s * XSTAGE_BYTES);
+                const uint64_t da = sdesc_sw128(st), db = sdesc_sw128(st + TILE_A_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    umma_bf16(tacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                              (kb != kb0 || kk != 0) ? 1u : 0u);
+                umma_commit(&empty_bar[s]);
+            }
+            umma_commit(&tfull_bar[b]);
+            if (!ok) break;
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue
+        const int q = warp & 3;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+        const int row = m0 + 32 * q + lane;
+        int32_t acc[XBN];
+#pragma unroll
+        for (int j = 0; j < XBN; ++j) acc[j] = 0;
+        bool have_run = false;
+        bool alive = true;
+        for (int u = 0; u < nunits; ++u) {
+            const int p = u / nchunks, c = u % nchunks;
+            const int b = u & 1;
+            bool got = alive && mbar_wait(&tfull_bar[b], (uint32_t)((u >> 1) & 1), deadline, &abort_flag, args.err);
+            got = __all_sync(0xffffffffu, got);
+            alive = got;
+            tc_fence_after();
+            if (got) {
+#pragma unroll
+                for (int c0 = 0; c0 < XBN; c0 += 16) {
+                    float f[16];
+                    tmem_ld16(lane_base + (uint32_t)(b * XBN + c0), f);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[c0 + j] += __float2int_rn(f[j]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty_bar[b]);
+            const int level = args.pa[p] + args.pb[p] + 2;
+            const bool last_of_level =
+                c == nchunks - 1 && (p == args.npairs - 1 || args.pa[p + 1] + args.pb[p + 1] + 2 != level);
+            if (last_of_level && got) {
+                // fold the level into the FP64 running sum (tensor memory, two words per value)
+                const double w = ldexp(1.0, -(7 * level - 2));
+#pragma unroll
+                for (int c0 = 0; c0 < XBN; c0 += 8) {
+                    uint32_t r[16];
+                    if (have_run) {
+                        float f[16];
+                        tmem_ld16(lane_base + (uint32_t)(kRunCol + 2 * c0), f);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(f[j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        double v = have_run ? __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]) : 0.0;
+                        v = fma((double)acc[c0 + j], w, v);
+                        r[2 * j] = (uint32_t)__double2loint(v);
+                        r[2 * j + 1] = (uint32_t)__double2hiint(v);
+                        acc[c0 + j] = 0;
+                    }
+                    tmem_st16(lane_base + (uint32_t)(kRunCol + 2 * c0), r);
+                }
+                have_run = true;
+            }
+        }
+        // final: C = alpha 2^(eA + eB) run + beta Cin
+        const bool ok = __all_sync(0xffffffffu, alive && have_run);
+        double *C = args.C + (int64_t)z * args.c_step;
+        const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
+        const int *eA = args.eA + (int64_t)z * args.eA_step;
+        const int *eB = args.eB + (int64_t)z * args.eB_step;
+        const int ea = row < args.M ? eA[row] : 0;
+#pragma unroll
+        for (int c0 = 0; c0 < XBN; c0 += 8) {
+            double v[8];
+            if (ok) {
+                float f[16];
+                tmem_ld16(lane_base + (uint32_t)(kRunCol + 2 * c0), f);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    v[j] = __hiloint2double((int)__float_as_uint(f[2 * j + 1]), (int)__float_as_uint(f[2 * j]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = 0.0;
+            }
+            if (row < args.M) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col >= args.N) break;
+                    double out = args.alpha * ldexp(v[j], ea + eB[col]);
+                    if (Cin != nullptr) out = fma(args.beta, Cin[row + (int64_t)col * args.ldcin], out);
+                    C[row + (int64_t)col * args.ldc] = out;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ------------------------------------------------------------------ digit packing
+__device__ __forceinline__ int row_exponent(double mx) {
+    // 2^e > mx >= 2^(e-1): the scaled row lies in (-1, 1)
+    return mx > 0.0 ? ilogb(mx) + 1 : 0;
+}
+
+__device__ __forceinline__ void put_digits(double a, int s, __nv_bfloat16 *dst, int64_t o, int64_t plane) {
+    double x = a * 64.0;
+    for (int t = 0; t < s; ++t) {
+        const double d = rint(x);
+        dst[t * plane + o] = __double2bfloat16(d);   // |d| <= 64: exact
+        x = (x - d) * 128.0;
+    }
+}
+
+// K along the source's rows: operand row r is source column r (warp per column).
+__global__ void exp_cm_kernel(int64_t K, int64_t R, const double *__restrict__ X, int64_t ld, int *e,
+                              const DevState *state) {
+    if (state != nullptr && *((volatile const int *)&state->done)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < R; r += nw) {
+        double mx = 0.0;
+        for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[k + r * ld]));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (lane == 0) e[r] = row_exponent(mx);
+    }
+}
+
+// K along the source's columns: operand row r is source row r (thread per row).
+__global__ void exp_t_kernel(int64_t R, int64_t K, const double *__restrict__ X, int64_t ld, int *e,
+                             const DevState *state) {
+    if (state != nullptr && *((volatile const int *)&state->done)) return;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        double mx = 0.0;
+        for (int64_t k = 0; k < K; ++k) mx = fmax(mx, fabs(X[r + k * ld]));
+        e[r] = row_exponent(mx);
+    }
+}
+
+__global__ void digits_cm_kernel(int64_t K, int64_t R, const double *__restrict__ X, int64_t ld,
+                                 const int *__restrict__ e, __nv_bfloat16 *dst, int64_t ldk, int64_t plane,
+                                 int s, const DevState *state) {
+    if (state != nullptr && *((volatile const int *)&state->done)) return;
+    const int64_t total = K * R;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t % K, r = t / K;
+        put_digits(ldexp(X[k + r * ld], -e[r]), s, dst, r * ldk + k, plane);
+    }
+}
+
+__global__ void digits_t_kernel(int64_t R, int64_t K, const double *__restrict__ X, int64_t ld,
+                                const int *__restrict__ e, __nv_bfloat16 *dst, int64_t ldk, int64_t plane, int s,
+                                const DevState *state) {
+    if (state != nullptr && *((volatile const int *)&state->done)) return;
+    __shared__ double tile[32][33];
+    const int64_t tr = (int64_t)blockIdx.x * 32, tk = (int64_t)blockIdx.y * 32;
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    for (int i = ly; i < 32; i += 8) {
+        const int64_t r = tr + lx, k = tk + i;
+        tile[i][lx] = (r < R && k < K) ? X[r + k * ld] : 0.0;
+    }
+    __syncthreads();
+    for (int i = ly; i < 32; i += 8) {
+        const int64_t r = tr + i, k = tk + lx;
+        if (r < R && k < K) put_digits(ldexp(tile[lx][i], -e[r]), s, dst, r * ldk + k, plane);
+    }
+}
+
+int grid_for(int64_t work, int per_block) {
+    int64_t nb = ceil_div(work, per_block);
+    if (nb > 152 * 16) nb = 152 * 16;
+    return (int)(nb < 1 ? 1 : nb);
+}
+
+}  // namespace
+
+void exact_pairs(int s, ExactArgs &a) {
+    int k = 0;
+    for (int lvl = 2; lvl <= s + 1; ++lvl)
+        for (int t = 1; t <= s; ++t) {
+            const int u = lvl - t;
+            if (u < 1 || u > s) continue;
+            a.pa[k] = (uint8_t)(t - 1);
+            a.pb[k] = (uint8_t)(u - 1);
+            ++k;
+        }
+    a.npairs = k;
+}
+
+int exact_pack(bool k_along_rows, int64_t rows, int64_t cols, const double *X, int64_t ld, int *e,
+               __nv_bfloat16 *dst, int64_t ldk, int64_t plane, int s, const DevState *state, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return OMM_OK;
+    if (s < 1 || s > kExactMaxDigits) return OMM_ERR_ARG;
+    if (k_along_rows) {   // K = rows, operand rows = cols
+        exp_cm_kernel<<<grid_for(cols * 32, 256), 256, 0, st>>>(rows, cols, X, ld, e, state);
+        count_launch();
+        OMM_CUDA_TRY(cudaGetLastError());
+        digits_cm_kernel<<<grid_for(rows * cols, 256 * 4), 256, 0, st>>>(rows, cols, X, ld, e, dst, ldk, plane, s,
+                                                                          state);
+        count_launch();
+        OMM_CUDA_TRY(cudaGetLastError());
+    } else {              // K = cols, operand rows = rows
+        exp_t_kernel<<<grid_for(rows, 256), 256, 0, st>>>(rows, cols, X, ld, e, state);
+        count_launch();
+        OMM_CUDA_TRY(cudaGetLastError());
+        dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32));
+        digits_t_kernel<<<grid, 256, 0, st>>>(rows, cols, X, ld, e, dst, ldk, plane, s, state);
+        count_launch();
+        OMM_CUDA_TRY(cudaGetLastError());
+    }
+    return OMM_OK;
+}
+
+int exact_gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const ExactArgs &a, int nbatch, cudaStream_t st) {
+    if (a.M <= 0 || a.N <= 0 || a.K <= 0 || a.npairs < 1 || a.npairs > kExactMaxPairs || nbatch < 1)
+        return OMM_ERR_ARG;
+    const int smem = XSTAGES * XSTAGE_BYTES + 1024;
+    static int attr_bytes = 0;
+    if (smem > attr_bytes) {
+        OMM_CUDA_TRY(cudaFuncSetAttribute(tc_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_bytes = smem;
+    }
+    dim3 grid((unsigned)ceil_div(a.M, BM), (unsigned)ceil_div(a.N, XBN), (unsigned)nbatch);
+    tc_exact_kernel<<<grid, 192, smem, st>>>(mapA, mapB, a);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+}  // namespace tc
+}  // namespace omm
+
+// ---------------------------------------------------------------- op-level entry
+extern "C" int64_t omm_op_exact_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int32_t ndigits) {
+    if (M < 0 || N < 0 || K < 0 || ndigits < 1 || ndigits > omm::tc::kExactMaxDigits) return -1;
+    const int64_t ldk = (K + 7) / 8 * 8;
+    return (int64_t)ndigits * (M + N) * ldk * 2 + (M + N) * 4 + 2048;
+}
+
+extern "C" int omm_op_exact_gemm(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K,
+                                 int32_t ndigits, double alpha, const double *A, int64_t lda,
+                                 const double *B, int64_t ldb, double beta, const double *Cin,
+                                 int64_t ldcin, double *C, int64_t ldc, void *workspace,
+                                 int64_t workspace_bytes, void *stream) {
+    using namespace omm;
+    if (M <= 0 || N <= 0 || K <= 0 || ndigits < 1 || ndigits > tc::kExactMaxDigits) return OMM_ERR_ARG;
+    if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return OMM_ERR_ARG;
+    if (A == nullptr || B == nullptr || C == nullptr || workspace == nullptr) return OMM_ERR_ARG;
+    if (lda < (transA ? K : M) || ldb < (transB ? N : K) || ldc < M) return OMM_ERR_ARG;
+    if (beta != 0.0 && (Cin == nullptr || ldcin < M)) return OMM_ERR_ARG;
+    if (workspace_bytes < omm_op_exact_gemm_workspace_bytes(M, N, K, ndigits)) return OMM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ldk = (K + 7) / 8 * 8;
+    uintptr_t base = ((uintptr_t)workspace + 255) & ~(uintptr_t)255;
+    __nv_bfloat16 *Ad = (__nv_bfloat16 *)base;
+    __nv_bfloat16 *Bd = Ad + (int64_t)ndigits * M * ldk;
+    int *eA = (int *)(Bd + (int64_t)ndigits * N * ldk);
+    int *eB = eA + M;
+    int rc;
+    // op(A) M x K: rows of op(A) are K-major operand rows
+    if ((rc = tc::exact_pack(transA != 0, transA ? K : M, transA ? M : K, A, lda, eA, Ad, ldk, M * ldk, ndigits,
+                             nullptr, st)))
+        return rc;
+    // op(B) K x N: columns of op(B) are K-major operand rows
+    if ((rc = tc::exact_pack(transB == 0, transB ? N : K, transB ? K : N, B, ldb, eB, Bd, ldk, N * ldk, ndigits,
+                             nullptr, st)))
+        return rc;
+    CUtensorMap ma, mb;
+    if ((rc = tc::make_digit_map(&ma, Ad, K, M, ldk, M * ldk, ndigits, 128))) return rc;
+    if ((rc = tc::make_digit_map(&mb, Bd, K, N, ldk, N * ldk, ndigits, 128))) return rc;
+    tc::ExactArgs a{};
+    tc::exact_pairs(ndigits, a);
+    a.M = (int)M;
+    a.N = (int)N;
+    a.K = (int)K;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.Cin = beta != 0.0 ? Cin : nullptr;
+    a.ldcin = ldcin;
+    a.C = C;
+    a.ldc = ldc;
+    a.eA = eA;
+    a.eB = eB;
+    return tc::exact_gemm(ma, mb, a, 1, st);
+}

@@ -19,6 +19,7 @@ OK = 0
 ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_NOT_SPD, ERR_LINESEARCH = -1, -2, -3, -4, -5
 ERR_MAXITER, ERR_PATTERN, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = -6, -7, -8, -9, -10, -11
 PREC_FP64, PREC_MIXED = 0, 1
+REFINE_EXACT, REFINE_FP64 = 0, 1
 
 ARRAY_W, ARRAY_HW, ARRAY_SW, ARRAY_G, ARRAY_D, ARRAY_HW_N, ARRAY_SW_N = range(7)
 
@@ -26,7 +27,8 @@ ARRAY_W, ARRAY_HW, ARRAY_SW, ARRAY_G, ARRAY_D, ARRAY_HW_N, ARRAY_SW_N = range(7)
 class Options(C.Structure):
     _fields_ = [("eta", C.c_double), ("eta_auto", C.c_int32), ("precision", C.c_int32),
                 ("cholesky", C.c_int32), ("max_iter", C.c_int32), ("orth_tol", C.c_double),
-                ("filter_eps", C.c_double), ("stream", C.c_void_p)]
+                ("filter_eps", C.c_double), ("stream", C.c_void_p), ("refine", C.c_int32),
+                ("exact_digits", C.c_int32)]
 
 
 class Pattern(C.Structure):
@@ -75,6 +77,11 @@ _SIGS = {
     "omm_get_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "omm_kernel_launches": (C.c_int64, []),
     "omm_last_error": (C.c_char_p, []),
+    "omm_op_exact_gemm_workspace_bytes": (C.c_int64, [C.c_int64, C.c_int64, C.c_int64, C.c_int32]),
+    "omm_op_exact_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                    C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                    C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                    C.c_void_p, C.c_int64, C.c_void_p]),
     "omm_op_split_gemm_workspace_bytes": (C.c_int64, [C.c_int64, C.c_int64, C.c_int64, C.c_int32]),
     "omm_op_split_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                     C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
@@ -245,6 +252,18 @@ def op_dgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C
 
 def kernel_launches() -> int:
     return int(lib().omm_kernel_launches())
+
+
+def op_exact_gemm_workspace_bytes(M, N, K, ndigits) -> int:
+    return int(lib().omm_op_exact_gemm_workspace_bytes(M, N, K, ndigits))
+
+
+def op_exact_gemm(transA, transB, M, N, K, ndigits, alpha, A, lda, B, ldb, beta, Cin, ldcin, Cout, ldc,
+                  workspace, workspace_bytes, stream=0):
+    return lib().omm_op_exact_gemm(int(transA), int(transB), M, N, K, int(ndigits), float(alpha),
+                                   _ptr(A)[0], lda, _ptr(B)[0], ldb, float(beta), _ptr(Cin)[0], ldcin,
+                                   _ptr(Cout)[0], ldc, _ptr(workspace)[0], workspace_bytes,
+                                   C.c_void_p(stream) if stream else None)
 
 
 def op_split_gemm_workspace_bytes(M, N, K, ndigits) -> int:

@@ -24,13 +24,15 @@ def dev(a):
     return torch.from_numpy(np.asfortranarray(a)).to("cuda")
 
 
-@pytest.mark.parametrize("dims", [(4, 4, 4), (3, 4, 5), (5, 5, 5)])
-def test_mixed_solve_matches_oracle(omm, dims):
+@pytest.mark.parametrize("dims,refine", [((4, 4, 4), "exact"), ((3, 4, 5), "exact"), ((5, 5, 5), "exact"),
+                                         ((4, 4, 4), "fp64"), ((3, 4, 5), "fp64")])
+def test_mixed_solve_matches_oracle(omm, dims, refine):
     import synth
     sysm = synth.make_system(*dims, seed=0)
     H, S = sysm.dense_H(), sysm.dense_S()
     W0 = np.asfortranarray(sysm.W0_dense())
-    s = omm.Solver(sysm.m, sysm.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6)
+    s = omm.Solver(sysm.m, sysm.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6,
+                   refine=omm.REFINE_EXACT if refine == "exact" else omm.REFINE_FP64)
     s.set_HS(dev(H), dev(S))
     W = torch.zeros((sysm.n, sysm.m), dtype=torch.float64, device="cuda").T
     E, iters, st = s.solve(dev(W0), tol=1e-10, W_out=W)
