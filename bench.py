@@ -340,6 +340,33 @@ def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
             "peak_source": f"bf16 sustained ({pk_kind}); achieved counts FP64-equivalent flops"}
 
 
+def run_profile(args):
+    """One solve, nothing else: the command the ncu summaries under profiles/ are taken from."""
+    import torch
+    from paper_2209_05934_gb300 import omm
+
+    omm.lib()
+    sysm = synth.make_system(*WORKLOAD["dims"], seed=WORKLOAD["seed"])
+    dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
+    H, S, W0 = dev(sysm.dense_H()), dev(sysm.dense_S()), dev(sysm.W0_dense())
+    prec = args.precision
+    opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
+                orth_tol=TOL[prec]["orth_tol"], stream=torch.cuda.current_stream().cuda_stream)
+    if args.max_iter > 0:
+        opts["max_iter"] = args.max_iter
+    solver = omm.Solver(sysm.m, sysm.n, 8, **opts)
+    solver.set_profiling(True)
+    solver.set_HS(H, S)
+    E, iters, st = solver.solve(W0, tol=TOL[prec]["tol"], raise_on_error=False)
+    torch.cuda.synchronize()
+    ms, cnt = solver.stage_times()
+    print(json.dumps({"profile": True, "precision": prec, "E": E, "iters": iters, "status": st,
+                      "stages_ms": {n: ms[i] for i, n in enumerate(STAGES)},
+                      "stage_launches": {n: int(cnt[i]) for i, n in enumerate(STAGES)},
+                      "gpu_launches": omm.kernel_launches()}), flush=True)
+    solver.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,7 +374,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="omm", choices=["omm", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--profile", action="store_true",
+                    help="run one solve only (for ncu captures); prints stage times, no benchmark line")
+    ap.add_argument("--max-iter", type=int, default=0, help="with --profile: cap on CG steps")
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(192, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM;
-    const int n0 = blockIdx.y * XBN;
+    const int m0 = blockIdx.y * BM;     // N tiles vary fastest: CTAs in flight share A tiles in L2
+    const int n0 = blockIdx.x * XBN;
     const int nkb_total = (args.K + BK - 1) / BK;
     const int kb_per_chunk = kChunkMax / BK;
     const int nchunks = (nkb_total + kb_per_chunk - 1) / kb_per_chunk;
@@ -260,14 +260,28 @@ __global__ void exp_cm_kernel(int64_t K, int64_t R, const double *__restrict__ X
     }
 }
 
-// K along the source's columns: operand row r is source row r (thread per row).
+// K along the source's columns: operand row r is source row r.  A block covers
+// 32 rows: lane x reads row tr + x (coalesced), the 8 warps split the columns,
+// then the 8 partial maxima of each row are combined in shared memory.
 __global__ void exp_t_kernel(int64_t R, int64_t K, const double *__restrict__ X, int64_t ld, int *e,
                              const DevState *state) {
     if (state != nullptr && *((volatile const int *)&state->done)) return;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+    __shared__ double part[8][32];
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    for (int64_t tr = (int64_t)blockIdx.x * 32; tr < R; tr += (int64_t)gridDim.x * 32) {
+        const int64_t r = tr + lx;
         double mx = 0.0;
-        for (int64_t k = 0; k < K; ++k) mx = fmax(mx, fabs(X[r + k * ld]));
-        e[r] = row_exponent(mx);
+        if (r < R)
+            for (int64_t k = ly; k < K; k += 8) mx = fmax(mx, fabs(X[r + k * ld]));
+        part[ly][lx] = mx;
+        __syncthreads();
+        if (ly == 0 && r < R) {
+            double m2 = part[0][lx];
+#pragma unroll
+            for (int w = 1; w < 8; ++w) m2 = fmax(m2, part[w][lx]);
+            e[r] = row_exponent(m2);
+        }
+        __syncthreads();
     }
 }
 
@@ -334,7 +348,7 @@ int exact_pack(bool k_along_rows, int64_t rows, int64_t cols, const double *X, i
         count_launch();
         OMM_CUDA_TRY(cudaGetLastError());
     } else {              // K = cols, operand rows = rows
-        exp_t_kernel<<<grid_for(rows, 256), 256, 0, st>>>(rows, cols, X, ld, e, state);
+        exp_t_kernel<<<grid_for(rows * 8, 256), 256, 0, st>>>(rows, cols, X, ld, e, state);
         count_launch();
         OMM_CUDA_TRY(cudaGetLastError());
         dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32));
@@ -354,7 +368,7 @@ int exact_gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const ExactArgs
         OMM_CUDA_TRY(cudaFuncSetAttribute(tc_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_bytes = smem;
     }
-    dim3 grid((unsigned)ceil_div(a.M, BM), (unsigned)ceil_div(a.N, XBN), (unsigned)nbatch);
+    dim3 grid((unsigned)ceil_div(a.N, XBN), (unsigned)ceil_div(a.M, BM), (unsigned)nbatch);
     tc_exact_kernel<<<grid, 192, smem, st>>>(mapA, mapB, a);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());

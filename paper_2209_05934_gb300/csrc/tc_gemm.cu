@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(192, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM;
-    const int n0 = blockIdx.y * BN;
+    const int m0 = blockIdx.y * BM;     // N tiles vary fastest: CTAs in flight share A tiles in L2
+    const int n0 = blockIdx.x * BN;
     const int nkb = (args.K + BK - 1) / BK;
 
     if (threadIdx.x == 0) {
@@ -260,7 +260,7 @@ int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int
     int kacc = 512 / BN;
     while (kacc > 1 && kacc > nkb) kacc >>= 1;
     b.kacc = kacc;
-    dim3 grid((unsigned)ceil_div(a.M, BM), (unsigned)ceil_div(a.N, BN), (unsigned)nbatch);
+    dim3 grid((unsigned)ceil_div(a.N, BN), (unsigned)ceil_div(a.M, BM), (unsigned)nbatch);
     tc_gemm_kernel<BN, STAGES><<<grid, 192, smem, st>>>(ma, mb, b);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
