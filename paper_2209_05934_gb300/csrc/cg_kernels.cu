@@ -5,6 +5,7 @@
 // per-block partials in block order, so equal inputs give bitwise equal
 // results (needed for the batched and serving forms, whose results must not
 // depend on what else runs).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <mutex>
@@ -77,6 +78,19 @@ __device__ bool publish_and_collect(const double (&v)[NV], double *partials, uns
 }
 
 __device__ inline bool finite(double x) { return isfinite(x); }
+
+// Three BF16 digits d1 = bf16(v), d2 = bf16(v - d1), d3 = bf16(v - d1 - d2),
+// written to the planes of a DigitOut at element offset o.
+__device__ __forceinline__ void put3(const DigitOut &d, int64_t o, double v) {
+    const __nv_bfloat16 d1 = __double2bfloat16(v);
+    const double r1 = v - (double)__bfloat162float(d1);
+    const __nv_bfloat16 d2 = __double2bfloat16(r1);
+    const __nv_bfloat16 d3 = __double2bfloat16(r1 - (double)__bfloat162float(d2));
+    __nv_bfloat16 *p = (__nv_bfloat16 *)d.ptr;
+    p[o] = d1;
+    p[d.plane + o] = d2;
+    p[2 * d.plane + o] = d3;
+}
 
 __device__ inline double quartic_val(const double *c, double x) {
     return c[0] + x * (c[1] + x * (c[2] + x * (c[3] + x * c[4])));
@@ -264,7 +278,7 @@ __global__ void __launch_bounds__(NT) nn_update_kernel(int n, double *h0, double
                                                         const double *__restrict__ s2,
                                                         int64_t ldz, double *partials,
                                                         unsigned int *counter, DevState *state,
-                                                        int mode) {
+                                                        int mode, DigitOut hsw) {
     if (*((volatile int *)&state->done)) return;
     __shared__ double Tt[4][TILE][TILE + 1];
     __shared__ double red[(NT / 32) * NE];
@@ -304,6 +318,10 @@ __global__ void __launch_bounds__(NT) nn_update_kernel(int n, double *h0, double
                 vs = vs + x * (ys + x * s2s);
                 h0[i + j * ldh] = vh;
                 s0[i + j * ldh] = vs;
+            }
+            if (hsw.ptr != nullptr) {   // column j of [H_W ; S_W] is digit row j, K index i and n + i
+                put3(hsw, j * hsw.ld + i, vh);
+                put3(hsw, j * hsw.ld + n + i, vs);
             }
             if (i == j) v[0] += vh;
             v[1] = fma(vs, vh, v[1]);
@@ -352,16 +370,51 @@ __global__ void __launch_bounds__(NT) nn_update_kernel(int n, double *h0, double
 }
 
 // ---------------------------------------------------------------- m x n kernels
-__global__ void axpy3_kernel(int64_t mn, double *W, const double *__restrict__ D, double *HW,
-                             const double *__restrict__ HD, double *SW,
-                             const double *__restrict__ SD, const DevState *state) {
+// W += x D, H'W += x H'D, SW += x SD over 32 x 32 tiles of the m x n arrays
+// (column-major, ld = m); optionally writes the digits of the new W (column
+// j = digit row j) and of the rows of [SW | H'W] (digit row i, K index j and
+// n + j) through a shared-memory transpose.
+__global__ void __launch_bounds__(NT) update_kernel(int m, int n, double *W, const double *__restrict__ D,
+                                                     double *HW, const double *__restrict__ HD, double *SW,
+                                                     const double *__restrict__ SD, const DevState *state,
+                                                     DigitOut wd, DigitOut swhw) {
     if (*((volatile const int *)&state->done)) return;
+    __shared__ double tH[TILE][TILE + 1];
+    __shared__ double tS[TILE][TILE + 1];
     const double x = state->x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mn;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        W[i] = fma(x, D[i], W[i]);
-        HW[i] = fma(x, HD[i], HW[i]);
-        SW[i] = fma(x, SD[i], SW[i]);
+    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int Tm = (m + TILE - 1) / TILE, Tn = (n + TILE - 1) / TILE;
+    for (int t = blockIdx.x; t < Tm * Tn; t += gridDim.x) {
+        const int ti = t % Tm, tj = t / Tm;
+        const int i = ti * TILE + lx;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int jl = ly + 8 * r, j = tj * TILE + jl;
+            if (i < m && j < n) {
+                const int64_t o = (int64_t)j * m + i;
+                const double w = fma(x, D[o], W[o]);
+                const double hw = fma(x, HD[o], HW[o]);
+                const double sw = fma(x, SD[o], SW[o]);
+                W[o] = w;
+                HW[o] = hw;
+                SW[o] = sw;
+                if (wd.ptr != nullptr) put3(wd, (int64_t)j * wd.ld + i, w);
+                tH[jl][lx] = hw;
+                tS[jl][lx] = sw;
+            }
+        }
+        if (swhw.ptr != nullptr) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int il = ly + 8 * r, ii = ti * TILE + il, jj = tj * TILE + lx;
+                if (ii < m && jj < n) {
+                    put3(swhw, (int64_t)ii * swhw.ld + jj, tS[lx][il]);
+                    put3(swhw, (int64_t)ii * swhw.ld + n + jj, tH[lx][il]);
+                }
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -410,17 +463,20 @@ __global__ void __launch_bounds__(NT) dots_kernel(int64_t mn, const double *__re
     state->restart = restart;
 }
 
-__global__ void direction_kernel(int64_t mn, const double *__restrict__ G, double *Gp, double *D,
-                                 const DevState *state) {
+__global__ void direction_kernel(int m, int n, const double *__restrict__ G, double *Gp, double *D,
+                                 const DevState *state, DigitOut dd) {
     if (*((volatile const int *)&state->done)) return;
     const double beta = state->beta;
     const bool restart = state->restart != 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mn;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double g = G[i];
-        D[i] = restart ? -g : fma(beta, D[i], -g);
-        Gp[i] = g;
-    }
+    for (int j = blockIdx.y; j < n; j += gridDim.y)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+            const int64_t o = (int64_t)j * m + i;
+            const double g = G[o];
+            const double d = restart ? -g : fma(beta, D[o], -g);
+            D[o] = d;
+            Gp[o] = g;
+            if (dd.ptr != nullptr) put3(dd, (int64_t)j * dd.ld + i, d);
+        }
 }
 
 __global__ void shift_kernel(int64_t mm, const double *H, const double *__restrict__ S, double *Hs,
@@ -538,9 +594,11 @@ int launch_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh
     return OMM_OK;
 }
 
-int launch_axpy3(int64_t mn, double *W, const double *D, double *HW, const double *HD, double *SW,
-                 const double *SD, const DevState *state, cudaStream_t st) {
-    axpy3_kernel<<<ew_blocks(mn), NT, 0, st>>>(mn, W, D, HW, HD, SW, SD, state);
+int launch_update(int64_t m, int64_t n, double *W, const double *D, double *HW, const double *HD, double *SW,
+                  const double *SD, const DevState *state, DigitOut wd, DigitOut swhw, cudaStream_t st) {
+    int64_t nb = ceil_div(m, TILE) * ceil_div(n, TILE);
+    if (nb > 152 * 8) nb = 152 * 8;
+    update_kernel<<<(unsigned)nb, NT, 0, st>>>((int)m, (int)n, W, D, HW, HD, SW, SD, state, wd, swhw);
     omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
@@ -548,13 +606,13 @@ int launch_axpy3(int64_t mn, double *W, const double *D, double *HW, const doubl
 
 int launch_nn_update_energy(int n, double *h0, double *s0, int64_t ldh, const double *Z,
                             int64_t ldz, double *scratch, unsigned int *counter, DevState *state,
-                            int mode, cudaStream_t st) {
+                            int mode, cudaStream_t st, DigitOut hsw) {
     const double *X = Z;
     const double *Y = Z + (int64_t)n * ldz;
     const double *h2 = Z + n;
     const double *s2 = Z + n + (int64_t)n * ldz;
     nn_update_kernel<<<red_blocks_for_tiles(n), NT, 0, st>>>(n, h0, s0, ldh, X, Y, h2, s2, ldz,
-                                                             scratch, counter, state, mode);
+                                                             scratch, counter, state, mode, hsw);
     omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
@@ -569,9 +627,10 @@ int launch_dots_beta(int64_t mn, const double *G, const double *Gp, const double
     return OMM_OK;
 }
 
-int launch_direction(int64_t mn, const double *G, double *Gp, double *D, const DevState *state,
-                     cudaStream_t st) {
-    direction_kernel<<<ew_blocks(mn), NT, 0, st>>>(mn, G, Gp, D, state);
+int launch_direction(int64_t m, int64_t n, const double *G, double *Gp, double *D, const DevState *state,
+                     cudaStream_t st, DigitOut dd) {
+    dim3 grid((unsigned)ceil_div(m, NT), (unsigned)(n < 1024 ? n : 1024));
+    direction_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, G, Gp, D, state, dd);
     omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

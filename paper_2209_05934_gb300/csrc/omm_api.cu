@@ -188,7 +188,8 @@ int dense_iteration(omm_handle *h) {
                                      ctr(h, 0), s, nullptr, st, true)); }
     // W += x D, H'W += x H'D, SW += x SD; then H_W, S_W update, energy, RelTol test
     { StageTimer t(h, OMM_STAGE_UPDATE);
-      TRY(omm::launch_axpy3(mn, h->WD, h->WD + mn, h->SWHW + mn, h->HDSD, h->SWHW, h->HDSD + mn, s, st));
+      TRY(omm::launch_update(m, n, h->WD, h->WD + mn, h->SWHW + mn, h->HDSD, h->SWHW, h->HDSD + mn, s,
+                             omm::DigitOut{nullptr, 0, 0}, omm::DigitOut{nullptr, 0, 0}, st));
       TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
                                        ctr(h, 1), s, 0, st)); }
     // G = 4 H'W - 2 [SW H'W][H_W ; S_W]
@@ -197,7 +198,7 @@ int dense_iteration(omm_handle *h) {
     { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, s, st)); }
     { StageTimer t(h, OMM_STAGE_DIRECTION);
       TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 0, st));
-      TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st)); }
+      TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st)); }
     return OMM_OK;
 }
 
@@ -221,16 +222,18 @@ int dense_start(omm_handle *h) {
     g.A[0] = h->SWHW; g.B[0] = h->h0s0; g.Cin[0] = h->SWHW + mn; g.C[0] = h->G;
     TRY(omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, s, st));
     TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 1, st));
-    TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st));
+    TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st));
     return OMM_OK;
 }
 
 // ---------------------------------------------------------------- mixed precision
 constexpr int kDig = 3;
+constexpr int kBK = 32;   // K-block width of the split products (64-byte swizzle, 4-stage ring)
 
 omm::tc::TcArgs tc_args(omm_handle *h, int M, int N, int K) {
     omm::tc::TcArgs a{};
     omm::tc::pairs_for_digits(kDig, a);
+    a.bk = kBK;
     a.M = M;
     a.N = N;
     a.K = K;
@@ -251,12 +254,12 @@ int mixed_alloc(omm_handle *h) {
     TRY(dalloc(&x.HDSDd, (size_t)(kDig * 2 * n * x.ldm)));
     TRY(dalloc(&x.SWHWd, (size_t)(kDig * m * x.ld2n)));
     TRY(dalloc(&x.HSWd, (size_t)(kDig * n * x.ld2n)));
-    TRY(omm::tc::make_digit_map(&x.mapHS_A, x.HSd, m, 2 * m, x.ldm, 2 * m * x.ldm, kDig, 128));
-    TRY(omm::tc::make_digit_map(&x.mapWD_A, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128));
-    TRY(omm::tc::make_digit_map(&x.mapWD_B, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128));
-    TRY(omm::tc::make_digit_map(&x.mapHDSD_B, x.HDSDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128));
-    TRY(omm::tc::make_digit_map(&x.mapSWHW_A, x.SWHWd, 2 * n, m, x.ld2n, m * x.ld2n, kDig, 128));
-    TRY(omm::tc::make_digit_map(&x.mapHSW_B, x.HSWd, 2 * n, n, x.ld2n, n * x.ld2n, kDig, 128));
+    TRY(omm::tc::make_digit_map(&x.mapHS_A, x.HSd, m, 2 * m, x.ldm, 2 * m * x.ldm, kDig, 128, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapWD_A, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapWD_B, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapHDSD_B, x.HDSDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapSWHW_A, x.SWHWd, 2 * n, m, x.ld2n, m * x.ld2n, kDig, 128, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapHSW_B, x.HSWd, 2 * n, n, x.ld2n, n * x.ld2n, kDig, 128, kBK));
     return OMM_OK;
 }
 
@@ -280,6 +283,13 @@ int pack_HSW(omm_handle *h) {
     return omm::tc::pack_cm(2 * h->n, h->n, h->h0s0, 2 * h->n, x.HSWd, x.ld2n, h->n * x.ld2n, kDig,
                             h->dstate, h->stream);
 }
+
+// Digit outputs fused into the elementwise kernels of the mixed form.
+omm::DigitOut dig_W(omm_handle *h) { return {h->mx.WDd, h->mx.ldm, 2 * h->n * h->mx.ldm}; }
+omm::DigitOut dig_D(omm_handle *h) { return {h->mx.WDd + h->n * h->mx.ldm, h->mx.ldm, 2 * h->n * h->mx.ldm}; }
+omm::DigitOut dig_SWHW(omm_handle *h) { return {h->mx.SWHWd, h->mx.ld2n, h->m * h->mx.ld2n}; }
+omm::DigitOut dig_HSW(omm_handle *h) { return {h->mx.HSWd, h->mx.ld2n, h->n * h->mx.ld2n}; }
+constexpr omm::DigitOut kNoDigits{nullptr, 0, 0};
 
 // [H'; S] times the digits of W (rows b_row0 = 0) or D (b_row0 = n) of WDd:
 // FP64 results to C (H' part) and C + c_step (S part), digits to HDSDd.
@@ -436,7 +446,7 @@ int exact_anchor(omm_handle *h) {
     {
         StageTimer t(h, OMM_STAGE_DIRECTION);
         TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 1, st));
-        TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st));
+        TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st));
     }
     return OMM_OK;
 }
@@ -465,14 +475,13 @@ int mixed_start(omm_handle *h) {
     {
         StageTimer t(h, OMM_STAGE_DIRECTION);
         TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 1, st));
-        TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st));
+        TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st, dig_D(h)));
     }
-    { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_D(h)); }
     return OMM_OK;
 }
 
 // One CG step with split-precision products; accurate_gradient selects the
-// FP64 gradient of the refinement sweep.
+// accurate gradient of the refinement sweep (exact-digit or FP64 products).
 int mixed_iteration(omm_handle *h, bool accurate_gradient) {
     const int64_t m = h->m, n = h->n, mn = m * n;
     cudaStream_t st = h->stream;
@@ -483,11 +492,11 @@ int mixed_iteration(omm_handle *h, bool accurate_gradient) {
       TRY(omm::launch_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 0),
                                      ctr(h, 0), s, nullptr, st, true)); }
     { StageTimer t(h, OMM_STAGE_UPDATE);
-      TRY(omm::launch_axpy3(mn, h->WD, h->WD + mn, h->SWHW + mn, h->HDSD, h->SWHW, h->HDSD + mn, s, st));
+      TRY(omm::launch_update(m, n, h->WD, h->WD + mn, h->SWHW + mn, h->HDSD, h->SWHW, h->HDSD + mn, s,
+                             dig_W(h), accurate_gradient ? kNoDigits : dig_SWHW(h), st));
       TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
-                                       ctr(h, 1), s, 0, st)); }
+                                       ctr(h, 1), s, 0, st, accurate_gradient ? kNoDigits : dig_HSW(h))); }
     if (accurate_gradient) {
-        { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
         if (h->opt.refine == OMM_REFINE_EXACT) {
             TRY(exact_gradient(h));
         } else {
@@ -495,13 +504,12 @@ int mixed_iteration(omm_handle *h, bool accurate_gradient) {
             TRY(fp64_gradient(h));
         }
     } else {
-        { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); TRY(pack_SWHW(h)); TRY(pack_HSW(h)); }
-        { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(split_gradient(h)); }
+        StageTimer t(h, OMM_STAGE_GRADIENT);
+        TRY(split_gradient(h));
     }
     { StageTimer t(h, OMM_STAGE_DIRECTION);
       TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 0, st));
-      TRY(omm::launch_direction(mn, h->G, h->Gp, h->WD + mn, s, st)); }
-    { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_D(h)); }
+      TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st, dig_D(h))); }
     return OMM_OK;
 }
 

@@ -71,24 +71,33 @@ int launch_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh
                           int64_t ldz, double *scratch, unsigned int *counter, DevState *state,
                           double *coeffs_out, cudaStream_t st, bool do_linemin);
 
-// W += x D, HW += x HD, SW += x SD  (three m x n arrays, ld = m)
-int launch_axpy3(int64_t mn, double *W, const double *D, double *HW, const double *HD, double *SW,
-                 const double *SD, const DevState *state, cudaStream_t st);
+// Optional BF16 digit output of an elementwise kernel: planes of `plane`
+// elements, digit row stride `ld`; ptr == nullptr disables it.
+struct DigitOut {
+    void *ptr;
+    int64_t ld;
+    int64_t plane;
+};
+
+// W += x D, HW += x HD, SW += x SD  (three m x n arrays, ld = m), optionally
+// writing the digits of W (columns) and of the rows of [SW | HW]
+int launch_update(int64_t m, int64_t n, double *W, const double *D, double *HW, const double *HD, double *SW,
+                  const double *SD, const DevState *state, DigitOut wd, DigitOut swhw, cudaStream_t st);
 
 // h0 += x (X + X^T) + x^2 sym(h2); s0 likewise; then energy, orthonormality,
 // convergence test (mode 0), or initial symmetrisation + energy (mode 1).
 int launch_nn_update_energy(int n, double *h0, double *s0, int64_t ldh, const double *Z,
                             int64_t ldz, double *scratch, unsigned int *counter, DevState *state,
-                            int mode, cudaStream_t st);
+                            int mode, cudaStream_t st, DigitOut hsw = DigitOut{nullptr, 0, 0});
 
 // <G,G>, <G,Gp>, <G,D> then beta (PR+) and the restart decision
 int launch_dots_beta(int64_t mn, const double *G, const double *Gp, const double *D,
                      double *scratch, unsigned int *counter, DevState *state, int first,
                      cudaStream_t st);
 
-// D = -G + beta D (or -G on restart); Gp = G
-int launch_direction(int64_t mn, const double *G, double *Gp, double *D, const DevState *state,
-                     cudaStream_t st);
+// D = -G + beta D (or -G on restart); Gp = G; optionally the digits of D (columns)
+int launch_direction(int64_t m, int64_t n, const double *G, double *Gp, double *D, const DevState *state,
+                     cudaStream_t st, DigitOut dd = DigitOut{nullptr, 0, 0});
 
 // H' = H - eta S (dense, m x m), eta read from state
 int launch_shift(int64_t mm, const double *H, const double *S, double *Hs, const DevState *state,

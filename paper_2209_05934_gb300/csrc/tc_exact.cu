@@ -232,7 +232,14 @@ __global__ void __launch_bounds__(192, 1)
 // ------------------------------------------------------------------ digit packing
 __device__ __forceinline__ int row_exponent(double mx) {
     // 2^e > mx >= 2^(e-1): the scaled row lies in (-1, 1)
-    return mx > 0.0 ? ilogb(mx) + 1 : 0;
+    if (!(mx > 0.0)) return 0;
+    const int e = ilogb(mx) + 1;
+    return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+}
+
+// 2^k as a double for |k| <= 1022 (an exact power of two)
+__device__ __forceinline__ double scale_pow2(int k) {
+    return __longlong_as_double((long long)(1023 + k) << 52);
 }
 
 __device__ __forceinline__ void put_digits(double a, int s, __nv_bfloat16 *dst, int64_t o, int64_t plane) {
@@ -289,10 +296,10 @@ __global__ void digits_cm_kernel(int64_t K, int64_t R, const double *__restrict_
                                  const int *__restrict__ e, __nv_bfloat16 *dst, int64_t ldk, int64_t plane,
                                  int s, const DevState *state) {
     if (state != nullptr && *((volatile const int *)&state->done)) return;
-    const int64_t total = K * R;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = t % K, r = t / K;
-        put_digits(ldexp(X[k + r * ld], -e[r]), s, dst, r * ldk + k, plane);
+    for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
+        const double sc = scale_pow2(-e[r]);
+        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x)
+            put_digits(X[k + r * ld] * sc, s, dst, r * ldk + k, plane);
     }
 }
 
@@ -310,7 +317,7 @@ __global__ void digits_t_kernel(int64_t R, int64_t K, const double *__restrict__
     __syncthreads();
     for (int i = ly; i < 32; i += 8) {
         const int64_t r = tr + i, k = tk + lx;
-        if (r < R && k < K) put_digits(ldexp(tile[lx][i], -e[r]), s, dst, r * ldk + k, plane);
+        if (r < R && k < K) put_digits(tile[lx][i] * scale_pow2(-e[r]), s, dst, r * ldk + k, plane);
     }
 }
 
@@ -343,8 +350,8 @@ int exact_pack(bool k_along_rows, int64_t rows, int64_t cols, const double *X, i
         exp_cm_kernel<<<grid_for(cols * 32, 256), 256, 0, st>>>(rows, cols, X, ld, e, state);
         count_launch();
         OMM_CUDA_TRY(cudaGetLastError());
-        digits_cm_kernel<<<grid_for(rows * cols, 256 * 4), 256, 0, st>>>(rows, cols, X, ld, e, dst, ldk, plane, s,
-                                                                          state);
+        dim3 grid((unsigned)ceil_div(rows, 256 * 2), (unsigned)(cols < 8192 ? cols : 8192));
+        digits_cm_kernel<<<grid, 256, 0, st>>>(rows, cols, X, ld, e, dst, ldk, plane, s, state);
         count_launch();
         OMM_CUDA_TRY(cudaGetLastError());
     } else {              // K = cols, operand rows = rows

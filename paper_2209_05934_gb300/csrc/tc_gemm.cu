@@ -46,15 +46,16 @@ __device__ __forceinline__ void split3(double v, __nv_bfloat16 &d1, __nv_bfloat1
 }
 
 // ------------------------------------------------------------------ the GEMM kernel
-template <int BN, int STAGES>
+template <int BN, int STAGES, int BKT>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const TcArgs args) {
     if (args.state != nullptr && *((volatile const int *)&args.state->done)) return;
     const int z = blockIdx.z;
     const int nA = args.nA, nB = args.nB;
-    const int tileB = BN * BK * 2;
-    const int stage_bytes = nA * TILE_A_BYTES + nB * tileB;
+    constexpr int TILE_A = BM * BKT * 2;
+    const int tileB = BN * BKT * 2;
+    const int stage_bytes = nA * TILE_A + nB * tileB;
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(192, 1)
     const int lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM;     // N tiles vary fastest: CTAs in flight share A tiles in L2
     const int n0 = blockIdx.x * BN;
-    const int nkb = (args.K + BK - 1) / BK;
+    const int nkb = (args.K + BKT - 1) / BKT;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -98,9 +99,9 @@ __global__ void __launch_bounds__(192, 1)
             mbar_arrive_expect_tx(&full_bar[s], (uint32_t)stage_bytes);
             uint8_t *st = smem + s * stage_bytes;
             for (int p = 0; p < nA; ++p)
-                tma_load_3d(st + p * TILE_A_BYTES, &mapA, kb * BK, a_row, p, &full_bar[s]);
+                tma_load_3d(st + p * TILE_A, &mapA, kb * BKT, a_row, p, &full_bar[s]);
             for (int q = 0; q < nB; ++q)
-                tma_load_3d(st + nA * TILE_A_BYTES + q * tileB, &mapB, kb * BK, b_row, q, &full_bar[s]);
+                tma_load_3d(st + nA * TILE_A + q * tileB, &mapB, kb * BKT, b_row, q, &full_bar[s]);
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
@@ -117,11 +118,12 @@ __global__ void __launch_bounds__(192, 1)
             const bool first_kb = kb == 0 || ((kb - 1) * kacc) / nkb != acc;
             const uint32_t tacc = tmem + (uint32_t)(acc * BN);
             for (int pr = 0; pr < args.npairs; ++pr) {
-                const uint32_t sa = st + args.pa[pr] * TILE_A_BYTES;
-                const uint32_t sb = st + nA * TILE_A_BYTES + args.pb[pr] * tileB;
-                const uint64_t da = sdesc_sw128(sa), db = sdesc_sw128(sb);
+                const uint32_t sa = st + args.pa[pr] * TILE_A;
+                const uint32_t sb = st + nA * TILE_A + args.pb[pr] * tileB;
+                const uint64_t da = BKT == 64 ? sdesc_sw128(sa) : sdesc_sw64(sa);
+                const uint64_t db = BKT == 64 ? sdesc_sw128(sb) : sdesc_sw64(sb);
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
+                for (int kk = 0; kk < BKT / 16; ++kk) {
                     // advance 16 elements (32 bytes) along K inside the swizzle row
                     umma_bf16(tacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                               (!first_kb || pr != 0 || kk != 0) ? 1u : 0u);
@@ -189,17 +191,16 @@ __global__ void pack_cm_kernel(int64_t rows, int64_t cols, const double *__restr
                                __nv_bfloat16 *dst, int64_t ldd, int64_t plane, int ndig,
                                const DevState *state) {
     if (state != nullptr && *((volatile const int *)&state->done)) return;
-    const int64_t total = rows * cols;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t % rows, j = t / rows;
-        __nv_bfloat16 d1, d2, d3;
-        split3(src[i + j * ld_src], d1, d2, d3);
-        const int64_t o = j * ldd + i;
-        dst[o] = d1;
-        if (ndig > 1) dst[plane + o] = d2;
-        if (ndig > 2) dst[2 * plane + o] = d3;
-    }
+    for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            __nv_bfloat16 d1, d2, d3;
+            split3(src[i + j * ld_src], d1, d2, d3);
+            const int64_t o = j * ldd + i;
+            dst[o] = d1;
+            if (ndig > 1) dst[plane + o] = d2;
+            if (ndig > 2) dst[2 * plane + o] = d3;
+        }
 }
 
 // column-major source (rows x cols) -> planes [ndig][rows][ldd], element (i, j)
@@ -246,22 +247,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int BKT>
 int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int nbatch, cudaStream_t st) {
-    const int smem = STAGES * (a.nA * TILE_A_BYTES + a.nB * BN * BK * 2) + 1024;
+    const int smem = STAGES * (a.nA * BM * BKT * 2 + a.nB * BN * BKT * 2) + 1024;
     static int attr_bytes = 0;
     if (smem > attr_bytes) {
-        OMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+        OMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, BKT>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_bytes = smem;
     }
     TcArgs b = a;
-    const int nkb = (a.K + BK - 1) / BK;
+    const int nkb = (a.K + BKT - 1) / BKT;
     int kacc = 512 / BN;
     while (kacc > 1 && kacc > nkb) kacc >>= 1;
     b.kacc = kacc;
     dim3 grid((unsigned)ceil_div(a.N, BN), (unsigned)ceil_div(a.M, BM), (unsigned)nbatch);
-    tc_gemm_kernel<BN, STAGES><<<grid, 192, smem, st>>>(ma, mb, b);
+    tc_gemm_kernel<BN, STAGES, BKT><<<grid, 192, smem, st>>>(ma, mb, b);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
@@ -270,18 +271,20 @@ int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int
 }  // namespace
 
 int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
-                   int64_t plane_elems, int nplanes, int box_rows) {
+                   int64_t plane_elems, int nplanes, int box_rows, int bk) {
     auto enc = encode_fn();
     if (enc == nullptr) return OMM_ERR_CUDA;
     if ((ld % 8) != 0 || (plane_elems % 8) != 0 || (((uintptr_t)base) & 15u) != 0) return OMM_ERR_ARG;
     if (K <= 0 || rows <= 0 || nplanes <= 0 || box_rows <= 0 || box_rows > 256) return OMM_ERR_ARG;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nplanes};
     cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)plane_elems * 2};
-    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    if (bk != 64 && bk != 32) return OMM_ERR_ARG;
+    cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     memset(map, 0, sizeof(*map));
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)base, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d): K=%lld rows=%lld ld=%lld planes=%d box_rows=%d",
@@ -297,20 +300,25 @@ int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int 
     if (a.npairs < 1 || a.npairs > 9 || nbatch < 1) return OMM_ERR_ARG;
     for (int p = 0; p < a.npairs; ++p)
         if (a.pa[p] >= a.nA || a.pb[p] >= a.nB) return OMM_ERR_ARG;
-    if (bn == 256) {
-        if (a.nA + 2 * a.nB <= 4) return launch_tc<256, 3>(mapA, mapB, a, nbatch, st);
-        return launch_tc<256, 1>(mapA, mapB, a, nbatch, st);
+    // The tensor maps decide the K-block width: 64 (128-byte swizzle) or 32 (64-byte).
+    if (a.bk == 32) {
+        if (bn == 256) return launch_tc<256, 2, 32>(mapA, mapB, a, nbatch, st);
+        if (a.nA + a.nB <= 4) return launch_tc<128, 6, 32>(mapA, mapB, a, nbatch, st);
+        return launch_tc<128, 4, 32>(mapA, mapB, a, nbatch, st);
     }
-    if (a.nA + a.nB <= 4) return launch_tc<128, 3>(mapA, mapB, a, nbatch, st);
-    return launch_tc<128, 2>(mapA, mapB, a, nbatch, st);
+    if (bn == 256) {
+        if (a.nA + 2 * a.nB <= 4) return launch_tc<256, 3, 64>(mapA, mapB, a, nbatch, st);
+        return launch_tc<256, 1, 64>(mapA, mapB, a, nbatch, st);
+    }
+    if (a.nA + a.nB <= 4) return launch_tc<128, 3, 64>(mapA, mapB, a, nbatch, st);
+    return launch_tc<128, 2, 64>(mapA, mapB, a, nbatch, st);
 }
 
 int pack_cm(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,
             int64_t plane, int ndig, const DevState *state, cudaStream_t st) {
     if (rows <= 0 || cols <= 0) return OMM_OK;
-    int64_t nb = ceil_div(rows * cols, 256 * 4);
-    if (nb > 152 * 16) nb = 152 * 16;
-    pack_cm_kernel<<<(unsigned)nb, 256, 0, st>>>(rows, cols, src, ld_src, dst, ldd, plane, ndig, state);
+    dim3 grid((unsigned)ceil_div(rows, 256 * 2), (unsigned)(cols < 8192 ? cols : 8192));
+    pack_cm_kernel<<<grid, 256, 0, st>>>(rows, cols, src, ld_src, dst, ldd, plane, ndig, state);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
@@ -380,11 +388,13 @@ extern "C" int omm_op_split_gemm(int32_t transA, int32_t transB, int64_t M, int6
     else rc = tc::pack_cm(K, N, B, ldb, Bd, ldk, N * ldk, ndigits, nullptr, st);
     if (rc) return rc;
     CUtensorMap ma, mb;
-    if ((rc = tc::make_digit_map(&ma, Ad, K, M, ldk, M * ldk, ndigits, 128))) return rc;
+    const int bk = ndigits >= 2 ? 32 : 64;
+    if ((rc = tc::make_digit_map(&ma, Ad, K, M, ldk, M * ldk, ndigits, 128, bk))) return rc;
     const int bn = (N > 128 && ndigits == 1) ? 256 : 128;
-    if ((rc = tc::make_digit_map(&mb, Bd, K, N, ldk, N * ldk, ndigits, bn))) return rc;
+    if ((rc = tc::make_digit_map(&mb, Bd, K, N, ldk, N * ldk, ndigits, bn, bk))) return rc;
     tc::TcArgs a{};
     tc::pairs_for_digits(ndigits, a);
+    a.bk = bk;
     a.M = (int)M;
     a.N = (int)N;
     a.K = (int)K;

@@ -31,10 +31,11 @@ struct TcArgs {
     const DevState *state;       // nullable: return at once when state->done
     int *err;                    // nullable: set to 1 when a bounded wait times out
     int kacc;                    // set by the launcher: K-range accumulators in tensor memory
+    int bk;                      // K-block width of the tensor maps: 64 (128-byte swizzle) or 32
 };
 
 int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
-                   int64_t plane_elems, int nplanes, int box_rows);
+                   int64_t plane_elems, int nplanes, int box_rows, int bk = 64);
 int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int nbatch, int bn,
          cudaStream_t st);
 int pack_cm(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,
