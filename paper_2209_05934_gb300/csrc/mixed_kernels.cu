@@ -1,0 +1,498 @@
+// FP32 "glue" kernels of the mixed-precision CG step.
+//
+// GB300 runs FP64 (and conversions from FP64) on a small unit: about two FP64
+// operations per clock per SM against thousands of tensor-core flops.  So the
+// mixed form keeps FP64 only for the state that must stay accurate -- W, H'W,
+// SW, H_W, S_W -- and carries every increment in FP32: the products H'D, SD
+// and the contractions X, Y, h2, s2 come out of the split tensor-core GEMMs as
+// FP32, the gradient and search direction are FP32, and each state update is
+// one FP32 increment added in FP64.  The increments are only as accurate as
+// the 24-bit split products that feed them, so nothing is lost by rounding
+// them to FP32.  Reductions multiply and accumulate in FP32 per thread and
+// combine per-block partials in FP64 in a fixed order (bitwise repeatable).
+//
+// Two quantities avoid cancellation by construction:
+//   c1 = 2 <G, D>   the slope of the line, taken from the CG dot products
+//                   (it equals 2 [4 tr X - 2 <S_W, X> - 2 <Y, H_W>] exactly);
+//   E_{k+1} = c0 + c1 x + c2 x^2 + c3 x^3 + c4 x^4  at the line minimum x,
+//                   the quartic being exact along the line.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "omm_internal.cuh"
+
+namespace omm {
+namespace {
+
+constexpr int NT = 256;
+constexpr int TILE = 32;
+
+// Three BF16 digits of an FP32 value (exact: 3 x 8 significant bits)
+__device__ __forceinline__ void put3f(const DigitOut &d, int64_t o, float v) {
+    const __nv_bfloat16 d1 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(d1);
+    const __nv_bfloat16 d2 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 d3 = __float2bfloat16_rn(r1 - __bfloat162float(d2));
+    __nv_bfloat16 *p = (__nv_bfloat16 *)d.ptr;
+    p[o] = d1;
+    p[d.plane + o] = d2;
+    p[2 * d.plane + o] = d3;
+}
+
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *red) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = v[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        v[q] = s;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[warp * NV + q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += red[w * NV + q];
+            v[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <int NV>
+__device__ bool publish_and_collect(const double (&v)[NV], double *partials, unsigned int *counter,
+                                    double (&tot)[NV], double *red) {
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) partials[blockIdx.x * NV + q] = v[q];
+        __threadfence();
+        is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double w[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) w[q] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += NT)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) w[q] += __ldcg(&partials[b * NV + q]);
+    block_sum<NV>(w, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) tot[q] = w[q];
+        *counter = 0u;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- line search
+__device__ inline double quartic_val(const double *c, double x) {
+    return c[0] + x * (c[1] + x * (c[2] + x * (c[3] + x * c[4])));
+}
+
+__device__ int cubic_real_roots(double a, double b, double c, double d, double *r) {
+    auto f = [&](double x) { return ((a * x + b) * x + c) * x + d; };
+    auto fp = [&](double x) { return (3.0 * a * x + 2.0 * b) * x + c; };
+    const double R = 1.0 + fmax(fabs(b), fmax(fabs(c), fabs(d))) / a;
+    double lo = -R, hi = R, x = 0.0;
+    for (int it = 0; it < 400; ++it) {
+        const double fx = f(x);
+        if (fx == 0.0) break;
+        if (fx < 0.0) lo = x; else hi = x;
+        const double dx = fp(x);
+        double xn = (dx != 0.0) ? x - fx / dx : 0.5 * (lo + hi);
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (xn == x || hi - lo <= 4e-16 * fmax(1.0, fabs(x))) { x = xn; break; }
+        x = xn;
+    }
+    int nr = 0;
+    r[nr++] = x;
+    const double p = b + a * x, q = c + p * x;
+    const double disc = p * p - 4.0 * a * q;
+    if (disc >= 0.0) {
+        const double sq = sqrt(disc);
+        const double t = -0.5 * (p + (p >= 0.0 ? sq : -sq));
+        if (t != 0.0) { r[nr++] = t / a; r[nr++] = q / t; } else { r[nr++] = 0.0; }
+    }
+    for (int i = 0; i < nr; ++i)
+        for (int it = 0; it < 3; ++it) {
+            const double dx = fp(r[i]);
+            if (dx == 0.0) break;
+            const double xn = r[i] - f(r[i]) / dx;
+            if (!isfinite(xn)) break;
+            if (fabs(f(xn)) <= fabs(f(r[i]))) r[i] = xn; else break;
+        }
+    return nr;
+}
+
+// same rule as the FP64 path: lowest value among the positive-curvature roots
+__device__ int quartic_min(const double *c, double *xout) {
+    for (int i = 0; i < 5; ++i)
+        if (!isfinite(c[i])) return OMM_ERR_NONFINITE;
+    if (c[4] == 0.0 && c[3] == 0.0) {
+        if (c[2] > 0.0) { *xout = -c[1] / (2.0 * c[2]); return OMM_OK; }
+        return OMM_ERR_LINESEARCH;
+    }
+    if (c[4] < 0.0) return OMM_ERR_LINESEARCH;
+    double r[3];
+    int nr = 0;
+    if (c[4] > 0.0) {
+        nr = cubic_real_roots(4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1], r);
+    } else {
+        const double a = 3.0 * c[3], b = 2.0 * c[2], cc = c[1];
+        const double disc = b * b - 4.0 * a * cc;
+        if (disc >= 0.0) {
+            const double sq = sqrt(disc);
+            const double t = -0.5 * (b + (b >= 0.0 ? sq : -sq));
+            if (t != 0.0) { r[nr++] = t / a; r[nr++] = cc / t; }
+        }
+    }
+    bool have = false;
+    double best = 0.0, bestv = 0.0;
+    for (int pass = 0; pass < 2 && !have; ++pass)
+        for (int i = 0; i < nr; ++i) {
+            const double x = r[i];
+            if (!isfinite(x)) continue;
+            const double curv = 12.0 * c[4] * x * x + 6.0 * c[3] * x + 2.0 * c[2];
+            if (pass == 0 && !(curv > 0.0)) continue;
+            if (pass == 1 && !(c[4] > 0.0)) continue;
+            const double v = quartic_val(c, x);
+            if (!have || v < bestv || (v == bestv && (fabs(x) < fabs(best) || (fabs(x) == fabs(best) && x > best)))) {
+                have = true;
+                best = x;
+                bestv = v;
+            }
+        }
+    if (!have) return OMM_ERR_LINESEARCH;
+    *xout = best;
+    return OMM_OK;
+}
+
+// ---------------------------------------------------------------- coefficients
+// partials: 0 tr h2, 1 <s0,h2>, 2 <Y,X>, 3 <Y,X^T>, 4 <s2,h0>, 5 <Y,h2>, 6 <s2,X>, 7 <s2,h2>
+constexpr int NC = 8;
+
+__global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__restrict__ h0,
+                                                        const double *__restrict__ s0, int64_t ldh,
+                                                        const float *__restrict__ Z, int64_t ldz,
+                                                        double *partials, unsigned int *counter,
+                                                        DevState *state) {
+    if (*((volatile int *)&state->done)) return;
+    __shared__ float Xt[TILE][TILE + 1];
+    __shared__ double red[(NT / 32) * NC];
+    const float *X = Z, *Y = Z + (int64_t)n * ldz, *h2 = Z + n, *s2 = Z + n + (int64_t)n * ldz;
+    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int T = (n + TILE - 1) / TILE;
+    float f[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) f[q] = 0.f;
+    for (int t = blockIdx.x; t < T * T; t += gridDim.x) {
+        const int ti = t % T, tj = t / T;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int a = ly + 8 * r, gi = tj * TILE + lx, gj = ti * TILE + a;
+            Xt[a][lx] = (gi < n && gj < n) ? X[gi + (int64_t)gj * ldz] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = ti * TILE + lx, j = tj * TILE + ly + 8 * r;
+            if (i >= n || j >= n) continue;
+            const int64_t oz = i + (int64_t)j * ldz, oh = i + (int64_t)j * ldh;
+            const float vh0 = (float)h0[oh], vs0 = (float)s0[oh];
+            const float vx = X[oz], vy = Y[oz], vh2 = h2[oz], vs2 = s2[oz], vxt = Xt[lx][ly + 8 * r];
+            if (i == j) f[0] += vh2;
+            f[1] = fmaf(vs0, vh2, f[1]);
+            f[2] = fmaf(vy, vx, f[2]);
+            f[3] = fmaf(vy, vxt, f[3]);
+            f[4] = fmaf(vs2, vh0, f[4]);
+            f[5] = fmaf(vy, vh2, f[5]);
+            f[6] = fmaf(vs2, vx, f[6]);
+            f[7] = fmaf(vs2, vh2, f[7]);
+        }
+    }
+    double v[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) v[q] = (double)f[q];
+    block_sum<NC>(v, red);
+    double tot[NC];
+    if (!publish_and_collect<NC>(v, partials, counter, tot, red)) return;
+    if (threadIdx.x != 0) return;
+    double c[5];
+    c[0] = state->E - 2.0 * state->eta * (double)n;   // the shifted functional at x = 0
+    c[1] = 2.0 * state->gD;
+    c[2] = 2.0 * (2.0 * tot[0] - tot[1] - 2.0 * (tot[2] + tot[3]) - tot[4]);
+    c[3] = 2.0 * (-2.0 * tot[5] - 2.0 * tot[6]);
+    c[4] = -2.0 * tot[7];
+    for (int q = 0; q < 5; ++q) state->c[q] = c[q];
+    double x = 0.0;
+    const int st = quartic_min(c, &x);
+    state->x = x;
+    state->E_next = quartic_val(c, x) + 2.0 * state->eta * (double)n;
+    if (st != OMM_OK) {
+        state->status = st;
+        state->done = 1;
+    }
+}
+
+// ---------------------------------------------------------------- H_W, S_W update
+// h0 += x (X + X^T) + x^2 sym(h2), s0 likewise (FP32 increments, FP64 sums);
+// ||s0 - I||_F^2 for the orthonormality test; digits of [H_W ; S_W] columns.
+__global__ void __launch_bounds__(NT) mx_nn_update_kernel(int n, double *h0, double *s0, int64_t ldh,
+                                                           const float *__restrict__ Z, int64_t ldz,
+                                                           double *partials, unsigned int *counter,
+                                                           DevState *state, DigitOut hsw) {
+    if (*((volatile int *)&state->done)) return;
+    __shared__ float Tt[4][TILE][TILE + 1];
+    __shared__ double red[(NT / 32)];
+    const float *X = Z, *Y = Z + (int64_t)n * ldz, *h2 = Z + n, *s2 = Z + n + (int64_t)n * ldz;
+    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int T = (n + TILE - 1) / TILE;
+    const float x = (float)state->x;
+    float orth = 0.f;
+    for (int t = blockIdx.x; t < T * T; t += gridDim.x) {
+        const int ti = t % T, tj = t / T;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int a = ly + 8 * r, gi = tj * TILE + lx, gj = ti * TILE + a;
+            const bool in = gi < n && gj < n;
+            const int64_t o = gi + (int64_t)gj * ldz;
+            Tt[0][a][lx] = in ? X[o] : 0.f;
+            Tt[1][a][lx] = in ? Y[o] : 0.f;
+            Tt[2][a][lx] = in ? h2[o] : 0.f;
+            Tt[3][a][lx] = in ? s2[o] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = ti * TILE + lx, j = tj * TILE + ly + 8 * r, b = ly + 8 * r;
+            if (i >= n || j >= n) continue;
+            const int64_t oz = i + (int64_t)j * ldz, oh = i + (int64_t)j * ldh;
+            const float xs = X[oz] + Tt[0][lx][b], ys = Y[oz] + Tt[1][lx][b];
+            const float h2s = 0.5f * (h2[oz] + Tt[2][lx][b]), s2s = 0.5f * (s2[oz] + Tt[3][lx][b]);
+            const double vh = h0[oh] + (double)(x * fmaf(x, h2s, xs));
+            const double vs = s0[oh] + (double)(x * fmaf(x, s2s, ys));
+            h0[oh] = vh;
+            s0[oh] = vs;
+            const float fvs = (float)vs;
+            const float e = (i == j) ? (float)(vs - 1.0) : fvs;
+            orth = fmaf(e, e, orth);
+            if (hsw.ptr != nullptr) {
+                put3f(hsw, (int64_t)j * hsw.ld + i, (float)vh);
+                put3f(hsw, (int64_t)j * hsw.ld + n + i, fvs);
+            }
+        }
+    }
+    double v[1] = {(double)orth};
+    block_sum<1>(v, red);
+    double tot[1];
+    if (!publish_and_collect<1>(v, partials, counter, tot, red)) return;
+    if (threadIdx.x != 0) return;
+    const double E = state->E_next;
+    state->orth2 = tot[0];
+    if (!isfinite(E)) {
+        state->status = OMM_ERR_NONFINITE;
+        state->done = 1;
+        return;
+    }
+    const double Ep = state->E;
+    const double rel = fabs(2.0 * (E - Ep) / (E + Ep));
+    state->E_prev = Ep;
+    state->E = E;
+    state->rel = rel;
+    state->k += 1;
+    const bool orth_ok = !(state->orth_tol > 0.0) || sqrt(tot[0]) < state->orth_tol;
+    if (rel < state->tol && orth_ok) {
+        state->status = OMM_OK;
+        state->done = 1;
+    } else if (state->k >= state->max_iter) {
+        state->status = OMM_ERR_MAXITER;
+        state->done = 1;
+    }
+}
+
+// ---------------------------------------------------------------- W, H'W, SW update
+__global__ void __launch_bounds__(NT) mx_update_kernel(int m, int n, double *W, const float *__restrict__ D,
+                                                        double *HW, const float *__restrict__ HD, double *SW,
+                                                        const float *__restrict__ SD, const DevState *state,
+                                                        DigitOut wd, DigitOut swhw) {
+    if (*((volatile const int *)&state->done)) return;
+    __shared__ float tH[TILE][TILE + 1];
+    __shared__ float tS[TILE][TILE + 1];
+    const float x = (float)state->x;
+    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int Tm = (m + TILE - 1) / TILE, Tn = (n + TILE - 1) / TILE;
+    for (int t = blockIdx.x; t < Tm * Tn; t += gridDim.x) {
+        const int ti = t % Tm, tj = t / Tm;
+        const int i = ti * TILE + lx;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int jl = ly + 8 * r, j = tj * TILE + jl;
+            if (i < m && j < n) {
+                const int64_t o = (int64_t)j * m + i;
+                const double w = W[o] + (double)(x * D[o]);
+                const double hw = HW[o] + (double)(x * HD[o]);
+                const double sw = SW[o] + (double)(x * SD[o]);
+                W[o] = w;
+                HW[o] = hw;
+                SW[o] = sw;
+                if (wd.ptr != nullptr) put3f(wd, (int64_t)j * wd.ld + i, (float)w);
+                tH[jl][lx] = (float)hw;
+                tS[jl][lx] = (float)sw;
+            }
+        }
+        if (swhw.ptr != nullptr) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int il = ly + 8 * r, ii = ti * TILE + il, jj = tj * TILE + lx;
+                if (ii < m && jj < n) {
+                    put3f(swhw, (int64_t)ii * swhw.ld + jj, tS[lx][il]);
+                    put3f(swhw, (int64_t)ii * swhw.ld + n + jj, tH[lx][il]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- CG dots and direction
+constexpr int ND = 3;   // <G,G>, <G,Gp>, <G,D>
+
+__global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__restrict__ G,
+                                                      const float *__restrict__ Gp, const float *__restrict__ D,
+                                                      double *partials, unsigned int *counter, DevState *state,
+                                                      int first) {
+    if (*((volatile int *)&state->done)) return;
+    __shared__ double red[(NT / 32) * ND];
+    float f[ND] = {0.f, 0.f, 0.f};
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < mn; i += (int64_t)gridDim.x * NT) {
+        const float g = G[i];
+        f[0] = fmaf(g, g, f[0]);
+        if (!first) {
+            f[1] = fmaf(g, Gp[i], f[1]);
+            f[2] = fmaf(g, D[i], f[2]);
+        }
+    }
+    double v[ND] = {(double)f[0], (double)f[1], (double)f[2]};
+    block_sum<ND>(v, red);
+    double tot[ND];
+    if (!publish_and_collect<ND>(v, partials, counter, tot, red)) return;
+    if (threadIdx.x != 0) return;
+    const double gg = tot[0];
+    double beta = 0.0;
+    int restart = 1;
+    if (!first) {
+        const double gpgp = state->gg_prev;
+        beta = (gpgp > 0.0) ? fmax(0.0, (gg - tot[1]) / gpgp) : 0.0;
+        restart = (-gg + beta * tot[2] >= 0.0) ? 1 : 0;
+        if (restart) beta = 0.0;
+    }
+    if (!isfinite(gg) || !isfinite(beta)) {
+        state->status = OMM_ERR_NONFINITE;
+        state->done = 1;
+        return;
+    }
+    state->gg = gg;
+    state->ggp = tot[1];
+    state->gd = tot[2];
+    state->gg_prev = gg;
+    state->beta = beta;
+    state->restart = restart;
+    state->gD = restart ? -gg : -gg + beta * tot[2];   // <G, D_new>
+}
+
+__global__ void mx_direction_kernel(int m, int n, const float *__restrict__ G, float *Gp, float *D,
+                                    const DevState *state, DigitOut dd) {
+    if (*((volatile const int *)&state->done)) return;
+    const float beta = (float)state->beta;
+    const bool restart = state->restart != 0;
+    for (int j = blockIdx.y; j < n; j += gridDim.y)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+            const int64_t o = (int64_t)j * m + i;
+            const float g = G[o];
+            const float d = restart ? -g : fmaf(beta, D[o], -g);
+            D[o] = d;
+            Gp[o] = g;
+            if (dd.ptr != nullptr) put3f(dd, (int64_t)j * dd.ld + i, d);
+        }
+}
+
+__global__ void mx_round_kernel(int64_t count, const double *__restrict__ src, float *dst, const DevState *state) {
+    if (state != nullptr && *((volatile const int *)&state->done)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+int tiles_blocks(int64_t a, int64_t b) {
+    int64_t nb = ceil_div(a, TILE) * ceil_div(b, TILE);
+    if (nb > kRedBlocksMax) nb = kRedBlocksMax;
+    return (int)(nb < 1 ? 1 : nb);
+}
+
+}  // namespace
+
+int mx_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh, const float *Z, int64_t ldz,
+                      double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
+    mx_coeffs_kernel<<<tiles_blocks(n, n), NT, 0, st>>>(n, h0, s0, ldh, Z, ldz, scratch, counter, state);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int mx_update(int64_t m, int64_t n, double *W, const float *D, double *HW, const float *HD, double *SW,
+              const float *SD, const DevState *state, DigitOut wd, DigitOut swhw, cudaStream_t st) {
+    int64_t nb = ceil_div(m, TILE) * ceil_div(n, TILE);
+    if (nb > 152 * 8) nb = 152 * 8;
+    mx_update_kernel<<<(unsigned)nb, NT, 0, st>>>((int)m, (int)n, W, D, HW, HD, SW, SD, state, wd, swhw);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int mx_nn_update(int n, double *h0, double *s0, int64_t ldh, const float *Z, int64_t ldz, double *scratch,
+                 unsigned int *counter, DevState *state, DigitOut hsw, cudaStream_t st) {
+    mx_nn_update_kernel<<<tiles_blocks(n, n), NT, 0, st>>>(n, h0, s0, ldh, Z, ldz, scratch, counter, state, hsw);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int mx_dots_beta(int64_t mn, const float *G, const float *Gp, const float *D, double *scratch,
+                 unsigned int *counter, DevState *state, int first, cudaStream_t st) {
+    int64_t nb = ceil_div(mn, (int64_t)NT * 16);
+    if (nb > kRedBlocksMax) nb = kRedBlocksMax;
+    mx_dots_kernel<<<(unsigned)(nb < 1 ? 1 : nb), NT, 0, st>>>(mn, G, Gp, D, scratch, counter, state, first);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int mx_direction(int64_t m, int64_t n, const float *G, float *Gp, float *D, const DevState *state, DigitOut dd,
+                 cudaStream_t st) {
+    dim3 grid((unsigned)ceil_div(m, NT), (unsigned)(n < 1024 ? n : 1024));
+    mx_direction_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, G, Gp, D, state, dd);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int mx_round(int64_t count, const double *src, float *dst, const DevState *state, cudaStream_t st) {
+    int64_t nb = ceil_div(count, 256 * 4);
+    if (nb > 152 * 8) nb = 152 * 8;
+    mx_round_kernel<<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, st>>>(count, src, dst, state);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+}  // namespace omm

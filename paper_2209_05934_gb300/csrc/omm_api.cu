@@ -28,10 +28,13 @@
 //   HDSDd [3][2n][ldm]   columns of [H'D | SD]                      B of Z
 //   SWHWd [3][m][ld2n]   rows of [SW | H'W]                         A of the gradient
 //   HSWd  [3][n][ld2n]   columns of [H_W ; S_W]                     B of the gradient
+// FP32 increments of the mixed form (column-major): HDSD32 = [H'D | SD] (m x 2n),
+// Z32 = [[X, Y], [h2, s2]] (2n x 2n), G32, Gp32, D32 (m x n).
 struct MixedBufs {
     int64_t ldm = 0, ld2n = 0;
     __nv_bfloat16 *HSd = nullptr, *WDd = nullptr, *HDSDd = nullptr, *SWHWd = nullptr, *HSWd = nullptr;
     CUtensorMap mapHS_A, mapWD_A, mapWD_B, mapHDSD_B, mapSWHW_A, mapHSW_B;
+    float *HDSD32 = nullptr, *Z32 = nullptr, *G32 = nullptr, *Gp32 = nullptr, *D32 = nullptr;
 };
 
 // Exact-digit operands of the refinement sweep (s digits, row-scaled), each
@@ -111,6 +114,11 @@ void free_handle(omm_handle *h) {
     cudaFree(h->mx.HDSDd);
     cudaFree(h->mx.SWHWd);
     cudaFree(h->mx.HSWd);
+    cudaFree(h->mx.HDSD32);
+    cudaFree(h->mx.Z32);
+    cudaFree(h->mx.G32);
+    cudaFree(h->mx.Gp32);
+    cudaFree(h->mx.D32);
     cudaFree(h->ex.HSx);
     cudaFree(h->ex.Wx);
     cudaFree(h->ex.HWSWx);
@@ -254,6 +262,11 @@ int mixed_alloc(omm_handle *h) {
     TRY(dalloc(&x.HDSDd, (size_t)(kDig * 2 * n * x.ldm)));
     TRY(dalloc(&x.SWHWd, (size_t)(kDig * m * x.ld2n)));
     TRY(dalloc(&x.HSWd, (size_t)(kDig * n * x.ld2n)));
+    TRY(dalloc(&x.HDSD32, (size_t)(2 * m * n)));
+    TRY(dalloc(&x.Z32, (size_t)(4 * n * n)));
+    TRY(dalloc(&x.G32, (size_t)(m * n)));
+    TRY(dalloc(&x.Gp32, (size_t)(m * n)));
+    TRY(dalloc(&x.D32, (size_t)(m * n)));
     TRY(omm::tc::make_digit_map(&x.mapHS_A, x.HSd, m, 2 * m, x.ldm, 2 * m * x.ldm, kDig, 128, kBK));
     TRY(omm::tc::make_digit_map(&x.mapWD_A, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
     TRY(omm::tc::make_digit_map(&x.mapWD_B, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
@@ -293,7 +306,7 @@ constexpr omm::DigitOut kNoDigits{nullptr, 0, 0};
 
 // [H'; S] times the digits of W (rows b_row0 = 0) or D (b_row0 = n) of WDd:
 // FP64 results to C (H' part) and C + c_step (S part), digits to HDSDd.
-int split_products(omm_handle *h, int b_row0, double *C, int64_t c_step, int64_t dout_row0,
+int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_step, int64_t dout_row0,
                    int64_t dout_step) {
     const int64_t m = h->m, n = h->n;
     MixedBufs &x = h->mx;
@@ -303,6 +316,7 @@ int split_products(omm_handle *h, int b_row0, double *C, int64_t c_step, int64_t
     a.b_row0 = b_row0;
     a.b_row_step = 0;
     a.C = C;
+    a.C32 = C32;
     a.ldc = m;
     a.c_step = c_step;
     a.Dout = x.HDSDd + dout_row0 * x.ldm;
@@ -318,7 +332,7 @@ int split_contract(omm_handle *h) {
     const int64_t m = h->m, n = h->n;
     MixedBufs &x = h->mx;
     omm::tc::TcArgs a = tc_args(h, (int)(2 * n), (int)(2 * n), (int)m);
-    a.C = h->Z;
+    a.C32 = x.Z32;
     a.ldc = 2 * n;
     return omm::tc::gemm(x.mapWD_A, x.mapHDSD_B, a, 1, 128, h->stream);
 }
@@ -332,16 +346,18 @@ int split_gradient(omm_handle *h) {
     a.beta = 4.0;
     a.Cin = h->SWHW + m * n;
     a.ldcin = m;
-    a.C = h->G;
+    a.C32 = x.G32;
     a.ldc = m;
     return omm::tc::gemm(x.mapSWHW_A, x.mapHSW_B, a, 1, 128, h->stream);
 }
 
+// FP64 gradient (CUDA cores), rounded to the FP32 gradient of the mixed form
 int fp64_gradient(omm_handle *h) {
     const int64_t m = h->m, n = h->n, mn = m * n;
     omm::GemmBatch g{};
     g.A[0] = h->SWHW; g.B[0] = h->h0s0; g.Cin[0] = h->SWHW + mn; g.C[0] = h->G;
-    return omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, h->dstate, h->stream);
+    TRY(omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, h->dstate, h->stream));
+    return omm::mx_round(mn, h->G, h->mx.G32, h->dstate, h->stream);
 }
 
 int exact_alloc(omm_handle *h) {
@@ -399,7 +415,7 @@ int exact_gradient(omm_handle *h) {
     a.beta = 4.0;
     a.Cin = h->SWHW + m * n;
     a.ldcin = m;
-    a.C = h->G;
+    a.C32 = h->mx.G32;
     a.ldc = m;
     a.eA = e.eSWHW;
     a.eB = e.eHSW;
@@ -443,12 +459,16 @@ int exact_anchor(omm_handle *h) {
     TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
                                      ctr(h, 1), s, 1, st));
     TRY(exact_gradient(h));
-    {
-        StageTimer t(h, OMM_STAGE_DIRECTION);
-        TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 1, st));
-        TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st));
-    }
     return OMM_OK;
+}
+
+// CG dots + direction of the mixed form (FP32 G, Gp, D; digits of D)
+int mixed_direction(omm_handle *h, int first) {
+    const int64_t m = h->m, n = h->n;
+    StageTimer t(h, OMM_STAGE_DIRECTION);
+    TRY(omm::mx_dots_beta(m * n, h->mx.G32, h->mx.Gp32, h->mx.D32, scr(h, 2), ctr(h, 2), h->dstate, first,
+                          h->stream));
+    return omm::mx_direction(m, n, h->mx.G32, h->mx.Gp32, h->mx.D32, h->dstate, dig_D(h), h->stream);
 }
 
 // Start of the split-precision phase: H'W, SW, H_W, S_W, energy, G, D from W.
@@ -457,8 +477,8 @@ int mixed_start(omm_handle *h) {
     cudaStream_t st = h->stream;
     omm::DevState *s = h->dstate;
     { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
-    // H'W -> SWHW + mn, SW -> SWHW; their digits to HDSDd rows [0, n) and [n, 2n)
-    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(split_products(h, 0, h->SWHW + mn, -mn, 0, n)); }
+    // H'W -> SWHW + mn, SW -> SWHW (FP64 state); their digits to HDSDd rows [0, n) and [n, 2n)
+    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(split_products(h, 0, h->SWHW + mn, nullptr, -mn, 0, n)); }
     {
         StageTimer t(h, OMM_STAGE_CONTRACT);
         omm::tc::TcArgs a = tc_args(h, (int)n, (int)n, (int)m);
@@ -472,30 +492,26 @@ int mixed_start(omm_handle *h) {
                                      ctr(h, 1), s, 1, st));
     { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_SWHW(h)); TRY(pack_HSW(h)); }
     { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(split_gradient(h)); }
-    {
-        StageTimer t(h, OMM_STAGE_DIRECTION);
-        TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 1, st));
-        TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st, dig_D(h)));
-    }
-    return OMM_OK;
+    return mixed_direction(h, 1);
 }
 
-// One CG step with split-precision products; accurate_gradient selects the
+// One CG step of the mixed form: split-precision products with FP32 outputs,
+// FP64 state updated from FP32 increments; accurate_gradient selects the
 // accurate gradient of the refinement sweep (exact-digit or FP64 products).
 int mixed_iteration(omm_handle *h, bool accurate_gradient) {
     const int64_t m = h->m, n = h->n, mn = m * n;
     cudaStream_t st = h->stream;
     omm::DevState *s = h->dstate;
-    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(split_products(h, (int)n, h->HDSD, mn, 0, n)); }
+    MixedBufs &x = h->mx;
+    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(split_products(h, (int)n, nullptr, x.HDSD32, mn, 0, n)); }
     { StageTimer t(h, OMM_STAGE_CONTRACT); TRY(split_contract(h)); }
     { StageTimer t(h, OMM_STAGE_LINESEARCH);
-      TRY(omm::launch_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 0),
-                                     ctr(h, 0), s, nullptr, st, true)); }
+      TRY(omm::mx_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 0), ctr(h, 0), s, st)); }
     { StageTimer t(h, OMM_STAGE_UPDATE);
-      TRY(omm::launch_update(m, n, h->WD, h->WD + mn, h->SWHW + mn, h->HDSD, h->SWHW, h->HDSD + mn, s,
-                             dig_W(h), accurate_gradient ? kNoDigits : dig_SWHW(h), st));
-      TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
-                                       ctr(h, 1), s, 0, st, accurate_gradient ? kNoDigits : dig_HSW(h))); }
+      TRY(omm::mx_update(m, n, h->WD, x.D32, h->SWHW + mn, x.HDSD32, h->SWHW, x.HDSD32 + mn, s, dig_W(h),
+                         accurate_gradient ? kNoDigits : dig_SWHW(h), st));
+      TRY(omm::mx_nn_update((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 1), ctr(h, 1), s,
+                            accurate_gradient ? kNoDigits : dig_HSW(h), st)); }
     if (accurate_gradient) {
         if (h->opt.refine == OMM_REFINE_EXACT) {
             TRY(exact_gradient(h));
@@ -507,10 +523,7 @@ int mixed_iteration(omm_handle *h, bool accurate_gradient) {
         StageTimer t(h, OMM_STAGE_GRADIENT);
         TRY(split_gradient(h));
     }
-    { StageTimer t(h, OMM_STAGE_DIRECTION);
-      TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 0, st));
-      TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st, dig_D(h))); }
-    return OMM_OK;
+    return mixed_direction(h, 0);
 }
 
 // Run chunks of iterations until the device state says done; checks the
@@ -719,8 +732,10 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
             } else {
                 StageTimer t(h, OMM_STAGE_ANCHOR);
                 TRY(dense_start(h));
+                TRY(omm::mx_round(mn, h->G, h->mx.G32, h->dstate, st));
             }
-            { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); TRY(pack_D(h)); }
+            TRY(mixed_direction(h, 1));
+            { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
             TRY(run_until_done(h, [&] { return mixed_iteration(h, true); }));
         }
     } else {

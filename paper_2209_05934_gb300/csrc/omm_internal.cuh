@@ -44,6 +44,8 @@ struct DevState {
     double trh0, sh, orth2;      // tr h0, <s0,h0>, ||s0 - I||_F^2
     double charge;
     int wait_timeout;            // set by a tensor-core kernel whose bounded wait gave up
+    double gD;                   // <G, D> of the current direction (= c1 / 2)
+    double E_next;               // energy at the line minimum, from the quartic
 };
 
 // -------- FP64 GEMM (dense_fp64.cu)
@@ -106,6 +108,21 @@ int launch_shift(int64_t mm, const double *H, const double *S, double *Hs, const
 // Gershgorin bound into state->eta (dense, column-major m x m, symmetric)
 int launch_gershgorin(int64_t m, const double *H, const double *S, double *scratch,
                       unsigned int *counter, DevState *state, cudaStream_t st);
+
+// -------- FP32-glue kernels of the mixed form (mixed_kernels.cu).  The FP64
+// state (W, H'W, SW, H_W, S_W) is updated from FP32 increments; the search
+// direction, gradient and products are FP32 (see mixed_kernels.cu).
+int mx_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh, const float *Z, int64_t ldz,
+                      double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
+int mx_update(int64_t m, int64_t n, double *W, const float *D, double *HW, const float *HD, double *SW,
+              const float *SD, const DevState *state, DigitOut wd, DigitOut swhw, cudaStream_t st);
+int mx_nn_update(int n, double *h0, double *s0, int64_t ldh, const float *Z, int64_t ldz, double *scratch,
+                 unsigned int *counter, DevState *state, DigitOut hsw, cudaStream_t st);
+int mx_dots_beta(int64_t mn, const float *G, const float *Gp, const float *D, double *scratch,
+                 unsigned int *counter, DevState *state, int first, cudaStream_t st);
+int mx_direction(int64_t m, int64_t n, const float *G, float *Gp, float *D, const DevState *state, DigitOut dd,
+                 cudaStream_t st);
+int mx_round(int64_t count, const double *src, float *dst, const DevState *state, cudaStream_t st);
 
 __device__ __host__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

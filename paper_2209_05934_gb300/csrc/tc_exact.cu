@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(192, 1)
         }
         // final: C = alpha 2^(eA + eB) run + beta Cin
         const bool ok = __all_sync(0xffffffffu, alive && have_run);
-        double *C = args.C + (int64_t)z * args.c_step;
+        double *C = args.C != nullptr ? args.C + (int64_t)z * args.c_step : nullptr;
+        float *C32 = args.C32 != nullptr ? args.C32 + (int64_t)z * args.c_step : nullptr;
         const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
         const int *eA = args.eA + (int64_t)z * args.eA_step;
         const int *eB = args.eB + (int64_t)z * args.eB_step;
@@ -215,7 +216,8 @@ __global__ void __launch_bounds__(192, 1)
                     if (col >= args.N) break;
                     double out = args.alpha * ldexp(v[j], ea + eB[col]);
                     if (Cin != nullptr) out = fma(args.beta, Cin[row + (int64_t)col * args.ldcin], out);
-                    C[row + (int64_t)col * args.ldc] = out;
+                    if (C32 != nullptr) C32[row + (int64_t)col * args.ldc] = (float)out;
+                    else C[row + (int64_t)col * args.ldc] = out;
                 }
             }
         }

@@ -22,7 +22,8 @@ struct ExactArgs {
     double alpha, beta;
     const double *Cin;
     int64_t ldcin, cin_step;
-    double *C;
+    double *C;         // FP64 output, or nullptr when C32 is set
+    float *C32;        // FP32 output (the result is rounded once, after the FP64 combination)
     int64_t ldc, c_step;
     const int *eA;     // row exponents of A (indexed by output row)
     const int *eB;     // row exponents of B (indexed by output column)

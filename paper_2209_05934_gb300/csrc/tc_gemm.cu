@@ -139,37 +139,75 @@ __global__ void __launch_bounds__(192, 1)
         bool got = nkb > 0 && mbar_wait(&acc_bar, 0, deadline, &abort_flag, args.err);
         const bool have_acc = __all_sync(0xffffffffu, got);   // tcgen05.ld is warp-collective
         tc_fence_after();
-        double *C = args.C + (int64_t)z * args.c_step;
+        double *C = args.C != nullptr ? args.C + (int64_t)z * args.c_step : nullptr;
         const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
         __nv_bfloat16 *Dd = args.Dout ? args.Dout + (int64_t)z * args.dout_step : nullptr;
         const int nacc = nkb < kacc ? nkb : kacc;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            double v[16];
+        if (args.C32 != nullptr) {
+            // FP32 epilogue: no FP64 arithmetic except reading an FP64 Cin
+            float *C32 = args.C32 + (int64_t)z * args.c_step;
+            const float alpha = (float)args.alpha, beta = (float)args.beta;
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.0;
-            if (have_acc) {
-                for (int ac = 0; ac < nacc; ++ac) {
-                    float f[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * BN + c0), f);
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                if (have_acc) {
+                    for (int ac = 0; ac < nacc; ++ac) {
+                        float f[16];
+                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * BN + c0), f);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += (double)f[i];
+                        for (int i = 0; i < 16; ++i) v[i] += f[i];
+                    }
+                }
+                if (row < args.M) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int col = n0 + c0 + i;
+                        if (col >= args.N) break;
+                        float out = alpha * v[i];
+                        if (Cin != nullptr) out = fmaf(beta, (float)Cin[row + (int64_t)col * args.ldcin], out);
+                        C32[row + (int64_t)col * args.ldc] = out;
+                        if (Dd != nullptr) {
+                            const int64_t o = row + (int64_t)col * args.ldd;
+                            const __nv_bfloat16 d1 = __float2bfloat16_rn(out);
+                            const float r1 = out - __bfloat162float(d1);
+                            const __nv_bfloat16 d2 = __float2bfloat16_rn(r1);
+                            Dd[o] = d1;
+                            if (args.ndig > 1) Dd[args.dplane + o] = d2;
+                            if (args.ndig > 2) Dd[2 * args.dplane + o] = __float2bfloat16_rn(r1 - __bfloat162float(d2));
+                        }
+                    }
                 }
             }
-            if (row < args.M) {
+        } else {
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                double v[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = n0 + c0 + i;
-                    if (col >= args.N) break;
-                    double out = args.alpha * v[i];
-                    if (Cin != nullptr) out = fma(args.beta, Cin[row + (int64_t)col * args.ldcin], out);
-                    C[row + (int64_t)col * args.ldc] = out;
-                    if (Dd != nullptr) {
-                        __nv_bfloat16 d1, d2, d3;
-                        split3(out, d1, d2, d3);
-                        const int64_t o = row + (int64_t)col * args.ldd;
-                        Dd[o] = d1;
-                        if (args.ndig > 1) Dd[args.dplane + o] = d2;
-                        if (args.ndig > 2) Dd[2 * args.dplane + o] = d3;
+                for (int i = 0; i < 16; ++i) v[i] = 0.0;
+                if (have_acc) {
+                    for (int ac = 0; ac < nacc; ++ac) {
+                        float f[16];
+                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * BN + c0), f);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] += (double)f[i];
+                    }
+                }
+                if (row < args.M) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int col = n0 + c0 + i;
+                        if (col >= args.N) break;
+                        double out = args.alpha * v[i];
+                        if (Cin != nullptr) out = fma(args.beta, Cin[row + (int64_t)col * args.ldcin], out);
+                        C[row + (int64_t)col * args.ldc] = out;
+                        if (Dd != nullptr) {
+                            __nv_bfloat16 d1, d2, d3;
+                            split3(out, d1, d2, d3);
+                            const int64_t o = row + (int64_t)col * args.ldd;
+                            Dd[o] = d1;
+                            if (args.ndig > 1) Dd[args.dplane + o] = d2;
+                            if (args.ndig > 2) Dd[2 * args.dplane + o] = d3;
+                        }
                     }
                 }
             }

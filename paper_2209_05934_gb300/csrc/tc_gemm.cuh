@@ -23,7 +23,8 @@ struct TcArgs {
     double alpha, beta;
     const double *Cin;           // nullable
     int64_t ldcin, cin_step;
-    double *C;                   // FP64 column-major output
+    double *C;                   // FP64 column-major output (or nullptr when C32 is set)
+    float *C32;                  // FP32 column-major output: accumulate, scale and split in FP32
     int64_t ldc, c_step;
     __nv_bfloat16 *Dout;         // nullable: BF16 digits of C, planes [ndig][..][ldd]
     int64_t ldd, dplane, dout_step;
