@@ -236,7 +236,8 @@ int dense_start(omm_handle *h) {
 
 // ---------------------------------------------------------------- mixed precision
 constexpr int kDig = 3;
-constexpr int kBK = 32;   // K-block width of the split products (64-byte swizzle, 4-stage ring)
+constexpr int kBK = 32;   // K-block width of the split products (64-byte swizzle)
+constexpr int kBN = 256;  // output tile width of the split products (UMMA N = 256)
 
 omm::tc::TcArgs tc_args(omm_handle *h, int M, int N, int K) {
     omm::tc::TcArgs a{};
@@ -269,10 +270,10 @@ int mixed_alloc(omm_handle *h) {
     TRY(dalloc(&x.D32, (size_t)(m * n)));
     TRY(omm::tc::make_digit_map(&x.mapHS_A, x.HSd, m, 2 * m, x.ldm, 2 * m * x.ldm, kDig, 128, kBK));
     TRY(omm::tc::make_digit_map(&x.mapWD_A, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
-    TRY(omm::tc::make_digit_map(&x.mapWD_B, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
-    TRY(omm::tc::make_digit_map(&x.mapHDSD_B, x.HDSDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapWD_B, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, kBN, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapHDSD_B, x.HDSDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, kBN, kBK));
     TRY(omm::tc::make_digit_map(&x.mapSWHW_A, x.SWHWd, 2 * n, m, x.ld2n, m * x.ld2n, kDig, 128, kBK));
-    TRY(omm::tc::make_digit_map(&x.mapHSW_B, x.HSWd, 2 * n, n, x.ld2n, n * x.ld2n, kDig, 128, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapHSW_B, x.HSWd, 2 * n, n, x.ld2n, n * x.ld2n, kDig, kBN, kBK));
     return OMM_OK;
 }
 
@@ -324,7 +325,7 @@ int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_s
     a.dplane = 2 * n * x.ldm;
     a.dout_step = dout_step * x.ldm;
     a.ndig = kDig;
-    return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, 128, h->stream);
+    return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, kBN, h->stream);
 }
 
 // Z = [W D]^T [H'D SD]
@@ -334,7 +335,7 @@ int split_contract(omm_handle *h) {
     omm::tc::TcArgs a = tc_args(h, (int)(2 * n), (int)(2 * n), (int)m);
     a.C32 = x.Z32;
     a.ldc = 2 * n;
-    return omm::tc::gemm(x.mapWD_A, x.mapHDSD_B, a, 1, 128, h->stream);
+    return omm::tc::gemm(x.mapWD_A, x.mapHDSD_B, a, 1, kBN, h->stream);
 }
 
 // G = 4 H'W - 2 [SW H'W][H_W ; S_W]
@@ -348,7 +349,7 @@ int split_gradient(omm_handle *h) {
     a.ldcin = m;
     a.C32 = x.G32;
     a.ldc = m;
-    return omm::tc::gemm(x.mapSWHW_A, x.mapHSW_B, a, 1, 128, h->stream);
+    return omm::tc::gemm(x.mapSWHW_A, x.mapHSW_B, a, 1, kBN, h->stream);
 }
 
 // FP64 gradient (CUDA cores), rounded to the FP32 gradient of the mixed form
@@ -486,7 +487,7 @@ int mixed_start(omm_handle *h) {
         a.C = h->h0s0;
         a.ldc = 2 * n;
         a.c_step = n;             // H_W in rows [0, n), S_W in rows [n, 2n)
-        TRY(omm::tc::gemm(h->mx.mapWD_A, h->mx.mapHDSD_B, a, 2, 128, st));
+        TRY(omm::tc::gemm(h->mx.mapWD_A, h->mx.mapHDSD_B, a, 2, kBN, st));
     }
     TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
                                      ctr(h, 1), s, 1, st));

@@ -340,7 +340,7 @@ int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int 
         if (a.pa[p] >= a.nA || a.pb[p] >= a.nB) return OMM_ERR_ARG;
     // The tensor maps decide the K-block width: 64 (128-byte swizzle) or 32 (64-byte).
     if (a.bk == 32) {
-        if (bn == 256) return launch_tc<256, 2, 32>(mapA, mapB, a, nbatch, st);
+        if (bn == 256) return launch_tc<256, 3, 32>(mapA, mapB, a, nbatch, st);
         if (a.nA + a.nB <= 4) return launch_tc<128, 6, 32>(mapA, mapB, a, nbatch, st);
         return launch_tc<128, 4, 32>(mapA, mapB, a, nbatch, st);
     }
@@ -428,7 +428,7 @@ extern "C" int omm_op_split_gemm(int32_t transA, int32_t transB, int64_t M, int6
     CUtensorMap ma, mb;
     const int bk = ndigits >= 2 ? 32 : 64;
     if ((rc = tc::make_digit_map(&ma, Ad, K, M, ldk, M * ldk, ndigits, 128, bk))) return rc;
-    const int bn = (N > 128 && ndigits == 1) ? 256 : 128;
+    const int bn = N > 128 ? 256 : 128;
     if ((rc = tc::make_digit_map(&mb, Bd, K, N, ldk, N * ldk, ndigits, bn, bk))) return rc;
     tc::TcArgs a{};
     tc::pairs_for_digits(ndigits, a);
