@@ -81,8 +81,11 @@ __global__ void __launch_bounds__(192, 1)
         abort_flag = 0;
         mbar_fence_init();
     }
-    const int kacc = args.kacc;   // accumulators in tensor memory, each owning a contiguous K range
-    if (warp == 1) tmem_alloc(&tmem_base, (uint32_t)(BN * kacc));
+    // Accumulators in tensor memory: kacc contiguous K ranges x ncls pair classes
+    // (class 0: the leading digit pair (1,1); class 1: every smaller pair).
+    const int kacc = args.kacc, ncls = args.ncls;
+    const uint32_t tmem_cols = (uint32_t)(BN * kacc * ncls);
+    if (warp == 1) tmem_alloc(&tmem_base, tmem_cols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -107,17 +110,19 @@ __global__ void __launch_bounds__(192, 1)
         // ---------------- MMA issuer
         constexpr uint32_t idesc = idesc_bf16(BM, BN);
         bool ok = true;
+        uint32_t written = 0;   // accumulators already holding a partial sum
         for (int kb = 0; kb < nkb && ok; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
             if (!mbar_wait(&full_bar[s], ph, deadline, &abort_flag, args.err)) { ok = false; break; }
             tc_fence_after();
             const uint32_t st = smem_u32(smem + s * stage_bytes);
-            // k-block kb feeds accumulator (kb * kacc) / nkb; its first k-block overwrites
-            const int acc = (kb * kacc) / nkb;
-            const bool first_kb = kb == 0 || ((kb - 1) * kacc) / nkb != acc;
-            const uint32_t tacc = tmem + (uint32_t)(acc * BN);
+            // k-block kb feeds K slot (kb * kacc) / nkb; the first MMA into an accumulator overwrites it
+            const int slot = (kb * kacc) / nkb;
             for (int pr = 0; pr < args.npairs; ++pr) {
+                const int cls = (ncls == 2 && (args.pa[pr] != 0 || args.pb[pr] != 0)) ? 1 : 0;
+                const int acc = slot * ncls + cls;
+                const uint32_t tacc = tmem + (uint32_t)(acc * BN);
                 const uint32_t sa = st + args.pa[pr] * TILE_A;
                 const uint32_t sb = st + nA * TILE_A + args.pb[pr] * tileB;
                 const uint64_t da = BKT == 64 ? sdesc_sw128(sa) : sdesc_sw64(sa);
@@ -126,7 +131,8 @@ __global__ void __launch_bounds__(192, 1)
                 for (int kk = 0; kk < BKT / 16; ++kk) {
                     // advance 16 elements (32 bytes) along K inside the swizzle row
                     umma_bf16(tacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                              (!first_kb || pr != 0 || kk != 0) ? 1u : 0u);
+                              ((written >> acc) & 1u) ? 1u : 0u);
+                    written |= 1u << acc;
                 }
             }
             umma_commit(&empty_bar[s]);
@@ -142,7 +148,7 @@ __global__ void __launch_bounds__(192, 1)
         double *C = args.C != nullptr ? args.C + (int64_t)z * args.c_step : nullptr;
         const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
         __nv_bfloat16 *Dd = args.Dout ? args.Dout + (int64_t)z * args.dout_step : nullptr;
-        const int nacc = nkb < kacc ? nkb : kacc;
+        const int nacc = (nkb < kacc ? nkb : kacc) * ncls;   // accumulators that were written
         if (args.C32 != nullptr) {
             // FP32 epilogue: no FP64 arithmetic except reading an FP64 Cin
             float *C32 = args.C32 + (int64_t)z * args.c_step;
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem, (uint32_t)(BN * kacc));
+        tmem_dealloc(tmem, tmem_cols);
     }
 }
 
@@ -296,7 +302,12 @@ int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int
     }
     TcArgs b = a;
     const int nkb = (a.K + BKT - 1) / BKT;
-    int kacc = 512 / BN;
+    bool has_main = false, has_small = false;
+    for (int p = 0; p < a.npairs; ++p) {
+        if (a.pa[p] == 0 && a.pb[p] == 0) has_main = true; else has_small = true;
+    }
+    b.ncls = (has_main && has_small) ? 2 : 1;
+    int kacc = 512 / (BN * b.ncls);
     while (kacc > 1 && kacc > nkb) kacc >>= 1;
     b.kacc = kacc;
     dim3 grid((unsigned)ceil_div(a.N, BN), (unsigned)ceil_div(a.M, BM), (unsigned)nbatch);

@@ -32,6 +32,7 @@ struct TcArgs {
     const DevState *state;       // nullable: return at once when state->done
     int *err;                    // nullable: set to 1 when a bounded wait times out
     int kacc;                    // set by the launcher: K-range accumulators in tensor memory
+    int ncls;                    // set by the launcher: 2 = leading digit pair kept apart
     int bk;                      // K-block width of the tensor maps: 64 (128-byte swizzle) or 32
 };
 
