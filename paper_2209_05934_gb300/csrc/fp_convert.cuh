@@ -1,0 +1,47 @@
+// Double <-> float conversion on the integer pipe.
+//
+// On GB300 a hardware FP64 -> FP32 conversion issues on the small FP64 unit
+// (measured about 0.2 per clock per SM, ten times slower than an FP64 FMA),
+// so kernels that convert every element become conversion-bound.  These
+// versions take the IEEE-754 bit fields apart with integer instructions.
+// d2f rounds to nearest, ties to even, exactly like the hardware conversion
+// for every double whose float result is a normal number or zero; results
+// that would be subnormal flush to a signed zero and overflow saturates to
+// infinity.  f2d is exact for every finite float.
+#pragma once
+
+#include <stdint.h>
+
+namespace omm {
+
+__device__ __forceinline__ float sw_d2f(double d) {
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;   // biased float exponent
+    const uint64_t m = b & 0xFFFFFFFFFFFFFull;               // 52-bit fraction
+    if (e <= 0) return __uint_as_float(sign);               // zero, subnormal range: signed zero
+    if (e >= 255) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));  // inf / nan
+    uint32_t f = ((uint32_t)e << 23) | (uint32_t)(m >> 29);
+    const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFu);       // 29 dropped bits
+    if (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) f += 1u;   // may carry into the exponent
+    return __uint_as_float(sign | f);
+}
+
+__device__ __forceinline__ double sw_f2d(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+    const uint32_t e = (u >> 23) & 0xFF;
+    const uint64_t m = u & 0x7FFFFFu;
+    if (e == 0) {
+        if (m == 0) return __longlong_as_double((long long)sign);
+        // subnormal float: normalise
+        const int lz = __clz((int)m) - 8;                      // leading zeros inside the 23-bit field
+        const uint64_t mm = (m << (lz + 1)) & 0x7FFFFFull;
+        const uint64_t ed = (uint64_t)(1023 - 127 - lz);
+        return __longlong_as_double((long long)(sign | (ed << 52) | (mm << 29)));
+    }
+    if (e == 255) return __longlong_as_double((long long)(sign | (0x7FFull << 52) | (m << 29)));
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e - 127 + 1023) << 52) | (m << 29)));
+}
+
+}  // namespace omm

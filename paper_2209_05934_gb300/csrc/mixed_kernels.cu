@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include "fp_convert.cuh"
 #include "omm_internal.cuh"
 
 namespace omm {
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
             const int i = ti * TILE + lx, j = tj * TILE + ly + 8 * r;
             if (i >= n || j >= n) continue;
             const int64_t oz = i + (int64_t)j * ldz, oh = i + (int64_t)j * ldh;
-            const float vh0 = (float)h0[oh], vs0 = (float)s0[oh];
+            const float vh0 = sw_d2f(h0[oh]), vs0 = sw_d2f(s0[oh]);
             const float vx = X[oz], vy = Y[oz], vh2 = h2[oz], vs2 = s2[oz], vxt = Xt[lx][ly + 8 * r];
             if (i == j) f[0] += vh2;
             f[1] = fmaf(vs0, vh2, f[1]);
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
     double x = 0.0;
     const int st = quartic_min(c, &x);
     state->x = x;
+    state->x_f = (float)x;
     state->E_next = quartic_val(c, x) + 2.0 * state->eta * (double)n;
     if (st != OMM_OK) {
         state->status = st;
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(NT) mx_nn_update_kernel(int n, double *h0, dou
     const float *X = Z, *Y = Z + (int64_t)n * ldz, *h2 = Z + n, *s2 = Z + n + (int64_t)n * ldz;
     const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
     const int T = (n + TILE - 1) / TILE;
-    const float x = (float)state->x;
+    const float x = state->x_f;
     float orth = 0.f;
     for (int t = blockIdx.x; t < T * T; t += gridDim.x) {
         const int ti = t % T, tj = t / T;
@@ -279,15 +281,15 @@ __global__ void __launch_bounds__(NT) mx_nn_update_kernel(int n, double *h0, dou
             const int64_t oz = i + (int64_t)j * ldz, oh = i + (int64_t)j * ldh;
             const float xs = X[oz] + Tt[0][lx][b], ys = Y[oz] + Tt[1][lx][b];
             const float h2s = 0.5f * (h2[oz] + Tt[2][lx][b]), s2s = 0.5f * (s2[oz] + Tt[3][lx][b]);
-            const double vh = h0[oh] + (double)(x * fmaf(x, h2s, xs));
-            const double vs = s0[oh] + (double)(x * fmaf(x, s2s, ys));
+            const double vh = h0[oh] + sw_f2d(x * fmaf(x, h2s, xs));
+            const double vs = s0[oh] + sw_f2d(x * fmaf(x, s2s, ys));
             h0[oh] = vh;
             s0[oh] = vs;
-            const float fvs = (float)vs;
-            const float e = (i == j) ? (float)(vs - 1.0) : fvs;
+            const float fvs = sw_d2f(vs);
+            const float e = (i == j) ? sw_d2f(vs - 1.0) : fvs;
             orth = fmaf(e, e, orth);
             if (hsw.ptr != nullptr) {
-                put3f(hsw, (int64_t)j * hsw.ld + i, (float)vh);
+                put3f(hsw, (int64_t)j * hsw.ld + i, sw_d2f(vh));
                 put3f(hsw, (int64_t)j * hsw.ld + n + i, fvs);
             }
         }
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(NT) mx_update_kernel(int m, int n, double *W, 
     if (*((volatile const int *)&state->done)) return;
     __shared__ float tH[TILE][TILE + 1];
     __shared__ float tS[TILE][TILE + 1];
-    const float x = (float)state->x;
+    const float x = state->x_f;
     const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
     const int Tm = (m + TILE - 1) / TILE, Tn = (n + TILE - 1) / TILE;
     for (int t = blockIdx.x; t < Tm * Tn; t += gridDim.x) {
@@ -339,15 +341,15 @@ __global__ void __launch_bounds__(NT) mx_update_kernel(int m, int n, double *W, 
             const int jl = ly + 8 * r, j = tj * TILE + jl;
             if (i < m && j < n) {
                 const int64_t o = (int64_t)j * m + i;
-                const double w = W[o] + (double)(x * D[o]);
-                const double hw = HW[o] + (double)(x * HD[o]);
-                const double sw = SW[o] + (double)(x * SD[o]);
+                const double w = W[o] + sw_f2d(x * D[o]);
+                const double hw = HW[o] + sw_f2d(x * HD[o]);
+                const double sw = SW[o] + sw_f2d(x * SD[o]);
                 W[o] = w;
                 HW[o] = hw;
                 SW[o] = sw;
-                if (wd.ptr != nullptr) put3f(wd, (int64_t)j * wd.ld + i, (float)w);
-                tH[jl][lx] = (float)hw;
-                tS[jl][lx] = (float)sw;
+                if (wd.ptr != nullptr) put3f(wd, (int64_t)j * wd.ld + i, sw_d2f(w));
+                tH[jl][lx] = sw_d2f(hw);
+                tS[jl][lx] = sw_d2f(sw);
             }
         }
         if (swhw.ptr != nullptr) {
@@ -407,6 +409,7 @@ __global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__
     state->gd = tot[2];
     state->gg_prev = gg;
     state->beta = beta;
+    state->beta_f = (float)beta;
     state->restart = restart;
     state->gD = restart ? -gg : -gg + beta * tot[2];   // <G, D_new>
 }
@@ -414,7 +417,7 @@ __global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__
 __global__ void mx_direction_kernel(int m, int n, const float *__restrict__ G, float *Gp, float *D,
                                     const DevState *state, DigitOut dd) {
     if (*((volatile const int *)&state->done)) return;
-    const float beta = (float)state->beta;
+    const float beta = state->beta_f;
     const bool restart = state->restart != 0;
     for (int j = blockIdx.y; j < n; j += gridDim.y)
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
@@ -430,7 +433,7 @@ __global__ void mx_direction_kernel(int m, int n, const float *__restrict__ G, f
 __global__ void mx_round_kernel(int64_t count, const double *__restrict__ src, float *dst, const DevState *state) {
     if (state != nullptr && *((volatile const int *)&state->done)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
+        dst[i] = sw_d2f(src[i]);
 }
 
 int tiles_blocks(int64_t a, int64_t b) {

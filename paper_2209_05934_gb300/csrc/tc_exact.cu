@@ -3,10 +3,9 @@
 // Error-free splitting in the manner of Ozaki, Ogita, Oishi & Rump (2012),
 // applied to BF16 tensor cores as in Mukunoki et al. (2020): every K-major
 // row r of an operand is scaled by 2^-e_r so its entries lie in (-1, 1), then
-// cut into fixed-point digits
-//     d_1 = rint(a * 64),  a_1 = a * 64 - d_1,
-//     d_t = rint(a_{t-1} * 128),  a_t = a_{t-1} * 128 - d_t,
-// so a = sum_t d_t 2^-(7t-1) + O(2^-(7s)), each |d_t| <= 64 (exact in BF16).
+// cut into s fixed-point digits: the integer F = round(a 2^(6 + 7(s-1))) is
+// written in balanced base 128, so a = sum_t d_t 2^-(7t-1) + O(2^-(7s)) with
+// each |d_t| <= 64 (exact in BF16).
 // A product of two digits is at most 2^12 in magnitude, so a sum of up to
 // 4096 of them is an integer below 2^24: the tensor cores accumulate every
 // digit pair (t, u) over a K chunk of <= 4096 exactly in FP32.  Pairs with
@@ -232,25 +231,42 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 // ------------------------------------------------------------------ digit packing
-__device__ __forceinline__ int row_exponent(double mx) {
-    // 2^e > mx >= 2^(e-1): the scaled row lies in (-1, 1)
-    if (!(mx > 0.0)) return 0;
-    const int e = ilogb(mx) + 1;
+// All integer arithmetic: the FP64 unit of GB300 is far too narrow for
+// per-element digit splitting.
+//
+// A row's exponent e makes the scaled row lie in (-1, 1): 2^e > max |a|.
+// Magnitudes of non-negative doubles order like their bit patterns, so the
+// row maximum is an integer max over the bits with the sign cleared.
+__device__ __forceinline__ int exponent_from_maxbits(uint64_t mb) {
+    const int be = (int)(mb >> 52);                 // biased exponent of max |a|
+    if (be == 0) return 0;                           // zero (or subnormal) row
+    int e = be - 1023 + 1;                           // 2^e > max |a| >= 2^(e-1)
     return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
 }
 
-// 2^k as a double for |k| <= 1022 (an exact power of two)
-__device__ __forceinline__ double scale_pow2(int k) {
-    return __longlong_as_double((long long)(1023 + k) << 52);
-}
-
-__device__ __forceinline__ void put_digits(double a, int s, __nv_bfloat16 *dst, int64_t o, int64_t plane) {
-    double x = a * 64.0;
-    for (int t = 0; t < s; ++t) {
-        const double d = rint(x);
-        dst[t * plane + o] = __double2bfloat16(d);   // |d| <= 64: exact
-        x = (x - d) * 128.0;
+// Digits of a = v 2^-e: F = round(v 2^(B-e)) with B = 6 + 7(s-1), then balanced
+// base-128 digits from the bottom: F = sum_t d_t 128^(s-t), d_t in [-64, 64].
+// d_t then carries the weight 2^-(7t-1) of the fixed-point splitting.
+__device__ __forceinline__ void put_digits(double v, int e, int s, __nv_bfloat16 *dst, int64_t o, int64_t plane) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int be = (int)((b >> 52) & 0x7FF);
+    int64_t F = 0;
+    if (be != 0) {
+        const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // v = mant 2^(be - 1075)
+        const int shift = be - 1075 + (6 + 7 * (s - 1)) - e;
+        if (shift >= 0) {
+            F = (int64_t)(mant << shift);             // |F| < 2^(6 + 7(s-1)) <= 2^55
+        } else if (shift > -64) {
+            F = (int64_t)((mant + (1ull << (-shift - 1))) >> (-shift));
+        }
+        if (b >> 63) F = -F;
     }
+    for (int t = s - 1; t >= 1; --t) {
+        const int64_t r = ((F + 64) & 127) - 64;      // in [-64, 63]
+        dst[t * plane + o] = __float2bfloat16_rn((float)r);
+        F = (F - r) >> 7;
+    }
+    dst[o] = __float2bfloat16_rn((float)F);           // |F| <= 64
 }
 
 // K along the source's rows: operand row r is source column r (warp per column).
@@ -260,12 +276,19 @@ __global__ void exp_cm_kernel(int64_t K, int64_t R, const double *__restrict__ X
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t *Xb = (const uint64_t *)X;
     for (int64_t r = w; r < R; r += nw) {
-        double mx = 0.0;
-        for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[k + r * ld]));
+        unsigned long long mx = 0;
+        for (int64_t k = lane; k < K; k += 32) {
+            const unsigned long long a = Xb[k + r * ld] & 0x7FFFFFFFFFFFFFFFull;
+            mx = a > mx ? a : mx;
+        }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        if (lane == 0) e[r] = row_exponent(mx);
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+            mx = o > mx ? o : mx;
+        }
+        if (lane == 0) e[r] = exponent_from_maxbits(mx);
     }
 }
 
@@ -275,20 +298,24 @@ __global__ void exp_cm_kernel(int64_t K, int64_t R, const double *__restrict__ X
 __global__ void exp_t_kernel(int64_t R, int64_t K, const double *__restrict__ X, int64_t ld, int *e,
                              const DevState *state) {
     if (state != nullptr && *((volatile const int *)&state->done)) return;
-    __shared__ double part[8][32];
+    __shared__ unsigned long long part[8][32];
     const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const uint64_t *Xb = (const uint64_t *)X;
     for (int64_t tr = (int64_t)blockIdx.x * 32; tr < R; tr += (int64_t)gridDim.x * 32) {
         const int64_t r = tr + lx;
-        double mx = 0.0;
+        unsigned long long mx = 0;
         if (r < R)
-            for (int64_t k = ly; k < K; k += 8) mx = fmax(mx, fabs(X[r + k * ld]));
+            for (int64_t k = ly; k < K; k += 8) {
+                const unsigned long long a = Xb[r + k * ld] & 0x7FFFFFFFFFFFFFFFull;
+                mx = a > mx ? a : mx;
+            }
         part[ly][lx] = mx;
         __syncthreads();
         if (ly == 0 && r < R) {
-            double m2 = part[0][lx];
+            unsigned long long m2 = part[0][lx];
 #pragma unroll
-            for (int w = 1; w < 8; ++w) m2 = fmax(m2, part[w][lx]);
-            e[r] = row_exponent(m2);
+            for (int w = 1; w < 8; ++w) m2 = part[w][lx] > m2 ? part[w][lx] : m2;
+            e[r] = exponent_from_maxbits(m2);
         }
         __syncthreads();
     }
@@ -299,9 +326,9 @@ __global__ void digits_cm_kernel(int64_t K, int64_t R, const double *__restrict_
                                  int s, const DevState *state) {
     if (state != nullptr && *((volatile const int *)&state->done)) return;
     for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
-        const double sc = scale_pow2(-e[r]);
+        const int er = e[r];
         for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x)
-            put_digits(X[k + r * ld] * sc, s, dst, r * ldk + k, plane);
+            put_digits(X[k + r * ld], er, s, dst, r * ldk + k, plane);
     }
 }
 
@@ -319,7 +346,7 @@ __global__ void digits_t_kernel(int64_t R, int64_t K, const double *__restrict__
     __syncthreads();
     for (int i = ly; i < 32; i += 8) {
         const int64_t r = tr + i, k = tk + lx;
-        if (r < R && k < K) put_digits(tile[lx][i] * scale_pow2(-e[r]), s, dst, r * ldk + k, plane);
+        if (r < R && k < K) put_digits(tile[lx][i], e[r], s, dst, r * ldk + k, plane);
     }
 }
 

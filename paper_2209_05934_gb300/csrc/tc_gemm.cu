@@ -27,6 +27,7 @@
 #include <cudaTypedefs.h>
 #include <string.h>
 
+#include "fp_convert.cuh"
 #include "omm_internal.cuh"
 #include "tc_gemm.cuh"
 #include "tc_ptx.cuh"
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(192, 1)
                         const int col = n0 + c0 + i;
                         if (col >= args.N) break;
                         float out = alpha * v[i];
-                        if (Cin != nullptr) out = fmaf(beta, (float)Cin[row + (int64_t)col * args.ldcin], out);
+                        if (Cin != nullptr) out = fmaf(beta, sw_d2f(Cin[row + (int64_t)col * args.ldcin]), out);
                         C32[row + (int64_t)col * args.ldc] = out;
                         if (Dd != nullptr) {
                             const int64_t o = row + (int64_t)col * args.ldd;
