@@ -88,10 +88,10 @@ typedef struct {
     int32_t cholesky;      /* 1: Cholesky-reduced variant (dense only), S = L L^T */
     int32_t max_iter;      /* CG step limit, default 10000 */
     double orth_tol;       /* > 0: also require ||W^T S W - I||_F < orth_tol to stop */
-    double filter_eps;     /* block filtering threshold on Frobenius norms, default 1e-8:
-                              input blocks with ||B||_F < eps are dropped from the stored
-                              pattern; block products with ||A_ik|| ||B_kj|| < eps are
-                              skipped (screening never changes a stored pattern) */
+    double filter_eps;     /* block filtering threshold, default 1e-8 (sparse form): an
+                              input block pair is dropped from the stored H/S pattern
+                              when both ||H_b||_F < eps and ||S_b||_F < eps (squares summed
+                              in row-major element order, strict comparison) */
     void *stream;          /* cudaStream_t for all work of the handle, NULL = own stream */
     int32_t refine;        /* arithmetic of the mixed form's refinement sweep (re-anchoring
                               and gradient): OMM_REFINE_EXACT (default) or OMM_REFINE_FP64 */
@@ -172,6 +172,22 @@ int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device);
 
 void omm_destroy(omm_handle *h);
 const char *omm_status_str(int status);
+
+/*
+ * Block patterns of a linear-scaling handle (host block-CSR arrays; rowptr
+ * receives nrows + 1 entries, col the entries counted by omm_get_diag's nnzb_*):
+ *   OMM_PATTERN_H   stored pattern of H and S after the block filtering of the
+ *                   last omm_set_HS (nbr rows);
+ *   OMM_PATTERN_W   localisation pattern of W (nbr rows);
+ *   OMM_PATTERN_HW  structural pattern of H W, the union over K in row I of H
+ *                   of the W rows K (nbr rows) -- where H'W, SW, H'D, SD live;
+ *   OMM_PATTERN_N   structural pattern of W^T H W on n x n blocks of bn x bn
+ *                   (nbc rows) -- where H_W, S_W and the contractions live.
+ * The product patterns follow the pattern given at omm_create; blocks that the
+ * filter drops are stored as zeros.
+ */
+enum { OMM_PATTERN_H = 0, OMM_PATTERN_W = 1, OMM_PATTERN_HW = 2, OMM_PATTERN_N = 3 };
+int omm_get_pattern(omm_handle *h, int32_t which, int64_t *rowptr, int32_t *col);
 
 /* Human-readable detail of the last failure on the calling thread (which
  * CUDA call failed and why); empty when none.  Owned by the library. */

@@ -353,6 +353,12 @@ def filter_blocks(vals, eps: float) -> np.ndarray:
     return ~(s < eps * eps)
 
 
+def filter_hs_blocks(H_vals, S_vals, eps: float) -> np.ndarray:
+    """Keep-mask of the shared H/S pattern: a block is dropped only when both its
+    H and its S block are below eps (H' = H - eta S is then negligible too)."""
+    return filter_blocks(H_vals, eps) | filter_blocks(S_vals, eps)
+
+
 def structural_pattern_product(rowptr_a, col_a, rowptr_b, col_b, nb_cols):
     """Boolean block pattern of A*B (block CSR in, block CSR out, sorted)."""
     na = rowptr_a.shape[0] - 1

@@ -15,9 +15,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "omm_internal.cuh"
+#include "sparse.cuh"
 #include "tc_exact.cuh"
 #include "tc_gemm.cuh"
 
@@ -71,6 +74,8 @@ struct omm_handle {
     int chunk = 8;
     MixedBufs mx;
     ExactBufs ex;
+    omm::sp::Host sh;   // linear-scaling form: patterns and gather lists (host)
+    omm::sp::Dev sd;    // linear-scaling form: device arrays
     // optional per-stage device timing (omm_set_profiling)
     bool profiling = false;
     static constexpr int kMaxEv = 2048;
@@ -125,6 +130,7 @@ void free_handle(omm_handle *h) {
     cudaFree(h->ex.SWHWx);
     cudaFree(h->ex.HSWx);
     cudaFree(h->ex.e);
+    omm::sp::release(h->sd);
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -527,6 +533,39 @@ int mixed_iteration(omm_handle *h, bool accurate_gradient) {
     return mixed_direction(h, 0);
 }
 
+// ---------------------------------------------------------------- linear-scaling form
+int sparse_start(omm_handle *h) {
+    omm::sp::Dev &d = h->sd;
+    cudaStream_t st = h->stream;
+    omm::DevState *s = h->dstate;
+    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(omm::sp::products(d, d.W, d.HW, d.SW, s, st)); }
+    // H_W = W^T H'W and S_W = W^T S W through the contraction kernel (D := W)
+    { StageTimer t(h, OMM_STAGE_CONTRACT); TRY(omm::sp::contract(d, d.W, d.W, d.HW, d.SW, d.h0, d.s0, d.h2, d.s2, s, st)); }
+    TRY(omm::sp::nn_update(d, h->n, 1, scr(h, 1), ctr(h, 1), s, st));
+    { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(omm::sp::gradient(d, s, st)); }
+    { StageTimer t(h, OMM_STAGE_DIRECTION);
+      TRY(omm::sp::dots(d, 1, scr(h, 2), ctr(h, 2), s, st));
+      TRY(omm::sp::direction(d, s, st)); }
+    return OMM_OK;
+}
+
+int sparse_iteration(omm_handle *h) {
+    omm::sp::Dev &d = h->sd;
+    cudaStream_t st = h->stream;
+    omm::DevState *s = h->dstate;
+    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(omm::sp::products(d, d.D, d.HD, d.SD, s, st)); }
+    { StageTimer t(h, OMM_STAGE_CONTRACT); TRY(omm::sp::contract(d, d.W, d.D, d.HD, d.SD, d.X, d.Y, d.h2, d.s2, s, st)); }
+    { StageTimer t(h, OMM_STAGE_LINESEARCH); TRY(omm::sp::coeffs(d, scr(h, 0), ctr(h, 0), s, st)); }
+    { StageTimer t(h, OMM_STAGE_UPDATE);
+      TRY(omm::sp::axpy(d, s, st));
+      TRY(omm::sp::nn_update(d, h->n, 0, scr(h, 1), ctr(h, 1), s, st)); }
+    { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(omm::sp::gradient(d, s, st)); }
+    { StageTimer t(h, OMM_STAGE_DIRECTION);
+      TRY(omm::sp::dots(d, 0, scr(h, 2), ctr(h, 2), s, st));
+      TRY(omm::sp::direction(d, s, st)); }
+    return OMM_OK;
+}
+
 // Run chunks of iterations until the device state says done; checks the
 // bounded-wait error word after every chunk.
 template <class F>
@@ -589,7 +628,14 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
     if (m <= 0 || n <= 0 || n > m) return OMM_ERR_ARG;
     if (n > 2147483647 / 2 || m > ((int64_t)1 << 31)) return OMM_ERR_ARG;
     if (block_size < 0) return OMM_ERR_ARG;
-    if (pattern != nullptr) return OMM_ERR_UNSUPPORTED;   // sparse form: separate handle type
+    if (pattern != nullptr) {
+        if (pattern->bm <= 0 || pattern->bn <= 0 || pattern->bm != block_size || pattern->nbr * pattern->bm != m ||
+            pattern->nbc * pattern->bn != n || pattern->H_rowptr == nullptr || pattern->H_col == nullptr ||
+            pattern->W_rowptr == nullptr || pattern->W_col == nullptr)
+            return OMM_ERR_PATTERN;
+        if (pattern->bm != 8 || pattern->bn != 2) return OMM_ERR_UNSUPPORTED;
+        if (opt != nullptr && (opt->precision != OMM_PREC_FP64 || opt->cholesky != 0)) return OMM_ERR_UNSUPPORTED;
+    }
     omm_handle *h = new (std::nothrow) omm_handle();
     if (h == nullptr) return OMM_ERR_NOMEM;
     h->m = m;
@@ -616,7 +662,28 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         h->own_stream = true;
     }
     const int64_t mn = m * n;
-    if ((rc = dalloc(&h->HS, (size_t)(2 * m * m))) ||
+    if (pattern != nullptr) {
+        h->sparse = true;
+        omm::sp::Pattern P;
+        P.bm = pattern->bm;
+        P.bn = pattern->bn;
+        P.nbr = pattern->nbr;
+        P.nbc = pattern->nbc;
+        P.Hrp = pattern->H_rowptr;
+        P.Hcol = pattern->H_col;
+        P.Wrp = pattern->W_rowptr;
+        P.Wcol = pattern->W_col;
+        if ((rc = omm::sp::build(P, h->sh)) || (rc = omm::sp::upload(h->sh, h->sd)) ||
+            (rc = dalloc(&h->scratch, (size_t)(4 * omm::kRedBlocksMax * omm::kRedSlots))) ||
+            (rc = dalloc(&h->counters, (size_t)(64 * 8))) || (rc = dalloc(&h->dstate, 1))) {
+            free_handle(h);
+            return rc;
+        }
+        h->diag.nnzb_H = h->sd.nnzH;
+        h->diag.nnzb_W = h->sd.nnzW;
+        h->diag.nnzb_HW = h->sd.nnzHW;
+        h->diag.nnzb_N = h->sd.nnzN;
+    } else if ((rc = dalloc(&h->HS, (size_t)(2 * m * m))) ||
         (rc = dalloc(&h->WD, (size_t)(2 * mn))) || (rc = dalloc(&h->HDSD, (size_t)(2 * mn))) ||
         (rc = dalloc(&h->SWHW, (size_t)(2 * mn))) || (rc = dalloc(&h->h0s0, (size_t)(2 * n * n))) ||
         (rc = dalloc(&h->Z, (size_t)(4 * n * n))) || (rc = dalloc(&h->G, (size_t)mn)) ||
@@ -655,6 +722,34 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
     const int64_t m = h->m, mm = m * m;
     cudaStream_t st = h->stream;
     OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
+    if (h->sparse) {
+        omm::DevState init{};
+        init.eta = h->opt.eta;
+        *h->hstate = init;
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
+        {
+            StageTimer t(h, OMM_STAGE_SETUP);
+            TRY(omm::sp::set_HS(h->sd, H, S, on_device != 0, h->opt.filter_eps, h->opt.eta_auto != 0, scr(h, 3),
+                                ctr(h, 3), h->dstate, st));
+        }
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
+        OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
+        OMM_CUDA_TRY(cudaStreamSynchronize(st));
+        harvest_stage_times(h);
+        if (h->hstate->status != OMM_OK) return h->hstate->status;
+        // stored H/S pattern after filtering
+        std::vector<unsigned char> keep((size_t)h->sd.nnzH);
+        OMM_CUDA_TRY(cudaMemcpy(keep.data(), h->sd.keep, keep.size(), cudaMemcpyDeviceToHost));
+        int64_t kept = 0;
+        for (unsigned char k : keep) kept += k != 0;
+        h->diag.nnzb_H = kept;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        h->diag.t_setup_ms = ms;
+        h->diag.eta = h->hstate->eta;
+        h->have_HS = true;
+        return OMM_OK;
+    }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     // S goes to its slot; H is staged in the H' slot and shifted in place
     OMM_CUDA_TRY(cudaMemcpyAsync(h->HS + mm, S, mm * sizeof(double), kind, st));
@@ -696,10 +791,12 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
     if (!h->have_HS) return OMM_ERR_STATE;
     if (W0 == nullptr && !h->have_W) return OMM_ERR_STATE;
     const int64_t m = h->m, n = h->n, mn = m * n;
+    const int64_t wlen = h->sparse ? h->sd.nnzW * h->sd.bm * h->sd.bn : mn;   // doubles in W
+    double *Wdev = h->sparse ? h->sd.W : h->WD;
     cudaStream_t st = h->stream;
     OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
     if (W0 != nullptr)
-        OMM_CUDA_TRY(cudaMemcpyAsync(h->WD, W0, mn * sizeof(double),
+        OMM_CUDA_TRY(cudaMemcpyAsync(Wdev, W0, wlen * sizeof(double),
                                      W0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     omm::DevState init{};
     init.eta = h->diag.eta;
@@ -710,7 +807,11 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
     *h->hstate = init;
     OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
     int k_mixed = 0;
-    if (h->opt.precision == OMM_PREC_MIXED) {
+    if (h->sparse) {
+        { StageTimer t(h, OMM_STAGE_START); TRY(sparse_start(h)); }
+        h->have_W = true;
+        TRY(run_until_done(h, [&] { return sparse_iteration(h); }));
+    } else if (h->opt.precision == OMM_PREC_MIXED) {
         // phase 1: split-precision CG to a tolerance a decade below the target
         omm::DevState ph = init;
         ph.tol = fmax(0.1 * tol, 1e-12);
@@ -746,7 +847,7 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
     }
     OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
     if (W_out != nullptr)
-        OMM_CUDA_TRY(cudaMemcpyAsync(W_out, h->WD, mn * sizeof(double),
+        OMM_CUDA_TRY(cudaMemcpyAsync(W_out, Wdev, wlen * sizeof(double),
                                      W_out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
     const omm::DevState &s = *h->hstate;
@@ -776,6 +877,26 @@ int omm_get_diag(omm_handle *h, omm_diag *d) {
 
 int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device) {
     if (h == nullptr || dst == nullptr) return OMM_ERR_ARG;
+    if (h->sparse) {
+        const omm::sp::Dev &d = h->sd;
+        const int64_t bw = (int64_t)d.bm * d.bn, bq = (int64_t)d.bn * d.bn;
+        const double *src = nullptr;
+        int64_t len = 0;
+        switch (which) {
+            case 0: src = d.W; len = d.nnzW * bw; break;
+            case 1: src = d.HW; len = d.nnzHW * bw; break;
+            case 2: src = d.SW; len = d.nnzHW * bw; break;
+            case 3: src = d.G; len = d.nnzW * bw; break;
+            case 4: src = d.D; len = d.nnzW * bw; break;
+            case 5: src = d.h0; len = d.nnzN * bq; break;
+            case 6: src = d.s0; len = d.nnzN * bq; break;
+            default: return OMM_ERR_ARG;
+        }
+        OMM_CUDA_TRY(cudaMemcpyAsync(dst, src, len * sizeof(double),
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+        OMM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        return OMM_OK;
+    }
     const int64_t m = h->m, n = h->n, mn = m * n;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaStream_t st = h->stream;
@@ -798,6 +919,41 @@ int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device) 
 }
 
 void omm_destroy(omm_handle *h) { free_handle(h); }
+
+int omm_get_pattern(omm_handle *h, int32_t which, int64_t *rowptr, int32_t *col) {
+    if (h == nullptr || !h->sparse || rowptr == nullptr || col == nullptr) return OMM_ERR_ARG;
+    const omm::sp::Host &hs = h->sh;
+    const int64_t nbr = hs.P.nbr;
+    switch (which) {
+        case OMM_PATTERN_H: {
+            if (!h->have_HS) return OMM_ERR_STATE;
+            std::vector<unsigned char> keep((size_t)h->sd.nnzH);
+            OMM_CUDA_TRY(cudaMemcpy(keep.data(), h->sd.keep, keep.size(), cudaMemcpyDeviceToHost));
+            int64_t k = 0;
+            rowptr[0] = 0;
+            for (int64_t I = 0; I < nbr; ++I) {
+                for (int64_t b = hs.Hrp[I]; b < hs.Hrp[I + 1]; ++b)
+                    if (keep[b]) col[k++] = hs.Hcol[b];
+                rowptr[I + 1] = k;
+            }
+            return OMM_OK;
+        }
+        case OMM_PATTERN_W:
+            std::copy(hs.Wrp.begin(), hs.Wrp.end(), rowptr);
+            std::copy(hs.Wcol.begin(), hs.Wcol.end(), col);
+            return OMM_OK;
+        case OMM_PATTERN_HW:
+            std::copy(hs.HWrp.begin(), hs.HWrp.end(), rowptr);
+            std::copy(hs.HWcol.begin(), hs.HWcol.end(), col);
+            return OMM_OK;
+        case OMM_PATTERN_N:
+            std::copy(hs.Nrp.begin(), hs.Nrp.end(), rowptr);
+            std::copy(hs.Ncol.begin(), hs.Ncol.end(), col);
+            return OMM_OK;
+        default:
+            return OMM_ERR_ARG;
+    }
+}
 
 int omm_set_profiling(omm_handle *h, int32_t on) {
     if (h == nullptr) return OMM_ERR_ARG;

@@ -1,0 +1,930 @@
+// Linear-scaling (block-sparse) form of the OMM CG step.
+//
+// H and S share one block pattern P_H of bm x bm blocks; W (and D, G) live on
+// the localisation pattern P_W of bm x bn blocks, fixed for the whole
+// minimisation, and the gradient is kept on it (section "Solver library").
+// The products live on structural patterns built once on the host:
+//   P_HW = P_H . P_W            (H'W, SW, H'D, SD; contains P_W)
+//   P_N  = P_W^T . P_HW         (H_W, S_W, X, Y, h2, s2; symmetric)
+// Every output block is a gather over a precomputed list of operand-block
+// pairs, summed in list order: no atomics, bitwise repeatable results.
+//
+// Device storage (FP64, blocks row-major, in pattern order):
+//   HS   [nnzH][2][bm*bm]   H' and S block k side by side
+//   W, D, G, Gp  [nnzW][bm*bn]
+//   HW, SW, HD, SD [nnzHW][bm*bn]
+//   h0, s0, X, Y, h2, s2  [nnzN][bn*bn]
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "omm_internal.cuh"
+#include "sparse.cuh"
+
+namespace omm {
+namespace sp {
+
+// ======================================================================== host: patterns
+namespace {
+
+// union of the W rows K over K in P_H(I, :): row I of P_HW
+void build_hw(const Pattern &P, std::vector<int64_t> &rp, std::vector<int32_t> &col) {
+    const int64_t nbr = P.nbr;
+    rp.assign(nbr + 1, 0);
+    col.clear();
+    std::vector<int32_t> mark(P.nbc, -1);
+    std::vector<int32_t> row;
+    for (int64_t I = 0; I < nbr; ++I) {
+        row.clear();
+        for (int64_t h = P.Hrp[I]; h < P.Hrp[I + 1]; ++h) {
+            const int32_t K = P.Hcol[h];
+            for (int64_t w = P.Wrp[K]; w < P.Wrp[K + 1]; ++w) {
+                const int32_t J = P.Wcol[w];
+                if (mark[J] != (int32_t)I) {
+                    mark[J] = (int32_t)I;
+                    row.push_back(J);
+                }
+            }
+        }
+        std::sort(row.begin(), row.end());
+        col.insert(col.end(), row.begin(), row.end());
+        rp[I + 1] = (int64_t)col.size();
+    }
+}
+
+// P_N = P_W^T P_HW via one bitset row per W block column
+void build_n(const Pattern &P, const std::vector<int64_t> &hwrp, const std::vector<int32_t> &hwcol,
+             std::vector<int64_t> &rp, std::vector<int32_t> &col) {
+    const int64_t nbc = P.nbc, words = (nbc + 63) / 64;
+    std::vector<uint64_t> bits((size_t)(nbc * words), 0ull);
+    std::vector<uint64_t> rowbits((size_t)words);
+    for (int64_t I = 0; I < P.nbr; ++I) {
+        std::fill(rowbits.begin(), rowbits.end(), 0ull);
+        for (int64_t b = hwrp[I]; b < hwrp[I + 1]; ++b) rowbits[hwcol[b] >> 6] |= 1ull << (hwcol[b] & 63);
+        for (int64_t a = P.Wrp[I]; a < P.Wrp[I + 1]; ++a) {
+            uint64_t *dst = &bits[(size_t)P.Wcol[a] * words];
+            for (int64_t q = 0; q < words; ++q) dst[q] |= rowbits[q];
+        }
+    }
+    rp.assign(nbc + 1, 0);
+    col.clear();
+    for (int64_t J = 0; J < nbc; ++J) {
+        const uint64_t *src = &bits[(size_t)J * words];
+        for (int64_t q = 0; q < words; ++q) {
+            uint64_t v = src[q];
+            while (v) {
+                const int t = __builtin_ctzll(v);
+                col.push_back((int32_t)(q * 64 + t));
+                v &= v - 1;
+            }
+        }
+        rp[J + 1] = (int64_t)col.size();
+    }
+}
+
+}  // namespace
+
+int build(const Pattern &P, Host &out) {
+    // ---- validate
+    if (P.nbr <= 0 || P.nbc <= 0 || P.bm <= 0 || P.bn <= 0) return OMM_ERR_PATTERN;
+    for (int which = 0; which < 2; ++which) {
+        const int64_t *rp = which ? P.Wrp : P.Hrp;
+        const int32_t *c = which ? P.Wcol : P.Hcol;
+        const int64_t ncol = which ? P.nbc : P.nbr;
+        if (rp[0] != 0) return OMM_ERR_PATTERN;
+        for (int64_t I = 0; I < P.nbr; ++I) {
+            if (rp[I + 1] < rp[I]) return OMM_ERR_PATTERN;
+            for (int64_t k = rp[I]; k < rp[I + 1]; ++k) {
+                if (c[k] < 0 || c[k] >= ncol) return OMM_ERR_PATTERN;
+                if (k > rp[I] && c[k] <= c[k - 1]) return OMM_ERR_PATTERN;   // sorted, unique
+            }
+        }
+    }
+    // H must hold its diagonal blocks and be structurally symmetric
+    for (int64_t I = 0; I < P.nbr; ++I) {
+        const int32_t *b = P.Hcol + P.Hrp[I], *e = P.Hcol + P.Hrp[I + 1];
+        if (!std::binary_search(b, e, (int32_t)I)) return OMM_ERR_PATTERN;
+        for (const int32_t *k = b; k < e; ++k) {
+            const int32_t *b2 = P.Hcol + P.Hrp[*k], *e2 = P.Hcol + P.Hrp[*k + 1];
+            if (!std::binary_search(b2, e2, (int32_t)I)) return OMM_ERR_PATTERN;
+        }
+    }
+    out.P = P;
+    out.Hrp.assign(P.Hrp, P.Hrp + P.nbr + 1);
+    out.Hcol.assign(P.Hcol, P.Hcol + P.Hrp[P.nbr]);
+    out.Wrp.assign(P.Wrp, P.Wrp + P.nbr + 1);
+    out.Wcol.assign(P.Wcol, P.Wcol + P.Wrp[P.nbr]);
+    out.P.Hrp = out.Hrp.data();
+    out.P.Hcol = out.Hcol.data();
+    out.P.Wrp = out.Wrp.data();
+    out.P.Wcol = out.Wcol.data();
+    const Pattern &Q = out.P;
+    build_hw(Q, out.HWrp, out.HWcol);
+    build_n(Q, out.HWrp, out.HWcol, out.Nrp, out.Ncol);
+    const int64_t nnzH = Q.Hrp[Q.nbr], nnzW = Q.Wrp[Q.nbr];
+    const int64_t nnzHW = out.HWrp[Q.nbr], nnzN = out.Nrp[Q.nbc];
+
+    // ---- transpose of P_N (symmetric pattern): index of (J2, J1) for each (J1, J2)
+    out.Ntr.assign(nnzN, -1);
+    out.Ndiag.assign(nnzN, 0);
+    for (int64_t J = 0; J < Q.nbc; ++J)
+        for (int64_t q = out.Nrp[J]; q < out.Nrp[J + 1]; ++q) {
+            const int32_t J2 = out.Ncol[q];
+            const int32_t *b = out.Ncol.data() + out.Nrp[J2], *e = out.Ncol.data() + out.Nrp[J2 + 1];
+            const int32_t *f = std::lower_bound(b, e, (int32_t)J);
+            if (f == e || *f != (int32_t)J) return OMM_ERR_PATTERN;
+            out.Ntr[q] = (int32_t)(f - out.Ncol.data());
+            out.Ndiag[q] = (J2 == J) ? 1 : 0;
+        }
+    // ---- W block -> its position inside P_HW
+    out.WtoHW.assign(nnzW, -1);
+    for (int64_t I = 0; I < Q.nbr; ++I)
+        for (int64_t a = Q.Wrp[I]; a < Q.Wrp[I + 1]; ++a) {
+            const int32_t *b = out.HWcol.data() + out.HWrp[I], *e = out.HWcol.data() + out.HWrp[I + 1];
+            const int32_t *f = std::lower_bound(b, e, Q.Wcol[a]);
+            out.WtoHW[a] = (int32_t)(f - out.HWcol.data());
+        }
+    // ---- product lists: HW block o = (I, J) <- (H block (I, K), W block (K, J)), K ascending
+    {
+        std::vector<int32_t> pos(Q.nbc, -1);
+        out.Prp.assign(nnzHW + 1, 0);
+        for (int pass = 0; pass < 2; ++pass) {
+            std::vector<int64_t> fill;
+            if (pass == 1) {
+                for (int64_t o = 0; o < nnzHW; ++o) out.Prp[o + 1] += out.Prp[o];
+                out.Ph.resize(out.Prp[nnzHW]);
+                out.Pw.resize(out.Prp[nnzHW]);
+                fill.assign(out.Prp.begin(), out.Prp.end() - 1);
+            }
+            for (int64_t I = 0; I < Q.nbr; ++I) {
+                for (int64_t o = out.HWrp[I]; o < out.HWrp[I + 1]; ++o) pos[out.HWcol[o]] = (int32_t)o;
+                for (int64_t h = Q.Hrp[I]; h < Q.Hrp[I + 1]; ++h) {
+                    const int32_t K = Q.Hcol[h];
+                    for (int64_t w = Q.Wrp[K]; w < Q.Wrp[K + 1]; ++w) {
+                        const int32_t o = pos[Q.Wcol[w]];
+                        if (pass == 0) {
+                            out.Prp[o + 1] += 1;
+                        } else {
+                            out.Ph[fill[o]] = (int32_t)h;
+                            out.Pw[fill[o]] = (int32_t)w;
+                            ++fill[o];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // ---- contraction lists: N block q = (J1, J2) <- (W block (I, J1), HW block (I, J2)), I ascending
+    {
+        // W blocks by column: (I, a) pairs with Wcol[a] = J, I ascending
+        std::vector<int64_t> crp(Q.nbc + 1, 0);
+        for (int64_t a = 0; a < nnzW; ++a) crp[Q.Wcol[a] + 1] += 1;
+        for (int64_t J = 0; J < Q.nbc; ++J) crp[J + 1] += crp[J];
+        std::vector<int64_t> cidx(nnzW), cfill(crp.begin(), crp.end() - 1);
+        std::vector<int32_t> crow(nnzW);
+        for (int64_t I = 0; I < Q.nbr; ++I)
+            for (int64_t a = Q.Wrp[I]; a < Q.Wrp[I + 1]; ++a) {
+                cidx[cfill[Q.Wcol[a]]] = a;
+                crow[cfill[Q.Wcol[a]]++] = (int32_t)I;
+            }
+        out.WcolRp = crp;
+        out.WcolIdx = cidx;
+        std::vector<int32_t> pos(Q.nbc, -1);
+        out.Crp.assign(nnzN + 1, 0);
+        for (int pass = 0; pass < 2; ++pass) {
+            std::vector<int64_t> fill;
+            if (pass == 1) {
+                for (int64_t q = 0; q < nnzN; ++q) out.Crp[q + 1] += out.Crp[q];
+                out.Ca.resize(out.Crp[nnzN]);
+                out.Cb.resize(out.Crp[nnzN]);
+                fill.assign(out.Crp.begin(), out.Crp.end() - 1);
+            }
+            for (int64_t J1 = 0; J1 < Q.nbc; ++J1) {
+                for (int64_t q = out.Nrp[J1]; q < out.Nrp[J1 + 1]; ++q) pos[out.Ncol[q]] = (int32_t)q;
+                for (int64_t c = crp[J1]; c < crp[J1 + 1]; ++c) {
+                    const int64_t a = cidx[c];
+                    const int32_t I = crow[c];
+                    for (int64_t b = out.HWrp[I]; b < out.HWrp[I + 1]; ++b) {
+                        const int32_t q = pos[out.HWcol[b]];
+                        if (pass == 0) {
+                            out.Crp[q + 1] += 1;
+                        } else {
+                            out.Ca[fill[q]] = (int32_t)a;
+                            out.Cb[fill[q]] = (int32_t)b;
+                            ++fill[q];
+                        }
+                    }
+                }
+                for (int64_t q = out.Nrp[J1]; q < out.Nrp[J1 + 1]; ++q) pos[out.Ncol[q]] = -1;
+            }
+        }
+    }
+    // ---- gradient lists: W block o = (I, J) <- (HW block (I, K), N block (K, J)), K ascending
+    {
+        std::vector<int32_t> posJ(Q.nbc, -1);
+        out.Grp.assign(nnzW + 1, 0);
+        for (int pass = 0; pass < 2; ++pass) {
+            std::vector<int64_t> fill;
+            if (pass == 1) {
+                for (int64_t o = 0; o < nnzW; ++o) out.Grp[o + 1] += out.Grp[o];
+                out.Gb.resize(out.Grp[nnzW]);
+                out.Gq.resize(out.Grp[nnzW]);
+                fill.assign(out.Grp.begin(), out.Grp.end() - 1);
+            }
+            for (int64_t J = 0; J < Q.nbc; ++J) {
+                // row J of P_N: posJ[K] = index of (J, K); (K, J) is its transpose
+                for (int64_t q = out.Nrp[J]; q < out.Nrp[J + 1]; ++q) posJ[out.Ncol[q]] = (int32_t)q;
+                for (int64_t c = out.WcolRp[J]; c < out.WcolRp[J + 1]; ++c) {
+                    const int64_t o = out.WcolIdx[c];
+                    int64_t I = 0;
+                    {   // row of W block o
+                        const int64_t *f = std::upper_bound(out.Wrp.data(), out.Wrp.data() + Q.nbr + 1, o);
+                        I = (f - out.Wrp.data()) - 1;
+                    }
+                    for (int64_t b = out.HWrp[I]; b < out.HWrp[I + 1]; ++b) {
+                        const int32_t qJK = posJ[out.HWcol[b]];
+                        if (qJK < 0) continue;
+                        if (pass == 0) {
+                            out.Grp[o + 1] += 1;
+                        } else {
+                            out.Gb[fill[o]] = (int32_t)b;
+                            out.Gq[fill[o]] = out.Ntr[qJK];
+                            ++fill[o];
+                        }
+                    }
+                }
+                for (int64_t q = out.Nrp[J]; q < out.Nrp[J + 1]; ++q) posJ[out.Ncol[q]] = -1;
+            }
+        }
+    }
+    (void)nnzH;
+    return OMM_OK;
+}
+
+// ======================================================================== device kernels
+namespace {
+
+constexpr int NT = 256;
+
+// Block sum / last-block combination (fixed order; same scheme as the dense kernels)
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *red) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = v[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        v[q] = s;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[warp * NV + q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += red[w * NV + q];
+            v[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <int NV>
+__device__ bool publish_and_collect(const double (&v)[NV], double *partials, unsigned int *counter,
+                                    double (&tot)[NV], double *red) {
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) partials[blockIdx.x * NV + q] = v[q];
+        __threadfence();
+        is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double w[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) w[q] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += NT)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) w[q] += __ldcg(&partials[b * NV + q]);
+    block_sum<NV>(w, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) tot[q] = w[q];
+        *counter = 0u;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool done(const DevState *s) { return s != nullptr && *((volatile const int *)&s->done); }
+
+// ---- block filtering: keep[b] = ||H_b||^2 >= eps^2 or ||S_b||^2 >= eps^2, squares
+// summed in row-major element order with one rounded product and add each.
+__global__ void filter_kernel(int64_t nnzH, int bb, const double *H, const double *S, double eps2,
+                              unsigned char *keep) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nnzH; b += (int64_t)gridDim.x * blockDim.x) {
+        double sh = 0.0, ss = 0.0;
+        for (int t = 0; t < bb; ++t) {
+            sh = __dadd_rn(sh, __dmul_rn(H[b * bb + t], H[b * bb + t]));
+            ss = __dadd_rn(ss, __dmul_rn(S[b * bb + t], S[b * bb + t]));
+        }
+        keep[b] = !(sh < eps2) || !(ss < eps2);
+    }
+}
+
+// HS[b] = (keep ? H_b - eta S_b : 0, keep ? S_b : 0)
+__global__ void shift_pack_kernel(int64_t nnzH, int bb, const double *H, const double *S,
+                                  const unsigned char *keep, const DevState *state, double *HS) {
+    const double eta = state->eta;
+    const int64_t total = nnzH * bb;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = t / bb;
+        const int e = (int)(t - b * bb);
+        const bool k = keep[b] != 0;
+        const double s = k ? S[t] : 0.0;
+        HS[(b * 2) * bb + e] = k ? H[t] - eta * s : 0.0;
+        HS[(b * 2 + 1) * bb + e] = s;
+    }
+}
+
+// Gershgorin bound over the block rows: thread per matrix row
+__global__ void __launch_bounds__(NT) gershgorin_kernel(int64_t nbr, int bm, const int64_t *Hrp, const int32_t *Hcol,
+                                                         const double *H, const double *S, double *partials,
+                                                         unsigned int *counter, DevState *state) {
+    __shared__ double red[(NT / 32) * 3];
+    double gmax = -INFINITY, lomin = INFINITY, himax = -INFINITY;
+    const int64_t nrows = nbr * bm;
+    for (int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x; row < nrows; row += (int64_t)gridDim.x * NT) {
+        const int64_t I = row / bm;
+        const int r = (int)(row - I * bm);
+        double sh = 0.0, ss = 0.0, dh = 0.0, ds = 0.0;
+        for (int64_t b = Hrp[I]; b < Hrp[I + 1]; ++b) {
+            const bool diag = Hcol[b] == (int32_t)I;
+            for (int c = 0; c < bm; ++c) {
+                const double vh = H[(b * bm + r) * bm + c], vs = S[(b * bm + r) * bm + c];
+                if (diag && c == r) { dh = vh; ds = vs; }
+                else { sh += fabs(vh); ss += fabs(vs); }
+            }
+        }
+        gmax = fmax(gmax, dh + sh);
+        lomin = fmin(lomin, ds - ss);
+        himax = fmax(himax, ds + ss);
+    }
+    // block max/min then last-block combination (order-independent)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        gmax = fmax(gmax, __shfl_down_sync(0xffffffffu, gmax, off));
+        lomin = fmin(lomin, __shfl_down_sync(0xffffffffu, lomin, off));
+        himax = fmax(himax, __shfl_down_sync(0xffffffffu, himax, off));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { red[w * 3] = gmax; red[w * 3 + 1] = lomin; red[w * 3 + 2] = himax; }
+    __syncthreads();
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) {
+        double v0 = -INFINITY, v1 = INFINITY, v2 = -INFINITY;
+        for (int q = 0; q < NT / 32; ++q) {
+            v0 = fmax(v0, red[q * 3]);
+            v1 = fmin(v1, red[q * 3 + 1]);
+            v2 = fmax(v2, red[q * 3 + 2]);
+        }
+        partials[blockIdx.x * 3] = v0;
+        partials[blockIdx.x * 3 + 1] = v1;
+        partials[blockIdx.x * 3 + 2] = v2;
+        __threadfence();
+        is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last || threadIdx.x != 0) return;
+    __threadfence();
+    double g = -INFINITY, lo = INFINITY, hi = -INFINITY;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+        g = fmax(g, __ldcg(&partials[b * 3]));
+        lo = fmin(lo, __ldcg(&partials[b * 3 + 1]));
+        hi = fmax(hi, __ldcg(&partials[b * 3 + 2]));
+    }
+    *counter = 0u;
+    if (!(lo > 0.0)) {
+        state->status = OMM_ERR_NOT_SPD;
+        state->eta = NAN;
+        return;
+    }
+    state->eta = (g >= 0.0) ? g / lo : g / hi;
+}
+
+// ---- products: HD_o = sum H'_(I,K) D_(K,J), SD_o likewise; warp per P_HW block,
+// lanes 0..15 -> H'D element (r, c), lanes 16..31 -> SD element.
+template <int BM, int BN>
+__global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64_t *__restrict__ Prp,
+                                                       const int32_t *__restrict__ Ph, const int32_t *__restrict__ Pw,
+                                                       const double *__restrict__ HS, const double *__restrict__ D,
+                                                       double *HD, double *SD, const DevState *state) {
+    if (done(state)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    if (o >= nnzHW) return;
+    constexpr int NE = BM * BN;          // outputs per block
+    const int which = lane / 16, e = lane % 16;   // which: 0 = H', 1 = S
+    const bool active = e < NE;
+    const int r = e / BN, c = e % BN;
+    double acc = 0.0;
+    for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
+        const double *A = HS + ((int64_t)Ph[t] * 2 + which) * BM * BM + r * BM;
+        const double *B = D + (int64_t)Pw[t] * BM * BN + c;
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < BM; ++k) acc = fma(A[k], B[k * BN], acc);
+        }
+    }
+    if (active) (which ? SD : HD)[o * NE + e] = acc;
+}
+
+// ---- contractions on P_N: warp per N block q; 16 outputs (X, Y, h2, s2 of 2x2)
+// with two lanes each splitting the basis index k.
+template <int BM, int BN>
+__global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_t *__restrict__ Crp,
+                                                       const int32_t *__restrict__ Ca, const int32_t *__restrict__ Cb,
+                                                       const double *__restrict__ W, const double *__restrict__ D,
+                                                       const double *__restrict__ HD, const double *__restrict__ SD,
+                                                       double *X, double *Y, double *h2, double *s2,
+                                                       const DevState *state) {
+    if (done(state)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t q = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    if (q >= nnzN) return;
+    static_assert(BN == 2, "contraction lanes assume 2 orbitals per W block");
+    const int v = lane >> 1, half = lane & 1;
+    const int mat = v >> 2, a = (v >> 1) & 1, b = v & 1;   // mat: 0 X, 1 Y, 2 h2, 3 s2
+    const double *L = (mat < 2) ? W : D;
+    const double *R = (mat == 0 || mat == 2) ? HD : SD;
+    double acc = 0.0;
+    for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
+        const double *l = L + (int64_t)Ca[t] * BM * BN + a;
+        const double *rr = R + (int64_t)Cb[t] * BM * BN + b;
+#pragma unroll
+        for (int kk = 0; kk < BM / 2; ++kk) {
+            const int k = half * (BM / 2) + kk;
+            acc = fma(l[k * BN], rr[k * BN], acc);
+        }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (half == 0) {
+        double *out = mat == 0 ? X : mat == 1 ? Y : mat == 2 ? h2 : s2;
+        out[q * 4 + a * 2 + b] = acc;
+    }
+}
+
+// ---- gradient on P_W: G_o = 2 (2 H'W_o - sum (SW_(I,K) h0_(K,J) + H'W_(I,K) s0_(K,J)))
+// half-warp per W block, one lane per element (r, c).
+template <int BM, int BN>
+__global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_t *__restrict__ Grp,
+                                                       const int32_t *__restrict__ Gb, const int32_t *__restrict__ Gq,
+                                                       const int32_t *__restrict__ WtoHW, const double *__restrict__ HW,
+                                                       const double *__restrict__ SW, const double *__restrict__ h0,
+                                                       const double *__restrict__ s0, double *G,
+                                                       const DevState *state) {
+    if (done(state)) return;
+    const int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 4;
+    const int e = threadIdx.x & 15;
+    if (o >= nnzW || e >= BM * BN) return;
+    const int r = e / BN, c = e % BN;
+    double acc = 0.0;
+    for (int64_t t = Grp[o]; t < Grp[o + 1]; ++t) {
+        const double *sw = SW + (int64_t)Gb[t] * BM * BN + r * BN;
+        const double *hw = HW + (int64_t)Gb[t] * BM * BN + r * BN;
+        const double *hq = h0 + (int64_t)Gq[t] * BN * BN + c;
+        const double *sq = s0 + (int64_t)Gq[t] * BN * BN + c;
+#pragma unroll
+        for (int k = 0; k < BN; ++k) {
+            acc = fma(sw[k], hq[k * BN], acc);
+            acc = fma(hw[k], sq[k * BN], acc);
+        }
+    }
+    G[o * BM * BN + e] = 2.0 * (2.0 * HW[(int64_t)WtoHW[o] * BM * BN + e] - acc);
+}
+
+// ---- quartic coefficients and line minimum on P_N (2x2 blocks)
+constexpr int NC = 13;
+__device__ int quartic_min(const double *c, double *xout);
+
+__global__ void __launch_bounds__(NT) coeffs_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr,
+                                                     const unsigned char *__restrict__ Ndiag,
+                                                     const double *__restrict__ h0, const double *__restrict__ s0,
+                                                     const double *__restrict__ X, const double *__restrict__ Y,
+                                                     const double *__restrict__ h2, const double *__restrict__ s2,
+                                                     double *partials, unsigned int *counter, DevState *state) {
+    if (done(state)) return;
+    __shared__ double red[(NT / 32) * NC];
+    double v[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) v[q] = 0.0;
+    const int64_t total = nnzN * 4;
+    for (int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x; t < total; t += (int64_t)gridDim.x * NT) {
+        const int64_t q = t >> 2;
+        const int e = (int)(t & 3), a = e >> 1, b = e & 1;
+        const int64_t tt = (int64_t)Ntr[q] * 4 + b * 2 + a;   // transposed element
+        const double vh0 = h0[t], vs0 = s0[t], vx = X[t], vy = Y[t], vh2 = h2[t], vs2 = s2[t];
+        if (Ndiag[q] && a == b) { v[0] += vh0; v[2] += vx; v[5] += vh2; }
+        v[1] = fma(vs0, vh0, v[1]);
+        v[3] = fma(vs0, vx, v[3]);
+        v[4] = fma(vy, vh0, v[4]);
+        v[6] = fma(vs0, vh2, v[6]);
+        v[7] = fma(vy, vx, v[7]);
+        v[8] = fma(vy, X[tt], v[8]);
+        v[9] = fma(vs2, vh0, v[9]);
+        v[10] = fma(vy, vh2, v[10]);
+        v[11] = fma(vs2, vx, v[11]);
+        v[12] = fma(vs2, vh2, v[12]);
+    }
+    block_sum<NC>(v, red);
+    double tot[NC];
+    if (!publish_and_collect<NC>(v, partials, counter, tot, red)) return;
+    if (threadIdx.x != 0) return;
+    double c[5];
+    c[0] = 2.0 * (2.0 * tot[0] - tot[1]);
+    c[1] = 2.0 * (4.0 * tot[2] - 2.0 * tot[3] - 2.0 * tot[4]);
+    c[2] = 2.0 * (2.0 * tot[5] - tot[6] - 2.0 * (tot[7] + tot[8]) - tot[9]);
+    c[3] = 2.0 * (-2.0 * tot[10] - 2.0 * tot[11]);
+    c[4] = -2.0 * tot[12];
+    for (int q = 0; q < 5; ++q) state->c[q] = c[q];
+    double x = 0.0;
+    const int st = quartic_min(c, &x);
+    state->x = x;
+    if (st != OMM_OK) {
+        state->status = st;
+        state->done = 1;
+    }
+}
+
+// ---- h0, s0 update on P_N + energy/orthonormality + RelTol test (mode 0), or
+// energy only (mode 1, start)
+constexpr int NE3 = 3;
+__global__ void __launch_bounds__(NT) nn_update_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr,
+                                                        const unsigned char *__restrict__ Ndiag, double *h0, double *s0,
+                                                        const double *__restrict__ X, const double *__restrict__ Y,
+                                                        const double *__restrict__ h2, const double *__restrict__ s2,
+                                                        int64_t n, double *partials, unsigned int *counter,
+                                                        DevState *state, int mode) {
+    if (done(state)) return;
+    __shared__ double red[(NT / 32) * NE3];
+    const double x = state->x;
+    double v[NE3] = {0.0, 0.0, 0.0};
+    const int64_t total = nnzN * 4;
+    for (int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x; t < total; t += (int64_t)gridDim.x * NT) {
+        const int64_t q = t >> 2;
+        const int e = (int)(t & 3), a = e >> 1, b = e & 1;
+        const int64_t tt = (int64_t)Ntr[q] * 4 + b * 2 + a;
+        double vh = h0[t], vs = s0[t];
+        if (mode == 0) {
+            vh = vh + x * ((X[t] + X[tt]) + x * (0.5 * (h2[t] + h2[tt])));
+            vs = vs + x * ((Y[t] + Y[tt]) + x * (0.5 * (s2[t] + s2[tt])));
+            h0[t] = vh;
+            s0[t] = vs;
+        }
+        const bool dg = Ndiag[q] && a == b;
+        if (dg) v[0] += vh;
+        v[1] = fma(vs, vh, v[1]);
+        const double ee = vs - (dg ? 1.0 : 0.0);
+        v[2] = fma(ee, ee, v[2]);
+    }
+    block_sum<NE3>(v, red);
+    double tot[NE3];
+    if (!publish_and_collect<NE3>(v, partials, counter, tot, red)) return;
+    if (threadIdx.x != 0) return;
+    const double E = 2.0 * (2.0 * tot[0] - tot[1]) + 2.0 * state->eta * (double)n;
+    state->orth2 = tot[2];
+    if (!isfinite(E)) {
+        state->status = OMM_ERR_NONFINITE;
+        state->done = 1;
+        state->E = E;
+        return;
+    }
+    if (mode == 1) {
+        state->E = E;
+        state->E_prev = E;
+        state->rel = 0.0;
+        if (state->max_iter <= 0) {
+            state->status = OMM_ERR_MAXITER;
+            state->done = 1;
+        }
+        return;
+    }
+    const double Ep = state->E;
+    const double rel = fabs(2.0 * (E - Ep) / (E + Ep));
+    state->E_prev = Ep;
+    state->E = E;
+    state->rel = rel;
+    state->k += 1;
+    const bool orth_ok = !(state->orth_tol > 0.0) || sqrt(tot[2]) < state->orth_tol;
+    if (rel < state->tol && orth_ok) {
+        state->status = OMM_OK;
+        state->done = 1;
+    } else if (state->k >= state->max_iter) {
+        state->status = OMM_ERR_MAXITER;
+        state->done = 1;
+    }
+}
+
+// ---- W += x D on P_W; H'W += x H'D, SW += x SD on P_HW
+__global__ void axpy_kernel(int64_t nW, double *W, const double *__restrict__ D, int64_t nHW, double *HW,
+                            const double *__restrict__ HD, double *SW, const double *__restrict__ SD,
+                            const DevState *state) {
+    if (done(state)) return;
+    const double x = state->x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nHW; i += (int64_t)gridDim.x * blockDim.x) {
+        HW[i] = fma(x, HD[i], HW[i]);
+        SW[i] = fma(x, SD[i], SW[i]);
+        if (i < nW) W[i] = fma(x, D[i], W[i]);
+    }
+}
+
+constexpr int ND = 3;
+__global__ void __launch_bounds__(NT) dots_kernel(int64_t len, const double *__restrict__ G,
+                                                   const double *__restrict__ Gp, const double *__restrict__ D,
+                                                   double *partials, unsigned int *counter, DevState *state, int first) {
+    if (done(state)) return;
+    __shared__ double red[(NT / 32) * ND];
+    double v[ND] = {0.0, 0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < len; i += (int64_t)gridDim.x * NT) {
+        const double g = G[i];
+        v[0] = fma(g, g, v[0]);
+        if (!first) {
+            v[1] = fma(g, Gp[i], v[1]);
+            v[2] = fma(g, D[i], v[2]);
+        }
+    }
+    block_sum<ND>(v, red);
+    double tot[ND];
+    if (!publish_and_collect<ND>(v, partials, counter, tot, red)) return;
+    if (threadIdx.x != 0) return;
+    const double gg = tot[0];
+    double beta = 0.0;
+    int restart = 1;
+    if (!first) {
+        const double gpgp = state->gg_prev;
+        beta = (gpgp > 0.0) ? fmax(0.0, (gg - tot[1]) / gpgp) : 0.0;
+        restart = (-gg + beta * tot[2] >= 0.0) ? 1 : 0;
+        if (restart) beta = 0.0;
+    }
+    if (!isfinite(gg) || !isfinite(beta)) {
+        state->status = OMM_ERR_NONFINITE;
+        state->done = 1;
+        return;
+    }
+    state->gg = gg;
+    state->gg_prev = gg;
+    state->beta = beta;
+    state->restart = restart;
+}
+
+__global__ void direction_kernel(int64_t len, const double *__restrict__ G, double *Gp, double *D,
+                                 const DevState *state) {
+    if (done(state)) return;
+    const double beta = state->beta;
+    const bool restart = state->restart != 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        const double g = G[i];
+        D[i] = restart ? -g : fma(beta, D[i], -g);
+        Gp[i] = g;
+    }
+}
+
+// ---- line minimum (same rule as the dense form)
+__device__ double qval(const double *c, double x) { return c[0] + x * (c[1] + x * (c[2] + x * (c[3] + x * c[4]))); }
+
+__device__ int cubic_roots(double a, double b, double c, double d, double *r) {
+    auto f = [&](double x) { return ((a * x + b) * x + c) * x + d; };
+    auto fp = [&](double x) { return (3.0 * a * x + 2.0 * b) * x + c; };
+    const double R = 1.0 + fmax(fabs(b), fmax(fabs(c), fabs(d))) / a;
+    double lo = -R, hi = R, x = 0.0;
+    for (int it = 0; it < 400; ++it) {
+        const double fx = f(x);
+        if (fx == 0.0) break;
+        if (fx < 0.0) lo = x; else hi = x;
+        const double dx = fp(x);
+        double xn = (dx != 0.0) ? x - fx / dx : 0.5 * (lo + hi);
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (xn == x || hi - lo <= 4e-16 * fmax(1.0, fabs(x))) { x = xn; break; }
+        x = xn;
+    }
+    int nr = 0;
+    r[nr++] = x;
+    const double p = b + a * x, q = c + p * x;
+    const double disc = p * p - 4.0 * a * q;
+    if (disc >= 0.0) {
+        const double sq = sqrt(disc);
+        const double t = -0.5 * (p + (p >= 0.0 ? sq : -sq));
+        if (t != 0.0) { r[nr++] = t / a; r[nr++] = q / t; } else { r[nr++] = 0.0; }
+    }
+    for (int i = 0; i < nr; ++i)
+        for (int it = 0; it < 3; ++it) {
+            const double dx = fp(r[i]);
+            if (dx == 0.0) break;
+            const double xn = r[i] - f(r[i]) / dx;
+            if (!isfinite(xn)) break;
+            if (fabs(f(xn)) <= fabs(f(r[i]))) r[i] = xn; else break;
+        }
+    return nr;
+}
+
+__device__ int quartic_min(const double *c, double *xout) {
+    for (int i = 0; i < 5; ++i)
+        if (!isfinite(c[i])) return OMM_ERR_NONFINITE;
+    if (c[4] == 0.0 && c[3] == 0.0) {
+        if (c[2] > 0.0) { *xout = -c[1] / (2.0 * c[2]); return OMM_OK; }
+        return OMM_ERR_LINESEARCH;
+    }
+    if (c[4] < 0.0) return OMM_ERR_LINESEARCH;
+    double r[3];
+    int nr = 0;
+    if (c[4] > 0.0) {
+        nr = cubic_roots(4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1], r);
+    } else {
+        const double a = 3.0 * c[3], b = 2.0 * c[2], cc = c[1];
+        const double disc = b * b - 4.0 * a * cc;
+        if (disc >= 0.0) {
+            const double sq = sqrt(disc);
+            const double t = -0.5 * (b + (b >= 0.0 ? sq : -sq));
+            if (t != 0.0) { r[nr++] = t / a; r[nr++] = cc / t; }
+        }
+    }
+    bool have = false;
+    double best = 0.0, bestv = 0.0;
+    for (int pass = 0; pass < 2 && !have; ++pass)
+        for (int i = 0; i < nr; ++i) {
+            const double x = r[i];
+            if (!isfinite(x)) continue;
+            const double curv = 12.0 * c[4] * x * x + 6.0 * c[3] * x + 2.0 * c[2];
+            if (pass == 0 && !(curv > 0.0)) continue;
+            if (pass == 1 && !(c[4] > 0.0)) continue;
+            const double vv = qval(c, x);
+            if (!have || vv < bestv || (vv == bestv && (fabs(x) < fabs(best) || (fabs(x) == fabs(best) && x > best)))) {
+                have = true;
+                best = x;
+                bestv = vv;
+            }
+        }
+    if (!have) return OMM_ERR_LINESEARCH;
+    *xout = best;
+    return OMM_OK;
+}
+
+int blocks_for(int64_t work, int per) {
+    int64_t nb = ceil_div(work, per);
+    if (nb > 152 * 16) nb = 152 * 16;
+    return (int)(nb < 1 ? 1 : nb);
+}
+int red_blocks(int64_t work) {
+    int64_t nb = ceil_div(work, (int64_t)NT * 4);
+    if (nb > kRedBlocksMax) nb = kRedBlocksMax;
+    return (int)(nb < 1 ? 1 : nb);
+}
+
+#define LAUNCHED()                             \
+    do {                                       \
+        count_launch();                        \
+        OMM_CUDA_TRY(cudaGetLastError());      \
+    } while (0)
+
+}  // namespace
+
+// ======================================================================== device side: handle pieces
+int upload(const Host &hs, Dev &d) {
+    auto up = [](auto **dst, const auto &src) -> int {
+        using T = typename std::remove_reference<decltype(src[0])>::type;
+        const size_t n = src.size() ? src.size() : 1;
+        if (cudaMalloc((void **)dst, n * sizeof(T)) != cudaSuccess) return OMM_ERR_NOMEM;
+        if (!src.empty() && cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+            return OMM_ERR_CUDA;
+        return OMM_OK;
+    };
+    const Pattern &P = hs.P;
+    d.bm = P.bm;
+    d.bn = P.bn;
+    d.nbr = P.nbr;
+    d.nbc = P.nbc;
+    d.nnzH = P.Hrp[P.nbr];
+    d.nnzW = P.Wrp[P.nbr];
+    d.nnzHW = hs.HWrp[P.nbr];
+    d.nnzN = hs.Nrp[P.nbc];
+    int rc;
+    if ((rc = up(&d.Hrp, hs.Hrp)) || (rc = up(&d.Hcol, hs.Hcol)) || (rc = up(&d.Prp, hs.Prp)) ||
+        (rc = up(&d.Ph, hs.Ph)) || (rc = up(&d.Pw, hs.Pw)) || (rc = up(&d.Crp, hs.Crp)) || (rc = up(&d.Ca, hs.Ca)) ||
+        (rc = up(&d.Cb, hs.Cb)) || (rc = up(&d.Grp, hs.Grp)) || (rc = up(&d.Gb, hs.Gb)) || (rc = up(&d.Gq, hs.Gq)) ||
+        (rc = up(&d.WtoHW, hs.WtoHW)) || (rc = up(&d.Ntr, hs.Ntr)) || (rc = up(&d.Ndiag, hs.Ndiag)))
+        return rc;
+    const int64_t bb = (int64_t)P.bm * P.bm, bw = (int64_t)P.bm * P.bn, bq = (int64_t)P.bn * P.bn;
+    auto al = [](double **p, int64_t n) -> int {
+        return cudaMalloc((void **)p, (size_t)(n > 0 ? n : 1) * sizeof(double)) == cudaSuccess ? OMM_OK : OMM_ERR_NOMEM;
+    };
+    if ((rc = al(&d.HS, 2 * d.nnzH * bb)) || (rc = al(&d.Hin, 2 * d.nnzH * bb)) || (rc = al(&d.W, d.nnzW * bw)) ||
+        (rc = al(&d.D, d.nnzW * bw)) || (rc = al(&d.G, d.nnzW * bw)) || (rc = al(&d.Gp, d.nnzW * bw)) ||
+        (rc = al(&d.HW, d.nnzHW * bw)) || (rc = al(&d.SW, d.nnzHW * bw)) || (rc = al(&d.HD, d.nnzHW * bw)) ||
+        (rc = al(&d.SD, d.nnzHW * bw)) || (rc = al(&d.h0, d.nnzN * bq)) || (rc = al(&d.s0, d.nnzN * bq)) ||
+        (rc = al(&d.X, d.nnzN * bq)) || (rc = al(&d.Y, d.nnzN * bq)) || (rc = al(&d.h2, d.nnzN * bq)) ||
+        (rc = al(&d.s2, d.nnzN * bq)))
+        return rc;
+    if (cudaMalloc((void **)&d.keep, (size_t)(d.nnzH > 0 ? d.nnzH : 1)) != cudaSuccess) return OMM_ERR_NOMEM;
+    return OMM_OK;
+}
+
+void release(Dev &d) {
+    void *ptrs[] = {d.Hrp, d.Hcol, d.Prp, d.Ph, d.Pw, d.Crp, d.Ca, d.Cb, d.Grp, d.Gb, d.Gq, d.WtoHW, d.Ntr,
+                    d.Ndiag, d.HS, d.Hin, d.W, d.D, d.G, d.Gp, d.HW, d.SW, d.HD, d.SD, d.h0, d.s0, d.X,
+                    d.Y, d.h2, d.s2, d.keep};
+    for (void *p : ptrs) cudaFree(p);
+    d = Dev{};
+}
+
+int set_HS(Dev &d, const double *H, const double *S, bool on_device, double eps, bool eta_auto, double *scratch,
+           unsigned int *counter, DevState *state, cudaStream_t st) {
+    const int64_t bb = (int64_t)d.bm * d.bm;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    double *Hc = d.Hin, *Sc = d.Hin + d.nnzH * bb;
+    OMM_CUDA_TRY(cudaMemcpyAsync(Hc, H, d.nnzH * bb * sizeof(double), kind, st));
+    OMM_CUDA_TRY(cudaMemcpyAsync(Sc, S, d.nnzH * bb * sizeof(double), kind, st));
+    filter_kernel<<<blocks_for(d.nnzH, 256), 256, 0, st>>>(d.nnzH, (int)bb, Hc, Sc, eps * eps, d.keep);
+    LAUNCHED();
+    if (eta_auto) {
+        gershgorin_kernel<<<red_blocks(d.nbr * d.bm), NT, 0, st>>>(d.nbr, d.bm, d.Hrp, d.Hcol, Hc, Sc, scratch,
+                                                                    counter, state);
+        LAUNCHED();
+    }
+    shift_pack_kernel<<<blocks_for(d.nnzH * bb, 256), 256, 0, st>>>(d.nnzH, (int)bb, Hc, Sc, d.keep, state, d.HS);
+    LAUNCHED();
+    return OMM_OK;
+}
+
+#define DISPATCH_BLOCKS(BMv, BNv, CALL)                              \
+    do {                                                             \
+        if ((BMv) == 8 && (BNv) == 2) { constexpr int BM = 8, BN = 2; CALL; } \
+        else return OMM_ERR_UNSUPPORTED;                             \
+    } while (0)
+
+int products(Dev &d, const double *Din, double *HDo, double *SDo, const DevState *state, cudaStream_t st) {
+    DISPATCH_BLOCKS(d.bm, d.bn, (products_kernel<BM, BN><<<blocks_for(d.nnzHW * 32, NT), NT, 0, st>>>(
+                                     d.nnzHW, d.Prp, d.Ph, d.Pw, d.HS, Din, HDo, SDo, state)));
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int contract(Dev &d, const double *Wl, const double *Dl, const double *HDr, const double *SDr, double *Xo,
+             double *Yo, double *h2o, double *s2o, const DevState *state, cudaStream_t st) {
+    DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
+                                     d.nnzN, d.Crp, d.Ca, d.Cb, Wl, Dl, HDr, SDr, Xo, Yo, h2o, s2o, state)));
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int gradient(Dev &d, const DevState *state, cudaStream_t st) {
+    DISPATCH_BLOCKS(d.bm, d.bn, (gradient_kernel<BM, BN><<<blocks_for(d.nnzW * 16, NT), NT, 0, st>>>(
+                                     d.nnzW, d.Grp, d.Gb, d.Gq, d.WtoHW, d.HW, d.SW, d.h0, d.s0, d.G, state)));
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int coeffs(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
+    coeffs_kernel<<<red_blocks(d.nnzN * 4), NT, 0, st>>>(d.nnzN, d.Ntr, d.Ndiag, d.h0, d.s0, d.X, d.Y, d.h2,
+                                                           d.s2, scratch, counter, state);
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int nn_update(Dev &d, int64_t n, int mode, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
+    nn_update_kernel<<<red_blocks(d.nnzN * 4), NT, 0, st>>>(d.nnzN, d.Ntr, d.Ndiag, d.h0, d.s0, d.X, d.Y, d.h2,
+                                                              d.s2, n, scratch, counter, state, mode);
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int axpy(Dev &d, const DevState *state, cudaStream_t st) {
+    const int64_t bw = (int64_t)d.bm * d.bn;
+    axpy_kernel<<<blocks_for(d.nnzHW * bw, 256 * 4), 256, 0, st>>>(d.nnzW * bw, d.W, d.D, d.nnzHW * bw, d.HW, d.HD,
+                                                                      d.SW, d.SD, state);
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int dots(Dev &d, int first, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
+    const int64_t len = d.nnzW * d.bm * d.bn;
+    dots_kernel<<<red_blocks(len), NT, 0, st>>>(len, d.G, d.Gp, d.D, scratch, counter, state, first);
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int direction(Dev &d, const DevState *state, cudaStream_t st) {
+    const int64_t len = d.nnzW * d.bm * d.bn;
+    direction_kernel<<<blocks_for(len, 256 * 4), 256, 0, st>>>(len, d.G, d.Gp, d.D, state);
+    LAUNCHED();
+    return OMM_OK;
+}
+
+}  // namespace sp
+}  // namespace omm

@@ -1,0 +1,75 @@
+// Linear-scaling form: host pattern structures and device pieces (sparse.cu).
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "omm_internal.cuh"
+
+namespace omm {
+namespace sp {
+
+// Block patterns as given by the caller (block CSR over basis-atom rows).
+struct Pattern {
+    int32_t bm = 0, bn = 0;
+    int64_t nbr = 0, nbc = 0;
+    const int64_t *Hrp = nullptr;
+    const int32_t *Hcol = nullptr;
+    const int64_t *Wrp = nullptr;
+    const int32_t *Wcol = nullptr;
+};
+
+// Host copy of the patterns, the structural product patterns and the gather lists.
+struct Host {
+    Pattern P;
+    std::vector<int64_t> Hrp, Wrp, HWrp, Nrp;
+    std::vector<int32_t> Hcol, Wcol, HWcol, Ncol;
+    std::vector<int32_t> Ntr;               // transpose index within P_N
+    std::vector<unsigned char> Ndiag;       // block on the diagonal of P_N
+    std::vector<int32_t> WtoHW;             // position of each W block inside P_HW
+    std::vector<int64_t> Prp;               // products: per P_HW block
+    std::vector<int32_t> Ph, Pw;
+    std::vector<int64_t> Crp;               // contractions: per P_N block
+    std::vector<int32_t> Ca, Cb;
+    std::vector<int64_t> Grp;               // gradient: per P_W block
+    std::vector<int32_t> Gb, Gq;
+    std::vector<int64_t> WcolRp, WcolIdx;   // W blocks by column
+};
+
+// Device arrays of one sparse handle.
+struct Dev {
+    int32_t bm = 0, bn = 0;
+    int64_t nbr = 0, nbc = 0, nnzH = 0, nnzW = 0, nnzHW = 0, nnzN = 0;
+    int64_t *Hrp = nullptr, *Prp = nullptr, *Crp = nullptr, *Grp = nullptr;
+    int32_t *Hcol = nullptr, *Ph = nullptr, *Pw = nullptr, *Ca = nullptr, *Cb = nullptr, *Gb = nullptr,
+            *Gq = nullptr, *WtoHW = nullptr, *Ntr = nullptr;
+    unsigned char *Ndiag = nullptr, *keep = nullptr;
+    double *HS = nullptr, *Hin = nullptr;
+    double *W = nullptr, *D = nullptr, *G = nullptr, *Gp = nullptr;
+    double *HW = nullptr, *SW = nullptr, *HD = nullptr, *SD = nullptr;
+    double *h0 = nullptr, *s0 = nullptr, *X = nullptr, *Y = nullptr, *h2 = nullptr, *s2 = nullptr;
+};
+
+// Validate the caller's patterns and build everything host-side (OMM_ERR_PATTERN on malformed input).
+int build(const Pattern &P, Host &out);
+int upload(const Host &hs, Dev &d);
+void release(Dev &d);
+
+// Per-(H,S) setup: copy, block filtering, Gershgorin eta (optional), shift and pack.
+int set_HS(Dev &d, const double *H, const double *S, bool on_device, double eps, bool eta_auto, double *scratch,
+           unsigned int *counter, DevState *state, cudaStream_t st);
+
+// One step's pieces
+int products(Dev &d, const double *Din, double *HDo, double *SDo, const DevState *state, cudaStream_t st);
+int contract(Dev &d, const double *Wl, const double *Dl, const double *HDr, const double *SDr, double *Xo,
+             double *Yo, double *h2o, double *s2o, const DevState *state, cudaStream_t st);
+int gradient(Dev &d, const DevState *state, cudaStream_t st);
+int coeffs(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
+int nn_update(Dev &d, int64_t n, int mode, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
+int axpy(Dev &d, const DevState *state, cudaStream_t st);
+int dots(Dev &d, int first, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
+int direction(Dev &d, const DevState *state, cudaStream_t st);
+
+}  // namespace sp
+}  // namespace omm

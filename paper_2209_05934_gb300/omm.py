@@ -22,6 +22,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 REFINE_EXACT, REFINE_FP64 = 0, 1
 
 ARRAY_W, ARRAY_HW, ARRAY_SW, ARRAY_G, ARRAY_D, ARRAY_HW_N, ARRAY_SW_N = range(7)
+PATTERN_H, PATTERN_W, PATTERN_HW, PATTERN_N = range(4)
 
 
 class Options(C.Structure):
@@ -77,6 +78,7 @@ _SIGS = {
     "omm_get_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "omm_kernel_launches": (C.c_int64, []),
     "omm_last_error": (C.c_char_p, []),
+    "omm_get_pattern": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "omm_op_exact_gemm_workspace_bytes": (C.c_int64, [C.c_int64, C.c_int64, C.c_int64, C.c_int32]),
     "omm_op_exact_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                     C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
@@ -241,6 +243,79 @@ class Solver:
         out = np.zeros((rows, self.n), order="F")
         check(lib().omm_get_array(self._h, which, C.c_void_p(out.ctypes.data), 0), "omm_get_array")
         return out
+
+
+class SparseSolver:
+    """omm_handle of the linear-scaling form: H, S on a block pattern P_H of
+    bm x bm blocks, W on a localisation pattern P_W of bm x bn blocks (block CSR
+    over basis-atom rows, int64 rowptr / int32 col).  Values are passed as
+    (nnzb, bm, bm) / (nnzb, bm, bn) float64 arrays, blocks row-major."""
+
+    def __init__(self, m, n, bm, bn, H_rowptr, H_col, W_rowptr, W_col, **options):
+        self.m, self.n, self.bm, self.bn = m, n, bm, bn
+        self._keep = [np.ascontiguousarray(H_rowptr, dtype=np.int64), np.ascontiguousarray(H_col, dtype=np.int32),
+                      np.ascontiguousarray(W_rowptr, dtype=np.int64), np.ascontiguousarray(W_col, dtype=np.int32)]
+        self.nbr = len(self._keep[0]) - 1
+        self.nbc = n // bn
+        pat = Pattern(bm, bn, self.nbr, self.nbc, *[C.c_void_p(a.ctypes.data) for a in self._keep])
+        self._opts = default_options(**options)
+        h = C.c_void_p()
+        check(lib().omm_create(m, n, bm, C.byref(pat), C.byref(self._opts), C.byref(h)), "omm_create")
+        self._h = h
+        d = self.diag()
+        self.nnzb = {"H": d.nnzb_H, "W": d.nnzb_W, "HW": d.nnzb_HW, "N": d.nnzb_N}
+
+    close = Solver.close
+    __del__ = Solver.__del__
+    diag = Solver.diag
+    set_profiling = Solver.set_profiling
+    stage_times = Solver.stage_times
+
+    def set_HS(self, Hv, Sv):
+        for a, name in ((Hv, "H"), (Sv, "S")):
+            if tuple(a.shape) != (self.nnzb["H"], self.bm, self.bm):
+                raise ValueError(f"{name}: expected {(self.nnzb['H'], self.bm, self.bm)}, got {tuple(a.shape)}")
+        pH, dH = _ptr(Hv)
+        pS, dS = _ptr(Sv)
+        if dH != dS:
+            raise ValueError("H and S must both be host or both device arrays")
+        st = check(lib().omm_set_HS(self._h, pH, pS, dH), "omm_set_HS")
+        self.nnzb["H_kept"] = self.diag().nnzb_H
+        return st
+
+    def solve(self, W0=None, tol=1e-10, W_out=None, raise_on_error=True):
+        shape = (self.nnzb["W"], self.bm, self.bn)
+        for a, name in ((W0, "W0"), (W_out, "W_out")):
+            if a is not None and tuple(a.shape) != shape:
+                raise ValueError(f"{name}: expected {shape}")
+        p0, d0 = _ptr(W0)
+        po, do = _ptr(W_out)
+        E = C.c_double(0.0)
+        it = C.c_int32(0)
+        st = lib().omm_solve(self._h, p0, d0, float(tol), po, do, C.byref(E), C.byref(it))
+        if raise_on_error and st != OK:
+            raise OmmError(st, "omm_solve")
+        return E.value, it.value, st
+
+    def get_array(self, which):
+        sizes = {ARRAY_W: ("W", self.bm * self.bn), ARRAY_HW: ("HW", self.bm * self.bn),
+                 ARRAY_SW: ("HW", self.bm * self.bn), ARRAY_G: ("W", self.bm * self.bn),
+                 ARRAY_D: ("W", self.bm * self.bn), ARRAY_HW_N: ("N", self.bn * self.bn),
+                 ARRAY_SW_N: ("N", self.bn * self.bn)}
+        key, bs = sizes[which]
+        out = np.zeros(self.nnzb[key] * bs)
+        check(lib().omm_get_array(self._h, which, C.c_void_p(out.ctypes.data), 0), "omm_get_array")
+        return out
+
+    def get_pattern(self, which):
+        nrows = self.nbc if which == PATTERN_N else self.nbr
+        nnz = {PATTERN_H: self.nnzb.get("H_kept", self.nnzb["H"]), PATTERN_W: self.nnzb["W"],
+               PATTERN_HW: self.nnzb["HW"], PATTERN_N: self.nnzb["N"]}[which]
+        rp = np.zeros(nrows + 1, dtype=np.int64)
+        col = np.zeros(max(nnz, 1), dtype=np.int32)
+        check(lib().omm_get_pattern(self._h, which, C.c_void_p(rp.ctypes.data), C.c_void_p(col.ctypes.data)),
+              "omm_get_pattern")
+        return rp, col[:nnz]
 
 
 # ---------------------------------------------------------------- op-level calls

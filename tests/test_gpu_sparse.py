@@ -1,0 +1,158 @@
+"""Linear-scaling (block-sparse) form against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import omm as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def omm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2209_05934_gb300 import omm as _omm
+    _omm.lib()
+    return _omm
+
+
+def _setup(omm, sysm, radius, **opts):
+    rp, col, Hv, Sv = sysm.bsr()
+    wrp, wcol = sysm.w_pattern(radius)
+    s = omm.SparseSolver(sysm.m, sysm.n, 8, 2, rp, col, wrp, wcol, **opts)
+    return s, (rp, col, Hv, Sv), (wrp, wcol)
+
+
+def _oracle_inputs(sysm, radius):
+    rp, col, Hv, Sv = sysm.bsr()
+    N = sysm.natoms
+    H = O.bsr_to_csr(rp, col, Hv, N, N)
+    S = O.bsr_to_csr(rp, col, Sv, N, N)
+    mask = sp.csr_matrix(sysm.w_mask(radius).astype(np.float64))
+    W0 = sp.csr_matrix(sysm.W0_local(radius))
+    return H, S, W0, mask
+
+
+def _w_blocks_to_dense(sysm, radius, vals):
+    wrp, wcol = sysm.w_pattern(radius)
+    W = np.zeros((sysm.m, sysm.n))
+    rows = np.repeat(np.arange(sysm.natoms), np.diff(wrp))
+    for b, (I, J) in enumerate(zip(rows, wcol)):
+        W[8 * I:8 * I + 8, 2 * J:2 * J + 2] = vals[b].reshape(8, 2)
+    return W
+
+
+@pytest.mark.parametrize("dims,radius", [((4, 4, 4), 4.5), ((3, 4, 5), 6.0)])
+def test_patterns_bit_exact(omm, dims, radius):
+    import synth
+    sysm = synth.make_system(*dims, seed=0)
+    s, (rp, col, Hv, Sv), (wrp, wcol) = _setup(omm, sysm, radius)
+    hwrp, hwcol = O.structural_pattern_product(rp, col, wrp, wcol, sysm.natoms)
+    # P_N = P_W^T P_HW
+    N = sysm.natoms
+    PW = sp.csr_matrix((np.ones(len(wcol)), wcol, wrp), shape=(N, N))
+    PHW = sp.csr_matrix((np.ones(len(hwcol)), hwcol, hwrp), shape=(N, N))
+    PN = (PW.T @ PHW).tocsr()
+    PN.sort_indices()
+    got_rp, got_col = s.get_pattern(omm.PATTERN_HW)
+    np.testing.assert_array_equal(got_rp, hwrp)
+    np.testing.assert_array_equal(got_col, hwcol)
+    got_rp, got_col = s.get_pattern(omm.PATTERN_N)
+    np.testing.assert_array_equal(got_rp, PN.indptr)
+    np.testing.assert_array_equal(got_col, PN.indices)
+    s.close()
+
+
+def test_block_filtering_bit_exact(omm):
+    import synth
+    sysm = synth.make_system(3, 3, 3, seed=1)
+    s, (rp, col, Hv, Sv), _ = _setup(omm, sysm, 6.0)
+    Hv = Hv.copy()
+    Sv = Sv.copy()
+    rng = np.random.default_rng(0)
+    offdiag = np.nonzero(np.repeat(np.arange(sysm.natoms), np.diff(rp)) != col)[0]
+    pick = rng.choice(offdiag, 12, replace=False)
+    scales = [1e-10, 3e-9, 9.99e-9, 1.0001e-8, 2e-8, 1e-7]
+    for i, b in enumerate(pick):
+        sc = scales[i % len(scales)] / 8.0        # ||block||_F ~ sc * 8 for unit entries
+        Hv[b] = sc * np.sign(Hv[b] + 1e-300)
+        Sv[b] = sc * np.sign(Sv[b] + 1e-300) if i % 2 == 0 else Sv[b]
+    s.set_HS(Hv, Sv)
+    keep = O.filter_hs_blocks(Hv, Sv, 1e-8)
+    assert not keep.all()
+    got_rp, got_col = s.get_pattern(omm.PATTERN_H)
+    rows = np.repeat(np.arange(sysm.natoms), np.diff(rp))
+    want_rp = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=sysm.natoms))])
+    np.testing.assert_array_equal(got_rp, want_rp)
+    np.testing.assert_array_equal(got_col, col[keep])
+    assert s.diag().nnzb_H == keep.sum()
+    s.close()
+
+
+@pytest.mark.parametrize("dims,radius,k", [((4, 4, 4), 4.5, 1), ((4, 4, 4), 4.5, 6), ((3, 4, 5), 6.0, 9)])
+def test_fixed_iterations_track_oracle(omm, dims, radius, k):
+    import synth
+    sysm = synth.make_system(*dims, seed=0)
+    s, (rp, col, Hv, Sv), _ = _setup(omm, sysm, radius, max_iter=k)
+    s.set_HS(Hv, Sv)
+    eta = s.diag().eta
+    H, S, W0, mask = _oracle_inputs(sysm, radius)
+    assert eta == pytest.approx(O.gershgorin_eta(H, S), rel=1e-13)
+    W0b = sysm.W0_bsr_values(radius)
+    Wout = np.zeros_like(W0b)
+    E, iters, st = s.solve(W0b, tol=0.0, W_out=Wout, raise_on_error=False)
+    ref = O.omm_cg(H, S, W0, tol=0.0, eta=eta, max_iter=k, mask=mask)
+    assert st == omm.ERR_MAXITER and iters == k == ref.iters
+    assert E == pytest.approx(ref.E, rel=1e-12)
+    np.testing.assert_allclose(_w_blocks_to_dense(sysm, radius, Wout), ref.W.toarray(), rtol=1e-8, atol=1e-10)
+    s.close()
+
+
+def test_converged_solve_matches_oracle(omm):
+    import synth
+    sysm = synth.make_system(3, 3, 2, seed=2)
+    radius = 3.6
+    s, (rp, col, Hv, Sv), _ = _setup(omm, sysm, radius)
+    s.set_HS(Hv, Sv)
+    eta = s.diag().eta
+    H, S, W0, mask = _oracle_inputs(sysm, radius)
+    E, iters, st = s.solve(sysm.W0_bsr_values(radius), tol=1e-11)
+    ref = O.omm_cg(sysm.dense_H(), sysm.dense_S(), sysm.W0_local(radius), tol=1e-11, eta=eta,
+                   mask=sysm.w_mask(radius))
+    assert st == omm.OK and ref.status == O.OK
+    assert abs(E - ref.E) / abs(ref.E) < 1e-10
+    s.close()
+
+
+def test_full_pattern_equals_dense_solve(omm):
+    """With every block allowed the localised form is the dense form."""
+    import synth
+    sysm = synth.make_system(3, 3, 2, seed=2)
+    s, (rp, col, Hv, Sv), _ = _setup(omm, sysm, 100.0)
+    s.set_HS(Hv, Sv)
+    E, iters, st = s.solve(sysm.W0_bsr_values(100.0), tol=1e-12)
+    d = omm.Solver(sysm.m, sysm.n, 8)
+    d.set_HS(np.asfortranarray(sysm.dense_H()), np.asfortranarray(sysm.dense_S()))
+    E2, it2, st2 = d.solve(np.asfortranarray(sysm.W0_local(100.0)), tol=1e-12)
+    assert st == st2 == omm.OK
+    assert E == pytest.approx(E2, rel=1e-12) and abs(iters - it2) <= 1
+    s.close()
+    d.close()
+
+
+def test_pattern_errors(omm):
+    import ctypes as C
+    rp = np.array([0, 1, 2], dtype=np.int64)
+    col = np.array([1, 0], dtype=np.int32)          # missing diagonal blocks
+    wrp = np.array([0, 1, 2], dtype=np.int64)
+    wcol = np.array([0, 1], dtype=np.int32)
+    with pytest.raises(omm.OmmError) as e:
+        omm.SparseSolver(16, 4, 8, 2, rp, col, wrp, wcol)
+    assert e.value.status == omm.ERR_PATTERN
+    col2 = np.array([0, 5], dtype=np.int32)         # out of range
+    with pytest.raises(omm.OmmError):
+        omm.SparseSolver(16, 4, 8, 2, rp, col2, wrp, wcol)
