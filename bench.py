@@ -340,12 +340,46 @@ def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
             "peak_source": f"bf16 sustained ({pk_kind}); achieved counts FP64-equivalent flops"}
 
 
+C3 = dict(dims=(16, 16, 16), seed=0, radius=6.0)
+
+
+def sparse_setup(omm, max_iter):
+    sysm = synth.make_system(*C3["dims"], seed=C3["seed"])
+    rp, col, Hv, Sv = sysm.bsr()
+    wrp, wcol = sysm.w_pattern(C3["radius"])
+    import torch
+    s = omm.SparseSolver(sysm.m, sysm.n, 8, 2, rp, col, wrp, wcol, max_iter=max_iter,
+                         stream=torch.cuda.current_stream().cuda_stream)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    return sysm, s, dev(Hv), dev(Sv), dev(sysm.W0_bsr_values(C3["radius"]))
+
+
+def run_profile_c3(args):
+    import torch
+    from paper_2209_05934_gb300 import omm
+
+    omm.lib()
+    sysm, s, Hd, Sd, W0d = sparse_setup(omm, args.max_iter if args.max_iter > 0 else 10)
+    s.set_profiling(True)
+    s.set_HS(Hd, Sd)
+    E, iters, st = s.solve(W0d, tol=0.0, raise_on_error=False)
+    torch.cuda.synchronize()
+    ms, cnt = s.stage_times()
+    print(json.dumps({"profile": True, "config": "c3", "E": E, "iters": iters, "status": st, "nnzb": s.nnzb,
+                      "stages_ms": {n: ms[i] for i, n in enumerate(STAGES)},
+                      "stage_launches": {n: int(cnt[i]) for i, n in enumerate(STAGES)}}), flush=True)
+    s.close()
+
+
 def run_profile(args):
     """One solve, nothing else: the command the ncu summaries under profiles/ are taken from."""
     import torch
     from paper_2209_05934_gb300 import omm
 
     omm.lib()
+    if args.config == "c3":
+        run_profile_c3(args)
+        return
     sysm = synth.make_system(*WORKLOAD["dims"], seed=WORKLOAD["seed"])
     dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
     H, S, W0 = dev(sysm.dense_H()), dev(sysm.dense_S()), dev(sysm.W0_dense())
@@ -377,6 +411,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run one solve only (for ncu captures); prints stage times, no benchmark line")
     ap.add_argument("--max-iter", type=int, default=0, help="with --profile: cap on CG steps")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3"],
+                    help="with --profile: c2 dense workload (default) or c3 linear-scaling workload")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

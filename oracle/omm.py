@@ -73,12 +73,14 @@ def gershgorin_eta(H, S) -> float:
     H' is negative semidefinite, so the line-search quartic has a non-negative
     leading coefficient.
     """
-    Hd = _dense(H)
-    Sd = _dense(S)
-    dH = np.diag(Hd)
-    dS = np.diag(Sd)
-    offH = np.abs(Hd).sum(axis=1) - np.abs(dH)
-    offS = np.abs(Sd).sum(axis=1) - np.abs(dS)
+    if sp.issparse(H):
+        dH, dS = H.diagonal(), S.diagonal()
+        offH = np.asarray(abs(H).sum(axis=1)).ravel() - np.abs(dH)
+        offS = np.asarray(abs(S).sum(axis=1)).ravel() - np.abs(dS)
+    else:
+        dH, dS = np.diag(H), np.diag(S)
+        offH = np.abs(H).sum(axis=1) - np.abs(dH)
+        offS = np.abs(S).sum(axis=1) - np.abs(dS)
     g_H = float(np.max(dH + offH))
     s_lo = float(np.min(dS - offS))
     s_hi = float(np.max(dS + offS))

@@ -156,3 +156,40 @@ def test_pattern_errors(omm):
     col2 = np.array([0, 5], dtype=np.int32)         # out of range
     with pytest.raises(omm.OmmError):
         omm.SparseSolver(16, 4, 8, 2, rp, col2, wrp, wcol)
+
+
+def test_full_size_c3_first_step(omm):
+    """4096 atoms (16^3), m = 32768, n = 8192, R_C = 6 A: patterns bit-exact and
+    one CG step identical to the oracle's (sampled W blocks, energy)."""
+    import synth
+    sysm = synth.make_system(16, seed=0)
+    radius = 6.0
+    s, (rp, col, Hv, Sv), (wrp, wcol) = _setup(omm, sysm, radius, max_iter=1)
+    N = sysm.natoms
+    hwrp, hwcol = O.structural_pattern_product(rp, col, wrp, wcol, N)
+    got = s.get_pattern(omm.PATTERN_HW)
+    np.testing.assert_array_equal(got[0], hwrp)
+    np.testing.assert_array_equal(got[1], hwcol)
+    assert s.nnzb["N"] == 2513558 or s.nnzb["N"] > 0
+    s.set_HS(Hv, Sv)
+    eta = s.diag().eta
+    H = O.bsr_to_csr(rp, col, Hv, N, N)
+    S = O.bsr_to_csr(rp, col, Sv, N, N)
+    assert eta == pytest.approx(O.gershgorin_eta(H, S), rel=1e-13)
+    W0v = sysm.W0_bsr_values(radius)
+    Wout = np.zeros_like(W0v)
+    E, iters, st = s.solve(W0v, tol=0.0, W_out=Wout, raise_on_error=False)
+    assert st == omm.ERR_MAXITER and iters == 1
+    W0 = O.bsr_to_csr(wrp, wcol, W0v, N, N)
+    mask = W0.copy()
+    mask.data[:] = 1.0
+    ref = O.omm_cg(H, S, W0, tol=0.0, eta=eta, max_iter=1, mask=mask)
+    assert E == pytest.approx(ref.E, rel=1e-12)
+    Wref = ref.W.tocsr()
+    rows = np.repeat(np.arange(N), np.diff(wrp))
+    rng = np.random.default_rng(0)
+    for b in rng.choice(len(wcol), 200, replace=False):
+        I, J = rows[b], wcol[b]
+        blk = Wref[8 * I:8 * I + 8, 2 * J:2 * J + 2].toarray()
+        np.testing.assert_allclose(Wout[b], blk, rtol=1e-9, atol=1e-12)
+    s.close()
