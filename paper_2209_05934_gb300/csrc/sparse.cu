@@ -428,22 +428,23 @@ __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64
                                                        double *HD, double *SD, const DevState *state) {
     if (done(state)) return;
     const int lane = threadIdx.x & 31;
-    const int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-    if (o >= nnzHW) return;
     constexpr int NE = BM * BN;          // outputs per block
     const int which = lane / 16, e = lane % 16;   // which: 0 = H', 1 = S
     const bool active = e < NE;
     const int r = e / BN, c = e % BN;
-    double acc = 0.0;
-    for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
-        const double *A = HS + ((int64_t)Ph[t] * 2 + which) * BM * BM + r * BM;
-        const double *B = D + (int64_t)Pw[t] * BM * BN + c;
-        if (active) {
+    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+    for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; o < nnzHW; o += nwarps) {
+        double acc = 0.0;
+        for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
+            const double *A = HS + ((int64_t)Ph[t] * 2 + which) * BM * BM + r * BM;
+            const double *B = D + (int64_t)Pw[t] * BM * BN + c;
+            if (active) {
 #pragma unroll
-            for (int k = 0; k < BM; ++k) acc = fma(A[k], B[k * BN], acc);
+                for (int k = 0; k < BM; ++k) acc = fma(A[k], B[k * BN], acc);
+            }
         }
+        if (active) (which ? SD : HD)[o * NE + e] = acc;
     }
-    if (active) (which ? SD : HD)[o * NE + e] = acc;
 }
 
 // ---- contractions on P_N: warp per N block q; 16 outputs (X, Y, h2, s2 of 2x2)
@@ -457,27 +458,26 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
                                                        const DevState *state) {
     if (done(state)) return;
     const int lane = threadIdx.x & 31;
-    const int64_t q = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-    if (q >= nnzN) return;
     static_assert(BN == 2, "contraction lanes assume 2 orbitals per W block");
     const int v = lane >> 1, half = lane & 1;
     const int mat = v >> 2, a = (v >> 1) & 1, b = v & 1;   // mat: 0 X, 1 Y, 2 h2, 3 s2
     const double *L = (mat < 2) ? W : D;
     const double *R = (mat == 0 || mat == 2) ? HD : SD;
-    double acc = 0.0;
-    for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
-        const double *l = L + (int64_t)Ca[t] * BM * BN + a;
-        const double *rr = R + (int64_t)Cb[t] * BM * BN + b;
+    double *out = mat == 0 ? X : mat == 1 ? Y : mat == 2 ? h2 : s2;
+    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+    for (int64_t q = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; q < nnzN; q += nwarps) {
+        double acc = 0.0;
+        for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
+            const double *l = L + (int64_t)Ca[t] * BM * BN + a;
+            const double *rr = R + (int64_t)Cb[t] * BM * BN + b;
 #pragma unroll
-        for (int kk = 0; kk < BM / 2; ++kk) {
-            const int k = half * (BM / 2) + kk;
-            acc = fma(l[k * BN], rr[k * BN], acc);
+            for (int kk = 0; kk < BM / 2; ++kk) {
+                const int k = half * (BM / 2) + kk;
+                acc = fma(l[k * BN], rr[k * BN], acc);
+            }
         }
-    }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    if (half == 0) {
-        double *out = mat == 0 ? X : mat == 1 ? Y : mat == 2 ? h2 : s2;
-        out[q * 4 + a * 2 + b] = acc;
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (half == 0) out[q * 4 + a * 2 + b] = acc;
     }
 }
 
@@ -491,10 +491,11 @@ __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_
                                                        const double *__restrict__ s0, double *G,
                                                        const DevState *state) {
     if (done(state)) return;
-    const int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 4;
     const int e = threadIdx.x & 15;
-    if (o >= nnzW || e >= BM * BN) return;
+    if (e >= BM * BN) return;
     const int r = e / BN, c = e % BN;
+    const int64_t ngroups = ((int64_t)gridDim.x * NT) >> 4;
+    for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 4; o < nnzW; o += ngroups) {
     double acc = 0.0;
     for (int64_t t = Grp[o]; t < Grp[o + 1]; ++t) {
         const double *sw = SW + (int64_t)Gb[t] * BM * BN + r * BN;
@@ -508,6 +509,7 @@ __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_
         }
     }
     G[o * BM * BN + e] = 2.0 * (2.0 * HW[(int64_t)WtoHW[o] * BM * BN + e] - acc);
+    }
 }
 
 // ---- quartic coefficients and line minimum on P_N (2x2 blocks)
