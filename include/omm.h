@@ -160,6 +160,35 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
 int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
               double *W_out, int32_t W_out_on_device, double *E_out, int32_t *iters_out);
 
+/*
+ * The same solve in three non-blocking steps, for drivers that keep several
+ * handles busy at once (batched and serving use).  omm_solve_begin enqueues
+ * the start-up and a first chunk of CG steps on the handle's stream and
+ * returns.  omm_solve_progress checks the chunk (blocking != 0: waits for it);
+ * when it has finished it enqueues the next chunk or the next phase
+ * (split-precision -> refinement), and sets *done = 1 once the solve is over.
+ * omm_solve_end copies W out (as omm_solve) and returns the solve's status.
+ * omm_solve(h, ...) is begin + progress(blocking) until done + end.
+ */
+int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, double tol);
+int omm_solve_progress(omm_handle *h, int32_t blocking, int32_t *done);
+int omm_solve_end(omm_handle *h, double *W_out, int32_t W_out_on_device, double *E_out,
+                  int32_t *iters_out);
+
+/*
+ * Batched solves: `count` distinct handles (any sizes, forms and options, each
+ * after its omm_set_HS) minimised together, each on its own stream so their
+ * kernels overlap on the device (independent k-points, spins or systems,
+ * section "Recommendations for OMM solver use": spin channels are solved in
+ * sequence by the paper; here they run at once).  W0[i] as in omm_solve (W0
+ * == NULL or W0[i] == NULL warm-starts); the solutions stay in the handles
+ * (omm_get_array).  E_out, iters_out, status_out: arrays of count entries,
+ * nullable.  Returns OMM_OK or the first non-OK per-handle status.  Results
+ * do not depend on what runs beside them: every reduction has a fixed order.
+ */
+int omm_batch_solve(omm_handle **handles, int32_t count, const double *const *W0, int32_t W0_on_device,
+                    double tol, double *E_out, int32_t *iters_out, int32_t *status_out);
+
 /* Diagnostics of the last set_HS / solve. */
 int omm_get_diag(omm_handle *h, omm_diag *d);
 

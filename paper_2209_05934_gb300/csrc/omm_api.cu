@@ -74,6 +74,11 @@ struct omm_handle {
     int chunk = 8;
     MixedBufs mx;
     ExactBufs ex;
+    int phase = 0;            // PH_* of the asynchronous driver
+    int k_mixed = 0;          // CG steps of the split-precision phase
+    int status = OMM_OK;      // status of the finished solve
+    double tol_target = 0.0;
+    cudaEvent_t ev_poll = nullptr;
     omm::sp::Host sh;   // linear-scaling form: patterns and gather lists (host)
     omm::sp::Dev sd;    // linear-scaling form: device arrays
     // optional per-stage device timing (omm_set_profiling)
@@ -134,6 +139,7 @@ void free_handle(omm_handle *h) {
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->ev_poll) cudaEventDestroy(h->ev_poll);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -566,22 +572,27 @@ int sparse_iteration(omm_handle *h) {
     return OMM_OK;
 }
 
-// Run chunks of iterations until the device state says done; checks the
-// bounded-wait error word after every chunk.
-template <class F>
-int run_until_done(omm_handle *h, F iteration) {
-    for (;;) {
-        for (int c = 0; c < h->chunk; ++c) TRY(iteration());
-        OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost,
-                                     h->stream));
-        OMM_CUDA_TRY(cudaStreamSynchronize(h->stream));
-        harvest_stage_times(h);
-        if (h->hstate->wait_timeout) {
-            omm::set_error("a bounded mbarrier wait in the tensor-core GEMM timed out");
-            return OMM_ERR_TIMEOUT;
+// Solve phases of the asynchronous driver (omm_solve_begin / _progress / _end)
+enum { PH_IDLE = 0, PH_MIXED = 1, PH_REFINE = 2, PH_FP64 = 3, PH_SPARSE = 4, PH_FINISHED = 5 };
+
+double *w_dev(omm_handle *h) { return h->sparse ? h->sd.W : h->WD; }
+int64_t w_len(omm_handle *h) { return h->sparse ? h->sd.nnzW * h->sd.bm * h->sd.bn : h->m * h->n; }
+
+// Enqueue one chunk of CG steps of the current phase, then the state copy
+// and the event the host polls.  Kernels of a finished solve return at once.
+int enqueue_chunk(omm_handle *h) {
+    for (int c = 0; c < h->chunk; ++c) {
+        switch (h->phase) {
+            case PH_MIXED: TRY(mixed_iteration(h, false)); break;
+            case PH_REFINE: TRY(mixed_iteration(h, true)); break;
+            case PH_FP64: TRY(dense_iteration(h)); break;
+            case PH_SPARSE: TRY(sparse_iteration(h)); break;
+            default: return OMM_ERR_STATE;
         }
-        if (h->hstate->done) return OMM_OK;
     }
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, h->stream));
+    OMM_CUDA_TRY(cudaEventRecord(h->ev_poll, h->stream));
+    return OMM_OK;
 }
 
 }  // namespace
@@ -709,6 +720,7 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
     if (cudaMemsetAsync(h->counters, 0, 64 * 8 * sizeof(unsigned int), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->dstate, 0, sizeof(omm::DevState), h->stream) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_poll, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         free_handle(h);
         return OMM_ERR_CUDA;
@@ -785,18 +797,16 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
     return OMM_OK;
 }
 
-int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol, double *W_out,
-              int32_t W_out_on_device, double *E_out, int32_t *iters_out) {
+int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, double tol) {
     if (h == nullptr || !(tol >= 0.0)) return OMM_ERR_ARG;
     if (!h->have_HS) return OMM_ERR_STATE;
     if (W0 == nullptr && !h->have_W) return OMM_ERR_STATE;
-    const int64_t m = h->m, n = h->n, mn = m * n;
-    const int64_t wlen = h->sparse ? h->sd.nnzW * h->sd.bm * h->sd.bn : mn;   // doubles in W
-    double *Wdev = h->sparse ? h->sd.W : h->WD;
+    if (h->phase != PH_IDLE && h->phase != PH_FINISHED) return OMM_ERR_STATE;
+    const int64_t n = h->n;
     cudaStream_t st = h->stream;
     OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
     if (W0 != nullptr)
-        OMM_CUDA_TRY(cudaMemcpyAsync(Wdev, W0, wlen * sizeof(double),
+        OMM_CUDA_TRY(cudaMemcpyAsync(w_dev(h), W0, w_len(h) * sizeof(double),
                                      W0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     omm::DevState init{};
     init.eta = h->diag.eta;
@@ -804,53 +814,101 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
     init.orth_tol = h->opt.orth_tol;
     init.max_iter = h->opt.max_iter;
     init.n = (int)n;
-    *h->hstate = init;
-    OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
-    int k_mixed = 0;
+    h->tol_target = tol;
+    h->k_mixed = 0;
+    h->status = OMM_OK;
     if (h->sparse) {
+        h->phase = PH_SPARSE;
+        *h->hstate = init;
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
         { StageTimer t(h, OMM_STAGE_START); TRY(sparse_start(h)); }
-        h->have_W = true;
-        TRY(run_until_done(h, [&] { return sparse_iteration(h); }));
     } else if (h->opt.precision == OMM_PREC_MIXED) {
         // phase 1: split-precision CG to a tolerance a decade below the target
+        h->phase = PH_MIXED;
         omm::DevState ph = init;
         ph.tol = fmax(0.1 * tol, 1e-12);
         ph.orth_tol = 0.0;
         *h->hstate = ph;
         OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
         { StageTimer t(h, OMM_STAGE_START); TRY(mixed_start(h)); }
-        h->have_W = true;
-        TRY(run_until_done(h, [&] { return mixed_iteration(h, false); }));
-        k_mixed = h->hstate->k;
-        if (h->hstate->status == OMM_OK) {
-            // phase 2: refinement sweep -- FP64 re-anchoring of H'W, SW, H_W,
-            // S_W and G, then CG steps with an FP64 gradient
-            omm::DevState rf = init;
-            rf.k = k_mixed;
-            *h->hstate = rf;
-            OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
-            if (h->opt.refine == OMM_REFINE_EXACT) {
-                TRY(exact_anchor(h));
-            } else {
-                StageTimer t(h, OMM_STAGE_ANCHOR);
-                TRY(dense_start(h));
-                TRY(omm::mx_round(mn, h->G, h->mx.G32, h->dstate, st));
-            }
-            TRY(mixed_direction(h, 1));
-            { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
-            TRY(run_until_done(h, [&] { return mixed_iteration(h, true); }));
-        }
     } else {
+        h->phase = PH_FP64;
+        *h->hstate = init;
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
         { StageTimer t(h, OMM_STAGE_START); TRY(dense_start(h)); }
-        h->have_W = true;
-        TRY(run_until_done(h, [&] { return dense_iteration(h); }));
     }
-    OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
+    h->have_W = true;
+    return enqueue_chunk(h);
+}
+
+int omm_solve_progress(omm_handle *h, int32_t blocking, int32_t *done) {
+    if (h == nullptr || done == nullptr) return OMM_ERR_ARG;
+    *done = 0;
+    if (h->phase == PH_IDLE) return OMM_ERR_STATE;
+    if (h->phase == PH_FINISHED) {
+        *done = 1;
+        return OMM_OK;
+    }
+    if (blocking) {
+        OMM_CUDA_TRY(cudaEventSynchronize(h->ev_poll));
+    } else {
+        const cudaError_t q = cudaEventQuery(h->ev_poll);
+        if (q == cudaErrorNotReady) return OMM_OK;
+        OMM_CUDA_TRY(q);
+    }
+    harvest_stage_times(h);
+    if (h->hstate->wait_timeout) {
+        omm::set_error("a bounded mbarrier wait in the tensor-core GEMM timed out");
+        h->status = OMM_ERR_TIMEOUT;
+        h->phase = PH_FINISHED;
+        *done = 1;
+        return OMM_OK;
+    }
+    if (!h->hstate->done) return enqueue_chunk(h);
+    if (h->phase == PH_MIXED && h->hstate->status == OMM_OK) {
+        // phase 2: refinement sweep -- accurate re-anchoring of H'W, SW, H_W,
+        // S_W and G, then CG steps with an accurate gradient
+        const int64_t mn = h->m * h->n;
+        cudaStream_t st = h->stream;
+        h->k_mixed = h->hstate->k;
+        omm::DevState rf{};
+        rf.eta = h->diag.eta;
+        rf.tol = h->tol_target;
+        rf.orth_tol = h->opt.orth_tol;
+        rf.max_iter = h->opt.max_iter;
+        rf.n = (int)h->n;
+        rf.k = h->k_mixed;
+        *h->hstate = rf;
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
+        if (h->opt.refine == OMM_REFINE_EXACT) {
+            TRY(exact_anchor(h));
+        } else {
+            StageTimer t(h, OMM_STAGE_ANCHOR);
+            TRY(dense_start(h));
+            TRY(omm::mx_round(mn, h->G, h->mx.G32, h->dstate, st));
+        }
+        TRY(mixed_direction(h, 1));
+        { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
+        h->phase = PH_REFINE;
+        return enqueue_chunk(h);
+    }
+    h->status = h->hstate->status;
+    h->phase = PH_FINISHED;
+    OMM_CUDA_TRY(cudaEventRecord(h->ev1, h->stream));
+    *done = 1;
+    return OMM_OK;
+}
+
+int omm_solve_end(omm_handle *h, double *W_out, int32_t W_out_on_device, double *E_out, int32_t *iters_out) {
+    if (h == nullptr) return OMM_ERR_ARG;
+    if (h->phase != PH_FINISHED) return OMM_ERR_STATE;
+    cudaStream_t st = h->stream;
     if (W_out != nullptr)
-        OMM_CUDA_TRY(cudaMemcpyAsync(W_out, Wdev, wlen * sizeof(double),
+        OMM_CUDA_TRY(cudaMemcpyAsync(W_out, w_dev(h), w_len(h) * sizeof(double),
                                      W_out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
     const omm::DevState &s = *h->hstate;
+    const int64_t n = h->n;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     h->diag.t_solve_ms = ms;
@@ -861,12 +919,65 @@ int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol,
     // ||S_W||^2 - 2 tr S_W + n:  n_e = 2 (n - ||S_W - I||^2)
     h->diag.charge = 2.0 * ((double)n - s.orth2);
     h->diag.iters = s.k;
-    h->diag.status = s.status;
-    h->diag.iters_mixed = k_mixed;
-    h->diag.iters_refine = s.k - k_mixed;
+    h->diag.status = h->status;
+    h->diag.iters_mixed = h->k_mixed;
+    h->diag.iters_refine = s.k - h->k_mixed;
     if (E_out) *E_out = s.E;
     if (iters_out) *iters_out = s.k;
-    return s.status;
+    h->phase = PH_IDLE;
+    return h->status;
+}
+
+int omm_solve(omm_handle *h, const double *W0, int32_t W0_on_device, double tol, double *W_out,
+              int32_t W_out_on_device, double *E_out, int32_t *iters_out) {
+    TRY(omm_solve_begin(h, W0, W0_on_device, tol));
+    for (int32_t done = 0; !done;) TRY(omm_solve_progress(h, 1, &done));
+    return omm_solve_end(h, W_out, W_out_on_device, E_out, iters_out);
+}
+
+int omm_batch_solve(omm_handle **handles, int32_t count, const double *const *W0, int32_t W0_on_device, double tol,
+                    double *E_out, int32_t *iters_out, int32_t *status_out) {
+    if (handles == nullptr || count < 0) return OMM_ERR_ARG;
+    for (int32_t i = 0; i < count; ++i) {
+        if (handles[i] == nullptr) return OMM_ERR_ARG;
+        for (int32_t j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) return OMM_ERR_ARG;
+    }
+    std::vector<int32_t> done(count, 0);
+    for (int32_t i = 0; i < count; ++i) {
+        const int rc = omm_solve_begin(handles[i], W0 ? W0[i] : nullptr, W0_on_device, tol);
+        if (rc != OMM_OK) return rc;
+    }
+    int32_t remaining = count;
+    while (remaining > 0) {
+        int ready = 0, first_open = -1;
+        for (int32_t i = 0; i < count; ++i) {
+            if (done[i]) continue;
+            if (first_open < 0) first_open = i;
+            if (cudaEventQuery(handles[i]->ev_poll) == cudaErrorNotReady) continue;
+            ++ready;
+            const int rc = omm_solve_progress(handles[i], 0, &done[i]);   // enqueues the next chunk
+            if (rc != OMM_OK) return rc;
+            if (done[i]) --remaining;
+        }
+        if (remaining > 0 && ready == 0) {
+            // nothing ready: wait for the oldest open chunk instead of spinning
+            const int rc = omm_solve_progress(handles[first_open], 1, &done[first_open]);
+            if (rc != OMM_OK) return rc;
+            if (done[first_open]) --remaining;
+        }
+    }
+    int worst = OMM_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        double E = 0.0;
+        int32_t it = 0;
+        const int st = omm_solve_end(handles[i], nullptr, 0, &E, &it);
+        if (E_out) E_out[i] = E;
+        if (iters_out) iters_out[i] = it;
+        if (status_out) status_out[i] = st;
+        if (st != OMM_OK && worst == OMM_OK) worst = st;
+    }
+    return worst;
 }
 
 int omm_get_diag(omm_handle *h, omm_diag *d) {

@@ -79,6 +79,11 @@ _SIGS = {
     "omm_kernel_launches": (C.c_int64, []),
     "omm_last_error": (C.c_char_p, []),
     "omm_get_pattern": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "omm_solve_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double]),
+    "omm_solve_progress": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "omm_solve_end": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "omm_batch_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
     "omm_op_exact_gemm_workspace_bytes": (C.c_int64, [C.c_int64, C.c_int64, C.c_int64, C.c_int32]),
     "omm_op_exact_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                     C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
@@ -228,6 +233,25 @@ class Solver:
         check(lib().omm_get_diag(self._h, C.byref(d)), "omm_get_diag")
         return d
 
+    # asynchronous driver
+    def begin(self, W0=None, tol: float = 1e-10):
+        p0, d0 = _ptr(W0)
+        return check(lib().omm_solve_begin(self._h, p0, d0, float(tol)), "omm_solve_begin")
+
+    def progress(self, blocking: bool = False) -> bool:
+        done = C.c_int32(0)
+        check(lib().omm_solve_progress(self._h, int(blocking), C.byref(done)), "omm_solve_progress")
+        return bool(done.value)
+
+    def end(self, W_out=None, raise_on_error=True):
+        po, do = _ptr(W_out)
+        E = C.c_double(0.0)
+        it = C.c_int32(0)
+        st = lib().omm_solve_end(self._h, po, do, C.byref(E), C.byref(it))
+        if raise_on_error and st != OK:
+            raise OmmError(st, "omm_solve_end")
+        return E.value, it.value, st
+
     def set_profiling(self, on: bool):
         check(lib().omm_set_profiling(self._h, int(on)), "omm_set_profiling")
 
@@ -268,6 +292,9 @@ class SparseSolver:
     close = Solver.close
     __del__ = Solver.__del__
     diag = Solver.diag
+    begin = Solver.begin
+    progress = Solver.progress
+    end = Solver.end
     set_profiling = Solver.set_profiling
     stage_times = Solver.stage_times
 
@@ -316,6 +343,28 @@ class SparseSolver:
         check(lib().omm_get_pattern(self._h, which, C.c_void_p(rp.ctypes.data), C.c_void_p(col.ctypes.data)),
               "omm_get_pattern")
         return rp, col[:nnz]
+
+
+def batch_solve(solvers, W0s=None, tol: float = 1e-10):
+    """Minimise several handles together (omm_batch_solve); returns (E, iters, status) arrays."""
+    k = len(solvers)
+    hs = (C.c_void_p * k)(*[s._h.value for s in solvers])
+    if W0s is None:
+        w = None
+        on_dev = 0
+    else:
+        ptrs = [_ptr(a) for a in W0s]
+        on = {d for p, d in ptrs if p is not None}
+        if len(on) > 1:
+            raise ValueError("W0s must be all host or all device arrays")
+        on_dev = on.pop() if on else 0
+        w = (C.c_void_p * k)(*[p.value if p is not None else None for p, _ in ptrs])
+    E = np.zeros(k)
+    it = np.zeros(k, dtype=np.int32)
+    st = np.zeros(k, dtype=np.int32)
+    lib().omm_batch_solve(hs, k, w, on_dev, float(tol), C.c_void_p(E.ctypes.data), C.c_void_p(it.ctypes.data),
+                          C.c_void_p(st.ctypes.data))
+    return E, it, st
 
 
 # ---------------------------------------------------------------- op-level calls
