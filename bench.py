@@ -401,6 +401,116 @@ def run_profile(args):
     solver.close()
 
 
+# ---------------------------------------------------------------- C4: batched uneven solves
+def run_c4(args):
+    import torch
+    from paper_2209_05934_gb300 import omm
+
+    omm.lib()
+    count = args.batch
+    sizes = synth.batch_sizes(count, seed=4, lo=32, hi=384)
+    systems = [synth.make_batch_system(int(N), seed=4000 + i) for i, N in enumerate(sizes)]
+    dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
+    data = [(dev(s.dense_H()), dev(s.dense_S()), dev(s.W0_dense())) for s in systems]
+    solvers = [omm.Solver(s.m, s.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6) for s in systems]
+
+    def batch_step():
+        for sv, (H, S, _) in zip(solvers, data):
+            sv.set_HS(H, S)
+        return omm.batch_solve(solvers, [d[2] for d in data], tol=1e-10)
+
+    def serial_step():
+        out = []
+        for sv, (H, S, W0) in zip(solvers, data):
+            sv.set_HS(H, S)
+            out.append(sv.solve(W0, tol=1e-10, raise_on_error=False))
+        return out
+
+    for _ in range(args.warmup):
+        batch_step()
+    torch.cuda.synchronize()
+    launches0 = omm.kernel_launches()
+    t0 = time.perf_counter()
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            E, it, st = batch_step()
+        torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / args.steps
+    launches = omm.kernel_launches() - launches0
+    t0 = time.perf_counter()
+    serial = serial_step()
+    torch.cuda.synchronize()
+    t_serial = time.perf_counter() - t0
+    same = all(serial[i][0] == E[i] and serial[i][1] == it[i] for i in range(count))
+    line = {"metric": "OMM solves/s, batched uneven systems", "value": count / t_batch, "unit": "solves/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split+f64",
+            "data": "synthetic",
+            "config": {"workload": (f"{count} dense systems, atoms round(exp(U(ln 32, ln 384))) (seed 4): "
+                                    f"m {int(min(s.m for s in systems))}..{int(max(s.m for s in systems))}, n = m/4"),
+                       "precision": "mixed", "tol": 1e-10, "orth_tol": 1e-6,
+                       "execution": "one handle per system on its own stream, driven together"},
+            "one_by_one": {"value": count / t_serial, "unit": "solves/s", "ms": 1e3 * t_serial},
+            "results_equal_alone": bool(same), "all_ok": bool((st == omm.OK).all()),
+            "iters": {"min": int(it.min()), "max": int(it.max())},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    for sv in solvers:
+        sv.close()
+
+
+# ---------------------------------------------------------------- C5: serving
+def run_c5(args):
+    import torch
+    from paper_2209_05934_gb300 import omm, serving
+
+    omm.lib()
+    rng = np.random.Generator(np.random.PCG64(5))
+    seqs = []
+    for i in range(args.sequences):
+        side = int(rng.choice([4, 5, 6, 8]))          # 64..512 atoms: m = 512..4096
+        seqs.append(synth.make_system(side, seed=5000 + i))
+    dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
+    base = [(dev(s.dense_H()), dev(s.dense_S()), dev(s.W0_dense()), dev((s.dense_H() != 0).astype(np.float64)))
+            for s in seqs]
+
+    def make_inputs_factory(i):
+        H0, S, _, mask = base[i]
+
+        def make(k):
+            if k == 0:
+                return H0, S
+            g = torch.Generator(device="cuda")
+            g.manual_seed(10_000 * i + k)
+            noise = torch.randn(H0.shape, generator=g, device="cuda", dtype=torch.float64) * 1e-3
+            noise = 0.5 * (noise + noise.T) * mask
+            return (H0 + noise).T.contiguous().T, S
+        return make
+
+    out = {"metric": "OMM serving: solves/s and p50/p99 time-to-converge", "unit": "solves/s", "n_gpus": 1,
+           "data": "synthetic", "higher_is_better": True, "dtype": "bf16-split+f64",
+           "config": {"workload": (f"{args.sequences} sequences per rate, each 1 + {args.scf_steps - 1} SCF-like "
+                                   "perturbations H <- H + sym(N(0, 1e-3)) on the nonzeros, warm-started; "
+                                   "dense m in {512, 1000, 1728, 4096}, n = m/4"),
+                      "precision": "mixed", "tol": 1e-10, "orth_tol": 1e-6}, "rates": []}
+    for rate in args.rates:
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(seqs)))
+        arrivals -= arrivals[0]
+        reqs = [serving.Request(rid=i, arrival=float(arrivals[i]), m=seqs[i].m, n=seqs[i].n, steps=args.scf_steps,
+                                make_inputs=make_inputs_factory(i), W0=base[i][2]) for i in range(len(seqs))]
+        server = serving.Server(hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)))
+        t0 = time.perf_counter()
+        recs = server.run(reqs)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st = serving.latency_stats(recs)
+        out["rates"].append({"rate_seq_per_s": rate, "solves": st["solves"], "solves_per_s": st["solves"] / wall,
+                             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_inflight": server.max_inflight,
+                             "all_ok": all(r.status == omm.OK for r in recs)})
+    out["value"] = max(r["solves_per_s"] for r in out["rates"])
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,14 +521,26 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run one solve only (for ncu captures); prints stage times, no benchmark line")
     ap.add_argument("--max-iter", type=int, default=0, help="with --profile: cap on CG steps")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3"],
-                    help="with --profile: c2 dense workload (default) or c3 linear-scaling workload")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2 dense workload (default); c3 linear-scaling (with --profile); "
+                         "c4 batched uneven solves; c5 serving loop")
+    ap.add_argument("--batch", type=int, default=64, help="c4: number of systems")
+    ap.add_argument("--sequences", type=int, default=12, help="c5: sequences per arrival rate")
+    ap.add_argument("--scf-steps", type=int, default=11, help="c5: solves per sequence (1 + perturbations)")
+    ap.add_argument("--rates", type=float, nargs="+", default=[10.0, 50.0, 200.0], help="c5: arrivals per second")
+    ap.add_argument("--hbm-budget-gb", type=float, default=200.0, help="c5: admission budget")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
         return
     if args.warmup < 3:
         args.warmup = 3
+    if args.config == "c4":
+        run_c4(args)
+        return
+    if args.config == "c5":
+        run_c5(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
