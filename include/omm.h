@@ -24,7 +24,9 @@
  *     keeps and never frees caller memory;
  *   - "stream" arguments are cudaStream_t values passed as void*; NULL means
  *     the legacy default stream for op-level calls and a library-owned stream
- *     for handles.
+ *     for handles.  A library-owned stream is non-blocking: device inputs must
+ *     be complete before a call that reads them (synchronize the stream that
+ *     produced them, or pass that stream in omm_options.stream).
  * A handle is not thread-safe: one host thread at a time per handle.
  */
 #ifndef OMM_GB300_H
