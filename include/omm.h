@@ -87,7 +87,11 @@ typedef struct {
     int32_t eta_auto;      /* 1 (default): eta = Gershgorin upper bound of the spectrum,
                               which makes every line-search quartic bounded below */
     int32_t precision;     /* OMM_PREC_FP64 (default) or OMM_PREC_MIXED (dense only) */
-    int32_t cholesky;      /* 1: Cholesky-reduced variant (dense only), S = L L^T */
+    int32_t cholesky;      /* 1: Cholesky-reduced variant (dense only, either precision):
+                              S = L L^T, the CG runs on W~ = L^T W with H~ = L^-1 H' L^-T and
+                              overlap I; W_out (and OMM_ARRAY_W after omm_solve_end) is
+                              mapped back with W = L^-T W~; the other arrays describe the
+                              reduced problem */
     int32_t max_iter;      /* CG step limit, default 10000 */
     double orth_tol;       /* > 0: also require ||W^T S W - I||_F < orth_tol to stop */
     double filter_eps;     /* block filtering threshold, default 1e-8 (sparse form): an
@@ -197,7 +201,10 @@ int omm_get_diag(omm_handle *h, omm_diag *d);
 /*
  * Copy one internal m x n or n x n FP64 array of the handle (for inspection
  * and tests).  which: 0 W, 1 H'W, 2 S W, 3 G, 4 D, 5 H_W (n x n), 6 S_W (n x n).
- * Dense only; dst is host memory unless on_device.
+ * dst is host memory unless on_device.  With the Cholesky variant, 0 is W in
+ * the original basis (after omm_solve_end) and 1..6 belong to the reduced
+ * problem (H~, I, W~).  Sparse handles return the block values of the
+ * corresponding patterns.
  */
 int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device);
 

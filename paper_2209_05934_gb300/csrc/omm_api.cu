@@ -19,6 +19,7 @@
 #include <new>
 #include <vector>
 
+#include "chol.cuh"
 #include "omm_internal.cuh"
 #include "sparse.cuh"
 #include "tc_exact.cuh"
@@ -74,6 +75,8 @@ struct omm_handle {
     int chunk = 8;
     MixedBufs mx;
     ExactBufs ex;
+    double *L = nullptr;      // Cholesky variant: factor of S (m x m)
+    double *Wsave = nullptr;  // Cholesky variant: W in the original basis (m x n)
     int phase = 0;            // PH_* of the asynchronous driver
     int k_mixed = 0;          // CG steps of the split-precision phase
     int status = OMM_OK;      // status of the finished solve
@@ -135,6 +138,8 @@ void free_handle(omm_handle *h) {
     cudaFree(h->ex.SWHWx);
     cudaFree(h->ex.HSWx);
     cudaFree(h->ex.e);
+    cudaFree(h->L);
+    cudaFree(h->Wsave);
     omm::sp::release(h->sd);
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -658,7 +663,7 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         delete h;
         return OMM_ERR_ARG;
     }
-    if (h->opt.cholesky != 0 || (h->opt.precision != OMM_PREC_FP64 && h->opt.precision != OMM_PREC_MIXED)) {
+    if (h->opt.precision != OMM_PREC_FP64 && h->opt.precision != OMM_PREC_MIXED) {
         delete h;
         return OMM_ERR_UNSUPPORTED;
     }
@@ -708,6 +713,11 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         free_handle(h);
         return rc;
     }
+    if (!h->sparse && h->opt.cholesky &&
+        ((rc = dalloc(&h->L, (size_t)(m * m))) || (rc = dalloc(&h->Wsave, (size_t)mn)))) {
+        free_handle(h);
+        return rc;
+    }
     if (h->opt.precision == OMM_PREC_MIXED && h->opt.refine == OMM_REFINE_EXACT && (rc = exact_alloc(h))) {
         free_handle(h);
         return rc;
@@ -731,8 +741,10 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
 
 int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_device) {
     if (h == nullptr || H == nullptr || S == nullptr) return OMM_ERR_ARG;
+    if (h->phase != PH_IDLE && h->phase != PH_FINISHED) return OMM_ERR_STATE;
     const int64_t m = h->m, mm = m * m;
     cudaStream_t st = h->stream;
+    h->have_HS = false;   // set again only when this setup succeeds
     OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
     if (h->sparse) {
         omm::DevState init{};
@@ -775,6 +787,7 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
         if (h->opt.eta_auto)
             TRY(omm::launch_gershgorin(m, h->HS, h->HS + mm, scr(h, 3), ctr(h, 3), h->dstate, st));
         TRY(omm::launch_shift(mm, h->HS, h->HS + mm, h->HS, h->dstate, st));
+        if (h->opt.cholesky) TRY(omm::chol::reduce_standard(h->HS, h->HS + mm, h->L, m, h->dstate, st));
     }
     if (h->opt.precision == OMM_PREC_MIXED) {
         // columns of [H' | S] become the K-major rows of the A operand (symmetric)
@@ -805,9 +818,21 @@ int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, doubl
     const int64_t n = h->n;
     cudaStream_t st = h->stream;
     OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
-    if (W0 != nullptr)
+    if (h->opt.cholesky && !h->sparse) {
+        // W~ = L^T W: W0, or the previous solution kept in the original basis
+        if (W0 != nullptr)
+            OMM_CUDA_TRY(cudaMemcpyAsync(h->Wsave, W0, w_len(h) * sizeof(double),
+                                         W0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        omm::GemmBatch b{};
+        b.A[0] = h->L;
+        b.B[0] = h->Wsave;
+        b.C[0] = h->WD;
+        StageTimer t(h, OMM_STAGE_SETUP);
+        TRY(omm::dgemm_batched(true, false, h->m, h->n, h->m, 1.0, b, 1, h->m, h->m, 0.0, h->m, h->m, nullptr, st));
+    } else if (W0 != nullptr) {
         OMM_CUDA_TRY(cudaMemcpyAsync(w_dev(h), W0, w_len(h) * sizeof(double),
                                      W0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    }
     omm::DevState init{};
     init.eta = h->diag.eta;
     init.tol = tol;
@@ -903,8 +928,15 @@ int omm_solve_end(omm_handle *h, double *W_out, int32_t W_out_on_device, double 
     if (h == nullptr) return OMM_ERR_ARG;
     if (h->phase != PH_FINISHED) return OMM_ERR_STATE;
     cudaStream_t st = h->stream;
+    const double *Wres = w_dev(h);
+    if (h->opt.cholesky && !h->sparse) {
+        // W = L^-T W~, kept for warm starts in the original basis
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->Wsave, h->WD, w_len(h) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        TRY(omm::chol::trsm_llt(h->L, h->m, h->Wsave, h->m, h->n, st));
+        Wres = h->Wsave;
+    }
     if (W_out != nullptr)
-        OMM_CUDA_TRY(cudaMemcpyAsync(W_out, w_dev(h), w_len(h) * sizeof(double),
+        OMM_CUDA_TRY(cudaMemcpyAsync(W_out, Wres, w_len(h) * sizeof(double),
                                      W_out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
     const omm::DevState &s = *h->hstate;
@@ -1012,7 +1044,7 @@ int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device) 
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaStream_t st = h->stream;
     switch (which) {
-        case 0: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->WD, mn * 8, kind, st)); break;
+        case 0: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->opt.cholesky ? h->Wsave : h->WD, mn * 8, kind, st)); break;
         case 1: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->SWHW + mn, mn * 8, kind, st)); break;
         case 2: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->SWHW, mn * 8, kind, st)); break;
         case 3: OMM_CUDA_TRY(cudaMemcpyAsync(dst, h->G, mn * 8, kind, st)); break;
