@@ -207,7 +207,7 @@ def run_omm(args):
     Wout = torch.zeros((n, m), dtype=torch.float64, device="cuda").T
     stream = torch.cuda.current_stream()
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
-                orth_tol=TOL[prec]["orth_tol"], stream=stream.cuda_stream)
+                orth_tol=TOL[prec]["orth_tol"], stream=stream.cuda_stream, cholesky=int(args.cholesky))
     solver = omm.Solver(m, n, 8, **opts)
     tol = TOL[prec]["tol"]
 
@@ -289,7 +289,8 @@ def run_omm(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else "bf16-split+f64",
         "data": "synthetic",
-        "config": {"workload": workload_name(sysm), "precision": prec, "tol": tol,
+        "config": {"workload": workload_name(sysm) + (" cholesky-reduced" if args.cholesky else ""),
+                   "precision": prec, "tol": tol, "cholesky": bool(args.cholesky),
                    "refine": "exact-digit tensor cores" if prec == "mixed" else None,
                    "orth_tol": TOL[prec]["orth_tol"], "parallelism": f"replicas x{ws}",
                    "l2": "working set (H, S = 256 MiB, plus W/D/products) exceeds the 129 MB L2"},
@@ -385,7 +386,8 @@ def run_profile(args):
     H, S, W0 = dev(sysm.dense_H()), dev(sysm.dense_S()), dev(sysm.W0_dense())
     prec = args.precision
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
-                orth_tol=TOL[prec]["orth_tol"], stream=torch.cuda.current_stream().cuda_stream)
+                orth_tol=TOL[prec]["orth_tol"], stream=torch.cuda.current_stream().cuda_stream,
+                cholesky=int(args.cholesky))
     if args.max_iter > 0:
         opts["max_iter"] = args.max_iter
     solver = omm.Solver(sysm.m, sysm.n, 8, **opts)
@@ -527,6 +529,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run one solve only (for ncu captures); prints stage times, no benchmark line")
     ap.add_argument("--max-iter", type=int, default=0, help="with --profile: cap on CG steps")
+    ap.add_argument("--cholesky", action="store_true",
+                    help="c2: Cholesky-reduced variant (S = L L^T factored inside each step's setup)")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2 dense workload (default); c3 linear-scaling (with --profile); "
                          "c4 batched uneven solves; c5 serving loop")

@@ -154,6 +154,17 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
 int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_device);
 
 /*
+ * Replace H only (dense handles): the overlap of the last successful
+ * omm_set_HS is kept, and with the Cholesky variant so are its factor L and
+ * L^-1, so only the shift, H~ = L^-1 H' L^-T and the packing run.  This is the
+ * SCF case where the basis, hence S, is fixed and the Hamiltonian changes
+ * between solves.  The result equals omm_set_HS(h, H, S_previous) bit for bit.
+ * Returns OMM_ERR_STATE before a successful omm_set_HS or while a solve is in
+ * flight, OMM_ERR_UNSUPPORTED for sparse handles.
+ */
+int omm_set_H(omm_handle *h, const double *H, int32_t on_device);
+
+/*
  * Minimise from W0 (m x n column-major; sparse: 8x2-style block values in the
  * W pattern's order) to the RelTol criterion of Table 1:
  *     |2 (E_k - E_{k-1}) / (E_k + E_{k-1})| < tol   at k >= 1,

@@ -6,15 +6,31 @@
 namespace omm {
 namespace chol {
 
+constexpr int kChunkK = 512;  // K chunk of the W transforms
+
+// Device workspace of one handle: the digit planes of the exact-digit GEMMs
+// (bytes) and Y = L^-1 (Linv, m x m column-major, zero above the diagonal).
+struct Work {
+    void *ws = nullptr;
+    int64_t bytes = 0;
+    int s = 7;               // digits of the exact-digit GEMM
+    double *Linv = nullptr;
+};
+
+int64_t work_bytes(int64_t m, int64_t n, int s);
+int64_t linv_elems(int64_t m);
+
 // In place: lower triangle of A (column-major m x m, ld m) <- L with A = L L^T;
-// strict upper triangle zeroed; state->status = OMM_ERR_NOT_SPD on a bad pivot.
-int cholesky(double *A, int64_t m, DevState *state, cudaStream_t st);
-// B (m x nrhs, ld ldb) <- L^-1 B
-int trsm_ll(const double *L, int64_t m, double *B, int64_t ldb, int64_t nrhs, cudaStream_t st);
-// Hs <- L^-1 Hs L^-T (symmetrised), S <- I, L <- Cholesky factor of S (m x m each)
-int reduce_standard(double *Hs, double *S, double *L, int64_t m, DevState *state, cudaStream_t st);
-// B <- L^-T B
-int trsm_llt(const double *L, int64_t m, double *B, int64_t ldb, int64_t nrhs, cudaStream_t st);
+// strict upper triangle zeroed; w.Linv <- L^-1; state->status = OMM_ERR_NOT_SPD
+// on a non-positive pivot.
+int cholesky(double *A, int64_t m, const Work &w, DevState *state, cudaStream_t st);
+// Wt (m x n, ld m) <- T^T W for a lower-triangular T: W~ = L^T W with T = L,
+// W = L^-T W~ with T = L^-1
+int lt_times(const double *T, int64_t m, const double *W, double *Wt, int64_t n, const Work &w, cudaStream_t st);
+// L <- Cholesky factor of S, w.Linv <- L^-1 (m x m each)
+int factor(const double *S, double *L, int64_t m, const Work &w, DevState *state, cudaStream_t st);
+// Hs <- L^-1 Hs L^-T (symmetrised) with L^-1 from factor(); T (m x m scratch) <- I
+int transform(double *Hs, double *T, int64_t m, const Work &w, cudaStream_t st);
 
 }  // namespace chol
 }  // namespace omm

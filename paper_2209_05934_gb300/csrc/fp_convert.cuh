@@ -44,4 +44,40 @@ __device__ __forceinline__ double sw_f2d(float x) {
     return __longlong_as_double((long long)(sign | ((uint64_t)(e - 127 + 1023) << 52) | (m << 29)));
 }
 
+// v * 2^e2 for a 64-bit integer v, rounded to nearest (ties to even); the
+// caller keeps the result in the normal range (|v| 2^e2 between 2^-1000 and
+// 2^1000).
+__device__ __forceinline__ double sw_i64_scaled(int64_t v, int e2) {
+    if (v == 0) return 0.0;
+    const uint64_t sign = v < 0 ? (1ull << 63) : 0ull;
+    const uint64_t a = v < 0 ? (0ull - (uint64_t)v) : (uint64_t)v;
+    int p = 63 - __clzll((long long)a);                        // position of the leading one
+    uint64_t q;
+    if (p <= 52) {
+        q = a << (52 - p);
+    } else {
+        const int sh = p - 52;
+        q = a >> sh;
+        const uint64_t rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (q & 1ull))) {
+            q += 1ull;
+            if (q >> 53) {
+                q >>= 1;
+                ++p;
+            }
+        }
+    }
+    return __longlong_as_double((long long)(sign | ((uint64_t)(1023 + p + e2) << 52) | (q & 0xFFFFFFFFFFFFFull)));
+}
+
+// x * 2^e by an exponent add when x and the result are normal; other cases
+// (zero, subnormal, overflow, non-finite) go through ldexp.
+__device__ __forceinline__ double sw_scale2(double x, int e) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int be = (int)((b >> 52) & 0x7FF);
+    const int ne = be + e;
+    if (be == 0 || be == 0x7FF || ne <= 0 || ne >= 0x7FF) return ldexp(x, e);
+    return __longlong_as_double((long long)((b & ~(0x7FFull << 52)) | ((uint64_t)ne << 52)));
+}
+
 }  // namespace omm

@@ -70,6 +70,7 @@ struct omm_handle {
     omm::DevState *dstate = nullptr;
     omm::DevState *hstate = nullptr;   // pinned
     bool have_HS = false, have_W = false;
+    bool have_S = false;      // a successful dense setup left S (and the Cholesky factor) in place
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     omm_diag diag{};
     int chunk = 8;
@@ -77,6 +78,8 @@ struct omm_handle {
     ExactBufs ex;
     double *L = nullptr;      // Cholesky variant: factor of S (m x m)
     double *Wsave = nullptr;  // Cholesky variant: W in the original basis (m x n)
+    double *S0 = nullptr;     // Cholesky variant: the original S (its slot holds I)
+    omm::chol::Work cw;       // Cholesky variant: GEMM workspace and inverted diagonal blocks
     int phase = 0;            // PH_* of the asynchronous driver
     int k_mixed = 0;          // CG steps of the split-precision phase
     int status = OMM_OK;      // status of the finished solve
@@ -140,6 +143,9 @@ void free_handle(omm_handle *h) {
     cudaFree(h->ex.e);
     cudaFree(h->L);
     cudaFree(h->Wsave);
+    cudaFree(h->S0);
+    cudaFree(h->cw.ws);
+    cudaFree(h->cw.Linv);
     omm::sp::release(h->sd);
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -194,6 +200,10 @@ double *scr(omm_handle *h, int i) {
 
 // One CG step of the dense FP64 form (products, contractions, line search,
 // update, energy + convergence, gradient, direction).
+// Cholesky variant: the overlap of the reduced problem is I, so S D = D and
+// S W = W are copies, not products.
+bool s_identity(const omm_handle *h) { return h->opt.cholesky != 0 && !h->sparse; }
+
 int dense_iteration(omm_handle *h) {
     const int64_t m = h->m, n = h->n, mn = m * n;
     cudaStream_t st = h->stream;
@@ -202,7 +212,12 @@ int dense_iteration(omm_handle *h) {
     // H'D and S D
     b.A[0] = h->HS;          b.B[0] = h->WD + mn; b.C[0] = h->HDSD;      b.Cin[0] = nullptr;
     b.A[1] = h->HS + m * m;  b.B[1] = h->WD + mn; b.C[1] = h->HDSD + mn; b.Cin[1] = nullptr;
-    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(omm::dgemm_batched(false, false, m, n, m, 1.0, b, 2, m, m, 0.0, m, m, s, st)); }
+    {
+        StageTimer t(h, OMM_STAGE_PRODUCTS);
+        TRY(omm::dgemm_batched(false, false, m, n, m, 1.0, b, s_identity(h) ? 1 : 2, m, m, 0.0, m, m, s, st));
+        if (s_identity(h))
+            OMM_CUDA_TRY(cudaMemcpyAsync(h->HDSD + mn, h->WD + mn, mn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
     // Z = [W D]^T [H'D SD]
     omm::GemmBatch z{};
     z.A[0] = h->WD; z.B[0] = h->HDSD; z.C[0] = h->Z;
@@ -233,9 +248,11 @@ int dense_start(omm_handle *h) {
     omm::DevState *s = h->dstate;
     omm::GemmBatch b{};
     // SW = S W, H'W = H' W
-    b.A[0] = h->HS + m * m; b.B[0] = h->WD; b.C[0] = h->SWHW;
-    b.A[1] = h->HS;         b.B[1] = h->WD; b.C[1] = h->SWHW + mn;
-    TRY(omm::dgemm_batched(false, false, m, n, m, 1.0, b, 2, m, m, 0.0, m, m, s, st));
+    b.A[0] = h->HS;         b.B[0] = h->WD; b.C[0] = h->SWHW + mn;
+    b.A[1] = h->HS + m * m; b.B[1] = h->WD; b.C[1] = h->SWHW;
+    TRY(omm::dgemm_batched(false, false, m, n, m, 1.0, b, s_identity(h) ? 1 : 2, m, m, 0.0, m, m, s, st));
+    if (s_identity(h))
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->SWHW, h->WD, mn * sizeof(double), cudaMemcpyDeviceToDevice, st));
     // H_W = W^T H'W, S_W = W^T S W
     omm::GemmBatch c{};
     c.A[0] = h->WD; c.B[0] = h->SWHW + mn; c.C[0] = h->h0s0;
@@ -342,7 +359,20 @@ int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_s
     a.dplane = 2 * n * x.ldm;
     a.dout_step = dout_step * x.ldm;
     a.ndig = kDig;
-    return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, kBN, h->stream);
+    if (!s_identity(h)) return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, kBN, h->stream);
+    TRY(omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 1, kBN, h->stream));
+    // z = 1 (S times the B rows) is the B rows themselves: their FP32/FP64 values and digits
+    const int64_t mn = m * n;
+    if (C32 != nullptr)   // iteration: S D = D
+        OMM_CUDA_TRY(cudaMemcpyAsync(C32 + c_step, x.D32, mn * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    else                  // start: S W = W
+        OMM_CUDA_TRY(cudaMemcpyAsync(C + c_step, h->WD + b_row0 * m, mn * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     h->stream));
+    const size_t pitch = (size_t)(2 * n * x.ldm) * sizeof(__nv_bfloat16);
+    OMM_CUDA_TRY(cudaMemcpy2DAsync(x.HDSDd + (dout_row0 + dout_step) * x.ldm, pitch, x.WDd + b_row0 * x.ldm, pitch,
+                                   (size_t)(n * x.ldm) * sizeof(__nv_bfloat16), kDig, cudaMemcpyDeviceToDevice,
+                                   h->stream));
+    return OMM_OK;
 }
 
 // Z = [W D]^T [H'D SD]
@@ -459,7 +489,9 @@ int exact_anchor(omm_handle *h) {
         a.eA = e.eHS;
         a.eA_step = m;
         a.eB = e.eW;
-        TRY(omm::tc::exact_gemm(e.mapHS_A, e.mapW, a, 2, st));
+        TRY(omm::tc::exact_gemm(e.mapHS_A, e.mapW, a, s_identity(h) ? 1 : 2, st));
+        if (s_identity(h))
+            OMM_CUDA_TRY(cudaMemcpyAsync(h->SWHW, h->WD, mn * sizeof(double), cudaMemcpyDeviceToDevice, st));
         TRY(omm::tc::exact_pack(true, m, n, h->SWHW + mn, m, e.eHWSW, e.HWSWx, x.ldm, 2 * n * x.ldm, e.s, s, st));
         TRY(omm::tc::exact_pack(true, m, n, h->SWHW, m, e.eHWSW + n, e.HWSWx + n * x.ldm, x.ldm, 2 * n * x.ldm, e.s,
                                 s, st));
@@ -600,6 +632,62 @@ int enqueue_chunk(omm_handle *h) {
     return OMM_OK;
 }
 
+// Dense setup for omm_set_HS (S given) and omm_set_H (S == nullptr: the
+// previous S, and with the Cholesky variant its factor, are kept).
+int dense_set(omm_handle *h, const double *H, const double *S, bool on_device) {
+    const int64_t m = h->m, mm = m * m;
+    cudaStream_t st = h->stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const bool chol = h->opt.cholesky != 0;
+    // S goes to its slot (kept by omm_set_H; with the Cholesky variant restored
+    // from its copy, since the slot then holds I); H is staged in the H' slot
+    // and shifted in place
+    if (S != nullptr) {
+        h->have_S = false;
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->HS + mm, S, mm * sizeof(double), kind, st));
+        if (chol) OMM_CUDA_TRY(cudaMemcpyAsync(h->S0, h->HS + mm, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else if (chol) {
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->HS + mm, h->S0, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->HS, H, mm * sizeof(double), kind, st));
+    omm::DevState init{};
+    init.eta = h->opt.eta;
+    *h->hstate = init;
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
+    {
+        StageTimer t(h, OMM_STAGE_SETUP);
+        if (h->opt.eta_auto)
+            TRY(omm::launch_gershgorin(m, h->HS, h->HS + mm, scr(h, 3), ctr(h, 3), h->dstate, st));
+        TRY(omm::launch_shift(mm, h->HS, h->HS + mm, h->HS, h->dstate, st));
+        if (chol) {
+            if (S != nullptr) TRY(omm::chol::factor(h->HS + mm, h->L, m, h->cw, h->dstate, st));
+            TRY(omm::chol::transform(h->HS, h->HS + mm, m, h->cw, st));
+        }
+    }
+    if (h->opt.precision == OMM_PREC_MIXED) {
+        // columns of [H' | S] become the K-major rows of the A operand (symmetric);
+        // omm_set_H and the Cholesky variant's S = I repack H' only
+        StageTimer t(h, OMM_STAGE_PACK);
+        const int64_t cols = (S == nullptr || s_identity(h)) ? m : 2 * m;
+        TRY(omm::tc::pack_cm(m, cols, h->HS, m, h->mx.HSd, h->mx.ldm, 2 * m * h->mx.ldm, kDig, nullptr, st));
+        if (h->opt.refine == OMM_REFINE_EXACT)
+            TRY(omm::tc::exact_pack(true, m, cols, h->HS, m, h->ex.eHS, h->ex.HSx, h->mx.ldm, 2 * m * h->mx.ldm,
+                                    h->ex.s, nullptr, st));
+    }
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    harvest_stage_times(h);
+    if (h->hstate->status != OMM_OK) return h->hstate->status;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    h->diag.t_setup_ms = ms;
+    h->diag.eta = h->hstate->eta;
+    h->have_HS = true;
+    h->have_S = true;
+    return OMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -713,10 +801,16 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         free_handle(h);
         return rc;
     }
-    if (!h->sparse && h->opt.cholesky &&
-        ((rc = dalloc(&h->L, (size_t)(m * m))) || (rc = dalloc(&h->Wsave, (size_t)mn)))) {
-        free_handle(h);
-        return rc;
+    if (!h->sparse && h->opt.cholesky) {
+        h->cw.s = h->opt.exact_digits;
+        h->cw.bytes = omm::chol::work_bytes(m, n, h->cw.s);
+        if ((rc = dalloc(&h->L, (size_t)(m * m))) || (rc = dalloc(&h->Wsave, (size_t)mn)) ||
+            (rc = dalloc(&h->S0, (size_t)(m * m))) ||
+            (rc = dalloc(&h->cw.Linv, (size_t)omm::chol::linv_elems(m))) ||
+            (cudaMalloc(&h->cw.ws, (size_t)h->cw.bytes) != cudaSuccess ? (rc = OMM_ERR_NOMEM) : 0)) {
+            free_handle(h);
+            return rc;
+        }
     }
     if (h->opt.precision == OMM_PREC_MIXED && h->opt.refine == OMM_REFINE_EXACT && (rc = exact_alloc(h))) {
         free_handle(h);
@@ -742,7 +836,6 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
 int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_device) {
     if (h == nullptr || H == nullptr || S == nullptr) return OMM_ERR_ARG;
     if (h->phase != PH_IDLE && h->phase != PH_FINISHED) return OMM_ERR_STATE;
-    const int64_t m = h->m, mm = m * m;
     cudaStream_t st = h->stream;
     h->have_HS = false;   // set again only when this setup succeeds
     OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
@@ -774,40 +867,17 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
         h->have_HS = true;
         return OMM_OK;
     }
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    // S goes to its slot; H is staged in the H' slot and shifted in place
-    OMM_CUDA_TRY(cudaMemcpyAsync(h->HS + mm, S, mm * sizeof(double), kind, st));
-    OMM_CUDA_TRY(cudaMemcpyAsync(h->HS, H, mm * sizeof(double), kind, st));
-    omm::DevState init{};
-    init.eta = h->opt.eta;
-    *h->hstate = init;
-    OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
-    {
-        StageTimer t(h, OMM_STAGE_SETUP);
-        if (h->opt.eta_auto)
-            TRY(omm::launch_gershgorin(m, h->HS, h->HS + mm, scr(h, 3), ctr(h, 3), h->dstate, st));
-        TRY(omm::launch_shift(mm, h->HS, h->HS + mm, h->HS, h->dstate, st));
-        if (h->opt.cholesky) TRY(omm::chol::reduce_standard(h->HS, h->HS + mm, h->L, m, h->dstate, st));
-    }
-    if (h->opt.precision == OMM_PREC_MIXED) {
-        // columns of [H' | S] become the K-major rows of the A operand (symmetric)
-        StageTimer t(h, OMM_STAGE_PACK);
-        TRY(omm::tc::pack_cm(m, 2 * m, h->HS, m, h->mx.HSd, h->mx.ldm, 2 * m * h->mx.ldm, kDig, nullptr, st));
-        if (h->opt.refine == OMM_REFINE_EXACT)
-            TRY(omm::tc::exact_pack(true, m, 2 * m, h->HS, m, h->ex.eHS, h->ex.HSx, h->mx.ldm, 2 * m * h->mx.ldm,
-                                    h->ex.s, nullptr, st));
-    }
-    OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
-    OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
-    OMM_CUDA_TRY(cudaStreamSynchronize(st));
-    harvest_stage_times(h);
-    if (h->hstate->status != OMM_OK) return h->hstate->status;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-    h->diag.t_setup_ms = ms;
-    h->diag.eta = h->hstate->eta;
-    h->have_HS = true;
-    return OMM_OK;
+    return dense_set(h, H, S, on_device != 0);
+}
+
+int omm_set_H(omm_handle *h, const double *H, int32_t on_device) {
+    if (h == nullptr || H == nullptr) return OMM_ERR_ARG;
+    if (h->sparse) return OMM_ERR_UNSUPPORTED;
+    if (h->phase != PH_IDLE && h->phase != PH_FINISHED) return OMM_ERR_STATE;
+    if (!h->have_S) return OMM_ERR_STATE;
+    h->have_HS = false;
+    OMM_CUDA_TRY(cudaEventRecord(h->ev0, h->stream));
+    return dense_set(h, H, nullptr, on_device != 0);
 }
 
 int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, double tol) {
@@ -823,12 +893,8 @@ int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, doubl
         if (W0 != nullptr)
             OMM_CUDA_TRY(cudaMemcpyAsync(h->Wsave, W0, w_len(h) * sizeof(double),
                                          W0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        omm::GemmBatch b{};
-        b.A[0] = h->L;
-        b.B[0] = h->Wsave;
-        b.C[0] = h->WD;
         StageTimer t(h, OMM_STAGE_SETUP);
-        TRY(omm::dgemm_batched(true, false, h->m, h->n, h->m, 1.0, b, 1, h->m, h->m, 0.0, h->m, h->m, nullptr, st));
+        TRY(omm::chol::lt_times(h->L, h->m, h->Wsave, h->WD, h->n, h->cw, st));
     } else if (W0 != nullptr) {
         OMM_CUDA_TRY(cudaMemcpyAsync(w_dev(h), W0, w_len(h) * sizeof(double),
                                      W0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -931,8 +997,7 @@ int omm_solve_end(omm_handle *h, double *W_out, int32_t W_out_on_device, double 
     const double *Wres = w_dev(h);
     if (h->opt.cholesky && !h->sparse) {
         // W = L^-T W~, kept for warm starts in the original basis
-        OMM_CUDA_TRY(cudaMemcpyAsync(h->Wsave, h->WD, w_len(h) * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        TRY(omm::chol::trsm_llt(h->L, h->m, h->Wsave, h->m, h->n, st));
+        TRY(omm::chol::lt_times(h->cw.Linv, h->m, h->WD, h->Wsave, h->n, h->cw, st));
         Wres = h->Wsave;
     }
     if (W_out != nullptr)

@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include "fp_convert.cuh"
 #include "omm_internal.cuh"
 #include "tc_exact.cuh"
 #include "tc_gemm.cuh"
@@ -139,7 +140,19 @@ __global__ void __launch_bounds__(192, 1)
         int32_t acc[XBN];
 #pragma unroll
         for (int j = 0; j < XBN; ++j) acc[j] = 0;
-        bool have_run = false;
+        // Running sum in tensor memory (two words per value): the integer
+        // R = sum_L acc_L 2^(7 (Lr - L)) over the levels folded so far, counted
+        // in units of level Lr, updated with integer instructions only:
+        // R <- 128 R + acc_L (Lr <- L) while a bound on |R|, the same in every
+        // thread, stays below 2^62; past that, Lr stays and a later level adds
+        // acc_L 2^-7(L - Lr) rounded to an integer.  With 7 digits and K up to
+        // 32768 every level is exact; otherwise the rounding is below 2^-47 of
+        // the scaled operands' unit, far inside an FP64 GEMM's error bound.
+        // The code stays compact on purpose: an unrolled per-element body
+        // with heavy conversions overflows the instruction cache.
+        int mode = 0;           // 0 empty, 1 growing, 2 fixed units
+        int lvl_r = 0;          // level whose units R counts in
+        double bound = 0.0;     // bound on |R|
         bool alive = true;
         for (int u = 0; u < nunits; ++u) {
             const int p = u / nchunks, c = u % nchunks;
@@ -149,12 +162,26 @@ __global__ void __launch_bounds__(192, 1)
             alive = got;
             tc_fence_after();
             if (got) {
+                // four 16-column loads in flight per wait
 #pragma unroll
-                for (int c0 = 0; c0 < XBN; c0 += 16) {
-                    float f[16];
-                    tmem_ld16(lane_base + (uint32_t)(b * XBN + c0), f);
+                for (int c0 = 0; c0 < XBN; c0 += 64) {
+                    uint32_t r0[16], r1[16], r2[16], r3[16];
+                    const uint32_t t = lane_base + (uint32_t)(b * XBN + c0);
+                    tmem_ld16_async(t, r0);
+                    tmem_ld16_async(t + 16, r1);
+                    tmem_ld16_async(t + 32, r2);
+                    tmem_ld16_async(t + 48, r3);
+                    tmem_wait_ld(r0);
+                    tmem_pin16(r1);
+                    tmem_pin16(r2);
+                    tmem_pin16(r3);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[c0 + j] += __float2int_rn(f[j]);
+                    for (int j = 0; j < 16; ++j) {
+                        acc[c0 + j] += __float2int_rn(__uint_as_float(r0[j]));
+                        acc[c0 + 16 + j] += __float2int_rn(__uint_as_float(r1[j]));
+                        acc[c0 + 32 + j] += __float2int_rn(__uint_as_float(r2[j]));
+                        acc[c0 + 48 + j] += __float2int_rn(__uint_as_float(r3[j]));
+                    }
                 }
             }
             tc_fence_before();
@@ -163,59 +190,87 @@ __global__ void __launch_bounds__(192, 1)
             const bool last_of_level =
                 c == nchunks - 1 && (p == args.npairs - 1 || args.pa[p + 1] + args.pb[p + 1] + 2 != level);
             if (last_of_level && got) {
-                // fold the level into the FP64 running sum (tensor memory, two words per value)
-                const double w = ldexp(1.0, -(7 * level - 2));
+                int np = 0;   // pairs on this level
+                for (int p2 = 0; p2 < args.npairs; ++p2) np += (args.pa[p2] + args.pb[p2] + 2 == level);
+                const double add = (double)np * (double)nchunks * 16777216.0;   // |acc| < np nchunks 2^24
+                int next = mode;
+                if (mode == 0) next = 1;
+                else if (mode == 1 && !(bound * 128.0 + add < 4.6e18)) next = 2;
+                const int sh = next == 2 ? 7 * (level - lvl_r) : 0;            // fixed units: right shift
+                const int64_t half = sh > 0 ? ((int64_t)1 << (sh - 1)) : 0;
 #pragma unroll
-                for (int c0 = 0; c0 < XBN; c0 += 8) {
-                    uint32_t r[16];
-                    if (have_run) {
-                        float f[16];
-                        tmem_ld16(lane_base + (uint32_t)(kRunCol + 2 * c0), f);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(f[j]);
+                for (int c0 = 0; c0 < XBN; c0 += 32) {
+                    uint32_t r[4][16];
+                    const uint32_t t = lane_base + (uint32_t)(kRunCol + 2 * c0);
+                    if (mode != 0) {
+                        tmem_ld16_async(t, r[0]);
+                        tmem_ld16_async(t + 16, r[1]);
+                        tmem_ld16_async(t + 32, r[2]);
+                        tmem_ld16_async(t + 48, r[3]);
+                        tmem_wait_ld(r[0]);
+                        tmem_pin16(r[1]);
+                        tmem_pin16(r[2]);
+                        tmem_pin16(r[3]);
                     }
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        double v = have_run ? __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]) : 0.0;
-                        v = fma((double)acc[c0 + j], w, v);
-                        r[2 * j] = (uint32_t)__double2loint(v);
-                        r[2 * j + 1] = (uint32_t)__double2hiint(v);
-                        acc[c0 + j] = 0;
-                    }
-                    tmem_st16(lane_base + (uint32_t)(kRunCol + 2 * c0), r);
+                    for (int g = 0; g < 4; ++g)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int64_t a = (int64_t)acc[c0 + 8 * g + j];
+                            const int64_t old = mode == 0 ? 0 : (int64_t)(((uint64_t)r[g][2 * j + 1] << 32) | r[g][2 * j]);
+                            const int64_t nv = next == 1 ? old * 128 + a : old + ((a + half) >> sh);
+                            r[g][2 * j] = (uint32_t)(uint64_t)nv;
+                            r[g][2 * j + 1] = (uint32_t)((uint64_t)nv >> 32);
+                        }
+                    tmem_st16_async(t, r[0]);
+                    tmem_st16_async(t + 16, r[1]);
+                    tmem_st16_async(t + 32, r[2]);
+                    tmem_st16_async(t + 48, r[3]);
                 }
-                have_run = true;
+                tmem_wait_st();
+#pragma unroll
+                for (int j = 0; j < XBN; ++j) acc[j] = 0;
+                if (next == 1) {
+                    bound = mode == 0 ? add : bound * 128.0 + add;
+                    lvl_r = level;
+                } else {
+                    bound += add / ldexp(1.0, sh) + 1.0;
+                }
+                mode = next;
             }
         }
-        // final: C = alpha 2^(eA + eB) run + beta Cin
-        const bool ok = __all_sync(0xffffffffu, alive && have_run);
+        // final: C = alpha 2^(eA + eB) R 2^-(7 Lr - 2) + beta Cin, one integer-op
+        // conversion per value (rolled loop: compact code)
+        const bool ok = __all_sync(0xffffffffu, alive && mode != 0);
         double *C = args.C != nullptr ? args.C + (int64_t)z * args.c_step : nullptr;
         float *C32 = args.C32 != nullptr ? args.C32 + (int64_t)z * args.c_step : nullptr;
         const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
         const int *eA = args.eA + (int64_t)z * args.eA_step;
         const int *eB = args.eB + (int64_t)z * args.eB_step;
-        const int ea = row < args.M ? eA[row] : 0;
-#pragma unroll
+        const int e_row = (row < args.M ? eA[row] : 0) - (7 * lvl_r - 2);
+#pragma unroll 1
         for (int c0 = 0; c0 < XBN; c0 += 8) {
-            double v[8];
+            uint32_t r[16];
             if (ok) {
-                float f[16];
-                tmem_ld16(lane_base + (uint32_t)(kRunCol + 2 * c0), f);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    v[j] = __hiloint2double((int)__float_as_uint(f[2 * j + 1]), (int)__float_as_uint(f[2 * j]));
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = 0.0;
+                tmem_ld16_async(lane_base + (uint32_t)(kRunCol + 2 * c0), r);
+                tmem_wait_ld(r);
             }
             if (row < args.M) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int col = n0 + c0 + j;
                     if (col >= args.N) break;
-                    double out = args.alpha * ldexp(v[j], ea + eB[col]);
+                    double out = 0.0;
+                    if (ok) {
+                        const int64_t R = (int64_t)(((uint64_t)r[2 * j + 1] << 32) | r[2 * j]);
+                        const int e = e_row + eB[col];
+                        // normal-range results by integer ops; anything else (never for
+                        // operands within 2^+-900) through ldexp
+                        out = (e > -960 && e < 900) ? sw_i64_scaled(R, e) : ldexp((double)R, e);
+                    }
+                    if (args.alpha != 1.0) out *= args.alpha;
                     if (Cin != nullptr) out = fma(args.beta, Cin[row + (int64_t)col * args.ldcin], out);
-                    if (C32 != nullptr) C32[row + (int64_t)col * args.ldc] = (float)out;
+                    if (C32 != nullptr) C32[row + (int64_t)col * args.ldc] = sw_d2f(out);
                     else C[row + (int64_t)col * args.ldc] = out;
                 }
             }

@@ -56,6 +56,7 @@ _SIGS = {
     "omm_create": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_void_p, C.POINTER(Options),
                              C.POINTER(C.c_void_p)]),
     "omm_set_HS": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "omm_set_H": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "omm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
                             C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "omm_get_diag": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
@@ -213,6 +214,12 @@ class Solver:
         if dH != dS:
             raise ValueError("H and S must both be host or both device arrays")
         return check(lib().omm_set_HS(self._h, pH, pS, dH), "omm_set_HS")
+
+    def set_H(self, H):
+        """New H with the previous S (and Cholesky factor) kept; see omm_set_H."""
+        _check_colmajor(H, self.m, self.m, "H")
+        pH, dH = _ptr(H)
+        return check(lib().omm_set_H(self._h, pH, dH), "omm_set_H")
 
     def solve(self, W0=None, tol: float = 1e-10, W_out=None, raise_on_error=True):
         if W0 is not None:

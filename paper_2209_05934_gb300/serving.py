@@ -45,6 +45,8 @@ class Request:
     tol: float = 1e-10
     precision: int = omm.PREC_MIXED
     orth_tol: float = 1e-6
+    fixed_S: bool = True                 # later solves change H only (omm_set_H keeps S)
+    cholesky: int = 0
 
 
 @dataclasses.dataclass
@@ -98,7 +100,7 @@ class Server:
         need = footprint_bytes(req.m, req.n, req.precision)
         if self.active and self.used + need > self.budget:
             return False
-        s = omm.Solver(req.m, req.n, 8, precision=req.precision, orth_tol=req.orth_tol)
+        s = omm.Solver(req.m, req.n, 8, precision=req.precision, orth_tol=req.orth_tol, cholesky=req.cholesky)
         self.used += need
         H, S = req.make_inputs(0)
         s.set_HS(H, S)
@@ -138,7 +140,10 @@ class Server:
                 a.step += 1
                 if a.step < a.req.steps:
                     H, S = a.req.make_inputs(a.step)
-                    a.solver.set_HS(H, S)
+                    if a.req.fixed_S:
+                        a.solver.set_H(H)
+                    else:
+                        a.solver.set_HS(H, S)
                     a.t_submit = a.t_start = clock() - t0
                     a.solver.begin(None, tol=a.req.tol)        # warm start from the resident W
                 else:

@@ -166,3 +166,46 @@ def test_cholesky_not_spd_is_reported(omm, eta_auto):
     E, it, st = s.solve(dev(sysm.W0_dense()), tol=1e-10, raise_on_error=False)
     assert st == omm.ERR_STATE
     s.close()
+
+
+@pytest.mark.parametrize("chol,prec", [(0, "fp64"), (1, "fp64"), (0, "mixed"), (1, "mixed")])
+def test_set_H_equals_set_HS(omm, chol, prec):
+    """omm_set_H keeps S (and the factor): the next solve is bit-identical to one
+    after omm_set_HS with the same S."""
+    import synth
+    sysm = synth.make_system(4, 3, 3, seed=8)
+    H, S = dev(sysm.dense_H()), dev(sysm.dense_S())
+    Hp = dev(synth.perturb_pairs(sysm, 3, 1).dense_H())
+    W0 = dev(sysm.W0_dense())
+    p = omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64
+    out = []
+    for use_set_H in (False, True):
+        s = omm.Solver(sysm.m, sysm.n, 8, cholesky=chol, precision=p, orth_tol=1e-6)
+        s.set_HS(H, S)
+        s.solve(W0, tol=1e-10)
+        if use_set_H:
+            s.set_H(Hp)
+        else:
+            s.set_HS(Hp, S)
+        W = empty_cm(sysm.m, sysm.n)
+        E, it, st = s.solve(None, tol=1e-10, W_out=W)
+        assert st == omm.OK
+        out.append((E, it, s.diag().eta, W.cpu().numpy()))
+        s.close()
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    np.testing.assert_array_equal(out[0][3], out[1][3])
+    # the minimum of the perturbed problem, by the oracle
+    Hp_np = synth.perturb_pairs(sysm, 3, 1).dense_H()
+    oracle = O.omm_cg_cholesky if chol else O.omm_cg
+    ref = oracle(Hp_np, sysm.dense_S(), out[0][3], tol=1e-12, eta=out[0][2])
+    assert abs(out[1][0] - ref.E) / abs(ref.E) < 1e-9
+
+
+def test_set_H_requires_set_HS(omm):
+    import synth
+    sysm = synth.make_system(3, 3, 2, seed=1)
+    s = omm.Solver(sysm.m, sysm.n, 8)
+    with pytest.raises(omm.OmmError) as ei:
+        s.set_H(dev(sysm.dense_H()))
+    assert ei.value.status == omm.ERR_STATE
+    s.close()
