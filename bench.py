@@ -252,6 +252,32 @@ def run_omm(args):
     e_exact = g.get("exact_E")
     rel_err = abs(E - e_exact) / abs(e_exact) if e_exact else None
 
+    # ---- the plain FP64 GPU form beside the chosen one: one whole FP64 solve
+    fp64_beside = None
+    if prec == "mixed" and not args.no_fp64_beside:
+        warm = omm.Solver(m, n, 8, precision=omm.PREC_FP64, stream=stream.cuda_stream, max_iter=2,
+                          cholesky=int(args.cholesky))
+        warm.set_HS(Hd, Sd)
+        warm.solve(W0d, tol=TOL["fp64"]["tol"], raise_on_error=False)
+        warm.close()
+        s64 = omm.Solver(m, n, 8, precision=omm.PREC_FP64, stream=stream.cuda_stream,
+                         orth_tol=TOL["mixed"]["orth_tol"], cholesky=int(args.cholesky))
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.set_HS(Hd, Sd)
+        E64, it64, st64 = s64.solve(W0d, tol=TOL["fp64"]["tol"], raise_on_error=False)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        d64 = s64.diag()
+        fp64_beside = {"form": "plain FP64 on CUDA cores (DFMA GEMMs), same handle API", "ms_per_solve": ms64,
+                       "solves_per_s": 1e3 / ms64, "E": E64, "status": int(st64), "iters": int(it64),
+                       "orth": d64.orth, "tol": TOL["fp64"]["tol"],
+                       "rel_err": abs(E64 - e_exact) / abs(e_exact) if e_exact else None,
+                       "chosen_form_speedup": ms64 / (t_max / args.steps)}
+        s64.close()
+
     # ---- e2e: the same solves through the C ABI from pinned host buffers
     Hh = torch.from_numpy(np.asfortranarray(H)).pin_memory()
     Sh = torch.from_numpy(np.asfortranarray(S)).pin_memory()
@@ -302,6 +328,7 @@ def run_omm(args):
         "stages_ms_per_step": {name: ms_stage[i] / args.steps for i, name in enumerate(STAGES)},
         "roofline": roof,
         "cpu_baseline": cpu,
+        "fp64_gpu_beside": fp64_beside,
         "e2e": {"value": ws * e2e_steps / (t_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(2 * m * m * 8 + m * n * 8),
                 "d2h_bytes_per_step": int(m * n * 8 + 8)},
@@ -516,6 +543,32 @@ def run_c5(args):
                              "iters_first_solve_mean": float(np.mean([r.iters for r in recs if r.step == 0])),
                              "iters_warm_mean": float(np.mean([r.iters for r in recs if r.step > 0]))})
     out["value"] = max(r["solves_per_s"] for r in out["rates"])
+
+    # the same request set served by the mixed form and by the plain FP64 GPU form
+    if args.fp64_sequences > 0:
+        k = min(args.fp64_sequences, len(seqs))
+        rate = 50.0
+        arrivals = np.cumsum(np.random.Generator(np.random.PCG64(55)).exponential(1.0 / rate, size=k))
+        arrivals -= arrivals[0]
+        cmp = {"sequences": k, "rate_seq_per_s": rate, "m": [int(seqs[i].m) for i in range(k)]}
+        for name, p in (("mixed", omm.PREC_MIXED), ("fp64", omm.PREC_FP64)):
+            reqs = [serving.Request(rid=i, arrival=float(arrivals[i]), m=seqs[i].m, n=seqs[i].n,
+                                    steps=args.scf_steps, make_inputs=make_inputs_factory(i), W0=base[i][2],
+                                    precision=p) for i in range(k)]
+            server = serving.Server(hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)))
+            t0 = time.perf_counter()
+            recs = server.run(reqs)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            st = serving.latency_stats(recs)
+            cmp[name] = {"solves_per_s": st["solves"] / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                         "all_ok": all(r.status == omm.OK for r in recs),
+                         "E_last": {r.rid: float(r.E) for r in recs if r.step == args.scf_steps - 1}}
+        cmp["max_rel_E_diff"] = max(abs(cmp["mixed"]["E_last"][i] - cmp["fp64"]["E_last"][i])
+                                    / abs(cmp["fp64"]["E_last"][i]) for i in range(k))
+        for name in ("mixed", "fp64"):
+            del cmp[name]["E_last"]
+        out["mixed_vs_fp64"] = cmp
     print(json.dumps(out), flush=True)
 
 
@@ -529,6 +582,10 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run one solve only (for ncu captures); prints stage times, no benchmark line")
     ap.add_argument("--max-iter", type=int, default=0, help="with --profile: cap on CG steps")
+    ap.add_argument("--no-fp64-beside", action="store_true",
+                    help="c2: skip the plain FP64 GPU solve reported beside the mixed form")
+    ap.add_argument("--fp64-sequences", type=int, default=6,
+                    help="c5: sequences of the mixed-vs-FP64 serving comparison (0 skips it)")
     ap.add_argument("--cholesky", action="store_true",
                     help="c2: Cholesky-reduced variant (S = L L^T factored inside each step's setup)")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],

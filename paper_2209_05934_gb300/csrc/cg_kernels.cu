@@ -10,6 +10,7 @@
 
 #include <mutex>
 
+#include "linemin.cuh"
 #include "omm_internal.cuh"
 
 namespace omm {
@@ -92,101 +93,6 @@ __device__ __forceinline__ void put3(const DigitOut &d, int64_t o, double v) {
     p[2 * d.plane + o] = d3;
 }
 
-__device__ inline double quartic_val(const double *c, double x) {
-    return c[0] + x * (c[1] + x * (c[2] + x * (c[3] + x * c[4])));
-}
-
-// Real roots of a x^3 + b x^2 + c x + d (a > 0): one root by safeguarded
-// Newton/bisection on the Cauchy bracket, deflation, a stable quadratic
-// formula for the rest, then Newton polishing of every root.
-__device__ int cubic_real_roots(double a, double b, double c, double d, double *r) {
-    auto f = [&](double x) { return ((a * x + b) * x + c) * x + d; };
-    auto fp = [&](double x) { return (3.0 * a * x + 2.0 * b) * x + c; };
-    const double R = 1.0 + fmax(fabs(b), fmax(fabs(c), fabs(d))) / a;
-    double lo = -R, hi = R;   // f(lo) < 0 < f(hi)
-    double x = 0.0;
-    for (int it = 0; it < 400; ++it) {
-        const double fx = f(x);
-        if (fx == 0.0) break;
-        if (fx < 0.0) lo = x; else hi = x;
-        const double dx = fp(x);
-        double xn = (dx != 0.0) ? x - fx / dx : 0.5 * (lo + hi);
-        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-        if (xn == x || hi - lo <= 4e-16 * fmax(1.0, fabs(x))) { x = xn; break; }
-        x = xn;
-    }
-    int nr = 0;
-    r[nr++] = x;
-    // a x^3 + b x^2 + c x + d = (x - x1)(a x^2 + p x + q)
-    const double p = b + a * x;
-    const double q = c + p * x;
-    const double disc = p * p - 4.0 * a * q;
-    if (disc >= 0.0) {
-        const double sq = sqrt(disc);
-        const double t = -0.5 * (p + (p >= 0.0 ? sq : -sq));
-        if (t != 0.0) {
-            r[nr++] = t / a;
-            r[nr++] = q / t;
-        } else {
-            r[nr++] = 0.0;
-        }
-    }
-    for (int i = 0; i < nr; ++i) {
-        for (int it = 0; it < 3; ++it) {
-            const double dx = fp(r[i]);
-            if (dx == 0.0) break;
-            const double xn = r[i] - f(r[i]) / dx;
-            if (!isfinite(xn)) break;
-            if (fabs(f(xn)) <= fabs(f(r[i]))) r[i] = xn; else break;
-        }
-    }
-    return nr;
-}
-
-// Minimiser of the quartic c0 + c1 x + ... + c4 x^4; returns status.
-__device__ int quartic_min(const double *c, double *xout) {
-    for (int i = 0; i < 5; ++i)
-        if (!finite(c[i])) return OMM_ERR_NONFINITE;
-    if (c[4] == 0.0 && c[3] == 0.0) {
-        if (c[2] > 0.0) { *xout = -c[1] / (2.0 * c[2]); return OMM_OK; }
-        return OMM_ERR_LINESEARCH;
-    }
-    if (c[4] < 0.0) return OMM_ERR_LINESEARCH;
-    double r[3];
-    int nr;
-    if (c[4] > 0.0) {
-        nr = cubic_real_roots(4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1], r);
-    } else {
-        // c4 == 0, c3 != 0: derivative 3 c3 x^2 + 2 c2 x + c1
-        const double a = 3.0 * c[3], b = 2.0 * c[2], cc = c[1];
-        const double disc = b * b - 4.0 * a * cc;
-        nr = 0;
-        if (disc >= 0.0) {
-            const double sq = sqrt(disc);
-            const double t = -0.5 * (b + (b >= 0.0 ? sq : -sq));
-            if (t != 0.0) { r[nr++] = t / a; r[nr++] = cc / t; }
-        }
-    }
-    bool have = false;
-    double best = 0.0, bestv = 0.0;
-    for (int pass = 0; pass < 2 && !have; ++pass) {
-        for (int i = 0; i < nr; ++i) {
-            const double x = r[i];
-            if (!finite(x)) continue;
-            const double curv = 12.0 * c[4] * x * x + 6.0 * c[3] * x + 2.0 * c[2];
-            if (pass == 0 && !(curv > 0.0)) continue;
-            if (pass == 1 && !(c[4] > 0.0)) continue;
-            const double v = quartic_val(c, x);
-            bool better = !have || v < bestv ||
-                          (v == bestv && (fabs(x) < fabs(best) || (fabs(x) == fabs(best) && x > best)));
-            if (better) { have = true; best = x; bestv = v; }
-        }
-    }
-    if (!have) return OMM_ERR_LINESEARCH;
-    *xout = best;
-    return OMM_OK;
-}
-
 // ---------------------------------------------------------------- coefficients
 // partial sums: 0 tr h0, 1 <s0,h0>, 2 tr X, 3 <s0,X>, 4 <Y,h0>, 5 tr h2, 6 <s0,h2>,
 // 7 <Y,X>, 8 <Y,X^T>, 9 <s2,h0>, 10 <Y,h2>, 11 <s2,X>, 12 <s2,h2>
@@ -242,22 +148,26 @@ __global__ void __launch_bounds__(NT) coeffs_kernel(int n, const double *__restr
         }
     }
     block_sum<NC>(v, red);
-    double tot[NC];
+    double tot[NC] = {};
     if (!publish_and_collect<NC>(v, partials, counter, tot, red)) return;
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;   // warp 0: the line minimum
+#pragma unroll
+    for (int q = 0; q < NC; ++q) tot[q] = __shfl_sync(0xffffffffu, tot[q], 0);
     double c[5];
     c[0] = 2.0 * (2.0 * tot[0] - tot[1]);
     c[1] = 2.0 * (4.0 * tot[2] - 2.0 * tot[3] - 2.0 * tot[4]);
     c[2] = 2.0 * (2.0 * tot[5] - tot[6] - 2.0 * (tot[7] + tot[8]) - tot[9]);
     c[3] = 2.0 * (-2.0 * tot[10] - 2.0 * tot[11]);
     c[4] = -2.0 * tot[12];
+    double x = 0.0;
+    int st = OMM_OK;
+    if (state != nullptr && do_linemin) st = lm::quartic_min_warp(c, &x);
+    if (threadIdx.x != 0) return;
     if (coeffs_out != nullptr)
         for (int q = 0; q < 5; ++q) coeffs_out[q] = c[q];
     if (state != nullptr) {
         for (int q = 0; q < 5; ++q) state->c[q] = c[q];
         if (do_linemin) {
-            double x = 0.0;
-            const int st = quartic_min(c, &x);
             state->x = x;
             if (st != OMM_OK) {
                 state->status = st;
@@ -656,11 +566,13 @@ int launch_gershgorin(int64_t m, const double *H, const double *S, double *scrat
 
 // ---------------------------------------------------------------- op-level entries
 namespace {
+// one warp
 __global__ void line_min_kernel(const double *c, double *x_out, int32_t *status_out) {
     double cc[5];
     for (int q = 0; q < 5; ++q) cc[q] = c[q];
     double x = 0.0;
-    const int st = quartic_min(cc, &x);
+    const int st = lm::quartic_min_warp(cc, &x);
+    if (threadIdx.x != 0) return;
     *x_out = x;
     *status_out = st;
 }
@@ -699,7 +611,7 @@ extern "C" int omm_op_quartic_coeffs(int64_t n, const double *h0, const double *
 extern "C" int omm_op_line_min(const double *coeffs, double *x_out, int32_t *status_out,
                                void *stream) {
     if (coeffs == nullptr || x_out == nullptr || status_out == nullptr) return OMM_ERR_ARG;
-    omm::line_min_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(coeffs, x_out, status_out);
+    omm::line_min_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(coeffs, x_out, status_out);
     omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

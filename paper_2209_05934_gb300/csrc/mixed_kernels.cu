@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include "fp_convert.cuh"
+#include "linemin.cuh"
 #include "omm_internal.cuh"
 
 namespace omm {
@@ -40,14 +41,66 @@ __device__ __forceinline__ void put3f(const DigitOut &d, int64_t o, float v) {
     p[2 * d.plane + o] = d3;
 }
 
+// Digits of four consecutive FP32 values (8-byte aligned offset o): same
+// rounding as put3f, two values per conversion, one 8-byte store per plane.
+__device__ __forceinline__ void put3f4(const DigitOut &d, int64_t o, float4 v) {
+    const __nv_bfloat162 a1 = __floats2bfloat162_rn(v.x, v.y), b1 = __floats2bfloat162_rn(v.z, v.w);
+    const float2 fa1 = __bfloat1622float2(a1), fb1 = __bfloat1622float2(b1);
+    const float r0 = v.x - fa1.x, r1 = v.y - fa1.y, r2 = v.z - fb1.x, r3 = v.w - fb1.y;
+    const __nv_bfloat162 a2 = __floats2bfloat162_rn(r0, r1), b2 = __floats2bfloat162_rn(r2, r3);
+    const float2 fa2 = __bfloat1622float2(a2), fb2 = __bfloat1622float2(b2);
+    const __nv_bfloat162 a3 = __floats2bfloat162_rn(r0 - fa2.x, r1 - fa2.y);
+    const __nv_bfloat162 b3 = __floats2bfloat162_rn(r2 - fb2.x, r3 - fb2.y);
+    __nv_bfloat16 *p = (__nv_bfloat16 *)d.ptr;
+    auto pack = [](__nv_bfloat162 lo, __nv_bfloat162 hi) {
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t *>(&lo);
+        u.y = *reinterpret_cast<const uint32_t *>(&hi);
+        return u;
+    };
+    *reinterpret_cast<uint2 *>(p + o) = pack(a1, b1);
+    *reinterpret_cast<uint2 *>(p + d.plane + o) = pack(a2, b2);
+    *reinterpret_cast<uint2 *>(p + 2 * d.plane + o) = pack(a3, b3);
+}
+
+// Digits of two consecutive FP32 values (4-byte aligned offset o), as put3f.
+__device__ __forceinline__ void put3f2(const DigitOut &d, int64_t o, float v0, float v1) {
+    const __nv_bfloat162 a1 = __floats2bfloat162_rn(v0, v1);
+    const float2 f1 = __bfloat1622float2(a1);
+    const float r0 = v0 - f1.x, r1 = v1 - f1.y;
+    const __nv_bfloat162 a2 = __floats2bfloat162_rn(r0, r1);
+    const float2 f2 = __bfloat1622float2(a2);
+    const __nv_bfloat162 a3 = __floats2bfloat162_rn(r0 - f2.x, r1 - f2.y);
+    __nv_bfloat16 *p = (__nv_bfloat16 *)d.ptr;
+    *reinterpret_cast<__nv_bfloat162 *>(p + o) = a1;
+    *reinterpret_cast<__nv_bfloat162 *>(p + d.plane + o) = a2;
+    *reinterpret_cast<__nv_bfloat162 *>(p + 2 * d.plane + o) = a3;
+}
+
+// FP32 per-thread partials: summed across the warp in FP32 (their inputs are
+// FP32 products, so this adds error of the same order), then converted to
+// FP64 on the integer pipe; block_sum then adds the warps' values in FP64.
 template <int NV>
-__device__ void block_sum(double (&v)[NV], double *red) {
+__device__ __forceinline__ void to_f64(const float (&f)[NV], double (&v)[NV]) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-        double s = v[q];
+        float t = f[q];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        v[q] = s;
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+        v[q] = (threadIdx.x & 31) == 0 ? sw_f2d(t) : 0.0;
+    }
+}
+
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *red, bool lane0_only = false) {
+    if (!lane0_only) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = v[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+            v[q] = s;
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0)
@@ -91,89 +144,6 @@ __device__ bool publish_and_collect(const double (&v)[NV], double *partials, uns
         *counter = 0u;
     }
     return true;
-}
-
-// ---------------------------------------------------------------- line search
-__device__ inline double quartic_val(const double *c, double x) {
-    return c[0] + x * (c[1] + x * (c[2] + x * (c[3] + x * c[4])));
-}
-
-__device__ int cubic_real_roots(double a, double b, double c, double d, double *r) {
-    auto f = [&](double x) { return ((a * x + b) * x + c) * x + d; };
-    auto fp = [&](double x) { return (3.0 * a * x + 2.0 * b) * x + c; };
-    const double R = 1.0 + fmax(fabs(b), fmax(fabs(c), fabs(d))) / a;
-    double lo = -R, hi = R, x = 0.0;
-    for (int it = 0; it < 400; ++it) {
-        const double fx = f(x);
-        if (fx == 0.0) break;
-        if (fx < 0.0) lo = x; else hi = x;
-        const double dx = fp(x);
-        double xn = (dx != 0.0) ? x - fx / dx : 0.5 * (lo + hi);
-        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-        if (xn == x || hi - lo <= 4e-16 * fmax(1.0, fabs(x))) { x = xn; break; }
-        x = xn;
-    }
-    int nr = 0;
-    r[nr++] = x;
-    const double p = b + a * x, q = c + p * x;
-    const double disc = p * p - 4.0 * a * q;
-    if (disc >= 0.0) {
-        const double sq = sqrt(disc);
-        const double t = -0.5 * (p + (p >= 0.0 ? sq : -sq));
-        if (t != 0.0) { r[nr++] = t / a; r[nr++] = q / t; } else { r[nr++] = 0.0; }
-    }
-    for (int i = 0; i < nr; ++i)
-        for (int it = 0; it < 3; ++it) {
-            const double dx = fp(r[i]);
-            if (dx == 0.0) break;
-            const double xn = r[i] - f(r[i]) / dx;
-            if (!isfinite(xn)) break;
-            if (fabs(f(xn)) <= fabs(f(r[i]))) r[i] = xn; else break;
-        }
-    return nr;
-}
-
-// same rule as the FP64 path: lowest value among the positive-curvature roots
-__device__ int quartic_min(const double *c, double *xout) {
-    for (int i = 0; i < 5; ++i)
-        if (!isfinite(c[i])) return OMM_ERR_NONFINITE;
-    if (c[4] == 0.0 && c[3] == 0.0) {
-        if (c[2] > 0.0) { *xout = -c[1] / (2.0 * c[2]); return OMM_OK; }
-        return OMM_ERR_LINESEARCH;
-    }
-    if (c[4] < 0.0) return OMM_ERR_LINESEARCH;
-    double r[3];
-    int nr = 0;
-    if (c[4] > 0.0) {
-        nr = cubic_real_roots(4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1], r);
-    } else {
-        const double a = 3.0 * c[3], b = 2.0 * c[2], cc = c[1];
-        const double disc = b * b - 4.0 * a * cc;
-        if (disc >= 0.0) {
-            const double sq = sqrt(disc);
-            const double t = -0.5 * (b + (b >= 0.0 ? sq : -sq));
-            if (t != 0.0) { r[nr++] = t / a; r[nr++] = cc / t; }
-        }
-    }
-    bool have = false;
-    double best = 0.0, bestv = 0.0;
-    for (int pass = 0; pass < 2 && !have; ++pass)
-        for (int i = 0; i < nr; ++i) {
-            const double x = r[i];
-            if (!isfinite(x)) continue;
-            const double curv = 12.0 * c[4] * x * x + 6.0 * c[3] * x + 2.0 * c[2];
-            if (pass == 0 && !(curv > 0.0)) continue;
-            if (pass == 1 && !(c[4] > 0.0)) continue;
-            const double v = quartic_val(c, x);
-            if (!have || v < bestv || (v == bestv && (fabs(x) < fabs(best) || (fabs(x) == fabs(best) && x > best)))) {
-                have = true;
-                best = x;
-                bestv = v;
-            }
-        }
-    if (!have) return OMM_ERR_LINESEARCH;
-    *xout = best;
-    return OMM_OK;
 }
 
 // ---------------------------------------------------------------- coefficients
@@ -221,24 +191,26 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
         }
     }
     double v[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) v[q] = (double)f[q];
-    block_sum<NC>(v, red);
-    double tot[NC];
+    to_f64<NC>(f, v);
+    block_sum<NC>(v, red, true);
+    double tot[NC] = {};
     if (!publish_and_collect<NC>(v, partials, counter, tot, red)) return;
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;   // warp 0: the line minimum
+#pragma unroll
+    for (int q = 0; q < NC; ++q) tot[q] = __shfl_sync(0xffffffffu, tot[q], 0);
     double c[5];
     c[0] = state->E - 2.0 * state->eta * (double)n;   // the shifted functional at x = 0
     c[1] = 2.0 * state->gD;
     c[2] = 2.0 * (2.0 * tot[0] - tot[1] - 2.0 * (tot[2] + tot[3]) - tot[4]);
     c[3] = 2.0 * (-2.0 * tot[5] - 2.0 * tot[6]);
     c[4] = -2.0 * tot[7];
-    for (int q = 0; q < 5; ++q) state->c[q] = c[q];
     double x = 0.0;
-    const int st = quartic_min(c, &x);
+    const int st = lm::quartic_min_warp(c, &x);
+    if (threadIdx.x != 0) return;
+    for (int q = 0; q < 5; ++q) state->c[q] = c[q];
     state->x = x;
     state->x_f = (float)x;
-    state->E_next = quartic_val(c, x) + 2.0 * state->eta * (double)n;
+    state->E_next = lm::quartic_val(c, x) + 2.0 * state->eta * (double)n;
     if (st != OMM_OK) {
         state->status = st;
         state->done = 1;
@@ -294,8 +266,10 @@ __global__ void __launch_bounds__(NT) mx_nn_update_kernel(int n, double *h0, dou
             }
         }
     }
-    double v[1] = {(double)orth};
-    block_sum<1>(v, red);
+    const float fo[1] = {orth};
+    double v[1];
+    to_f64<1>(fo, v);
+    block_sum<1>(v, red, true);
     double tot[1];
     if (!publish_and_collect<1>(v, partials, counter, tot, red)) return;
     if (threadIdx.x != 0) return;
@@ -367,6 +341,60 @@ __global__ void __launch_bounds__(NT) mx_update_kernel(int m, int n, double *W, 
     }
 }
 
+// Two consecutive rows per thread on 64 x 32 tiles (m even, 16-byte aligned
+// FP64 arrays): double2 / float2 accesses, paired digit conversions.
+constexpr int TI2 = 64;
+__global__ void __launch_bounds__(NT) mx_update2_kernel(int m, int n, double2 *W, const float2 *__restrict__ D,
+                                                         double2 *HW, const float2 *__restrict__ HD, double2 *SW,
+                                                         const float2 *__restrict__ SD, const DevState *state,
+                                                         DigitOut wd, DigitOut swhw) {
+    if (*((volatile const int *)&state->done)) return;
+    __shared__ float tH[TILE][TI2 + 1];
+    __shared__ float tS[TILE][TI2 + 1];
+    const float x = state->x_f;
+    const int lx = threadIdx.x % 32, ly = threadIdx.x / 32;
+    const int Tm = (m + TI2 - 1) / TI2, Tn = (n + TILE - 1) / TILE;
+    for (int t = blockIdx.x; t < Tm * Tn; t += gridDim.x) {
+        const int ti = t % Tm, tj = t / Tm;
+        const int i = ti * TI2 + 2 * lx;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int jl = ly + 8 * r, j = tj * TILE + jl;
+            if (i < m && j < n) {
+                const int64_t o2 = ((int64_t)j * m + i) >> 1;
+                const float2 d = D[o2], hd = HD[o2], sd = SD[o2];
+                double2 w = W[o2], hw = HW[o2], sw = SW[o2];
+                w.x += sw_f2d(x * d.x);
+                w.y += sw_f2d(x * d.y);
+                hw.x += sw_f2d(x * hd.x);
+                hw.y += sw_f2d(x * hd.y);
+                sw.x += sw_f2d(x * sd.x);
+                sw.y += sw_f2d(x * sd.y);
+                W[o2] = w;
+                HW[o2] = hw;
+                SW[o2] = sw;
+                if (wd.ptr != nullptr) put3f2(wd, (int64_t)j * wd.ld + i, sw_d2f(w.x), sw_d2f(w.y));
+                tH[jl][2 * lx] = sw_d2f(hw.x);
+                tH[jl][2 * lx + 1] = sw_d2f(hw.y);
+                tS[jl][2 * lx] = sw_d2f(sw.x);
+                tS[jl][2 * lx + 1] = sw_d2f(sw.y);
+            }
+        }
+        if (swhw.ptr != nullptr) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < TI2 / 8; ++r) {
+                const int il = ly + 8 * r, ii = ti * TI2 + il, jj = tj * TILE + lx;
+                if (ii < m && jj < n) {
+                    put3f(swhw, (int64_t)ii * swhw.ld + jj, tS[lx][il]);
+                    put3f(swhw, (int64_t)ii * swhw.ld + n + jj, tH[lx][il]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // ---------------------------------------------------------------- CG dots and direction
 constexpr int ND = 3;   // <G,G>, <G,Gp>, <G,D>
 
@@ -377,7 +405,19 @@ __global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__
     if (*((volatile int *)&state->done)) return;
     __shared__ double red[(NT / 32) * ND];
     float f[ND] = {0.f, 0.f, 0.f};
-    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < mn; i += (int64_t)gridDim.x * NT) {
+    const int64_t n4 = mn / 4, stride = (int64_t)gridDim.x * NT;
+    const float4 *G4 = reinterpret_cast<const float4 *>(G), *Gp4 = reinterpret_cast<const float4 *>(Gp),
+                 *D4 = reinterpret_cast<const float4 *>(D);
+    for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n4; k += stride) {
+        const float4 g = G4[k];
+        f[0] = fmaf(g.x, g.x, fmaf(g.y, g.y, fmaf(g.z, g.z, fmaf(g.w, g.w, f[0]))));
+        if (!first) {
+            const float4 p = Gp4[k], d = D4[k];
+            f[1] = fmaf(g.x, p.x, fmaf(g.y, p.y, fmaf(g.z, p.z, fmaf(g.w, p.w, f[1]))));
+            f[2] = fmaf(g.x, d.x, fmaf(g.y, d.y, fmaf(g.z, d.z, fmaf(g.w, d.w, f[2]))));
+        }
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * NT + threadIdx.x; i < mn; i += stride) {   // tail
         const float g = G[i];
         f[0] = fmaf(g, g, f[0]);
         if (!first) {
@@ -385,8 +425,9 @@ __global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__
             f[2] = fmaf(g, D[i], f[2]);
         }
     }
-    double v[ND] = {(double)f[0], (double)f[1], (double)f[2]};
-    block_sum<ND>(v, red);
+    double v[ND];
+    to_f64<ND>(f, v);
+    block_sum<ND>(v, red, true);
     double tot[ND];
     if (!publish_and_collect<ND>(v, partials, counter, tot, red)) return;
     if (threadIdx.x != 0) return;
@@ -430,6 +471,34 @@ __global__ void mx_direction_kernel(int m, int n, const float *__restrict__ G, f
         }
 }
 
+// four consecutive rows of one column per thread (m % 4 == 0, 16-byte aligned arrays)
+__global__ void __launch_bounds__(NT) mx_direction4_kernel(int m, int64_t mn, const float4 *__restrict__ G,
+                                                            float4 *Gp, float4 *D, const DevState *state,
+                                                            DigitOut dd) {
+    if (*((volatile const int *)&state->done)) return;
+    const float beta = state->beta_f;
+    const bool restart = state->restart != 0;
+    const int64_t n4 = mn / 4;
+    for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n4; k += (int64_t)gridDim.x * NT) {
+        const float4 g = G[k];
+        float4 d = D[k];
+        if (restart) {
+            d = make_float4(-g.x, -g.y, -g.z, -g.w);
+        } else {
+            d.x = fmaf(beta, d.x, -g.x);
+            d.y = fmaf(beta, d.y, -g.y);
+            d.z = fmaf(beta, d.z, -g.z);
+            d.w = fmaf(beta, d.w, -g.w);
+        }
+        D[k] = d;
+        Gp[k] = g;
+        if (dd.ptr != nullptr) {
+            const int64_t o = 4 * k, j = o / m, i = o - j * m;
+            put3f4(dd, j * dd.ld + i, d);
+        }
+    }
+}
+
 __global__ void mx_round_kernel(int64_t count, const double *__restrict__ src, float *dst, const DevState *state) {
     if (state != nullptr && *((volatile const int *)&state->done)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
@@ -454,6 +523,20 @@ int mx_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh, co
 
 int mx_update(int64_t m, int64_t n, double *W, const float *D, double *HW, const float *HD, double *SW,
               const float *SD, const DevState *state, DigitOut wd, DigitOut swhw, cudaStream_t st) {
+    const bool aligned = ((((uintptr_t)W) | ((uintptr_t)HW) | ((uintptr_t)SW)) & 15u) == 0 &&
+                         ((((uintptr_t)D) | ((uintptr_t)HD) | ((uintptr_t)SD)) & 7u) == 0 &&
+                         (wd.ptr == nullptr || ((((uintptr_t)wd.ptr) & 3u) == 0 && wd.ld % 2 == 0 && wd.plane % 2 == 0));
+    if (m % 2 == 0 && aligned) {
+        int64_t nb = ceil_div(m, TI2) * ceil_div(n, TILE);
+        if (nb > 152 * 8) nb = 152 * 8;
+        mx_update2_kernel<<<(unsigned)nb, NT, 0, st>>>(
+            (int)m, (int)n, reinterpret_cast<double2 *>(W), reinterpret_cast<const float2 *>(D),
+            reinterpret_cast<double2 *>(HW), reinterpret_cast<const float2 *>(HD), reinterpret_cast<double2 *>(SW),
+            reinterpret_cast<const float2 *>(SD), state, wd, swhw);
+        count_launch();
+        OMM_CUDA_TRY(cudaGetLastError());
+        return OMM_OK;
+    }
     int64_t nb = ceil_div(m, TILE) * ceil_div(n, TILE);
     if (nb > 152 * 8) nb = 152 * 8;
     mx_update_kernel<<<(unsigned)nb, NT, 0, st>>>((int)m, (int)n, W, D, HW, HD, SW, SD, state, wd, swhw);
@@ -472,8 +555,9 @@ int mx_nn_update(int n, double *h0, double *s0, int64_t ldh, const float *Z, int
 
 int mx_dots_beta(int64_t mn, const float *G, const float *Gp, const float *D, double *scratch,
                  unsigned int *counter, DevState *state, int first, cudaStream_t st) {
-    int64_t nb = ceil_div(mn, (int64_t)NT * 16);
-    if (nb > kRedBlocksMax) nb = kRedBlocksMax;
+    if (((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)D)) & 15u) != 0) return OMM_ERR_ARG;
+    int64_t nb = ceil_div(mn, (int64_t)NT * 32);
+    if (nb > 152 * 2) nb = 152 * 2;
     mx_dots_kernel<<<(unsigned)(nb < 1 ? 1 : nb), NT, 0, st>>>(mn, G, Gp, D, scratch, counter, state, first);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
@@ -482,6 +566,18 @@ int mx_dots_beta(int64_t mn, const float *G, const float *Gp, const float *D, do
 
 int mx_direction(int64_t m, int64_t n, const float *G, float *Gp, float *D, const DevState *state, DigitOut dd,
                  cudaStream_t st) {
+    const bool aligned = ((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)D)) & 15u) == 0 &&
+                         (dd.ptr == nullptr || ((((uintptr_t)dd.ptr) & 7u) == 0 && dd.ld % 4 == 0 && dd.plane % 4 == 0));
+    if (m % 4 == 0 && aligned) {
+        int64_t nb = ceil_div(m * n / 4, (int64_t)NT * 4);
+        if (nb > 152 * 8) nb = 152 * 8;
+        mx_direction4_kernel<<<(unsigned)(nb < 1 ? 1 : nb), NT, 0, st>>>(
+            (int)m, m * n, reinterpret_cast<const float4 *>(G), reinterpret_cast<float4 *>(Gp),
+            reinterpret_cast<float4 *>(D), state, dd);
+        count_launch();
+        OMM_CUDA_TRY(cudaGetLastError());
+        return OMM_OK;
+    }
     dim3 grid((unsigned)ceil_div(m, NT), (unsigned)(n < 1024 ? n : 1024));
     mx_direction_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, G, Gp, D, state, dd);
     count_launch();

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "linemin.cuh"
 #include "omm_internal.cuh"
 #include "sparse.cuh"
 
@@ -514,7 +515,6 @@ __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_
 
 // ---- quartic coefficients and line minimum on P_N (2x2 blocks)
 constexpr int NC = 13;
-__device__ int quartic_min(const double *c, double *xout);
 
 __global__ void __launch_bounds__(NT) coeffs_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr,
                                                      const unsigned char *__restrict__ Ndiag,
@@ -546,18 +546,21 @@ __global__ void __launch_bounds__(NT) coeffs_kernel(int64_t nnzN, const int32_t 
         v[12] = fma(vs2, vh2, v[12]);
     }
     block_sum<NC>(v, red);
-    double tot[NC];
+    double tot[NC] = {};
     if (!publish_and_collect<NC>(v, partials, counter, tot, red)) return;
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;   // warp 0: the line minimum
+#pragma unroll
+    for (int q = 0; q < NC; ++q) tot[q] = __shfl_sync(0xffffffffu, tot[q], 0);
     double c[5];
     c[0] = 2.0 * (2.0 * tot[0] - tot[1]);
     c[1] = 2.0 * (4.0 * tot[2] - 2.0 * tot[3] - 2.0 * tot[4]);
     c[2] = 2.0 * (2.0 * tot[5] - tot[6] - 2.0 * (tot[7] + tot[8]) - tot[9]);
     c[3] = 2.0 * (-2.0 * tot[10] - 2.0 * tot[11]);
     c[4] = -2.0 * tot[12];
-    for (int q = 0; q < 5; ++q) state->c[q] = c[q];
     double x = 0.0;
-    const int st = quartic_min(c, &x);
+    const int st = lm::quartic_min_warp(c, &x);
+    if (threadIdx.x != 0) return;
+    for (int q = 0; q < 5; ++q) state->c[q] = c[q];
     state->x = x;
     if (st != OMM_OK) {
         state->status = st;
@@ -696,86 +699,6 @@ __global__ void direction_kernel(int64_t len, const double *__restrict__ G, doub
         D[i] = restart ? -g : fma(beta, D[i], -g);
         Gp[i] = g;
     }
-}
-
-// ---- line minimum (same rule as the dense form)
-__device__ double qval(const double *c, double x) { return c[0] + x * (c[1] + x * (c[2] + x * (c[3] + x * c[4]))); }
-
-__device__ int cubic_roots(double a, double b, double c, double d, double *r) {
-    auto f = [&](double x) { return ((a * x + b) * x + c) * x + d; };
-    auto fp = [&](double x) { return (3.0 * a * x + 2.0 * b) * x + c; };
-    const double R = 1.0 + fmax(fabs(b), fmax(fabs(c), fabs(d))) / a;
-    double lo = -R, hi = R, x = 0.0;
-    for (int it = 0; it < 400; ++it) {
-        const double fx = f(x);
-        if (fx == 0.0) break;
-        if (fx < 0.0) lo = x; else hi = x;
-        const double dx = fp(x);
-        double xn = (dx != 0.0) ? x - fx / dx : 0.5 * (lo + hi);
-        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-        if (xn == x || hi - lo <= 4e-16 * fmax(1.0, fabs(x))) { x = xn; break; }
-        x = xn;
-    }
-    int nr = 0;
-    r[nr++] = x;
-    const double p = b + a * x, q = c + p * x;
-    const double disc = p * p - 4.0 * a * q;
-    if (disc >= 0.0) {
-        const double sq = sqrt(disc);
-        const double t = -0.5 * (p + (p >= 0.0 ? sq : -sq));
-        if (t != 0.0) { r[nr++] = t / a; r[nr++] = q / t; } else { r[nr++] = 0.0; }
-    }
-    for (int i = 0; i < nr; ++i)
-        for (int it = 0; it < 3; ++it) {
-            const double dx = fp(r[i]);
-            if (dx == 0.0) break;
-            const double xn = r[i] - f(r[i]) / dx;
-            if (!isfinite(xn)) break;
-            if (fabs(f(xn)) <= fabs(f(r[i]))) r[i] = xn; else break;
-        }
-    return nr;
-}
-
-__device__ int quartic_min(const double *c, double *xout) {
-    for (int i = 0; i < 5; ++i)
-        if (!isfinite(c[i])) return OMM_ERR_NONFINITE;
-    if (c[4] == 0.0 && c[3] == 0.0) {
-        if (c[2] > 0.0) { *xout = -c[1] / (2.0 * c[2]); return OMM_OK; }
-        return OMM_ERR_LINESEARCH;
-    }
-    if (c[4] < 0.0) return OMM_ERR_LINESEARCH;
-    double r[3];
-    int nr = 0;
-    if (c[4] > 0.0) {
-        nr = cubic_roots(4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1], r);
-    } else {
-        const double a = 3.0 * c[3], b = 2.0 * c[2], cc = c[1];
-        const double disc = b * b - 4.0 * a * cc;
-        if (disc >= 0.0) {
-            const double sq = sqrt(disc);
-            const double t = -0.5 * (b + (b >= 0.0 ? sq : -sq));
-            if (t != 0.0) { r[nr++] = t / a; r[nr++] = cc / t; }
-        }
-    }
-    bool have = false;
-    double best = 0.0, bestv = 0.0;
-    for (int pass = 0; pass < 2 && !have; ++pass)
-        for (int i = 0; i < nr; ++i) {
-            const double x = r[i];
-            if (!isfinite(x)) continue;
-            const double curv = 12.0 * c[4] * x * x + 6.0 * c[3] * x + 2.0 * c[2];
-            if (pass == 0 && !(curv > 0.0)) continue;
-            if (pass == 1 && !(c[4] > 0.0)) continue;
-            const double vv = qval(c, x);
-            if (!have || vv < bestv || (vv == bestv && (fabs(x) < fabs(best) || (fabs(x) == fabs(best) && x > best)))) {
-                have = true;
-                best = x;
-                bestv = vv;
-            }
-        }
-    if (!have) return OMM_ERR_LINESEARCH;
-    *xout = best;
-    return OMM_OK;
 }
 
 int blocks_for(int64_t work, int per) {
