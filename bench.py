@@ -207,7 +207,8 @@ def run_omm(args):
     Wout = torch.zeros((n, m), dtype=torch.float64, device="cuda").T
     stream = torch.cuda.current_stream()
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
-                orth_tol=TOL[prec]["orth_tol"], stream=stream.cuda_stream, cholesky=int(args.cholesky))
+                orth_tol=TOL[prec]["orth_tol"], stream=stream.cuda_stream, cholesky=int(args.cholesky),
+                split_digits=args.split_digits)
     solver = omm.Solver(m, n, 8, **opts)
     tol = TOL[prec]["tol"]
 
@@ -317,6 +318,7 @@ def run_omm(args):
         "data": "synthetic",
         "config": {"workload": workload_name(sysm) + (" cholesky-reduced" if args.cholesky else ""),
                    "precision": prec, "tol": tol, "cholesky": bool(args.cholesky),
+                   "split_digits": args.split_digits,
                    "refine": "exact-digit tensor cores" if prec == "mixed" else None,
                    "orth_tol": TOL[prec]["orth_tol"], "parallelism": f"replicas x{ws}",
                    "l2": "working set (H, S = 256 MiB, plus W/D/products) exceeds the 129 MB L2"},
@@ -414,7 +416,7 @@ def run_profile(args):
     prec = args.precision
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
                 orth_tol=TOL[prec]["orth_tol"], stream=torch.cuda.current_stream().cuda_stream,
-                cholesky=int(args.cholesky))
+                cholesky=int(args.cholesky), split_digits=args.split_digits)
     if args.max_iter > 0:
         opts["max_iter"] = args.max_iter
     solver = omm.Solver(sysm.m, sysm.n, 8, **opts)
@@ -423,7 +425,9 @@ def run_profile(args):
     E, iters, st = solver.solve(W0, tol=TOL[prec]["tol"], raise_on_error=False)
     torch.cuda.synchronize()
     ms, cnt = solver.stage_times()
+    d = solver.diag()
     print(json.dumps({"profile": True, "precision": prec, "E": E, "iters": iters, "status": st,
+                      "iters_mixed": d.iters_mixed, "iters_refine": d.iters_refine, "orth": d.orth,
                       "stages_ms": {n: ms[i] for i, n in enumerate(STAGES)},
                       "stage_launches": {n: int(cnt[i]) for i, n in enumerate(STAGES)},
                       "gpu_launches": omm.kernel_launches()}), flush=True)
@@ -586,6 +590,8 @@ def main():
                     help="c2: skip the plain FP64 GPU solve reported beside the mixed form")
     ap.add_argument("--fp64-sequences", type=int, default=6,
                     help="c5: sequences of the mixed-vs-FP64 serving comparison (0 skips it)")
+    ap.add_argument("--split-digits", type=int, default=2, choices=[2, 3],
+                    help="mixed form: BF16 digits per operand in the first phase (3 pairs or 6)")
     ap.add_argument("--cholesky", action="store_true",
                     help="c2: Cholesky-reduced variant (S = L L^T factored inside each step's setup)")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],

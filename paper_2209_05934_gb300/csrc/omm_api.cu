@@ -74,6 +74,7 @@ struct omm_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     omm_diag diag{};
     int chunk = 8;
+    int cur_dig = 3;          // digits of the split products of the current phase
     MixedBufs mx;
     ExactBufs ex;
     double *L = nullptr;      // Cholesky variant: factor of S (m x m)
@@ -275,7 +276,7 @@ constexpr int kBN = 256;  // output tile width of the split products (UMMA N = 2
 
 omm::tc::TcArgs tc_args(omm_handle *h, int M, int N, int K) {
     omm::tc::TcArgs a{};
-    omm::tc::pairs_for_digits(kDig, a);
+    omm::tc::pairs_for_digits(h->cur_dig, a);
     a.bk = kBK;
     a.M = M;
     a.N = N;
@@ -524,6 +525,7 @@ int mixed_direction(omm_handle *h, int first) {
 // Start of the split-precision phase: H'W, SW, H_W, S_W, energy, G, D from W.
 int mixed_start(omm_handle *h) {
     const int64_t m = h->m, n = h->n, mn = m * n;
+    h->cur_dig = h->opt.split_digits;
     cudaStream_t st = h->stream;
     omm::DevState *s = h->dstate;
     { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
@@ -550,6 +552,7 @@ int mixed_start(omm_handle *h) {
 // accurate gradient of the refinement sweep (exact-digit or FP64 products).
 int mixed_iteration(omm_handle *h, bool accurate_gradient) {
     const int64_t m = h->m, n = h->n, mn = m * n;
+    h->cur_dig = accurate_gradient ? kDig : h->opt.split_digits;   // the refinement uses all three digits
     cudaStream_t st = h->stream;
     omm::DevState *s = h->dstate;
     MixedBufs &x = h->mx;
@@ -705,6 +708,7 @@ void omm_default_options(omm_options *opt) {
     opt->stream = nullptr;
     opt->refine = OMM_REFINE_EXACT;
     opt->exact_digits = 7;
+    opt->split_digits = 2;
 }
 
 const char *omm_status_str(int status) {
@@ -747,7 +751,8 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
     h->bm = block_size;
     if (opt) h->opt = *opt; else omm_default_options(&h->opt);
     if (h->opt.max_iter < 0 || (h->opt.refine != OMM_REFINE_EXACT && h->opt.refine != OMM_REFINE_FP64) ||
-        h->opt.exact_digits < 1 || h->opt.exact_digits > omm::tc::kExactMaxDigits) {
+        h->opt.exact_digits < 1 || h->opt.exact_digits > omm::tc::kExactMaxDigits || h->opt.split_digits < 2 ||
+        h->opt.split_digits > 3) {
         delete h;
         return OMM_ERR_ARG;
     }
@@ -914,10 +919,14 @@ int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, doubl
         OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
         { StageTimer t(h, OMM_STAGE_START); TRY(sparse_start(h)); }
     } else if (h->opt.precision == OMM_PREC_MIXED) {
-        // phase 1: split-precision CG to a tolerance a decade below the target
+        // phase 1: split-precision CG to a tolerance a decade below the target.
+        // With two digits the increments carry ~1e-5 relative error, so the
+        // phase-1 state drifts at that level and its energy changes cannot
+        // fall far below it: phase 1 then stops at 1e-8 and the refinement,
+        // re-anchored exactly, takes the solve the rest of the way.
         h->phase = PH_MIXED;
         omm::DevState ph = init;
-        ph.tol = fmax(0.1 * tol, 1e-12);
+        ph.tol = h->opt.split_digits == 2 ? fmax(0.1 * tol, 1e-8) : fmax(0.1 * tol, 1e-12);
         ph.orth_tol = 0.0;
         *h->hstate = ph;
         OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
