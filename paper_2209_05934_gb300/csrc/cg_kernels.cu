@@ -90,7 +90,7 @@ __device__ __forceinline__ void put3(const DigitOut &d, int64_t o, double v) {
     __nv_bfloat16 *p = (__nv_bfloat16 *)d.ptr;
     p[o] = d1;
     p[d.plane + o] = d2;
-    p[2 * d.plane + o] = d3;
+    if (d.nd > 2) p[2 * d.plane + o] = d3;
 }
 
 // ---------------------------------------------------------------- coefficients

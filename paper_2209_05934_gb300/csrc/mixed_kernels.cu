@@ -38,7 +38,7 @@ __device__ __forceinline__ void put3f(const DigitOut &d, int64_t o, float v) {
     __nv_bfloat16 *p = (__nv_bfloat16 *)d.ptr;
     p[o] = d1;
     p[d.plane + o] = d2;
-    p[2 * d.plane + o] = d3;
+    if (d.nd > 2) p[2 * d.plane + o] = d3;
 }
 
 // Digits of four consecutive FP32 values (8-byte aligned offset o): same
@@ -60,7 +60,7 @@ __device__ __forceinline__ void put3f4(const DigitOut &d, int64_t o, float4 v) {
     };
     *reinterpret_cast<uint2 *>(p + o) = pack(a1, b1);
     *reinterpret_cast<uint2 *>(p + d.plane + o) = pack(a2, b2);
-    *reinterpret_cast<uint2 *>(p + 2 * d.plane + o) = pack(a3, b3);
+    if (d.nd > 2) *reinterpret_cast<uint2 *>(p + 2 * d.plane + o) = pack(a3, b3);
 }
 
 // Digits of two consecutive FP32 values (4-byte aligned offset o), as put3f.
@@ -74,7 +74,7 @@ __device__ __forceinline__ void put3f2(const DigitOut &d, int64_t o, float v0, f
     __nv_bfloat16 *p = (__nv_bfloat16 *)d.ptr;
     *reinterpret_cast<__nv_bfloat162 *>(p + o) = a1;
     *reinterpret_cast<__nv_bfloat162 *>(p + d.plane + o) = a2;
-    *reinterpret_cast<__nv_bfloat162 *>(p + 2 * d.plane + o) = a3;
+    if (d.nd > 2) *reinterpret_cast<__nv_bfloat162 *>(p + 2 * d.plane + o) = a3;
 }
 
 // FP32 per-thread partials: summed across the warp in FP32 (their inputs are

@@ -334,10 +334,13 @@ int pack_HSW(omm_handle *h) {
 }
 
 // Digit outputs fused into the elementwise kernels of the mixed form.
-omm::DigitOut dig_W(omm_handle *h) { return {h->mx.WDd, h->mx.ldm, 2 * h->n * h->mx.ldm}; }
-omm::DigitOut dig_D(omm_handle *h) { return {h->mx.WDd + h->n * h->mx.ldm, h->mx.ldm, 2 * h->n * h->mx.ldm}; }
-omm::DigitOut dig_SWHW(omm_handle *h) { return {h->mx.SWHWd, h->mx.ld2n, h->m * h->mx.ld2n}; }
-omm::DigitOut dig_HSW(omm_handle *h) { return {h->mx.HSWd, h->mx.ld2n, h->n * h->mx.ld2n}; }
+// digit outputs carry as many planes as the current phase's products read
+omm::DigitOut dig_W(omm_handle *h) { return {h->mx.WDd, h->mx.ldm, 2 * h->n * h->mx.ldm, h->cur_dig}; }
+omm::DigitOut dig_D(omm_handle *h) {
+    return {h->mx.WDd + h->n * h->mx.ldm, h->mx.ldm, 2 * h->n * h->mx.ldm, h->cur_dig};
+}
+omm::DigitOut dig_SWHW(omm_handle *h) { return {h->mx.SWHWd, h->mx.ld2n, h->m * h->mx.ld2n, h->cur_dig}; }
+omm::DigitOut dig_HSW(omm_handle *h) { return {h->mx.HSWd, h->mx.ld2n, h->n * h->mx.ld2n, h->cur_dig}; }
 constexpr omm::DigitOut kNoDigits{nullptr, 0, 0};
 
 // [H'; S] times the digits of W (rows b_row0 = 0) or D (b_row0 = n) of WDd:
@@ -359,7 +362,7 @@ int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_s
     a.ldd = x.ldm;
     a.dplane = 2 * n * x.ldm;
     a.dout_step = dout_step * x.ldm;
-    a.ndig = kDig;
+    a.ndig = h->cur_dig;
     if (!s_identity(h)) return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, kBN, h->stream);
     TRY(omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 1, kBN, h->stream));
     // z = 1 (S times the B rows) is the B rows themselves: their FP32/FP64 values and digits
@@ -371,7 +374,7 @@ int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_s
                                      h->stream));
     const size_t pitch = (size_t)(2 * n * x.ldm) * sizeof(__nv_bfloat16);
     OMM_CUDA_TRY(cudaMemcpy2DAsync(x.HDSDd + (dout_row0 + dout_step) * x.ldm, pitch, x.WDd + b_row0 * x.ldm, pitch,
-                                   (size_t)(n * x.ldm) * sizeof(__nv_bfloat16), kDig, cudaMemcpyDeviceToDevice,
+                                   (size_t)(n * x.ldm) * sizeof(__nv_bfloat16), h->cur_dig, cudaMemcpyDeviceToDevice,
                                    h->stream));
     return OMM_OK;
 }
@@ -987,6 +990,7 @@ int omm_solve_progress(omm_handle *h, int32_t blocking, int32_t *done) {
             TRY(dense_start(h));
             TRY(omm::mx_round(mn, h->G, h->mx.G32, h->dstate, st));
         }
+        h->cur_dig = kDig;   // the refinement's products read three digits of D and W
         TRY(mixed_direction(h, 1));
         { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
         h->phase = PH_REFINE;

@@ -80,6 +80,7 @@ struct DigitOut {
     void *ptr;
     int64_t ld;
     int64_t plane;
+    int nd = 3;   // planes written (the consumer's digit count, 2 or 3)
 };
 
 // W += x D, HW += x HD, SW += x SD  (three m x n arrays, ld = m), optionally
