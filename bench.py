@@ -301,8 +301,23 @@ def run_omm(args):
 
     # ---- roofline of the dominant stage
     pk, pk_kind = peaks()
-    dom = int(np.argmax(ms_stage[:6])) if sum(ms_stage[:6]) > 0 else 0
+    # the dominant kernel is the split GEMM (tc_gemm); its products stage launches nothing
+    # else, while the gradient and contraction stages also hold exact-digit GEMMs.  The
+    # FP64 form reports its largest stage.
+    dom = 0 if prec == "mixed" else (int(np.argmax(ms_stage[:6])) if sum(ms_stage[:6]) > 0 else 0)
     roof = roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind)
+    if roof is not None and prec == "mixed":
+        # BF16 pair products per FP64-equivalent product: 3 in the two-digit first
+        # phase (its start included), 6 in the refinement
+        d_ = solver.diag()
+        p1 = (d_.iters_mixed + 1) * (3 if args.split_digits == 2 else 6)
+        p2 = d_.iters_refine * 6
+        pairs = (p1 + p2) / max(1, d_.iters_mixed + 1 + d_.iters_refine)
+        roof["bf16_pairs_per_product"] = pairs
+        roof["tensor_pipe_frac"] = roof["frac"] * pairs
+    if roof is not None and roof.get("kernel") in TRAFFIC and prec == "mixed":
+        roof["traffic"] = TRAFFIC[roof["kernel"]]["bytes_per_launch"]
+        roof["traffic_source"] = TRAFFIC[roof["kernel"]]["source"]
 
     if rank != 0:
         solver.close()
@@ -343,6 +358,11 @@ def run_omm(args):
 
 STAGES = ["products", "contract", "linesearch", "update", "gradient", "direction", "setup", "start",
           "pack", "anchor"]
+
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture of the current
+# kernel (profiles/ names the file and the command); None until captured.
+TRAFFIC = {}
 
 
 def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
@@ -445,7 +465,8 @@ def run_c4(args):
     systems = [synth.make_batch_system(int(N), seed=4000 + i) for i, N in enumerate(sizes)]
     dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
     data = [(dev(s.dense_H()), dev(s.dense_S()), dev(s.W0_dense())) for s in systems]
-    solvers = [omm.Solver(s.m, s.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6) for s in systems]
+    solvers = [omm.Solver(s.m, s.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6, graphs=args.graphs)
+               for s in systems]
 
     def batch_step():
         for sv, (H, S, _) in zip(solvers, data):
@@ -482,7 +503,9 @@ def run_c4(args):
             "config": {"workload": (f"{count} dense systems, atoms round(exp(U(ln 32, ln 384))) (seed 4): "
                                     f"m {int(min(s.m for s in systems))}..{int(max(s.m for s in systems))}, n = m/4"),
                        "precision": "mixed", "tol": 1e-10, "orth_tol": 1e-6,
-                       "execution": "one handle per system on its own stream, driven together"},
+                       "execution": "one handle per system on its own stream, driven together"
+                                    + ("; chunks of CG steps replayed as CUDA graphs" if args.graphs else ""),
+                       "graphs": bool(args.graphs)},
             "one_by_one": {"value": count / t_serial, "unit": "solves/s", "ms": 1e3 * t_serial},
             "results_equal_alone": bool(same), "all_ok": bool((st == omm.OK).all()),
             "iters": {"min": int(it.min()), "max": int(it.max())},
@@ -533,7 +556,8 @@ def run_c5(args):
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(seqs)))
         arrivals -= arrivals[0]
         reqs = [serving.Request(rid=i, arrival=float(arrivals[i]), m=seqs[i].m, n=seqs[i].n, steps=args.scf_steps,
-                                make_inputs=make_inputs_factory(i), W0=base[i][2]) for i in range(len(seqs))]
+                                make_inputs=make_inputs_factory(i), W0=base[i][2], graphs=args.graphs)
+                for i in range(len(seqs))]
         server = serving.Server(hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)))
         t0 = time.perf_counter()
         recs = server.run(reqs)
@@ -592,6 +616,8 @@ def main():
                     help="c5: sequences of the mixed-vs-FP64 serving comparison (0 skips it)")
     ap.add_argument("--split-digits", type=int, default=2, choices=[2, 3],
                     help="mixed form: BF16 digits per operand in the first phase (3 pairs or 6)")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="c4/c5: replay chunks of CG steps as captured CUDA graphs")
     ap.add_argument("--cholesky", action="store_true",
                     help="c2: Cholesky-reduced variant (S = L L^T factored inside each step's setup)")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],

@@ -104,9 +104,13 @@ typedef struct {
     int32_t exact_digits;  /* digits per operand of the exact-digit products, 1..8, default 7 */
     int32_t split_digits;  /* BF16 digits per operand of the mixed form's first phase, 2 or 3
                               (3 digit pairs or 6), default 2: the first phase then stops at
-                              RelTol 1e-8 (its increments carry ~1e-5 relative error) and the
+                              RelTol 1e-7 (its increments carry ~1e-5 relative error) and the
                               refinement, always with 3 digits and exact re-anchoring, reaches
                               tol; 3 runs the first phase to max(0.1 tol, 1e-12) */
+    int32_t graphs;        /* 1 (default): after one eager chunk of CG steps per phase, replay
+                              the chunk as a captured CUDA graph (needs a stream other than
+                              the legacy default stream; off while profiling); 0: launch
+                              every kernel from the host */
 } omm_options;
 
 enum {

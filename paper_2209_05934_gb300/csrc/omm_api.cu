@@ -75,6 +75,12 @@ struct omm_handle {
     omm_diag diag{};
     int chunk = 8;
     int cur_dig = 3;          // digits of the split products of the current phase
+    // one CUDA graph per phase for the chunk of CG steps, captured after one
+    // eager chunk of that phase (modules loaded, kernel attributes set)
+    static constexpr int kPhases = 6;
+    cudaGraphExec_t graph[kPhases] = {};
+    int64_t graph_kernels[kPhases] = {};
+    int graph_eager[kPhases] = {};
     MixedBufs mx;
     ExactBufs ex;
     double *L = nullptr;      // Cholesky variant: factor of S (m x m)
@@ -113,6 +119,8 @@ int dalloc(T **p, size_t count) {
 void free_handle(omm_handle *h) {
     if (h == nullptr) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < omm_handle::kPhases; ++i)
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
     for (int i = 0; i < omm_handle::kMaxEv; ++i)
         if (h->evs[i]) cudaEventDestroy(h->evs[i]);
     cudaFree(h->HS);
@@ -623,7 +631,7 @@ int64_t w_len(omm_handle *h) { return h->sparse ? h->sd.nnzW * h->sd.bm * h->sd.
 
 // Enqueue one chunk of CG steps of the current phase, then the state copy
 // and the event the host polls.  Kernels of a finished solve return at once.
-int enqueue_chunk(omm_handle *h) {
+int chunk_body(omm_handle *h) {
     for (int c = 0; c < h->chunk; ++c) {
         switch (h->phase) {
             case PH_MIXED: TRY(mixed_iteration(h, false)); break;
@@ -633,6 +641,52 @@ int enqueue_chunk(omm_handle *h) {
             default: return OMM_ERR_STATE;
         }
     }
+    return OMM_OK;
+}
+
+// A chunk's launches are the same every time for a phase (every kernel reads
+// its scalars from the device state), so after one eager chunk the sequence is
+// captured into a graph and replayed: one launch from the host instead of
+// ~100, which is what bounds small systems driven together.  Not on the
+// legacy default stream (it cannot be captured) nor while profiling.
+int run_chunk(omm_handle *h) {
+    const int ph = h->phase;
+    const bool capturable = h->opt.graphs != 0 && !h->profiling && h->stream != nullptr &&
+                            h->stream != cudaStreamLegacy && h->stream != cudaStreamPerThread;
+    if (!capturable) return chunk_body(h);
+    if (h->graph[ph] == nullptr && h->graph_eager[ph] == 0) {
+        ++h->graph_eager[ph];
+        return chunk_body(h);
+    }
+    if (h->graph[ph] == nullptr) {
+        const int64_t before = omm_kernel_launches();
+        OMM_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = chunk_body(h);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+        if (rc != OMM_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            omm::set_error("chunk capture failed: %s", cudaGetErrorString(ce));
+            return rc != OMM_OK ? rc : OMM_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&h->graph[ph], g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            h->graph[ph] = nullptr;
+            omm::set_error("chunk graph instantiation failed: %s", cudaGetErrorString(ie));
+            return OMM_ERR_CUDA;
+        }
+        // captured launches are counted each time the graph runs
+        h->graph_kernels[ph] = omm_kernel_launches() - before;
+        omm::count_launch(-h->graph_kernels[ph]);
+    }
+    OMM_CUDA_TRY(cudaGraphLaunch(h->graph[ph], h->stream));
+    omm::count_launch(h->graph_kernels[ph]);
+    return OMM_OK;
+}
+
+int enqueue_chunk(omm_handle *h) {
+    TRY(run_chunk(h));
     OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, h->stream));
     OMM_CUDA_TRY(cudaEventRecord(h->ev_poll, h->stream));
     return OMM_OK;
@@ -712,6 +766,7 @@ void omm_default_options(omm_options *opt) {
     opt->refine = OMM_REFINE_EXACT;
     opt->exact_digits = 7;
     opt->split_digits = 2;
+    opt->graphs = 1;
 }
 
 const char *omm_status_str(int status) {
@@ -922,14 +977,16 @@ int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, doubl
         OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
         { StageTimer t(h, OMM_STAGE_START); TRY(sparse_start(h)); }
     } else if (h->opt.precision == OMM_PREC_MIXED) {
-        // phase 1: split-precision CG to a tolerance a decade below the target.
-        // With two digits the increments carry ~1e-5 relative error, so the
-        // phase-1 state drifts at that level and its energy changes cannot
-        // fall far below it: phase 1 then stops at 1e-8 and the refinement,
-        // re-anchored exactly, takes the solve the rest of the way.
+        // phase 1: split-precision CG.  With three digits it runs to a
+        // tolerance a decade below the target.  With two, the increments carry
+        // ~1e-5 relative error and the phase-1 state drifts at that level, so
+        // its energy changes cannot fall far below it: phase 1 stops at 1e-7
+        // and the refinement, re-anchored exactly, takes the solve the rest of
+        // the way (at m = 4096 a tighter first phase only adds iterations; a
+        // looser one adds refinement steps, which cost twice as much).
         h->phase = PH_MIXED;
         omm::DevState ph = init;
-        ph.tol = h->opt.split_digits == 2 ? fmax(0.1 * tol, 1e-8) : fmax(0.1 * tol, 1e-12);
+        ph.tol = h->opt.split_digits == 2 ? fmax(0.1 * tol, 1e-7) : fmax(0.1 * tol, 1e-12);
         ph.orth_tol = 0.0;
         *h->hstate = ph;
         OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));

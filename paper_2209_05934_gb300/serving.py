@@ -47,6 +47,7 @@ class Request:
     orth_tol: float = 1e-6
     fixed_S: bool = True                 # later solves change H only (omm_set_H keeps S)
     cholesky: int = 0
+    graphs: int = 1                      # replay chunks of CG steps as CUDA graphs
 
 
 @dataclasses.dataclass
@@ -100,7 +101,8 @@ class Server:
         need = footprint_bytes(req.m, req.n, req.precision)
         if self.active and self.used + need > self.budget:
             return False
-        s = omm.Solver(req.m, req.n, 8, precision=req.precision, orth_tol=req.orth_tol, cholesky=req.cholesky)
+        s = omm.Solver(req.m, req.n, 8, precision=req.precision, orth_tol=req.orth_tol, cholesky=req.cholesky,
+                       graphs=req.graphs)
         self.used += need
         H, S = req.make_inputs(0)
         s.set_HS(H, S)
