@@ -256,6 +256,14 @@ __global__ void __launch_bounds__(192, 1)
                 tmem_wait_ld(r);
             }
             if (row < args.M) {
+                // Cin first: C may alias it as far as the compiler knows, so a load
+                // after a store would wait for that store
+                double cin[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int col = n0 + c0 + j;
+                    cin[j] = (Cin != nullptr && col < args.N) ? __ldg(&Cin[row + (int64_t)col * args.ldcin]) : 0.0;
+                }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int col = n0 + c0 + j;
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(192, 1)
                         out = (e > -960 && e < 900) ? sw_i64_scaled(R, e) : ldexp((double)R, e);
                     }
                     if (args.alpha != 1.0) out *= args.alpha;
-                    if (Cin != nullptr) out = fma(args.beta, Cin[row + (int64_t)col * args.ldcin], out);
+                    if (Cin != nullptr) out = fma(args.beta, cin[j], out);
                     if (C32 != nullptr) C32[row + (int64_t)col * args.ldc] = sw_d2f(out);
                     else C[row + (int64_t)col * args.ldc] = out;
                 }

@@ -154,7 +154,22 @@ __global__ void __launch_bounds__(192, 1)
             // FP32 epilogue: no FP64 arithmetic except reading an FP64 Cin
             float *C32 = args.C32 + (int64_t)z * args.c_step;
             const float alpha = (float)args.alpha, beta = (float)args.beta;
+            // Cin is fetched one 16-column chunk ahead as raw FP64 and converted
+            // only when used: the compiler cannot rule out that C32 aliases Cin,
+            // so a load placed after a store, or tied to a branchy conversion,
+            // would wait out one DRAM round trip per output
+            const bool rd = Cin != nullptr && row < args.M;
+            auto load_cin = [&](int c0, double (&dst)[16]) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = n0 + c0 + i;
+                    dst[i] = (rd && col < args.N) ? __ldg(&Cin[row + (int64_t)col * args.ldcin]) : 0.0;
+                }
+            };
+            double cin[16], cin_next[16];
+            load_cin(0, cin);
             for (int c0 = 0; c0 < BN; c0 += 16) {
+                if (c0 + 16 < BN) load_cin(c0 + 16, cin_next);
                 float v[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] = 0.f;
@@ -172,7 +187,7 @@ __global__ void __launch_bounds__(192, 1)
                         const int col = n0 + c0 + i;
                         if (col >= args.N) break;
                         float out = alpha * v[i];
-                        if (Cin != nullptr) out = fmaf(beta, sw_d2f(Cin[row + (int64_t)col * args.ldcin]), out);
+                        if (Cin != nullptr) out = fmaf(beta, sw_d2f(cin[i]), out);
                         C32[row + (int64_t)col * args.ldc] = out;
                         if (Dd != nullptr) {
                             const int64_t o = row + (int64_t)col * args.ldd;
@@ -185,9 +200,23 @@ __global__ void __launch_bounds__(192, 1)
                         }
                     }
                 }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) cin[i] = cin_next[i];
             }
         } else {
+            // Cin one chunk ahead of the stores, as in the FP32 epilogue
+            const bool rd = Cin != nullptr && row < args.M;
+            auto load_cin = [&](int c0, double (&dst)[16]) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = n0 + c0 + i;
+                    dst[i] = (rd && col < args.N) ? __ldg(&Cin[row + (int64_t)col * args.ldcin]) : 0.0;
+                }
+            };
+            double cin[16], cin_next[16];
+            load_cin(0, cin);
             for (int c0 = 0; c0 < BN; c0 += 16) {
+                if (c0 + 16 < BN) load_cin(c0 + 16, cin_next);
                 double v[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] = 0.0;
@@ -205,7 +234,7 @@ __global__ void __launch_bounds__(192, 1)
                         const int col = n0 + c0 + i;
                         if (col >= args.N) break;
                         double out = args.alpha * v[i];
-                        if (Cin != nullptr) out = fma(args.beta, Cin[row + (int64_t)col * args.ldcin], out);
+                        if (Cin != nullptr) out = fma(args.beta, cin[i], out);
                         C[row + (int64_t)col * args.ldc] = out;
                         if (Dd != nullptr) {
                             __nv_bfloat16 d1, d2, d3;
@@ -217,6 +246,8 @@ __global__ void __launch_bounds__(192, 1)
                         }
                     }
                 }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) cin[i] = cin_next[i];
             }
         }
     }
