@@ -102,11 +102,13 @@ typedef struct {
     int32_t refine;        /* arithmetic of the mixed form's refinement sweep (re-anchoring
                               and gradient): OMM_REFINE_EXACT (default) or OMM_REFINE_FP64 */
     int32_t exact_digits;  /* digits per operand of the exact-digit products, 1..8, default 7 */
-    int32_t split_digits;  /* BF16 digits per operand of the mixed form's first phase, 2 or 3
-                              (3 digit pairs or 6), default 2: the first phase then stops at
-                              RelTol 1e-7 (its increments carry ~1e-5 relative error) and the
-                              refinement, always with 3 digits and exact re-anchoring, reaches
-                              tol; 3 runs the first phase to max(0.1 tol, 1e-12) */
+    int32_t split_digits;  /* BF16 digits per operand of the mixed form's split products (the
+                              CG increments H'D, SD, the contractions and the first phase's
+                              gradient), 2 or 3 (3 digit pairs or 6), default 2: the first
+                              phase then stops at RelTol 1e-7 (its increments carry ~1e-5
+                              relative error) and the refinement, re-anchored exactly and with
+                              an exact-digit gradient, reaches tol; 3 runs the first phase to
+                              max(0.1 tol, 1e-12) */
     int32_t graphs;        /* 1 (default): after one eager chunk of CG steps per phase, replay
                               the chunk as a captured CUDA graph (needs a stream other than
                               the legacy default stream; off while profiling); 0: launch

@@ -563,7 +563,10 @@ int mixed_start(omm_handle *h) {
 // accurate gradient of the refinement sweep (exact-digit or FP64 products).
 int mixed_iteration(omm_handle *h, bool accurate_gradient) {
     const int64_t m = h->m, n = h->n, mn = m * n;
-    h->cur_dig = accurate_gradient ? kDig : h->opt.split_digits;   // the refinement uses all three digits
+    // the increments keep the split digit count in both phases: in the
+    // refinement they are small against the exactly re-anchored state and the
+    // exact-digit gradient, so two digits cost no extra steps at C2
+    h->cur_dig = h->opt.split_digits;
     cudaStream_t st = h->stream;
     omm::DevState *s = h->dstate;
     MixedBufs &x = h->mx;
@@ -1047,7 +1050,7 @@ int omm_solve_progress(omm_handle *h, int32_t blocking, int32_t *done) {
             TRY(dense_start(h));
             TRY(omm::mx_round(mn, h->G, h->mx.G32, h->dstate, st));
         }
-        h->cur_dig = kDig;   // the refinement's products read three digits of D and W
+        h->cur_dig = h->opt.split_digits;
         TRY(mixed_direction(h, 1));
         { StageTimer t(h, OMM_STAGE_PACK); TRY(pack_W(h)); }
         h->phase = PH_REFINE;
