@@ -464,13 +464,20 @@ int exact_gradient(omm_handle *h) {
     const MixedBufs &x = h->mx;
     ExactBufs &e = h->ex;
     cudaStream_t st = h->stream;
+    // The gradient is consumed in FP32, but its digits must beat the
+    // cancellation between 4 H'W and 2 [SW H_W + H'W S_W] near convergence.
+    // Six digits (21 pair products instead of 28; error ~2^-41 of the terms)
+    // keep the refinement's step count at m = 4096 and on the batched systems;
+    // five digits (~2^-34) stalled it at m = 4096.
+    const int sg = e.s < 6 ? e.s : 6;
     {
         StageTimer t(h, OMM_STAGE_PACK);
-        TRY(omm::tc::exact_pack(false, m, 2 * n, h->SWHW, m, e.eSWHW, e.SWHWx, x.ld2n, m * x.ld2n, e.s, h->dstate, st));
-        TRY(omm::tc::exact_pack(true, 2 * n, n, h->h0s0, 2 * n, e.eHSW, e.HSWx, x.ld2n, n * x.ld2n, e.s, h->dstate, st));
+        TRY(omm::tc::exact_pack(false, m, 2 * n, h->SWHW, m, e.eSWHW, e.SWHWx, x.ld2n, m * x.ld2n, sg, h->dstate, st));
+        TRY(omm::tc::exact_pack(true, 2 * n, n, h->h0s0, 2 * n, e.eHSW, e.HSWx, x.ld2n, n * x.ld2n, sg, h->dstate, st));
     }
     StageTimer t(h, OMM_STAGE_GRADIENT);
     omm::tc::ExactArgs a = exact_args(h, (int)m, (int)n, (int)(2 * n));
+    omm::tc::exact_pairs(sg, a);
     a.alpha = -2.0;
     a.beta = 4.0;
     a.Cin = h->SWHW + m * n;
