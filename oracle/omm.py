@@ -189,14 +189,14 @@ def line_min(c) -> tuple[float, int]:
     then to x > 0.  With c4 = c3 = 0 and c2 > 0 the parabola's vertex is taken.
     Returns (x, status); status is ERR_LINESEARCH when no minimum exists (the
     paper warns that the line minimisation can have none, section
-    "Recommendations for OMM solver use").
+    "Recommendations for OMM solver use").  With c4 < 0 (the Kim functional with
+    eta inside the gap, where H' has positive eigenvalues) the quartic is
+    unbounded below, and the lowest local minimum is taken when there is one.
     """
     c = np.asarray(c, dtype=np.float64)
     if c[4] == 0.0 and c[3] == 0.0:
         if c[2] > 0.0:
             return -c[1] / (2.0 * c[2]), OK
-        return 0.0, ERR_LINESEARCH
-    if c[4] < 0.0:
         return 0.0, ERR_LINESEARCH
     deriv = [4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1]]
     while deriv and deriv[0] == 0.0:
@@ -235,16 +235,18 @@ class Result:
 
 
 def omm_cg(H, S, W0, tol: float = 1e-10, eta: float | None = None, max_iter: int = 10000,
-           orth_tol: float | None = None, mask=None) -> Result:
+           orth_tol: float | None = None, mask=None, n_occ: int | None = None) -> Result:
     """Conjugate-gradient minimisation of the (shifted) Ordejon-Mauri functional.
 
     Steps, in the paper's order (sections "Overview of OMM approaches" and
     "Solver library", Table 1):
-      0. H' = H - eta S (Kim shift with n' = n; eta=None picks the Gershgorin
-         bound so the exact line search is always well posed).
+      0. H' = H - eta S (the Kim shift; eta=None picks the Gershgorin bound so
+         the exact line search is always well posed).  The Kim functional
+         proper (section "Overview of OMM approaches", steps (1)-(3)) takes
+         n' = W0.shape[1] > n_occ columns and eta inside the gap.
       each iteration k:
       1. H_W = W^T H' W, S_W = W^T S W by definition; energy
-         E_k = 2 (2 tr H_W - <S_W, H_W>) + 2 eta n.
+         E_k = 2 (2 tr H_W - <S_W, H_W>) + 2 eta n_occ (n_occ = n' by default).
       2. stop at k >= 1 when |2 (E_k - E_{k-1}) / (E_k + E_{k-1})| < tol
          (OMM.RelTol) and, if orth_tol is given, ||S_W - I||_F < orth_tol.
       3. G = 2 (2 H'W - S W H_W - H'W S_W), restricted to W's pattern.
@@ -258,6 +260,7 @@ def omm_cg(H, S, W0, tol: float = 1e-10, eta: float | None = None, max_iter: int
         eta = gershgorin_eta(H, S)
     Hs = shift(H, S, eta)
     n = W0.shape[1]
+    n_occ = n if n_occ is None else n_occ
     W = apply_mask(W0.copy() if not sp.issparse(W0) else W0.copy(), mask)
     if sp.issparse(W):
         W = sp.csr_matrix(W)
@@ -272,7 +275,7 @@ def omm_cg(H, S, W0, tol: float = 1e-10, eta: float | None = None, max_iter: int
         SW = S @ W
         H_W = W.T @ HW
         S_W = W.T @ SW
-        E = 2.0 * (2.0 * trace(H_W) - frob(S_W, H_W)) + 2.0 * eta * n
+        E = 2.0 * (2.0 * trace(H_W) - frob(S_W, H_W)) + 2.0 * eta * n_occ
         history.append(E)
         orth = float(np.linalg.norm(_dense(S_W) - np.eye(n)))
         if k >= 1:

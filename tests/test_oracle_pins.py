@@ -146,6 +146,14 @@ def test_line_min_closed_forms():
     # unbounded below: no minimum
     assert O.line_min([0.0, -1.0, 1.0, 0.0, -1.0])[1] == O.ERR_LINESEARCH
     assert O.line_min([0.0, -1.0, -1.0, 0.0, 0.0])[1] == O.ERR_LINESEARCH
+    # c4 < 0 with a local minimum between two maxima (Kim functional, eta in
+    # the gap): -x^4 + 2x^2 - 0.5x has its wells' bottom near 0.127 and maxima
+    # near -1.06 and 0.93; brute force between the maxima
+    c = [0.0, -0.5, 2.0, 0.0, -1.0]
+    x, st = O.line_min(c)
+    grid = np.linspace(-1.0, 0.9, 1900001)
+    assert st == O.OK and x == pytest.approx(grid[np.argmin(O.quartic(c, grid))], abs=2e-6)
+    assert abs(-4 * x ** 3 + 4 * x - 0.5) < 1e-12
 
 
 def test_gershgorin_bounds_spectrum(c1_system):
@@ -171,6 +179,27 @@ def test_cg_reaches_jacobi_ground_state(tiny_system):
     rho = O.density_matrix(res.W, S)
     # (rho/2) S (rho/2) = rho/2: projector onto the occupied subspace
     np.testing.assert_allclose(0.25 * rho @ S @ rho, 0.5 * rho, atol=1e-7)
+
+
+def test_kim_functional_reaches_jacobi_ground_state(tiny_system):
+    """Kim construction (section "Overview of OMM approaches", steps (1)-(3)):
+    n' = n + 4 columns, eta inside the gap, energy + 2 eta n.  The minimum is
+    still 2 x the sum of the n lowest eigenvalues; the extra columns carry no
+    charge (2 Tr[(2I - S_W) S_W] = 2n) and rho/2 is the occupied projector."""
+    H, S, n = tiny_system.dense_H(), tiny_system.dense_S(), tiny_system.n
+    lam = jacobi.generalized_eigenvalues(H.tolist(), S.tolist())
+    eta = 0.5 * (lam[n - 1] + lam[n])
+    rng = np.random.default_rng(5)
+    # small start: along an unoccupied direction the functional 4 lam t^2 - 2 lam t^4
+    # (lam > 0) has its barrier at t = 1, so the columns start well inside it
+    W0 = 0.2 * np.hstack([tiny_system.W0_dense(), rng.standard_normal((tiny_system.m, 4)) / np.sqrt(tiny_system.m)])
+    res = O.omm_cg(H, S, W0, tol=1e-15, eta=eta, n_occ=n, max_iter=20000)
+    assert res.status in (O.OK, O.ERR_MAXITER)
+    e_min = 2.0 * sum(lam[:n])
+    assert res.E == pytest.approx(e_min, rel=1e-9)
+    assert O.charge(res.W, S) == pytest.approx(2 * n, rel=1e-8)
+    rho = O.density_matrix(res.W, S)
+    np.testing.assert_allclose(0.25 * rho @ S @ rho, 0.5 * rho, atol=1e-6)
 
 
 def test_cg_c1_energy_and_monotone(c1_system):
