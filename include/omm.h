@@ -113,6 +113,15 @@ typedef struct {
                               the chunk as a captured CUDA graph (needs a stream other than
                               the legacy default stream; off while profiling); 0: launch
                               every kernel from the host */
+    int32_t n_occupied;    /* Kim functional (section "Overview of OMM approaches", steps
+                              (1)-(3)): with 0 < n_occupied < n the handle's n columns are
+                              n' > n_occupied trial orbitals, the reported energy is
+                              E~_eta + 2 eta n_occupied, and eta must be given inside the gap
+                              (eta_auto = 0; the Gershgorin bound lies above the spectrum).
+                              Start from small coefficients (the functional is unbounded
+                              along unoccupied directions beyond a barrier near unit norm) and
+                              leave orth_tol at 0: S_W converges to diag(I, 0).  0 (default):
+                              n_occupied = n */
 } omm_options;
 
 enum {

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(NT) nn_update_kernel(int n, double *h0, double
     double tot[NE];
     if (!publish_and_collect<NE>(v, partials, counter, tot, red)) return;
     if (threadIdx.x != 0) return;
-    const double E = 2.0 * (2.0 * tot[0] - tot[1]) + 2.0 * state->eta * (double)n;
+    const double E = 2.0 * (2.0 * tot[0] - tot[1]) + state->e_shift;
     state->trh0 = tot[0];
     state->sh = tot[1];
     state->orth2 = tot[2];

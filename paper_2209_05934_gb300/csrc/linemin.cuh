@@ -2,9 +2,11 @@
 // (the exact line search of the Introduction), shared by every CG form.
 //
 // Rule: among the real roots of E'(x) with positive curvature, the lowest E
-// wins; ties go to the smaller |x|, then to x > 0.  c4 < 0 (no minimum) and
-// c4 = c3 = 0 with c2 <= 0 are OMM_ERR_LINESEARCH; non-finite data is
-// OMM_ERR_NONFINITE.
+// wins; ties go to the smaller |x|, then to x > 0.  With c4 < 0 (the Kim
+// functional with eta inside the gap, where H' has positive eigenvalues) the
+// quartic is unbounded below and only its local minima are candidates.  No
+// candidate, or c4 = c3 = 0 with c2 <= 0, is OMM_ERR_LINESEARCH; non-finite
+// data is OMM_ERR_NONFINITE.
 //
 // The roots of E' = 4c4 x^3 + 3c3 x^2 + 2c2 x + c1 are found by one warp:
 // multisection on the Cauchy bracket (-R, R) -- every round the 32 lanes
@@ -64,7 +66,6 @@ __device__ __forceinline__ int trivial_cases(const double *c, double *r, int *nr
         }
         return OMM_ERR_LINESEARCH;
     }
-    if (c[4] < 0.0) return OMM_ERR_LINESEARCH;
     *done = false;
     *nr = 0;
     if (c[4] == 0.0) {   // c3 != 0: E' = 3 c3 x^2 + 2 c2 x + c1
@@ -126,7 +127,9 @@ __device__ inline int quartic_min_warp(const double *c, double *xout) {
     bool done;
     const int st = trivial_cases(c, r, &nr, xout, &done);
     if (done) return st;
-    const double a = 4.0 * c[4], b = 3.0 * c[3], cc = 2.0 * c[2], d = c[1];
+    // E' with a positive leading coefficient (negated when c4 < 0: same roots)
+    const double sg = c[4] > 0.0 ? 1.0 : -1.0;
+    const double a = sg * 4.0 * c[4], b = sg * 3.0 * c[3], cc = sg * 2.0 * c[2], d = sg * c[1];
     auto f = [&](double t) { return ((a * t + b) * t + cc) * t + d; };
     const double R = 1.0 + fmax(fabs(b), fmax(fabs(cc), fabs(d))) / a;
     double lo = -R, hi = R;   // f(lo) < 0 < f(hi): a > 0 and every root lies inside

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
 #pragma unroll
     for (int q = 0; q < NC; ++q) tot[q] = __shfl_sync(0xffffffffu, tot[q], 0);
     double c[5];
-    c[0] = state->E - 2.0 * state->eta * (double)n;   // the shifted functional at x = 0
+    c[0] = state->E - state->e_shift;   // the shifted functional at x = 0
     c[1] = 2.0 * state->gD;
     c[2] = 2.0 * (2.0 * tot[0] - tot[1] - 2.0 * (tot[2] + tot[3]) - tot[4]);
     c[3] = 2.0 * (-2.0 * tot[5] - 2.0 * tot[6]);
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
     for (int q = 0; q < 5; ++q) state->c[q] = c[q];
     state->x = x;
     state->x_f = (float)x;
-    state->E_next = lm::quartic_val(c, x) + 2.0 * state->eta * (double)n;
+    state->E_next = lm::quartic_val(c, x) + state->e_shift;
     if (st != OMM_OK) {
         state->status = st;
         state->done = 1;

@@ -213,6 +213,10 @@ double *scr(omm_handle *h, int i) {
 // S W = W are copies, not products.
 bool s_identity(const omm_handle *h) { return h->opt.cholesky != 0 && !h->sparse; }
 
+// electron pairs counted in the energy's 2 eta n_occ term: n, or fewer with the
+// Kim functional's extra columns
+int64_t n_occ(const omm_handle *h) { return h->opt.n_occupied > 0 ? h->opt.n_occupied : h->n; }
+
 int dense_iteration(omm_handle *h) {
     const int64_t m = h->m, n = h->n, mn = m * n;
     cudaStream_t st = h->stream;
@@ -777,6 +781,7 @@ void omm_default_options(omm_options *opt) {
     opt->exact_digits = 7;
     opt->split_digits = 2;
     opt->graphs = 1;
+    opt->n_occupied = 0;
 }
 
 const char *omm_status_str(int status) {
@@ -820,7 +825,8 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
     if (opt) h->opt = *opt; else omm_default_options(&h->opt);
     if (h->opt.max_iter < 0 || (h->opt.refine != OMM_REFINE_EXACT && h->opt.refine != OMM_REFINE_FP64) ||
         h->opt.exact_digits < 1 || h->opt.exact_digits > omm::tc::kExactMaxDigits || h->opt.split_digits < 2 ||
-        h->opt.split_digits > 3) {
+        h->opt.split_digits > 3 || h->opt.n_occupied < 0 || h->opt.n_occupied > n ||
+        (h->opt.n_occupied > 0 && h->opt.n_occupied < n && h->opt.eta_auto)) {
         delete h;
         return OMM_ERR_ARG;
     }
@@ -974,6 +980,7 @@ int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, doubl
     }
     omm::DevState init{};
     init.eta = h->diag.eta;
+    init.e_shift = 2.0 * h->diag.eta * (double)n_occ(h);
     init.tol = tol;
     init.orth_tol = h->opt.orth_tol;
     init.max_iter = h->opt.max_iter;
@@ -1043,6 +1050,7 @@ int omm_solve_progress(omm_handle *h, int32_t blocking, int32_t *done) {
         h->k_mixed = h->hstate->k;
         omm::DevState rf{};
         rf.eta = h->diag.eta;
+        rf.e_shift = 2.0 * h->diag.eta * (double)n_occ(h);
         rf.tol = h->tol_target;
         rf.orth_tol = h->opt.orth_tol;
         rf.max_iter = h->opt.max_iter;

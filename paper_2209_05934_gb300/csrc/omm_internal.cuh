@@ -46,6 +46,7 @@ struct DevState {
     int wait_timeout;            // set by a tensor-core kernel whose bounded wait gave up
     double gD;                   // <G, D> of the current direction (= c1 / 2)
     double E_next;               // energy at the line minimum, from the quartic
+    double e_shift;              // constant of the reported energy: 2 eta n_occ
     float x_f, beta_f;           // x and beta rounded once for the FP32 kernels
 };
 

@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(NT) nn_update_kernel(int64_t nnzN, const int32
     double tot[NE3];
     if (!publish_and_collect<NE3>(v, partials, counter, tot, red)) return;
     if (threadIdx.x != 0) return;
-    const double E = 2.0 * (2.0 * tot[0] - tot[1]) + 2.0 * state->eta * (double)n;
+    const double E = 2.0 * (2.0 * tot[0] - tot[1]) + state->e_shift;
     state->orth2 = tot[2];
     if (!isfinite(E)) {
         state->status = OMM_ERR_NONFINITE;

@@ -29,7 +29,8 @@ class Options(C.Structure):
     _fields_ = [("eta", C.c_double), ("eta_auto", C.c_int32), ("precision", C.c_int32),
                 ("cholesky", C.c_int32), ("max_iter", C.c_int32), ("orth_tol", C.c_double),
                 ("filter_eps", C.c_double), ("stream", C.c_void_p), ("refine", C.c_int32),
-                ("exact_digits", C.c_int32), ("split_digits", C.c_int32), ("graphs", C.c_int32)]
+                ("exact_digits", C.c_int32), ("split_digits", C.c_int32), ("graphs", C.c_int32),
+                ("n_occupied", C.c_int32)]
 
 
 class Pattern(C.Structure):

@@ -87,6 +87,12 @@ def test_line_min_matches_oracle(omm):
         cases.append(c)
     p = np.polynomial.polynomial.polymul([1, -2, 1], [4, 4, 1])
     cases.append(np.array(p) + np.array([0, 0.5, 0, 0, 0]))
+    # c4 < 0 (Kim functional, eta in the gap): a local minimum, or none
+    cases += [np.array([0.0, -0.5, 2.0, 0.0, -1.0]), np.array([1.0, 0.3, 1.5, -0.2, -0.4])]
+    for _ in range(20):
+        c = rng.standard_normal(5)
+        c[4] = -abs(c[4]) - 1e-3
+        cases.append(c)
     cin = torch.zeros(5, dtype=torch.float64, device="cuda")
     x = torch.zeros(1, dtype=torch.float64, device="cuda")
     stt = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -165,6 +171,41 @@ def test_host_buffers_and_warm_start(omm):
     assert abs(E3 - ref3.E) / abs(ref3.E) < 1e-10
     assert it3 < it1
     s.close()
+
+
+def _kim_inputs(dims, seed, extra):
+    import synth
+    import scipy.linalg as sla
+    sysm = synth.make_system(*dims, seed=seed)
+    H, S = sysm.dense_H(), sysm.dense_S()
+    lam = sla.eigh(H, S, eigvals_only=True)
+    eta = 0.5 * (lam[sysm.n - 1] + lam[sysm.n])       # inside the gap
+    rng = np.random.default_rng(seed + 7)
+    # small start: inside the barrier the unoccupied directions have at unit norm
+    W0 = 0.2 * np.hstack([sysm.W0_dense(), rng.standard_normal((sysm.m, extra)) / np.sqrt(sysm.m)])
+    return sysm, H, S, np.asfortranarray(W0), eta, 2.0 * lam[:sysm.n].sum()
+
+
+def test_kim_functional_matches_oracle(omm):
+    """Kim construction: n' = n + 8 columns, eta in the gap, energy + 2 eta n."""
+    sysm, H, S, W0, eta, e_min = _kim_inputs((4, 4, 3), 2, 8)
+    n1 = W0.shape[1]
+    s = omm.Solver(sysm.m, n1, 8, eta_auto=0, eta=eta, n_occupied=sysm.n)
+    s.set_HS(dev(H), dev(S))
+    W = empty_cm(sysm.m, n1)
+    E, iters, st = s.solve(dev(W0), tol=1e-13, W_out=W)
+    ref = O.omm_cg(H, S, W0, tol=1e-13, eta=eta, n_occ=sysm.n)
+    assert st == omm.OK and ref.status == O.OK
+    assert abs(E - ref.E) / abs(ref.E) < 1e-10
+    assert abs(E - e_min) / abs(e_min) < 1e-10
+    Wn = W.cpu().numpy()
+    assert O.charge(Wn, S) == pytest.approx(2 * sysm.n, rel=1e-8)
+    assert s.diag().charge == pytest.approx(2 * sysm.n, rel=1e-8)
+    np.testing.assert_allclose(O.density_matrix(Wn, S), O.density_matrix(ref.W, S), atol=2e-5)
+    s.close()
+    # the Gershgorin bound is not in a gap: refused with extra columns
+    with pytest.raises(omm.OmmError):
+        omm.Solver(sysm.m, n1, 8, n_occupied=sysm.n)
 
 
 def test_state_and_argument_errors(omm):

@@ -51,6 +51,28 @@ def test_mixed_solve_matches_oracle(omm, dims, refine):
     s.close()
 
 
+def test_kim_functional_mixed(omm):
+    """Kim construction in the mixed form (orth_tol stays 0: S_W -> diag(I, 0))."""
+    import synth
+    import scipy.linalg as sla
+    sysm = synth.make_system(4, 4, 3, seed=2)
+    H, S = sysm.dense_H(), sysm.dense_S()
+    lam = sla.eigh(H, S, eigvals_only=True)
+    eta = 0.5 * (lam[sysm.n - 1] + lam[sysm.n])
+    rng = np.random.default_rng(9)
+    W0 = np.asfortranarray(0.2 * np.hstack([sysm.W0_dense(), rng.standard_normal((sysm.m, 8)) / np.sqrt(sysm.m)]))
+    n1 = W0.shape[1]
+    s = omm.Solver(sysm.m, n1, 8, precision=omm.PREC_MIXED, eta_auto=0, eta=eta, n_occupied=sysm.n)
+    s.set_HS(dev(H), dev(S))
+    W = torch.zeros((n1, sysm.m), dtype=torch.float64, device="cuda").T
+    E, iters, st = s.solve(dev(W0), tol=1e-11, W_out=W)
+    e_min = 2.0 * lam[:sysm.n].sum()
+    assert st == omm.OK
+    assert abs(E - e_min) / abs(e_min) < 1e-8
+    assert O.charge(W.cpu().numpy(), S) == pytest.approx(2 * sysm.n, rel=1e-6)
+    s.close()
+
+
 def test_mixed_repeatable_bitwise(omm):
     """Fixed reduction orders: the same solve twice gives identical bits."""
     import synth
