@@ -142,8 +142,10 @@ def density_matrix(W, S):
 
 
 def energy_density_matrix(W, H, S, eta: float = 0.0):
-    """rho_E = 2 W H_W W^T, plus eta*rho for the Kim functional (defined with Eq. 6 and the
-    Kim construction, step (3)); H is the unshifted Hamiltonian."""
+    """rho_E = 2 W H_W W^T (defined with Eq. 6), plus eta*rho in the Kim construction
+    (step (3)).  H is the Hamiltonian the functional was minimised for, i.e. the
+    shifted H' = H - eta S when eta != 0, so that at S_W = I the result equals
+    2 W H_W W^T of the unshifted H."""
     Wd = _dense(W)
     H_W = Wd.T @ (_dense(H) @ Wd)
     rho_E = 2.0 * Wd @ H_W @ Wd.T

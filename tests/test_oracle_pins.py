@@ -181,6 +181,20 @@ def test_cg_reaches_jacobi_ground_state(tiny_system):
     np.testing.assert_allclose(0.25 * rho @ S @ rho, 0.5 * rho, atol=1e-7)
 
 
+def test_density_matrices_at_the_minimum(small_system):
+    """At the exact minimum, rho = 2 V V^T and rho_E = 2 V Lambda V^T for the n
+    lowest S-orthonormal generalised eigenvectors V (Eq. 5 and the energy
+    density defined with Eq. 6), with the shifted Hamiltonian and its eta."""
+    H, S, n = small_system.dense_H(), small_system.dense_S(), small_system.n
+    lam, V = sla.eigh(H, S)
+    res = O.omm_cg(H, S, small_system.W0_dense(), tol=1e-15, max_iter=5000)
+    Vn = V[:, :n]
+    np.testing.assert_allclose(O.density_matrix(res.W, S), 2 * Vn @ Vn.T, atol=1e-7)
+    Hs = O.shift(H, S, res.eta)
+    np.testing.assert_allclose(O.energy_density_matrix(res.W, Hs, S, res.eta),
+                               2 * Vn @ np.diag(lam[:n]) @ Vn.T, atol=1e-6)
+
+
 def test_kim_functional_reaches_jacobi_ground_state(tiny_system):
     """Kim construction (section "Overview of OMM approaches", steps (1)-(3)):
     n' = n + 4 columns, eta inside the gap, energy + 2 eta n.  The minimum is
