@@ -261,6 +261,20 @@ def run_omm(args):
     e_exact = g.get("exact_E")
     rel_err = abs(E - e_exact) / abs(e_exact) if e_exact else None
 
+    # ---- the density matrix of the solution (Eq. 5), what an SCF step consumes
+    rho_d = torch.zeros((m, m), dtype=torch.float64, device="cuda").T
+    solver.get_density(omm.DENSITY_RHO, rho_d)          # first call allocates its workspace
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(3):
+        solver.get_density(omm.DENSITY_RHO, rho_d)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    density = {"rho_ms": r0.elapsed_time(r1) / 3, "trace_rho_S": float(torch.sum(rho_d * Sd).item()),
+               "electrons": 2 * n}
+    del rho_d
+
     # ---- the plain FP64 GPU form beside the chosen one: one whole FP64 solve
     fp64_beside = None
     if prec == "mixed" and not args.no_fp64_beside:
@@ -354,6 +368,7 @@ def run_omm(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "fp64_gpu_beside": fp64_beside,
+        "density_matrix": density,
         "e2e": {"value": ws * e2e_steps / (t_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(2 * m * m * 8 + m * n * 8),
                 "d2h_bytes_per_step": int(m * n * 8 + 8)},

@@ -239,6 +239,25 @@ int omm_get_diag(omm_handle *h, omm_diag *d);
  */
 int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device);
 
+/*
+ * Density matrix (Eq. 5) or energy density (defined with Eq. 6) of the last
+ * solve, as an SCF step and the forces consume them:
+ *   OMM_DENSITY_RHO    rho   = 2 W (2I - S_W) W^T
+ *   OMM_DENSITY_RHO_E  rho_E = 2 W H'_W W^T + eta rho
+ * with H' = H - eta S the matrix the functional was minimised for (the Kim
+ * construction's step (3); at S_W = I this is 2 W H_W W^T of the unshifted H).
+ * W is the solution in the original basis (also for the Cholesky variant);
+ * S_W and H'_W are formed afresh from it.  dst: m x m column-major, host
+ * unless on_device.  Every product runs as an exact-digit tensor-core GEMM
+ * (FP64-accurate).  The first call allocates the handle's workspace for it
+ * (about 14 (m + n) m bytes with 7 digits, plus m^2 doubles for host output).  Dense handles only (OMM_ERR_UNSUPPORTED for
+ * sparse); OMM_ERR_STATE unless omm_solve / omm_solve_end returned since the
+ * last omm_set_HS / omm_set_H.
+ */
+#define OMM_DENSITY_RHO 0
+#define OMM_DENSITY_RHO_E 1
+int omm_get_density(omm_handle *h, int32_t which, double *dst, int32_t on_device);
+
 void omm_destroy(omm_handle *h);
 const char *omm_status_str(int status);
 

@@ -554,6 +554,28 @@ int launch_shift(int64_t mm, const double *H, const double *S, double *Hs, const
     return OMM_OK;
 }
 
+namespace {
+// K = 2I - S_W (mode 0) or H'_W + eta (2I - S_W) (mode 1), n x n column-major,
+// from [H'_W ; S_W] (2n x n, ld 2n)
+__global__ void density_K_kernel(int64_t n, const double *__restrict__ h0s0, double eta, int mode, double *K) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx % n, j = idx / n;
+        const double t = (i == j ? 2.0 : 0.0) - h0s0[(n + i) + j * 2 * n];
+        K[i + j * n] = mode == 0 ? t : fma(eta, t, h0s0[i + j * 2 * n]);
+    }
+}
+}  // namespace
+
+int launch_density_K(int64_t n, const double *h0s0, double eta, int mode, double *K, cudaStream_t st) {
+    int64_t nb = ceil_div(n * n, 256);
+    if (nb > 152 * 8) nb = 152 * 8;
+    density_K_kernel<<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, st>>>(n, h0s0, eta, mode, K);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
 int launch_gershgorin(int64_t m, const double *H, const double *S, double *scratch,
                       unsigned int *counter, DevState *state, cudaStream_t st) {
     int64_t nb = ceil_div(m, NT / 32);

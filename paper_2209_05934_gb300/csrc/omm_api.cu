@@ -71,6 +71,12 @@ struct omm_handle {
     omm::DevState *hstate = nullptr;   // pinned
     bool have_HS = false, have_W = false;
     bool have_S = false;      // a successful dense setup left S (and the Cholesky factor) in place
+    bool solved = false;      // omm_solve_end has returned a solution for the current H, S
+    // density matrices (omm_get_density): K (n x n), T = W K (m x n), the
+    // exact-digit GEMM workspace and, for host output, an m x m staging array
+    double *dK = nullptr, *dT = nullptr, *dOut = nullptr;
+    void *dWs = nullptr;
+    int64_t dWs_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     omm_diag diag{};
     int chunk = 8;
@@ -155,6 +161,10 @@ void free_handle(omm_handle *h) {
     cudaFree(h->S0);
     cudaFree(h->cw.ws);
     cudaFree(h->cw.Linv);
+    cudaFree(h->dK);
+    cudaFree(h->dT);
+    cudaFree(h->dOut);
+    cudaFree(h->dWs);
     omm::sp::release(h->sd);
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -710,6 +720,7 @@ int enqueue_chunk(omm_handle *h) {
 // previous S, and with the Cholesky variant its factor, are kept).
 int dense_set(omm_handle *h, const double *H, const double *S, bool on_device) {
     const int64_t m = h->m, mm = m * m;
+    h->solved = false;
     cudaStream_t st = h->stream;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const bool chol = h->opt.cholesky != 0;
@@ -961,6 +972,7 @@ int omm_set_H(omm_handle *h, const double *H, int32_t on_device) {
 
 int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, double tol) {
     if (h == nullptr || !(tol >= 0.0)) return OMM_ERR_ARG;
+    h->solved = false;
     if (!h->have_HS) return OMM_ERR_STATE;
     if (W0 == nullptr && !h->have_W) return OMM_ERR_STATE;
     if (h->phase != PH_IDLE && h->phase != PH_FINISHED) return OMM_ERR_STATE;
@@ -1110,6 +1122,7 @@ int omm_solve_end(omm_handle *h, double *W_out, int32_t W_out_on_device, double 
     if (E_out) *E_out = s.E;
     if (iters_out) *iters_out = s.k;
     h->phase = PH_IDLE;
+    h->solved = true;
     return h->status;
 }
 
@@ -1168,6 +1181,52 @@ int omm_batch_solve(omm_handle **handles, int32_t count, const double *const *W0
 int omm_get_diag(omm_handle *h, omm_diag *d) {
     if (h == nullptr || d == nullptr) return OMM_ERR_ARG;
     *d = h->diag;
+    return OMM_OK;
+}
+
+int omm_get_density(omm_handle *h, int32_t which, double *dst, int32_t on_device) {
+    if (h == nullptr || dst == nullptr || (which != OMM_DENSITY_RHO && which != OMM_DENSITY_RHO_E))
+        return OMM_ERR_ARG;
+    if (h->sparse) return OMM_ERR_UNSUPPORTED;
+    if (!h->solved || h->phase != PH_IDLE) return OMM_ERR_STATE;
+    const int64_t m = h->m, n = h->n, mm = m * m;
+    cudaStream_t st = h->stream;
+    const int s = h->opt.exact_digits;
+    if (h->dK == nullptr) {
+        const int64_t b1 = omm_op_exact_gemm_workspace_bytes(m, n, m, s);   // [H'|S] W
+        const int64_t b2 = omm_op_exact_gemm_workspace_bytes(m, m, n, s);   // 2 T W^T
+        h->dWs_bytes = b1 > b2 ? b1 : b2;
+        TRY(dalloc(&h->dK, (size_t)(3 * n * n)));   // K, then [H'_W ; S_W] (2n x n)
+        TRY(dalloc(&h->dT, (size_t)(m * n)));
+        if (cudaMalloc(&h->dWs, (size_t)h->dWs_bytes) != cudaSuccess) return OMM_ERR_NOMEM;
+    }
+    double *out = dst;
+    if (!on_device) {
+        if (h->dOut == nullptr) TRY(dalloc(&h->dOut, (size_t)mm));
+        out = h->dOut;
+    }
+    // H'_W and S_W afresh from the returned W (Eq. 5 defines rho from W; the
+    // solve's running copies carry its increments' rounding), in the basis the
+    // CG ran in: W~ with H~ and S = I for the Cholesky variant (W~^T W~ = W^T S W)
+    const double *Wr = h->WD;
+    const double *Wout = h->opt.cholesky ? h->Wsave : h->WD;   // the solution in the original basis
+    double *K = h->dK, *HSW = h->dK + n * n;                    // HSW: [H'_W ; S_W], ld 2n
+    const int need_h = which == OMM_DENSITY_RHO_E;
+    for (int part = need_h ? 0 : 1; part < 2; ++part) {
+        const double *A = h->HS + part * mm;                    // part 0: H', part 1: S
+        TRY(omm_op_exact_gemm(0, 0, m, n, m, s, 1.0, A, m, Wr, m, 0.0, nullptr, m, h->dT, m, h->dWs, h->dWs_bytes,
+                              st));
+        TRY(omm_op_exact_gemm(1, 0, n, n, m, s, 1.0, Wr, m, h->dT, m, 0.0, nullptr, n, HSW + part * n, 2 * n,
+                              h->dWs, h->dWs_bytes, st));
+    }
+    TRY(omm::launch_density_K(n, HSW, h->diag.eta, need_h, K, st));
+    // T = W K, then 2 T W^T, both with exact-digit tensor-core products
+    TRY(omm_op_exact_gemm(0, 0, m, n, n, s, 1.0, Wout, m, K, n, 0.0, nullptr, m, h->dT, m, h->dWs, h->dWs_bytes,
+                          st));
+    TRY(omm_op_exact_gemm(0, 1, m, m, n, s, 2.0, h->dT, m, Wout, m, 0.0, nullptr, m, out, m, h->dWs, h->dWs_bytes,
+                          st));
+    if (!on_device) OMM_CUDA_TRY(cudaMemcpyAsync(dst, out, (size_t)mm * sizeof(double), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
     return OMM_OK;
 }
 

@@ -64,6 +64,9 @@ int dgemm_batched(bool tA, bool tB, int64_t M, int64_t N, int64_t K, double alph
                   const GemmBatch &bt, int nbatch, int64_t lda, int64_t ldb, double beta,
                   int64_t ldcin, int64_t ldc, const DevState *state, cudaStream_t st);
 
+// K for the density matrices (omm_get_density): 2I - S_W, or H'_W + eta (2I - S_W)
+int launch_density_K(int64_t n, const double *h0s0, double eta, int mode, double *K, cudaStream_t st);
+
 // -------- reductions and CG updates (cg_kernels.cu)
 constexpr int kRedBlocksMax = 512;
 constexpr int kRedSlots = 16;

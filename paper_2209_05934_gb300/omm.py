@@ -23,6 +23,7 @@ REFINE_EXACT, REFINE_FP64 = 0, 1
 
 ARRAY_W, ARRAY_HW, ARRAY_SW, ARRAY_G, ARRAY_D, ARRAY_HW_N, ARRAY_SW_N = range(7)
 PATTERN_H, PATTERN_W, PATTERN_HW, PATTERN_N = range(4)
+DENSITY_RHO, DENSITY_RHO_E = 0, 1
 
 
 class Options(C.Structure):
@@ -62,6 +63,7 @@ _SIGS = {
                             C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "omm_get_diag": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
     "omm_get_array": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "omm_get_density": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
     "omm_destroy": (None, [C.c_void_p]),
     "omm_status_str": (C.c_char_p, [C.c_int]),
     "omm_op_dgemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_double,
@@ -274,6 +276,16 @@ class Solver:
         rows = self.n if which in (ARRAY_HW_N, ARRAY_SW_N) else self.m
         out = np.zeros((rows, self.n), order="F")
         check(lib().omm_get_array(self._h, which, C.c_void_p(out.ctypes.data), 0), "omm_get_array")
+        return out
+
+    def get_density(self, which: int = DENSITY_RHO, out=None):
+        """rho (Eq. 5) or rho_E of the last solve, m x m; into `out` (column-major
+        host or device array) or a new host array."""
+        if out is None:
+            out = np.zeros((self.m, self.m), order="F")
+        _check_colmajor(out, self.m, self.m, "out")
+        p, d = _ptr(out)
+        check(lib().omm_get_density(self._h, which, p, d), "omm_get_density")
         return out
 
 
