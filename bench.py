@@ -440,7 +440,16 @@ def run_profile_c3(args):
     E, iters, st = s.solve(W0d, tol=0.0, raise_on_error=False)
     torch.cuda.synchronize()
     ms, cnt = s.stage_times()
+    # rho on the pattern of S: first call builds its gather lists, the second is timed
+    t0 = time.perf_counter()
+    s.get_density(omm.DENSITY_RHO)
+    t_first = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s.get_density(omm.DENSITY_RHO)
+    t_rho = time.perf_counter() - t0
     print(json.dumps({"profile": True, "config": "c3", "E": E, "iters": iters, "status": st, "nnzb": s.nnzb,
+                      "rho_ms": {"first_call_with_list_build": 1e3 * t_first,
+                                 "call_including_host_copy": 1e3 * t_rho},
                       "stages_ms": {n: ms[i] for i, n in enumerate(STAGES)},
                       "stage_launches": {n: int(cnt[i]) for i, n in enumerate(STAGES)}}), flush=True)
     s.close()

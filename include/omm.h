@@ -250,9 +250,12 @@ int omm_get_array(omm_handle *h, int32_t which, double *dst, int32_t on_device);
  * S_W and H'_W are formed afresh from it.  dst: m x m column-major, host
  * unless on_device.  Every product runs as an exact-digit tensor-core GEMM
  * (FP64-accurate).  The first call allocates the handle's workspace for it
- * (about 14 (m + n) m bytes with 7 digits, plus m^2 doubles for host output).  Dense handles only (OMM_ERR_UNSUPPORTED for
- * sparse); OMM_ERR_STATE unless omm_solve / omm_solve_end returned since the
- * last omm_set_HS / omm_set_H.
+ * (about 14 (m + n) m bytes with 7 digits, plus m^2 doubles for host output).
+ * Linear-scaling form: rho / rho_E only on the pattern of S (section "Solver
+ * library"), i.e. every block of the P_H given to omm_create, as nnzb(P_H)
+ * blocks of bm x bm, row-major within a block, in P_H's CSR order; FP64 block
+ * kernels over gather lists built at the first request.  OMM_ERR_STATE unless
+ * omm_solve / omm_solve_end returned since the last omm_set_HS / omm_set_H.
  */
 #define OMM_DENSITY_RHO 0
 #define OMM_DENSITY_RHO_E 1

@@ -928,6 +928,7 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
     if (h->phase != PH_IDLE && h->phase != PH_FINISHED) return OMM_ERR_STATE;
     cudaStream_t st = h->stream;
     h->have_HS = false;   // set again only when this setup succeeds
+    h->solved = false;
     OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
     if (h->sparse) {
         omm::DevState init{};
@@ -1187,8 +1188,27 @@ int omm_get_diag(omm_handle *h, omm_diag *d) {
 int omm_get_density(omm_handle *h, int32_t which, double *dst, int32_t on_device) {
     if (h == nullptr || dst == nullptr || (which != OMM_DENSITY_RHO && which != OMM_DENSITY_RHO_E))
         return OMM_ERR_ARG;
-    if (h->sparse) return OMM_ERR_UNSUPPORTED;
     if (!h->solved || h->phase != PH_IDLE) return OMM_ERR_STATE;
+    if (h->sparse) {
+        // rho / rho_E on the pattern of S (section "Solver library"): P_H's blocks
+        omm::sp::Dev &d = h->sd;
+        if (d.Trp == nullptr) {
+            omm::sp::DensHost dh;
+            TRY(omm::sp::build_density(h->sh, dh));
+            TRY(omm::sp::upload_density(dh, d));
+        }
+        const int64_t len = d.nnzH * d.bm * d.bm;
+        double *out = dst;
+        if (!on_device) {
+            if (h->dOut == nullptr) TRY(dalloc(&h->dOut, (size_t)len));
+            out = h->dOut;
+        }
+        TRY(omm::sp::density(d, which == OMM_DENSITY_RHO_E ? 1 : 0, h->diag.eta, out, h->stream));
+        if (!on_device)
+            OMM_CUDA_TRY(cudaMemcpyAsync(dst, out, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        OMM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        return OMM_OK;
+    }
     const int64_t m = h->m, n = h->n, mm = m * m;
     cudaStream_t st = h->stream;
     const int s = h->opt.exact_digits;

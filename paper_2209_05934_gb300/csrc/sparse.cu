@@ -265,6 +265,71 @@ int build(const Pattern &P, Host &out) {
     return OMM_OK;
 }
 
+int build_density(const Host &hs, DensHost &out) {
+    const Pattern &Q = hs.P;
+    const int64_t nnzH = Q.Hrp[Q.nbr], nnzHW = hs.HWrp[Q.nbr];
+    // T lists: (I, b) in P_HW <- W (I, a), N (a, b)
+    {
+        std::vector<int32_t> pos(Q.nbc, -1);
+        out.Trp.assign(nnzHW + 1, 0);
+        for (int pass = 0; pass < 2; ++pass) {
+            std::vector<int64_t> fill;
+            if (pass == 1) {
+                for (int64_t o = 0; o < nnzHW; ++o) out.Trp[o + 1] += out.Trp[o];
+                out.Tw.resize(out.Trp[nnzHW]);
+                out.Tq.resize(out.Trp[nnzHW]);
+                fill.assign(out.Trp.begin(), out.Trp.end() - 1);
+            }
+            for (int64_t I = 0; I < Q.nbr; ++I) {
+                for (int64_t o = hs.HWrp[I]; o < hs.HWrp[I + 1]; ++o) pos[hs.HWcol[o]] = (int32_t)o;
+                for (int64_t w = Q.Wrp[I]; w < Q.Wrp[I + 1]; ++w) {
+                    const int32_t a = Q.Wcol[w];
+                    for (int64_t q = hs.Nrp[a]; q < hs.Nrp[a + 1]; ++q) {
+                        const int32_t o = pos[hs.Ncol[q]];
+                        if (o < 0) continue;
+                        if (pass == 0) {
+                            out.Trp[o + 1] += 1;
+                        } else {
+                            out.Tw[fill[o]] = (int32_t)w;
+                            out.Tq[fill[o]] = (int32_t)q;
+                            ++fill[o];
+                        }
+                    }
+                }
+                for (int64_t o = hs.HWrp[I]; o < hs.HWrp[I + 1]; ++o) pos[hs.HWcol[o]] = -1;
+            }
+        }
+    }
+    // rho lists: (I, J) in P_H <- T (I, b), W (J, b) for b in row J of P_W
+    // ((I, b) is in P_HW since J is in row I of P_H)
+    {
+        std::vector<int32_t> pos(Q.nbc, -1);
+        out.Rrp.assign(nnzH + 1, 0);
+        for (int64_t I = 0; I < Q.nbr; ++I)
+            for (int64_t h = Q.Hrp[I]; h < Q.Hrp[I + 1]; ++h) {
+                const int32_t J = Q.Hcol[h];
+                out.Rrp[h + 1] = out.Rrp[h] + (Q.Wrp[J + 1] - Q.Wrp[J]);
+            }
+        out.Rt.resize(out.Rrp[nnzH]);
+        out.Rw.resize(out.Rrp[nnzH]);
+        for (int64_t I = 0; I < Q.nbr; ++I) {
+            for (int64_t o = hs.HWrp[I]; o < hs.HWrp[I + 1]; ++o) pos[hs.HWcol[o]] = (int32_t)o;
+            for (int64_t h = Q.Hrp[I]; h < Q.Hrp[I + 1]; ++h) {
+                const int32_t J = Q.Hcol[h];
+                int64_t f = out.Rrp[h];
+                for (int64_t w = Q.Wrp[J]; w < Q.Wrp[J + 1]; ++w, ++f) {
+                    const int32_t o = pos[Q.Wcol[w]];
+                    if (o < 0) return OMM_ERR_PATTERN;   // cannot happen for P_HW = P_H P_W
+                    out.Rt[f] = o;
+                    out.Rw[f] = (int32_t)w;
+                }
+            }
+            for (int64_t o = hs.HWrp[I]; o < hs.HWrp[I + 1]; ++o) pos[hs.HWcol[o]] = -1;
+        }
+    }
+    return OMM_OK;
+}
+
 // ======================================================================== device kernels
 namespace {
 
@@ -701,6 +766,69 @@ __global__ void direction_kernel(int64_t len, const double *__restrict__ G, doub
     }
 }
 
+// ---- density matrices
+// K = 2I - S_W (mode 0) or H'_W + eta (2I - S_W) (mode 1) on P_N (bn x bn blocks)
+__global__ void density_K_kernel(int64_t nnzN, int bn, const unsigned char *__restrict__ Ndiag,
+                                 const double *__restrict__ HW_N, const double *__restrict__ SW_N, int mode,
+                                 double eta, double *K) {
+    const int64_t bb = (int64_t)bn * bn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnzN * bb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = i / bb;
+        const int e = (int)(i % bb);
+        const double t = ((Ndiag[q] && e / bn == e % bn) ? 2.0 : 0.0) - SW_N[i];
+        K[i] = mode == 0 ? t : fma(eta, t, HW_N[i]);
+    }
+}
+
+// T_(I,b) = sum W_(I,a) K_(a,b): half-warp per P_HW block, one lane per element
+template <int BM, int BN>
+__global__ void __launch_bounds__(NT) density_T_kernel(int64_t nnzHW, const int64_t *__restrict__ Trp,
+                                                        const int32_t *__restrict__ Tw, const int32_t *__restrict__ Tq,
+                                                        const double *__restrict__ W, const double *__restrict__ K,
+                                                        double *T) {
+    const int e = threadIdx.x & 15;
+    if (e >= BM * BN) return;
+    const int r = e / BN, c = e % BN;
+    const int64_t ngroups = ((int64_t)gridDim.x * NT) >> 4;
+    for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 4; o < nnzHW; o += ngroups) {
+        double acc = 0.0;
+        for (int64_t t = Trp[o]; t < Trp[o + 1]; ++t) {
+            const double *w = W + (int64_t)Tw[t] * BM * BN + r * BN;
+            const double *k = K + (int64_t)Tq[t] * BN * BN + c;
+#pragma unroll
+            for (int j = 0; j < BN; ++j) acc = fma(w[j], k[j * BN], acc);
+        }
+        T[o * BM * BN + e] = acc;
+    }
+}
+
+// rho_(I,J) = 2 sum T_(I,b) W_(J,b)^T: two warps' worth of lanes per P_H block
+// (BM*BM = 64 outputs), each lane two outputs
+template <int BM, int BN>
+__global__ void __launch_bounds__(NT) density_rho_kernel(int64_t nnzH, const int64_t *__restrict__ Rrp,
+                                                          const int32_t *__restrict__ Rt,
+                                                          const int32_t *__restrict__ Rw,
+                                                          const double *__restrict__ T,
+                                                          const double *__restrict__ W, double *rho) {
+    const int lane = threadIdx.x & 31;
+    constexpr int NE = BM * BM;
+    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+    for (int64_t h = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; h < nnzH; h += nwarps) {
+        for (int e = lane; e < NE; e += 32) {
+            const int r = e / BM, c = e % BM;
+            double acc = 0.0;
+            for (int64_t t = Rrp[h]; t < Rrp[h + 1]; ++t) {
+                const double *tt = T + (int64_t)Rt[t] * BM * BN + r * BN;
+                const double *ww = W + (int64_t)Rw[t] * BM * BN + c * BN;
+#pragma unroll
+                for (int j = 0; j < BN; ++j) acc = fma(tt[j], ww[j], acc);
+            }
+            rho[h * NE + e] = 2.0 * acc;
+        }
+    }
+}
+
 int blocks_for(int64_t work, int per) {
     int64_t nb = ceil_div(work, per);
     if (nb > 152 * 16) nb = 152 * 16;
@@ -761,7 +889,8 @@ int upload(const Host &hs, Dev &d) {
 }
 
 void release(Dev &d) {
-    void *ptrs[] = {d.Hrp, d.Hcol, d.Prp, d.Ph, d.Pw, d.Crp, d.Ca, d.Cb, d.Grp, d.Gb, d.Gq, d.WtoHW, d.Ntr,
+    void *ptrs[] = {d.Trp, d.Rrp, d.Tw, d.Tq, d.Rt, d.Rw, d.K, d.T,
+                    d.Hrp, d.Hcol, d.Prp, d.Ph, d.Pw, d.Crp, d.Ca, d.Cb, d.Grp, d.Gb, d.Gq, d.WtoHW, d.Ntr,
                     d.Ndiag, d.HS, d.Hin, d.W, d.D, d.G, d.Gp, d.HW, d.SW, d.HD, d.SD, d.h0, d.s0, d.X,
                     d.Y, d.h2, d.s2, d.keep};
     for (void *p : ptrs) cudaFree(p);
@@ -804,6 +933,43 @@ int contract(Dev &d, const double *Wl, const double *Dl, const double *HDr, cons
              double *Yo, double *h2o, double *s2o, const DevState *state, cudaStream_t st) {
     DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
                                      d.nnzN, d.Crp, d.Ca, d.Cb, Wl, Dl, HDr, SDr, Xo, Yo, h2o, s2o, state)));
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int upload_density(const DensHost &dh, Dev &d) {
+    auto up64 = [](int64_t **dst, const std::vector<int64_t> &v) -> int {
+        if (cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(int64_t)) != cudaSuccess) return OMM_ERR_NOMEM;
+        return cudaMemcpy(*dst, v.data(), v.size() * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess
+                   ? OMM_OK : OMM_ERR_CUDA;
+    };
+    auto up32 = [](int32_t **dst, const std::vector<int32_t> &v) -> int {
+        if (cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(int32_t)) != cudaSuccess) return OMM_ERR_NOMEM;
+        return cudaMemcpy(*dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice) == cudaSuccess
+                   ? OMM_OK : OMM_ERR_CUDA;
+    };
+    int rc;
+    if ((rc = up64(&d.Trp, dh.Trp)) || (rc = up32(&d.Tw, dh.Tw)) || (rc = up32(&d.Tq, dh.Tq)) ||
+        (rc = up64(&d.Rrp, dh.Rrp)) || (rc = up32(&d.Rt, dh.Rt)) || (rc = up32(&d.Rw, dh.Rw)))
+        return rc;
+    if (cudaMalloc(&d.K, (size_t)(d.nnzN * d.bn * d.bn) * sizeof(double)) != cudaSuccess) return OMM_ERR_NOMEM;
+    if (cudaMalloc(&d.T, (size_t)(d.nnzHW * d.bm * d.bn) * sizeof(double)) != cudaSuccess) return OMM_ERR_NOMEM;
+    return OMM_OK;
+}
+
+int density(Dev &d, int mode, double eta, double *out, cudaStream_t st) {
+    // H'W, SW on P_HW and H'_W = W^T H'W, S_W = W^T SW on P_N, afresh from W
+    int rc;
+    if ((rc = products(d, d.W, d.HD, d.SD, nullptr, st))) return rc;
+    if ((rc = contract(d, d.W, d.W, d.HD, d.SD, d.X, d.Y, d.h2, d.s2, nullptr, st))) return rc;
+    const int64_t bb = (int64_t)d.bn * d.bn;
+    density_K_kernel<<<blocks_for(d.nnzN * bb, 256), 256, 0, st>>>(d.nnzN, d.bn, d.Ndiag, d.X, d.Y, mode, eta, d.K);
+    LAUNCHED();
+    DISPATCH_BLOCKS(d.bm, d.bn, (density_T_kernel<BM, BN><<<blocks_for(d.nnzHW * 16, NT), NT, 0, st>>>(
+                                     d.nnzHW, d.Trp, d.Tw, d.Tq, d.W, d.K, d.T)));
+    LAUNCHED();
+    DISPATCH_BLOCKS(d.bm, d.bn, (density_rho_kernel<BM, BN><<<blocks_for(d.nnzH * 32, NT), NT, 0, st>>>(
+                                     d.nnzH, d.Rrp, d.Rt, d.Rw, d.T, d.W, out)));
     LAUNCHED();
     return OMM_OK;
 }

@@ -37,6 +37,14 @@ struct Host {
     std::vector<int64_t> WcolRp, WcolIdx;   // W blocks by column
 };
 
+// Gather lists of the density matrices (built at their first request):
+//   T = W (2I - S_W) on P_HW: block (I, b) <- W block (I, a) x N block (a, b);
+//   rho on P_H:              block (I, J) <- T block (I, b) x W block (J, b)^T.
+struct DensHost {
+    std::vector<int64_t> Trp, Rrp;
+    std::vector<int32_t> Tw, Tq, Rt, Rw;
+};
+
 // Device arrays of one sparse handle.
 struct Dev {
     int32_t bm = 0, bn = 0;
@@ -49,6 +57,10 @@ struct Dev {
     double *W = nullptr, *D = nullptr, *G = nullptr, *Gp = nullptr;
     double *HW = nullptr, *SW = nullptr, *HD = nullptr, *SD = nullptr;
     double *h0 = nullptr, *s0 = nullptr, *X = nullptr, *Y = nullptr, *h2 = nullptr, *s2 = nullptr;
+    // density matrices (allocated with their lists)
+    int64_t *Trp = nullptr, *Rrp = nullptr;
+    int32_t *Tw = nullptr, *Tq = nullptr, *Rt = nullptr, *Rw = nullptr;
+    double *K = nullptr, *T = nullptr;
 };
 
 // Validate the caller's patterns and build everything host-side (OMM_ERR_PATTERN on malformed input).
@@ -59,6 +71,12 @@ void release(Dev &d);
 // Per-(H,S) setup: copy, block filtering, Gershgorin eta (optional), shift and pack.
 int set_HS(Dev &d, const double *H, const double *S, bool on_device, double eps, bool eta_auto, double *scratch,
            unsigned int *counter, DevState *state, cudaStream_t st);
+
+int build_density(const Host &hs, DensHost &out);
+int upload_density(const DensHost &dh, Dev &d);
+// rho (mode 0) or rho_E (mode 1) on P_H into out (nnzH blocks of bm x bm, row-major,
+// P_H's CSR order), from W with S_W and H'_W formed afresh
+int density(Dev &d, int mode, double eta, double *out, cudaStream_t st);
 
 // One step's pieces
 int products(Dev &d, const double *Din, double *HDo, double *SDo, const DevState *state, cudaStream_t st);

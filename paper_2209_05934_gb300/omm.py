@@ -344,6 +344,12 @@ class SparseSolver:
             raise OmmError(st, "omm_solve")
         return E.value, it.value, st
 
+    def get_density(self, which: int = DENSITY_RHO):
+        """rho (Eq. 5) or rho_E of the last solve on the pattern of S: (nnzb_H, bm, bm)."""
+        out = np.zeros((len(self._keep[1]), self.bm, self.bm))
+        check(lib().omm_get_density(self._h, which, C.c_void_p(out.ctypes.data), 0), "omm_get_density")
+        return out
+
     def get_array(self, which):
         sizes = {ARRAY_W: ("W", self.bm * self.bn), ARRAY_HW: ("HW", self.bm * self.bn),
                  ARRAY_SW: ("HW", self.bm * self.bn), ARRAY_G: ("W", self.bm * self.bn),

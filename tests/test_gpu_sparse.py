@@ -193,3 +193,30 @@ def test_full_size_c3_first_step(omm):
         blk = Wref[8 * I:8 * I + 8, 2 * J:2 * J + 2].toarray()
         np.testing.assert_allclose(Wout[b], blk, rtol=1e-9, atol=1e-12)
     s.close()
+
+
+def test_sparse_density_on_S_pattern(omm):
+    """rho (Eq. 5) and rho_E of the linear-scaling solve, only on the pattern of
+    S (section "Solver library"), against the oracle's definitions on the
+    returned W; every block of P_H, the block filter off so that both sides see
+    the same S."""
+    import synth
+    sysm = synth.make_system(3, 3, 2, seed=2)
+    radius = 3.6
+    s, (rp, col, Hv, Sv), _ = _setup(omm, sysm, radius, filter_eps=0.0)
+    s.set_HS(Hv, Sv)
+    eta = s.diag().eta
+    s.solve(sysm.W0_bsr_values(radius), tol=1e-11)
+    W = _w_blocks_to_dense(sysm, radius, s.get_array(omm.ARRAY_W).reshape(-1, 8, 2))
+    H, S = sysm.dense_H(), sysm.dense_S()
+    rows = np.repeat(np.arange(sysm.natoms), np.diff(rp))
+    for which, ref in ((omm.DENSITY_RHO, O.density_matrix(W, S)),
+                       (omm.DENSITY_RHO_E, O.energy_density_matrix(W, O.shift(H, S, eta), S, eta))):
+        got = s.get_density(which)
+        assert got.shape == (len(col), 8, 8)
+        want = np.stack([ref[8 * I:8 * I + 8, 8 * J:8 * J + 8] for I, J in zip(rows, col)])
+        np.testing.assert_allclose(got, want, atol=1e-12 * np.abs(want).max())
+    # the charge sums over S's pattern only: Tr(rho S) = sum over blocks of <rho_IJ, S_IJ>
+    rho = s.get_density(omm.DENSITY_RHO)
+    assert float(np.sum(rho * Sv)) == pytest.approx(O.charge(W, S), rel=1e-10)
+    s.close()
