@@ -15,7 +15,8 @@ on scipy.sparse matrices: the paper states that the sparse and dense forms
 run the same equations, with sparse matrices instead of dense ones and the
 gradient restricted to the sparsity pattern of W (section "Solver library").
 Library primitives used as single steps: matrix products (numpy / scipy.sparse),
-polynomial roots (numpy.roots), Cholesky and triangular solves (scipy.linalg).
+polynomial roots (numpy.roots), Cholesky and triangular solves (scipy.linalg),
+and one positive-definite linear solve for the kinetic-energy preconditioner.
 """
 from __future__ import annotations
 
@@ -236,8 +237,33 @@ class Result:
     orth: float = float("nan")                     # ||S_W - I||_F at the final W
 
 
+def cg_direction(G, Z, G_prev, Z_prev, D):
+    """Step 4 of omm_cg: the new search direction from the gradient G and the
+    preconditioned gradient Z (Z = G without a preconditioner); D = None and
+    G_prev = None at the first step."""
+    if D is None:
+        return -Z
+    beta = max(0.0, frob(Z, G - G_prev) / frob(Z_prev, G_prev))
+    D = -Z + beta * D
+    if frob(G, D) >= 0.0:
+        D = -Z
+    return D
+
+
+RY_EV = 13.605693122994      # one Rydberg in eV (CODATA 2018)
+TAU_T_DEFAULT = 10.0 * RY_EV  # default kinetic-energy scale, 10 Ry (Table 1, OMM.TPreconScale)
+
+
+def kinetic_preconditioner(S, T, tau: float = TAU_T_DEFAULT):
+    """P = (S + T / tau)^-1 (Eq. 6), dense; T is the kinetic-energy matrix and
+    tau the kinetic-energy scale in the energy unit of H.  One library solve
+    against the identity."""
+    M = _dense(S) + _dense(T) / tau
+    return sla.solve(M, np.eye(M.shape[0]), assume_a="pos")
+
+
 def omm_cg(H, S, W0, tol: float = 1e-10, eta: float | None = None, max_iter: int = 10000,
-           orth_tol: float | None = None, mask=None, n_occ: int | None = None) -> Result:
+           orth_tol: float | None = None, mask=None, n_occ: int | None = None, P=None) -> Result:
     """Conjugate-gradient minimisation of the (shifted) Ordejon-Mauri functional.
 
     Steps, in the paper's order (sections "Overview of OMM approaches" and
@@ -255,6 +281,11 @@ def omm_cg(H, S, W0, tol: float = 1e-10, eta: float | None = None, max_iter: int
       4. D = -G at k = 0; otherwise Polak-Ribiere+ beta =
          max(0, <G, G - G_prev> / <G_prev, G_prev>), D = -G + beta D, and D = -G
          whenever <G, D> >= 0.  (The paper does not name its CG variant.)
+         With a preconditioner P (dense only; Eq. 6, section "Overview of OMM
+         approaches") the gradient is multiplied by P, Z = P G, and every G of
+         step 4 that forms the direction or beta's numerator and denominator
+         pairs with Z: beta = max(0, <Z, G - G_prev> / <Z_prev, G_prev>),
+         D = -Z + beta D, and D = -Z whenever <G, D> >= 0.
       5. exact line search: coefficients of E~(W + x D), the quartic's minimum x.
       6. W <- W + x D.
     """
@@ -269,8 +300,11 @@ def omm_cg(H, S, W0, tol: float = 1e-10, eta: float | None = None, max_iter: int
     history = []
     E_prev = None
     G_prev = None
+    Z_prev = None
     D = None
     k = 0
+    if P is not None and (sp.issparse(W0) or mask is not None):
+        raise ValueError("the kinetic-energy preconditioner is defined for the dense form only")
     status = OK
     while True:
         HW = Hs @ W
@@ -288,13 +322,8 @@ def omm_cg(H, S, W0, tol: float = 1e-10, eta: float | None = None, max_iter: int
             status = ERR_MAXITER
             break
         G = apply_mask(2.0 * (2.0 * HW - SW @ H_W - HW @ S_W), mask)
-        if D is None:
-            D = -G
-        else:
-            beta = max(0.0, frob(G, G - G_prev) / frob(G_prev, G_prev))
-            D = -G + beta * D
-            if frob(G, D) >= 0.0:
-                D = -G
+        Z = G if P is None else P @ G
+        D = cg_direction(G, Z, G_prev, Z_prev, D)
         c = quartic_coeffs(W, D, Hs, S)
         x, st = line_min(c)
         if st != OK:
@@ -303,6 +332,7 @@ def omm_cg(H, S, W0, tol: float = 1e-10, eta: float | None = None, max_iter: int
         W = W + x * D
         E_prev = E
         G_prev = G
+        Z_prev = Z
         k += 1
     E_unshifted = functional(W, H, S)
     return Result(W=W, E=E, E_unshifted=E_unshifted, iters=k, status=status, eta=eta,

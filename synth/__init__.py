@@ -25,6 +25,17 @@ an insulating gap, n/m = 1/4 occupied orbitals, localised W patterns):
   dense W0 ~ N(0, 1/sqrt(m)); localised W0 keeps only entries whose basis
   atom lies within R_C of the orbital's host atom (orbital j lives on atom
   j // 2) and rescales column j by sqrt(m / nnz_j), i.e. sigma_j = 1/sqrt(nnz_j).
+* Kinetic-energy matrix T (for the preconditioner of Eq. 6), on the pairs of
+  H and S: onsite diagonal (2, 2, 0.5, 20, 50, 100, 200, 400) eV + N(0, 0.05)
+  per orbital -- small on the two occupied-like orbitals and on one low
+  unoccupied orbital (the gap stays), a wide range on the others, as for the
+  polarisation orbitals of a DZP basis -- and off-site
+  T_IJ = 0.05 exp(-r/1.2) K_IJ with K_IJ ~ U(-1,1)^{8x8}/8, T_JI = T_IJ^T.
+  Off-site row sums of |T| stay below 0.05 eV < 0.5 eV - 4 sigma, so T is SPD.
+  Drawn from a third PCG64 stream seeded with seed + 2*10**6: onsite noise
+  (N x 8), then all K blocks (npairs x 8 x 8) in pair order; H, S and W0 are
+  unchanged by it.  The kinetic workload's Hamiltonian is H + T (spectrum
+  widened to ~400 eV above a gap of a few eV).
 * Batched systems: N atoms = round(exp(U(ln 32, ln 384))) drawn from a PCG64
   stream seeded with the batch seed; the first N sites of the ceil(N^(1/3))^3
   grid in index order.
@@ -45,6 +56,9 @@ W_RADIUS = 6.0
 ONSITE = np.array([-5.0, -5.0, 5.0, 5.0, 5.0, 5.0, 5.0, 5.0])
 ONSITE_SIGMA = 0.3
 W0_SEED_OFFSET = 10 ** 6
+T_SEED_OFFSET = 2 * 10 ** 6
+KINETIC_ONSITE = np.array([2.0, 2.0, 0.5, 20.0, 50.0, 100.0, 200.0, 400.0])
+KINETIC_SIGMA = 0.05
 
 
 @dataclass
@@ -79,6 +93,22 @@ class System:
     def dense_S(self) -> np.ndarray:
         eye = np.broadcast_to(np.eye(ORB_PER_ATOM), (self.natoms, ORB_PER_ATOM, ORB_PER_ATOM))
         return _assemble_dense(self.natoms, eye, self.pairs, self.S_pair)
+
+    def dense_T(self) -> np.ndarray:
+        """Kinetic-energy matrix on the pattern of H and S (eV), symmetric positive definite."""
+        rng = np.random.Generator(np.random.PCG64(self.seed + T_SEED_OFFSET))
+        N = self.natoms
+        diag = KINETIC_ONSITE[None, :] + rng.normal(0.0, KINETIC_SIGMA, size=(N, ORB_PER_ATOM))
+        onsite = np.zeros((N, ORB_PER_ATOM, ORB_PER_ATOM))
+        idx = np.arange(ORB_PER_ATOM)
+        onsite[:, idx, idx] = diag
+        K = rng.uniform(-1.0, 1.0, size=(self.pairs.shape[0], ORB_PER_ATOM, ORB_PER_ATOM)) / ORB_PER_ATOM
+        T_pair = (0.05 * np.exp(-self.pair_r / 1.2))[:, None, None] * K
+        return _assemble_dense(N, onsite, self.pairs, T_pair)
+
+    def dense_H_kinetic(self) -> np.ndarray:
+        """Hamiltonian of the kinetic workload: H + T (a wide, kinetic-dominated spectrum)."""
+        return self.dense_H() + self.dense_T()
 
     # ---------------------------------------------------------------- block CSR
     def bsr(self):

@@ -94,3 +94,45 @@ def test_wrong_root_choice_is_caught():
     best = grid[np.argmin(O.quartic(c, grid))]
     assert abs(bad_x - best) > 1e-2
     assert abs(O.line_min(c)[0] - best) < 1e-5
+
+
+# --------------------------------------------------------------- preconditioned direction
+def _precon_pin_ok(system, monkeypatch=None, bad=None):
+    """The transformed-variables pin of the preconditioned CG, at 6 steps."""
+    H, S, T = system.dense_H(), system.dense_S(), system.dense_T()
+    W0 = system.W0_dense()
+    eta = O.gershgorin_eta(H, S)
+    tau = 2.0
+    R = sla.cholesky(S + T / tau, lower=True)
+    sand = lambda A: sla.solve_triangular(R, sla.solve_triangular(R, A, lower=True).T, lower=True).T
+    Hv, Sv = sand(H), sand(S)
+    Hv, Sv = 0.5 * (Hv + Hv.T), 0.5 * (Sv + Sv.T)
+    b = O.omm_cg(Hv, Sv, R.T @ W0, tol=0.0, eta=eta, max_iter=6)
+    if bad is not None:
+        monkeypatch.setattr(O, "cg_direction", bad)
+    a = O.omm_cg(H, S, W0, tol=0.0, eta=eta, max_iter=6, P=O.kinetic_preconditioner(S, T, tau))
+    return np.allclose(a.W, sla.solve_triangular(R.T, b.W, lower=False), rtol=1e-8, atol=1e-10)
+
+
+def test_precon_pin_accepts_the_oracle(small_system):
+    assert _precon_pin_ok(small_system)
+
+
+def test_precon_beta_with_unpreconditioned_denominator_is_caught(small_system, monkeypatch):
+    def bad(G, Z, G_prev, Z_prev, D):
+        if D is None:
+            return -Z
+        beta = max(0.0, O.frob(Z, G - G_prev) / O.frob(G_prev, G_prev))   # <G_prev, G_prev>
+        D = -Z + beta * D
+        return -Z if O.frob(G, D) >= 0.0 else D
+    assert not _precon_pin_ok(small_system, monkeypatch, bad)
+
+
+def test_precon_unpreconditioned_direction_is_caught(small_system, monkeypatch):
+    def bad(G, Z, G_prev, Z_prev, D):
+        if D is None:
+            return -Z
+        beta = max(0.0, O.frob(Z, G - G_prev) / O.frob(Z_prev, G_prev))
+        D = -G + beta * D                                                   # lost P
+        return -Z if O.frob(G, D) >= 0.0 else D
+    assert not _precon_pin_ok(small_system, monkeypatch, bad)

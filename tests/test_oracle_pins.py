@@ -234,6 +234,67 @@ def test_cholesky_variant_same_minimum(small_system):
     np.testing.assert_allclose(O.density_matrix(b.W, S), O.density_matrix(a.W, S), atol=1e-6)
 
 
+# --------------------------------------------------------------- kinetic-energy preconditioning
+def _transformed_problem(H, S, T, tau, W0):
+    """M = S + T / tau = R R^T; in the variables V = R^T W the functional is the
+    same with H_V = R^-1 H R^-T and S_V = R^-1 S R^-T, and its gradient is
+    R^-1 G.  Plain CG there, mapped back with W = R^-T V, is CG preconditioned
+    with P = M^-1 = R^-T R^-1 (Eq. 6)."""
+    R = sla.cholesky(S + T / tau, lower=True)
+
+    def sandwich(A):
+        X = sla.solve_triangular(R, sla.solve_triangular(R, A, lower=True).T, lower=True).T
+        return 0.5 * (X + X.T)
+    return R, sandwich(H), sandwich(S), R.T @ W0
+
+
+@pytest.mark.parametrize("tau", [2.0, O.TAU_T_DEFAULT])
+def test_preconditioned_cg_is_cg_in_transformed_variables(small_system, tau):
+    """Every iterate of the preconditioned CG equals R^-T times the iterate of
+    plain CG run on the transformed problem, for the same eta: this fixes the
+    product Z = P G, both dot products of beta and the restart test."""
+    H, S, T = small_system.dense_H(), small_system.dense_S(), small_system.dense_T()
+    W0 = small_system.W0_dense()
+    eta = O.gershgorin_eta(H, S)
+    R, Hv, Sv, V0 = _transformed_problem(H, S, T, tau, W0)
+    P = O.kinetic_preconditioner(S, T, tau)
+    for k in (1, 3, 8, 20):
+        a = O.omm_cg(H, S, W0, tol=0.0, eta=eta, max_iter=k, P=P)
+        b = O.omm_cg(Hv, Sv, V0, tol=0.0, eta=eta, max_iter=k)
+        assert a.iters == b.iters == k
+        np.testing.assert_allclose(a.history, b.history, rtol=1e-12)
+        np.testing.assert_allclose(a.W, sla.solve_triangular(R.T, b.W, lower=False), rtol=1e-8, atol=1e-10)
+
+
+def test_preconditioner_without_kinetic_term_is_the_cholesky_variant(small_system):
+    """T = 0 gives P = S^-1, i.e. CG on the Cholesky-reduced problem (the
+    oracle's reduction runs on W~ = L^T W with overlap I)."""
+    H, S = small_system.dense_H(), small_system.dense_S()
+    W0 = small_system.W0_dense()
+    eta = O.gershgorin_eta(H, S)
+    P = O.kinetic_preconditioner(S, np.zeros_like(S), 1.0)
+    np.testing.assert_allclose(P @ S, np.eye(S.shape[0]), atol=1e-12)
+    for k in (2, 6):
+        a = O.omm_cg(H, S, W0, tol=0.0, eta=eta, max_iter=k, P=P)
+        b = O.omm_cg_cholesky(H, S, W0, tol=0.0, eta=eta, max_iter=k)
+        np.testing.assert_allclose(a.history, b.history, rtol=1e-12)
+        np.testing.assert_allclose(a.W, b.W, rtol=1e-8, atol=1e-10)
+
+
+def test_preconditioned_cg_reaches_jacobi_ground_state(tiny_system):
+    """Preconditioning changes the path, not the minimum: 2 x the sum of the n
+    lowest generalised eigenvalues, S_W = I, charge 2n."""
+    H, S, T, n = tiny_system.dense_H_kinetic(), tiny_system.dense_S(), tiny_system.dense_T(), tiny_system.n
+    P = O.kinetic_preconditioner(S, T)
+    res = O.omm_cg(H, S, tiny_system.W0_dense(), tol=1e-15, max_iter=5000, P=P)
+    assert res.status in (O.OK, O.ERR_MAXITER)
+    lam = jacobi.generalized_eigenvalues(H.tolist(), S.tolist())
+    assert res.E == pytest.approx(2.0 * sum(lam[:n]), rel=1e-11)
+    assert np.linalg.norm(res.W.T @ S @ res.W - np.eye(n)) < 1e-6
+    hist = np.array(res.history)
+    assert np.all(np.diff(hist) <= 1e-12 * np.abs(hist[1:]))
+
+
 # --------------------------------------------------------------- linear-scaling form
 def _sparse_inputs(sysm, radius):
     rp, col, Hv, Sv = sysm.bsr()
