@@ -301,6 +301,33 @@ def run_omm(args):
                        "chosen_form_speedup": ms64 / (t_max / args.steps)}
         s64.close()
 
+    # ---- kinetic-energy preconditioning (Eq. 6) on the kinetic workload H + T:
+    # the same S and W0, a spectrum widened by the kinetic term; one warm solve
+    # per form (P is formed, chunks captured), then one timed solve each
+    kinetic = None
+    if prec == "mixed" and not args.cholesky and not args.no_kinetic:
+        Hk, Tk = dev(sysm.dense_H_kinetic()), dev(sysm.dense_T())
+        kinetic = {"workload": workload_name(sysm) + ", H + T (kinetic onsite 0.5-400 eV)",
+                   "tau_T_eV": omm.default_options().tau_T}
+        for name, extra in (("plain", {}), ("precon", {"precon": -1})):
+            sk = omm.Solver(m, n, 8, **opts, **extra)
+            sk.set_HS(Hk, Sd)
+            if extra:
+                sk.set_T(Tk)
+            sk.solve(W0d, tol=tol, raise_on_error=False)
+            torch.cuda.synchronize()
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            Ek, itk, stk = sk.solve(W0d, tol=tol, raise_on_error=False)
+            k1.record(stream)
+            torch.cuda.synchronize()
+            dk = sk.diag()
+            kinetic[name] = {"ms_per_solve": k0.elapsed_time(k1), "iters": int(itk), "iters_mixed": dk.iters_mixed,
+                             "iters_refine": dk.iters_refine, "E": Ek, "status": int(stk), "orth": dk.orth}
+            sk.close()
+        kinetic["E_rel_diff"] = abs(kinetic["precon"]["E"] - kinetic["plain"]["E"]) / abs(kinetic["plain"]["E"])
+        del Hk, Tk
+
     # ---- e2e: the same solves through the C ABI from pinned host buffers
     Hh = torch.from_numpy(np.asfortranarray(H)).pin_memory()
     Sh = torch.from_numpy(np.asfortranarray(S)).pin_memory()
@@ -369,6 +396,7 @@ def run_omm(args):
         "cpu_baseline": cpu,
         "fp64_gpu_beside": fp64_beside,
         "density_matrix": density,
+        "kinetic_preconditioning": kinetic,
         "e2e": {"value": ws * e2e_steps / (t_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(2 * m * m * 8 + m * n * 8),
                 "d2h_bytes_per_step": int(m * n * 8 + 8)},
@@ -380,7 +408,7 @@ def run_omm(args):
 
 
 STAGES = ["products", "contract", "linesearch", "update", "gradient", "direction", "setup", "start",
-          "pack", "anchor"]
+          "pack", "anchor", "precon"]
 
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the current
@@ -652,6 +680,8 @@ def main():
                     help="mixed form: BF16 digits per operand in the first phase (3 pairs or 6)")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="c4/c5: replay chunks of CG steps as captured CUDA graphs")
+    ap.add_argument("--no-kinetic", action="store_true",
+                    help="skip the kinetic-energy preconditioning comparison on H + T")
     ap.add_argument("--cholesky", action="store_true",
                     help="c2: Cholesky-reduced variant (S = L L^T factored inside each step's setup)")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],

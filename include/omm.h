@@ -122,6 +122,15 @@ typedef struct {
                               along unoccupied directions beyond a barrier near unit norm) and
                               leave orth_tol at 0: S_W converges to diag(I, 0).  0 (default):
                               n_occupied = n */
+    int32_t precon;        /* kinetic-energy preconditioning (Eq. 6; dense handles only, not
+                              with the Cholesky variant): the CG gradient G is multiplied by
+                              P = (S + T / tau_T)^-1 before it forms the search direction and
+                              the Polak-Ribiere ratio.  0 (default): off; k > 0: applied in the
+                              first k solves after each omm_set_T (the OMM.Precon count of
+                              Table 1, counted in solves); < 0: applied in every solve.  T is
+                              given with omm_set_T */
+    double tau_T;          /* kinetic-energy scale of P, in the energy unit of H; default
+                              10 Ry = 136.0569 eV (Table 1, OMM.TPreconScale) */
 } omm_options;
 
 enum {
@@ -183,6 +192,23 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
  * flight, OMM_ERR_UNSUPPORTED for sparse handles.
  */
 int omm_set_H(omm_handle *h, const double *H, int32_t on_device);
+
+/*
+ * Kinetic-energy matrix T (m x m column-major FP64, symmetric, host or device
+ * memory; copied into the handle) of the preconditioner P = (S + T/tau_T)^-1
+ * of Eq. 6 (section "Overview of OMM approaches").  P is formed on the GPU at
+ * the first preconditioned solve after omm_set_T or a new S (omm_set_HS):
+ * Cholesky factor of S + T/tau_T, its inverse Y = L^-1 and P = Y^T Y, with
+ * exact-digit tensor-core products; omm_set_H keeps it.  Each CG step then
+ * adds one m x m by m x n product Z = P G (FP64 form: FP64 product; mixed
+ * form: split product on the FP32 gradient).  Resets the count of
+ * preconditioned solves (omm_options.precon > 0).  Returns
+ * OMM_ERR_UNSUPPORTED for sparse handles and handles created with precon = 0,
+ * OMM_ERR_STATE while a solve is in flight.  A solve with precon != 0 and no T
+ * returns OMM_ERR_STATE; S + T/tau_T that is not positive definite makes that
+ * solve return OMM_ERR_NOT_SPD.
+ */
+int omm_set_T(omm_handle *h, const double *T, int32_t on_device);
 
 /*
  * Minimise from W0 (m x n column-major; sparse: 8x2-style block values in the
@@ -293,13 +319,13 @@ const char *omm_last_error(void);
  * line-search coefficients and minimum (2); W/H'W/SW and H_W/S_W update with
  * energy test (3); gradient (4); CG direction (5); per-(H,S) setup (6);
  * solve start-up (7); split-precision operand packing (8); refinement
- * re-anchoring (9).
+ * re-anchoring (9); kinetic-energy preconditioner product P G (10).
  */
 enum {
     OMM_STAGE_PRODUCTS = 0, OMM_STAGE_CONTRACT = 1, OMM_STAGE_LINESEARCH = 2,
     OMM_STAGE_UPDATE = 3, OMM_STAGE_GRADIENT = 4, OMM_STAGE_DIRECTION = 5,
     OMM_STAGE_SETUP = 6, OMM_STAGE_START = 7, OMM_STAGE_PACK = 8, OMM_STAGE_ANCHOR = 9,
-    OMM_NSTAGES = 10
+    OMM_STAGE_PRECON = 10, OMM_NSTAGES = 11
 };
 int omm_set_profiling(omm_handle *h, int32_t on);
 int omm_get_stage_times(omm_handle *h, double *ms, int64_t *launches, int32_t nstages,

@@ -328,9 +328,12 @@ __global__ void __launch_bounds__(NT) update_kernel(int m, int n, double *W, con
     }
 }
 
-constexpr int ND = 3;   // <G,G>, <G,Gp>, <G,D>
+// <Z,G>, <Z,Gp>, <G,D> with Z = P G the preconditioned gradient (Z = G without
+// preconditioning: then <G,G>, <G,Gp>, <G,D>)
+constexpr int ND = 3;
 
 __global__ void __launch_bounds__(NT) dots_kernel(int64_t mn, const double *__restrict__ G,
+                                                   const double *__restrict__ Zg,
                                                    const double *__restrict__ Gp,
                                                    const double *__restrict__ D, double *partials,
                                                    unsigned int *counter, DevState *state,
@@ -339,10 +342,10 @@ __global__ void __launch_bounds__(NT) dots_kernel(int64_t mn, const double *__re
     __shared__ double red[(NT / 32) * ND];
     double v[ND] = {0.0, 0.0, 0.0};
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < mn; i += (int64_t)gridDim.x * NT) {
-        const double g = G[i];
-        v[0] = fma(g, g, v[0]);
+        const double g = G[i], z = Zg[i];
+        v[0] = fma(z, g, v[0]);
         if (!first) {
-            v[1] = fma(g, Gp[i], v[1]);
+            v[1] = fma(z, Gp[i], v[1]);
             v[2] = fma(g, D[i], v[2]);
         }
     }
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(NT) dots_kernel(int64_t mn, const double *__re
     if (!first) {
         const double gpgp = state->gg_prev;
         beta = (gpgp > 0.0) ? fmax(0.0, (gg - tot[1]) / gpgp) : 0.0;
-        // <G, -G + beta D> >= 0 means no descent: restart with -G
+        // <G, -Z + beta D> >= 0 means no descent: restart with -Z
         restart = (-gg + beta * tot[2] >= 0.0) ? 1 : 0;
         if (restart) beta = 0.0;
     }
@@ -373,16 +376,17 @@ __global__ void __launch_bounds__(NT) dots_kernel(int64_t mn, const double *__re
     state->restart = restart;
 }
 
-__global__ void direction_kernel(int m, int n, const double *__restrict__ G, double *Gp, double *D,
-                                 const DevState *state, DigitOut dd) {
+// D = -Z + beta D (D = -Z on a restart); Gp <- G
+__global__ void direction_kernel(int m, int n, const double *__restrict__ G, const double *__restrict__ Zg,
+                                 double *Gp, double *D, const DevState *state, DigitOut dd) {
     if (*((volatile const int *)&state->done)) return;
     const double beta = state->beta;
     const bool restart = state->restart != 0;
     for (int j = blockIdx.y; j < n; j += gridDim.y)
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
             const int64_t o = (int64_t)j * m + i;
-            const double g = G[o];
-            const double d = restart ? -g : fma(beta, D[o], -g);
+            const double g = G[o], z = Zg[o];
+            const double d = restart ? -z : fma(beta, D[o], -z);
             D[o] = d;
             Gp[o] = g;
             if (dd.ptr != nullptr) put3(dd, (int64_t)j * dd.ld + i, d);
@@ -528,19 +532,19 @@ int launch_nn_update_energy(int n, double *h0, double *s0, int64_t ldh, const do
     return OMM_OK;
 }
 
-int launch_dots_beta(int64_t mn, const double *G, const double *Gp, const double *D,
+int launch_dots_beta(int64_t mn, const double *G, const double *Zg, const double *Gp, const double *D,
                      double *scratch, unsigned int *counter, DevState *state, int first,
                      cudaStream_t st) {
-    dots_kernel<<<red_blocks_for_len(mn), NT, 0, st>>>(mn, G, Gp, D, scratch, counter, state, first);
+    dots_kernel<<<red_blocks_for_len(mn), NT, 0, st>>>(mn, G, Zg, Gp, D, scratch, counter, state, first);
     omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
 
-int launch_direction(int64_t m, int64_t n, const double *G, double *Gp, double *D, const DevState *state,
-                     cudaStream_t st, DigitOut dd) {
+int launch_direction(int64_t m, int64_t n, const double *G, const double *Zg, double *Gp, double *D,
+                     const DevState *state, cudaStream_t st, DigitOut dd) {
     dim3 grid((unsigned)ceil_div(m, NT), (unsigned)(n < 1024 ? n : 1024));
-    direction_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, G, Gp, D, state, dd);
+    direction_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, G, Zg, Gp, D, state, dd);
     omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

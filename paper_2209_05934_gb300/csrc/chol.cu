@@ -126,6 +126,13 @@ __global__ void identity_kernel(double *a, int64_t m) {
             a[i + j * m] = (i == j) ? 1.0 : 0.0;
 }
 
+// M = S + T / tau, elementwise (the division as written, not a reciprocal product)
+__global__ void spd_sum_kernel(const double *__restrict__ S, const double *__restrict__ T, double tau, double *M,
+                               int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        M[i] = S[i] + T[i] / tau;
+}
+
 int blocks(int64_t n, int per) {
     int64_t b = ceil_div(n, per);
     if (b > 152 * 8) b = 152 * 8;
@@ -243,6 +250,28 @@ int transform(double *Hs, double *T, int64_t m, const Work &w, cudaStream_t st) 
     OMM_CUDA_TRY(cudaGetLastError());
     dim3 gi((unsigned)blocks(m, 256), (unsigned)(m < 4096 ? m : 4096));
     identity_kernel<<<gi, 256, 0, st>>>(T, m);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int precon(const double *S, const double *T, double tau, double *P, int64_t m, const Work &w, DevState *state,
+           cudaStream_t st) {
+    spd_sum_kernel<<<blocks(m * m, 256), 256, 0, st>>>(S, T, tau, P, m * m);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    int rc = cholesky(P, m, w, state, st);
+    if (rc != OMM_OK) return rc;
+    // P = Y^T Y by row blocks: rows [r0, r0 + rr) of P take columns [r0, r0 + rr)
+    // of Y, which are zero above row r0, so the K range is [r0, m)
+    const double *Y = w.Linv;
+    for (int64_t r0 = 0; r0 < m; r0 += kRowBlock) {
+        const int64_t rr = m - r0 < kRowBlock ? m - r0 : kRowBlock;
+        if ((rc = xmm(true, false, rr, m, m - r0, 1.0, Y + r0 + r0 * m, m, Y + r0, m, 0.0, P + r0, m, w, st)))
+            return rc;
+    }
+    dim3 g((unsigned)ceil_div(m, 32), (unsigned)ceil_div(m, 32));
+    symmetrize_kernel<<<g, 256, 0, st>>>(P, m);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

@@ -31,6 +31,11 @@ int lt_times(const double *T, int64_t m, const double *W, double *Wt, int64_t n,
 int factor(const double *S, double *L, int64_t m, const Work &w, DevState *state, cudaStream_t st);
 // Hs <- L^-1 Hs L^-T (symmetrised) with L^-1 from factor(); T (m x m scratch) <- I
 int transform(double *Hs, double *T, int64_t m, const Work &w, cudaStream_t st);
+// Kinetic-energy preconditioner (Eq. 6): P <- (S + T / tau)^-1 = Y^T Y with
+// Y = L^-1 of the Cholesky factor of S + T / tau (symmetrised; w.Linv <- Y);
+// state->status = OMM_ERR_NOT_SPD when S + T / tau is not positive definite.
+int precon(const double *S, const double *T, double tau, double *P, int64_t m, const Work &w, DevState *state,
+           cudaStream_t st);
 
 }  // namespace chol
 }  // namespace omm

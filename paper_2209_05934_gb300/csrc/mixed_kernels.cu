@@ -396,32 +396,35 @@ __global__ void __launch_bounds__(NT) mx_update2_kernel(int m, int n, double2 *W
 }
 
 // ---------------------------------------------------------------- CG dots and direction
-constexpr int ND = 3;   // <G,G>, <G,Gp>, <G,D>
+// <Z,G>, <Z,Gp>, <G,D> with Z = P G (PRE) or Z = G
+constexpr int ND = 3;
 
+template <bool PRE>
 __global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__restrict__ G,
-                                                      const float *__restrict__ Gp, const float *__restrict__ D,
-                                                      double *partials, unsigned int *counter, DevState *state,
-                                                      int first) {
+                                                      const float *__restrict__ Zg, const float *__restrict__ Gp,
+                                                      const float *__restrict__ D, double *partials,
+                                                      unsigned int *counter, DevState *state, int first) {
     if (*((volatile int *)&state->done)) return;
     __shared__ double red[(NT / 32) * ND];
     float f[ND] = {0.f, 0.f, 0.f};
     const int64_t n4 = mn / 4, stride = (int64_t)gridDim.x * NT;
     const float4 *G4 = reinterpret_cast<const float4 *>(G), *Gp4 = reinterpret_cast<const float4 *>(Gp),
-                 *D4 = reinterpret_cast<const float4 *>(D);
+                 *D4 = reinterpret_cast<const float4 *>(D), *Z4 = reinterpret_cast<const float4 *>(Zg);
     for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n4; k += stride) {
         const float4 g = G4[k];
-        f[0] = fmaf(g.x, g.x, fmaf(g.y, g.y, fmaf(g.z, g.z, fmaf(g.w, g.w, f[0]))));
+        const float4 z = PRE ? Z4[k] : g;
+        f[0] = fmaf(z.x, g.x, fmaf(z.y, g.y, fmaf(z.z, g.z, fmaf(z.w, g.w, f[0]))));
         if (!first) {
             const float4 p = Gp4[k], d = D4[k];
-            f[1] = fmaf(g.x, p.x, fmaf(g.y, p.y, fmaf(g.z, p.z, fmaf(g.w, p.w, f[1]))));
+            f[1] = fmaf(z.x, p.x, fmaf(z.y, p.y, fmaf(z.z, p.z, fmaf(z.w, p.w, f[1]))));
             f[2] = fmaf(g.x, d.x, fmaf(g.y, d.y, fmaf(g.z, d.z, fmaf(g.w, d.w, f[2]))));
         }
     }
     for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * NT + threadIdx.x; i < mn; i += stride) {   // tail
-        const float g = G[i];
-        f[0] = fmaf(g, g, f[0]);
+        const float g = G[i], z = PRE ? Zg[i] : g;
+        f[0] = fmaf(z, g, f[0]);
         if (!first) {
-            f[1] = fmaf(g, Gp[i], f[1]);
+            f[1] = fmaf(z, Gp[i], f[1]);
             f[2] = fmaf(g, D[i], f[2]);
         }
     }
@@ -455,16 +458,17 @@ __global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__
     state->gD = restart ? -gg : -gg + beta * tot[2];   // <G, D_new>
 }
 
-__global__ void mx_direction_kernel(int m, int n, const float *__restrict__ G, float *Gp, float *D,
-                                    const DevState *state, DigitOut dd) {
+// D = -Z + beta D (D = -Z on a restart), Z = P G (Zg) or G; Gp <- G
+__global__ void mx_direction_kernel(int m, int n, const float *__restrict__ G, const float *__restrict__ Zg,
+                                    float *Gp, float *D, const DevState *state, DigitOut dd) {
     if (*((volatile const int *)&state->done)) return;
     const float beta = state->beta_f;
     const bool restart = state->restart != 0;
     for (int j = blockIdx.y; j < n; j += gridDim.y)
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
             const int64_t o = (int64_t)j * m + i;
-            const float g = G[o];
-            const float d = restart ? -g : fmaf(beta, D[o], -g);
+            const float g = G[o], z = Zg != nullptr ? Zg[o] : g;
+            const float d = restart ? -z : fmaf(beta, D[o], -z);
             D[o] = d;
             Gp[o] = g;
             if (dd.ptr != nullptr) put3f(dd, (int64_t)j * dd.ld + i, d);
@@ -472,23 +476,25 @@ __global__ void mx_direction_kernel(int m, int n, const float *__restrict__ G, f
 }
 
 // four consecutive rows of one column per thread (m % 4 == 0, 16-byte aligned arrays)
+template <bool PRE>
 __global__ void __launch_bounds__(NT) mx_direction4_kernel(int m, int64_t mn, const float4 *__restrict__ G,
-                                                            float4 *Gp, float4 *D, const DevState *state,
-                                                            DigitOut dd) {
+                                                            const float4 *__restrict__ Zg, float4 *Gp, float4 *D,
+                                                            const DevState *state, DigitOut dd) {
     if (*((volatile const int *)&state->done)) return;
     const float beta = state->beta_f;
     const bool restart = state->restart != 0;
     const int64_t n4 = mn / 4;
     for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n4; k += (int64_t)gridDim.x * NT) {
         const float4 g = G[k];
+        const float4 z = PRE ? Zg[k] : g;
         float4 d = D[k];
         if (restart) {
-            d = make_float4(-g.x, -g.y, -g.z, -g.w);
+            d = make_float4(-z.x, -z.y, -z.z, -z.w);
         } else {
-            d.x = fmaf(beta, d.x, -g.x);
-            d.y = fmaf(beta, d.y, -g.y);
-            d.z = fmaf(beta, d.z, -g.z);
-            d.w = fmaf(beta, d.w, -g.w);
+            d.x = fmaf(beta, d.x, -z.x);
+            d.y = fmaf(beta, d.y, -z.y);
+            d.z = fmaf(beta, d.z, -z.z);
+            d.w = fmaf(beta, d.w, -z.w);
         }
         D[k] = d;
         Gp[k] = g;
@@ -497,6 +503,23 @@ __global__ void __launch_bounds__(NT) mx_direction4_kernel(int m, int64_t mn, co
             put3f4(dd, j * dd.ld + i, d);
         }
     }
+}
+
+// Digits of four consecutive rows of one column per thread (m % 4 == 0)
+__global__ void __launch_bounds__(NT) mx_digits4_kernel(int m, int64_t mn, const float4 *__restrict__ A,
+                                                         const DevState *state, DigitOut dd) {
+    if (*((volatile const int *)&state->done)) return;
+    for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < mn / 4; k += (int64_t)gridDim.x * NT) {
+        const int64_t o = 4 * k, j = o / m, i = o - j * m;
+        put3f4(dd, j * dd.ld + i, A[k]);
+    }
+}
+
+__global__ void mx_digits_kernel(int m, int n, const float *__restrict__ A, const DevState *state, DigitOut dd) {
+    if (*((volatile const int *)&state->done)) return;
+    for (int j = blockIdx.y; j < n; j += gridDim.y)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+            put3f(dd, (int64_t)j * dd.ld + i, A[(int64_t)j * m + i]);
 }
 
 __global__ void mx_round_kernel(int64_t count, const double *__restrict__ src, float *dst, const DevState *state) {
@@ -553,33 +576,60 @@ int mx_nn_update(int n, double *h0, double *s0, int64_t ldh, const float *Z, int
     return OMM_OK;
 }
 
-int mx_dots_beta(int64_t mn, const float *G, const float *Gp, const float *D, double *scratch,
+int mx_dots_beta(int64_t mn, const float *G, const float *Zg, const float *Gp, const float *D, double *scratch,
                  unsigned int *counter, DevState *state, int first, cudaStream_t st) {
-    if (((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)D)) & 15u) != 0) return OMM_ERR_ARG;
+    if (((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)D) | ((uintptr_t)Zg)) & 15u) != 0) return OMM_ERR_ARG;
     int64_t nb = ceil_div(mn, (int64_t)NT * 32);
     if (nb > 152 * 2) nb = 152 * 2;
-    mx_dots_kernel<<<(unsigned)(nb < 1 ? 1 : nb), NT, 0, st>>>(mn, G, Gp, D, scratch, counter, state, first);
+    const unsigned grid = (unsigned)(nb < 1 ? 1 : nb);
+    if (Zg != nullptr)
+        mx_dots_kernel<true><<<grid, NT, 0, st>>>(mn, G, Zg, Gp, D, scratch, counter, state, first);
+    else
+        mx_dots_kernel<false><<<grid, NT, 0, st>>>(mn, G, G, Gp, D, scratch, counter, state, first);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
 }
 
-int mx_direction(int64_t m, int64_t n, const float *G, float *Gp, float *D, const DevState *state, DigitOut dd,
-                 cudaStream_t st) {
-    const bool aligned = ((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)D)) & 15u) == 0 &&
+int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *D, const DevState *state,
+                 DigitOut dd, cudaStream_t st) {
+    const bool aligned = ((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)D) | ((uintptr_t)Zg)) & 15u) == 0 &&
                          (dd.ptr == nullptr || ((((uintptr_t)dd.ptr) & 7u) == 0 && dd.ld % 4 == 0 && dd.plane % 4 == 0));
     if (m % 4 == 0 && aligned) {
         int64_t nb = ceil_div(m * n / 4, (int64_t)NT * 4);
         if (nb > 152 * 8) nb = 152 * 8;
-        mx_direction4_kernel<<<(unsigned)(nb < 1 ? 1 : nb), NT, 0, st>>>(
-            (int)m, m * n, reinterpret_cast<const float4 *>(G), reinterpret_cast<float4 *>(Gp),
-            reinterpret_cast<float4 *>(D), state, dd);
+        const unsigned grid = (unsigned)(nb < 1 ? 1 : nb);
+        const float4 *G4 = reinterpret_cast<const float4 *>(G);
+        if (Zg != nullptr)
+            mx_direction4_kernel<true><<<grid, NT, 0, st>>>((int)m, m * n, G4, reinterpret_cast<const float4 *>(Zg),
+                                                             reinterpret_cast<float4 *>(Gp),
+                                                             reinterpret_cast<float4 *>(D), state, dd);
+        else
+            mx_direction4_kernel<false><<<grid, NT, 0, st>>>((int)m, m * n, G4, G4, reinterpret_cast<float4 *>(Gp),
+                                                              reinterpret_cast<float4 *>(D), state, dd);
         count_launch();
         OMM_CUDA_TRY(cudaGetLastError());
         return OMM_OK;
     }
     dim3 grid((unsigned)ceil_div(m, NT), (unsigned)(n < 1024 ? n : 1024));
-    mx_direction_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, G, Gp, D, state, dd);
+    mx_direction_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, G, Zg, Gp, D, state, dd);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int mx_digits(int64_t m, int64_t n, const float *A, const DevState *state, DigitOut dd, cudaStream_t st) {
+    const bool aligned = (((uintptr_t)A) & 15u) == 0 && (((uintptr_t)dd.ptr) & 7u) == 0 && dd.ld % 4 == 0 &&
+                         dd.plane % 4 == 0;
+    if (m % 4 == 0 && aligned) {
+        int64_t nb = ceil_div(m * n / 4, (int64_t)NT * 4);
+        if (nb > 152 * 8) nb = 152 * 8;
+        mx_digits4_kernel<<<(unsigned)(nb < 1 ? 1 : nb), NT, 0, st>>>((int)m, m * n,
+                                                                       reinterpret_cast<const float4 *>(A), state, dd);
+    } else {
+        dim3 grid((unsigned)ceil_div(m, NT), (unsigned)(n < 1024 ? n : 1024));
+        mx_digits_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, A, state, dd);
+    }
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

@@ -12,6 +12,7 @@
 // The side-by-side layouts turn each step into one GEMM: the two products
 // H'D and SD share D; the four n x n contractions are [W D]^T [H'D SD]; the
 // gradient is 4 H'W - 2 [SW H'W] [H_W ; S_W].
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -34,11 +35,16 @@
 //   HSWd  [3][n][ld2n]   columns of [H_W ; S_W]                     B of the gradient
 // FP32 increments of the mixed form (column-major): HDSD32 = [H'D | SD] (m x 2n),
 // Z32 = [[X, Y], [h2, s2]] (2n x 2n), G32, Gp32, D32 (m x n).
+// Kinetic-energy preconditioning: Pd [3][m][ldm] columns of P (= rows) as the A
+// operand and Gd [3][n][ldm] columns of G as the B operand of P G -> PG32 (m x n).
 struct MixedBufs {
     int64_t ldm = 0, ld2n = 0;
     __nv_bfloat16 *HSd = nullptr, *WDd = nullptr, *HDSDd = nullptr, *SWHWd = nullptr, *HSWd = nullptr;
     CUtensorMap mapHS_A, mapWD_A, mapWD_B, mapHDSD_B, mapSWHW_A, mapHSW_B;
     float *HDSD32 = nullptr, *Z32 = nullptr, *G32 = nullptr, *Gp32 = nullptr, *D32 = nullptr;
+    __nv_bfloat16 *Pd = nullptr, *Gd = nullptr;
+    CUtensorMap mapP_A, mapG_B;
+    float *PG32 = nullptr;
 };
 
 // Exact-digit operands of the refinement sweep (s digits, row-scaled), each
@@ -92,7 +98,15 @@ struct omm_handle {
     double *L = nullptr;      // Cholesky variant: factor of S (m x m)
     double *Wsave = nullptr;  // Cholesky variant: W in the original basis (m x n)
     double *S0 = nullptr;     // Cholesky variant: the original S (its slot holds I)
-    omm::chol::Work cw;       // Cholesky variant: GEMM workspace and inverted diagonal blocks
+    omm::chol::Work cw;       // Cholesky variant and preconditioner: GEMM workspace and L^-1
+    // kinetic-energy preconditioning (Eq. 6): T as given, P = (S + T/tau)^-1 and
+    // the preconditioned gradient P G (m x n)
+    double *Tk = nullptr, *P = nullptr, *PG = nullptr;
+    bool have_T = false;      // omm_set_T has run
+    bool p_ready = false;     // P matches the current S and T
+    bool precon_on = false;   // the current solve applies P
+    bool graph_precon = false;  // precon_on of the captured chunk graphs
+    int precon_left = 0;      // preconditioned solves left (omm_options.precon > 0)
     int phase = 0;            // PH_* of the asynchronous driver
     int k_mixed = 0;          // CG steps of the split-precision phase
     int status = OMM_OK;      // status of the finished solve
@@ -165,6 +179,12 @@ void free_handle(omm_handle *h) {
     cudaFree(h->dT);
     cudaFree(h->dOut);
     cudaFree(h->dWs);
+    cudaFree(h->Tk);
+    cudaFree(h->P);
+    cudaFree(h->PG);
+    cudaFree(h->mx.Pd);
+    cudaFree(h->mx.Gd);
+    cudaFree(h->mx.PG32);
     omm::sp::release(h->sd);
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -227,6 +247,24 @@ bool s_identity(const omm_handle *h) { return h->opt.cholesky != 0 && !h->sparse
 // Kim functional's extra columns
 int64_t n_occ(const omm_handle *h) { return h->opt.n_occupied > 0 ? h->opt.n_occupied : h->n; }
 
+// CG dots, beta and direction of the dense FP64 form; with the kinetic-energy
+// preconditioner the gradient is first multiplied by P (Eq. 6): Z = P G.
+int dense_direction(omm_handle *h, int first) {
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    cudaStream_t st = h->stream;
+    const double *Zg = h->G;
+    if (h->precon_on) {
+        StageTimer t(h, OMM_STAGE_PRECON);
+        omm::GemmBatch p{};
+        p.A[0] = h->P; p.B[0] = h->G; p.C[0] = h->PG; p.Cin[0] = nullptr;
+        TRY(omm::dgemm_batched(false, false, m, n, m, 1.0, p, 1, m, m, 0.0, m, m, h->dstate, st));
+        Zg = h->PG;
+    }
+    StageTimer t(h, OMM_STAGE_DIRECTION);
+    TRY(omm::launch_dots_beta(mn, h->G, Zg, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), h->dstate, first, st));
+    return omm::launch_direction(m, n, h->G, Zg, h->Gp, h->WD + mn, h->dstate, st);
+}
+
 int dense_iteration(omm_handle *h) {
     const int64_t m = h->m, n = h->n, mn = m * n;
     cudaStream_t st = h->stream;
@@ -259,10 +297,7 @@ int dense_iteration(omm_handle *h) {
     omm::GemmBatch g{};
     g.A[0] = h->SWHW; g.B[0] = h->h0s0; g.Cin[0] = h->SWHW + mn; g.C[0] = h->G;
     { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, s, st)); }
-    { StageTimer t(h, OMM_STAGE_DIRECTION);
-      TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 0, st));
-      TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st)); }
-    return OMM_OK;
+    return dense_direction(h, 0);
 }
 
 int dense_start(omm_handle *h) {
@@ -286,9 +321,7 @@ int dense_start(omm_handle *h) {
     omm::GemmBatch g{};
     g.A[0] = h->SWHW; g.B[0] = h->h0s0; g.Cin[0] = h->SWHW + mn; g.C[0] = h->G;
     TRY(omm::dgemm_batched(false, false, m, n, 2 * n, -2.0, g, 1, m, 2 * n, 4.0, m, m, s, st));
-    TRY(omm::launch_dots_beta(mn, h->G, h->Gp, h->WD + mn, scr(h, 2), ctr(h, 2), s, 1, st));
-    TRY(omm::launch_direction(m, n, h->G, h->Gp, h->WD + mn, s, st));
-    return OMM_OK;
+    return dense_direction(h, 1);
 }
 
 // ---------------------------------------------------------------- mixed precision
@@ -545,13 +578,25 @@ int exact_anchor(omm_handle *h) {
     return OMM_OK;
 }
 
-// CG dots + direction of the mixed form (FP32 G, Gp, D; digits of D)
+// CG dots + direction of the mixed form (FP32 G, Gp, D; digits of D).  With the
+// kinetic-energy preconditioner: digits of G, then the split product
+// Z = P G in FP32 (Eq. 6), which forms the direction and beta.
 int mixed_direction(omm_handle *h, int first) {
     const int64_t m = h->m, n = h->n;
+    MixedBufs &x = h->mx;
+    const float *Zg = nullptr;
+    if (h->precon_on) {
+        StageTimer t(h, OMM_STAGE_PRECON);
+        TRY(omm::mx_digits(m, n, x.G32, h->dstate, omm::DigitOut{x.Gd, x.ldm, n * x.ldm, h->cur_dig}, h->stream));
+        omm::tc::TcArgs a = tc_args(h, (int)m, (int)n, (int)m);
+        a.C32 = x.PG32;
+        a.ldc = m;
+        TRY(omm::tc::gemm(x.mapP_A, x.mapG_B, a, 1, kBN, h->stream));
+        Zg = x.PG32;
+    }
     StageTimer t(h, OMM_STAGE_DIRECTION);
-    TRY(omm::mx_dots_beta(m * n, h->mx.G32, h->mx.Gp32, h->mx.D32, scr(h, 2), ctr(h, 2), h->dstate, first,
-                          h->stream));
-    return omm::mx_direction(m, n, h->mx.G32, h->mx.Gp32, h->mx.D32, h->dstate, dig_D(h), h->stream);
+    TRY(omm::mx_dots_beta(m * n, x.G32, Zg, x.Gp32, x.D32, scr(h, 2), ctr(h, 2), h->dstate, first, h->stream));
+    return omm::mx_direction(m, n, x.G32, Zg, x.Gp32, x.D32, h->dstate, dig_D(h), h->stream);
 }
 
 // Start of the split-precision phase: H'W, SW, H_W, S_W, energy, G, D from W.
@@ -716,6 +761,62 @@ int enqueue_chunk(omm_handle *h) {
     return OMM_OK;
 }
 
+// Buffers of the kinetic-energy preconditioner (T, P, P G; the exact-digit GEMM
+// workspace and L^-1 of its Cholesky factor; the mixed form's digit planes).
+int precon_alloc(omm_handle *h) {
+    const int64_t m = h->m, n = h->n;
+    h->cw.s = h->opt.exact_digits;
+    h->cw.bytes = omm::chol::work_bytes(m, n, h->cw.s);
+    TRY(dalloc(&h->Tk, (size_t)(m * m)));
+    TRY(dalloc(&h->P, (size_t)(m * m)));
+    TRY(dalloc(&h->PG, (size_t)(m * n)));
+    TRY(dalloc(&h->cw.Linv, (size_t)omm::chol::linv_elems(m)));
+    if (cudaMalloc(&h->cw.ws, (size_t)h->cw.bytes) != cudaSuccess) {
+        h->cw.ws = nullptr;
+        return OMM_ERR_NOMEM;
+    }
+    if (h->opt.precision == OMM_PREC_MIXED) {
+        MixedBufs &x = h->mx;
+        TRY(dalloc(&x.Pd, (size_t)(kDig * m * x.ldm)));
+        TRY(dalloc(&x.Gd, (size_t)(kDig * n * x.ldm)));
+        TRY(dalloc(&x.PG32, (size_t)(m * n)));
+        TRY(omm::tc::make_digit_map(&x.mapP_A, x.Pd, m, m, x.ldm, m * x.ldm, kDig, 128, kBK));
+        TRY(omm::tc::make_digit_map(&x.mapG_B, x.Gd, m, n, x.ldm, n * x.ldm, kDig, kBN, kBK));
+    }
+    return OMM_OK;
+}
+
+// P = (S + T / tau)^-1 for the current S and T (synchronous; OMM_ERR_NOT_SPD
+// when S + T / tau is not positive definite), and its digits for the mixed form.
+int precon_build(omm_handle *h) {
+    const int64_t m = h->m;
+    cudaStream_t st = h->stream;
+    omm::DevState init{};
+    *h->hstate = init;
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
+    {
+        StageTimer t(h, OMM_STAGE_SETUP);
+        TRY(omm::chol::precon(h->HS + m * m, h->Tk, h->opt.tau_T, h->P, m, h->cw, h->dstate, st));
+        if (h->opt.precision == OMM_PREC_MIXED)
+            TRY(omm::tc::pack_cm(m, m, h->P, m, h->mx.Pd, h->mx.ldm, m * h->mx.ldm, kDig, nullptr, st));
+    }
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->hstate->status != OMM_OK) return h->hstate->status;
+    h->p_ready = true;
+    return OMM_OK;
+}
+
+// Captured chunk graphs hold the launches of one choice of preconditioning.
+void drop_graphs(omm_handle *h) {
+    for (int i = 0; i < omm_handle::kPhases; ++i) {
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        h->graph[i] = nullptr;
+        h->graph_kernels[i] = 0;
+        h->graph_eager[i] = 0;
+    }
+}
+
 // Dense setup for omm_set_HS (S given) and omm_set_H (S == nullptr: the
 // previous S, and with the Cholesky variant its factor, are kept).
 int dense_set(omm_handle *h, const double *H, const double *S, bool on_device) {
@@ -729,6 +830,7 @@ int dense_set(omm_handle *h, const double *H, const double *S, bool on_device) {
     // and shifted in place
     if (S != nullptr) {
         h->have_S = false;
+        h->p_ready = false;
         OMM_CUDA_TRY(cudaMemcpyAsync(h->HS + mm, S, mm * sizeof(double), kind, st));
         if (chol) OMM_CUDA_TRY(cudaMemcpyAsync(h->S0, h->HS + mm, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
     } else if (chol) {
@@ -793,6 +895,8 @@ void omm_default_options(omm_options *opt) {
     opt->split_digits = 2;
     opt->graphs = 1;
     opt->n_occupied = 0;
+    opt->precon = 0;
+    opt->tau_T = 136.05693122994;   // 10 Ry in eV
 }
 
 const char *omm_status_str(int status) {
@@ -826,7 +930,8 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
             pattern->W_rowptr == nullptr || pattern->W_col == nullptr)
             return OMM_ERR_PATTERN;
         if (pattern->bm != 8 || pattern->bn != 2) return OMM_ERR_UNSUPPORTED;
-        if (opt != nullptr && (opt->precision != OMM_PREC_FP64 || opt->cholesky != 0)) return OMM_ERR_UNSUPPORTED;
+        if (opt != nullptr && (opt->precision != OMM_PREC_FP64 || opt->cholesky != 0 || opt->precon != 0))
+            return OMM_ERR_UNSUPPORTED;
     }
     omm_handle *h = new (std::nothrow) omm_handle();
     if (h == nullptr) return OMM_ERR_NOMEM;
@@ -837,9 +942,14 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
     if (h->opt.max_iter < 0 || (h->opt.refine != OMM_REFINE_EXACT && h->opt.refine != OMM_REFINE_FP64) ||
         h->opt.exact_digits < 1 || h->opt.exact_digits > omm::tc::kExactMaxDigits || h->opt.split_digits < 2 ||
         h->opt.split_digits > 3 || h->opt.n_occupied < 0 || h->opt.n_occupied > n ||
-        (h->opt.n_occupied > 0 && h->opt.n_occupied < n && h->opt.eta_auto)) {
+        (h->opt.n_occupied > 0 && h->opt.n_occupied < n && h->opt.eta_auto) ||
+        (h->opt.precon != 0 && !(h->opt.tau_T > 0.0 && isfinite(h->opt.tau_T)))) {
         delete h;
         return OMM_ERR_ARG;
+    }
+    if (h->opt.precon != 0 && h->opt.cholesky != 0) {   // two answers to the same ill-conditioning
+        delete h;
+        return OMM_ERR_UNSUPPORTED;
     }
     if (h->opt.precision != OMM_PREC_FP64 && h->opt.precision != OMM_PREC_MIXED) {
         delete h;
@@ -903,6 +1013,10 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         }
     }
     if (h->opt.precision == OMM_PREC_MIXED && h->opt.refine == OMM_REFINE_EXACT && (rc = exact_alloc(h))) {
+        free_handle(h);
+        return rc;
+    }
+    if (!h->sparse && h->opt.precon != 0 && (rc = precon_alloc(h))) {
         free_handle(h);
         return rc;
     }
@@ -971,15 +1085,39 @@ int omm_set_H(omm_handle *h, const double *H, int32_t on_device) {
     return dense_set(h, H, nullptr, on_device != 0);
 }
 
+int omm_set_T(omm_handle *h, const double *T, int32_t on_device) {
+    if (h == nullptr || T == nullptr) return OMM_ERR_ARG;
+    if (h->sparse || h->opt.precon == 0) return OMM_ERR_UNSUPPORTED;
+    if (h->phase != PH_IDLE && h->phase != PH_FINISHED) return OMM_ERR_STATE;
+    h->have_T = false;
+    h->p_ready = false;
+    OMM_CUDA_TRY(cudaMemcpyAsync(h->Tk, T, (size_t)(h->m * h->m) * sizeof(double),
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    OMM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->have_T = true;
+    h->precon_left = h->opt.precon > 0 ? h->opt.precon : 0;
+    return OMM_OK;
+}
+
 int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, double tol) {
     if (h == nullptr || !(tol >= 0.0)) return OMM_ERR_ARG;
     h->solved = false;
     if (!h->have_HS) return OMM_ERR_STATE;
     if (W0 == nullptr && !h->have_W) return OMM_ERR_STATE;
     if (h->phase != PH_IDLE && h->phase != PH_FINISHED) return OMM_ERR_STATE;
+    if (h->opt.precon != 0 && !h->have_T) return OMM_ERR_STATE;
     const int64_t n = h->n;
     cudaStream_t st = h->stream;
     OMM_CUDA_TRY(cudaEventRecord(h->ev0, st));
+    h->precon_on = h->opt.precon < 0 || (h->opt.precon > 0 && h->precon_left > 0);
+    if (h->precon_on) {
+        if (!h->p_ready) TRY(precon_build(h));
+        if (h->opt.precon > 0) --h->precon_left;
+    }
+    if (h->precon_on != h->graph_precon) {
+        drop_graphs(h);
+        h->graph_precon = h->precon_on;
+    }
     if (h->opt.cholesky && !h->sparse) {
         // W~ = L^T W: W0, or the previous solution kept in the original basis
         if (W0 != nullptr)

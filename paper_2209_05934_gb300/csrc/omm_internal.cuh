@@ -98,14 +98,15 @@ int launch_nn_update_energy(int n, double *h0, double *s0, int64_t ldh, const do
                             int64_t ldz, double *scratch, unsigned int *counter, DevState *state,
                             int mode, cudaStream_t st, DigitOut hsw = DigitOut{nullptr, 0, 0});
 
-// <G,G>, <G,Gp>, <G,D> then beta (PR+) and the restart decision
-int launch_dots_beta(int64_t mn, const double *G, const double *Gp, const double *D,
+// <Z,G>, <Z,Gp>, <G,D> then beta (PR+) and the restart decision; Z = P G is the
+// preconditioned gradient (Z = G without preconditioning)
+int launch_dots_beta(int64_t mn, const double *G, const double *Zg, const double *Gp, const double *D,
                      double *scratch, unsigned int *counter, DevState *state, int first,
                      cudaStream_t st);
 
-// D = -G + beta D (or -G on restart); Gp = G; optionally the digits of D (columns)
-int launch_direction(int64_t m, int64_t n, const double *G, double *Gp, double *D, const DevState *state,
-                     cudaStream_t st, DigitOut dd = DigitOut{nullptr, 0, 0});
+// D = -Z + beta D (or -Z on restart); Gp = G; optionally the digits of D (columns)
+int launch_direction(int64_t m, int64_t n, const double *G, const double *Zg, double *Gp, double *D,
+                     const DevState *state, cudaStream_t st, DigitOut dd = DigitOut{nullptr, 0, 0});
 
 // H' = H - eta S (dense, m x m), eta read from state
 int launch_shift(int64_t mm, const double *H, const double *S, double *Hs, const DevState *state,
@@ -124,10 +125,13 @@ int mx_update(int64_t m, int64_t n, double *W, const float *D, double *HW, const
               const float *SD, const DevState *state, DigitOut wd, DigitOut swhw, cudaStream_t st);
 int mx_nn_update(int n, double *h0, double *s0, int64_t ldh, const float *Z, int64_t ldz, double *scratch,
                  unsigned int *counter, DevState *state, DigitOut hsw, cudaStream_t st);
-int mx_dots_beta(int64_t mn, const float *G, const float *Gp, const float *D, double *scratch,
+// Zg: the preconditioned gradient P G, or nullptr (Z = G)
+int mx_dots_beta(int64_t mn, const float *G, const float *Zg, const float *Gp, const float *D, double *scratch,
                  unsigned int *counter, DevState *state, int first, cudaStream_t st);
-int mx_direction(int64_t m, int64_t n, const float *G, float *Gp, float *D, const DevState *state, DigitOut dd,
-                 cudaStream_t st);
+int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *D, const DevState *state,
+                 DigitOut dd, cudaStream_t st);
+// digits of an FP32 m x n column-major array: column j -> row j of the planes
+int mx_digits(int64_t m, int64_t n, const float *A, const DevState *state, DigitOut dd, cudaStream_t st);
 int mx_round(int64_t count, const double *src, float *dst, const DevState *state, cudaStream_t st);
 
 __device__ __host__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

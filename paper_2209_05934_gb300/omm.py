@@ -31,7 +31,7 @@ class Options(C.Structure):
                 ("cholesky", C.c_int32), ("max_iter", C.c_int32), ("orth_tol", C.c_double),
                 ("filter_eps", C.c_double), ("stream", C.c_void_p), ("refine", C.c_int32),
                 ("exact_digits", C.c_int32), ("split_digits", C.c_int32), ("graphs", C.c_int32),
-                ("n_occupied", C.c_int32)]
+                ("n_occupied", C.c_int32), ("precon", C.c_int32), ("tau_T", C.c_double)]
 
 
 class Pattern(C.Structure):
@@ -59,6 +59,7 @@ _SIGS = {
                              C.POINTER(C.c_void_p)]),
     "omm_set_HS": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "omm_set_H": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "omm_set_T": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "omm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
                             C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "omm_get_diag": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
@@ -100,7 +101,7 @@ _SIGS = {
                                     C.c_void_p, C.c_int64, C.c_void_p]),
 }
 
-NSTAGES = 10
+NSTAGES = 11
 
 
 def lib():
@@ -223,6 +224,12 @@ class Solver:
         _check_colmajor(H, self.m, self.m, "H")
         pH, dH = _ptr(H)
         return check(lib().omm_set_H(self._h, pH, dH), "omm_set_H")
+
+    def set_T(self, T):
+        """Kinetic-energy matrix of the preconditioner P = (S + T/tau_T)^-1; see omm_set_T."""
+        _check_colmajor(T, self.m, self.m, "T")
+        pT, dT = _ptr(T)
+        return check(lib().omm_set_T(self._h, pT, dT), "omm_set_T")
 
     def solve(self, W0=None, tol: float = 1e-10, W_out=None, raise_on_error=True):
         if W0 is not None:
