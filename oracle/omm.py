@@ -368,6 +368,42 @@ def omm_cg_cholesky(H, S, W0, tol: float = 1e-10, eta: float | None = None,
 # ----------------------------------------------------------------------------
 # sparse-form helpers
 # ----------------------------------------------------------------------------
+def md_guess(W1, pat1, pat_new, W2=None, pat2=None):
+    """Initial W of a new MD step (section "C† matrix initialization and update").
+
+    The previous step's W blocks (W1 on pattern pat1) are carried onto the new
+    localisation pattern pat_new: a block whose atoms moved farther apart than
+    R_C is not in pat_new and is dropped; a block of pat_new that W1 does not
+    hold (its atoms came within R_C) starts at zero.  With the step before
+    (W2 on pat2) the guess is the linear extrapolation 2 W1 - W2 on the blocks
+    W1 holds, a block that W2 lacks counting as zero there.  W1, W2: block
+    values (nnz, bm, bn); patterns: (rowptr, col) over basis-atom rows.
+    """
+    def where(pat):
+        rp, col = pat
+        return {(I, int(col[b])): b for I in range(len(rp) - 1) for b in range(rp[I], rp[I + 1])}
+
+    at1 = where(pat1)
+    at2 = where(pat2) if W2 is not None else None
+    rp, col = pat_new
+    out = np.zeros((len(col),) + tuple(W1.shape[1:]))
+    for I in range(len(rp) - 1):
+        for b in range(rp[I], rp[I + 1]):
+            key = (I, int(col[b]))
+            if key not in at1:
+                continue
+            if W2 is None:
+                out[b] = W1[at1[key]]
+            else:
+                out[b] = 2.0 * W1[at1[key]] - (W2[at2[key]] if key in at2 else 0.0)
+    return out
+
+
+def md_guess_dense(W1, W2=None):
+    """Dense form of md_guess: W1, or the linear extrapolation 2 W1 - W2."""
+    return np.array(W1, copy=True) if W2 is None else 2.0 * W1 - W2
+
+
 def bsr_to_csr(rowptr, col, vals, nbrows: int, nbcols: int):
     """Assemble a scipy CSR matrix from block-CSR arrays (blocks row-major)."""
     bm, bn = vals.shape[1], vals.shape[2]

@@ -36,6 +36,13 @@ an insulating gap, n/m = 1/4 occupied orbitals, localised W patterns):
   (N x 8), then all K blocks (npairs x 8 x 8) in pair order; H, S and W0 are
   unchanged by it.  The kinetic workload's Hamiltonian is H + T (spectrum
   widened to ~400 eV above a gap of a few eV).
+* MD trajectories (the pattern update and extrapolation of W between MD
+  steps): make_md_system places the atoms at grid + jitter + t * step * v,
+  with the jitter and onsite noise drawn as in make_system and one velocity
+  v ~ N(0,1)^3 per atom from a PCG64 stream seeded with seed + 3*10**6.  Its
+  pair blocks are keyed by the pair: R_IJ, then B_IJ, from a PCG64 stream
+  seeded with (seed, I, J), so H and S change smoothly with the positions and
+  a pair entering the 5 A cutoff brings its own block (small at the cutoff).
 * Batched systems: N atoms = round(exp(U(ln 32, ln 384))) drawn from a PCG64
   stream seeded with the batch seed; the first N sites of the ceil(N^(1/3))^3
   grid in index order.
@@ -274,6 +281,42 @@ def make_system(nx: int, ny: int | None = None, nz: int | None = None, seed: int
     r = np.sqrt(dv[:, 0] * dv[:, 0] + dv[:, 1] * dv[:, 1] + dv[:, 2] * dv[:, 2])
     R = rng.standard_normal(size=(pairs.shape[0], ORB_PER_ATOM, ORB_PER_ATOM))
     B = rng.uniform(-1.0, 1.0, size=(pairs.shape[0], ORB_PER_ATOM, ORB_PER_ATOM)) / ORB_PER_ATOM
+    H_pair = (0.8 * np.exp(-r / 1.5))[:, None, None] * R
+    S_pair = (0.15 * np.exp(-r / 1.2))[:, None, None] * B
+    return System(seed=seed, positions=pos, onsite_H=onsite, pairs=pairs, pair_r=r,
+                  H_pair=H_pair, S_pair=S_pair)
+
+
+MD_SEED_OFFSET = 3 * 10 ** 6
+
+
+def make_md_system(nx: int, ny: int | None = None, nz: int | None = None, seed: int = 0, t: float = 0.0,
+                   step: float = 0.1) -> System:
+    """Snapshot t of a straight-line MD trajectory of the make_system geometry
+    (velocity N(0,1)^3 per atom, `step` Angstrom per unit of t), with pair
+    blocks keyed by (seed, I, J) so that H and S follow the positions smoothly."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    base = grid_positions(nx, ny, nz)
+    N = base.shape[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos = base + rng.uniform(-JITTER, JITTER, size=(N, 3))
+    onsite_diag = ONSITE[None, :] + rng.normal(0.0, ONSITE_SIGMA, size=(N, ORB_PER_ATOM))
+    vel = np.random.Generator(np.random.PCG64(seed + MD_SEED_OFFSET)).standard_normal((N, 3))
+    pos = pos + (t * step) * vel
+    onsite = np.zeros((N, ORB_PER_ATOM, ORB_PER_ATOM))
+    idx = np.arange(ORB_PER_ATOM)
+    onsite[:, idx, idx] = onsite_diag
+    I, J = _pairs_within(pos, HS_CUTOFF, include_self=False, both=False)
+    pairs = np.stack([I, J], axis=1)
+    dv = pos[I] - pos[J]
+    r = np.sqrt(dv[:, 0] * dv[:, 0] + dv[:, 1] * dv[:, 1] + dv[:, 2] * dv[:, 2])
+    R = np.empty((pairs.shape[0], ORB_PER_ATOM, ORB_PER_ATOM))
+    B = np.empty_like(R)
+    for p, (a, b) in enumerate(pairs):
+        prng = np.random.Generator(np.random.PCG64([seed, int(a), int(b)]))
+        R[p] = prng.standard_normal((ORB_PER_ATOM, ORB_PER_ATOM))
+        B[p] = prng.uniform(-1.0, 1.0, size=(ORB_PER_ATOM, ORB_PER_ATOM)) / ORB_PER_ATOM
     H_pair = (0.8 * np.exp(-r / 1.5))[:, None, None] * R
     S_pair = (0.15 * np.exp(-r / 1.2))[:, None, None] * B
     return System(seed=seed, positions=pos, onsite_H=onsite, pairs=pairs, pair_r=r,

@@ -376,3 +376,69 @@ def test_block_filter_threshold():
     vals[1, 1, 1] = 1e-8                     # exactly eps: kept (strict comparison)
     vals[2] = 0.3
     assert list(O.filter_blocks(vals, 1e-8)) == [False, True, True]
+
+
+# --------------------------------------------------------------- MD-step guess
+def _blocks_dense(vals, pat, nbr, nbc, bm, bn):
+    """Expand block values on a block-CSR pattern into a dense array (test-side loop)."""
+    rp, col = pat
+    A = np.zeros((nbr * bm, nbc * bn))
+    for I in range(nbr):
+        for b in range(rp[I], rp[I + 1]):
+            J = col[b]
+            A[I * bm:(I + 1) * bm, J * bn:(J + 1) * bn] = vals[b]
+    return A
+
+
+def _pattern_mask(pat, nbr, nbc, bm, bn):
+    rp, col = pat
+    return _blocks_dense(np.ones((len(col), bm, bn)), pat, nbr, nbc, bm, bn)
+
+
+def test_md_guess_same_pattern_is_identity(small_system):
+    pat = small_system.w_pattern(4.5)
+    W = np.random.default_rng(0).standard_normal((len(pat[1]), 8, 2))
+    np.testing.assert_array_equal(O.md_guess(W, pat, pat), W)
+
+
+def test_md_guess_extrapolation_is_exact_on_a_straight_line(small_system):
+    """W(t) = A + t B on a fixed pattern: the guess from t = 1 and t = 0 is W(2)."""
+    pat = small_system.w_pattern(4.5)
+    rng = np.random.default_rng(1)
+    A, B = rng.standard_normal((2, len(pat[1]), 8, 2))
+    np.testing.assert_allclose(O.md_guess(A + B, pat, pat, A, pat), A + 2 * B, rtol=1e-14, atol=1e-14)
+    Wd = rng.standard_normal((64, 16))
+    np.testing.assert_allclose(O.md_guess_dense(Wd + 0.5, Wd), Wd + 1.0, rtol=1e-14, atol=1e-14)
+
+
+def test_md_guess_pattern_rules():
+    """Three snapshots of a trajectory whose W pattern changes: in dense terms the
+    guess is mask_new * mask_1 * (2 W1 - W2) -- blocks that left the radius are
+    gone, blocks that entered it are zero, W2's missing blocks count as zero."""
+    import synth
+    snaps = [synth.make_md_system(3, 3, 2, seed=4, t=t, step=0.25) for t in (0.0, 1.0, 2.0)]
+    pats = [s.w_pattern(4.5) for s in snaps]
+    nbr, nbc = snaps[0].natoms, snaps[0].natoms
+    masks = [_pattern_mask(p, nbr, nbc, 8, 2) for p in pats]
+    assert np.any(masks[0] != masks[1]) and np.any(masks[1] != masks[2])
+    assert np.any(masks[1] * (1 - masks[2]) > 0) or np.any(masks[2] * (1 - masks[1]) > 0)
+    rng = np.random.default_rng(2)
+    W0 = rng.standard_normal((len(pats[0][1]), 8, 2))
+    W1 = rng.standard_normal((len(pats[1][1]), 8, 2))
+    d0 = _blocks_dense(W0, pats[0], nbr, nbc, 8, 2)
+    d1 = _blocks_dense(W1, pats[1], nbr, nbc, 8, 2)
+    carried = O.md_guess(W1, pats[1], pats[2])
+    np.testing.assert_array_equal(_blocks_dense(carried, pats[2], nbr, nbc, 8, 2), masks[2] * masks[1] * d1)
+    extra = O.md_guess(W1, pats[1], pats[2], W0, pats[0])
+    np.testing.assert_allclose(_blocks_dense(extra, pats[2], nbr, nbc, 8, 2),
+                               masks[2] * masks[1] * (2.0 * d1 - d0), rtol=0, atol=1e-15)
+
+
+def test_md_system_is_smooth_in_time():
+    """The MD snapshots share seeds per pair: a small time step moves H and S by
+    a small amount (needed for a guess from earlier steps to help)."""
+    import synth
+    a = synth.make_md_system(3, 3, 2, seed=4, t=1.0, step=0.05)
+    b = synth.make_md_system(3, 3, 2, seed=4, t=1.001, step=0.05)
+    assert np.abs(a.dense_H() - b.dense_H()).max() < 1e-3
+    assert np.abs(a.dense_S() - b.dense_S()).max() < 1e-3
