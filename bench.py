@@ -516,6 +516,103 @@ def run_profile(args):
     solver.close()
 
 
+# ---------------------------------------------------------------- MD steps
+def run_md(args):
+    """Successive MD snapshots of a straight-line trajectory (section "C† matrix
+    initialization and update"): each step's solve starts fresh from W0, from
+    the previous step's W carried onto the new pattern, or from the linear
+    extrapolation of the two previous steps (omm_md_guess).  Dense: the C2
+    geometry, mixed precision, one handle per chain.  Sparse: a 6x6x6 system,
+    R_C = 4.5 A, FP64, one handle per snapshot (the W pattern changes)."""
+    import torch
+    from paper_2209_05934_gb300 import omm
+
+    omm.lib()
+    nsteps, step = args.md_steps, args.md_step
+    dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
+    stream = torch.cuda.Stream()
+    launches0 = omm.kernel_launches()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    # ---- dense chains
+    snaps = [synth.make_md_system(*WORKLOAD["dims"], seed=WORKLOAD["seed"], t=float(t), step=step)
+             for t in range(nsteps)]
+    m, n = snaps[0].m, snaps[0].n
+    HS = [(dev(s.dense_H()), dev(s.dense_S())) for s in snaps]
+    W0 = dev(snaps[0].W0_dense())
+    opts = dict(precision=omm.PREC_MIXED, orth_tol=TOL["mixed"]["orth_tol"], stream=stream.cuda_stream)
+    tol = TOL["mixed"]["tol"]
+    warm = omm.Solver(m, n, 8, **opts)       # graphs captured, modules loaded
+    warm.set_HS(*HS[0])
+    warm.solve(W0, tol=tol)
+    warm.close()
+    chains = {"fresh": [omm.Solver(m, n, 8, **opts)], "carried": [omm.Solver(m, n, 8, **opts)],
+              "extrapolated": [omm.Solver(m, n, 8, **opts), omm.Solver(m, n, 8, **opts)]}
+    dense = {k: [] for k in chains}
+    for t in range(nsteps):
+        for mode, hs in chains.items():
+            h = hs[t % len(hs)]
+            h.set_HS(*HS[t])
+            if mode == "fresh" or t == 0:
+                (E, it, st), ms = timed(lambda: h.solve(W0, tol=tol, raise_on_error=False))
+            else:
+                if mode == "extrapolated" and t >= 2:
+                    # h holds W_{t-2}, the other handle W_{t-1}: 2 W_{t-1} - W_{t-2} in place
+                    h.md_guess(hs[(t - 1) % 2], h)
+                elif mode == "extrapolated":
+                    h.md_guess(hs[(t - 1) % 2])
+                (E, it, st), ms = timed(lambda: h.solve(None, tol=tol, raise_on_error=False))
+            dense[mode].append({"t": t, "iters": int(it), "ms": ms, "E": E, "status": int(st)})
+    for hs in chains.values():
+        for h in hs:
+            h.close()
+    del HS
+
+    # ---- sparse chains: one handle per snapshot and chain
+    R_C = 4.5
+    ssnaps = [synth.make_md_system(6, 6, 6, seed=1, t=float(t), step=step) for t in range(nsteps)]
+    sparse = {k: [] for k in ("fresh", "carried", "extrapolated")}
+    guess_ms = []
+    for mode in sparse:
+        prev = []
+        for t, sysm in enumerate(ssnaps):
+            rp, col, Hv, Sv = sysm.bsr()
+            wrp, wcol = sysm.w_pattern(R_C)
+            h = omm.SparseSolver(sysm.m, sysm.n, 8, 2, rp, col, wrp, wcol, stream=stream.cuda_stream,
+                                 max_iter=args.md_max_iter)
+            h.set_HS(Hv, Sv)
+            if mode == "fresh" or t == 0:
+                (E, it, st), ms = timed(lambda: h.solve(sysm.W0_bsr_values(R_C), tol=1e-10, raise_on_error=False))
+            else:
+                g0 = time.perf_counter()
+                h.md_guess(prev[-1], prev[-2] if mode == "extrapolated" and t >= 2 else None)
+                guess_ms.append((time.perf_counter() - g0) * 1e3)
+                (E, it, st), ms = timed(lambda: h.solve(None, tol=1e-10, raise_on_error=False))
+            sparse[mode].append({"t": t, "iters": int(it), "ms": ms, "E": E, "status": int(st),
+                                 "nnzb_W": int(len(wcol))})
+            prev.append(h)
+            if len(prev) > 2:
+                prev.pop(0).close()
+        for h in prev:
+            h.close()
+    print(json.dumps({"md": True, "step_A_per_unit_t": step, "steps": nsteps,
+                      "dense": {"workload": workload_name(snaps[0]) + ", MD snapshots", "precision": "mixed",
+                                "tol": tol, "chains": dense},
+                      "sparse": {"workload": f"localised OMM-CG, 216 atoms (6x6x6), m={ssnaps[0].m}, "
+                                             f"n={ssnaps[0].n}, R_C={R_C} A, MD snapshots",
+                                 "precision": "fp64", "tol": 1e-10, "chains": sparse,
+                                 "md_guess_ms_host_wall": guess_ms},
+                      "gpu_launches": int(omm.kernel_launches() - launches0)}), flush=True)
+
+
 # ---------------------------------------------------------------- C4: batched uneven solves
 def run_c4(args):
     import torch
@@ -684,10 +781,13 @@ def main():
                     help="skip the kinetic-energy preconditioning comparison on H + T")
     ap.add_argument("--cholesky", action="store_true",
                     help="c2: Cholesky-reduced variant (S = L L^T factored inside each step's setup)")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "md"],
                     help="c2 dense workload (default); c3 linear-scaling (with --profile); "
                          "c4 batched uneven solves; c5 serving loop")
     ap.add_argument("--batch", type=int, default=64, help="c4: number of systems")
+    ap.add_argument("--md-steps", type=int, default=5, help="md: snapshots per chain")
+    ap.add_argument("--md-step", type=float, default=0.03, help="md: Angstrom per snapshot per unit velocity")
+    ap.add_argument("--md-max-iter", type=int, default=20000, help="md: CG step cap of the sparse solves")
     ap.add_argument("--sequences", type=int, default=12, help="c5: sequences per arrival rate")
     ap.add_argument("--scf-steps", type=int, default=11, help="c5: solves per sequence (1 + perturbations)")
     ap.add_argument("--rates", type=float, nargs="+", default=[10.0, 50.0, 200.0], help="c5: arrivals per second")
@@ -703,6 +803,9 @@ def main():
         return
     if args.config == "c5":
         run_c5(args)
+        return
+    if args.config == "md":
+        run_md(args)
         return
     if args.impl == "reference":
         run_reference(args)

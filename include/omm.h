@@ -211,6 +211,25 @@ int omm_set_H(omm_handle *h, const double *H, int32_t on_device);
 int omm_set_T(omm_handle *h, const double *T, int32_t on_device);
 
 /*
+ * Initial guess of a new MD step (section "C† matrix initialization and
+ * update"): the resident W of dst (the warm start of its next solve with
+ * W0 == NULL) <- the resident W of prev, the previous MD step's solution,
+ * carried onto dst's localisation pattern, or with prev2 != NULL (the step
+ * before) the linear extrapolation 2 W_prev - W_prev2 (Table 1,
+ * OMM.Extrapolate).  Sparse handles: a W block of dst's pattern that prev does
+ * not hold (its atoms came within R_C) is zero; blocks of prev outside dst's
+ * pattern (atoms moved apart) are dropped; a block prev2 lacks counts as zero
+ * in the extrapolation.  The block maps are merged on the host from the three
+ * handles' patterns and the values gathered on the GPU on dst's stream.  Dense
+ * handles: W elementwise; the Cholesky variant reads and writes W in the
+ * original basis.  dst may be prev or prev2 (dense, or an identical pattern).
+ * Synchronous.  OMM_ERR_ARG: NULL dst or prev, or handles of different form,
+ * sizes or block shapes; OMM_ERR_STATE: a source without a solution, or a
+ * handle with a solve in flight.
+ */
+int omm_md_guess(omm_handle *dst, omm_handle *prev, omm_handle *prev2);
+
+/*
  * Minimise from W0 (m x n column-major; sparse: 8x2-style block values in the
  * W pattern's order) to the RelTol criterion of Table 1:
  *     |2 (E_k - E_{k-1}) / (E_k + E_{k-1})| < tol   at k >= 1,

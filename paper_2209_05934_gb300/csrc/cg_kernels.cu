@@ -393,6 +393,28 @@ __global__ void direction_kernel(int m, int n, const double *__restrict__ G, con
         }
 }
 
+// one element per thread-iteration; every element reads only its own source
+// elements, so Wd may alias W1 or W2 when the maps are the identity
+__global__ void md_guess_kernel(int64_t nblk, int blk, double *Wd, const double *W1, const int64_t *i1,
+                                const double *W2, const int64_t *i2) {
+    const int64_t total = nblk * blk;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / blk, k = e - b * blk;
+        const int64_t a1 = i1 != nullptr ? i1[b] : b;
+        double v = 0.0;
+        if (a1 >= 0) {
+            const double w1 = W1[a1 * blk + k];
+            if (W2 == nullptr) {
+                v = w1;
+            } else {
+                const int64_t a2 = i2 != nullptr ? i2[b] : b;
+                v = fma(2.0, w1, a2 >= 0 ? -W2[a2 * blk + k] : 0.0);   // 2 w1 exact: one rounding
+            }
+        }
+        Wd[e] = v;
+    }
+}
+
 __global__ void shift_kernel(int64_t mm, const double *H, const double *__restrict__ S, double *Hs,
                              const DevState *state) {
     const double eta = state->eta;
@@ -545,6 +567,16 @@ int launch_direction(int64_t m, int64_t n, const double *G, const double *Zg, do
                      const DevState *state, cudaStream_t st, DigitOut dd) {
     dim3 grid((unsigned)ceil_div(m, NT), (unsigned)(n < 1024 ? n : 1024));
     direction_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, G, Zg, Gp, D, state, dd);
+    omm::count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int launch_md_guess(int64_t nblk, int blk, double *Wd, const double *W1, const int64_t *i1, const double *W2,
+                    const int64_t *i2, cudaStream_t st) {
+    int64_t nb = ceil_div(nblk * blk, (int64_t)NT);
+    if (nb > 152 * 8) nb = 152 * 8;
+    md_guess_kernel<<<(unsigned)(nb < 1 ? 1 : nb), NT, 0, st>>>(nblk, blk, Wd, W1, i1, W2, i2);
     omm::count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

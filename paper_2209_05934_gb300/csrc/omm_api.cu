@@ -875,6 +875,29 @@ int dense_set(omm_handle *h, const double *H, const double *S, bool on_device) {
     return OMM_OK;
 }
 
+// Position of every block of `to`'s W pattern in `from`'s W pattern (-1 where
+// `from` has no such block): a merge of the sorted column lists of each row.
+void w_block_map(const omm::sp::Host &to, const omm::sp::Host &from, std::vector<int64_t> &map) {
+    const int64_t nbr = (int64_t)to.Wrp.size() - 1;
+    map.assign((size_t)to.Wrp[nbr], -1);
+    for (int64_t I = 0; I < nbr; ++I) {
+        int64_t a = from.Wrp[I];
+        const int64_t ae = from.Wrp[I + 1];
+        for (int64_t b = to.Wrp[I]; b < to.Wrp[I + 1]; ++b) {
+            while (a < ae && from.Wcol[a] < to.Wcol[b]) ++a;
+            if (a < ae && from.Wcol[a] == to.Wcol[b]) map[b] = a;
+        }
+    }
+}
+
+// Resident W in the original basis (the Cholesky variant keeps it in Wsave)
+double *w_orig(omm_handle *h) {
+    if (h->sparse) return h->sd.W;
+    return h->opt.cholesky ? h->Wsave : h->WD;
+}
+
+bool idle(const omm_handle *h) { return h->phase == PH_IDLE || h->phase == PH_FINISHED; }
+
 }  // namespace
 
 extern "C" {
@@ -1096,6 +1119,50 @@ int omm_set_T(omm_handle *h, const double *T, int32_t on_device) {
     OMM_CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->have_T = true;
     h->precon_left = h->opt.precon > 0 ? h->opt.precon : 0;
+    return OMM_OK;
+}
+
+int omm_md_guess(omm_handle *dst, omm_handle *prev, omm_handle *prev2) {
+    if (dst == nullptr || prev == nullptr) return OMM_ERR_ARG;
+    for (omm_handle *x : {prev, prev2}) {
+        if (x == nullptr) continue;
+        if (x->sparse != dst->sparse || x->m != dst->m || x->n != dst->n) return OMM_ERR_ARG;
+        if (x->sparse && (x->sd.bm != dst->sd.bm || x->sd.bn != dst->sd.bn || x->sd.nbr != dst->sd.nbr ||
+                          x->sd.nbc != dst->sd.nbc))
+            return OMM_ERR_ARG;
+        if (!x->have_W || !idle(x)) return OMM_ERR_STATE;
+    }
+    if (!idle(dst)) return OMM_ERR_STATE;
+    // the sources' W are complete: their last writes were on their own streams
+    OMM_CUDA_TRY(cudaStreamSynchronize(prev->stream));
+    if (prev2 != nullptr) OMM_CUDA_TRY(cudaStreamSynchronize(prev2->stream));
+    cudaStream_t st = dst->stream;
+    const double *W1 = w_orig(prev), *W2 = prev2 != nullptr ? w_orig(prev2) : nullptr;
+    int rc = OMM_OK;
+    if (!dst->sparse) {
+        rc = omm::launch_md_guess(dst->m * dst->n, 1, w_orig(dst), W1, nullptr, W2, nullptr, st);
+        if (rc == OMM_OK) OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        // index maps of dst's W blocks in the sources' patterns, uploaded for the gather
+        std::vector<int64_t> map1, map2;
+        w_block_map(dst->sh, prev->sh, map1);
+        if (prev2 != nullptr) w_block_map(dst->sh, prev2->sh, map2);
+        const int64_t nnz = dst->sd.nnzW, blk = (int64_t)dst->sd.bm * dst->sd.bn;
+        int64_t *dmap = nullptr;
+        TRY(dalloc(&dmap, (size_t)(2 * nnz)));
+        if (cudaMemcpyAsync(dmap, map1.data(), nnz * sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            (prev2 != nullptr && cudaMemcpyAsync(dmap + nnz, map2.data(), nnz * sizeof(int64_t),
+                                                 cudaMemcpyHostToDevice, st) != cudaSuccess))
+            rc = OMM_ERR_CUDA;
+        if (rc == OMM_OK)
+            rc = omm::launch_md_guess(nnz, (int)blk, dst->sd.W, W1, dmap, W2, prev2 != nullptr ? dmap + nnz : nullptr,
+                                      st);
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == OMM_OK) rc = OMM_ERR_CUDA;
+        cudaFree(dmap);
+    }
+    if (rc != OMM_OK) return rc;
+    dst->have_W = true;
+    dst->solved = false;
     return OMM_OK;
 }
 

@@ -108,6 +108,12 @@ int launch_dots_beta(int64_t mn, const double *G, const double *Zg, const double
 int launch_direction(int64_t m, int64_t n, const double *G, const double *Zg, double *Gp, double *D,
                      const DevState *state, cudaStream_t st, DigitOut dd = DigitOut{nullptr, 0, 0});
 
+// MD-step guess: Wd block b <- W1 block i1[b], or 2 W1[i1[b]] - W2[i2[b]] with
+// W2 given (a negative index reads zero; i1[b] < 0 makes the block zero).
+// Blocks of blk doubles; i1 = i2 = nullptr means the identity map.
+int launch_md_guess(int64_t nblk, int blk, double *Wd, const double *W1, const int64_t *i1, const double *W2,
+                    const int64_t *i2, cudaStream_t st);
+
 // H' = H - eta S (dense, m x m), eta read from state
 int launch_shift(int64_t mm, const double *H, const double *S, double *Hs, const DevState *state,
                  cudaStream_t st);

@@ -60,6 +60,7 @@ _SIGS = {
     "omm_set_HS": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "omm_set_H": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "omm_set_T": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "omm_md_guess": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "omm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
                             C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "omm_get_diag": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
@@ -231,6 +232,12 @@ class Solver:
         pT, dT = _ptr(T)
         return check(lib().omm_set_T(self._h, pT, dT), "omm_set_T")
 
+    def md_guess(self, prev, prev2=None):
+        """Resident W <- prev's solution carried onto this handle's pattern, or the
+        linear extrapolation 2 W_prev - W_prev2; see omm_md_guess."""
+        return check(lib().omm_md_guess(self._h, prev._h, prev2._h if prev2 is not None else None),
+                     "omm_md_guess")
+
     def solve(self, W0=None, tol: float = 1e-10, W_out=None, raise_on_error=True):
         if W0 is not None:
             _check_colmajor(W0, self.m, self.n, "W0")
@@ -324,6 +331,7 @@ class SparseSolver:
     end = Solver.end
     set_profiling = Solver.set_profiling
     stage_times = Solver.stage_times
+    md_guess = Solver.md_guess
 
     def set_HS(self, Hv, Sv):
         for a, name in ((Hv, "H"), (Sv, "S")):
