@@ -41,12 +41,9 @@ struct MixedBufs {
     int64_t ldm = 0, ld2n = 0;
     __nv_bfloat16 *HSd = nullptr, *WDd = nullptr, *HDSDd = nullptr, *SWHWd = nullptr, *HSWd = nullptr;
     CUtensorMap mapHS_A, mapWD_A, mapWD_B, mapHDSD_B, mapSWHW_A, mapHSW_B;
-    // B operands again with 128-row boxes: the two-CTA multicast form of the split
-    // GEMM loads half of a 256-row B tile per CTA (mapWD_A serves WDd)
-    CUtensorMap mapHDSD_Bh, mapHSW_Bh;
     float *HDSD32 = nullptr, *Z32 = nullptr, *G32 = nullptr, *Gp32 = nullptr, *D32 = nullptr;
     __nv_bfloat16 *Pd = nullptr, *Gd = nullptr;
-    CUtensorMap mapP_A, mapG_B, mapG_Bh;
+    CUtensorMap mapP_A, mapG_B;
     float *PG32 = nullptr;
 };
 
@@ -367,8 +364,6 @@ int mixed_alloc(omm_handle *h) {
     TRY(omm::tc::make_digit_map(&x.mapHDSD_B, x.HDSDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, kBN, kBK));
     TRY(omm::tc::make_digit_map(&x.mapSWHW_A, x.SWHWd, 2 * n, m, x.ld2n, m * x.ld2n, kDig, 128, kBK));
     TRY(omm::tc::make_digit_map(&x.mapHSW_B, x.HSWd, 2 * n, n, x.ld2n, n * x.ld2n, kDig, kBN, kBK));
-    TRY(omm::tc::make_digit_map(&x.mapHDSD_Bh, x.HDSDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, kBN / 2, kBK));
-    TRY(omm::tc::make_digit_map(&x.mapHSW_Bh, x.HSWd, 2 * n, n, x.ld2n, n * x.ld2n, kDig, kBN / 2, kBK));
     return OMM_OK;
 }
 
@@ -423,8 +418,8 @@ int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_s
     a.dplane = 2 * n * x.ldm;
     a.dout_step = dout_step * x.ldm;
     a.ndig = h->cur_dig;
-    if (!s_identity(h)) return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, kBN, h->stream, &x.mapWD_A);
-    TRY(omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 1, kBN, h->stream, &x.mapWD_A));
+    if (!s_identity(h)) return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, kBN, h->stream);
+    TRY(omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 1, kBN, h->stream));
     // z = 1 (S times the B rows) is the B rows themselves: their FP32/FP64 values and digits
     const int64_t mn = m * n;
     if (C32 != nullptr)   // iteration: S D = D
@@ -446,7 +441,7 @@ int split_contract(omm_handle *h) {
     omm::tc::TcArgs a = tc_args(h, (int)(2 * n), (int)(2 * n), (int)m);
     a.C32 = x.Z32;
     a.ldc = 2 * n;
-    return omm::tc::gemm(x.mapWD_A, x.mapHDSD_B, a, 1, kBN, h->stream, &x.mapHDSD_Bh);
+    return omm::tc::gemm(x.mapWD_A, x.mapHDSD_B, a, 1, kBN, h->stream);
 }
 
 // G = 4 H'W - 2 [SW H'W][H_W ; S_W]
@@ -460,7 +455,7 @@ int split_gradient(omm_handle *h) {
     a.ldcin = m;
     a.C32 = x.G32;
     a.ldc = m;
-    return omm::tc::gemm(x.mapSWHW_A, x.mapHSW_B, a, 1, kBN, h->stream, &x.mapHSW_Bh);
+    return omm::tc::gemm(x.mapSWHW_A, x.mapHSW_B, a, 1, kBN, h->stream);
 }
 
 // FP64 gradient (CUDA cores), rounded to the FP32 gradient of the mixed form
@@ -596,7 +591,7 @@ int mixed_direction(omm_handle *h, int first) {
         omm::tc::TcArgs a = tc_args(h, (int)m, (int)n, (int)m);
         a.C32 = x.PG32;
         a.ldc = m;
-        TRY(omm::tc::gemm(x.mapP_A, x.mapG_B, a, 1, kBN, h->stream, &x.mapG_Bh));
+        TRY(omm::tc::gemm(x.mapP_A, x.mapG_B, a, 1, kBN, h->stream));
         Zg = x.PG32;
     }
     StageTimer t(h, OMM_STAGE_DIRECTION);
@@ -620,7 +615,7 @@ int mixed_start(omm_handle *h) {
         a.C = h->h0s0;
         a.ldc = 2 * n;
         a.c_step = n;             // H_W in rows [0, n), S_W in rows [n, 2n)
-        TRY(omm::tc::gemm(h->mx.mapWD_A, h->mx.mapHDSD_B, a, 2, kBN, st, &h->mx.mapHDSD_Bh));
+        TRY(omm::tc::gemm(h->mx.mapWD_A, h->mx.mapHDSD_B, a, 2, kBN, st));
     }
     TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
                                      ctr(h, 1), s, 1, st));
@@ -787,7 +782,6 @@ int precon_alloc(omm_handle *h) {
         TRY(dalloc(&x.PG32, (size_t)(m * n)));
         TRY(omm::tc::make_digit_map(&x.mapP_A, x.Pd, m, m, x.ldm, m * x.ldm, kDig, 128, kBK));
         TRY(omm::tc::make_digit_map(&x.mapG_B, x.Gd, m, n, x.ldm, n * x.ldm, kDig, kBN, kBK));
-        TRY(omm::tc::make_digit_map(&x.mapG_Bh, x.Gd, m, n, x.ldm, n * x.ldm, kDig, kBN / 2, kBK));
     }
     return OMM_OK;
 }

@@ -22,15 +22,6 @@
 // in FP64 (column-major), optionally with the BF16 digits of C as well.
 // Every mbarrier wait is bounded; on timeout the kernel records an error and
 // unwinds (tensor memory is always released).
-//
-// Cluster form (CL = 2): the two CTAs of a cluster take vertically adjacent
-// tiles (the same BN columns), so they need the same B tile.  Each loads one
-// half of it with a multicast TMA into both CTAs' shared memory, which halves
-// the B traffic from L2 per CTA (B is the larger operand of a 128 x 256 tile);
-// a stage is reused only after both CTAs' MMAs have released it (each MMA
-// commit arrives on both CTAs' empty barriers), and neither CTA exits before
-// the other has drained its stages.  The MMAs and their order are unchanged,
-// so the results equal the single-CTA form bit for bit.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -56,11 +47,10 @@ __device__ __forceinline__ void split3(double v, __nv_bfloat16 &d1, __nv_bfloat1
 }
 
 // ------------------------------------------------------------------ the GEMM kernel
-template <int BN, int STAGES, int BKT, int CL>
+template <int BN, int STAGES, int BKT>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const TcArgs args) {
-    // (the done flag was written by earlier kernels of the stream: both CTAs of a cluster see the same value)
     if (args.state != nullptr && *((volatile const int *)&args.state->done)) return;
     const int z = blockIdx.z;
     const int nA = args.nA, nB = args.nB;
@@ -86,7 +76,7 @@ __global__ void __launch_bounds__(192, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], CL);   // released by the MMAs of every CTA of the cluster
+            mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&acc_bar, 1);
         abort_flag = 0;
@@ -101,41 +91,21 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    if constexpr (CL > 1) cluster_sync();   // the peer's barriers exist before any multicast reaches them
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
         const int a_row = args.a_row0 + z * args.a_row_step + m0;
         const int b_row = args.b_row0 + z * args.b_row_step + n0;
-        const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
-        bool ok = true;
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-            if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, args.err)) { ok = false; break; }
-            // the full stage arrives here: own A, both halves of B
+            if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, args.err)) break;
             mbar_arrive_expect_tx(&full_bar[s], (uint32_t)stage_bytes);
             uint8_t *st = smem + s * stage_bytes;
             for (int p = 0; p < nA; ++p)
                 tma_load_3d(st + p * TILE_A, &mapA, kb * BKT, a_row, p, &full_bar[s]);
-            for (int q = 0; q < nB; ++q) {
-                if constexpr (CL == 1)
-                    tma_load_3d(st + nA * TILE_A + q * tileB, &mapB, kb * BKT, b_row, q, &full_bar[s]);
-                else   // this CTA's share of the B rows (mapB's box is BN / CL rows), to every CTA
-                    tma_load_3d_mc(st + nA * TILE_A + q * tileB + rank * (tileB / CL), &mapB, kb * BKT,
-                                   b_row + rank * (BN / CL), q, &full_bar[s], kMask);
-            }
-        }
-        if constexpr (CL > 1) {
-            // drain: the last use of every stage released by both CTAs, so no MMA
-            // commit of the peer still targets this CTA's barriers when it exits
-            for (int kb = nkb; ok && kb < nkb + STAGES; ++kb) {
-                if (kb - STAGES < 0) continue;
-                const int s = kb % STAGES;
-                const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-                if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, args.err)) ok = false;
-            }
+            for (int q = 0; q < nB; ++q)
+                tma_load_3d(st + nA * TILE_A + q * tileB, &mapB, kb * BKT, b_row, q, &full_bar[s]);
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
@@ -166,10 +136,7 @@ __global__ void __launch_bounds__(192, 1)
                     written |= 1u << acc;
                 }
             }
-            if constexpr (CL == 1)
-                umma_commit(&empty_bar[s]);
-            else
-                umma_commit_mc(&empty_bar[s], kMask);
+            umma_commit(&empty_bar[s]);
         }
         umma_commit(&acc_bar);
     } else if (warp >= 2) {
@@ -291,7 +258,6 @@ __global__ void __launch_bounds__(192, 1)
         tc_fence_after();
         tmem_dealloc(tmem, tmem_cols);
     }
-    if constexpr (CL > 1) cluster_sync();   // neither CTA leaves while the other may still signal it
 }
 
 // ------------------------------------------------------------------ digit packing
@@ -357,12 +323,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int BN, int STAGES, int BKT, int CL = 1>
+template <int BN, int STAGES, int BKT>
 int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int nbatch, cudaStream_t st) {
     const int smem = STAGES * (a.nA * BM * BKT * 2 + a.nB * BN * BKT * 2) + 1024;
     static int attr_bytes = 0;
     if (smem > attr_bytes) {
-        OMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, BKT, CL>,
+        OMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, BKT>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_bytes = smem;
     }
@@ -376,27 +342,8 @@ int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int
     int kacc = 512 / (BN * b.ncls);
     while (kacc > 1 && kacc > nkb) kacc >>= 1;
     b.kacc = kacc;
-    // M tiles rounded up to whole clusters; a CTA past M loads (zero-filled or
-    // unused rows) and computes like the others and stores nothing
-    const int64_t mt = ceil_div(ceil_div(a.M, BM), CL) * CL;
-    dim3 grid((unsigned)ceil_div(a.N, BN), (unsigned)mt, (unsigned)nbatch);
-    if constexpr (CL == 1) {
-        tc_gemm_kernel<BN, STAGES, BKT, 1><<<grid, 192, smem, st>>>(ma, mb, b);
-    } else {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = grid;
-        cfg.blockDim = dim3(192, 1, 1);
-        cfg.dynamicSmemBytes = (size_t)smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 1;
-        attr[0].val.clusterDim.y = CL;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        OMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, STAGES, BKT, CL>, ma, mb, b));
-    }
+    dim3 grid((unsigned)ceil_div(a.N, BN), (unsigned)ceil_div(a.M, BM), (unsigned)nbatch);
+    tc_gemm_kernel<BN, STAGES, BKT><<<grid, 192, smem, st>>>(ma, mb, b);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
@@ -429,16 +376,13 @@ int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64
 }
 
 int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int nbatch, int bn,
-         cudaStream_t st, const CUtensorMap *mapBhalf) {
+         cudaStream_t st) {
     if (a.M <= 0 || a.N <= 0 || a.K < 0 || a.nA < 1 || a.nA > 3 || a.nB < 1 || a.nB > 3) return OMM_ERR_ARG;
     if (a.npairs < 1 || a.npairs > 9 || nbatch < 1) return OMM_ERR_ARG;
     for (int p = 0; p < a.npairs; ++p)
         if (a.pa[p] >= a.nA || a.pb[p] >= a.nB) return OMM_ERR_ARG;
     // The tensor maps decide the K-block width: 64 (128-byte swizzle) or 32 (64-byte).
     if (a.bk == 32) {
-        // 128 x 256 tiles: pairs of vertically adjacent tiles share B by multicast
-        // when the caller provides B's map with half-height (128-row) boxes
-        if (bn == 256 && mapBhalf != nullptr) return launch_tc<256, 3, 32, 2>(mapA, *mapBhalf, a, nbatch, st);
         if (bn == 256) return launch_tc<256, 3, 32>(mapA, mapB, a, nbatch, st);
         if (a.nA + a.nB <= 4) return launch_tc<128, 6, 32>(mapA, mapB, a, nbatch, st);
         return launch_tc<128, 4, 32>(mapA, mapB, a, nbatch, st);
@@ -529,9 +473,6 @@ extern "C" int omm_op_split_gemm(int32_t transA, int32_t transB, int64_t M, int6
     if ((rc = tc::make_digit_map(&ma, Ad, K, M, ldk, M * ldk, ndigits, 128, bk))) return rc;
     const int bn = N > 128 ? 256 : 128;
     if ((rc = tc::make_digit_map(&mb, Bd, K, N, ldk, N * ldk, ndigits, bn, bk))) return rc;
-    CUtensorMap mbh;   // 128-row boxes of B: the two-CTA multicast form (256-wide tiles, bk 32)
-    const bool half = bn == 256 && bk == 32;
-    if (half && (rc = tc::make_digit_map(&mbh, Bd, K, N, ldk, N * ldk, ndigits, 128, bk))) return rc;
     tc::TcArgs a{};
     tc::pairs_for_digits(ndigits, a);
     a.bk = bk;
@@ -545,5 +486,5 @@ extern "C" int omm_op_split_gemm(int32_t transA, int32_t transB, int64_t M, int6
     a.C = C;
     a.ldc = ldc;
     a.err = nullptr;
-    return tc::gemm(ma, mb, a, 1, bn, st, half ? &mbh : nullptr);
+    return tc::gemm(ma, mb, a, 1, bn, st);
 }

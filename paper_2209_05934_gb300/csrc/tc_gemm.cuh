@@ -38,10 +38,8 @@ struct TcArgs {
 
 int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
                    int64_t plane_elems, int nplanes, int box_rows, int bk = 64);
-// mapBhalf (optional, bk 32 and bn 256): B's map with 128-row boxes, which
-// selects the two-CTA cluster form that multicasts the B tile
 int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int nbatch, int bn,
-         cudaStream_t st, const CUtensorMap *mapBhalf = nullptr);
+         cudaStream_t st);
 int pack_cm(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,
             int64_t plane, int ndig, const DevState *state, cudaStream_t st);
 int pack_t(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,

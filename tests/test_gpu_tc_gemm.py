@@ -39,9 +39,6 @@ def run_split(omm, tA, tB, M, N, K, nd, A, B, alpha=1.0, beta=0.0, Cin=None):
 REL = {3: 1e-5, 2: 1e-4, 1: 2e-2}
 
 
-# N > 128 with two or three digits takes the two-CTA multicast form (256-wide
-# tiles, pairs of vertically adjacent tiles); an odd number of 128-row tiles
-# (M = 300, 640) adds a cluster partner past M that computes but stores nothing
 @pytest.mark.parametrize("tA,tB,M,N,K", [(0, 0, 256, 128, 256), (1, 0, 100, 70, 33), (0, 1, 300, 200, 520),
                                          (1, 1, 129, 257, 64), (0, 0, 128, 128, 4096), (1, 0, 16, 8, 8),
                                          (0, 0, 640, 520, 1544)])
