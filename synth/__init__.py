@@ -323,6 +323,27 @@ def make_md_system(nx: int, ny: int | None = None, nz: int | None = None, seed: 
                   H_pair=H_pair, S_pair=S_pair)
 
 
+def make_dense_gapped(m: int, n: int, seed: int):
+    """Generic dense inputs of any size (the ragged-size cases, m not a multiple
+    of the block or tile sizes): H = Q diag(lam) Q^T with n eigenvalues
+    U(-6, -3) and m - n eigenvalues U(3, 8) eV, Q the Q factor of an N(0,1)
+    matrix; S = I + (A + A^T)/2 with A ~ N(0, 0.15/m) (strictly diagonally
+    dominant, SPD); T = I + (B B^T)/m with B ~ N(0,1) (SPD); W0 ~ N(0, 1/sqrt(m)).
+    One PCG64 stream seeded with `seed`, drawn in that order.  Returns
+    (H, S, T, W0) as Fortran-ordered arrays."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    lam = np.concatenate([rng.uniform(-6.0, -3.0, n), rng.uniform(3.0, 8.0, m - n)])
+    H = (Q * lam) @ Q.T
+    H = 0.5 * (H + H.T)
+    A = rng.normal(0.0, 0.15 / m, size=(m, m))
+    S = np.eye(m) + 0.5 * (A + A.T)
+    B = rng.standard_normal((m, m))
+    T = np.eye(m) + (B @ B.T) / m
+    W0 = rng.normal(0.0, 1.0 / math.sqrt(m), size=(m, n))
+    return tuple(np.asfortranarray(x) for x in (H, S, T, W0))
+
+
 def batch_sizes(count: int, seed: int, lo: int = 32, hi: int = 384) -> np.ndarray:
     """Atom counts for a batch of uneven systems: round(exp(U(ln lo, ln hi)))."""
     rng = np.random.Generator(np.random.PCG64(seed))
