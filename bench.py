@@ -124,11 +124,13 @@ def dist_env():
 
 
 def barrier_max(value: float, ws: int):
+    """Max of a per-rank value over the job (NCCL on the GPUs, gloo on host tensors)."""
     if ws == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
