@@ -353,6 +353,18 @@ int omm_get_stage_times(omm_handle *h, double *ms, int64_t *launches, int32_t ns
 /* Total number of CUDA kernels this library has launched in the process. */
 int64_t omm_kernel_launches(void);
 
+/*
+ * Self-test of the bounded waits.  Every mbarrier wait in the tensor-core
+ * kernels gives up at a deadline, records the timeout and unwinds, so that a
+ * lost signal ends in OMM_ERR_TIMEOUT from the solve instead of a hung GPU.
+ * This call runs one such wait on a barrier that nothing completes, limited
+ * to limit_ns (1e3 .. 1e10 ns), on `stream`, and waits for it:
+ * *status_out = OMM_ERR_TIMEOUT when the wait gave up (the expected outcome),
+ * OMM_OK if the barrier completed.  The CUDA context stays usable.
+ * Returns OMM_ERR_ARG for a limit out of range or a NULL status_out.
+ */
+int omm_selftest_bounded_wait(int64_t limit_ns, int32_t *status_out, void *stream);
+
 /* ------------------------------------------------------------------------
  * Op-level entry points: single steps of the hot path on caller-owned device
  * memory, enqueued on `stream`, asynchronous.  They allocate nothing.

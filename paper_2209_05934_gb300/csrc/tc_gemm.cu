@@ -260,6 +260,25 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+// ------------------------------------------------------------------ bounded-wait self-test
+// One mbarrier wait that nothing completes, through the same bounded wait as
+// the GEMM kernels' pipelines: it must give up at the deadline and report it.
+__global__ void wait_probe_kernel(uint64_t limit_ns, int *err, int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t deadline = globaltimer_ns() + limit_ns;
+        const bool ok = mbar_wait(&bar, 0u, deadline, &abort_flag, err);   // phase 0 never completes
+        *status = ok ? OMM_OK : OMM_ERR_TIMEOUT;
+    }
+}
+
 // ------------------------------------------------------------------ digit packing
 // column-major source (rows x cols, ld_src) -> planes [ndig][cols][ldd], element
 // (i, j) at j*ldd + i (the K-major layout when K runs along the rows).
@@ -435,6 +454,29 @@ void pairs_for_digits(int ndig, TcArgs &a) {
 }  // namespace omm
 
 // ---------------------------------------------------------------- op-level entry
+extern "C" int omm_selftest_bounded_wait(int64_t limit_ns, int32_t *status_out, void *stream) {
+    using namespace omm;
+    if (status_out == nullptr || limit_ns < 1000 || limit_ns > 10000000000ll) return OMM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *d = nullptr;   // [0] error flag, [1] status
+    OMM_CUDA_TRY(cudaMalloc(&d, 2 * sizeof(int)));
+    int h[2] = {0, OMM_ERR_STATE};
+    int rc = OMM_OK;
+    if (cudaMemcpyAsync(d, h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = OMM_ERR_CUDA;
+    if (rc == OMM_OK) {
+        tc::wait_probe_kernel<<<1, 32, 0, st>>>((uint64_t)limit_ns, d, d + 1);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = OMM_ERR_CUDA;
+    }
+    cudaFree(d);
+    if (rc != OMM_OK) return rc;
+    *status_out = h[1];
+    return OMM_OK;
+}
+
 extern "C" int64_t omm_op_split_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int32_t ndigits) {
     if (M < 0 || N < 0 || K < 0 || ndigits < 1 || ndigits > 3) return -1;
     const int64_t ldk = (K + 7) / 8 * 8;

@@ -61,6 +61,7 @@ _SIGS = {
     "omm_set_H": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "omm_set_T": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "omm_md_guess": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "omm_selftest_bounded_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), C.c_void_p]),
     "omm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
                             C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "omm_get_diag": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
@@ -175,6 +176,15 @@ def _check_colmajor(x, rows, cols, name):
             raise ValueError(f"{name}: shape {x.shape} != {(rows, cols)}")
         if not x.flags["F_CONTIGUOUS"] or x.dtype != np.float64:
             raise ValueError(f"{name}: must be a float64 Fortran-ordered array")
+
+
+def selftest_bounded_wait(limit_ns: int, stream=None) -> int:
+    """Run one bounded mbarrier wait that nothing completes; returns its status
+    (ERR_TIMEOUT expected); see omm_selftest_bounded_wait."""
+    st = C.c_int32(0)
+    check(lib().omm_selftest_bounded_wait(int(limit_ns), C.byref(st), C.c_void_p(stream) if stream else None),
+          "omm_selftest_bounded_wait")
+    return st.value
 
 
 def default_options(**kw) -> Options:

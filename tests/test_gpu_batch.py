@@ -116,3 +116,23 @@ def test_graph_replay_equals_eager(omm, prec):
         s.close()
     assert runs[0][0] == runs[1][0]
     np.testing.assert_array_equal(runs[0][1], runs[1][1])
+
+
+def test_bounded_wait_gives_up_and_context_survives(omm):
+    """A wait that nothing completes ends in OMM_ERR_TIMEOUT at its limit (the
+    deadline mechanism of every tcgen05 pipeline wait); a solve runs afterwards."""
+    import time
+    t0 = time.perf_counter()
+    st = omm.selftest_bounded_wait(50_000_000)          # 50 ms
+    elapsed = time.perf_counter() - t0
+    assert st == omm.ERR_TIMEOUT
+    assert 0.045 <= elapsed < 5.0
+    with pytest.raises(omm.OmmError):
+        omm.selftest_bounded_wait(10)                   # limit out of range
+    import synth
+    sysm = synth.make_system(2, 2, 2, seed=0)
+    s = omm.Solver(sysm.m, sysm.n, 8, precision=omm.PREC_MIXED)
+    s.set_HS(np.asfortranarray(sysm.dense_H()), np.asfortranarray(sysm.dense_S()))
+    E, it, status = s.solve(np.asfortranarray(sysm.W0_dense()), tol=1e-10)
+    assert status == omm.OK
+    s.close()
