@@ -537,17 +537,22 @@ int exact_gradient(omm_handle *h) {
 }
 
 // Refinement start with exact-digit products: H'W, SW, H_W, S_W, energy, G, D.
+// Six digits (21 pair products instead of 28; ~2^-41 of |A||B|) anchor the
+// state far below what the refinement's RelTol and orthonormality bars can
+// see; H' and S keep their seven-digit planes, of which the first six are read.
 int exact_anchor(omm_handle *h) {
     const int64_t m = h->m, n = h->n, mn = m * n;
     const MixedBufs &x = h->mx;
     ExactBufs &e = h->ex;
     cudaStream_t st = h->stream;
     omm::DevState *s = h->dstate;
+    const int sa = e.s < 6 ? e.s : 6;
     {
         StageTimer t(h, OMM_STAGE_ANCHOR);
-        TRY(omm::tc::exact_pack(true, m, n, h->WD, m, e.eW, e.Wx, x.ldm, n * x.ldm, e.s, s, st));
+        TRY(omm::tc::exact_pack(true, m, n, h->WD, m, e.eW, e.Wx, x.ldm, n * x.ldm, sa, s, st));
         // z = 0: H'W -> SWHW + mn;  z = 1: SW -> SWHW
         omm::tc::ExactArgs a = exact_args(h, (int)m, (int)n, (int)m);
+        omm::tc::exact_pairs(sa, a);
         a.a_row_step = (int)m;
         a.C = h->SWHW + mn;
         a.ldc = m;
@@ -558,11 +563,12 @@ int exact_anchor(omm_handle *h) {
         TRY(omm::tc::exact_gemm(e.mapHS_A, e.mapW, a, s_identity(h) ? 1 : 2, st));
         if (s_identity(h))
             OMM_CUDA_TRY(cudaMemcpyAsync(h->SWHW, h->WD, mn * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        TRY(omm::tc::exact_pack(true, m, n, h->SWHW + mn, m, e.eHWSW, e.HWSWx, x.ldm, 2 * n * x.ldm, e.s, s, st));
-        TRY(omm::tc::exact_pack(true, m, n, h->SWHW, m, e.eHWSW + n, e.HWSWx + n * x.ldm, x.ldm, 2 * n * x.ldm, e.s,
+        TRY(omm::tc::exact_pack(true, m, n, h->SWHW + mn, m, e.eHWSW, e.HWSWx, x.ldm, 2 * n * x.ldm, sa, s, st));
+        TRY(omm::tc::exact_pack(true, m, n, h->SWHW, m, e.eHWSW + n, e.HWSWx + n * x.ldm, x.ldm, 2 * n * x.ldm, sa,
                                 s, st));
         // z = 0: H_W = W^T H'W -> rows [0, n) of h0s0;  z = 1: S_W -> rows [n, 2n)
         omm::tc::ExactArgs b = exact_args(h, (int)n, (int)n, (int)m);
+        omm::tc::exact_pairs(sa, b);
         b.b_row_step = (int)n;
         b.C = h->h0s0;
         b.ldc = 2 * n;
