@@ -539,7 +539,7 @@ int exact_gradient(omm_handle *h) {
 // Refinement start with exact-digit products: H'W, SW, H_W, S_W, energy, G, D.
 // Six digits (21 pair products instead of 28; ~2^-41 of |A||B|) anchor the
 // state far below what the refinement's RelTol and orthonormality bars can
-// see; H' and S keep their seven-digit planes, of which the first six are read.
+// see; omm_set_HS packs six digits of H' and S for it.
 int exact_anchor(omm_handle *h) {
     const int64_t m = h->m, n = h->n, mn = m * n;
     const MixedBufs &x = h->mx;
@@ -863,9 +863,10 @@ int dense_set(omm_handle *h, const double *H, const double *S, bool on_device) {
         StageTimer t(h, OMM_STAGE_PACK);
         const int64_t cols = (S == nullptr || s_identity(h)) ? m : 2 * m;
         TRY(omm::tc::pack_cm(m, cols, h->HS, m, h->mx.HSd, h->mx.ldm, 2 * m * h->mx.ldm, kDig, nullptr, st));
+        // the re-anchor reads six digits of H' and S (see exact_anchor)
         if (h->opt.refine == OMM_REFINE_EXACT)
             TRY(omm::tc::exact_pack(true, m, cols, h->HS, m, h->ex.eHS, h->ex.HSx, h->mx.ldm, 2 * m * h->mx.ldm,
-                                    h->ex.s, nullptr, st));
+                                    h->ex.s < 6 ? h->ex.s : 6, nullptr, st));
     }
     OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
