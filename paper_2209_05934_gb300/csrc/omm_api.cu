@@ -862,7 +862,9 @@ int dense_set(omm_handle *h, const double *H, const double *S, bool on_device) {
         // omm_set_H and the Cholesky variant's S = I repack H' only
         StageTimer t(h, OMM_STAGE_PACK);
         const int64_t cols = (S == nullptr || s_identity(h)) ? m : 2 * m;
-        TRY(omm::tc::pack_cm(m, cols, h->HS, m, h->mx.HSd, h->mx.ldm, 2 * m * h->mx.ldm, kDig, nullptr, st));
+        // the split products of both phases read split_digits planes
+        TRY(omm::tc::pack_cm(m, cols, h->HS, m, h->mx.HSd, h->mx.ldm, 2 * m * h->mx.ldm, h->opt.split_digits, nullptr,
+                             st));
         // the re-anchor reads six digits of H' and S (see exact_anchor)
         if (h->opt.refine == OMM_REFINE_EXACT)
             TRY(omm::tc::exact_pack(true, m, cols, h->HS, m, h->ex.eHS, h->ex.HSx, h->mx.ldm, 2 * m * h->mx.ldm,
