@@ -190,6 +190,10 @@ def selftest_bounded_wait(limit_ns: int, stream=None) -> int:
 def default_options(**kw) -> Options:
     o = Options()
     lib().omm_default_options(C.byref(o))
+    known = {name for name, _ in Options._fields_}
+    unknown = sorted(set(kw) - known)
+    if unknown:
+        raise TypeError(f"unknown omm option(s) {unknown}; known: {sorted(known)}")
     for k, v in kw.items():
         if k == "stream":
             v = C.c_void_p(v) if v is not None else None

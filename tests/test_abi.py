@@ -56,3 +56,12 @@ def test_argument_errors_without_gpu(built):
     assert built.omm_solve(None, None, 0, 1e-10, None, 0, None, None) == omm.ERR_ARG
     assert omm.op_dgemm(0, 0, -1, 2, 2, 1.0, None, 1, None, 1, 0.0, None, 1, None, 1) == omm.ERR_ARG
     assert omm.op_line_min(None, None, None) == omm.ERR_ARG
+
+
+def test_options_reject_unknown_names(built):
+    """Option names are checked against the C struct (a misspelt option must not pass silently)."""
+    from paper_2209_05934_gb300 import omm
+    o = omm.default_options(precon=-1, tau_T=5.0, split_digits=3)
+    assert (o.precon, o.tau_T, o.split_digits, o.graphs) == (-1, 5.0, 3, 1)
+    with pytest.raises(TypeError):
+        omm.default_options(precond=-1)
