@@ -120,7 +120,10 @@ typedef struct {
                               (eta_auto = 0; the Gershgorin bound lies above the spectrum).
                               Start from small coefficients (the functional is unbounded
                               along unoccupied directions beyond a barrier near unit norm) and
-                              leave orth_tol at 0: S_W converges to diag(I, 0).  0 (default):
+                              leave orth_tol at 0: S_W converges to diag(I, 0).  With the
+                              mixed form take split_digits = 3: two-digit increments (~1e-5
+                              relative error) can carry an iterate across that barrier, after
+                              which the solve ends in OMM_ERR_NONFINITE.  0 (default):
                               n_occupied = n */
     int32_t precon;        /* kinetic-energy preconditioning (Eq. 6; dense handles only, not
                               with the Cholesky variant): the CG gradient G is multiplied by

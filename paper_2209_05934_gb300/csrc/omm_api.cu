@@ -39,6 +39,7 @@
 // operand and Gd [3][n][ldm] columns of G as the B operand of P G -> PG32 (m x n).
 struct MixedBufs {
     int64_t ldm = 0, ld2n = 0;
+    int bk = 32;   // K-block width of the split products: 64 (128-byte swizzle) with two digits, else 32
     __nv_bfloat16 *HSd = nullptr, *WDd = nullptr, *HDSDd = nullptr, *SWHWd = nullptr, *HSWd = nullptr;
     CUtensorMap mapHS_A, mapWD_A, mapWD_B, mapHDSD_B, mapSWHW_A, mapHSW_B;
     float *HDSD32 = nullptr, *Z32 = nullptr, *G32 = nullptr, *Gp32 = nullptr, *D32 = nullptr;
@@ -326,13 +327,17 @@ int dense_start(omm_handle *h) {
 
 // ---------------------------------------------------------------- mixed precision
 constexpr int kDig = 3;
-constexpr int kBK = 32;   // K-block width of the split products (64-byte swizzle)
+// K-block width of the split products.  With two digits a 64-wide K block
+// (128-byte swizzle, two 96 KB stages) is read by the tensor cores without
+// the shared-memory bank conflicts of the 64-byte swizzle; three digits keep
+// 32-wide blocks (a 64-wide stage would leave room for only one).
+int split_bk(int digits) { return digits == 2 ? 64 : 32; }
 constexpr int kBN = 256;  // output tile width of the split products (UMMA N = 256)
 
 omm::tc::TcArgs tc_args(omm_handle *h, int M, int N, int K) {
     omm::tc::TcArgs a{};
     omm::tc::pairs_for_digits(h->cur_dig, a);
-    a.bk = kBK;
+    a.bk = h->mx.bk;
     a.M = M;
     a.N = N;
     a.K = K;
@@ -347,6 +352,8 @@ int mixed_alloc(omm_handle *h) {
     const int64_t m = h->m, n = h->n;
     MixedBufs &x = h->mx;
     x.ldm = (m + 7) / 8 * 8;
+    x.bk = split_bk(h->opt.split_digits);
+    const int kBK = x.bk;
     x.ld2n = (2 * n + 7) / 8 * 8;
     TRY(dalloc(&x.HSd, (size_t)(kDig * 2 * m * x.ldm)));
     TRY(dalloc(&x.WDd, (size_t)(kDig * 2 * n * x.ldm)));
@@ -786,8 +793,8 @@ int precon_alloc(omm_handle *h) {
         TRY(dalloc(&x.Pd, (size_t)(kDig * m * x.ldm)));
         TRY(dalloc(&x.Gd, (size_t)(kDig * n * x.ldm)));
         TRY(dalloc(&x.PG32, (size_t)(m * n)));
-        TRY(omm::tc::make_digit_map(&x.mapP_A, x.Pd, m, m, x.ldm, m * x.ldm, kDig, 128, kBK));
-        TRY(omm::tc::make_digit_map(&x.mapG_B, x.Gd, m, n, x.ldm, n * x.ldm, kDig, kBN, kBK));
+        TRY(omm::tc::make_digit_map(&x.mapP_A, x.Pd, m, m, x.ldm, m * x.ldm, kDig, 128, x.bk));
+        TRY(omm::tc::make_digit_map(&x.mapG_B, x.Gd, m, n, x.ldm, n * x.ldm, kDig, kBN, x.bk));
     }
     return OMM_OK;
 }

@@ -408,6 +408,7 @@ int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int 
     }
     if (bn == 256) {
         if (a.nA + 2 * a.nB <= 4) return launch_tc<256, 3, 64>(mapA, mapB, a, nbatch, st);
+        if (a.nA + a.nB <= 4) return launch_tc<256, 2, 64>(mapA, mapB, a, nbatch, st);   // 2 x 96 KB stages
         return launch_tc<256, 1, 64>(mapA, mapB, a, nbatch, st);
     }
     if (a.nA + a.nB <= 4) return launch_tc<128, 3, 64>(mapA, mapB, a, nbatch, st);

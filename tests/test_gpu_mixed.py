@@ -52,7 +52,9 @@ def test_mixed_solve_matches_oracle(omm, dims, refine):
 
 
 def test_kim_functional_mixed(omm):
-    """Kim construction in the mixed form (orth_tol stays 0: S_W -> diag(I, 0))."""
+    """Kim construction in the mixed form (orth_tol stays 0: S_W -> diag(I, 0)),
+    with three-digit split products: the functional is unbounded beyond a barrier
+    along unoccupied directions, and two-digit increments can cross it."""
     import synth
     import scipy.linalg as sla
     sysm = synth.make_system(4, 4, 3, seed=2)
@@ -62,7 +64,8 @@ def test_kim_functional_mixed(omm):
     rng = np.random.default_rng(9)
     W0 = np.asfortranarray(0.2 * np.hstack([sysm.W0_dense(), rng.standard_normal((sysm.m, 8)) / np.sqrt(sysm.m)]))
     n1 = W0.shape[1]
-    s = omm.Solver(sysm.m, n1, 8, precision=omm.PREC_MIXED, eta_auto=0, eta=eta, n_occupied=sysm.n)
+    s = omm.Solver(sysm.m, n1, 8, precision=omm.PREC_MIXED, eta_auto=0, eta=eta, n_occupied=sysm.n,
+                   split_digits=3)
     s.set_HS(dev(H), dev(S))
     W = torch.zeros((n1, sysm.m), dtype=torch.float64, device="cuda").T
     E, iters, st = s.solve(dev(W0), tol=1e-11, W_out=W)
