@@ -579,8 +579,10 @@ int mx_nn_update(int n, double *h0, double *s0, int64_t ldh, const float *Z, int
 int mx_dots_beta(int64_t mn, const float *G, const float *Zg, const float *Gp, const float *D, double *scratch,
                  unsigned int *counter, DevState *state, int first, cudaStream_t st) {
     if (((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)D) | ((uintptr_t)Zg)) & 15u) != 0) return OMM_ERR_ARG;
-    int64_t nb = ceil_div(mn, (int64_t)NT * 32);
-    if (nb > 152 * 2) nb = 152 * 2;
+    // up to kRedBlocksMax blocks (the partial-sum slots): enough warps per SM to
+    // keep the three streams' loads in flight
+    int64_t nb = ceil_div(mn, (int64_t)NT * 8);
+    if (nb > kRedBlocksMax) nb = kRedBlocksMax;
     const unsigned grid = (unsigned)(nb < 1 ? 1 : nb);
     if (Zg != nullptr)
         mx_dots_kernel<true><<<grid, NT, 0, st>>>(mn, G, Zg, Gp, D, scratch, counter, state, first);
