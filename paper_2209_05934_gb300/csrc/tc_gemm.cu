@@ -46,6 +46,19 @@ __device__ __forceinline__ void split3(double v, __nv_bfloat16 &d1, __nv_bfloat1
     d3 = __double2bfloat16(r2);
 }
 
+// The same three digits taken from the double's float rounding: the FP64 -> FP32
+// step on the integer pipe (sw_d2f), the splits in FP32.  They keep the same
+// ~24 significant bits (d1 + d2 + d3 = RN24(v) up to the last bit of d3)
+// without FP64 arithmetic or conversions, which are slow on this part; used by
+// the packing kernels, which touch every element of H' and S.
+__device__ __forceinline__ void split3_i(double v, __nv_bfloat16 &d1, __nv_bfloat16 &d2, __nv_bfloat16 &d3) {
+    const float f = sw_d2f(v);
+    d1 = __float2bfloat16_rn(f);
+    const float r1 = f - __bfloat162float(d1);
+    d2 = __float2bfloat16_rn(r1);
+    d3 = __float2bfloat16_rn(r1 - __bfloat162float(d2));
+}
+
 // ------------------------------------------------------------------ the GEMM kernel
 template <int BN, int STAGES, int BKT>
 __global__ void __launch_bounds__(192, 1)
@@ -290,7 +303,7 @@ __global__ void pack_cm_kernel(int64_t rows, int64_t cols, const double *__restr
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
              i += (int64_t)gridDim.x * blockDim.x) {
             __nv_bfloat16 d1, d2, d3;
-            split3(src[i + j * ld_src], d1, d2, d3);
+            split3_i(src[i + j * ld_src], d1, d2, d3);
             const int64_t o = j * ldd + i;
             dst[o] = d1;
             if (ndig > 1) dst[plane + o] = d2;
@@ -316,7 +329,7 @@ __global__ void pack_t_kernel(int64_t rows, int64_t cols, const double *__restri
         const int64_t i = ti + r, j = tj + lx;
         if (i < rows && j < cols) {
             __nv_bfloat16 d1, d2, d3;
-            split3(tile[lx][r], d1, d2, d3);
+            split3_i(tile[lx][r], d1, d2, d3);
             const int64_t o = i * ldd + j;
             dst[o] = d1;
             if (ndig > 1) dst[plane + o] = d2;
