@@ -28,8 +28,11 @@ def built():
 
 def test_header_declares_entry_points():
     names = _declared()
-    for must in ("omm_create", "omm_set_HS", "omm_solve", "omm_get_diag", "omm_destroy",
-                 "omm_status_str", "omm_op_dgemm", "omm_op_quartic_coeffs", "omm_op_line_min"):
+    for must in ("omm_create", "omm_set_HS", "omm_set_H", "omm_set_T", "omm_solve", "omm_solve_begin",
+                 "omm_solve_progress", "omm_solve_end", "omm_batch_solve", "omm_md_guess", "omm_get_diag",
+                 "omm_get_array", "omm_get_density", "omm_get_pattern", "omm_destroy", "omm_status_str",
+                 "omm_op_dgemm", "omm_op_split_gemm", "omm_op_exact_gemm", "omm_op_quartic_coeffs",
+                 "omm_op_quartic_coeffs_static", "omm_op_line_min", "omm_selftest_bounded_wait"):
         assert must in names
 
 
