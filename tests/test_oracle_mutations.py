@@ -136,3 +136,60 @@ def test_precon_unpreconditioned_direction_is_caught(small_system, monkeypatch):
         D = -G + beta * D                                                   # lost P
         return -Z if O.frob(G, D) >= 0.0 else D
     assert not _precon_pin_ok(small_system, monkeypatch, bad)
+
+
+# --------------------------------------------------------------- MD-step guess
+def _md_pin_ok(guess):
+    """The pattern-rules pin of the MD-step guess with a given implementation:
+    in dense terms the extrapolated guess is mask_new * mask_1 * (2 W1 - W2)."""
+    import synth
+    snaps = [synth.make_md_system(3, 3, 2, seed=4, t=t, step=0.25) for t in (0.0, 1.0, 2.0)]
+    pats = [s.w_pattern(4.5) for s in snaps]
+    N = snaps[0].natoms
+
+    def dense(vals, pat):
+        A = np.zeros((8 * N, 2 * N))
+        rp, col = pat
+        for I in range(N):
+            for b in range(rp[I], rp[I + 1]):
+                A[8 * I:8 * I + 8, 2 * col[b]:2 * col[b] + 2] = vals[b]
+        return A
+
+    mask = [dense(np.ones((len(p[1]), 8, 2)), p) for p in pats]
+    rng = np.random.default_rng(2)
+    W0 = rng.standard_normal((len(pats[0][1]), 8, 2))
+    W1 = rng.standard_normal((len(pats[1][1]), 8, 2))
+    ok = True
+    # the next snapshot's pattern, and the older one's again (blocks that left the
+    # radius at the middle step and came back: zero, whatever the older step held)
+    for new in (2, 0):
+        got = dense(guess(W1, pats[1], pats[new], W0, pats[0]), pats[new])
+        want = mask[new] * mask[1] * (2.0 * dense(W1, pats[1]) - dense(W0, pats[0]))
+        ok = ok and np.allclose(got, want, rtol=0, atol=1e-15)
+    return ok
+
+
+def test_md_pin_accepts_the_oracle():
+    assert _md_pin_ok(O.md_guess)
+
+
+def test_md_guess_new_blocks_from_the_older_step_are_caught():
+    def bad(W1, pat1, pat_new, W2, pat2):
+        # a block W1 lacks takes -W2 (the extrapolation run over the union of the patterns)
+        out = O.md_guess(W1, pat1, pat_new, W2, pat2)
+        at1 = {(I, int(pat1[1][b])) for I in range(len(pat1[0]) - 1) for b in range(pat1[0][I], pat1[0][I + 1])}
+        at2 = {(I, int(pat2[1][b])): b for I in range(len(pat2[0]) - 1) for b in range(pat2[0][I], pat2[0][I + 1])}
+        rp, col = pat_new
+        for I in range(len(rp) - 1):
+            for b in range(rp[I], rp[I + 1]):
+                key = (I, int(col[b]))
+                if key not in at1 and key in at2:
+                    out[b] = -W2[at2[key]]
+        return out
+    assert not _md_pin_ok(bad)
+
+
+def test_md_guess_lost_factor_two_is_caught():
+    def bad(W1, pat1, pat_new, W2, pat2):
+        return O.md_guess(W1, pat1, pat_new) - (O.md_guess(W2, pat2, pat_new) * (O.md_guess(W1, pat1, pat_new) != 0))
+    assert not _md_pin_ok(bad)
