@@ -83,6 +83,12 @@ def test_sparse_md_guess_matches_oracle(omm):
     h2.md_guess(h1, h0)
     g2 = resident_W(h2)
     np.testing.assert_array_equal(g2, O.md_guess(W1, p1, p2, W0, p0))
+    # onto the oldest snapshot's pattern again: blocks that left the radius at
+    # the middle step and came back start at zero, whatever the older step held
+    h3, p3 = sparse_handle(omm, snaps[0], max_iter=k)
+    h3.md_guess(h1, h0)
+    np.testing.assert_array_equal(resident_W(h3), O.md_guess(W1, p1, p3, W0, p0))
+    h3.close()
     E2, it2, st2 = h2.solve(None, tol=0.0, raise_on_error=False)
     ref2 = oracle_steps_from(snaps[2], g2, p2, h2.diag().eta, k)
     assert it2 == k and E2 == pytest.approx(ref2.E, rel=1e-12)
