@@ -446,3 +446,111 @@ def structural_pattern_product(rowptr_a, col_a, rowptr_b, col_b, nb_cols):
     P = (Pa @ Pb).tocsr()
     P.sort_indices()
     return P.indptr.astype(np.int64), P.indices.astype(np.int32)
+
+
+# ----------------------------------------------------------------------------
+# norm-based screening of block products (linear-scaling form)
+# ----------------------------------------------------------------------------
+def _blocks(A, br: int, bc: int) -> np.ndarray:
+    """Dense A of shape (NI*br, NJ*bc) viewed as blocks (NI, NJ, br, bc)."""
+    A = _dense(A)
+    NI, NJ = A.shape[0] // br, A.shape[1] // bc
+    return A.reshape(NI, br, NJ, bc).transpose(0, 2, 1, 3)
+
+
+def block_norms2(A, br: int, bc: int) -> np.ndarray:
+    """Squared Frobenius norm of every br x bc block of A, shape (NI, NJ)."""
+    Ab = _blocks(A, br, bc)
+    return np.sum(Ab * Ab, axis=(2, 3))
+
+
+def screened_product(A, B, br: int, bk: int, bc: int, eps: float):
+    """C = A B computed block by block, skipping every block product A_ik B_kj
+    with ||A_ik||_F ||B_kj||_F < eps (compared as ||A_ik||^2 ||B_kj||^2 < eps^2).
+
+    A is cut into br x bk blocks, B into bk x bc blocks.  This is the
+    norm-based filtering of the products of a DBCSR-style block-sparse
+    multiply (section "Solver library": the sparse matrices and their algebra
+    are DBCSR's): a skipped product changes C_ij by at most ||A_ik|| ||B_kj||
+    < eps in Frobenius norm and never changes which blocks are stored.  A
+    block that is not stored is a zero block, whose products are skipped for
+    any eps > 0 and contribute nothing for eps = 0, so the result is the same
+    on the structural pattern either way.  eps = 0 skips nothing: C = A B.
+    """
+    Ab, Bb = _blocks(A, br, bk), _blocks(B, bk, bc)
+    nA = np.sum(Ab * Ab, axis=(2, 3))
+    nB = np.sum(Bb * Bb, axis=(2, 3))
+    NI, NK, NJ = Ab.shape[0], Ab.shape[1], Bb.shape[1]
+    Cb = np.zeros((NI, NJ, br, bc))
+    for k in range(NK):
+        keep = ~(nA[:, k][:, None] * nB[k][None, :] < eps * eps)       # (NI, NJ)
+        Cb += np.einsum("iab,jbc->ijac", Ab[:, k], Bb[k]) * keep[:, :, None, None]
+    return Cb.transpose(0, 2, 1, 3).reshape(NI * br, NJ * bc)
+
+
+def omm_cg_screened(H, S, W0, bm: int, bn: int, eps: float, tol: float = 1e-10,
+                    eta: float | None = None, max_iter: int = 10000, mask=None) -> Result:
+    """Linear-scaling CG with norm-based screening of every block product.
+
+    The same minimisation as omm_cg (same shift, energy, RelTol test,
+    gradient kept on W's pattern, PR+ direction, exact quartic line search),
+    written with the products a block-sparse step forms (section "Solver
+    library"), each one screened by screened_product with threshold eps:
+      start:  H'W, SW; H_W = W^T (H'W), S_W = W^T (SW);
+      step:   G = 2 (2 H'W - (SW) H_W - (H'W) S_W) on W's pattern; D;
+              H'D, SD; X = W^T (H'D), Y = W^T (SD), h2 = D^T (H'D), s2 = D^T (SD);
+              the line quartic of H_W(x) = H_W + x (X + X^T) + x^2 h2 and
+              S_W(x) = S_W + x (Y + Y^T) + x^2 s2 (H' and S symmetric);
+              W, H'W, SW, H_W, S_W carried to W + x D by the same expansions.
+    Blocks: bm x bm for H and S, bm x bn for W (basis atom x orbitals of one
+    atom), bn x bn for the n x n matrices.  Dense arrays in, zero blocks
+    standing for blocks that are not stored.  With eps = 0 nothing is skipped
+    and the iterates are omm_cg's up to rounding.
+    """
+    H, S = _dense(H), _dense(S)
+    if eta is None:
+        eta = gershgorin_eta(H, S)
+    Hs = shift(H, S, eta)
+    n = W0.shape[1]
+
+    def P(A, B, br, bk, bc):
+        return screened_product(A, B, br, bk, bc, eps)
+
+    W = apply_mask(np.array(_dense(W0), dtype=np.float64), mask)
+    HW, SW = P(Hs, W, bm, bm, bn), P(S, W, bm, bm, bn)
+    h0, s0 = P(W.T, HW, bn, bm, bn), P(W.T, SW, bn, bm, bn)
+    history, E_prev, G_prev, D = [], None, None, None
+    k, status = 0, OK
+    while True:
+        E = 2.0 * (2.0 * np.trace(h0) - frob(s0, h0)) + 2.0 * eta * n
+        history.append(E)
+        orth = float(np.linalg.norm(s0 - np.eye(n)))
+        if k >= 1 and abs(2.0 * (E - E_prev) / (E + E_prev)) < tol:
+            break
+        if k >= max_iter:
+            status = ERR_MAXITER
+            break
+        G = apply_mask(2.0 * (2.0 * HW - P(SW, h0, bm, bn, bn) - P(HW, s0, bm, bn, bn)), mask)
+        D = cg_direction(G, G, G_prev, G_prev, D)
+        HD, SD = P(Hs, D, bm, bm, bn), P(S, D, bm, bm, bn)
+        X, Y = P(W.T, HD, bn, bm, bn), P(W.T, SD, bn, bm, bn)
+        h2, s2 = P(D.T, HD, bn, bm, bn), P(D.T, SD, bn, bm, bn)
+        A_ = [h0, X + X.T, h2]
+        B_ = [s0, Y + Y.T, s2]
+        c = np.zeros(5)
+        for i in range(3):
+            c[i] += 2.0 * 2.0 * np.trace(A_[i])
+            for j in range(3):
+                c[i + j] -= 2.0 * frob(B_[i], A_[j])
+        x, st = line_min(c)
+        if st != OK:
+            status = st
+            break
+        W = W + x * D
+        HW, SW = HW + x * HD, SW + x * SD
+        h0 = h0 + x * A_[1] + x * x * h2
+        s0 = s0 + x * B_[1] + x * x * s2
+        E_prev, G_prev = E, G
+        k += 1
+    return Result(W=W, E=E, E_unshifted=functional(W, H, S), iters=k, status=status, eta=eta,
+                  history=history, orth=orth)

@@ -193,3 +193,98 @@ def test_md_guess_lost_factor_two_is_caught():
     def bad(W1, pat1, pat_new, W2, pat2):
         return O.md_guess(W1, pat1, pat_new) - (O.md_guess(W2, pat2, pat_new) * (O.md_guess(W1, pat1, pat_new) != 0))
     assert not _md_pin_ok(bad)
+
+
+# --------------------------------------------------------------- patterns, filter, shift, screening
+# Each case plants a mistake in one oracle helper and runs that helper's pin
+# from test_oracle_pins, which must then fail.
+import test_oracle_pins as pins  # noqa: E402
+
+
+def _pin_fails(pin, monkeypatch, name, bad, *args):
+    monkeypatch.setattr(O, name, bad)
+    with pytest.raises(AssertionError):
+        pin(*args)
+
+
+def test_hs_filter_and_instead_of_or_is_caught(monkeypatch):
+    bad = lambda H, S, eps: O.filter_blocks(H, eps) & O.filter_blocks(S, eps)
+    _pin_fails(pins.test_hs_block_filter_keeps_a_block_when_either_matrix_is_above_eps, monkeypatch,
+               "filter_hs_blocks", bad)
+
+
+def test_pattern_product_dropped_entry_is_caught(monkeypatch):
+    good = O.structural_pattern_product
+
+    def bad(rp_a, col_a, rp_b, col_b, nb):
+        rp, col = good(rp_a, col_a, rp_b, col_b, nb)
+        r = (len(rp) - 1) // 2
+        while rp[r + 1] == rp[r]:
+            r += 1
+        col = np.delete(col, rp[r + 1] - 1)                # a middle row loses its last block
+        rp = rp.copy()
+        rp[r + 1:] -= 1
+        return rp, col
+    _pin_fails(pins.test_structural_pattern_product_against_triple_loop, monkeypatch,
+               "structural_pattern_product", bad)
+
+
+def test_gershgorin_wrong_branch_is_caught(monkeypatch):
+    good = O.gershgorin_eta
+
+    def bad(H, S):      # always divides by the lower overlap bound
+        Hd, Sd = (H.toarray(), S.toarray()) if hasattr(H, "toarray") else (H, S)
+        g = float(np.max(np.diag(Hd) + np.abs(Hd).sum(axis=1) - np.abs(np.diag(Hd))))
+        return g / float(np.min(np.diag(Sd) - (np.abs(Sd).sum(axis=1) - np.abs(np.diag(Sd)))))
+    assert bad(np.diag([1.0, 2.0]), np.eye(2)) == good(np.diag([1.0, 2.0]), np.eye(2))
+    _pin_fails(pins.test_gershgorin_eta_closed_form_both_branches, monkeypatch, "gershgorin_eta", bad)
+
+
+def test_screening_on_one_operand_norm_is_caught(monkeypatch):
+    def bad(A, B, br, bk, bc, eps):     # skips on ||A_ik|| < eps alone
+        Ab, Bb = O._blocks(A, br, bk), O._blocks(B, bk, bc)
+        nA = np.sum(Ab * Ab, axis=(2, 3))
+        Cb = np.zeros((Ab.shape[0], Bb.shape[1], br, bc))
+        for k in range(Ab.shape[1]):
+            keep = ~(nA[:, k] < eps * eps)
+            Cb += np.einsum("iab,jbc->ijac", Ab[:, k], Bb[k]) * keep[:, None, None, None]
+        return Cb.transpose(0, 2, 1, 3).reshape(Ab.shape[0] * br, Bb.shape[1] * bc)
+    _pin_fails(pins.test_screened_product_drops_exactly_the_tiny_blocks, monkeypatch, "screened_product", bad)
+
+
+def test_screening_on_norm_sum_is_caught(monkeypatch):
+    def bad(A, B, br, bk, bc, eps):     # ||A_ik|| + ||B_kj|| < eps
+        Ab, Bb = O._blocks(A, br, bk), O._blocks(B, bk, bc)
+        nA, nB = np.sqrt(np.sum(Ab * Ab, axis=(2, 3))), np.sqrt(np.sum(Bb * Bb, axis=(2, 3)))
+        Cb = np.zeros((Ab.shape[0], Bb.shape[1], br, bc))
+        for k in range(Ab.shape[1]):
+            keep = ~(nA[:, k][:, None] + nB[k][None, :] < eps)
+            Cb += np.einsum("iab,jbc->ijac", Ab[:, k], Bb[k]) * keep[:, :, None, None]
+        return Cb.transpose(0, 2, 1, 3).reshape(Ab.shape[0] * br, Bb.shape[1] * bc)
+    _pin_fails(pins.test_screened_product_drops_exactly_the_tiny_blocks, monkeypatch, "screened_product", bad)
+
+
+def test_screened_cg_lost_dsd_term_is_caught(monkeypatch):
+    """A screened CG that loses D^T S D (s2) from its line quartic and its S_W
+    update no longer takes omm_cg's steps at eps = 0."""
+    good = O.omm_cg_screened
+
+    def bad(H, S, W0, bm, bn, eps, tol=1e-10, eta=None, max_iter=10000, mask=None):
+        calls = {"n": 0}
+        real = O.screened_product
+
+        def spy(A, B, br, bk, bc, e):
+            C = real(A, B, br, bk, bc, e)
+            calls["n"] += 1
+            # products per step: G (2), H'D, SD, X, Y, h2, s2; the 8th is s2 -> zero it
+            if calls["n"] > 4 and (calls["n"] - 4) % 8 == 0:
+                return 0.0 * C
+            return C
+        monkeypatch.setattr(O, "screened_product", spy)
+        try:
+            return good(H, S, W0, bm, bn, eps, tol=tol, eta=eta, max_iter=max_iter, mask=mask)
+        finally:
+            monkeypatch.setattr(O, "screened_product", real)
+    monkeypatch.setattr(O, "omm_cg_screened", bad)
+    with pytest.raises(AssertionError):
+        pins.test_screened_cg_without_threshold_is_the_cg()

@@ -442,3 +442,149 @@ def test_md_system_is_smooth_in_time():
     b = synth.make_md_system(3, 3, 2, seed=4, t=1.001, step=0.05)
     assert np.abs(a.dense_H() - b.dense_H()).max() < 1e-3
     assert np.abs(a.dense_S() - b.dense_S()).max() < 1e-3
+
+
+# --------------------------------------------------------------- pattern, filter and shift helpers
+def _pattern_product_by_hand(rp_a, col_a, rp_b, col_b):
+    """Block pattern of A B by a plain loop over block triples (i, k, j)."""
+    rows = []
+    for i in range(len(rp_a) - 1):
+        cols = set()
+        for a in range(rp_a[i], rp_a[i + 1]):
+            k = col_a[a]
+            for b in range(rp_b[k], rp_b[k + 1]):
+                cols.add(int(col_b[b]))
+        rows.append(sorted(cols))
+    rp = np.cumsum([0] + [len(r) for r in rows])
+    return rp, np.array([c for r in rows for c in r], dtype=np.int64)
+
+
+def test_structural_pattern_product_small_by_hand():
+    """A 3 x 3 block pattern times a 3 x 2 one, worked out on paper:
+    A = [[x . x], [. x .], [x . x]], B = [[x .], [. x], [. .]]  ->  A B = [[x .], [. x], [x .]]."""
+    rp_a, col_a = np.array([0, 2, 3, 5]), np.array([0, 2, 1, 0, 2], dtype=np.int32)
+    rp_b, col_b = np.array([0, 1, 2, 2]), np.array([0, 1], dtype=np.int32)
+    rp, col = O.structural_pattern_product(rp_a, col_a, rp_b, col_b, 2)
+    assert rp.tolist() == [0, 1, 2, 3]
+    assert col.tolist() == [0, 1, 0]
+
+
+def test_structural_pattern_product_against_triple_loop():
+    """P_HW = P_H P_W and P_N = P_W^T P_HW of a 50-atom system (5 x 5 x 2 grid,
+    W radius 2.8 A) against a triple loop over blocks."""
+    import synth
+    sysm = synth.make_system(5, 5, 2, seed=4)
+    N = sysm.natoms
+    rp_h, col_h, _, _ = sysm.bsr()
+    rp_w, col_w = sysm.w_pattern(2.8)
+    rp_hw, col_hw = O.structural_pattern_product(rp_h, col_h, rp_w, col_w, N)
+    ref_rp, ref_col = _pattern_product_by_hand(rp_h, col_h, rp_w, col_w)
+    assert rp_hw.tolist() == ref_rp.tolist() and col_hw.tolist() == ref_col.tolist()
+    # W^T in block CSR by a loop, then P_N
+    t_rows = [[] for _ in range(N)]
+    for I in range(N):
+        for b in range(rp_w[I], rp_w[I + 1]):
+            t_rows[col_w[b]].append(I)
+    rp_wt = np.cumsum([0] + [len(r) for r in t_rows])
+    col_wt = np.array([c for r in t_rows for c in r], dtype=np.int32)
+    rp_n, col_n = O.structural_pattern_product(rp_wt, col_wt, rp_hw, col_hw, N)
+    ref_rp, ref_col = _pattern_product_by_hand(rp_wt, col_wt, rp_hw, col_hw)
+    assert rp_n.tolist() == ref_rp.tolist() and col_n.tolist() == ref_col.tolist()
+    assert 0 < len(col_n) < N * N                 # neither empty nor dense at this radius
+
+
+def test_hs_block_filter_keeps_a_block_when_either_matrix_is_above_eps():
+    """The shared H/S pattern keeps a block pair when H or S is at least eps."""
+    H = np.zeros((4, 2, 2))
+    S = np.zeros((4, 2, 2))
+    H[0, 0, 1] = 3e-8                          # H above, S zero      -> kept
+    S[1, 1, 0] = 2e-8                          # S above, H zero      -> kept
+    H[2, 0, 0], S[2, 1, 1] = 5e-9, 6e-9        # both below           -> dropped
+    H[3, 0, 0], S[3, 0, 0] = 1e-8, 0.0         # H exactly at eps     -> kept (strict)
+    assert list(O.filter_hs_blocks(H, S, 1e-8)) == [True, True, False, True]
+
+
+def test_gershgorin_eta_closed_form_both_branches():
+    """eta from hand-computed Gershgorin discs: g_H / s_lo when g_H >= 0, g_H / s_hi
+    when g_H < 0; each is an upper bound of the generalised spectrum, and in the
+    g_H < 0 case the other quotient would not be."""
+    S = np.array([[1.0, 0.1, 0.0], [0.1, 1.0, 0.2], [0.0, 0.2, 1.0]])
+    s_lo, s_hi = 0.7, 1.3                      # rows: 1 -+ 0.1, 1 -+ 0.3, 1 -+ 0.2
+    H_pos = np.array([[2.0, 1.0, -1.0], [1.0, -3.0, 0.5], [-1.0, 0.5, 1.0]])
+    g_pos = 4.0                                # max(2 + 2, -3 + 1.5, 1 + 1.5)
+    H_neg = np.array([[-10.0, 1.0, 0.0], [1.0, -12.0, 2.0], [0.0, 2.0, -9.0]])
+    g_neg = -7.0                               # max(-10 + 1, -12 + 3, -9 + 2)
+    for H, expect in ((H_pos, g_pos / s_lo), (H_neg, g_neg / s_hi)):
+        eta = O.gershgorin_eta(H, S)
+        assert eta == pytest.approx(expect, rel=1e-15)
+        assert eta >= sla.eigh(H, S, eigvals_only=True)[-1]
+        assert O.gershgorin_eta(sp.csr_matrix(H), sp.csr_matrix(S)) == pytest.approx(expect, rel=1e-15)
+    assert g_neg / s_lo < sla.eigh(H_neg, S, eigvals_only=True)[-1]   # the wrong quotient fails
+
+
+# --------------------------------------------------------------- screening of block products
+def _screen_case(seed=0):
+    """Block operands whose norms span decades, with a few tiny blocks in each."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((5 * 4, 6 * 3))
+    B = rng.standard_normal((6 * 3, 4 * 2))
+    tiny_a = [(0, 1), (3, 4), (4, 0)]
+    tiny_b = [(2, 3), (5, 1)]
+    for i, k in tiny_a:
+        A[4 * i:4 * i + 4, 3 * k:3 * k + 3] *= 1e-10
+    for k, j in tiny_b:
+        B[3 * k:3 * k + 3, 2 * j:2 * j + 2] *= 1e-10
+    A[8:12, 6:9] = 0.0                          # a block that is not stored
+    return A, B, tiny_a, tiny_b
+
+
+def test_screened_product_without_threshold_is_the_product():
+    A, B, _, _ = _screen_case()
+    np.testing.assert_allclose(O.screened_product(A, B, 4, 3, 2, 0.0), A @ B, rtol=0, atol=1e-13)
+
+
+def test_screened_product_drops_exactly_the_tiny_blocks():
+    """Every product with a 1e-10 block is below eps = 1e-6 and every other one
+    is above it, so screening equals the plain product with those blocks zeroed."""
+    A, B, tiny_a, tiny_b = _screen_case()
+    nA, nB = np.sqrt(O.block_norms2(A, 4, 3)), np.sqrt(O.block_norms2(B, 3, 2))
+    big = np.outer(nA[nA > 1e-5].min(keepdims=True), nB[nB > 1e-5].min(keepdims=True))
+    assert big.min() > 1e-3 and nA.max() * 1e-10 * 10 < 1e-6
+    A0, B0 = A.copy(), B.copy()
+    for i, k in tiny_a:
+        A0[4 * i:4 * i + 4, 3 * k:3 * k + 3] = 0.0
+    for k, j in tiny_b:
+        B0[3 * k:3 * k + 3, 2 * j:2 * j + 2] = 0.0
+    C = O.screened_product(A, B, 4, 3, 2, 1e-6)
+    np.testing.assert_allclose(C, A0 @ B0, rtol=0, atol=1e-13)
+    assert np.abs(C - A @ B).max() > 1e-12     # the skipped products were not zero
+
+
+def test_screened_product_error_bound():
+    """||C_ij - (A B)_ij||_F <= sum of ||A_ik|| ||B_kj|| over the skipped k."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((24, 24)) * np.kron(10.0 ** rng.uniform(-4, 0, (6, 6)), np.ones((4, 4)))
+    B = rng.standard_normal((24, 12)) * np.kron(10.0 ** rng.uniform(-4, 0, (6, 6)), np.ones((4, 2)))
+    eps = 1e-4
+    C = O.screened_product(A, B, 4, 4, 2, eps)
+    nA = np.sqrt(np.sum(A.reshape(6, 4, 6, 4) ** 2, axis=(1, 3)))
+    nB = np.sqrt(np.sum(B.reshape(6, 4, 6, 2) ** 2, axis=(1, 3)))
+    err = np.sqrt(np.sum((C - A @ B).reshape(6, 4, 6, 2) ** 2, axis=(1, 3)))
+    prod = nA[:, :, None] * nB[None, :, :]                   # (i, k, j)
+    skipped = np.where(prod < eps, prod, 0.0).sum(axis=1)
+    assert np.all(err <= skipped * (1 + 1e-12) + 1e-15)
+    assert skipped.max() > 0                                  # some products were skipped
+
+
+def test_screened_cg_without_threshold_is_the_cg():
+    """The screened linear-scaling CG with eps = 0 takes omm_cg's steps."""
+    import synth
+    sysm = synth.make_system(3, 3, 2, seed=2)
+    H, S, mask, W0 = sysm.dense_H(), sysm.dense_S(), sysm.w_mask(3.6), sysm.W0_local(3.6)
+    a = O.omm_cg_screened(H, S, W0, 8, 2, 0.0, tol=0.0, max_iter=25, mask=mask)
+    b = O.omm_cg(H, S, W0, tol=0.0, max_iter=25, mask=mask)
+    np.testing.assert_allclose(a.history, b.history, rtol=1e-13)
+    np.testing.assert_allclose(a.W, b.W, atol=1e-12)
+    c = O.omm_cg_screened(H, S, W0, 8, 2, 0.0, tol=1e-12, mask=mask)
+    d = O.omm_cg(H, S, W0, tol=1e-12, mask=mask)
+    assert c.status == d.status == O.OK and c.E == pytest.approx(d.E, rel=1e-12)
