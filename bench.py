@@ -158,33 +158,59 @@ def cpu_baseline(sysm, H, S, W0, full_iters: int, n_iter: int = 2):
 
 
 def run_reference(args):
+    """The oracle on this workload, timed on the host cores: one whole FP64 solve
+    (Gershgorin shift and CG to the same RelTol as the GPU arm's FP64 form),
+    measured, not scaled.  A solve takes about 40 s on 16 cores, so this arm
+    times exactly one, whatever --steps and --warmup say (the line reports
+    steps = 1, warmup = 0 and says so)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    from oracle import omm as O
     sysm = synth.make_system(*WORKLOAD["dims"], seed=WORKLOAD["seed"])
     H, S = sysm.dense_H(), sysm.dense_S()
     W0 = np.asfortranarray(sysm.W0_dense())
-    g = golden().get("c2", {})
-    full_iters = int(g.get("oracle_iters", 60))
-    for _ in range(args.warmup):
-        oracle_sample(sysm, H, S, W0, 1)
-    times = []
-    for _ in range(args.steps):
-        ts, ti = oracle_sample(sysm, H, S, W0, 1)
-        times.append(ts + full_iters * ti)
-    t = statistics.mean(times)
+    tol = TOL["fp64"]["tol"]
+    t0 = time.perf_counter()
+    res = O.omm_cg(H, S, W0, tol=tol)
+    t = time.perf_counter() - t0
+    e_exact = golden().get("c2", {}).get("exact_E")
     cores = len(os.sched_getaffinity(0))
     line = {
         "impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(sysm), "tol": TOL["fp64"]["tol"]},
+        "config": {"workload": workload_name(sysm), "tol": tol,
+                   "steps_note": (f"one whole oracle solve is timed (requested --steps {args.steps} "
+                                  f"--warmup {args.warmup}); a solve takes tens of seconds on the host")},
+        "accuracy": {"E": res.E, "iters": res.iters, "status": res.status,
+                     "rel_err": abs(res.E - e_exact) / abs(e_exact) if e_exact else None},
         "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": (f"per step: oracle setup + 1 FP64 CG step, scaled to the "
-                                    f"oracle's {full_iters} steps per solve")},
+                         "sample": f"one whole oracle solve of this workload ({res.iters} CG steps), measured"},
         "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def fp64_gemm_peak(size=8192, reps=5):
+    """FP64 throughput of cuBLAS DGEMM (torch.matmul in float64) on this GPU: the
+    measured FP64 denominator of the FP64 rooflines, as the driver's BF16 peak
+    is cuBLAS's.  Best of `reps` timed products after one warm-up, TFLOP/s."""
+    import torch
+    a = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    b = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    c = a @ b
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b, c
+    return 2.0 * size ** 3 / (best * 1e-3) / 1e12
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -352,21 +378,22 @@ def run_omm(args):
 
     # ---- roofline of the dominant stage
     pk, pk_kind = peaks()
+    fp64_peak = fp64_gemm_peak(4096)
+    pk = dict(pk, fp64_tflops=fp64_peak)
     # the dominant kernel is the split GEMM (tc_gemm); its products stage launches nothing
     # else, while the gradient and contraction stages also hold exact-digit GEMMs.  The
     # FP64 form reports its largest stage.
     dom = 0 if prec == "mixed" else (int(np.argmax(ms_stage[:6])) if sum(ms_stage[:6]) > 0 else 0)
     roof = roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind)
     if roof is not None and prec == "mixed":
-        # BF16 pair products per FP64-equivalent product: 3 in the two-digit first
-        # phase (its start included), 6 in the refinement
-        d_ = solver.diag()
-        p1 = (d_.iters_mixed + 1) * (3 if args.split_digits == 2 else 6)
-        p2 = d_.iters_refine * 6
-        pairs = (p1 + p2) / max(1, d_.iters_mixed + 1 + d_.iters_refine)
+        # BF16 digit-pair products per FP64-equivalent product in the products stage:
+        # both phases multiply the split_digits digits of [H'; S] and D, so 3 pairs
+        # with two digits and 6 with three; bf16_issue_frac counts the BF16 flops the
+        # tensor cores issue against the same measured BF16 peak
+        pairs = 3 if args.split_digits == 2 else 6
         roof["bf16_pairs_per_product"] = pairs
-        roof["tensor_pipe_frac"] = roof["frac"] * pairs
-    if roof is not None and roof.get("kernel") in TRAFFIC and prec == "mixed":
+        roof["bf16_issue_frac"] = roof["frac"] * pairs
+    if roof is not None and roof.get("kernel") in TRAFFIC and prec == "mixed" and args.split_digits == 2:
         roof["traffic"] = TRAFFIC[roof["kernel"]]["bytes_per_launch"]
         roof["traffic_source"] = TRAFFIC[roof["kernel"]]["source"]
 
@@ -399,6 +426,8 @@ def run_omm(args):
         "fp64_gpu_beside": fp64_beside,
         "density_matrix": density,
         "kinetic_preconditioning": kinetic,
+        "fp64_peak": {"tflops": fp64_peak, "how": "cuBLAS DGEMM via torch.matmul, float64 4096^3, best of 5, "
+                                                 "this run"},
         "e2e": {"value": ws * e2e_steps / (t_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(2 * m * m * 8 + m * n * 8),
                 "d2h_bytes_per_step": int(m * n * 8 + 8)},
@@ -413,11 +442,12 @@ STAGES = ["products", "contract", "linesearch", "update", "gradient", "direction
           "pack", "anchor", "precon"]
 
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture of the current
-# kernel (profiles/ names the file and the command); None until captured.
+# DRAM bytes per launch of the dominant kernel, from one ncu capture of the current
+# kernel on this workload (a first-phase products launch of the two-digit split
+# GEMM); replaced whenever the kernel changes and is captured again.
 TRAFFIC = {"products": {"bytes_per_launch": 167.2e6 + 40.3e6,
                         "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one first-phase "
-                                  "products launch, profiles/tc_gemm_split_c2.md"}}
+                                  "products launch of the split GEMM, m=4096, n=1024"}}
 
 
 def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
@@ -427,14 +457,14 @@ def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
     # algorithmic flops per launch of each stage (dense)
     flops = {0: 4.0 * m * m * n, 1: 2.0 * (2 * n) * (2 * n) * m, 4: 2.0 * m * n * (2 * n)}
     if prec == "fp64":
-        fp64_peak = pk.get("fp64_tflops", 1.19)
+        fp64_peak = pk["fp64_tflops"]
         f = flops.get(dom)
         if f is None:
             return None
         ach = f / (avg_ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": STAGES[dom], "achieved": ach, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "FP64 DFMA throughput measured on this GB300 by an FMA-chain probe"}
+                "peak_source": "cuBLAS DGEMM (4096^3, best of 5) measured in this run"}
     f = flops.get(dom)
     if f is None:
         return None
@@ -485,8 +515,107 @@ def run_profile_c3(args):
     s.close()
 
 
+def run_c3(args):
+    """The linear-scaling workload solved to convergence: 4096 atoms (16^3),
+    m = 32768, n = 8192, R_C = 6 A, FP64 block-sparse, RelTol 1e-10 (or
+    --max-iter steps).  One warm-up solve (gather lists uploaded, modules
+    loaded), then timed solves from W0 with set_HS inside each step; the
+    per-stage times of one extra profiled solve give the sparse kernels'
+    rooflines (FP64 flops and algorithmic bytes per launch)."""
+    import torch
+    from paper_2209_05934_gb300 import omm
+
+    omm.lib()
+    sysm = synth.make_system(*C3["dims"], seed=C3["seed"])
+    rp, col, Hv, Sv = sysm.bsr()
+    wrp, wcol = sysm.w_pattern(C3["radius"])
+    stream = torch.cuda.Stream()
+    max_iter = args.max_iter if args.max_iter > 0 else 20000
+    s = omm.SparseSolver(sysm.m, sysm.n, 8, 2, rp, col, wrp, wcol, max_iter=max_iter,
+                         stream=stream.cuda_stream, screen_eps=args.screen_eps)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    Hd, Sd, W0d = dev(Hv), dev(Sv), dev(sysm.W0_bsr_values(C3["radius"]))
+    torch.cuda.synchronize()
+    tol = 1e-10
+
+    def step():
+        s.set_HS(Hd, Sd)
+        return s.solve(W0d, tol=tol, raise_on_error=False)
+
+    step()
+    torch.cuda.synchronize()
+    launches0 = omm.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            E, iters, st = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1) / args.steps
+    launches = omm.kernel_launches() - launches0
+    s.set_profiling(True)
+    s.stage_times(reset=True)
+    step()
+    torch.cuda.synchronize()
+    s.set_profiling(False)
+    ms, cnt = s.stage_times(reset=True)
+    fp64_peak = fp64_gemm_peak(4096)
+    nnz = s.nnzb
+    # algorithmic work per launch (blocks 8x8 / 8x2 / 2x2, FP64): the block-product
+    # triples of each gather, counted from the structural patterns
+    TRIPLES = sparse_triples(sysm, rp, col, wrp, wcol)
+    d = s.diag()
+    rows = {
+        "products": {"flop": 2 * 2 * 8 * 8 * 2 * TRIPLES["HW"], "bytes": 8 * (2 * 64 * nnz["H"] + 16 * nnz["W"]
+                                                                              + 2 * 16 * nnz["HW"])},
+        "contract": {"flop": 4 * 2 * 2 * 2 * 8 * TRIPLES["N"], "bytes": 8 * (2 * 16 * nnz["W"] + 2 * 16 * nnz["HW"]
+                                                                             + 4 * 4 * nnz["N"])},
+        "gradient": {"flop": 2 * 2 * 8 * 2 * 2 * TRIPLES["G"], "bytes": 8 * (2 * 16 * nnz["HW"] + 2 * 4 * nnz["N"]
+                                                                             + 16 * nnz["W"])},
+    }
+    roof = {}
+    for i, name in enumerate(STAGES):
+        if name in rows and cnt[i] > 0:
+            per = ms[i] / cnt[i]
+            roof[name] = {"ms_per_launch": per, "fp64_tflops": rows[name]["flop"] / (per * 1e-3) / 1e12,
+                          "frac_fp64": rows[name]["flop"] / (per * 1e-3) / 1e12 / fp64_peak,
+                          "hbm_gbs": rows[name]["bytes"] / (per * 1e-3) / 1e9}
+    line = {"metric": "OMM solves/s & time-to-converge, linear-scaling form", "value": 1e3 / t_ms,
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": t_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": (f"linear-scaling OMM-CG, 4096 atoms (16x16x16 jittered grid), m={sysm.m}, "
+                                    f"n={sysm.n}, R_C={C3['radius']} A, BSR 8x8 / 8x2, filter 1e-8"),
+                       "tol": tol, "max_iter": max_iter, "screen_eps": args.screen_eps, "nnzb": nnz},
+            "time_to_converge_ms": t_ms, "iters": int(iters), "status": int(st), "E": E, "eta": d.eta,
+            "ms_per_iteration": t_ms / max(1, int(iters)),
+            "stages_ms_per_solve": {n_: ms[i] for i, n_ in enumerate(STAGES)},
+            "roofline": roof, "fp64_peak_tflops": fp64_peak,
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
+def sparse_triples(sysm, rp, col, wrp, wcol):
+    """Block-product triples of the sparse step: H'W (H block (I,K) x W block (K,J)),
+    the contractions W^T (H'W) (W block (I,J1) x H'W block (I,J2)) and the masked
+    gradient (H'W block (I,K) x N block (K,J) kept on W's pattern)."""
+    import scipy.sparse as sps
+    N = sysm.natoms
+    PH = sps.csr_matrix((np.ones(len(col)), col, rp), shape=(N, N))
+    PW = sps.csr_matrix((np.ones(len(wcol)), wcol, wrp), shape=(N, N))
+    PHW = (PH @ PW).tocsr()
+    PHW.data[:] = 1.0
+    PN = (PW.T @ PHW).tocsr()
+    PN.data[:] = 1.0
+    hw = float((PH @ PW).sum())
+    n_ = float((PW.T @ PHW).sum())
+    g = float((PHW @ PN).multiply(PW).sum())
+    return {"HW": hw, "N": n_, "G": g}
+
+
 def run_profile(args):
-    """One solve, nothing else: the command the ncu summaries under profiles/ are taken from."""
+    """One solve, nothing else: the command that ncu captures of the solve's kernels run."""
     import torch
     from paper_2209_05934_gb300 import omm
 
@@ -771,6 +900,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run one solve only (for ncu captures); prints stage times, no benchmark line")
     ap.add_argument("--max-iter", type=int, default=0, help="with --profile: cap on CG steps")
+    ap.add_argument("--fp64-peak", action="store_true",
+                    help="print the measured FP64 GEMM throughput (the FP64 roofline denominator) and exit")
     ap.add_argument("--no-fp64-beside", action="store_true",
                     help="c2: skip the plain FP64 GPU solve reported beside the mixed form")
     ap.add_argument("--fp64-sequences", type=int, default=6,
@@ -784,9 +915,11 @@ def main():
     ap.add_argument("--cholesky", action="store_true",
                     help="c2: Cholesky-reduced variant (S = L L^T factored inside each step's setup)")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "md"],
-                    help="c2 dense workload (default); c3 linear-scaling (with --profile); "
+                    help="c2 dense workload (default); c3 linear-scaling to convergence; "
                          "c4 batched uneven solves; c5 serving loop")
     ap.add_argument("--batch", type=int, default=64, help="c4: number of systems")
+    ap.add_argument("--screen-eps", type=float, default=0.0,
+                    help="c3: norm-based screening threshold of the sparse block products (0: off)")
     ap.add_argument("--md-steps", type=int, default=5, help="md: snapshots per chain")
     ap.add_argument("--md-step", type=float, default=0.03, help="md: Angstrom per snapshot per unit velocity")
     ap.add_argument("--md-max-iter", type=int, default=20000, help="md: CG step cap of the sparse solves")
@@ -795,11 +928,19 @@ def main():
     ap.add_argument("--rates", type=float, nargs="+", default=[10.0, 50.0, 200.0], help="c5: arrivals per second")
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0, help="c5: admission budget")
     args = ap.parse_args()
+    if args.fp64_peak:
+        import torch  # noqa: F401
+        print(json.dumps({"fp64_peak_tflops": {str(n): fp64_gemm_peak(n) for n in (2048, 4096, 8192)},
+                          "how": "cuBLAS DGEMM via torch.matmul in float64, n^3, best of 5"}), flush=True)
+        return
     if args.profile:
         run_profile(args)
         return
     if args.warmup < 3:
         args.warmup = 3
+    if args.config == "c3":
+        run_c3(args)
+        return
     if args.config == "c4":
         run_c4(args)
         return

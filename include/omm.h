@@ -134,6 +134,18 @@ typedef struct {
                               given with omm_set_T */
     double tau_T;          /* kinetic-energy scale of P, in the energy unit of H; default
                               10 Ry = 136.0569 eV (Table 1, OMM.TPreconScale) */
+    double screen_eps;     /* norm-based screening of the block products of the sparse form
+                              (the filtered block multiply of the DBCSR library the paper's
+                              linear-scaling solver runs on, section "Solver library"): a
+                              block product A_ik B_kj of H'W, SW, H'D, SD, W^T(H'W), W^T(SW),
+                              W^T(H'D), W^T(SD), D^T(H'D), D^T(SD), (SW) H_W or (H'W) S_W is
+                              skipped when ||A_ik||_F ||B_kj||_F < screen_eps (compared as
+                              squared norms against screen_eps^2).  Each skipped product
+                              changes its output block by less than screen_eps in Frobenius
+                              norm; stored patterns never change.  The squared norms of every
+                              operand block are kept on the device (about 8 doubles per
+                              block of H, W, H'W and W^T H W).  0 (default): off; must be
+                              finite and >= 0 (OMM_ERR_ARG); ignored by dense handles */
 } omm_options;
 
 enum {
@@ -414,11 +426,13 @@ int omm_op_quartic_coeffs(int64_t n, const double *h0, const double *s0, int64_t
  * the scratch is a static device array of omm_op_quartic_coeffs_static_max_bytes()
  * bytes (53,504) held by every GPU that loads the library until the process
  * exits.  The kernel never launches more blocks than that array has partial
- * slots for; a size whose launch would need more is rejected with
- * OMM_ERR_ARG and a message in omm_last_error(), as is n outside
- * [0, 2^31 - 1].  The first call on each device looks up the array's device
- * address and zeroes its completion counter (synchronous CUDA calls), so make
- * that first call before any stream capture.  All calls share the one array
+ * slots for, so every n in [0, 2^31 - 1] fits; n outside that range, a NULL
+ * input or output, or ld_h, ld_z < n is rejected with OMM_ERR_ARG and a
+ * message in omm_last_error().  Every call looks up the array's device address
+ * with the current device; the first call on a device (and the first after a
+ * device reset moved the array) also zeroes its completion counter and
+ * synchronises the device, so make that first call before any stream capture.
+ * All calls share the one array
  * and the kernel leaves the counter at zero for the next call: calls that may
  * overlap on the GPU (different streams, other host threads) race and must be
  * serialised by the caller.  Allocates nothing.
@@ -436,6 +450,24 @@ int omm_op_quartic_coeffs_static(int64_t n, const double *h0, const double *s0, 
  * wins, ties go to the smaller |x|, then to x > 0.
  */
 int omm_op_line_min(const double *coeffs, double *x_out, int32_t *status_out, void *stream);
+
+/*
+ * The integer-pipe conversions the solve's kernels inline (FP64 conversions
+ * issue on the narrow FP64 unit of this part), element by element over device
+ * arrays, so that each can be compared with the hardware conversion.  The
+ * paper has no counterpart; this is a self-test of the arithmetic of the mixed
+ * form.  op:
+ *   0  in double[n] -> out float[n]: round to nearest even; |x| < 2^-126 gives a
+ *      signed zero, overflow an infinity, NaN a quiet NaN;
+ *   1  in float[n] -> out double[n]: exact (subnormals included);
+ *   2  in int64[n], e int32[n] -> out double[n] = in * 2^e rounded to nearest
+ *      even (the caller keeps the result normal);
+ *   3  in double[n], e int32[n] -> out double[n] = in * 2^e (exact when the
+ *      result is normal; otherwise as ldexp).
+ * Asynchronous on `stream`; OMM_ERR_ARG for op outside 0..3, n < 0 or a NULL
+ * array (e is read only by ops 2 and 3).
+ */
+int omm_op_convert(int32_t op, int64_t n, const void *in, const int32_t *e, void *out, void *stream);
 
 /*
  * Split-precision tensor-core GEMM  C = alpha op(A) op(B) + beta Cin  (FP64 in

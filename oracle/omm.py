@@ -499,9 +499,19 @@ def omm_cg_screened(H, S, W0, bm: int, bn: int, eps: float, tol: float = 1e-10,
       start:  H'W, SW; H_W = W^T (H'W), S_W = W^T (SW);
       step:   G = 2 (2 H'W - (SW) H_W - (H'W) S_W) on W's pattern; D;
               H'D, SD; X = W^T (H'D), Y = W^T (SD), h2 = D^T (H'D), s2 = D^T (SD);
-              the line quartic of H_W(x) = H_W + x (X + X^T) + x^2 h2 and
-              S_W(x) = S_W + x (Y + Y^T) + x^2 s2 (H' and S symmetric);
-              W, H'W, SW, H_W, S_W carried to W + x D by the same expansions.
+              the line quartic's coefficients written out from
+              H_W(x) = H_W + x (X + X^T) + x^2 h2, S_W(x) = S_W + x (Y + Y^T) + x^2 s2
+              (H' and S symmetric) and E~(x) = 2 (2 tr H_W(x) - <S_W(x), H_W(x)>):
+                c0 = 2 (2 tr H_W - <S_W, H_W>)
+                c1 = 2 (4 tr X - 2 <S_W, X> - 2 <Y, H_W>)
+                c2 = 2 (2 tr h2 - <S_W, h2> - 2 (<Y, X> + <Y, X^T>) - <s2, H_W>)
+                c3 = 2 (-2 <Y, h2> - 2 <s2, X>)
+                c4 = -2 <s2, h2>;
+              W, H'W, SW carried to W + x D, and H_W, S_W by the expansions
+              above with h2, s2 replaced by their symmetric parts.
+    Screening makes X^T differ from D^T (H'W) and h2 from its transpose at
+    the level of the skipped products; the forms above are the reading taken
+    for a screened step (without screening they equal the definitions).
     Blocks: bm x bm for H and S, bm x bn for W (basis atom x orbitals of one
     atom), bn x bn for the n x n matrices.  Dense arrays in, zero blocks
     standing for blocks that are not stored.  With eps = 0 nothing is skipped
@@ -535,21 +545,20 @@ def omm_cg_screened(H, S, W0, bm: int, bn: int, eps: float, tol: float = 1e-10,
         HD, SD = P(Hs, D, bm, bm, bn), P(S, D, bm, bm, bn)
         X, Y = P(W.T, HD, bn, bm, bn), P(W.T, SD, bn, bm, bn)
         h2, s2 = P(D.T, HD, bn, bm, bn), P(D.T, SD, bn, bm, bn)
-        A_ = [h0, X + X.T, h2]
-        B_ = [s0, Y + Y.T, s2]
-        c = np.zeros(5)
-        for i in range(3):
-            c[i] += 2.0 * 2.0 * np.trace(A_[i])
-            for j in range(3):
-                c[i + j] -= 2.0 * frob(B_[i], A_[j])
+        c = np.array([
+            2.0 * (2.0 * np.trace(h0) - frob(s0, h0)),
+            2.0 * (4.0 * np.trace(X) - 2.0 * frob(s0, X) - 2.0 * frob(Y, h0)),
+            2.0 * (2.0 * np.trace(h2) - frob(s0, h2) - 2.0 * (frob(Y, X) + frob(Y, X.T)) - frob(s2, h0)),
+            2.0 * (-2.0 * frob(Y, h2) - 2.0 * frob(s2, X)),
+            -2.0 * frob(s2, h2)])
         x, st = line_min(c)
         if st != OK:
             status = st
             break
         W = W + x * D
         HW, SW = HW + x * HD, SW + x * SD
-        h0 = h0 + x * A_[1] + x * x * h2
-        s0 = s0 + x * B_[1] + x * x * s2
+        h0 = h0 + x * (X + X.T) + x * x * (0.5 * (h2 + h2.T))
+        s0 = s0 + x * (Y + Y.T) + x * x * (0.5 * (s2 + s2.T))
         E_prev, G_prev = E, G
         k += 1
     return Result(W=W, E=E, E_unshifted=functional(W, H, S), iters=k, status=status, eta=eta,

@@ -687,12 +687,19 @@ constexpr int64_t kCoeffPartialsBytes = (int64_t)omm::kRedBlocksMax * 13 * (int6
 constexpr int64_t kCoeffStaticBytes = kCoeffPartialsBytes + 256;   // + the counter, own 256-byte slot
 static __device__ __align__(256) unsigned char g_coeff_scratch[kCoeffStaticBytes];
 
+// red_blocks_for_tiles never launches more than kRedBlocksMax blocks, so every
+// n in [0, 2^31 - 1] fits the array.
+static_assert(kCoeffPartialsBytes >= (int64_t)omm::kRedBlocksMax * 13 * (int64_t)sizeof(double),
+              "one partial-sum slot per block of the largest launch");
+
 constexpr int kMaxDevices = 64;
 std::mutex g_coeff_mu;
-void *g_coeff_ptr[kMaxDevices] = {};   // device address of g_coeff_scratch, per device
+void *g_coeff_ptr[kMaxDevices] = {};   // device address of g_coeff_scratch last seen, per device
 
-// Once per device, with that device current: look up the array's device
-// address (its host-side name is only a stand-in) and zero the counter.
+// With the device current: look up the array's device address (its host-side
+// name is only a stand-in).  The lookup runs on every call, so a module loaded
+// again after a device reset is found at its new address; the counter is zeroed
+// (synchronously, before any kernel may use it) the first time an address is seen.
 int coeff_scratch_for_current_device(void **out) {
     int dev = -1;
     OMM_CUDA_TRY(cudaGetDevice(&dev));
@@ -700,14 +707,15 @@ int coeff_scratch_for_current_device(void **out) {
         omm::set_error("omm_op_quartic_coeffs_static: device ordinal %d outside 0..%d", dev, kMaxDevices - 1);
         return OMM_ERR_ARG;
     }
+    void *p = nullptr;
+    OMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_coeff_scratch));
     std::lock_guard<std::mutex> lock(g_coeff_mu);
-    if (g_coeff_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        OMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_coeff_scratch));
+    if (g_coeff_ptr[dev] != p) {
         OMM_CUDA_TRY(cudaMemset((char *)p + kCoeffPartialsBytes, 0, 256));
+        OMM_CUDA_TRY(cudaDeviceSynchronize());
         g_coeff_ptr[dev] = p;
     }
-    *out = g_coeff_ptr[dev];
+    *out = p;
     return OMM_OK;
 }
 }  // namespace
@@ -721,18 +729,21 @@ extern "C" int omm_op_quartic_coeffs_static(int64_t n, const double *h0, const d
         omm::set_error("omm_op_quartic_coeffs_static: n = %lld outside 0..2147483647", (long long)n);
         return OMM_ERR_ARG;
     }
-    // scratch this launch needs: partials of every block it launches + the counter
-    const int64_t blocks = omm::red_blocks_for_tiles((int)n);
-    const int64_t need = blocks * 13 * (int64_t)sizeof(double);
-    if (need > kCoeffPartialsBytes) {
-        omm::set_error("omm_op_quartic_coeffs_static: n = %lld needs %lld bytes of scratch, the static "
-                       "array holds %lld", (long long)n, (long long)need, (long long)kCoeffPartialsBytes);
+    const int64_t blocks = omm::red_blocks_for_tiles((int)n);   // at most kRedBlocksMax
+    if (coeffs == nullptr) {
+        omm::set_error("omm_op_quartic_coeffs_static: coeffs is NULL");
         return OMM_ERR_ARG;
     }
-    if (coeffs == nullptr) return OMM_ERR_ARG;
     if (n > 0 && (h0 == nullptr || s0 == nullptr || X == nullptr || Y == nullptr || h2 == nullptr ||
-                  s2 == nullptr || ld_h < n || ld_z < n))
+                  s2 == nullptr)) {
+        omm::set_error("omm_op_quartic_coeffs_static: an input array is NULL with n = %lld", (long long)n);
         return OMM_ERR_ARG;
+    }
+    if (n > 0 && (ld_h < n || ld_z < n)) {
+        omm::set_error("omm_op_quartic_coeffs_static: ld_h = %lld, ld_z = %lld below n = %lld", (long long)ld_h,
+                       (long long)ld_z, (long long)n);
+        return OMM_ERR_ARG;
+    }
     void *scratch = nullptr;
     const int rc = coeff_scratch_for_current_device(&scratch);
     if (rc != OMM_OK) return rc;

@@ -5,9 +5,11 @@
 // so kernels that convert every element become conversion-bound.  These
 // versions take the IEEE-754 bit fields apart with integer instructions.
 // d2f rounds to nearest, ties to even, exactly like the hardware conversion
-// for every double whose float result is a normal number or zero; results
-// that would be subnormal flush to a signed zero and overflow saturates to
-// infinity.  f2d is exact for every finite float.
+// for every double of magnitude at least 2^-126 (the smallest normal float);
+// a smaller magnitude gives a signed zero (the hardware would round to a
+// subnormal float, or up to 2^-126), overflow gives a signed infinity, and a
+// NaN gives a quiet NaN.  f2d is exact for every float, subnormals included
+// (a NaN keeps its payload bits).
 #pragma once
 
 #include <stdint.h>
@@ -17,10 +19,12 @@ namespace omm {
 __device__ __forceinline__ float sw_d2f(double d) {
     const uint64_t b = (uint64_t)__double_as_longlong(d);
     const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;   // biased float exponent
+    const int de = (int)((b >> 52) & 0x7FF);                 // biased double exponent
+    const int e = de - 1023 + 127;                           // biased float exponent
     const uint64_t m = b & 0xFFFFFFFFFFFFFull;               // 52-bit fraction
-    if (e <= 0) return __uint_as_float(sign);               // zero, subnormal range: signed zero
-    if (e >= 255) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));  // inf / nan
+    if (de == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));  // inf / nan
+    if (e <= 0) return __uint_as_float(sign);               // below 2^-126: signed zero
+    if (e >= 255) return __uint_as_float(sign | 0x7F800000u);   // overflow: infinity
     uint32_t f = ((uint32_t)e << 23) | (uint32_t)(m >> 29);
     const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFu);       // 29 dropped bits
     if (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) f += 1u;   // may carry into the exponent
@@ -35,9 +39,10 @@ __device__ __forceinline__ double sw_f2d(float x) {
     if (e == 0) {
         if (m == 0) return __longlong_as_double((long long)sign);
         // subnormal float: normalise
+        // m 2^-149 with the leading one at bit p = 23 - lz: 1.f x 2^(p - 149)
         const int lz = __clz((int)m) - 8;                      // leading zeros inside the 23-bit field
         const uint64_t mm = (m << (lz + 1)) & 0x7FFFFFull;
-        const uint64_t ed = (uint64_t)(1023 - 127 - lz);
+        const uint64_t ed = (uint64_t)(1023 - 126 - lz);
         return __longlong_as_double((long long)(sign | (ed << 52) | (mm << 29)));
     }
     if (e == 255) return __longlong_as_double((long long)(sign | (0x7FFull << 52) | (m << 29)));

@@ -673,18 +673,31 @@ int mixed_iteration(omm_handle *h, bool accurate_gradient) {
 }
 
 // ---------------------------------------------------------------- linear-scaling form
+// With screening on (omm_options.screen_eps > 0) each product skips the block
+// pairs whose norm product is below eps; the squared block norms of every
+// operand are refreshed right after the operand is written (omm::sp::norms is a
+// no-op otherwise, and the nullptr norm arguments select the plain kernels).
 int sparse_start(omm_handle *h) {
     omm::sp::Dev &d = h->sd;
     cudaStream_t st = h->stream;
     omm::DevState *s = h->dstate;
-    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(omm::sp::products(d, d.W, d.HW, d.SW, s, st)); }
+    const bool sc = d.screening();
+    { StageTimer t(h, OMM_STAGE_PRODUCTS);
+      TRY(omm::sp::norms(d, omm::sp::NRM_W, s, st));
+      TRY(omm::sp::products(d, d.W, d.HW, d.SW, sc ? d.nW : nullptr, s, st));
+      TRY(omm::sp::norms(d, omm::sp::NRM_HWSW, s, st)); }
     // H_W = W^T H'W and S_W = W^T S W through the contraction kernel (D := W)
-    { StageTimer t(h, OMM_STAGE_CONTRACT); TRY(omm::sp::contract(d, d.W, d.W, d.HW, d.SW, d.h0, d.s0, d.h2, d.s2, s, st)); }
+    { StageTimer t(h, OMM_STAGE_CONTRACT);
+      TRY(omm::sp::contract(d, d.W, d.W, d.HW, d.SW, d.h0, d.s0, d.h2, d.s2, sc ? d.nW : nullptr, d.nW, d.nHW,
+                            d.nSW, s, st)); }
     TRY(omm::sp::nn_update(d, h->n, 1, scr(h, 1), ctr(h, 1), s, st));
-    { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(omm::sp::gradient(d, s, st)); }
+    { StageTimer t(h, OMM_STAGE_GRADIENT);
+      TRY(omm::sp::norms(d, omm::sp::NRM_N, s, st));
+      TRY(omm::sp::gradient(d, s, st)); }
     { StageTimer t(h, OMM_STAGE_DIRECTION);
       TRY(omm::sp::dots(d, 1, scr(h, 2), ctr(h, 2), s, st));
-      TRY(omm::sp::direction(d, s, st)); }
+      TRY(omm::sp::direction(d, s, st));
+      TRY(omm::sp::norms(d, omm::sp::NRM_D, s, st)); }
     return OMM_OK;
 }
 
@@ -692,16 +705,23 @@ int sparse_iteration(omm_handle *h) {
     omm::sp::Dev &d = h->sd;
     cudaStream_t st = h->stream;
     omm::DevState *s = h->dstate;
-    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(omm::sp::products(d, d.D, d.HD, d.SD, s, st)); }
-    { StageTimer t(h, OMM_STAGE_CONTRACT); TRY(omm::sp::contract(d, d.W, d.D, d.HD, d.SD, d.X, d.Y, d.h2, d.s2, s, st)); }
+    const bool sc = d.screening();
+    { StageTimer t(h, OMM_STAGE_PRODUCTS);
+      TRY(omm::sp::products(d, d.D, d.HD, d.SD, sc ? d.nD : nullptr, s, st));
+      TRY(omm::sp::norms(d, omm::sp::NRM_HDSD, s, st)); }
+    { StageTimer t(h, OMM_STAGE_CONTRACT);
+      TRY(omm::sp::contract(d, d.W, d.D, d.HD, d.SD, d.X, d.Y, d.h2, d.s2, sc ? d.nW : nullptr, d.nD, d.nHD,
+                            d.nSD, s, st)); }
     { StageTimer t(h, OMM_STAGE_LINESEARCH); TRY(omm::sp::coeffs(d, scr(h, 0), ctr(h, 0), s, st)); }
     { StageTimer t(h, OMM_STAGE_UPDATE);
       TRY(omm::sp::axpy(d, s, st));
-      TRY(omm::sp::nn_update(d, h->n, 0, scr(h, 1), ctr(h, 1), s, st)); }
+      TRY(omm::sp::nn_update(d, h->n, 0, scr(h, 1), ctr(h, 1), s, st));
+      TRY(omm::sp::norms(d, omm::sp::NRM_W | omm::sp::NRM_HWSW | omm::sp::NRM_N, s, st)); }
     { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(omm::sp::gradient(d, s, st)); }
     { StageTimer t(h, OMM_STAGE_DIRECTION);
       TRY(omm::sp::dots(d, 0, scr(h, 2), ctr(h, 2), s, st));
-      TRY(omm::sp::direction(d, s, st)); }
+      TRY(omm::sp::direction(d, s, st));
+      TRY(omm::sp::norms(d, omm::sp::NRM_D, s, st)); }
     return OMM_OK;
 }
 
@@ -936,6 +956,7 @@ void omm_default_options(omm_options *opt) {
     opt->n_occupied = 0;
     opt->precon = 0;
     opt->tau_T = 136.05693122994;   // 10 Ry in eV
+    opt->screen_eps = 0.0;
 }
 
 const char *omm_status_str(int status) {
@@ -982,7 +1003,8 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         h->opt.exact_digits < 1 || h->opt.exact_digits > omm::tc::kExactMaxDigits || h->opt.split_digits < 2 ||
         h->opt.split_digits > 3 || h->opt.n_occupied < 0 || h->opt.n_occupied > n ||
         (h->opt.n_occupied > 0 && h->opt.n_occupied < n && h->opt.eta_auto) ||
-        (h->opt.precon != 0 && !(h->opt.tau_T > 0.0 && isfinite(h->opt.tau_T)))) {
+        (h->opt.precon != 0 && !(h->opt.tau_T > 0.0 && isfinite(h->opt.tau_T))) ||
+        !(h->opt.screen_eps >= 0.0 && isfinite(h->opt.screen_eps))) {
         delete h;
         return OMM_ERR_ARG;
     }
@@ -1017,6 +1039,7 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         P.Wrp = pattern->W_rowptr;
         P.Wcol = pattern->W_col;
         if ((rc = omm::sp::build(P, h->sh)) || (rc = omm::sp::upload(h->sh, h->sd)) ||
+            (rc = omm::sp::screen_alloc(h->sd, h->opt.screen_eps)) ||
             (rc = dalloc(&h->scratch, (size_t)(4 * omm::kRedBlocksMax * omm::kRedSlots))) ||
             (rc = dalloc(&h->counters, (size_t)(64 * 8))) || (rc = dalloc(&h->dstate, 1))) {
             free_handle(h);

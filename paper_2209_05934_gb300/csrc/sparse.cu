@@ -487,11 +487,16 @@ __global__ void __launch_bounds__(NT) gershgorin_kernel(int64_t nbr, int bm, con
 
 // ---- products: HD_o = sum H'_(I,K) D_(K,J), SD_o likewise; warp per P_HW block,
 // lanes 0..15 -> H'D element (r, c), lanes 16..31 -> SD element.
-template <int BM, int BN>
+// Screening (SCREEN): the block product H'_(I,K) D_(K,J) (or S_(I,K) D_(K,J)) is
+// skipped when ||H'_(I,K)||^2 ||D_(K,J)||^2 < eps^2, from the squared block norms
+// nHS ([nnzH][2]: H', S) and nB (one per D block).
+template <int BM, int BN, bool SCREEN>
 __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64_t *__restrict__ Prp,
                                                        const int32_t *__restrict__ Ph, const int32_t *__restrict__ Pw,
                                                        const double *__restrict__ HS, const double *__restrict__ D,
-                                                       double *HD, double *SD, const DevState *state) {
+                                                       double *HD, double *SD, const double *__restrict__ nHS,
+                                                       const double *__restrict__ nB, double eps2,
+                                                       const DevState *state) {
     if (done(state)) return;
     const int lane = threadIdx.x & 31;
     constexpr int NE = BM * BN;          // outputs per block
@@ -502,6 +507,7 @@ __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64
     for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; o < nnzHW; o += nwarps) {
         double acc = 0.0;
         for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
+            if (SCREEN && nHS[(int64_t)Ph[t] * 2 + which] * nB[Pw[t]] < eps2) continue;
             const double *A = HS + ((int64_t)Ph[t] * 2 + which) * BM * BM + r * BM;
             const double *B = D + (int64_t)Pw[t] * BM * BN + c;
             if (active) {
@@ -515,13 +521,17 @@ __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64
 
 // ---- contractions on P_N: warp per N block q; 16 outputs (X, Y, h2, s2 of 2x2)
 // with two lanes each splitting the basis index k.
-template <int BM, int BN>
+// Screening: the pair (L block a, R block b) is skipped when ||L_a||^2 ||R_b||^2 < eps^2,
+// with L = W or D and R = H'D or SD as the output matrix takes them.
+template <int BM, int BN, bool SCREEN>
 __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_t *__restrict__ Crp,
                                                        const int32_t *__restrict__ Ca, const int32_t *__restrict__ Cb,
                                                        const double *__restrict__ W, const double *__restrict__ D,
                                                        const double *__restrict__ HD, const double *__restrict__ SD,
                                                        double *X, double *Y, double *h2, double *s2,
-                                                       const DevState *state) {
+                                                       const double *__restrict__ nW, const double *__restrict__ nD,
+                                                       const double *__restrict__ nHD, const double *__restrict__ nSD,
+                                                       double eps2, const DevState *state) {
     if (done(state)) return;
     const int lane = threadIdx.x & 31;
     static_assert(BN == 2, "contraction lanes assume 2 orbitals per W block");
@@ -530,10 +540,13 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
     const double *L = (mat < 2) ? W : D;
     const double *R = (mat == 0 || mat == 2) ? HD : SD;
     double *out = mat == 0 ? X : mat == 1 ? Y : mat == 2 ? h2 : s2;
+    const double *nL = SCREEN ? ((mat < 2) ? nW : nD) : nullptr;
+    const double *nR = SCREEN ? ((mat == 0 || mat == 2) ? nHD : nSD) : nullptr;
     const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
     for (int64_t q = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; q < nnzN; q += nwarps) {
         double acc = 0.0;
         for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
+            if (SCREEN && nL[Ca[t]] * nR[Cb[t]] < eps2) continue;
             const double *l = L + (int64_t)Ca[t] * BM * BN + a;
             const double *rr = R + (int64_t)Cb[t] * BM * BN + b;
 #pragma unroll
@@ -549,13 +562,17 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
 
 // ---- gradient on P_W: G_o = 2 (2 H'W_o - sum (SW_(I,K) h0_(K,J) + H'W_(I,K) s0_(K,J)))
 // half-warp per W block, one lane per element (r, c).
-template <int BM, int BN>
+// Screening: SW_(I,K) h0_(K,J) and H'W_(I,K) s0_(K,J) are skipped separately when
+// the product of their squared block norms is below eps^2.
+template <int BM, int BN, bool SCREEN>
 __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_t *__restrict__ Grp,
                                                        const int32_t *__restrict__ Gb, const int32_t *__restrict__ Gq,
                                                        const int32_t *__restrict__ WtoHW, const double *__restrict__ HW,
                                                        const double *__restrict__ SW, const double *__restrict__ h0,
                                                        const double *__restrict__ s0, double *G,
-                                                       const DevState *state) {
+                                                       const double *__restrict__ nHW, const double *__restrict__ nSW,
+                                                       const double *__restrict__ nh0, const double *__restrict__ ns0,
+                                                       double eps2, const DevState *state) {
     if (done(state)) return;
     const int e = threadIdx.x & 15;
     if (e >= BM * BN) return;
@@ -568,6 +585,15 @@ __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_
         const double *hw = HW + (int64_t)Gb[t] * BM * BN + r * BN;
         const double *hq = h0 + (int64_t)Gq[t] * BN * BN + c;
         const double *sq = s0 + (int64_t)Gq[t] * BN * BN + c;
+        if (SCREEN) {
+            const bool use_s = !(nSW[Gb[t]] * nh0[Gq[t]] < eps2), use_h = !(nHW[Gb[t]] * ns0[Gq[t]] < eps2);
+#pragma unroll
+            for (int k = 0; k < BN; ++k) {
+                if (use_s) acc = fma(sw[k], hq[k * BN], acc);
+                if (use_h) acc = fma(hw[k], sq[k * BN], acc);
+            }
+            continue;
+        }
 #pragma unroll
         for (int k = 0; k < BN; ++k) {
             acc = fma(sw[k], hq[k * BN], acc);
@@ -829,6 +855,33 @@ __global__ void __launch_bounds__(NT) density_rho_kernel(int64_t nnzH, const int
     }
 }
 
+// ---- squared Frobenius norms of blocks, for screening: one thread per block,
+// up to four arrays per launch
+struct NormJob {
+    const double *vals;
+    double *out;
+    int64_t nblocks;
+    int bs;                 // values per block
+};
+struct NormJobs {
+    NormJob j[4];
+    int n;
+};
+
+__global__ void norms_kernel(NormJobs jobs, const DevState *state) {
+    if (done(state)) return;
+    for (int q = 0; q < jobs.n; ++q) {
+        const NormJob J = jobs.j[q];
+        for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < J.nblocks;
+             b += (int64_t)gridDim.x * blockDim.x) {
+            const double *v = J.vals + b * J.bs;
+            double s = 0.0;
+            for (int t = 0; t < J.bs; ++t) s = fma(v[t], v[t], s);
+            J.out[b] = s;
+        }
+    }
+}
+
 int blocks_for(int64_t work, int per) {
     int64_t nb = ceil_div(work, per);
     if (nb > 152 * 16) nb = 152 * 16;
@@ -892,7 +945,7 @@ void release(Dev &d) {
     void *ptrs[] = {d.Trp, d.Rrp, d.Tw, d.Tq, d.Rt, d.Rw, d.K, d.T,
                     d.Hrp, d.Hcol, d.Prp, d.Ph, d.Pw, d.Crp, d.Ca, d.Cb, d.Grp, d.Gb, d.Gq, d.WtoHW, d.Ntr,
                     d.Ndiag, d.HS, d.Hin, d.W, d.D, d.G, d.Gp, d.HW, d.SW, d.HD, d.SD, d.h0, d.s0, d.X,
-                    d.Y, d.h2, d.s2, d.keep};
+                    d.Y, d.h2, d.s2, d.keep, d.nrm};
     for (void *p : ptrs) cudaFree(p);
     d = Dev{};
 }
@@ -913,7 +966,7 @@ int set_HS(Dev &d, const double *H, const double *S, bool on_device, double eps,
     }
     shift_pack_kernel<<<blocks_for(d.nnzH * bb, 256), 256, 0, st>>>(d.nnzH, (int)bb, Hc, Sc, d.keep, state, d.HS);
     LAUNCHED();
-    return OMM_OK;
+    return norms(d, NRM_HS, nullptr, st);
 }
 
 #define DISPATCH_BLOCKS(BMv, BNv, CALL)                              \
@@ -922,17 +975,77 @@ int set_HS(Dev &d, const double *H, const double *S, bool on_device, double eps,
         else return OMM_ERR_UNSUPPORTED;                             \
     } while (0)
 
-int products(Dev &d, const double *Din, double *HDo, double *SDo, const DevState *state, cudaStream_t st) {
-    DISPATCH_BLOCKS(d.bm, d.bn, (products_kernel<BM, BN><<<blocks_for(d.nnzHW * 32, NT), NT, 0, st>>>(
-                                     d.nnzHW, d.Prp, d.Ph, d.Pw, d.HS, Din, HDo, SDo, state)));
+int screen_alloc(Dev &d, double eps) {
+    if (!(eps > 0.0)) return OMM_OK;
+    const int64_t total = 2 * d.nnzH + 2 * d.nnzW + 4 * d.nnzHW + 2 * d.nnzN;
+    if (cudaMalloc((void **)&d.nrm, (size_t)(total > 0 ? total : 1) * sizeof(double)) != cudaSuccess)
+        return OMM_ERR_NOMEM;
+    d.screen_eps2 = eps * eps;
+    d.nHS = d.nrm;
+    d.nW = d.nHS + 2 * d.nnzH;
+    d.nD = d.nW + d.nnzW;
+    d.nHW = d.nD + d.nnzW;
+    d.nSW = d.nHW + d.nnzHW;
+    d.nHD = d.nSW + d.nnzHW;
+    d.nSD = d.nHD + d.nnzHW;
+    d.nh0 = d.nSD + d.nnzHW;
+    d.ns0 = d.nh0 + d.nnzN;
+    return OMM_OK;
+}
+
+int norms(Dev &d, int which, const DevState *state, cudaStream_t st) {
+    if (!d.screening()) return OMM_OK;
+    const int bb = d.bm * d.bm, bw = d.bm * d.bn, bq = d.bn * d.bn;
+    NormJobs jobs{};
+    auto add = [&](const double *v, double *o, int64_t nb, int bs) { jobs.j[jobs.n++] = NormJob{v, o, nb, bs}; };
+    auto flush = [&]() -> int {
+        if (jobs.n == 0) return OMM_OK;
+        int64_t most = 0;
+        for (int q = 0; q < jobs.n; ++q) most = std::max(most, jobs.j[q].nblocks);
+        norms_kernel<<<blocks_for(most, 256), 256, 0, st>>>(jobs, state);
+        LAUNCHED();
+        jobs.n = 0;
+        return OMM_OK;
+    };
+    int rc;
+    if (which & NRM_HS) add(d.HS, d.nHS, 2 * d.nnzH, bb);
+    if (which & NRM_W) add(d.W, d.nW, d.nnzW, bw);
+    if (which & NRM_D) add(d.D, d.nD, d.nnzW, bw);
+    if ((rc = flush())) return rc;
+    if (which & NRM_HWSW) { add(d.HW, d.nHW, d.nnzHW, bw); add(d.SW, d.nSW, d.nnzHW, bw); }
+    if (which & NRM_HDSD) { add(d.HD, d.nHD, d.nnzHW, bw); add(d.SD, d.nSD, d.nnzHW, bw); }
+    if ((rc = flush())) return rc;
+    if (which & NRM_N) { add(d.h0, d.nh0, d.nnzN, bq); add(d.s0, d.ns0, d.nnzN, bq); }
+    return flush();
+}
+
+int products(Dev &d, const double *Din, double *HDo, double *SDo, const double *nDin, const DevState *state,
+             cudaStream_t st) {
+    if (nDin != nullptr && d.screening()) {
+        DISPATCH_BLOCKS(d.bm, d.bn, (products_kernel<BM, BN, true><<<blocks_for(d.nnzHW * 32, NT), NT, 0, st>>>(
+                                         d.nnzHW, d.Prp, d.Ph, d.Pw, d.HS, Din, HDo, SDo, d.nHS, nDin,
+                                         d.screen_eps2, state)));
+    } else {
+        DISPATCH_BLOCKS(d.bm, d.bn, (products_kernel<BM, BN, false><<<blocks_for(d.nnzHW * 32, NT), NT, 0, st>>>(
+                                         d.nnzHW, d.Prp, d.Ph, d.Pw, d.HS, Din, HDo, SDo, nullptr, nullptr, 0.0,
+                                         state)));
+    }
     LAUNCHED();
     return OMM_OK;
 }
 
 int contract(Dev &d, const double *Wl, const double *Dl, const double *HDr, const double *SDr, double *Xo,
-             double *Yo, double *h2o, double *s2o, const DevState *state, cudaStream_t st) {
-    DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
-                                     d.nnzN, d.Crp, d.Ca, d.Cb, Wl, Dl, HDr, SDr, Xo, Yo, h2o, s2o, state)));
+             double *Yo, double *h2o, double *s2o, const double *nWl, const double *nDl, const double *nHDr,
+             const double *nSDr, const DevState *state, cudaStream_t st) {
+    if (nWl != nullptr && d.screening()) {
+        DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, true><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
+                                         d.nnzN, d.Crp, d.Ca, d.Cb, Wl, Dl, HDr, SDr, Xo, Yo, h2o, s2o, nWl, nDl,
+                                         nHDr, nSDr, d.screen_eps2, state)));
+    } else {
+        DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, false><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
+                                         d.nnzN, d.Crp, d.Ca, d.Cb, Wl, Dl, HDr, SDr, Xo, Yo, h2o, s2o, nullptr,
+                                         nullptr, nullptr, nullptr, 0.0, state)));
+    }
     LAUNCHED();
     return OMM_OK;
 }
@@ -960,8 +1073,10 @@ int upload_density(const DensHost &dh, Dev &d) {
 int density(Dev &d, int mode, double eta, double *out, cudaStream_t st) {
     // H'W, SW on P_HW and H'_W = W^T H'W, S_W = W^T SW on P_N, afresh from W
     int rc;
-    if ((rc = products(d, d.W, d.HD, d.SD, nullptr, st))) return rc;
-    if ((rc = contract(d, d.W, d.W, d.HD, d.SD, d.X, d.Y, d.h2, d.s2, nullptr, st))) return rc;
+    if ((rc = products(d, d.W, d.HD, d.SD, nullptr, nullptr, st))) return rc;
+    if ((rc = contract(d, d.W, d.W, d.HD, d.SD, d.X, d.Y, d.h2, d.s2, nullptr, nullptr, nullptr, nullptr, nullptr,
+                       st)))
+        return rc;
     const int64_t bb = (int64_t)d.bn * d.bn;
     density_K_kernel<<<blocks_for(d.nnzN * bb, 256), 256, 0, st>>>(d.nnzN, d.bn, d.Ndiag, d.X, d.Y, mode, eta, d.K);
     LAUNCHED();
@@ -975,8 +1090,15 @@ int density(Dev &d, int mode, double eta, double *out, cudaStream_t st) {
 }
 
 int gradient(Dev &d, const DevState *state, cudaStream_t st) {
-    DISPATCH_BLOCKS(d.bm, d.bn, (gradient_kernel<BM, BN><<<blocks_for(d.nnzW * 16, NT), NT, 0, st>>>(
-                                     d.nnzW, d.Grp, d.Gb, d.Gq, d.WtoHW, d.HW, d.SW, d.h0, d.s0, d.G, state)));
+    if (d.screening()) {
+        DISPATCH_BLOCKS(d.bm, d.bn, (gradient_kernel<BM, BN, true><<<blocks_for(d.nnzW * 16, NT), NT, 0, st>>>(
+                                         d.nnzW, d.Grp, d.Gb, d.Gq, d.WtoHW, d.HW, d.SW, d.h0, d.s0, d.G, d.nHW,
+                                         d.nSW, d.nh0, d.ns0, d.screen_eps2, state)));
+    } else {
+        DISPATCH_BLOCKS(d.bm, d.bn, (gradient_kernel<BM, BN, false><<<blocks_for(d.nnzW * 16, NT), NT, 0, st>>>(
+                                         d.nnzW, d.Grp, d.Gb, d.Gq, d.WtoHW, d.HW, d.SW, d.h0, d.s0, d.G, nullptr,
+                                         nullptr, nullptr, nullptr, 0.0, state)));
+    }
     LAUNCHED();
     return OMM_OK;
 }

@@ -61,7 +61,17 @@ struct Dev {
     int64_t *Trp = nullptr, *Rrp = nullptr;
     int32_t *Tw = nullptr, *Tq = nullptr, *Rt = nullptr, *Rw = nullptr;
     double *K = nullptr, *T = nullptr;
+    // norm-based screening of the block products (allocated when eps > 0): squared
+    // Frobenius norms of H' and S ([nnzH][2]), W, D, H'W, SW, H'D, SD, H_W, S_W blocks
+    double screen_eps2 = 0.0;
+    double *nrm = nullptr;
+    double *nHS = nullptr, *nW = nullptr, *nD = nullptr, *nHW = nullptr, *nSW = nullptr, *nHD = nullptr,
+           *nSD = nullptr, *nh0 = nullptr, *ns0 = nullptr;
+    bool screening() const { return screen_eps2 > 0.0; }
 };
+
+// which block norms to refresh (norms())
+enum { NRM_HS = 1, NRM_W = 2, NRM_D = 4, NRM_HWSW = 8, NRM_HDSD = 16, NRM_N = 32 };
 
 // Validate the caller's patterns and build everything host-side (OMM_ERR_PATTERN on malformed input).
 int build(const Pattern &P, Host &out);
@@ -78,10 +88,21 @@ int upload_density(const DensHost &dh, Dev &d);
 // P_H's CSR order), from W with S_W and H'_W formed afresh
 int density(Dev &d, int mode, double eta, double *out, cudaStream_t st);
 
-// One step's pieces
-int products(Dev &d, const double *Din, double *HDo, double *SDo, const DevState *state, cudaStream_t st);
+// Norm-based screening of the CG's block products: a block product A_ik B_kj is
+// skipped when ||A_ik||_F ||B_kj||_F < eps (squared norms compared with eps^2).
+// eps <= 0 leaves screening off and allocates nothing.
+int screen_alloc(Dev &d, double eps);
+// refresh the squared norms named by `which` (NRM_* flags); no-op when screening is off
+int norms(Dev &d, int which, const DevState *state, cudaStream_t st);
+
+// One step's pieces.  The n* arguments are the squared norms of the right-hand
+// operand blocks (products: of Din; contract: of W-side, D-side, H'D-side and
+// SD-side operands); nullptr, or screening off, multiplies every block pair.
+int products(Dev &d, const double *Din, double *HDo, double *SDo, const double *nDin, const DevState *state,
+             cudaStream_t st);
 int contract(Dev &d, const double *Wl, const double *Dl, const double *HDr, const double *SDr, double *Xo,
-             double *Yo, double *h2o, double *s2o, const DevState *state, cudaStream_t st);
+             double *Yo, double *h2o, double *s2o, const double *nWl, const double *nDl, const double *nHDr,
+             const double *nSDr, const DevState *state, cudaStream_t st);
 int gradient(Dev &d, const DevState *state, cudaStream_t st);
 int coeffs(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
 int nn_update(Dev &d, int64_t n, int mode, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);

@@ -31,7 +31,8 @@ class Options(C.Structure):
                 ("cholesky", C.c_int32), ("max_iter", C.c_int32), ("orth_tol", C.c_double),
                 ("filter_eps", C.c_double), ("stream", C.c_void_p), ("refine", C.c_int32),
                 ("exact_digits", C.c_int32), ("split_digits", C.c_int32), ("graphs", C.c_int32),
-                ("n_occupied", C.c_int32), ("precon", C.c_int32), ("tau_T", C.c_double)]
+                ("n_occupied", C.c_int32), ("precon", C.c_int32), ("tau_T", C.c_double),
+                ("screen_eps", C.c_double)]
 
 
 class Pattern(C.Structure):
@@ -77,6 +78,7 @@ _SIGS = {
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_int64, C.c_void_p]),
     "omm_op_line_min": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "omm_op_convert": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "omm_op_quartic_coeffs_static_max_bytes": (C.c_int64, []),
     "omm_op_quartic_coeffs_static": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
@@ -473,6 +475,12 @@ def op_quartic_coeffs_static(n, h0, s0, ld_h, X, Y, h2, s2, ld_z, coeffs, stream
     return lib().omm_op_quartic_coeffs_static(n, _ptr(h0)[0], _ptr(s0)[0], ld_h, _ptr(X)[0], _ptr(Y)[0],
                                               _ptr(h2)[0], _ptr(s2)[0], ld_z, _ptr(coeffs)[0],
                                               C.c_void_p(stream) if stream else None)
+
+
+def op_convert(op, inp, out, e=None, stream=0):
+    """Integer-pipe conversion self-test (omm_op_convert): device tensors in, out (and e)."""
+    return lib().omm_op_convert(op, inp.numel(), _ptr(inp)[0], _ptr(e)[0] if e is not None else None,
+                                _ptr(out)[0], C.c_void_p(stream) if stream else None)
 
 
 def op_line_min(coeffs, x_out, status_out, stream=0):

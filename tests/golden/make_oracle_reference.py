@@ -38,11 +38,24 @@ def run(name):
     res = O.omm_cg(H, S, W0, tol=w["tol"])
     t = time.time() - t0
     e_exact = 2.0 * float(np.sum(lam[:sysm.n]))
+    # density matrix rho = 2 W (2I - S_W) W^T (Eq. 5) of the oracle's solve, and the
+    # exact one, 2 V V^T over the S-orthonormal lowest-n eigenvectors, on sampled
+    # entries (the full m x m matrix is too large to store)
+    rng = np.random.default_rng(7)
+    m, n = sysm.m, sysm.n
+    idx = np.concatenate([rng.integers(0, m, (1500, 2)), np.repeat(rng.integers(0, m, (100, 1)), 2, axis=1)])
+    W = np.asarray(res.W)
+    K = 2.0 * np.eye(n) - W.T @ (S @ W)
+    rho_oracle = 2.0 * np.einsum("ka,ab,kb->k", W[idx[:, 0]], K, W[idx[:, 1]])
+    _, V = sla.eigh(H, S, subset_by_index=[0, n - 1])
+    rho_exact = 2.0 * np.einsum("ka,ka->k", V[idx[:, 0]], V[idx[:, 1]])
     return {
         "dims": list(w["dims"]), "seed": w["seed"], "m": sysm.m, "n": sysm.n, "tol": w["tol"],
         "eta_gershgorin": res.eta, "oracle_iters": res.iters, "oracle_E": res.E,
         "exact_E": e_exact, "lambda_n": float(lam[sysm.n - 1]), "lambda_n_plus_1": float(lam[sysm.n]),
         "oracle_rel_err": abs(res.E - e_exact) / abs(e_exact), "oracle_seconds_here": t,
+        "rho_samples": {"idx": idx.tolist(), "oracle": rho_oracle.tolist(), "exact": rho_exact.tolist(),
+                        "max_abs_oracle_vs_exact": float(np.abs(rho_oracle - rho_exact).max())},
     }
 
 

@@ -32,7 +32,7 @@ def test_header_declares_entry_points():
                  "omm_solve_progress", "omm_solve_end", "omm_batch_solve", "omm_md_guess", "omm_get_diag",
                  "omm_get_array", "omm_get_density", "omm_get_pattern", "omm_destroy", "omm_status_str",
                  "omm_op_dgemm", "omm_op_split_gemm", "omm_op_exact_gemm", "omm_op_quartic_coeffs",
-                 "omm_op_quartic_coeffs_static", "omm_op_line_min", "omm_selftest_bounded_wait"):
+                 "omm_op_quartic_coeffs_static", "omm_op_line_min", "omm_selftest_bounded_wait", "omm_op_convert"):
         assert must in names
 
 
@@ -59,6 +59,8 @@ def test_argument_errors_without_gpu(built):
     assert built.omm_solve(None, None, 0, 1e-10, None, 0, None, None) == omm.ERR_ARG
     assert omm.op_dgemm(0, 0, -1, 2, 2, 1.0, None, 1, None, 1, 0.0, None, 1, None, 1) == omm.ERR_ARG
     assert omm.op_line_min(None, None, None) == omm.ERR_ARG
+    assert built.omm_op_convert(7, 4, None, None, None, None) == omm.ERR_ARG
+    assert built.omm_op_convert(0, 4, None, None, None, None) == omm.ERR_ARG
 
 
 def test_options_reject_unknown_names(built):

@@ -170,7 +170,15 @@ def test_full_size_c3_first_step(omm):
     got = s.get_pattern(omm.PATTERN_HW)
     np.testing.assert_array_equal(got[0], hwrp)
     np.testing.assert_array_equal(got[1], hwcol)
-    assert s.nnzb["N"] == 2513558 or s.nnzb["N"] > 0
+    # P_N = P_W^T P_HW, bit-exact at full size
+    PW = sp.csr_matrix((np.ones(len(wcol)), wcol, wrp), shape=(N, N))
+    PHW = sp.csr_matrix((np.ones(len(hwcol)), hwcol, hwrp), shape=(N, N))
+    PN = (PW.T @ PHW).tocsr()
+    PN.sort_indices()
+    got = s.get_pattern(omm.PATTERN_N)
+    np.testing.assert_array_equal(got[0], PN.indptr)
+    np.testing.assert_array_equal(got[1], PN.indices)
+    assert s.nnzb["N"] == PN.nnz == 2513558
     s.set_HS(Hv, Sv)
     eta = s.diag().eta
     H = O.bsr_to_csr(rp, col, Hv, N, N)
@@ -220,3 +228,57 @@ def test_sparse_density_on_S_pattern(omm):
     rho = s.get_density(omm.DENSITY_RHO)
     assert float(np.sum(rho * Sv)) == pytest.approx(O.charge(W, S), rel=1e-10)
     s.close()
+
+
+@pytest.mark.parametrize("eps,k", [(1e-3, 1), (1e-3, 8), (1e-2, 8)])
+def test_screened_steps_track_screened_oracle(omm, eps, k):
+    """Norm-based screening of the block products: k CG steps with screen_eps
+    equal the oracle's screened CG (same rule, its own norms) and differ from
+    the unscreened steps by far more than the tolerance.  At 1e-3 part of the
+    overlap products are skipped, at 1e-2 all off-diagonal overlap products."""
+    import synth
+    sysm = synth.make_system(3, 3, 3, seed=1)
+    radius = 4.5
+    s, (rp, col, Hv, Sv), _ = _setup(omm, sysm, radius, max_iter=k, screen_eps=eps)
+    s.set_HS(Hv, Sv)
+    eta = s.diag().eta
+    H, S, mask, W0 = sysm.dense_H(), sysm.dense_S(), sysm.w_mask(radius), sysm.W0_local(radius)
+    W0b = sysm.W0_bsr_values(radius)
+    Wout = np.zeros_like(W0b)
+    E, iters, st = s.solve(W0b, tol=0.0, W_out=Wout, raise_on_error=False)
+    ref = O.omm_cg_screened(H, S, W0, 8, 2, eps, tol=0.0, eta=eta, max_iter=k, mask=mask)
+    plain = O.omm_cg(H, S, W0, tol=0.0, eta=eta, max_iter=k, mask=mask)
+    assert st == omm.ERR_MAXITER and iters == k == ref.iters
+    assert E == pytest.approx(ref.E, rel=1e-12)
+    W = _w_blocks_to_dense(sysm, radius, Wout)
+    np.testing.assert_allclose(W, ref.W, rtol=1e-8, atol=1e-10)
+    assert np.abs(ref.W - plain.W).max() > 1e4 * 1e-10          # screening changed the steps
+    s.close()
+
+
+def test_screening_off_and_below_every_norm_is_bitwise_plain(omm):
+    """screen_eps below every block-norm product skips nothing: the steps equal
+    the unscreened solve bit for bit (the skip test never fires)."""
+    import synth
+    sysm = synth.make_system(3, 3, 3, seed=1)
+    radius = 4.5
+    outs = []
+    for eps in (0.0, 1e-30):
+        s, (rp, col, Hv, Sv), _ = _setup(omm, sysm, radius, max_iter=6, screen_eps=eps)
+        s.set_HS(Hv, Sv)
+        W0b = sysm.W0_bsr_values(radius)
+        Wout = np.zeros_like(W0b)
+        E, iters, st = s.solve(W0b, tol=0.0, W_out=Wout, raise_on_error=False)
+        outs.append((E, Wout))
+        s.close()
+    assert outs[0][0] == outs[1][0]
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+def test_screen_eps_rejected_when_invalid(omm):
+    import synth
+    sysm = synth.make_system(2, 2, 2, seed=1)
+    for bad in (-1e-8, float("nan"), float("inf")):
+        with pytest.raises(omm.OmmError) as e:
+            _setup(omm, sysm, 4.5, screen_eps=bad)
+        assert e.value.status == omm.ERR_ARG

@@ -35,6 +35,9 @@ def _inputs(n, seed):
 
 
 def test_static_scratch_matches_caller_scratch_twice(omm):
+    """Same kernel, block count and reduction order as the caller-scratch entry
+    point, so the results are equal bit for bit; the second call allocates no
+    device memory."""
     for call, (n, seed) in enumerate([(200, 1), (1024, 2)]):
         t = _inputs(n, seed)
         nb = omm.op_quartic_coeffs_scratch_bytes(n)
@@ -43,11 +46,15 @@ def test_static_scratch_matches_caller_scratch_twice(omm):
         got = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
         assert omm.op_quartic_coeffs(n, t["h0"], t["s0"], n, t["X"], t["Y"], t["h2"], t["s2"], n,
                                      ref, scratch, nb) == omm.OK
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = omm.op_quartic_coeffs_static(n, t["h0"], t["s0"], n, t["X"], t["Y"], t["h2"], t["s2"], n, got)
         assert st == omm.OK, omm.lib().omm_last_error()
         torch.cuda.synchronize()
+        if call > 0:
+            assert torch.cuda.mem_get_info()[0] == free0
         r, g = ref.cpu().numpy(), got.cpu().numpy()
-        np.testing.assert_allclose(g, r, rtol=1e-11, atol=1e-12 * np.abs(r).max(), err_msg=f"call {call}")
+        np.testing.assert_array_equal(g, r, err_msg=f"call {call}")
 
 
 def test_static_scratch_rejects_out_of_range_sizes(omm):
@@ -55,4 +62,6 @@ def test_static_scratch_rejects_out_of_range_sizes(omm):
     assert omm.op_quartic_coeffs_static(-1, None, None, 1, None, None, None, None, 1, c) == omm.ERR_ARG
     assert omm.op_quartic_coeffs_static(2 ** 31, None, None, 1, None, None, None, None, 1, c) == omm.ERR_ARG
     assert b"outside" in omm.lib().omm_last_error()
+    assert omm.op_quartic_coeffs_static(4, None, None, 4, None, None, None, None, 4, c) == omm.ERR_ARG
+    assert b"NULL" in omm.lib().omm_last_error()
     assert omm.lib().omm_op_quartic_coeffs_static_max_bytes() == 512 * 13 * 8 + 256
