@@ -239,7 +239,7 @@ def run_omm(args):
     torch.cuda.synchronize()
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
                 orth_tol=TOL[prec]["orth_tol"], stream=stream.cuda_stream, cholesky=int(args.cholesky),
-                split_digits=args.split_digits)
+                split_digits=args.split_digits, gemm_pair=args.gemm_pair)
     solver = omm.Solver(m, n, 8, **opts)
     tol = TOL[prec]["tol"]
 
@@ -411,7 +411,7 @@ def run_omm(args):
         "data": "synthetic",
         "config": {"workload": workload_name(sysm) + (" cholesky-reduced" if args.cholesky else ""),
                    "precision": prec, "tol": tol, "cholesky": bool(args.cholesky),
-                   "split_digits": args.split_digits,
+                   "split_digits": args.split_digits, "gemm_pair": bool(args.gemm_pair),
                    "refine": "exact-digit tensor cores" if prec == "mixed" else None,
                    "orth_tol": TOL[prec]["orth_tol"], "parallelism": f"replicas x{ws}",
                    "l2": "working set (H, S = 256 MiB, plus W/D/products) exceeds the 129 MB L2"},
@@ -629,7 +629,7 @@ def run_profile(args):
     prec = args.precision
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
                 orth_tol=TOL[prec]["orth_tol"], stream=torch.cuda.current_stream().cuda_stream,
-                cholesky=int(args.cholesky), split_digits=args.split_digits)
+                cholesky=int(args.cholesky), split_digits=args.split_digits, gemm_pair=args.gemm_pair)
     if args.max_iter > 0:
         opts["max_iter"] = args.max_iter
     solver = omm.Solver(sysm.m, sysm.n, 8, **opts)
@@ -908,6 +908,8 @@ def main():
                     help="c5: sequences of the mixed-vs-FP64 serving comparison (0 skips it)")
     ap.add_argument("--split-digits", type=int, default=2, choices=[2, 3],
                     help="mixed form: BF16 digits per operand in the first phase (3 pairs or 6)")
+    ap.add_argument("--gemm-pair", type=int, default=1, choices=[0, 1],
+                    help="mixed form: split products on CTA pairs (cta_group::2) or one CTA per tile")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="c4/c5: replay chunks of CG steps as captured CUDA graphs")
     ap.add_argument("--no-kinetic", action="store_true",

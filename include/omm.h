@@ -146,6 +146,10 @@ typedef struct {
                               operand block are kept on the device (about 8 doubles per
                               block of H, W, H'W and W^T H W).  0 (default): off; must be
                               finite and >= 0 (OMM_ERR_ARG); ignored by dense handles */
+    int32_t gemm_pair;     /* mixed form: 1 (default) runs the two-digit split products on CTA
+                              pairs (tcgen05.mma.cta_group::2: 256 x 256 tiles, each SM of a
+                              pair holding half of the B tile); 0: one CTA per 128 x 256 tile.
+                              Three-digit products always take one CTA per tile */
 } omm_options;
 
 enum {

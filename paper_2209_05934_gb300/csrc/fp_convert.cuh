@@ -39,9 +39,10 @@ __device__ __forceinline__ double sw_f2d(float x) {
     if (e == 0) {
         if (m == 0) return __longlong_as_double((long long)sign);
         // subnormal float: normalise
-        // m 2^-149 with the leading one at bit p = 23 - lz: 1.f x 2^(p - 149)
-        const int lz = __clz((int)m) - 8;                      // leading zeros inside the 23-bit field
-        const uint64_t mm = (m << (lz + 1)) & 0x7FFFFFull;
+        // m 2^-149 with the leading one at bit p = 23 - lz: 1.f x 2^(p - 149); shifting
+        // by lz puts that one at bit 23, which the 23-bit mask then drops
+        const int lz = __clz((int)m) - 8;                      // leading zeros inside the 24-bit field
+        const uint64_t mm = (m << lz) & 0x7FFFFFull;
         const uint64_t ed = (uint64_t)(1023 - 126 - lz);
         return __longlong_as_double((long long)(sign | (ed << 52) | (mm << 29)));
     }

@@ -42,6 +42,8 @@ struct MixedBufs {
     int bk = 32;   // K-block width of the split products: 64 (128-byte swizzle) with two digits, else 32
     __nv_bfloat16 *HSd = nullptr, *WDd = nullptr, *HDSDd = nullptr, *SWHWd = nullptr, *HSWd = nullptr;
     CUtensorMap mapHS_A, mapWD_A, mapWD_B, mapHDSD_B, mapSWHW_A, mapHSW_B;
+    // the B operands again with 128-row boxes: half of a 256-wide tile per CTA of a pair
+    CUtensorMap mapHDSD_H, mapHSW_H, mapG_H;
     float *HDSD32 = nullptr, *Z32 = nullptr, *G32 = nullptr, *Gp32 = nullptr, *D32 = nullptr;
     __nv_bfloat16 *Pd = nullptr, *Gd = nullptr;
     CUtensorMap mapP_A, mapG_B;
@@ -334,6 +336,12 @@ constexpr int kDig = 3;
 int split_bk(int digits) { return digits == 2 ? 64 : 32; }
 constexpr int kBN = 256;  // output tile width of the split products (UMMA N = 256)
 
+// The 128-row-box map of a split product's B operand when the handle runs its
+// split products on CTA pairs (omm_options.gemm_pair), else nullptr (one CTA per tile).
+const CUtensorMap *pair_map(omm_handle *h, const CUtensorMap &half) {
+    return h->opt.gemm_pair ? &half : nullptr;
+}
+
 omm::tc::TcArgs tc_args(omm_handle *h, int M, int N, int K) {
     omm::tc::TcArgs a{};
     omm::tc::pairs_for_digits(h->cur_dig, a);
@@ -371,6 +379,8 @@ int mixed_alloc(omm_handle *h) {
     TRY(omm::tc::make_digit_map(&x.mapHDSD_B, x.HDSDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, kBN, kBK));
     TRY(omm::tc::make_digit_map(&x.mapSWHW_A, x.SWHWd, 2 * n, m, x.ld2n, m * x.ld2n, kDig, 128, kBK));
     TRY(omm::tc::make_digit_map(&x.mapHSW_B, x.HSWd, 2 * n, n, x.ld2n, n * x.ld2n, kDig, kBN, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapHDSD_H, x.HDSDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
+    TRY(omm::tc::make_digit_map(&x.mapHSW_H, x.HSWd, 2 * n, n, x.ld2n, n * x.ld2n, kDig, 128, kBK));
     return OMM_OK;
 }
 
@@ -425,8 +435,8 @@ int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_s
     a.dplane = 2 * n * x.ldm;
     a.dout_step = dout_step * x.ldm;
     a.ndig = h->cur_dig;
-    if (!s_identity(h)) return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, kBN, h->stream);
-    TRY(omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 1, kBN, h->stream));
+    if (!s_identity(h)) return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, kBN, h->stream, pair_map(h, x.mapWD_A));
+    TRY(omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 1, kBN, h->stream, pair_map(h, x.mapWD_A)));
     // z = 1 (S times the B rows) is the B rows themselves: their FP32/FP64 values and digits
     const int64_t mn = m * n;
     if (C32 != nullptr)   // iteration: S D = D
@@ -448,7 +458,7 @@ int split_contract(omm_handle *h) {
     omm::tc::TcArgs a = tc_args(h, (int)(2 * n), (int)(2 * n), (int)m);
     a.C32 = x.Z32;
     a.ldc = 2 * n;
-    return omm::tc::gemm(x.mapWD_A, x.mapHDSD_B, a, 1, kBN, h->stream);
+    return omm::tc::gemm(x.mapWD_A, x.mapHDSD_B, a, 1, kBN, h->stream, pair_map(h, x.mapHDSD_H));
 }
 
 // G = 4 H'W - 2 [SW H'W][H_W ; S_W]
@@ -462,7 +472,7 @@ int split_gradient(omm_handle *h) {
     a.ldcin = m;
     a.C32 = x.G32;
     a.ldc = m;
-    return omm::tc::gemm(x.mapSWHW_A, x.mapHSW_B, a, 1, kBN, h->stream);
+    return omm::tc::gemm(x.mapSWHW_A, x.mapHSW_B, a, 1, kBN, h->stream, pair_map(h, x.mapHSW_H));
 }
 
 // FP64 gradient (CUDA cores), rounded to the FP32 gradient of the mixed form
@@ -604,7 +614,7 @@ int mixed_direction(omm_handle *h, int first) {
         omm::tc::TcArgs a = tc_args(h, (int)m, (int)n, (int)m);
         a.C32 = x.PG32;
         a.ldc = m;
-        TRY(omm::tc::gemm(x.mapP_A, x.mapG_B, a, 1, kBN, h->stream));
+        TRY(omm::tc::gemm(x.mapP_A, x.mapG_B, a, 1, kBN, h->stream, pair_map(h, x.mapG_H)));
         Zg = x.PG32;
     }
     StageTimer t(h, OMM_STAGE_DIRECTION);
@@ -628,7 +638,7 @@ int mixed_start(omm_handle *h) {
         a.C = h->h0s0;
         a.ldc = 2 * n;
         a.c_step = n;             // H_W in rows [0, n), S_W in rows [n, 2n)
-        TRY(omm::tc::gemm(h->mx.mapWD_A, h->mx.mapHDSD_B, a, 2, kBN, st));
+        TRY(omm::tc::gemm(h->mx.mapWD_A, h->mx.mapHDSD_B, a, 2, kBN, st, pair_map(h, h->mx.mapHDSD_H)));
     }
     TRY(omm::launch_nn_update_energy((int)n, h->h0s0, h->h0s0 + n, 2 * n, h->Z, 2 * n, scr(h, 1),
                                      ctr(h, 1), s, 1, st));
@@ -815,6 +825,7 @@ int precon_alloc(omm_handle *h) {
         TRY(dalloc(&x.PG32, (size_t)(m * n)));
         TRY(omm::tc::make_digit_map(&x.mapP_A, x.Pd, m, m, x.ldm, m * x.ldm, kDig, 128, x.bk));
         TRY(omm::tc::make_digit_map(&x.mapG_B, x.Gd, m, n, x.ldm, n * x.ldm, kDig, kBN, x.bk));
+        TRY(omm::tc::make_digit_map(&x.mapG_H, x.Gd, m, n, x.ldm, n * x.ldm, kDig, 128, x.bk));
     }
     return OMM_OK;
 }
@@ -957,6 +968,7 @@ void omm_default_options(omm_options *opt) {
     opt->precon = 0;
     opt->tau_T = 136.05693122994;   // 10 Ry in eV
     opt->screen_eps = 0.0;
+    opt->gemm_pair = 1;
 }
 
 const char *omm_status_str(int status) {

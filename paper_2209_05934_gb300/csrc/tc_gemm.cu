@@ -59,6 +59,119 @@ __device__ __forceinline__ void split3_i(double v, __nv_bfloat16 &d1, __nv_bfloa
     d3 = __float2bfloat16_rn(r1 - __bfloat162float(d2));
 }
 
+// ------------------------------------------------------------------ epilogue
+// One epilogue warp: TMEM lanes 32q..32q+31 (rows `row` = m0 + 32q + lane of the
+// tile) x BN columns from n0 -> C = alpha acc + beta Cin (FP32 or FP64,
+// column-major), optionally with the result's BF16 digits.  nacc accumulators
+// (K ranges x pair classes) are summed; have_acc false writes beta Cin only.
+template <int BN>
+__device__ __forceinline__ void tc_epilogue(const TcArgs &args, uint32_t tmem, int q, int row, int n0, int z,
+                                            int nacc, bool have_acc) {
+    double *C = args.C != nullptr ? args.C + (int64_t)z * args.c_step : nullptr;
+    const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
+    __nv_bfloat16 *Dd = args.Dout ? args.Dout + (int64_t)z * args.dout_step : nullptr;
+    if (args.C32 != nullptr) {
+        // FP32 epilogue: no FP64 arithmetic except reading an FP64 Cin
+        float *C32 = args.C32 + (int64_t)z * args.c_step;
+        const float alpha = (float)args.alpha, beta = (float)args.beta;
+        // Cin is fetched one 16-column chunk ahead as raw FP64 and converted
+        // only when used: the compiler cannot rule out that C32 aliases Cin,
+        // so a load placed after a store, or tied to a branchy conversion,
+        // would wait out one DRAM round trip per output
+        const bool rd = Cin != nullptr && row < args.M;
+        auto load_cin = [&](int c0, double (&dst)[16]) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = n0 + c0 + i;
+                dst[i] = (rd && col < args.N) ? __ldg(&Cin[row + (int64_t)col * args.ldcin]) : 0.0;
+            }
+        };
+        double cin[16], cin_next[16];
+        load_cin(0, cin);
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            if (c0 + 16 < BN) load_cin(c0 + 16, cin_next);
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            if (have_acc) {
+                for (int ac = 0; ac < nacc; ++ac) {
+                    float f[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * BN + c0), f);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += f[i];
+                }
+            }
+            if (row < args.M) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = n0 + c0 + i;
+                    if (col >= args.N) break;
+                    float out = alpha * v[i];
+                    if (Cin != nullptr) out = fmaf(beta, sw_d2f(cin[i]), out);
+                    C32[row + (int64_t)col * args.ldc] = out;
+                    if (Dd != nullptr) {
+                        const int64_t o = row + (int64_t)col * args.ldd;
+                        const __nv_bfloat16 d1 = __float2bfloat16_rn(out);
+                        const float r1 = out - __bfloat162float(d1);
+                        const __nv_bfloat16 d2 = __float2bfloat16_rn(r1);
+                        Dd[o] = d1;
+                        if (args.ndig > 1) Dd[args.dplane + o] = d2;
+                        if (args.ndig > 2) Dd[2 * args.dplane + o] = __float2bfloat16_rn(r1 - __bfloat162float(d2));
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) cin[i] = cin_next[i];
+        }
+    } else {
+        // Cin one chunk ahead of the stores, as in the FP32 epilogue
+        const bool rd = Cin != nullptr && row < args.M;
+        auto load_cin = [&](int c0, double (&dst)[16]) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = n0 + c0 + i;
+                dst[i] = (rd && col < args.N) ? __ldg(&Cin[row + (int64_t)col * args.ldcin]) : 0.0;
+            }
+        };
+        double cin[16], cin_next[16];
+        load_cin(0, cin);
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            if (c0 + 16 < BN) load_cin(c0 + 16, cin_next);
+            double v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.0;
+            if (have_acc) {
+                for (int ac = 0; ac < nacc; ++ac) {
+                    float f[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * BN + c0), f);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += (double)f[i];
+                }
+            }
+            if (row < args.M) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = n0 + c0 + i;
+                    if (col >= args.N) break;
+                    double out = args.alpha * v[i];
+                    if (Cin != nullptr) out = fma(args.beta, cin[i], out);
+                    C[row + (int64_t)col * args.ldc] = out;
+                    if (Dd != nullptr) {
+                        __nv_bfloat16 d1, d2, d3;
+                        split3(out, d1, d2, d3);
+                        const int64_t o = row + (int64_t)col * args.ldd;
+                        Dd[o] = d1;
+                        if (args.ndig > 1) Dd[args.dplane + o] = d2;
+                        if (args.ndig > 2) Dd[2 * args.dplane + o] = d3;
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) cin[i] = cin_next[i];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ the GEMM kernel
 template <int BN, int STAGES, int BKT>
 __global__ void __launch_bounds__(192, 1)
@@ -159,110 +272,8 @@ __global__ void __launch_bounds__(192, 1)
         bool got = nkb > 0 && mbar_wait(&acc_bar, 0, deadline, &abort_flag, args.err);
         const bool have_acc = __all_sync(0xffffffffu, got);   // tcgen05.ld is warp-collective
         tc_fence_after();
-        double *C = args.C != nullptr ? args.C + (int64_t)z * args.c_step : nullptr;
-        const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
-        __nv_bfloat16 *Dd = args.Dout ? args.Dout + (int64_t)z * args.dout_step : nullptr;
         const int nacc = (nkb < kacc ? nkb : kacc) * ncls;   // accumulators that were written
-        if (args.C32 != nullptr) {
-            // FP32 epilogue: no FP64 arithmetic except reading an FP64 Cin
-            float *C32 = args.C32 + (int64_t)z * args.c_step;
-            const float alpha = (float)args.alpha, beta = (float)args.beta;
-            // Cin is fetched one 16-column chunk ahead as raw FP64 and converted
-            // only when used: the compiler cannot rule out that C32 aliases Cin,
-            // so a load placed after a store, or tied to a branchy conversion,
-            // would wait out one DRAM round trip per output
-            const bool rd = Cin != nullptr && row < args.M;
-            auto load_cin = [&](int c0, double (&dst)[16]) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = n0 + c0 + i;
-                    dst[i] = (rd && col < args.N) ? __ldg(&Cin[row + (int64_t)col * args.ldcin]) : 0.0;
-                }
-            };
-            double cin[16], cin_next[16];
-            load_cin(0, cin);
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                if (c0 + 16 < BN) load_cin(c0 + 16, cin_next);
-                float v[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = 0.f;
-                if (have_acc) {
-                    for (int ac = 0; ac < nacc; ++ac) {
-                        float f[16];
-                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * BN + c0), f);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] += f[i];
-                    }
-                }
-                if (row < args.M) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int col = n0 + c0 + i;
-                        if (col >= args.N) break;
-                        float out = alpha * v[i];
-                        if (Cin != nullptr) out = fmaf(beta, sw_d2f(cin[i]), out);
-                        C32[row + (int64_t)col * args.ldc] = out;
-                        if (Dd != nullptr) {
-                            const int64_t o = row + (int64_t)col * args.ldd;
-                            const __nv_bfloat16 d1 = __float2bfloat16_rn(out);
-                            const float r1 = out - __bfloat162float(d1);
-                            const __nv_bfloat16 d2 = __float2bfloat16_rn(r1);
-                            Dd[o] = d1;
-                            if (args.ndig > 1) Dd[args.dplane + o] = d2;
-                            if (args.ndig > 2) Dd[2 * args.dplane + o] = __float2bfloat16_rn(r1 - __bfloat162float(d2));
-                        }
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 16; ++i) cin[i] = cin_next[i];
-            }
-        } else {
-            // Cin one chunk ahead of the stores, as in the FP32 epilogue
-            const bool rd = Cin != nullptr && row < args.M;
-            auto load_cin = [&](int c0, double (&dst)[16]) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = n0 + c0 + i;
-                    dst[i] = (rd && col < args.N) ? __ldg(&Cin[row + (int64_t)col * args.ldcin]) : 0.0;
-                }
-            };
-            double cin[16], cin_next[16];
-            load_cin(0, cin);
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                if (c0 + 16 < BN) load_cin(c0 + 16, cin_next);
-                double v[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = 0.0;
-                if (have_acc) {
-                    for (int ac = 0; ac < nacc; ++ac) {
-                        float f[16];
-                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * BN + c0), f);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] += (double)f[i];
-                    }
-                }
-                if (row < args.M) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int col = n0 + c0 + i;
-                        if (col >= args.N) break;
-                        double out = args.alpha * v[i];
-                        if (Cin != nullptr) out = fma(args.beta, cin[i], out);
-                        C[row + (int64_t)col * args.ldc] = out;
-                        if (Dd != nullptr) {
-                            __nv_bfloat16 d1, d2, d3;
-                            split3(out, d1, d2, d3);
-                            const int64_t o = row + (int64_t)col * args.ldd;
-                            Dd[o] = d1;
-                            if (args.ndig > 1) Dd[args.dplane + o] = d2;
-                            if (args.ndig > 2) Dd[2 * args.dplane + o] = d3;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 16; ++i) cin[i] = cin_next[i];
-            }
-        }
+        tc_epilogue<BN>(args, tmem, q, row, n0, z, nacc, have_acc);
     }
     tc_fence_before();
     __syncthreads();
@@ -270,6 +281,157 @@ __global__ void __launch_bounds__(192, 1)
         __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem, tmem_cols);
+    }
+}
+
+// ------------------------------------------------------------------ the GEMM on CTA pairs
+// A cluster of two CTAs computes a 256 x 256 tile with the pair MMA
+// (tcgen05.mma.cta_group::2, M = 256): CTA r holds A rows 128r..128r+127 and
+// B rows (output columns) 128r..128r+127 of the tile in its shared memory, and
+// its tensor memory receives output rows 128r..128r+127 for all 256 columns.
+// Each SM thus pulls half of the B tile through its shared memory per MMA
+// instead of all of it.  Roles:
+//   warp 0 (both CTAs): TMA of the CTA's own A and B digit tiles, completing on
+//     the CTA's own full barrier;
+//   warp 1, CTA 1: relays each completed stage to CTA 0 (remote arrive on its
+//     peer-full barrier), so every copy completes on the barrier of the CTA it
+//     writes into;
+//   warp 1, CTA 0: waits for both halves of a stage, issues the pair MMAs and
+//     commits to the empty barriers of both CTAs (multicast), finally to both
+//     accumulator barriers;
+//   warps 2..5 (both CTAs): the epilogue of the CTA's 128 rows.
+// All waits are bounded; the pair meets at cluster barriers only after every
+// role's loop has ended, and tensor memory is released by both CTAs together.
+template <int STAGES, int BKT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+    tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                        const TcArgs args) {
+    // state->done only changes between launches, so both CTAs of a pair return here together
+    if (args.state != nullptr && *((volatile const int *)&args.state->done)) return;
+    constexpr int BN = 256, BNH = 128;
+    const uint32_t rank = cluster_ctarank();
+    const int z = blockIdx.z;
+    const int nA = args.nA, nB = args.nB;
+    constexpr int TILE_A = BM * BKT * 2;
+    constexpr int TILE_B = BNH * BKT * 2;
+    const int stage_bytes = nA * TILE_A + nB * TILE_B;
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES];    // this CTA's copies of a stage landed
+    __shared__ __align__(8) uint64_t pfull_bar[STAGES];   // (CTA 0) the peer's copies landed
+    __shared__ __align__(8) uint64_t empty_bar[STAGES];   // the pair's MMAs of a stage completed
+    __shared__ __align__(8) uint64_t acc_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const uint64_t deadline = globaltimer_ns() + kWaitNs;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * (2 * BM) + BM * (int)rank;   // this CTA's output rows
+    const int n0 = (blockIdx.x >> 1) * BN;                   // the pair's output columns
+    const int nb0 = n0 + BNH * (int)rank;                    // this CTA's B rows
+    const int nkb = (args.K + BKT - 1) / BKT;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&pfull_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&acc_bar, 1);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    const int kacc = args.kacc, ncls = args.ncls;
+    const uint32_t tmem_cols = (uint32_t)(BN * kacc * ncls);
+    if (warp == 1) tmem_alloc_pair(&tmem_base, tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();   // barriers of both CTAs initialised before any remote arrive
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    int issued = 0;       // producer: k-blocks whose copies were issued
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer (both CTAs)
+        const int a_row = args.a_row0 + z * args.a_row_step + m0;
+        const int b_row = args.b_row0 + z * args.b_row_step + nb0;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+            if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, args.err)) break;
+            mbar_arrive_expect_tx(&full_bar[s], (uint32_t)stage_bytes);
+            uint8_t *st = smem + s * stage_bytes;
+            for (int p = 0; p < nA; ++p)
+                tma_load_3d(st + p * TILE_A, &mapA, kb * BKT, a_row, p, &full_bar[s]);
+            for (int q = 0; q < nB; ++q)
+                tma_load_3d(st + nA * TILE_A + q * TILE_B, &mapB, kb * BKT, b_row, q, &full_bar[s]);
+            issued = kb + 1;
+        }
+    } else if (warp == 1 && lane == 0 && rank == 1) {
+        // ---------------- relay (CTA 1): this CTA's stage landed -> CTA 0's peer-full barrier
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+            if (!mbar_wait(&full_bar[s], ph, deadline, &abort_flag, args.err)) break;
+            mbar_arrive_remote(mapa_shared(smem_u32(&pfull_bar[s]), 0u));
+        }
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+        // ---------------- pair MMA issuer (CTA 0)
+        constexpr uint32_t idesc = idesc_bf16(2 * BM, BN);
+        uint32_t written = 0;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+            if (!mbar_wait(&full_bar[s], ph, deadline, &abort_flag, args.err)) break;
+            if (!mbar_wait_cluster(&pfull_bar[s], ph, deadline, &abort_flag, args.err)) break;
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + s * stage_bytes);
+            const int slot = (kb * kacc) / nkb;
+            for (int pr = 0; pr < args.npairs; ++pr) {
+                const int cls = (ncls == 2 && (args.pa[pr] != 0 || args.pb[pr] != 0)) ? 1 : 0;
+                const int acc = slot * ncls + cls;
+                const uint32_t tacc = tmem + (uint32_t)(acc * BN);
+                const uint64_t da = sdesc_sw128(st + args.pa[pr] * TILE_A);
+                const uint64_t db = sdesc_sw128(st + nA * TILE_A + args.pb[pr] * TILE_B);
+#pragma unroll
+                for (int kk = 0; kk < BKT / 16; ++kk) {
+                    umma_bf16_pair(tacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                                   ((written >> acc) & 1u) ? 1u : 0u);
+                    written |= 1u << acc;
+                }
+            }
+            umma_commit_pair_mc(&empty_bar[s], (uint16_t)0x3);
+        }
+        umma_commit_pair_mc(&acc_bar, (uint16_t)0x3);
+    } else if (warp >= 2) {
+        // ---------------- epilogue (both CTAs): this CTA's 128 rows
+        const int q = warp & 3;
+        const int row = m0 + 32 * q + lane;
+        bool got = nkb > 0 && mbar_wait(&acc_bar, 0, deadline, &abort_flag, args.err);
+        const bool have_acc = __all_sync(0xffffffffu, got);
+        tc_fence_after();
+        const int nacc = (nkb < kacc ? nkb : kacc) * ncls;
+        tc_epilogue<BN>(args, tmem, q, row, n0, z, nacc, have_acc);
+    }
+    if (warp == 0 && lane == 0 && abort_flag) {
+        // an aborted pipeline: let this CTA's issued copies land before it can exit
+        const uint64_t until = globaltimer_ns() + 200000000ull;
+        for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
+            const uint32_t addr = smem_u32(&full_bar[kb % STAGES]);
+            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+            while (!mbar_try_wait(addr, ph) && globaltimer_ns() < until) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();   // neither CTA leaves while the pair's MMAs or arrivals may touch it
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, tmem_cols);
     }
 }
 
@@ -381,6 +543,33 @@ int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, int
     return OMM_OK;
 }
 
+template <int STAGES, int BKT>
+int launch_tc_pair(const CUtensorMap &ma, const CUtensorMap &mb_half, const TcArgs &a, int nbatch,
+                   cudaStream_t st) {
+    const int smem = STAGES * (a.nA * BM * BKT * 2 + a.nB * 128 * BKT * 2) + 1024;
+    static int attr_bytes = 0;
+    if (smem > attr_bytes) {
+        OMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_pair_kernel<STAGES, BKT>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_bytes = smem;
+    }
+    TcArgs b = a;
+    const int nkb = (a.K + BKT - 1) / BKT;
+    bool has_main = false, has_small = false;
+    for (int p = 0; p < a.npairs; ++p) {
+        if (a.pa[p] == 0 && a.pb[p] == 0) has_main = true; else has_small = true;
+    }
+    b.ncls = (has_main && has_small) ? 2 : 1;
+    int kacc = 512 / (256 * b.ncls);
+    while (kacc > 1 && kacc > nkb) kacc >>= 1;
+    b.kacc = kacc;
+    dim3 grid((unsigned)(2 * ceil_div(a.N, 256)), (unsigned)ceil_div(a.M, 2 * BM), (unsigned)nbatch);
+    tc_gemm_pair_kernel<STAGES, BKT><<<grid, 192, smem, st>>>(ma, mb_half, b);
+    count_launch();
+    OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
 }  // namespace
 
 int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
@@ -408,11 +597,17 @@ int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64
 }
 
 int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int nbatch, int bn,
-         cudaStream_t st) {
+         cudaStream_t st, const CUtensorMap *mapB_half) {
     if (a.M <= 0 || a.N <= 0 || a.K < 0 || a.nA < 1 || a.nA > 3 || a.nB < 1 || a.nB > 3) return OMM_ERR_ARG;
     if (a.npairs < 1 || a.npairs > 9 || nbatch < 1) return OMM_ERR_ARG;
     for (int p = 0; p < a.npairs; ++p)
         if (a.pa[p] >= a.nA || a.pb[p] >= a.nB) return OMM_ERR_ARG;
+    // CTA pairs: 256 x 256 tiles with the B tile split between the two SMs; needs the
+    // 64-wide K blocks and a B map whose box is 128 rows
+    if (mapB_half != nullptr && a.bk == 64 && bn == 256) {
+        if (a.nA + a.nB <= 4) return launch_tc_pair<3, 64>(mapA, *mapB_half, a, nbatch, st);   // 3 x 64 KB
+        return launch_tc_pair<2, 64>(mapA, *mapB_half, a, nbatch, st);                         // 2 x 96 KB
+    }
     // The tensor maps decide the K-block width: 64 (128-byte swizzle) or 32 (64-byte).
     if (a.bk == 32) {
         if (bn == 256) return launch_tc<256, 3, 32>(mapA, mapB, a, nbatch, st);

@@ -38,8 +38,11 @@ struct TcArgs {
 
 int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
                    int64_t plane_elems, int nplanes, int box_rows, int bk = 64);
+// mapB_half: a map of the same B planes with a 128-row box; when given (and the
+// maps use 64-wide K blocks and bn = 256), the GEMM runs on CTA pairs
+// (tcgen05.mma.cta_group::2, 256 x 256 tiles, half the B tile per SM)
 int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int nbatch, int bn,
-         cudaStream_t st);
+         cudaStream_t st, const CUtensorMap *mapB_half = nullptr);
 int pack_cm(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,
             int64_t plane, int ndig, const DevState *state, cudaStream_t st);
 int pack_t(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,

@@ -32,7 +32,7 @@ class Options(C.Structure):
                 ("filter_eps", C.c_double), ("stream", C.c_void_p), ("refine", C.c_int32),
                 ("exact_digits", C.c_int32), ("split_digits", C.c_int32), ("graphs", C.c_int32),
                 ("n_occupied", C.c_int32), ("precon", C.c_int32), ("tau_T", C.c_double),
-                ("screen_eps", C.c_double)]
+                ("screen_eps", C.c_double), ("gemm_pair", C.c_int32)]
 
 
 class Pattern(C.Structure):
