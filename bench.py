@@ -239,7 +239,7 @@ def run_omm(args):
     torch.cuda.synchronize()
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
                 orth_tol=TOL[prec]["orth_tol"], stream=stream.cuda_stream, cholesky=int(args.cholesky),
-                split_digits=args.split_digits, gemm_pair=args.gemm_pair)
+                split_digits=args.split_digits, gemm_pair=args.gemm_pair, gemm_persistent=args.gemm_persistent)
     solver = omm.Solver(m, n, 8, **opts)
     tol = TOL[prec]["tol"]
 
@@ -412,6 +412,7 @@ def run_omm(args):
         "config": {"workload": workload_name(sysm) + (" cholesky-reduced" if args.cholesky else ""),
                    "precision": prec, "tol": tol, "cholesky": bool(args.cholesky),
                    "split_digits": args.split_digits, "gemm_pair": bool(args.gemm_pair),
+                   "gemm_persistent": bool(args.gemm_persistent),
                    "refine": "exact-digit tensor cores" if prec == "mixed" else None,
                    "orth_tol": TOL[prec]["orth_tol"], "parallelism": f"replicas x{ws}",
                    "l2": "working set (H, S = 256 MiB, plus W/D/products) exceeds the 129 MB L2"},
@@ -629,7 +630,8 @@ def run_profile(args):
     prec = args.precision
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
                 orth_tol=TOL[prec]["orth_tol"], stream=torch.cuda.current_stream().cuda_stream,
-                cholesky=int(args.cholesky), split_digits=args.split_digits, gemm_pair=args.gemm_pair)
+                cholesky=int(args.cholesky), split_digits=args.split_digits, gemm_pair=args.gemm_pair,
+                gemm_persistent=args.gemm_persistent)
     if args.max_iter > 0:
         opts["max_iter"] = args.max_iter
     solver = omm.Solver(sysm.m, sysm.n, 8, **opts)
@@ -746,6 +748,11 @@ def run_md(args):
 
 # ---------------------------------------------------------------- C4: batched uneven solves
 def run_c4(args):
+    """64 uneven dense systems (k-point/spin-like), mixed precision, solved
+    together: as one group (each CG step's split products as one persistent
+    grouped launch over all systems, tile mode autotuned, chunks of steps as a
+    CUDA graph) and, for comparison in the same run, one handle per stream driven
+    together, and one by one."""
     import torch
     from paper_2209_05934_gb300 import omm
 
@@ -758,48 +765,65 @@ def run_c4(args):
     solvers = [omm.Solver(s.m, s.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6, graphs=args.graphs)
                for s in systems]
 
-    def batch_step():
+    def set_all():
         for sv, (H, S, _) in zip(solvers, data):
             sv.set_HS(H, S)
+
+    def grouped_step():
+        set_all()
+        E, it, st, rc = omm.batch_solve_grouped(solvers, [d[2] for d in data], tol=1e-10, tile_mode=args.tile_mode)
+        return E, it, st
+
+    def streams_step():
+        set_all()
         return omm.batch_solve(solvers, [d[2] for d in data], tol=1e-10)
 
-    def serial_step():
-        out = []
-        for sv, (H, S, W0) in zip(solvers, data):
-            sv.set_HS(H, S)
-            out.append(sv.solve(W0, tol=1e-10, raise_on_error=False))
-        return out
-
-    for _ in range(args.warmup):
-        batch_step()
-    torch.cuda.synchronize()
-    launches0 = omm.kernel_launches()
-    t0 = time.perf_counter()
-    with ClockSampler(0) as clk:
-        for _ in range(args.steps):
-            E, it, st = batch_step()
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            out = fn()
         torch.cuda.synchronize()
-    t_batch = (time.perf_counter() - t0) / args.steps
-    launches = omm.kernel_launches() - launches0
+        l0 = omm.kernel_launches()
+        t0 = time.perf_counter()
+        with ClockSampler(0) as clk:
+            for _ in range(steps):
+                out = fn()
+            torch.cuda.synchronize()
+        return out, (time.perf_counter() - t0) / steps, omm.kernel_launches() - l0, clk.summary()
+
+    (Eg, itg, stg), t_group, launches, clocks = timed(grouped_step, args.steps)
+    modes, tune_ms = omm.batch_last_tuning()
+    (Es, its, sts), t_streams, _, _ = timed(streams_step, max(1, args.steps // 2))
     t0 = time.perf_counter()
-    serial = serial_step()
+    serial = []
+    for sv, (H, S, W0) in zip(solvers, data):
+        sv.set_HS(H, S)
+        serial.append(sv.solve(W0, tol=1e-10, raise_on_error=False))
     torch.cuda.synchronize()
     t_serial = time.perf_counter() - t0
-    same = all(serial[i][0] == E[i] and serial[i][1] == it[i] for i in range(count))
-    line = {"metric": "OMM solves/s, batched uneven systems", "value": count / t_batch, "unit": "solves/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch,
+    same = all(serial[i][0] == Eg[i] and serial[i][1] == itg[i] for i in range(count))
+    same_streams = bool(np.array_equal(Es, Eg) and np.array_equal(its, itg))
+    names = ["single CTA", "CTA pair"]
+    line = {"metric": "OMM solves/s, batched uneven systems", "value": count / t_group, "unit": "solves/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_group,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split+f64",
             "data": "synthetic",
             "config": {"workload": (f"{count} dense systems, atoms round(exp(U(ln 32, ln 384))) (seed 4): "
                                     f"m {int(min(s.m for s in systems))}..{int(max(s.m for s in systems))}, n = m/4"),
                        "precision": "mixed", "tol": 1e-10, "orth_tol": 1e-6,
-                       "execution": "one handle per system on its own stream, driven together"
-                                    + ("; chunks of CG steps replayed as CUDA graphs" if args.graphs else ""),
-                       "graphs": bool(args.graphs)},
+                       "execution": ("one group: per CG step of the first phase, each split product of all "
+                                     "systems as one persistent grouped tensor-core launch, line minimum/updates/"
+                                     "direction per system on its own stream in between, chunks of 8 steps as "
+                                     "one CUDA graph; the refinement per system"),
+                       "tile_mode_requested": args.tile_mode},
+            "tuning": {"products": names[int(modes[0])], "contractions": names[int(modes[1])],
+                       "gradient": names[int(modes[2])],
+                       "timed_ms_single_pair": tune_ms.tolist()},
+            "streams": {"value": count / t_streams, "unit": "solves/s", "ms": 1e3 * t_streams,
+                        "results_equal_grouped": same_streams},
             "one_by_one": {"value": count / t_serial, "unit": "solves/s", "ms": 1e3 * t_serial},
-            "results_equal_alone": bool(same), "all_ok": bool((st == omm.OK).all()),
-            "iters": {"min": int(it.min()), "max": int(it.max())},
-            "gpu_launches": int(launches), "clocks": clk.summary()}
+            "results_equal_alone": bool(same), "all_ok": bool((stg == omm.OK).all()),
+            "iters": {"min": int(itg.min()), "max": int(itg.max())},
+            "gpu_launches": int(launches), "clocks": clocks}
     print(json.dumps(line), flush=True)
     for sv in solvers:
         sv.close()
@@ -807,18 +831,27 @@ def run_c4(args):
 
 # ---------------------------------------------------------------- C5: serving
 def run_c5(args):
+    """Serving loop: Poisson arrivals of SCF-like sequences (one dense system,
+    then perturbed Hamiltonians H <- H + sym(N(0, 1e-3 eV)) on its nonzeros,
+    each solve warm-started from the resident W), dense m = 8 x round(exp(U(ln 64,
+    ln 1024))) atoms (512 .. 8192), n = m/4.  The same sequence set is served at
+    every arrival rate; each rate's run is timed from the first arrival to the
+    last result, and every solve's time-to-converge runs from its submission
+    (the sequence's arrival, or the previous solve's result) to its result."""
     import torch
     from paper_2209_05934_gb300 import omm, serving
 
     omm.lib()
     rng = np.random.Generator(np.random.PCG64(5))
-    seqs = []
-    for i in range(args.sequences):
-        side = int(rng.choice([4, 5, 6, 8]))          # 64..512 atoms: m = 512..4096
-        seqs.append(synth.make_system(side, seed=5000 + i))
+    natoms = np.round(np.exp(rng.uniform(np.log(64), np.log(1024), args.sequences))).astype(int)
+    t_gen = time.perf_counter()
+    seqs = [synth.make_batch_system(int(N), seed=5000 + i) for i, N in enumerate(natoms)]
     dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
-    base = [(dev(s.dense_H()), dev(s.dense_S()), dev(s.W0_dense()), dev((s.dense_H() != 0).astype(np.float64)))
-            for s in seqs]
+    base = []
+    for sq in seqs:
+        H = sq.dense_H()
+        base.append((dev(H), dev(sq.dense_S()), dev(sq.W0_dense()), torch.from_numpy(H != 0).to("cuda")))
+    t_gen = time.perf_counter() - t_gen
 
     def make_inputs_factory(i):
         H0, S, _, mask = base[i]
@@ -836,43 +869,65 @@ def run_c5(args):
             return Hk, S
         return make
 
+    ms = [int(sq.m) for sq in seqs]
     out = {"metric": "OMM serving: solves/s and p50/p99 time-to-converge", "unit": "solves/s", "n_gpus": 1,
            "data": "synthetic", "higher_is_better": True, "dtype": "bf16-split+f64",
-           "config": {"workload": (f"{args.sequences} sequences per rate, each 1 + {args.scf_steps - 1} SCF-like "
-                                   "perturbations H <- H + sym(N(0, 1e-3)) on the nonzeros, warm-started; "
-                                   "dense m in {512, 1000, 1728, 4096}, n = m/4"),
-                      "precision": "mixed", "tol": 1e-10, "orth_tol": 1e-6}, "rates": []}
-    for rate in args.rates:
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(seqs)))
+           "config": {"workload": (f"{args.sequences} sequences served at each rate, each 1 + {args.scf_steps - 1} "
+                                   "SCF-like perturbations H <- H + sym(N(0, 1e-3 eV)) on the nonzeros, "
+                                   "warm-started; dense m = 8 round(exp(U(ln 64, ln 1024))), n = m/4"),
+                      "m_min": min(ms), "m_max": max(ms), "m_median": int(np.median(ms)),
+                      "precision": "mixed", "tol": 1e-10, "orth_tol": 1e-6,
+                      "hbm_budget_gb": args.hbm_budget_gb, "input_generation_s": t_gen}, "rates": []}
+    # warm-up: modules loaded, one small and one large solve
+    for i in (int(np.argmin(ms)), int(np.argmax(ms))):
+        w = omm.Solver(seqs[i].m, seqs[i].n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6)
+        w.set_HS(base[i][0], base[i][1])
+        w.solve(base[i][2], tol=1e-10, raise_on_error=False)
+        w.close()
+    torch.cuda.synchronize()
+    launches0 = omm.kernel_launches()
+    for ri, rate in enumerate(args.rates):
+        arr_rng = np.random.Generator(np.random.PCG64(500 + ri))
+        arrivals = np.cumsum(arr_rng.exponential(1.0 / rate, size=len(seqs)))
         arrivals -= arrivals[0]
         reqs = [serving.Request(rid=i, arrival=float(arrivals[i]), m=seqs[i].m, n=seqs[i].n, steps=args.scf_steps,
                                 make_inputs=make_inputs_factory(i), W0=base[i][2], graphs=args.graphs)
                 for i in range(len(seqs))]
         server = serving.Server(hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)))
-        t0 = time.perf_counter()
-        recs = server.run(reqs)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+        with ClockSampler(0) as clk:
+            t0 = time.perf_counter()
+            recs = server.run(reqs)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
         st = serving.latency_stats(recs)
+        cold = serving.latency_stats([r for r in recs if r.step == 0])
+        warm = serving.latency_stats([r for r in recs if r.step > 0])
+        big = serving.latency_stats([r for r in recs if r.m >= 4096])
         out["rates"].append({"rate_seq_per_s": rate, "solves": st["solves"], "solves_per_s": st["solves"] / wall,
-                             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_inflight": server.max_inflight,
+                             "wall_s": wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                             "cold": {"p50_ms": cold["p50_ms"], "p99_ms": cold["p99_ms"]},
+                             "warm": {"p50_ms": warm["p50_ms"], "p99_ms": warm["p99_ms"]},
+                             "m_ge_4096": {"p50_ms": big["p50_ms"], "p99_ms": big["p99_ms"], "solves": big["solves"]},
+                             "max_inflight": server.max_inflight,
                              "all_ok": all(r.status == omm.OK for r in recs),
                              "statuses": sorted({int(r.status) for r in recs}),
-                             "iters_first_solve_mean": float(np.mean([r.iters for r in recs if r.step == 0])),
-                             "iters_warm_mean": float(np.mean([r.iters for r in recs if r.step > 0]))})
+                             "iters_cold_mean": float(np.mean([r.iters for r in recs if r.step == 0])),
+                             "iters_warm_mean": float(np.mean([r.iters for r in recs if r.step > 0])),
+                             "clocks": clk.summary()})
     out["value"] = max(r["solves_per_s"] for r in out["rates"])
+    out["gpu_launches"] = int(omm.kernel_launches() - launches0)
 
     # the same request set served by the mixed form and by the plain FP64 GPU form
     if args.fp64_sequences > 0:
-        k = min(args.fp64_sequences, len(seqs))
+        pick = [i for i in np.argsort(ms) if ms[i] <= 2048][-args.fp64_sequences:]
         rate = 50.0
-        arrivals = np.cumsum(np.random.Generator(np.random.PCG64(55)).exponential(1.0 / rate, size=k))
+        arrivals = np.cumsum(np.random.Generator(np.random.PCG64(55)).exponential(1.0 / rate, size=len(pick)))
         arrivals -= arrivals[0]
-        cmp = {"sequences": k, "rate_seq_per_s": rate, "m": [int(seqs[i].m) for i in range(k)]}
+        cmp = {"sequences": len(pick), "rate_seq_per_s": rate, "m": [ms[i] for i in pick]}
         for name, p in (("mixed", omm.PREC_MIXED), ("fp64", omm.PREC_FP64)):
-            reqs = [serving.Request(rid=i, arrival=float(arrivals[i]), m=seqs[i].m, n=seqs[i].n,
-                                    steps=args.scf_steps, make_inputs=make_inputs_factory(i), W0=base[i][2],
-                                    precision=p) for i in range(k)]
+            reqs = [serving.Request(rid=int(i), arrival=float(arrivals[j]), m=seqs[i].m, n=seqs[i].n,
+                                    steps=args.scf_steps, make_inputs=make_inputs_factory(int(i)), W0=base[i][2],
+                                    precision=p) for j, i in enumerate(pick)]
             server = serving.Server(hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)))
             t0 = time.perf_counter()
             recs = server.run(reqs)
@@ -883,7 +938,7 @@ def run_c5(args):
                          "all_ok": all(r.status == omm.OK for r in recs),
                          "E_last": {r.rid: float(r.E) for r in recs if r.step == args.scf_steps - 1}}
         cmp["max_rel_E_diff"] = max(abs(cmp["mixed"]["E_last"][i] - cmp["fp64"]["E_last"][i])
-                                    / abs(cmp["fp64"]["E_last"][i]) for i in range(k))
+                                    / abs(cmp["fp64"]["E_last"][i]) for i in cmp["fp64"]["E_last"])
         for name in ("mixed", "fp64"):
             del cmp[name]["E_last"]
         out["mixed_vs_fp64"] = cmp
@@ -904,12 +959,14 @@ def main():
                     help="print the measured FP64 GEMM throughput (the FP64 roofline denominator) and exit")
     ap.add_argument("--no-fp64-beside", action="store_true",
                     help="c2: skip the plain FP64 GPU solve reported beside the mixed form")
-    ap.add_argument("--fp64-sequences", type=int, default=6,
+    ap.add_argument("--fp64-sequences", type=int, default=3,
                     help="c5: sequences of the mixed-vs-FP64 serving comparison (0 skips it)")
     ap.add_argument("--split-digits", type=int, default=2, choices=[2, 3],
                     help="mixed form: BF16 digits per operand in the first phase (3 pairs or 6)")
     ap.add_argument("--gemm-pair", type=int, default=1, choices=[0, 1],
                     help="mixed form: split products on CTA pairs (cta_group::2) or one CTA per tile")
+    ap.add_argument("--gemm-persistent", type=int, default=0, choices=[0, 1],
+                    help="mixed form: split products as persistent tile-list launches")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="c4/c5: replay chunks of CG steps as captured CUDA graphs")
     ap.add_argument("--no-kinetic", action="store_true",
@@ -920,14 +977,18 @@ def main():
                     help="c2 dense workload (default); c3 linear-scaling to convergence; "
                          "c4 batched uneven solves; c5 serving loop")
     ap.add_argument("--batch", type=int, default=64, help="c4: number of systems")
+    ap.add_argument("--tile-mode", type=int, default=-1, choices=[-1, 0, 1],
+                    help="c4: grouped launch tile mode (-1 autotune, 0 single CTA, 1 CTA pair)")
     ap.add_argument("--screen-eps", type=float, default=0.0,
                     help="c3: norm-based screening threshold of the sparse block products (0: off)")
     ap.add_argument("--md-steps", type=int, default=5, help="md: snapshots per chain")
     ap.add_argument("--md-step", type=float, default=0.03, help="md: Angstrom per snapshot per unit velocity")
     ap.add_argument("--md-max-iter", type=int, default=20000, help="md: CG step cap of the sparse solves")
-    ap.add_argument("--sequences", type=int, default=12, help="c5: sequences per arrival rate")
+    ap.add_argument("--sequences", type=int, default=91,
+                    help="c5: sequences served at each arrival rate (91 x 11 solves = 1001 per rate)")
     ap.add_argument("--scf-steps", type=int, default=11, help="c5: solves per sequence (1 + perturbations)")
-    ap.add_argument("--rates", type=float, nargs="+", default=[10.0, 50.0, 200.0], help="c5: arrivals per second")
+    ap.add_argument("--rates", type=float, nargs="+", default=[10.0, 20.0, 50.0, 100.0, 200.0, 500.0],
+                    help="c5: sequence arrivals per second")
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0, help="c5: admission budget")
     args = ap.parse_args()
     if args.fp64_peak:

@@ -150,6 +150,12 @@ typedef struct {
                               pairs (tcgen05.mma.cta_group::2: 256 x 256 tiles, each SM of a
                               pair holding half of the B tile); 0: one CTA per 128 x 256 tile.
                               Three-digit products always take one CTA per tile */
+    int32_t gemm_persistent; /* mixed form, 1: the step's split products (H'D and SD, the
+                              contractions, the first phase's gradient) run as persistent
+                              launches over a tile list (152 CTAs, or 76 pairs, each taking
+                              every 152nd tile; the next tile's operands load while the last
+                              one's results are written); 0 (default): one CTA (or pair) per
+                              tile.  The results are the same bits either way */
 } omm_options;
 
 enum {
@@ -289,6 +295,38 @@ int omm_solve_end(omm_handle *h, double *W_out, int32_t W_out_on_device, double 
  */
 int omm_batch_solve(omm_handle **handles, int32_t count, const double *const *W0, int32_t W0_on_device,
                     double tol, double *E_out, int32_t *iters_out, int32_t *status_out);
+
+/*
+ * The same batch as omm_batch_solve, run as one group (independent systems such
+ * as spins, k-points or the uneven systems of a batch; section "Recommendations
+ * for OMM solver use").  The first, split-precision phase of every system runs in
+ * lock step: each CG step's three split products (H'D and SD, the contractions,
+ * the gradient) are each ONE persistent grouped tensor-core launch over the tile
+ * lists of all systems (longest K first), while each system's line minimum,
+ * updates and direction run on its own stream in between; a chunk of 8 such steps
+ * is captured once as a CUDA graph and replayed until every system has left the
+ * first phase.  The refinement then runs per system as in omm_batch_solve.
+ * tile_mode: 0 one CTA per 128 x 256 tile, 1 CTA pairs (256 x 256 tiles,
+ * tcgen05.mma.cta_group::2), -1 autotune: the first call for a group of this
+ * shape (the systems' (m, n) in order) times both modes on each of the three
+ * products and keeps the faster per product for every later call of the same
+ * shape (omm_batch_last_tuning reports the choice).  Every result equals the same
+ * solve run alone with omm_solve, bit for bit, whatever the mode.
+ * Requirements: dense handles of the mixed form with split_digits = 2, no
+ * Cholesky variant, no preconditioning, profiling off, each on its own stream
+ * other than the legacy default stream (OMM_ERR_UNSUPPORTED otherwise).
+ * Arguments and results as omm_batch_solve; synchronous.
+ */
+int omm_batch_solve_grouped(omm_handle **handles, int32_t count, const double *const *W0, int32_t W0_on_device,
+                            double tol, int32_t tile_mode, double *E_out, int32_t *iters_out, int32_t *status_out);
+
+/*
+ * Tile modes of the last omm_batch_solve_grouped call: modes[3] for the products,
+ * the contractions and the gradient (0 single CTA, 1 CTA pair); ms[6] (nullable):
+ * the autotuner's timed milliseconds per product and mode, 0 when the mode was
+ * given or taken from an earlier call.
+ */
+int omm_batch_last_tuning(int32_t *modes, float *ms);
 
 /* Diagnostics of the last set_HS / solve. */
 int omm_get_diag(omm_handle *h, omm_diag *d);

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "chol.cuh"
@@ -65,6 +66,13 @@ struct ExactBufs {
     CUtensorMap mapHS_A, mapW, mapHWSW_B, mapSWHW_A, mapHSW_B;
 };
 
+// Device copy of a persistent tile list (one problem) of a handle's split product.
+struct HandleList {
+    omm::tc::TileProblem *probs = nullptr;
+    omm::tc::TileRef *tiles = nullptr;
+    int ntiles = 0;
+};
+
 struct omm_handle {
     int64_t m = 0, n = 0;
     int32_t bm = 0;
@@ -98,6 +106,7 @@ struct omm_handle {
     int graph_eager[kPhases] = {};
     MixedBufs mx;
     ExactBufs ex;
+    HandleList lists[3];      // persistent tile lists of the step's split products (gemm_persistent)
     double *L = nullptr;      // Cholesky variant: factor of S (m x m)
     double *Wsave = nullptr;  // Cholesky variant: W in the original basis (m x n)
     double *S0 = nullptr;     // Cholesky variant: the original S (its slot holds I)
@@ -188,6 +197,10 @@ void free_handle(omm_handle *h) {
     cudaFree(h->mx.Pd);
     cudaFree(h->mx.Gd);
     cudaFree(h->mx.PG32);
+    for (auto &L : h->lists) {
+        cudaFree(L.probs);
+        cudaFree(L.tiles);
+    }
     omm::sp::release(h->sd);
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -415,13 +428,22 @@ omm::DigitOut dig_SWHW(omm_handle *h) { return {h->mx.SWHWd, h->mx.ld2n, h->m * 
 omm::DigitOut dig_HSW(omm_handle *h) { return {h->mx.HSWd, h->mx.ld2n, h->n * h->mx.ld2n, h->cur_dig}; }
 constexpr omm::DigitOut kNoDigits{nullptr, 0, 0};
 
+// A split product of the mixed CG step: its arguments, operand maps and batch count.
+struct SplitCall {
+    omm::tc::TcArgs a;
+    const CUtensorMap *mA = nullptr, *mB = nullptr, *mBh = nullptr;   // B with 256-row / 128-row boxes
+    int nbatch = 1;
+};
+
 // [H'; S] times the digits of W (rows b_row0 = 0) or D (b_row0 = n) of WDd:
 // FP64 results to C (H' part) and C + c_step (S part), digits to HDSDd.
-int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_step, int64_t dout_row0,
-                   int64_t dout_step) {
+SplitCall products_call(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_step, int64_t dout_row0,
+                        int64_t dout_step) {
     const int64_t m = h->m, n = h->n;
     MixedBufs &x = h->mx;
-    omm::tc::TcArgs a = tc_args(h, (int)m, (int)n, (int)m);
+    SplitCall c;
+    omm::tc::TcArgs &a = c.a;
+    a = tc_args(h, (int)m, (int)n, (int)m);
     a.a_row0 = 0;
     a.a_row_step = (int)m;
     a.b_row0 = b_row0;
@@ -435,8 +457,92 @@ int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_s
     a.dplane = 2 * n * x.ldm;
     a.dout_step = dout_step * x.ldm;
     a.ndig = h->cur_dig;
-    if (!s_identity(h)) return omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 2, kBN, h->stream, pair_map(h, x.mapWD_A));
-    TRY(omm::tc::gemm(x.mapHS_A, x.mapWD_B, a, 1, kBN, h->stream, pair_map(h, x.mapWD_A)));
+    c.mA = &x.mapHS_A;
+    c.mB = &x.mapWD_B;
+    c.mBh = &x.mapWD_A;
+    c.nbatch = s_identity(h) ? 1 : 2;
+    return c;
+}
+
+// Z = [W D]^T [H'D SD]
+SplitCall contract_call(omm_handle *h) {
+    const int64_t m = h->m, n = h->n;
+    MixedBufs &x = h->mx;
+    SplitCall c;
+    c.a = tc_args(h, (int)(2 * n), (int)(2 * n), (int)m);
+    c.a.C32 = x.Z32;
+    c.a.ldc = 2 * n;
+    c.mA = &x.mapWD_A;
+    c.mB = &x.mapHDSD_B;
+    c.mBh = &x.mapHDSD_H;
+    return c;
+}
+
+// G = 4 H'W - 2 [SW H'W][H_W ; S_W]
+SplitCall gradient_call(omm_handle *h) {
+    const int64_t m = h->m, n = h->n;
+    MixedBufs &x = h->mx;
+    SplitCall c;
+    c.a = tc_args(h, (int)m, (int)n, (int)(2 * n));
+    c.a.alpha = -2.0;
+    c.a.beta = 4.0;
+    c.a.Cin = h->SWHW + m * n;
+    c.a.ldcin = m;
+    c.a.C32 = x.G32;
+    c.a.ldc = m;
+    c.mA = &x.mapSWHW_A;
+    c.mB = &x.mapHSW_B;
+    c.mBh = &x.mapHSW_H;
+    return c;
+}
+
+// Tile-list form of one of the step's three split products (0 products, 1
+// contraction, 2 gradient) for a persistent launch (omm_options.gemm_persistent):
+// the arguments are fixed for the handle's life, so the list is built once.
+int list_mode(omm_handle *h) { return h->opt.gemm_pair ? omm::tc::LIST_PAIR : omm::tc::LIST_SINGLE; }
+
+int list_ctas(int mode, int64_t ntiles) {
+    int64_t c = mode == omm::tc::LIST_PAIR ? 2 * ntiles : ntiles;
+    if (c > 152) c = 152;
+    return (int)c;
+}
+
+omm::tc::TileProblem tile_problem(const SplitCall &c, int mode) {
+    omm::tc::TileProblem p;
+    memset(&p, 0, sizeof(p));
+    p.mapA = *c.mA;
+    p.mapB = mode == omm::tc::LIST_PAIR ? *c.mBh : *c.mB;
+    p.a = c.a;
+    omm::tc::list_prepare(p.a);
+    return p;
+}
+
+int run_split(omm_handle *h, const SplitCall &c, int slot) {
+    const bool list = slot >= 0 && h->opt.gemm_persistent && c.a.bk == 64 && c.a.nA + c.a.nB <= 4;
+    if (!list) return omm::tc::gemm(*c.mA, *c.mB, c.a, c.nbatch, kBN, h->stream, pair_map(h, *c.mBh));
+    HandleList &L = h->lists[slot];
+    const int mode = list_mode(h);
+    if (L.probs == nullptr) {
+        const omm::tc::TileProblem p = tile_problem(c, mode);
+        std::vector<omm::tc::TileRef> tiles;
+        omm::tc::list_tiles(0, p.a, c.nbatch, mode, tiles);
+        OMM_CUDA_TRY(cudaMalloc((void **)&L.probs, sizeof(p)));
+        OMM_CUDA_TRY(cudaMalloc((void **)&L.tiles, tiles.size() * sizeof(omm::tc::TileRef)));
+        OMM_CUDA_TRY(cudaMemcpy(L.probs, &p, sizeof(p), cudaMemcpyHostToDevice));
+        OMM_CUDA_TRY(cudaMemcpy(L.tiles, tiles.data(), tiles.size() * sizeof(omm::tc::TileRef), cudaMemcpyHostToDevice));
+        L.ntiles = (int)tiles.size();
+    }
+    return omm::tc::gemm_list(L.probs, L.tiles, L.ntiles, mode, list_ctas(mode, L.ntiles), c.a.nA, c.a.nB, h->stream);
+}
+
+int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_step, int64_t dout_row0,
+                   int64_t dout_step) {
+    const int64_t m = h->m, n = h->n;
+    MixedBufs &x = h->mx;
+    const SplitCall c = products_call(h, b_row0, C, C32, c_step, dout_row0, dout_step);
+    // the iteration's products (D, FP32 out) have fixed arguments: list slot 0
+    TRY(run_split(h, c, (C32 != nullptr && b_row0 == (int)n) ? 0 : -1));
+    if (!s_identity(h)) return OMM_OK;
     // z = 1 (S times the B rows) is the B rows themselves: their FP32/FP64 values and digits
     const int64_t mn = m * n;
     if (C32 != nullptr)   // iteration: S D = D
@@ -451,29 +557,9 @@ int split_products(omm_handle *h, int b_row0, double *C, float *C32, int64_t c_s
     return OMM_OK;
 }
 
-// Z = [W D]^T [H'D SD]
-int split_contract(omm_handle *h) {
-    const int64_t m = h->m, n = h->n;
-    MixedBufs &x = h->mx;
-    omm::tc::TcArgs a = tc_args(h, (int)(2 * n), (int)(2 * n), (int)m);
-    a.C32 = x.Z32;
-    a.ldc = 2 * n;
-    return omm::tc::gemm(x.mapWD_A, x.mapHDSD_B, a, 1, kBN, h->stream, pair_map(h, x.mapHDSD_H));
-}
+int split_contract(omm_handle *h) { return run_split(h, contract_call(h), 1); }
 
-// G = 4 H'W - 2 [SW H'W][H_W ; S_W]
-int split_gradient(omm_handle *h) {
-    const int64_t m = h->m, n = h->n;
-    MixedBufs &x = h->mx;
-    omm::tc::TcArgs a = tc_args(h, (int)m, (int)n, (int)(2 * n));
-    a.alpha = -2.0;
-    a.beta = 4.0;
-    a.Cin = h->SWHW + m * n;
-    a.ldcin = m;
-    a.C32 = x.G32;
-    a.ldc = m;
-    return omm::tc::gemm(x.mapSWHW_A, x.mapHSW_B, a, 1, kBN, h->stream, pair_map(h, x.mapHSW_H));
-}
+int split_gradient(omm_handle *h) { return run_split(h, gradient_call(h), 2); }
 
 // FP64 gradient (CUDA cores), rounded to the FP32 gradient of the mixed form
 int fp64_gradient(omm_handle *h) {
@@ -647,6 +733,22 @@ int mixed_start(omm_handle *h) {
     return mixed_direction(h, 1);
 }
 
+// Line minimum and state updates of a mixed step (after the contractions).
+int mixed_glue1(omm_handle *h, bool accurate_gradient) {
+    const int64_t m = h->m, n = h->n, mn = m * n;
+    cudaStream_t st = h->stream;
+    omm::DevState *s = h->dstate;
+    MixedBufs &x = h->mx;
+    { StageTimer t(h, OMM_STAGE_LINESEARCH);
+      TRY(omm::mx_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 0), ctr(h, 0), s, st)); }
+    { StageTimer t(h, OMM_STAGE_UPDATE);
+      TRY(omm::mx_update(m, n, h->WD, x.D32, h->SWHW + mn, x.HDSD32, h->SWHW, x.HDSD32 + mn, s, dig_W(h),
+                         accurate_gradient ? kNoDigits : dig_SWHW(h), st));
+      TRY(omm::mx_nn_update((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 1), ctr(h, 1), s,
+                            accurate_gradient ? kNoDigits : dig_HSW(h), st)); }
+    return OMM_OK;
+}
+
 // One CG step of the mixed form: split-precision products with FP32 outputs,
 // FP64 state updated from FP32 increments; accurate_gradient selects the
 // accurate gradient of the refinement sweep (exact-digit or FP64 products).
@@ -656,18 +758,10 @@ int mixed_iteration(omm_handle *h, bool accurate_gradient) {
     // refinement they are small against the exactly re-anchored state and the
     // exact-digit gradient, so two digits cost no extra steps at C2
     h->cur_dig = h->opt.split_digits;
-    cudaStream_t st = h->stream;
-    omm::DevState *s = h->dstate;
     MixedBufs &x = h->mx;
     { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(split_products(h, (int)n, nullptr, x.HDSD32, mn, 0, n)); }
     { StageTimer t(h, OMM_STAGE_CONTRACT); TRY(split_contract(h)); }
-    { StageTimer t(h, OMM_STAGE_LINESEARCH);
-      TRY(omm::mx_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 0), ctr(h, 0), s, st)); }
-    { StageTimer t(h, OMM_STAGE_UPDATE);
-      TRY(omm::mx_update(m, n, h->WD, x.D32, h->SWHW + mn, x.HDSD32, h->SWHW, x.HDSD32 + mn, s, dig_W(h),
-                         accurate_gradient ? kNoDigits : dig_SWHW(h), st));
-      TRY(omm::mx_nn_update((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 1), ctr(h, 1), s,
-                            accurate_gradient ? kNoDigits : dig_HSW(h), st)); }
+    TRY(mixed_glue1(h, accurate_gradient));
     if (accurate_gradient) {
         if (h->opt.refine == OMM_REFINE_EXACT) {
             TRY(exact_gradient(h));
@@ -947,6 +1041,11 @@ bool idle(const omm_handle *h) { return h->phase == PH_IDLE || h->phase == PH_FI
 
 }  // namespace
 
+namespace {
+int begin_setup(omm_handle *h, const double *W0, int32_t W0_on_device, double tol);
+int drive_batch(omm_handle **handles, int32_t count, double *E_out, int32_t *iters_out, int32_t *status_out);
+}
+
 extern "C" {
 
 void omm_default_options(omm_options *opt) {
@@ -969,6 +1068,7 @@ void omm_default_options(omm_options *opt) {
     opt->tau_T = 136.05693122994;   // 10 Ry in eV
     opt->screen_eps = 0.0;
     opt->gemm_pair = 1;
+    opt->gemm_persistent = 0;
 }
 
 const char *omm_status_str(int status) {
@@ -1218,6 +1318,16 @@ int omm_md_guess(omm_handle *dst, omm_handle *prev, omm_handle *prev2) {
 }
 
 int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, double tol) {
+    TRY(begin_setup(h, W0, W0_on_device, tol));
+    return enqueue_chunk(h);
+}
+
+}  // extern "C"
+
+namespace {
+// Everything of omm_solve_begin but the first chunk: W0 in place, the phase's
+// device state, and the phase's start (H'W, SW, H_W, S_W, energy, G, D).
+int begin_setup(omm_handle *h, const double *W0, int32_t W0_on_device, double tol) {
     if (h == nullptr || !(tol >= 0.0)) return OMM_ERR_ARG;
     h->solved = false;
     if (!h->have_HS) return OMM_ERR_STATE;
@@ -1284,8 +1394,11 @@ int omm_solve_begin(omm_handle *h, const double *W0, int32_t W0_on_device, doubl
         { StageTimer t(h, OMM_STAGE_START); TRY(dense_start(h)); }
     }
     h->have_W = true;
-    return enqueue_chunk(h);
+    return OMM_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int omm_solve_progress(omm_handle *h, int32_t blocking, int32_t *done) {
     if (h == nullptr || done == nullptr) return OMM_ERR_ARG;
@@ -1398,11 +1511,20 @@ int omm_batch_solve(omm_handle **handles, int32_t count, const double *const *W0
         for (int32_t j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return OMM_ERR_ARG;
     }
-    std::vector<int32_t> done(count, 0);
     for (int32_t i = 0; i < count; ++i) {
         const int rc = omm_solve_begin(handles[i], W0 ? W0[i] : nullptr, W0_on_device, tol);
         if (rc != OMM_OK) return rc;
     }
+    return drive_batch(handles, count, E_out, iters_out, status_out);
+}
+
+}  // extern "C"
+
+namespace {
+// Poll every handle of a batch whose solves are under way, enqueue each one's
+// next chunk as its previous one completes, and collect the results.
+int drive_batch(omm_handle **handles, int32_t count, double *E_out, int32_t *iters_out, int32_t *status_out) {
+    std::vector<int32_t> done(count, 0);
     int32_t remaining = count;
     while (remaining > 0) {
         int ready = 0, first_open = -1;
@@ -1433,6 +1555,280 @@ int omm_batch_solve(omm_handle **handles, int32_t count, const double *const *W0
         if (st != OMM_OK && worst == OMM_OK) worst = st;
     }
     return worst;
+}
+}  // namespace
+
+extern "C" {
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- grouped batch
+namespace {
+
+// One stage's tile list over every system of a group (device copy).
+struct GroupList {
+    omm::tc::TileProblem *probs = nullptr;
+    omm::tc::TileRef *tiles = nullptr;
+    int ntiles = 0;
+    void release() {
+        cudaFree(probs);
+        cudaFree(tiles);
+        probs = nullptr;
+        tiles = nullptr;
+        ntiles = 0;
+    }
+};
+
+SplitCall stage_call(omm_handle *h, int stage) {
+    const int64_t m = h->m, n = h->n;
+    if (stage == 0) return products_call(h, (int)n, nullptr, h->mx.HDSD32, m * n, 0, n);
+    return stage == 1 ? contract_call(h) : gradient_call(h);
+}
+
+// Tiles of every system's split product of one stage, the systems with the longest
+// K loop first (a longest-first list over the persistent CTAs).
+int build_group_list(omm_handle **hs, int count, int stage, int mode, GroupList &L) {
+    std::vector<omm::tc::TileProblem> probs((size_t)count);
+    std::vector<int> order((size_t)count);
+    std::vector<int> nb((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const SplitCall c = stage_call(hs[i], stage);
+        probs[i] = tile_problem(c, mode);
+        nb[i] = c.nbatch;
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return probs[a].a.K > probs[b].a.K; });
+    std::vector<omm::tc::TileRef> tiles;
+    for (int i : order) omm::tc::list_tiles(i, probs[i].a, nb[i], mode, tiles);
+    OMM_CUDA_TRY(cudaMalloc((void **)&L.probs, probs.size() * sizeof(omm::tc::TileProblem)));
+    OMM_CUDA_TRY(cudaMalloc((void **)&L.tiles, tiles.size() * sizeof(omm::tc::TileRef)));
+    OMM_CUDA_TRY(cudaMemcpy(L.probs, probs.data(), probs.size() * sizeof(omm::tc::TileProblem), cudaMemcpyHostToDevice));
+    OMM_CUDA_TRY(cudaMemcpy(L.tiles, tiles.data(), tiles.size() * sizeof(omm::tc::TileRef), cudaMemcpyHostToDevice));
+    L.ntiles = (int)tiles.size();
+    return OMM_OK;
+}
+
+int run_group_list(const GroupList &L, int mode, omm_handle *h0, cudaStream_t st) {
+    return omm::tc::gemm_list(L.probs, L.tiles, L.ntiles, mode, list_ctas(mode, L.ntiles), h0->opt.split_digits,
+                              h0->opt.split_digits, st);
+}
+
+// Tile modes chosen by the autotuner per group signature (the systems' (m, n) in
+// order): timed once, then reused, so a group always runs the same schedule.  Both
+// modes give the same bits, so the choice never changes a result.
+struct TuneEntry {
+    std::vector<int64_t> sig;
+    int mode[3];
+    float ms[3][2];
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+TuneEntry g_last_tune;
+
+// Fork every system's stream off the group stream, run fn(h) on each, join back.
+template <class F>
+int fork_join(omm_handle **hs, int count, cudaStream_t gs, cudaEvent_t ev_fork, cudaEvent_t *ev_join, F fn) {
+    OMM_CUDA_TRY(cudaEventRecord(ev_fork, gs));
+    for (int i = 0; i < count; ++i) {
+        OMM_CUDA_TRY(cudaStreamWaitEvent(hs[i]->stream, ev_fork, 0));
+        TRY(fn(hs[i]));
+        OMM_CUDA_TRY(cudaEventRecord(ev_join[i], hs[i]->stream));
+        OMM_CUDA_TRY(cudaStreamWaitEvent(gs, ev_join[i], 0));
+    }
+    return OMM_OK;
+}
+
+// One first-phase CG step of every system: the three split products as grouped
+// persistent launches on the group stream, the per-system line minimum, updates
+// and direction on the systems' own streams in between.
+int group_iteration(omm_handle **hs, int count, const GroupList *L, const int *mode, cudaStream_t gs,
+                    cudaEvent_t ev_fork, cudaEvent_t *ev_join) {
+    TRY(run_group_list(L[0], mode[0], hs[0], gs));
+    TRY(run_group_list(L[1], mode[1], hs[0], gs));
+    TRY(fork_join(hs, count, gs, ev_fork, ev_join, [](omm_handle *h) { return mixed_glue1(h, false); }));
+    TRY(run_group_list(L[2], mode[2], hs[0], gs));
+    return fork_join(hs, count, gs, ev_fork, ev_join, [](omm_handle *h) { return mixed_direction(h, 0); });
+}
+
+}  // namespace
+
+extern "C" {
+
+int omm_batch_solve_grouped(omm_handle **handles, int32_t count, const double *const *W0, int32_t W0_on_device,
+                            double tol, int32_t tile_mode, double *E_out, int32_t *iters_out, int32_t *status_out) {
+    using omm::tc::LIST_PAIR;
+    using omm::tc::LIST_SINGLE;
+    if (handles == nullptr || count < 1 || tile_mode < -1 || tile_mode > 1) return OMM_ERR_ARG;
+    for (int32_t i = 0; i < count; ++i) {
+        omm_handle *h = handles[i];
+        if (h == nullptr) return OMM_ERR_ARG;
+        for (int32_t j = 0; j < i; ++j)
+            if (handles[j] == h) return OMM_ERR_ARG;
+        if (h->sparse || h->opt.precision != OMM_PREC_MIXED || h->opt.split_digits != 2 || h->opt.cholesky ||
+            h->opt.precon != 0 || h->profiling || h->stream == nullptr || h->stream == cudaStreamLegacy ||
+            h->stream == cudaStreamPerThread) {
+            omm::set_error("omm_batch_solve_grouped: handle %d is not a dense mixed-precision handle with two "
+                           "split digits, no Cholesky or preconditioning, profiling off and its own stream", i);
+            return OMM_ERR_UNSUPPORTED;
+        }
+        for (int32_t j = 0; j < i; ++j)
+            if (handles[j]->stream == h->stream) {
+                omm::set_error("omm_batch_solve_grouped: handles %d and %d share a stream", j, i);
+                return OMM_ERR_UNSUPPORTED;
+            }
+    }
+    // ---- phase 1 of every system in lock step
+    for (int32_t i = 0; i < count; ++i) TRY(begin_setup(handles[i], W0 ? W0[i] : nullptr, W0_on_device, tol));
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join((size_t)count, nullptr);
+    GroupList lists[2][3];
+    cudaGraphExec_t gexec = nullptr;
+    int rc = OMM_OK;
+    auto cleanup = [&]() {
+        if (gs) cudaStreamSynchronize(gs);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        for (auto &row : lists)
+            for (auto &L : row) L.release();
+        for (auto e : ev_join)
+            if (e) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (gs) cudaStreamDestroy(gs);
+    };
+#define GTRY(x)                  \
+    do {                         \
+        rc = (x);                \
+        if (rc != OMM_OK) {      \
+            cleanup();           \
+            return rc;           \
+        }                        \
+    } while (0)
+#define GCUDA(x) GTRY((x) == cudaSuccess ? OMM_OK : (omm::set_error("%s failed", #x), OMM_ERR_CUDA))
+    GCUDA(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+    GCUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    for (auto &e : ev_join) GCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (int32_t i = 0; i < count; ++i) {
+        GCUDA(cudaEventRecord(ev_join[i], handles[i]->stream));
+        GCUDA(cudaStreamWaitEvent(gs, ev_join[i], 0));
+    }
+    // ---- tile modes: given, stored for this group, or timed now (each stage's product
+    // is a function of operands the start has already written, so timing both modes
+    // once and then running the step changes nothing)
+    int mode[3] = {tile_mode, tile_mode, tile_mode};
+    TuneEntry te;
+    for (int k = 0; k < 3; ++k) {
+        te.mode[k] = tile_mode;
+        te.ms[k][0] = te.ms[k][1] = 0.f;
+    }
+    for (int32_t i = 0; i < count; ++i) {
+        te.sig.push_back(handles[i]->m);
+        te.sig.push_back(handles[i]->n);
+    }
+    bool tuned = tile_mode >= 0;
+    if (!tuned) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (const auto &e : g_tune)
+            if (e.sig == te.sig) {
+                for (int k = 0; k < 3; ++k) mode[k] = e.mode[k];
+                te = e;
+                tuned = true;
+            }
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int md : {LIST_SINGLE, LIST_PAIR})
+            if (!tuned || mode[k] == md) GTRY(build_group_list(handles, count, k, md, lists[md][k]));
+    if (!tuned) {
+        cudaEvent_t t0, t1;
+        GCUDA(cudaEventCreate(&t0));
+        GCUDA(cudaEventCreate(&t1));
+        for (int k = 0; k < 3; ++k) {
+            for (int md : {LIST_SINGLE, LIST_PAIR}) {
+                float best = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    GCUDA(cudaEventRecord(t0, gs));
+                    GTRY(run_group_list(lists[md][k], md, handles[0], gs));
+                    GCUDA(cudaEventRecord(t1, gs));
+                    GCUDA(cudaEventSynchronize(t1));
+                    float ms = 0.f;
+                    GCUDA(cudaEventElapsedTime(&ms, t0, t1));
+                    if (rep > 0 && ms < best) best = ms;
+                }
+                te.ms[k][md] = best;
+            }
+            mode[k] = te.ms[k][LIST_PAIR] <= te.ms[k][LIST_SINGLE] ? LIST_PAIR : LIST_SINGLE;
+            te.mode[k] = mode[k];
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune.push_back(te);
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_last_tune = te;
+        for (int k = 0; k < 3; ++k) g_last_tune.mode[k] = mode[k];
+    }
+    GroupList use[3] = {lists[mode[0]][0], lists[mode[1]][1], lists[mode[2]][2]};
+    // ---- a chunk of first-phase steps, captured once, replayed until every system is done
+    const int chunk = 8;
+    const int64_t before = omm_kernel_launches();
+    GCUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    int crc = OMM_OK;
+    for (int c = 0; c < chunk && crc == OMM_OK; ++c)
+        crc = group_iteration(handles, count, use, mode, gs, ev_fork, ev_join.data());
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(gs, &graph);
+    if (crc != OMM_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        omm::set_error("grouped chunk capture failed: %s", cudaGetErrorString(ce));
+        cleanup();
+        return crc != OMM_OK ? crc : OMM_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        gexec = nullptr;
+        omm::set_error("grouped chunk graph instantiation failed: %s", cudaGetErrorString(ie));
+        cleanup();
+        return OMM_ERR_CUDA;
+    }
+    const int64_t per_chunk = omm_kernel_launches() - before;
+    omm::count_launch(-per_chunk);
+    for (;;) {
+        GCUDA(cudaGraphLaunch(gexec, gs));
+        omm::count_launch(per_chunk);
+        for (int32_t i = 0; i < count; ++i)
+            GCUDA(cudaMemcpyAsync(handles[i]->hstate, handles[i]->dstate, sizeof(omm::DevState),
+                                  cudaMemcpyDeviceToHost, gs));
+        GCUDA(cudaStreamSynchronize(gs));
+        bool all = true;
+        for (int32_t i = 0; i < count; ++i)
+            if (!handles[i]->hstate->done && !handles[i]->hstate->wait_timeout) all = false;
+        if (all) break;
+    }
+    // ---- phase 2 (refinement) per system on its own stream, as omm_batch_solve
+    GCUDA(cudaEventRecord(ev_fork, gs));
+    for (int32_t i = 0; i < count; ++i) {
+        GCUDA(cudaStreamWaitEvent(handles[i]->stream, ev_fork, 0));
+        GCUDA(cudaEventRecord(handles[i]->ev_poll, handles[i]->stream));
+    }
+    cleanup();
+#undef GTRY
+#undef GCUDA
+    return drive_batch(handles, count, E_out, iters_out, status_out);
+}
+
+int omm_batch_last_tuning(int32_t *modes, float *ms) {
+    if (modes == nullptr) return OMM_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (int k = 0; k < 3; ++k) {
+        modes[k] = g_last_tune.mode[k];
+        if (ms) {
+            ms[2 * k] = g_last_tune.ms[k][0];
+            ms[2 * k + 1] = g_last_tune.ms[k][1];
+        }
+    }
+    return OMM_OK;
 }
 
 int omm_get_diag(omm_handle *h, omm_diag *d) {

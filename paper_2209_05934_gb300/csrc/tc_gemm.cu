@@ -291,13 +291,11 @@ __global__ void __launch_bounds__(192, 1)
 // its tensor memory receives output rows 128r..128r+127 for all 256 columns.
 // Each SM thus pulls half of the B tile through its shared memory per MMA
 // instead of all of it.  Roles:
-//   warp 0 (both CTAs): TMA of the CTA's own A and B digit tiles, completing on
-//     the CTA's own full barrier;
-//   warp 1, CTA 1: relays each completed stage to CTA 0 (remote arrive on its
-//     peer-full barrier), so every copy completes on the barrier of the CTA it
-//     writes into;
-//   warp 1, CTA 0: waits for both halves of a stage, issues the pair MMAs and
-//     commits to the empty barriers of both CTAs (multicast), finally to both
+//   warp 0 (both CTAs): TMA of the CTA's own A and B digit tiles; every copy
+//     completes on CTA 0's full barrier of the stage, which CTA 0's producer
+//     arms with the bytes of both CTAs;
+//   warp 1, CTA 0: waits for the stage, issues the pair MMAs and commits to
+//     the empty barriers of both CTAs (multicast), finally to both
 //     accumulator barriers;
 //   warps 2..5 (both CTAs): the epilogue of the CTA's 128 rows.
 // All waits are bounded; the pair meets at cluster barriers only after every
@@ -318,8 +316,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[STAGES];    // this CTA's copies of a stage landed
-    __shared__ __align__(8) uint64_t pfull_bar[STAGES];   // (CTA 0) the peer's copies landed
+    __shared__ __align__(8) uint64_t full_bar[STAGES];    // (CTA 0) both CTAs' copies of a stage landed
     __shared__ __align__(8) uint64_t empty_bar[STAGES];   // the pair's MMAs of a stage completed
     __shared__ __align__(8) uint64_t acc_bar;
     __shared__ uint32_t tmem_base;
@@ -336,7 +333,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&pfull_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&acc_bar, 1);
@@ -348,7 +344,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     if (warp == 1) tmem_alloc_pair(&tmem_base, tmem_cols);
     tc_fence_before();
     __syncthreads();
-    cluster_sync_all();   // barriers of both CTAs initialised before any remote arrive
+    cluster_sync_all();   // barriers of both CTAs initialised before any copy signals them
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     int issued = 0;       // producer: k-blocks whose copies were issued
@@ -361,21 +357,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
             if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, args.err)) break;
-            mbar_arrive_expect_tx(&full_bar[s], (uint32_t)stage_bytes);
             uint8_t *st = smem + s * stage_bytes;
-            for (int p = 0; p < nA; ++p)
-                tma_load_3d(st + p * TILE_A, &mapA, kb * BKT, a_row, p, &full_bar[s]);
-            for (int q = 0; q < nB; ++q)
-                tma_load_3d(st + nA * TILE_A + q * TILE_B, &mapB, kb * BKT, b_row, q, &full_bar[s]);
+            if (rank == 0) {
+                mbar_arrive_expect_tx(&full_bar[s], (uint32_t)(2 * stage_bytes));
+                for (int p = 0; p < nA; ++p)
+                    tma_load_3d(st + p * TILE_A, &mapA, kb * BKT, a_row, p, &full_bar[s]);
+                for (int q = 0; q < nB; ++q)
+                    tma_load_3d(st + nA * TILE_A + q * TILE_B, &mapB, kb * BKT, b_row, q, &full_bar[s]);
+            } else {
+                const uint32_t fb = mapa_shared(smem_u32(&full_bar[s]), 0u);
+                for (int p = 0; p < nA; ++p)
+                    tma_load_3d_pair(st + p * TILE_A, &mapA, kb * BKT, a_row, p, fb);
+                for (int q = 0; q < nB; ++q)
+                    tma_load_3d_pair(st + nA * TILE_A + q * TILE_B, &mapB, kb * BKT, b_row, q, fb);
+            }
             issued = kb + 1;
-        }
-    } else if (warp == 1 && lane == 0 && rank == 1) {
-        // ---------------- relay (CTA 1): this CTA's stage landed -> CTA 0's peer-full barrier
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-            if (!mbar_wait(&full_bar[s], ph, deadline, &abort_flag, args.err)) break;
-            mbar_arrive_remote(mapa_shared(smem_u32(&pfull_bar[s]), 0u));
         }
     } else if (warp == 1 && lane == 0 && rank == 0) {
         // ---------------- pair MMA issuer (CTA 0)
@@ -384,8 +380,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-            if (!mbar_wait(&full_bar[s], ph, deadline, &abort_flag, args.err)) break;
-            if (!mbar_wait_cluster(&pfull_bar[s], ph, deadline, &abort_flag, args.err)) break;
+            if (!mbar_wait_cluster(&full_bar[s], ph, deadline, &abort_flag, args.err)) break;
             tc_fence_after();
             const uint32_t st = smem_u32(smem + s * stage_bytes);
             const int slot = (kb * kacc) / nkb;
@@ -416,22 +411,217 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         tc_epilogue<BN>(args, tmem, q, row, n0, z, nacc, have_acc);
     }
     if (warp == 0 && lane == 0 && abort_flag) {
-        // an aborted pipeline: let this CTA's issued copies land before it can exit
-        const uint64_t until = globaltimer_ns() + 200000000ull;
-        for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
-            const uint32_t addr = smem_u32(&full_bar[kb % STAGES]);
-            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-            while (!mbar_try_wait(addr, ph) && globaltimer_ns() < until) {
+        // an aborted pipeline: let the issued copies land before the CTA can exit.  CTA 0
+        // watches its full barriers (they count both CTAs' copies); CTA 1 cannot see
+        // its copies complete and waits out a fixed 1 ms, far beyond a copy's latency.
+        const uint64_t now = globaltimer_ns();
+        if (rank == 0) {
+            const uint64_t until = now + 200000000ull;
+            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
+                const uint32_t addr = smem_u32(&full_bar[kb % STAGES]);
+                const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+                while (!mbar_try_wait_cluster(addr, ph) && globaltimer_ns() < until) {
+                }
+            }
+        } else {
+            while (globaltimer_ns() < now + 1000000ull) {
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync_all();   // neither CTA leaves while the pair's MMAs or arrivals may touch it
+    cluster_sync_all();   // neither CTA leaves while the pair's MMAs or copies may touch it
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
         tmem_dealloc_pair(tmem, tmem_cols);
+    }
+}
+
+// ------------------------------------------------------------------ persistent tile-list GEMM
+// One launch over a list of 256-column output tiles drawn from many problems
+// (the grouped products of many systems, or one system's tiles in a persistent
+// schedule).  CTA c (pair c with PAIR) takes tiles c, c + G, c + 2G, ... of the
+// list; a tile whose problem's solve has finished (state->done, fixed during
+// the launch) is skipped by every role alike.  The shared-memory ring and its
+// barrier phases run on across tiles, so the producer fills the next tile's
+// first stages while the epilogue drains the last one.  The accumulator
+// occupies all 512 tensor-memory columns (two pair classes of 256), so the MMA
+// of a tile waits for the epilogue warps of the previous tile (tmem_empty,
+// arrived by the four epilogue warps of each CTA).
+template <bool PAIR, int STAGES, int BKT>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_list_kernel(const TileProblem *__restrict__ probs, const TileRef *__restrict__ tiles, int ntiles) {
+    constexpr int BN = 256;
+    constexpr int BNC = PAIR ? 128 : 256;          // B rows per CTA
+    constexpr int TILE_A = BM * BKT * 2;
+    constexpr int TILE_B = BNC * BKT * 2;
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const int group = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int ngroups = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int nA = probs[0].a.nA, nB = probs[0].a.nB;
+    const int stage_bytes = nA * TILE_A + nB * TILE_B;
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES];
+    __shared__ __align__(8) uint64_t empty_bar[STAGES];
+    __shared__ __align__(8) uint64_t acc_bar;
+    __shared__ __align__(8) uint64_t tmem_empty_bar;   // (CTA 0) epilogues drained the accumulator
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const uint64_t deadline = globaltimer_ns() + kWaitNs;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    int *err = probs[0].a.err;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&acc_bar, 1);
+        mbar_init(&tmem_empty_bar, PAIR ? 8 : 4);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    constexpr uint32_t tmem_cols = 512;
+    if (warp == 1) {
+        if (PAIR) tmem_alloc_pair(&tmem_base, tmem_cols);
+        else tmem_alloc(&tmem_base, tmem_cols);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (PAIR) cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    auto live = [&](const TcArgs &a) {
+        return a.state == nullptr || !*((volatile const int *)&a.state->done);
+    };
+    int issued = 0;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer: the ring runs on across tiles
+        uint32_t g = 0;   // k-blocks issued so far
+        bool ok = true;
+        for (int t = group; t < ntiles && ok; t += ngroups) {
+            const TileRef tr = tiles[t];
+            const TileProblem *P = probs + tr.p;
+            const TcArgs &a = P->a;
+            if (!live(a)) continue;
+            const int m0 = tr.mi * (PAIR ? 2 * BM : BM) + BM * (int)rank;
+            const int a_row = a.a_row0 + tr.z * a.a_row_step + m0;
+            const int b_row = a.b_row0 + tr.z * a.b_row_step + tr.ni * BN + BNC * (int)rank;
+            const int nkb = (a.K + BKT - 1) / BKT;
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int s = (int)(g % STAGES);
+                const uint32_t ph = (g / STAGES) & 1u;
+                if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, err)) { ok = false; break; }
+                uint8_t *st = smem + s * stage_bytes;
+                if (rank == 0) {
+                    mbar_arrive_expect_tx(&full_bar[s], (uint32_t)((PAIR ? 2 : 1) * stage_bytes));
+                    for (int p = 0; p < nA; ++p)
+                        tma_load_3d(st + p * TILE_A, &P->mapA, kb * BKT, a_row, p, &full_bar[s]);
+                    for (int q = 0; q < nB; ++q)
+                        tma_load_3d(st + nA * TILE_A + q * TILE_B, &P->mapB, kb * BKT, b_row, q, &full_bar[s]);
+                } else {
+                    const uint32_t fb = mapa_shared(smem_u32(&full_bar[s]), 0u);
+                    for (int p = 0; p < nA; ++p)
+                        tma_load_3d_pair(st + p * TILE_A, &P->mapA, kb * BKT, a_row, p, fb);
+                    for (int q = 0; q < nB; ++q)
+                        tma_load_3d_pair(st + nA * TILE_A + q * TILE_B, &P->mapB, kb * BKT, b_row, q, fb);
+                }
+                issued = (int)g + 1;
+            }
+        }
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+        // ---------------- MMA issuer (the single CTA, or CTA 0 of the pair)
+        constexpr uint32_t idesc = idesc_bf16(PAIR ? 2 * BM : BM, BN);
+        uint32_t g = 0, tile_it = 0;
+        bool ok = true;
+        for (int t = group; t < ntiles && ok; t += ngroups) {
+            const TcArgs &a = probs[tiles[t].p].a;
+            if (!live(a)) continue;
+            // the previous tile's epilogues must have read the accumulator out
+            if (!mbar_wait_cluster(&tmem_empty_bar, (tile_it & 1u) ^ 1u, deadline, &abort_flag, err)) break;
+            tc_fence_after();
+            const int nkb = (a.K + BKT - 1) / BKT;
+            const int ncls = a.ncls, npairs = a.npairs;
+            uint32_t written = 0;
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int s = (int)(g % STAGES);
+                const uint32_t ph = (g / STAGES) & 1u;
+                if (!mbar_wait_cluster(&full_bar[s], ph, deadline, &abort_flag, err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + s * stage_bytes);
+                for (int pr = 0; pr < npairs; ++pr) {
+                    const int cls = (ncls == 2 && (a.pa[pr] != 0 || a.pb[pr] != 0)) ? 1 : 0;
+                    const uint32_t tacc = tmem + (uint32_t)(cls * BN);
+                    const uint64_t da = sdesc_sw128(st + a.pa[pr] * TILE_A);
+                    const uint64_t db = sdesc_sw128(st + nA * TILE_A + a.pb[pr] * TILE_B);
+#pragma unroll
+                    for (int kk = 0; kk < BKT / 16; ++kk) {
+                        const uint32_t accum = ((written >> cls) & 1u) ? 1u : 0u;
+                        if (PAIR) umma_bf16_pair(tacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, accum);
+                        else umma_bf16(tacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, accum);
+                        written |= 1u << cls;
+                    }
+                }
+                if (PAIR) umma_commit_pair_mc(&empty_bar[s], (uint16_t)0x3);
+                else umma_commit(&empty_bar[s]);
+            }
+            if (PAIR) umma_commit_pair_mc(&acc_bar, (uint16_t)0x3);
+            else umma_commit(&acc_bar);
+            ++tile_it;
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue: one tile at a time
+        const int q = warp & 3;
+        uint32_t tile_it = 0;
+        const uint32_t te_local = smem_u32(&tmem_empty_bar);
+        const uint32_t te_leader = PAIR ? mapa_shared(te_local, 0u) : te_local;
+        for (int t = group; t < ntiles; t += ngroups) {
+            const TileRef tr = tiles[t];
+            const TcArgs &a = probs[tr.p].a;
+            if (!live(a)) continue;
+            const bool got = mbar_wait(&acc_bar, tile_it & 1u, deadline, &abort_flag, err);
+            if (!__all_sync(0xffffffffu, got)) break;
+            tc_fence_after();
+            const int m0 = tr.mi * (PAIR ? 2 * BM : BM) + BM * (int)rank;
+            const int row = m0 + 32 * q + lane;
+            tc_epilogue<BN>(a, tmem, q, row, tr.ni * BN, tr.z, a.ncls, true);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (PAIR) mbar_arrive_remote(te_leader);
+                else mbar_arrive(&tmem_empty_bar);
+            }
+            ++tile_it;
+        }
+    }
+    if (warp == 0 && lane == 0 && abort_flag) {
+        const uint64_t now = globaltimer_ns();
+        if (rank == 0) {
+            const uint64_t until = now + 200000000ull;
+            for (int g = issued - STAGES < 0 ? 0 : issued - STAGES; g < issued; ++g) {
+                const uint32_t addr = smem_u32(&full_bar[g % STAGES]);
+                const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+                while (!mbar_try_wait_cluster(addr, ph) && globaltimer_ns() < until) {
+                }
+            }
+        } else {
+            while (globaltimer_ns() < now + 1000000ull) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (PAIR) cluster_sync_all();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        if (PAIR) tmem_dealloc_pair(tmem, tmem_cols);
+        else tmem_dealloc(tmem, tmem_cols);
     }
 }
 
@@ -570,7 +760,67 @@ int launch_tc_pair(const CUtensorMap &ma, const CUtensorMap &mb_half, const TcAr
     return OMM_OK;
 }
 
+template <bool PAIR>
+int launch_list(const TileProblem *probs, const TileRef *tiles, int ntiles, int ctas, int nA, int nB,
+                cudaStream_t st) {
+    constexpr int BKT = 64;
+    const int stage = nA * BM * BKT * 2 + nB * (PAIR ? 128 : 256) * BKT * 2;
+    // as many stages as fit in 220 KB (three 64 KB pair stages; two 96 KB single stages)
+    const int stages = (220 * 1024) / stage >= 3 ? 3 : 2;
+    const int smem = stages * stage + 1024;
+    auto kern = stages == 3 ? tc_gemm_list_kernel<PAIR, 3, BKT> : tc_gemm_list_kernel<PAIR, 2, BKT>;
+    static int attr3 = 0, attr2 = 0;
+    int &attr = stages == 3 ? attr3 : attr2;
+    if (smem > attr) {
+        OMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = smem;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctas, 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr_c[1];
+    attr_c[0].id = cudaLaunchAttributeClusterDimension;
+    attr_c[0].val.clusterDim.x = PAIR ? 2 : 1;
+    attr_c[0].val.clusterDim.y = 1;
+    attr_c[0].val.clusterDim.z = 1;
+    cfg.attrs = attr_c;
+    cfg.numAttrs = 1;
+    OMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, probs, tiles, ntiles));
+    count_launch();
+    return OMM_OK;
+}
+
 }  // namespace
+
+void list_prepare(TcArgs &a) {
+    bool has_main = false, has_small = false;
+    for (int p = 0; p < a.npairs; ++p) {
+        if (a.pa[p] == 0 && a.pb[p] == 0) has_main = true; else has_small = true;
+    }
+    a.ncls = (has_main && has_small) ? 2 : 1;
+    a.kacc = 1;
+}
+
+void list_tiles(int p, const TcArgs &a, int nbatch, int mode, std::vector<TileRef> &out) {
+    const int tm = (int)ceil_div(a.M, mode == LIST_PAIR ? 2 * BM : BM);
+    const int tn = (int)ceil_div(a.N, 256);
+    for (int z = 0; z < nbatch; ++z)
+        for (int mi = 0; mi < tm; ++mi)
+            for (int ni = 0; ni < tn; ++ni) out.push_back(TileRef{p, z, mi, ni});
+}
+
+int gemm_list(const TileProblem *probs, const TileRef *tiles, int ntiles, int mode, int ctas, int nA, int nB,
+              cudaStream_t st) {
+    if (ntiles <= 0) return OMM_OK;
+    if (nA < 1 || nB < 1 || nA + nB > 4 || ctas < 1) return OMM_ERR_ARG;
+    if (mode == LIST_PAIR) {
+        if (ctas & 1) return OMM_ERR_ARG;
+        return launch_list<true>(probs, tiles, ntiles, ctas, nA, nB, st);
+    }
+    return launch_list<false>(probs, tiles, ntiles, ctas, nA, nB, st);
+}
 
 int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
                    int64_t plane_elems, int nplanes, int box_rows, int bk) {

@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "omm_internal.cuh"
 
 namespace omm {
@@ -35,6 +37,30 @@ struct TcArgs {
     int ncls;                    // set by the launcher: 2 = leading digit pair kept apart
     int bk;                      // K-block width of the tensor maps: 64 (128-byte swizzle) or 32
 };
+
+// One problem of a grouped (tile-list) launch: its tensor maps (device copies)
+// and arguments.  Every problem of one launch has the same digit planes and
+// 64-wide K blocks; K > 0.
+struct alignas(64) TileProblem {
+    CUtensorMap mapA;        // A planes, 128-row box
+    CUtensorMap mapB;        // B planes, 256-row box (one CTA per tile) or 128-row box (CTA pairs)
+    TcArgs a;                // kacc, ncls filled by list_prepare
+};
+// One output tile: problem p, batch z, row tile mi, column tile ni (256 columns;
+// 128 rows per tile with one CTA, 256 with a CTA pair).
+struct TileRef {
+    int32_t p, z, mi, ni;
+};
+enum { LIST_SINGLE = 0, LIST_PAIR = 1 };
+
+// Fill kacc / ncls of a problem for the tile-list kernels (one K range per class).
+void list_prepare(TcArgs &a);
+// Tiles of problem p in (z, mi, ni) order for the given mode.
+void list_tiles(int p, const TcArgs &a, int nbatch, int mode, std::vector<TileRef> &out);
+// One persistent launch over a tile list: `ctas` CTAs (a multiple of 2 with
+// LIST_PAIR), each taking tiles ctas-apart (pairs: cluster-apart) in list order.
+int gemm_list(const TileProblem *probs, const TileRef *tiles, int ntiles, int mode, int ctas, int nA, int nB,
+              cudaStream_t st);
 
 int make_digit_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t K, int64_t rows, int64_t ld,
                    int64_t plane_elems, int nplanes, int box_rows, int bk = 64);

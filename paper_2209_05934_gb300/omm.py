@@ -32,7 +32,8 @@ class Options(C.Structure):
                 ("filter_eps", C.c_double), ("stream", C.c_void_p), ("refine", C.c_int32),
                 ("exact_digits", C.c_int32), ("split_digits", C.c_int32), ("graphs", C.c_int32),
                 ("n_occupied", C.c_int32), ("precon", C.c_int32), ("tau_T", C.c_double),
-                ("screen_eps", C.c_double), ("gemm_pair", C.c_int32)]
+                ("screen_eps", C.c_double), ("gemm_pair", C.c_int32),
+                ("gemm_persistent", C.c_int32)]
 
 
 class Pattern(C.Structure):
@@ -93,6 +94,9 @@ _SIGS = {
     "omm_solve_end": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "omm_batch_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
+    "omm_batch_solve_grouped": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_double, C.c_int32,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]),
+    "omm_batch_last_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "omm_op_exact_gemm_workspace_bytes": (C.c_int64, [C.c_int64, C.c_int64, C.c_int64, C.c_int32]),
     "omm_op_exact_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                     C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
@@ -400,6 +404,42 @@ class SparseSolver:
         check(lib().omm_get_pattern(self._h, which, C.c_void_p(rp.ctypes.data), C.c_void_p(col.ctypes.data)),
               "omm_get_pattern")
         return rp, col[:nnz]
+
+
+def _batch_args(solvers, W0s):
+    k = len(solvers)
+    hs = (C.c_void_p * k)(*[s._h.value for s in solvers])
+    if W0s is None:
+        return hs, None, 0
+    ptrs = [_ptr(a) for a in W0s]
+    on = {d for p, d in ptrs if p is not None}
+    if len(on) > 1:
+        raise ValueError("W0s must be all host or all device arrays")
+    on_dev = on.pop() if on else 0
+    return hs, (C.c_void_p * k)(*[p.value if p is not None else None for p, _ in ptrs]), on_dev
+
+
+def batch_solve_grouped(solvers, W0s=None, tol: float = 1e-10, tile_mode: int = -1):
+    """Minimise several dense mixed handles as one group (omm_batch_solve_grouped):
+    grouped persistent tensor-core launches per CG step, autotuned tile mode
+    (tile_mode -1), or 0 single CTA / 1 CTA pairs.  Returns (E, iters, status, rc)."""
+    k = len(solvers)
+    hs, w, on_dev = _batch_args(solvers, W0s)
+    E = np.zeros(k)
+    it = np.zeros(k, dtype=np.int32)
+    st = np.zeros(k, dtype=np.int32)
+    rc = lib().omm_batch_solve_grouped(hs, k, w, on_dev, float(tol), int(tile_mode), C.c_void_p(E.ctypes.data),
+                                       C.c_void_p(it.ctypes.data), C.c_void_p(st.ctypes.data))
+    return E, it, st, rc
+
+
+def batch_last_tuning():
+    """(modes[3], ms[3][2]) of the last grouped batch: products, contractions, gradient."""
+    modes = np.zeros(3, dtype=np.int32)
+    ms = np.zeros(6, dtype=np.float32)
+    check(lib().omm_batch_last_tuning(C.c_void_p(modes.ctypes.data), C.c_void_p(ms.ctypes.data)),
+          "omm_batch_last_tuning")
+    return modes, ms.reshape(3, 2)
 
 
 def batch_solve(solvers, W0s=None, tol: float = 1e-10):
