@@ -433,6 +433,9 @@ struct SplitCall {
     omm::tc::TcArgs a;
     const CUtensorMap *mA = nullptr, *mB = nullptr, *mBh = nullptr;   // B with 256-row / 128-row boxes
     int nbatch = 1;
+    // the B planes, for a map with another box (tile lists of narrow problems)
+    const __nv_bfloat16 *b_base = nullptr;
+    int64_t b_K = 0, b_rows = 0, b_ld = 0, b_plane = 0;
 };
 
 // [H'; S] times the digits of W (rows b_row0 = 0) or D (b_row0 = n) of WDd:
@@ -461,6 +464,11 @@ SplitCall products_call(omm_handle *h, int b_row0, double *C, float *C32, int64_
     c.mB = &x.mapWD_B;
     c.mBh = &x.mapWD_A;
     c.nbatch = s_identity(h) ? 1 : 2;
+    c.b_base = x.WDd;
+    c.b_K = m;
+    c.b_rows = 2 * n;
+    c.b_ld = x.ldm;
+    c.b_plane = 2 * n * x.ldm;
     return c;
 }
 
@@ -475,6 +483,11 @@ SplitCall contract_call(omm_handle *h) {
     c.mA = &x.mapWD_A;
     c.mB = &x.mapHDSD_B;
     c.mBh = &x.mapHDSD_H;
+    c.b_base = x.HDSDd;
+    c.b_K = m;
+    c.b_rows = 2 * n;
+    c.b_ld = x.ldm;
+    c.b_plane = 2 * n * x.ldm;
     return c;
 }
 
@@ -493,6 +506,11 @@ SplitCall gradient_call(omm_handle *h) {
     c.mA = &x.mapSWHW_A;
     c.mB = &x.mapHSW_B;
     c.mBh = &x.mapHSW_H;
+    c.b_base = x.HSWd;
+    c.b_K = 2 * n;
+    c.b_rows = n;
+    c.b_ld = x.ld2n;
+    c.b_plane = n * x.ld2n;
     return c;
 }
 
@@ -507,14 +525,21 @@ int list_ctas(int mode, int64_t ntiles) {
     return (int)c;
 }
 
-omm::tc::TileProblem tile_problem(const SplitCall &c, int mode) {
-    omm::tc::TileProblem p;
+int tile_problem(const SplitCall &c, int mode, omm::tc::TileProblem &p) {
     memset(&p, 0, sizeof(p));
     p.mapA = *c.mA;
-    p.mapB = mode == omm::tc::LIST_PAIR ? *c.mBh : *c.mB;
     p.a = c.a;
     omm::tc::list_prepare(p.a);
-    return p;
+    p.bn = omm::tc::list_tile_width(c.a.N, mode);
+    const int box = mode == omm::tc::LIST_PAIR ? p.bn / 2 : p.bn;
+    if (box == 256 && mode != omm::tc::LIST_PAIR) {
+        p.mapB = *c.mB;
+    } else if (box == 128 && mode == omm::tc::LIST_PAIR) {
+        p.mapB = *c.mBh;
+    } else {
+        TRY(omm::tc::make_digit_map(&p.mapB, c.b_base, c.b_K, c.b_rows, c.b_ld, c.b_plane, kDig, box, c.a.bk));
+    }
+    return OMM_OK;
 }
 
 int run_split(omm_handle *h, const SplitCall &c, int slot) {
@@ -523,9 +548,10 @@ int run_split(omm_handle *h, const SplitCall &c, int slot) {
     HandleList &L = h->lists[slot];
     const int mode = list_mode(h);
     if (L.probs == nullptr) {
-        const omm::tc::TileProblem p = tile_problem(c, mode);
+        omm::tc::TileProblem p;
+        TRY(tile_problem(c, mode, p));
         std::vector<omm::tc::TileRef> tiles;
-        omm::tc::list_tiles(0, p.a, c.nbatch, mode, tiles);
+        omm::tc::list_tiles(0, p.a, c.nbatch, mode, p.bn, tiles);
         OMM_CUDA_TRY(cudaMalloc((void **)&L.probs, sizeof(p)));
         OMM_CUDA_TRY(cudaMalloc((void **)&L.tiles, tiles.size() * sizeof(omm::tc::TileRef)));
         OMM_CUDA_TRY(cudaMemcpy(L.probs, &p, sizeof(p), cudaMemcpyHostToDevice));
@@ -1593,13 +1619,16 @@ int build_group_list(omm_handle **hs, int count, int stage, int mode, GroupList 
     std::vector<int> nb((size_t)count);
     for (int i = 0; i < count; ++i) {
         const SplitCall c = stage_call(hs[i], stage);
-        probs[i] = tile_problem(c, mode);
+        TRY(tile_problem(c, mode, probs[i]));
         nb[i] = c.nbatch;
         order[i] = i;
     }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return probs[a].a.K > probs[b].a.K; });
+    // longest tiles first: K loop times tile width
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (int64_t)probs[a].a.K * probs[a].bn > (int64_t)probs[b].a.K * probs[b].bn;
+    });
     std::vector<omm::tc::TileRef> tiles;
-    for (int i : order) omm::tc::list_tiles(i, probs[i].a, nb[i], mode, tiles);
+    for (int i : order) omm::tc::list_tiles(i, probs[i].a, nb[i], mode, probs[i].bn, tiles);
     OMM_CUDA_TRY(cudaMalloc((void **)&L.probs, probs.size() * sizeof(omm::tc::TileProblem)));
     OMM_CUDA_TRY(cudaMalloc((void **)&L.tiles, tiles.size() * sizeof(omm::tc::TileRef)));
     OMM_CUDA_TRY(cudaMemcpy(L.probs, probs.data(), probs.size() * sizeof(omm::tc::TileProblem), cudaMemcpyHostToDevice));

@@ -531,7 +531,8 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
                                                        double *X, double *Y, double *h2, double *s2,
                                                        const double *__restrict__ nW, const double *__restrict__ nD,
                                                        const double *__restrict__ nHD, const double *__restrict__ nSD,
-                                                       double eps2, const DevState *state) {
+                                                       double eps2, const int32_t *__restrict__ Ntr,
+                                                       const DevState *state) {
     if (done(state)) return;
     const int lane = threadIdx.x & 31;
     static_assert(BN == 2, "contraction lanes assume 2 orbitals per W block");
@@ -542,8 +543,31 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
     double *out = mat == 0 ? X : mat == 1 ? Y : mat == 2 ? h2 : s2;
     const double *nL = SCREEN ? ((mat < 2) ? nW : nD) : nullptr;
     const double *nR = SCREEN ? ((mat == 0 || mat == 2) ? nHD : nSD) : nullptr;
+    // lower-triangle blocks with `Ntr` given: D^T H'D and D^T S D are symmetric, so
+    // only X and Y are formed there (their transposes' blocks give h2, s2), each
+    // output by four lanes splitting the basis index k
+    const int v4 = lane >> 2, quarter = lane & 3;
+    const int mat4 = v4 >> 2, a4 = (v4 >> 1) & 1, b4 = v4 & 1;   // mat4: 0 X, 1 Y
+    const double *R4 = mat4 == 0 ? HD : SD;
+    double *out4 = mat4 == 0 ? X : Y;
     const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
     for (int64_t q = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; q < nnzN; q += nwarps) {
+        if (!SCREEN && Ntr != nullptr && Ntr[q] < q) {
+            double acc = 0.0;
+            for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
+                const double *l = W + (int64_t)Ca[t] * BM * BN + a4;
+                const double *rr = R4 + (int64_t)Cb[t] * BM * BN + b4;
+#pragma unroll
+                for (int kk = 0; kk < BM / 4; ++kk) {
+                    const int k = quarter * (BM / 4) + kk;
+                    acc = fma(l[k * BN], rr[k * BN], acc);
+                }
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (quarter == 0) out4[q * 4 + a4 * 2 + b4] = acc;
+            continue;
+        }
         double acc = 0.0;
         for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
             if (SCREEN && nL[Ca[t]] * nR[Cb[t]] < eps2) continue;
@@ -557,6 +581,21 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         if (half == 0) out[q * 4 + a * 2 + b] = acc;
+    }
+}
+
+// h2, s2 on the lower-triangle blocks of P_N from their transposes' blocks
+__global__ void mirror_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr, double *h2, double *s2,
+                              const DevState *state) {
+    if (done(state)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnzN * 4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = i >> 2;
+        const int64_t tq = Ntr[q];
+        if (tq >= q) continue;
+        const int e = (int)(i & 3), a = e >> 1, b = e & 1;
+        h2[i] = h2[tq * 4 + b * 2 + a];
+        s2[i] = s2[tq * 4 + b * 2 + a];
     }
 }
 
@@ -1040,13 +1079,22 @@ int contract(Dev &d, const double *Wl, const double *Dl, const double *HDr, cons
     if (nWl != nullptr && d.screening()) {
         DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, true><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
                                          d.nnzN, d.Crp, d.Ca, d.Cb, Wl, Dl, HDr, SDr, Xo, Yo, h2o, s2o, nWl, nDl,
-                                         nHDr, nSDr, d.screen_eps2, state)));
-    } else {
-        DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, false><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
-                                         d.nnzN, d.Crp, d.Ca, d.Cb, Wl, Dl, HDr, SDr, Xo, Yo, h2o, s2o, nullptr,
-                                         nullptr, nullptr, nullptr, 0.0, state)));
+                                         nHDr, nSDr, d.screen_eps2, nullptr, state)));
+        LAUNCHED();
+        return OMM_OK;
     }
+    // without screening D^T H'D and D^T S D are formed on the upper triangle of P_N
+    // and mirrored to the lower one (H' and S are symmetric); with D = W (the start,
+    // the density matrices) every block of every output is formed
+    const bool sym = Dl != Wl;
+    DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, false><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
+                                     d.nnzN, d.Crp, d.Ca, d.Cb, Wl, Dl, HDr, SDr, Xo, Yo, h2o, s2o, nullptr,
+                                     nullptr, nullptr, nullptr, 0.0, sym ? d.Ntr : nullptr, state)));
     LAUNCHED();
+    if (sym) {
+        mirror_kernel<<<blocks_for(d.nnzN * 4, 256), 256, 0, st>>>(d.nnzN, d.Ntr, h2o, s2o, state);
+        LAUNCHED();
+    }
     return OMM_OK;
 }
 

@@ -66,7 +66,7 @@ __device__ __forceinline__ void split3_i(double v, __nv_bfloat16 &d1, __nv_bfloa
 // (K ranges x pair classes) are summed; have_acc false writes beta Cin only.
 template <int BN>
 __device__ __forceinline__ void tc_epilogue(const TcArgs &args, uint32_t tmem, int q, int row, int n0, int z,
-                                            int nacc, bool have_acc) {
+                                            int nacc, bool have_acc, int bn = BN) {
     double *C = args.C != nullptr ? args.C + (int64_t)z * args.c_step : nullptr;
     const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
     __nv_bfloat16 *Dd = args.Dout ? args.Dout + (int64_t)z * args.dout_step : nullptr;
@@ -88,8 +88,8 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs &args, uint32_t tmem, i
         };
         double cin[16], cin_next[16];
         load_cin(0, cin);
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            if (c0 + 16 < BN) load_cin(c0 + 16, cin_next);
+        for (int c0 = 0; c0 < bn; c0 += 16) {
+            if (c0 + 16 < bn) load_cin(c0 + 16, cin_next);
             float v[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = 0.f;
@@ -135,8 +135,8 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs &args, uint32_t tmem, i
         };
         double cin[16], cin_next[16];
         load_cin(0, cin);
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            if (c0 + 16 < BN) load_cin(c0 + 16, cin_next);
+        for (int c0 = 0; c0 < bn; c0 += 16) {
+            if (c0 + 16 < bn) load_cin(c0 + 16, cin_next);
             double v[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = 0.0;
@@ -452,8 +452,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 template <bool PAIR, int STAGES, int BKT>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_list_kernel(const TileProblem *__restrict__ probs, const TileRef *__restrict__ tiles, int ntiles) {
-    constexpr int BN = 256;
-    constexpr int BNC = PAIR ? 128 : 256;          // B rows per CTA
+    constexpr int BN = 256;                        // accumulator columns per pair class
+    constexpr int BNC = PAIR ? 128 : 256;          // most B rows per CTA (a problem's tiles may be narrower)
     constexpr int TILE_A = BM * BKT * 2;
     constexpr int TILE_B = BNC * BKT * 2;
     const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
@@ -507,11 +507,15 @@ __global__ void __launch_bounds__(192, 1)
         for (int t = group; t < ntiles && ok; t += ngroups) {
             const TileRef tr = tiles[t];
             const TileProblem *P = probs + tr.p;
-            const TcArgs &a = P->a;
+            const TcArgs a = P->a;   // a register copy: the stores of other roles cannot alias it
             if (!live(a)) continue;
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P->mapA)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P->mapB)) : "memory");
+            const int bn = P->bn, bnc = PAIR ? bn / 2 : bn;   // this problem's tile width, B rows per CTA
+            const uint32_t tile_bytes = (uint32_t)(nA * TILE_A + nB * bnc * BKT * 2);
             const int m0 = tr.mi * (PAIR ? 2 * BM : BM) + BM * (int)rank;
             const int a_row = a.a_row0 + tr.z * a.a_row_step + m0;
-            const int b_row = a.b_row0 + tr.z * a.b_row_step + tr.ni * BN + BNC * (int)rank;
+            const int b_row = a.b_row0 + tr.z * a.b_row_step + tr.ni * bn + bnc * (int)rank;
             const int nkb = (a.K + BKT - 1) / BKT;
             for (int kb = 0; kb < nkb; ++kb, ++g) {
                 const int s = (int)(g % STAGES);
@@ -519,7 +523,7 @@ __global__ void __launch_bounds__(192, 1)
                 if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, err)) { ok = false; break; }
                 uint8_t *st = smem + s * stage_bytes;
                 if (rank == 0) {
-                    mbar_arrive_expect_tx(&full_bar[s], (uint32_t)((PAIR ? 2 : 1) * stage_bytes));
+                    mbar_arrive_expect_tx(&full_bar[s], (PAIR ? 2u : 1u) * tile_bytes);
                     for (int p = 0; p < nA; ++p)
                         tma_load_3d(st + p * TILE_A, &P->mapA, kb * BKT, a_row, p, &full_bar[s]);
                     for (int q = 0; q < nB; ++q)
@@ -536,12 +540,12 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else if (warp == 1 && lane == 0 && rank == 0) {
         // ---------------- MMA issuer (the single CTA, or CTA 0 of the pair)
-        constexpr uint32_t idesc = idesc_bf16(PAIR ? 2 * BM : BM, BN);
         uint32_t g = 0, tile_it = 0;
         bool ok = true;
         for (int t = group; t < ntiles && ok; t += ngroups) {
-            const TcArgs &a = probs[tiles[t].p].a;
+            const TcArgs a = probs[tiles[t].p].a;
             if (!live(a)) continue;
+            const uint32_t idesc = idesc_bf16(PAIR ? 2 * BM : BM, probs[tiles[t].p].bn);
             // the previous tile's epilogues must have read the accumulator out
             if (!mbar_wait_cluster(&tmem_empty_bar, (tile_it & 1u) ^ 1u, deadline, &abort_flag, err)) break;
             tc_fence_after();
@@ -554,7 +558,9 @@ __global__ void __launch_bounds__(192, 1)
                 if (!mbar_wait_cluster(&full_bar[s], ph, deadline, &abort_flag, err)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + s * stage_bytes);
-                for (int pr = 0; pr < npairs; ++pr) {
+#pragma unroll
+                for (int pr = 0; pr < 9; ++pr) {   // unrolled: the pair table stays in registers
+                    if (pr >= npairs) break;
                     const int cls = (ncls == 2 && (a.pa[pr] != 0 || a.pb[pr] != 0)) ? 1 : 0;
                     const uint32_t tacc = tmem + (uint32_t)(cls * BN);
                     const uint64_t da = sdesc_sw128(st + a.pa[pr] * TILE_A);
@@ -582,14 +588,15 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t te_leader = PAIR ? mapa_shared(te_local, 0u) : te_local;
         for (int t = group; t < ntiles; t += ngroups) {
             const TileRef tr = tiles[t];
-            const TcArgs &a = probs[tr.p].a;
+            const TcArgs a = probs[tr.p].a;
             if (!live(a)) continue;
+            const int bn = probs[tr.p].bn;
             const bool got = mbar_wait(&acc_bar, tile_it & 1u, deadline, &abort_flag, err);
             if (!__all_sync(0xffffffffu, got)) break;
             tc_fence_after();
             const int m0 = tr.mi * (PAIR ? 2 * BM : BM) + BM * (int)rank;
             const int row = m0 + 32 * q + lane;
-            tc_epilogue<BN>(a, tmem, q, row, tr.ni * BN, tr.z, a.ncls, true);
+            tc_epilogue<BN>(a, tmem, q, row, tr.ni * bn, tr.z, a.ncls, true, bn);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
@@ -803,9 +810,15 @@ void list_prepare(TcArgs &a) {
     a.kacc = 1;
 }
 
-void list_tiles(int p, const TcArgs &a, int nbatch, int mode, std::vector<TileRef> &out) {
+int list_tile_width(int N, int mode) {
+    const int q = mode == LIST_PAIR ? 32 : 16;   // the pair's half tile stays a multiple of 16 rows
+    const int w = (int)ceil_div(N, q) * q;
+    return w < 256 ? w : 256;
+}
+
+void list_tiles(int p, const TcArgs &a, int nbatch, int mode, int bn, std::vector<TileRef> &out) {
     const int tm = (int)ceil_div(a.M, mode == LIST_PAIR ? 2 * BM : BM);
-    const int tn = (int)ceil_div(a.N, 256);
+    const int tn = (int)ceil_div(a.N, bn);
     for (int z = 0; z < nbatch; ++z)
         for (int mi = 0; mi < tm; ++mi)
             for (int ni = 0; ni < tn; ++ni) out.push_back(TileRef{p, z, mi, ni});

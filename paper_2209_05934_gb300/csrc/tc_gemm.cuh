@@ -43,8 +43,9 @@ struct TcArgs {
 // 64-wide K blocks; K > 0.
 struct alignas(64) TileProblem {
     CUtensorMap mapA;        // A planes, 128-row box
-    CUtensorMap mapB;        // B planes, 256-row box (one CTA per tile) or 128-row box (CTA pairs)
+    CUtensorMap mapB;        // B planes, box of bn rows (one CTA per tile) or bn/2 rows (CTA pairs)
     TcArgs a;                // kacc, ncls filled by list_prepare
+    int bn;                  // output tile width: list_tile_width(N, mode)
 };
 // One output tile: problem p, batch z, row tile mi, column tile ni (256 columns;
 // 128 rows per tile with one CTA, 256 with a CTA pair).
@@ -55,8 +56,13 @@ enum { LIST_SINGLE = 0, LIST_PAIR = 1 };
 
 // Fill kacc / ncls of a problem for the tile-list kernels (one K range per class).
 void list_prepare(TcArgs &a);
-// Tiles of problem p in (z, mi, ni) order for the given mode.
-void list_tiles(int p, const TcArgs &a, int nbatch, int mode, std::vector<TileRef> &out);
+// Output tile width of a problem with N columns: N rounded up to 16 (32 for CTA
+// pairs), at most 256.  The MMA's N is the tile width, so a narrow problem does
+// no tensor work on columns it does not have; the width changes no result (every
+// output element accumulates over K in the same order).
+int list_tile_width(int N, int mode);
+// Tiles of problem p in (z, mi, ni) order for the given mode and tile width.
+void list_tiles(int p, const TcArgs &a, int nbatch, int mode, int bn, std::vector<TileRef> &out);
 // One persistent launch over a tile list: `ctas` CTAs (a multiple of 2 with
 // LIST_PAIR), each taking tiles ctas-apart (pairs: cluster-apart) in list order.
 int gemm_list(const TileProblem *probs, const TileRef *tiles, int ntiles, int mode, int ctas, int nA, int nB,
