@@ -326,10 +326,10 @@ __device__ __forceinline__ void put_digits(double v, int e, int s, __nv_bfloat16
     }
     for (int t = s - 1; t >= 1; --t) {
         const int64_t r = ((F + 64) & 127) - 64;      // in [-64, 63]
-        dst[t * plane + o] = __float2bfloat16_rn((float)r);
+        dst[t * plane + o] = __float2bfloat16_rn((float)(int)r);   // small integers: exact, 32-bit convert
         F = (F - r) >> 7;
     }
-    dst[o] = __float2bfloat16_rn((float)F);           // |F| <= 64
+    dst[o] = __float2bfloat16_rn((float)(int)F);      // |F| <= 64
 }
 
 // K along the source's rows: operand row r is source column r (warp per column).
@@ -355,33 +355,30 @@ __global__ void exp_cm_kernel(int64_t K, int64_t R, const double *__restrict__ X
     }
 }
 
-// K along the source's columns: operand row r is source row r.  A block covers
-// 32 rows: lane x reads row tr + x (coalesced), the 8 warps split the columns,
-// then the 8 partial maxima of each row are combined in shared memory.
-__global__ void exp_t_kernel(int64_t R, int64_t K, const double *__restrict__ X, int64_t ld, int *e,
-                             const DevState *state) {
+// Row exponents when K runs along the source's columns, split over K: each warp
+// takes 32 rows (one per lane, coalesced) and a slice of the columns, and folds
+// the biased exponent of its largest magnitude into be[r] with an integer
+// atomic max (be zeroed first); exp_finish_kernel turns be into exponents.
+__global__ void exp_t_split_kernel(int64_t R, int64_t K, const double *__restrict__ X, int64_t ld, int *be,
+                                   int64_t kslice, const DevState *state) {
     if (state != nullptr && *((volatile const int *)&state->done)) return;
-    __shared__ unsigned long long part[8][32];
     const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 32 + lx;
+    const int64_t k0 = (int64_t)blockIdx.y * kslice, k1 = k0 + kslice < K ? k0 + kslice : K;
     const uint64_t *Xb = (const uint64_t *)X;
-    for (int64_t tr = (int64_t)blockIdx.x * 32; tr < R; tr += (int64_t)gridDim.x * 32) {
-        const int64_t r = tr + lx;
-        unsigned long long mx = 0;
-        if (r < R)
-            for (int64_t k = ly; k < K; k += 8) {
-                const unsigned long long a = Xb[r + k * ld] & 0x7FFFFFFFFFFFFFFFull;
-                mx = a > mx ? a : mx;
-            }
-        part[ly][lx] = mx;
-        __syncthreads();
-        if (ly == 0 && r < R) {
-            unsigned long long m2 = part[0][lx];
-#pragma unroll
-            for (int w = 1; w < 8; ++w) m2 = part[w][lx] > m2 ? part[w][lx] : m2;
-            e[r] = exponent_from_maxbits(m2);
+    unsigned long long mx = 0;
+    if (r < R)
+        for (int64_t k = k0 + ly; k < k1; k += 8) {
+            const unsigned long long a = Xb[r + k * ld] & 0x7FFFFFFFFFFFFFFFull;
+            mx = a > mx ? a : mx;
         }
-        __syncthreads();
-    }
+    if (r < R && mx != 0) atomicMax(&be[r], (int)(mx >> 52));
+}
+
+__global__ void exp_finish_kernel(int64_t R, int *e, const DevState *state) {
+    if (state != nullptr && *((volatile const int *)&state->done)) return;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x)
+        e[r] = exponent_from_maxbits((uint64_t)e[r] << 52);
 }
 
 __global__ void digits_cm_kernel(int64_t K, int64_t R, const double *__restrict__ X, int64_t ld,
@@ -447,7 +444,14 @@ int exact_pack(bool k_along_rows, int64_t rows, int64_t cols, const double *X, i
         count_launch();
         OMM_CUDA_TRY(cudaGetLastError());
     } else {              // K = cols, operand rows = rows
-        exp_t_kernel<<<grid_for(rows * 8, 256), 256, 0, st>>>(rows, cols, X, ld, e, state);
+        // biased exponents by an atomic max over K slices of 256 columns, then exponents
+        OMM_CUDA_TRY(cudaMemsetAsync(e, 0, (size_t)rows * sizeof(int), st));
+        const int64_t kslice = 256;
+        dim3 eg((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, kslice));
+        exp_t_split_kernel<<<eg, 256, 0, st>>>(rows, cols, X, ld, e, kslice, state);
+        count_launch();
+        OMM_CUDA_TRY(cudaGetLastError());
+        exp_finish_kernel<<<grid_for(rows, 256), 256, 0, st>>>(rows, e, state);
         count_launch();
         OMM_CUDA_TRY(cudaGetLastError());
         dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32));

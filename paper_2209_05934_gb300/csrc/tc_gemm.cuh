@@ -41,7 +41,7 @@ struct TcArgs {
 // One problem of a grouped (tile-list) launch: its tensor maps (device copies)
 // and arguments.  Every problem of one launch has the same digit planes and
 // 64-wide K blocks; K > 0.
-struct alignas(64) TileProblem {
+struct TileProblem {   // CUtensorMap keeps the maps 64-byte aligned in arrays
     CUtensorMap mapA;        // A planes, 128-row box
     CUtensorMap mapB;        // B planes, box of bn rows (one CTA per tile) or bn/2 rows (CTA pairs)
     TcArgs a;                // kacc, ncls filled by list_prepare
