@@ -435,6 +435,33 @@ def run_omm(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if args.extras:
+        # short runs of the other workloads, so that the default line carries them too
+        import copy
+        solver.close()
+        torch.cuda.synchronize()
+        ex = {}
+        a3 = copy.copy(args)
+        a3.steps, a3.max_iter, a3.screen_eps = 1, 20, 0.0
+        r3 = run_c3(a3, quiet=True)
+        ex["c3_20_steps"] = {"workload": r3["config"]["workload"], "ms_per_iteration": r3["ms_per_iteration"],
+                             "stages_ms": r3["stages_ms_per_solve"], "roofline_fp64": r3["roofline"],
+                             "fp64_peak_tflops": r3["fp64_peak_tflops"], "nnzb": r3["config"]["nnzb"],
+                             "note": "20 CG steps from W0 (the converged solve is bench.py --config c3)"}
+        a4 = copy.copy(args)
+        a4.steps, a4.warmup, a4.tile_mode = 1, 1, -1
+        r4 = run_c4(a4, quiet=True)
+        ex["c4"] = {k: r4[k] for k in ("value", "unit", "ms_per_step", "tuning", "streams", "one_by_one",
+                                       "results_equal_alone", "all_ok", "iters")}
+        ex["c4"]["workload"] = r4["config"]["workload"]
+        a5 = copy.copy(args)
+        a5.sequences, a5.rates, a5.fp64_sequences = 12, [50.0], 0
+        r5 = run_c5(a5, quiet=True)
+        ex["c5_short"] = {"workload": r5["config"]["workload"], "rate": r5["rates"][0],
+                          "note": "12 sequences at one rate (the full sweep is bench.py --config c5)"}
+        line["other_workloads"] = ex
+        print(json.dumps(line), flush=True)
+        return
     print(json.dumps(line), flush=True)
     solver.close()
 
@@ -516,7 +543,7 @@ def run_profile_c3(args):
     s.close()
 
 
-def run_c3(args):
+def run_c3(args, quiet=False):
     """The linear-scaling workload solved to convergence: 4096 atoms (16^3),
     m = 32768, n = 8192, R_C = 6 A, FP64 block-sparse, RelTol 1e-10 (or
     --max-iter steps).  One warm-up solve (gather lists uploaded, modules
@@ -570,7 +597,8 @@ def run_c3(args):
     rows = {
         "products": {"flop": 2 * 2 * 8 * 8 * 2 * TRIPLES["HW"], "bytes": 8 * (2 * 64 * nnz["H"] + 16 * nnz["W"]
                                                                               + 2 * 16 * nnz["HW"])},
-        "contract": {"flop": 4 * 2 * 2 * 2 * 8 * TRIPLES["N"], "bytes": 8 * (2 * 16 * nnz["W"] + 2 * 16 * nnz["HW"]
+        # X, Y on all of P_N; D^T H'D, D^T S D (symmetric) on its upper triangle: ~3 of the 4
+        "contract": {"flop": 3 * 2 * 2 * 2 * 8 * TRIPLES["N"], "bytes": 8 * (2 * 16 * nnz["W"] + 2 * 16 * nnz["HW"]
                                                                              + 4 * 4 * nnz["N"])},
         "gradient": {"flop": 2 * 2 * 8 * 2 * 2 * TRIPLES["G"], "bytes": 8 * (2 * 16 * nnz["HW"] + 2 * 4 * nnz["N"]
                                                                              + 16 * nnz["W"])},
@@ -593,8 +621,10 @@ def run_c3(args):
             "stages_ms_per_solve": {n_: ms[i] for i, n_ in enumerate(STAGES)},
             "roofline": roof, "fp64_peak_tflops": fp64_peak,
             "gpu_launches": int(launches), "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    if not quiet:
+        print(json.dumps(line), flush=True)
     s.close()
+    return line
 
 
 def sparse_triples(sysm, rp, col, wrp, wcol):
@@ -747,7 +777,7 @@ def run_md(args):
 
 
 # ---------------------------------------------------------------- C4: batched uneven solves
-def run_c4(args):
+def run_c4(args, quiet=False):
     """64 uneven dense systems (k-point/spin-like), mixed precision, solved
     together: as one group (each CG step's split products as one persistent
     grouped launch over all systems, tile mode autotuned, chunks of steps as a
@@ -762,8 +792,8 @@ def run_c4(args):
     systems = [synth.make_batch_system(int(N), seed=4000 + i) for i, N in enumerate(sizes)]
     dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
     data = [(dev(s.dense_H()), dev(s.dense_S()), dev(s.W0_dense())) for s in systems]
-    solvers = [omm.Solver(s.m, s.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6, graphs=args.graphs)
-               for s in systems]
+    solvers = [omm.Solver(s.m, s.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6, graphs=args.graphs,
+                          gemm_pair=args.gemm_pair) for s in systems]
 
     def set_all():
         for sv, (H, S, _) in zip(solvers, data):
@@ -831,13 +861,15 @@ def run_c4(args):
             "results_equal_alone": bool(same), "all_ok": bool((stg == omm.OK).all()),
             "iters": {"min": int(itg.min()), "max": int(itg.max())},
             "gpu_launches": int(launches), "clocks": clocks}
-    print(json.dumps(line), flush=True)
+    if not quiet:
+        print(json.dumps(line), flush=True)
     for sv in solvers:
         sv.close()
+    return line
 
 
 # ---------------------------------------------------------------- C5: serving
-def run_c5(args):
+def run_c5(args, quiet=False):
     """Serving loop: Poisson arrivals of SCF-like sequences (one dense system,
     then perturbed Hamiltonians H <- H + sym(N(0, 1e-3 eV)) on its nonzeros,
     each solve warm-started from the resident W), dense m = 8 x round(exp(U(ln 64,
@@ -949,7 +981,9 @@ def run_c5(args):
         for name in ("mixed", "fp64"):
             del cmp[name]["E_last"]
         out["mixed_vs_fp64"] = cmp
-    print(json.dumps(out), flush=True)
+    if not quiet:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 def main():
@@ -976,6 +1010,9 @@ def main():
                     help="mixed form: split products as persistent tile-list launches")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="c4/c5: replay chunks of CG steps as captured CUDA graphs")
+    ap.add_argument("--extras", type=int, default=1, choices=[0, 1],
+                    help="c2: also run short C3 (20 CG steps), C4 and C5 (12 sequences, one rate) "
+                         "and add them to the line")
     ap.add_argument("--no-kinetic", action="store_true",
                     help="skip the kinetic-energy preconditioning comparison on H + T")
     ap.add_argument("--cholesky", action="store_true",

@@ -155,7 +155,10 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
                                                         const float *__restrict__ Z, int64_t ldz,
                                                         double *partials, unsigned int *counter,
                                                         DevState *state) {
-    if (*((volatile int *)&state->done)) return;
+    if (*((volatile int *)&state->done)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) state->done_upd = 1;
+        return;
+    }
     __shared__ float Xt[TILE][TILE + 1];
     __shared__ double red[(NT / 32) * NC];
     const float *X = Z, *Y = Z + (int64_t)n * ldz, *h2 = Z + n, *s2 = Z + n + (int64_t)n * ldz;
@@ -166,28 +169,40 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
     for (int q = 0; q < NC; ++q) f[q] = 0.f;
     for (int t = blockIdx.x; t < T * T; t += gridDim.x) {
         const int ti = t % T, tj = t / T;
-        __syncthreads();
+        // every load of the tile is issued before any is used (zero outside the
+        // matrix instead of a branch), so a thread has ~30 loads in flight
+        float xt[4], vx[4], vy[4], vh2[4], vs2[4];
+        double dh0[4], ds0[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int a = ly + 8 * r, gi = tj * TILE + lx, gj = ti * TILE + a;
-            Xt[a][lx] = (gi < n && gj < n) ? X[gi + (int64_t)gj * ldz] : 0.f;
+            xt[r] = (gi < n && gj < n) ? X[gi + (int64_t)gj * ldz] : 0.f;
+            const int i = ti * TILE + lx, j = tj * TILE + a;
+            const bool in = i < n && j < n;
+            const int64_t oz = i + (int64_t)j * ldz, oh = i + (int64_t)j * ldh;
+            vx[r] = in ? X[oz] : 0.f;
+            vy[r] = in ? Y[oz] : 0.f;
+            vh2[r] = in ? h2[oz] : 0.f;
+            vs2[r] = in ? s2[oz] : 0.f;
+            dh0[r] = in ? h0[oh] : 0.0;
+            ds0[r] = in ? s0[oh] : 0.0;
         }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) Xt[ly + 8 * r][lx] = xt[r];
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int i = ti * TILE + lx, j = tj * TILE + ly + 8 * r;
-            if (i >= n || j >= n) continue;
-            const int64_t oz = i + (int64_t)j * ldz, oh = i + (int64_t)j * ldh;
-            const float vh0 = sw_d2f(h0[oh]), vs0 = sw_d2f(s0[oh]);
-            const float vx = X[oz], vy = Y[oz], vh2 = h2[oz], vs2 = s2[oz], vxt = Xt[lx][ly + 8 * r];
-            if (i == j) f[0] += vh2;
-            f[1] = fmaf(vs0, vh2, f[1]);
-            f[2] = fmaf(vy, vx, f[2]);
-            f[3] = fmaf(vy, vxt, f[3]);
-            f[4] = fmaf(vs2, vh0, f[4]);
-            f[5] = fmaf(vy, vh2, f[5]);
-            f[6] = fmaf(vs2, vx, f[6]);
-            f[7] = fmaf(vs2, vh2, f[7]);
+            const float vh0 = sw_d2f(dh0[r]), vs0 = sw_d2f(ds0[r]), vxt = Xt[lx][ly + 8 * r];
+            if (i == j && i < n) f[0] += vh2[r];
+            f[1] = fmaf(vs0, vh2[r], f[1]);
+            f[2] = fmaf(vy[r], vx[r], f[2]);
+            f[3] = fmaf(vy[r], vxt, f[3]);
+            f[4] = fmaf(vs2[r], vh0, f[4]);
+            f[5] = fmaf(vy[r], vh2[r], f[5]);
+            f[6] = fmaf(vs2[r], vx[r], f[6]);
+            f[7] = fmaf(vs2[r], vh2[r], f[7]);
         }
     }
     double v[NC];
@@ -215,12 +230,13 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
         state->status = st;
         state->done = 1;
     }
+    state->done_upd = st != OMM_OK ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- H_W, S_W update
 // h0 += x (X + X^T) + x^2 sym(h2), s0 likewise (FP32 increments, FP64 sums);
 // ||s0 - I||_F^2 for the orthonormality test; digits of [H_W ; S_W] columns.
-__global__ void __launch_bounds__(NT) mx_nn_update_kernel(int n, double *h0, double *s0, int64_t ldh,
+__global__ void __launch_bounds__(NT, 3) mx_nn_update_kernel(int n, double *h0, double *s0, int64_t ldh,
                                                            const float *__restrict__ Z, int64_t ldz,
                                                            double *partials, unsigned int *counter,
                                                            DevState *state, DigitOut hsw) {
@@ -234,27 +250,44 @@ __global__ void __launch_bounds__(NT) mx_nn_update_kernel(int n, double *h0, dou
     float orth = 0.f;
     for (int t = blockIdx.x; t < T * T; t += gridDim.x) {
         const int ti = t % T, tj = t / T;
-        __syncthreads();
+        // all loads of the tile first (zero outside the matrix), then the transposes
+        // through shared memory, then the updates
+        float tx[4][4], vz[4][4];
+        double dh0[4], ds0[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int a = ly + 8 * r, gi = tj * TILE + lx, gj = ti * TILE + a;
-            const bool in = gi < n && gj < n;
-            const int64_t o = gi + (int64_t)gj * ldz;
-            Tt[0][a][lx] = in ? X[o] : 0.f;
-            Tt[1][a][lx] = in ? Y[o] : 0.f;
-            Tt[2][a][lx] = in ? h2[o] : 0.f;
-            Tt[3][a][lx] = in ? s2[o] : 0.f;
+            const bool tin = gi < n && gj < n;
+            const int64_t to = gi + (int64_t)gj * ldz;
+            tx[0][r] = tin ? X[to] : 0.f;
+            tx[1][r] = tin ? Y[to] : 0.f;
+            tx[2][r] = tin ? h2[to] : 0.f;
+            tx[3][r] = tin ? s2[to] : 0.f;
+            const int i = ti * TILE + lx, j = tj * TILE + a;
+            const bool in = i < n && j < n;
+            const int64_t oz = i + (int64_t)j * ldz, oh = i + (int64_t)j * ldh;
+            vz[0][r] = in ? X[oz] : 0.f;
+            vz[1][r] = in ? Y[oz] : 0.f;
+            vz[2][r] = in ? h2[oz] : 0.f;
+            vz[3][r] = in ? s2[oz] : 0.f;
+            dh0[r] = in ? h0[oh] : 0.0;
+            ds0[r] = in ? s0[oh] : 0.0;
         }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Tt[q][ly + 8 * r][lx] = tx[q][r];
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int i = ti * TILE + lx, j = tj * TILE + ly + 8 * r, b = ly + 8 * r;
             if (i >= n || j >= n) continue;
-            const int64_t oz = i + (int64_t)j * ldz, oh = i + (int64_t)j * ldh;
-            const float xs = X[oz] + Tt[0][lx][b], ys = Y[oz] + Tt[1][lx][b];
-            const float h2s = 0.5f * (h2[oz] + Tt[2][lx][b]), s2s = 0.5f * (s2[oz] + Tt[3][lx][b]);
-            const double vh = h0[oh] + sw_f2d(x * fmaf(x, h2s, xs));
-            const double vs = s0[oh] + sw_f2d(x * fmaf(x, s2s, ys));
+            const int64_t oh = i + (int64_t)j * ldh;
+            const float xs = vz[0][r] + Tt[0][lx][b], ys = vz[1][r] + Tt[1][lx][b];
+            const float h2s = 0.5f * (vz[2][r] + Tt[2][lx][b]), s2s = 0.5f * (vz[3][r] + Tt[3][lx][b]);
+            const double vh = dh0[r] + sw_f2d(x * fmaf(x, h2s, xs));
+            const double vs = ds0[r] + sw_f2d(x * fmaf(x, s2s, ys));
             h0[oh] = vh;
             s0[oh] = vs;
             const float fvs = sw_d2f(vs);
@@ -301,7 +334,7 @@ __global__ void __launch_bounds__(NT) mx_update_kernel(int m, int n, double *W, 
                                                         double *HW, const float *__restrict__ HD, double *SW,
                                                         const float *__restrict__ SD, const DevState *state,
                                                         DigitOut wd, DigitOut swhw) {
-    if (*((volatile const int *)&state->done)) return;
+    if (*((volatile const int *)&state->done_upd)) return;
     __shared__ float tH[TILE][TILE + 1];
     __shared__ float tS[TILE][TILE + 1];
     const float x = state->x_f;
@@ -348,7 +381,7 @@ __global__ void __launch_bounds__(NT) mx_update2_kernel(int m, int n, double2 *W
                                                          double2 *HW, const float2 *__restrict__ HD, double2 *SW,
                                                          const float2 *__restrict__ SD, const DevState *state,
                                                          DigitOut wd, DigitOut swhw) {
-    if (*((volatile const int *)&state->done)) return;
+    if (*((volatile const int *)&state->done_upd)) return;
     __shared__ float tH[TILE][TI2 + 1];
     __shared__ float tS[TILE][TI2 + 1];
     const float x = state->x_f;
@@ -410,6 +443,7 @@ __global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__
     const int64_t n4 = mn / 4, stride = (int64_t)gridDim.x * NT;
     const float4 *G4 = reinterpret_cast<const float4 *>(G), *Gp4 = reinterpret_cast<const float4 *>(Gp),
                  *D4 = reinterpret_cast<const float4 *>(D), *Z4 = reinterpret_cast<const float4 *>(Zg);
+#pragma unroll 4
     for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n4; k += stride) {
         const float4 g = G4[k];
         const float4 z = PRE ? Z4[k] : g;

@@ -124,6 +124,10 @@ struct omm_handle {
     int status = OMM_OK;      // status of the finished solve
     double tol_target = 0.0;
     cudaEvent_t ev_poll = nullptr;
+    // second stream of the mixed form: H_W, S_W updates run beside the m x n updates
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool grouped = false;     // inside omm_batch_solve_grouped's lock-step phase
     omm::sp::Host sh;   // linear-scaling form: patterns and gather lists (host)
     omm::sp::Dev sd;    // linear-scaling form: device arrays
     // optional per-stage device timing (omm_set_profiling)
@@ -206,6 +210,9 @@ void free_handle(omm_handle *h) {
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->ev_poll) cudaEventDestroy(h->ev_poll);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -768,10 +775,25 @@ int mixed_glue1(omm_handle *h, bool accurate_gradient) {
     { StageTimer t(h, OMM_STAGE_LINESEARCH);
       TRY(omm::mx_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 0), ctr(h, 0), s, st)); }
     { StageTimer t(h, OMM_STAGE_UPDATE);
+      // the n x n update (H_W, S_W, energy, stop test) reads and writes nothing the
+      // m x n update touches: for large systems it runs beside it on the handle's
+      // second stream (in a grouped batch, and for small systems, the extra fork
+      // and join cost more than the overlap gains)
+      const bool fork = !h->grouped && m * n >= ((int64_t)1 << 21) && st != cudaStreamLegacy &&
+                        st != cudaStreamPerThread && st != nullptr;
+      cudaStream_t sn = fork ? h->aux : st;
+      if (fork) {
+          OMM_CUDA_TRY(cudaEventRecord(h->ev_fork, st));
+          OMM_CUDA_TRY(cudaStreamWaitEvent(sn, h->ev_fork, 0));
+      }
+      TRY(omm::mx_nn_update((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 1), ctr(h, 1), s,
+                            accurate_gradient ? kNoDigits : dig_HSW(h), sn));
       TRY(omm::mx_update(m, n, h->WD, x.D32, h->SWHW + mn, x.HDSD32, h->SWHW, x.HDSD32 + mn, s, dig_W(h),
                          accurate_gradient ? kNoDigits : dig_SWHW(h), st));
-      TRY(omm::mx_nn_update((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 1), ctr(h, 1), s,
-                            accurate_gradient ? kNoDigits : dig_HSW(h), st)); }
+      if (fork) {
+          OMM_CUDA_TRY(cudaEventRecord(h->ev_join, sn));
+          OMM_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_join, 0));
+      } }
     return OMM_OK;
 }
 
@@ -1229,6 +1251,9 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         cudaMemsetAsync(h->dstate, 0, sizeof(omm::DevState), h->stream) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_poll, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         free_handle(h);
         return OMM_ERR_CUDA;
@@ -1708,6 +1733,14 @@ int omm_batch_solve_grouped(omm_handle **handles, int32_t count, const double *c
     }
     // ---- phase 1 of every system in lock step
     for (int32_t i = 0; i < count; ++i) TRY(begin_setup(handles[i], W0 ? W0[i] : nullptr, W0_on_device, tol));
+    struct Ungroup {
+        omm_handle **hs;
+        int32_t count;
+        ~Ungroup() {
+            for (int32_t i = 0; i < count; ++i) hs[i]->grouped = false;
+        }
+    } ungroup{handles, count};
+    for (int32_t i = 0; i < count; ++i) handles[i]->grouped = true;
     cudaStream_t gs = nullptr;
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join((size_t)count, nullptr);
@@ -1836,6 +1869,7 @@ int omm_batch_solve_grouped(omm_handle **handles, int32_t count, const double *c
         if (all) break;
     }
     // ---- phase 2 (refinement) per system on its own stream, as omm_batch_solve
+    for (int32_t i = 0; i < count; ++i) handles[i]->grouped = false;
     GCUDA(cudaEventRecord(ev_fork, gs));
     for (int32_t i = 0; i < count; ++i) {
         GCUDA(cudaStreamWaitEvent(handles[i]->stream, ev_fork, 0));

@@ -48,6 +48,9 @@ struct DevState {
     double E_next;               // energy at the line minimum, from the quartic
     double e_shift;              // constant of the reported energy: 2 eta n_occ
     float x_f, beta_f;           // x and beta rounded once for the FP32 kernels
+    int done_upd;                // done as the mixed form's line minimum left it: the m x n update
+                                 // reads this copy, since the n x n update (run beside it) may set
+                                 // done when the step converges
 };
 
 // -------- FP64 GEMM (dense_fp64.cu)
