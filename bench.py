@@ -445,7 +445,7 @@ def run_omm(args):
         a3.steps, a3.max_iter, a3.screen_eps = 1, 20, 0.0
         r3 = run_c3(a3, quiet=True)
         ex["c3_20_steps"] = {"workload": r3["config"]["workload"], "ms_per_iteration": r3["ms_per_iteration"],
-                             "stages_ms": r3["stages_ms_per_solve"], "roofline_fp64": r3["roofline"],
+                             "stages_ms": r3["stages_ms_20_steps"], "roofline_fp64": r3["roofline"],
                              "fp64_peak_tflops": r3["fp64_peak_tflops"], "nnzb": r3["config"]["nnzb"],
                              "note": "20 CG steps from W0 (the converged solve is bench.py --config c3)"}
         a4 = copy.copy(args)
@@ -546,10 +546,10 @@ def run_profile_c3(args):
 def run_c3(args, quiet=False):
     """The linear-scaling workload solved to convergence: 4096 atoms (16^3),
     m = 32768, n = 8192, R_C = 6 A, FP64 block-sparse, RelTol 1e-10 (or
-    --max-iter steps).  One warm-up solve (gather lists uploaded, modules
-    loaded), then timed solves from W0 with set_HS inside each step; the
-    per-stage times of one extra profiled solve give the sparse kernels'
-    rooflines (FP64 flops and algorithmic bytes per launch)."""
+    --max-iter steps).  A 20-step handle warms up (gather lists uploaded,
+    modules loaded) and gives the per-stage times of the sparse kernels'
+    rooflines (FP64 flops and algorithmic bytes per launch); the timed solve
+    runs from W0 with set_HS inside each step."""
     import torch
     from paper_2209_05934_gb300 import omm
 
@@ -559,19 +559,31 @@ def run_c3(args, quiet=False):
     wrp, wcol = sysm.w_pattern(C3["radius"])
     stream = torch.cuda.Stream()
     max_iter = args.max_iter if args.max_iter > 0 else 20000
-    s = omm.SparseSolver(sysm.m, sysm.n, 8, 2, rp, col, wrp, wcol, max_iter=max_iter,
-                         stream=stream.cuda_stream, screen_eps=args.screen_eps)
+    prec = omm.PREC_MIXED if args.c3_precision == "mixed" else omm.PREC_FP64
+    mk = lambda k: omm.SparseSolver(sysm.m, sysm.n, 8, 2, rp, col, wrp, wcol, max_iter=k,
+                                    stream=stream.cuda_stream, screen_eps=args.screen_eps, precision=prec)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
     Hd, Sd, W0d = dev(Hv), dev(Sv), dev(sysm.W0_bsr_values(C3["radius"]))
     torch.cuda.synchronize()
     tol = 1e-10
+    # warm-up and per-stage device times: 20 CG steps on their own handle
+    p = mk(20)
+    p.set_HS(Hd, Sd)
+    p.solve(W0d, tol=tol, raise_on_error=False)
+    torch.cuda.synchronize()
+    p.set_profiling(True)
+    p.stage_times(reset=True)
+    p.set_HS(Hd, Sd)
+    p.solve(W0d, tol=tol, raise_on_error=False)
+    torch.cuda.synchronize()
+    ms, cnt = p.stage_times(reset=True)
+    p.close()
+    s = mk(max_iter)
 
     def step():
         s.set_HS(Hd, Sd)
         return s.solve(W0d, tol=tol, raise_on_error=False)
 
-    step()
-    torch.cuda.synchronize()
     launches0 = omm.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
@@ -582,16 +594,8 @@ def run_c3(args, quiet=False):
         torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1) / args.steps
     launches = omm.kernel_launches() - launches0
-    s.set_profiling(True)
-    s.stage_times(reset=True)
-    step()
-    torch.cuda.synchronize()
-    s.set_profiling(False)
-    ms, cnt = s.stage_times(reset=True)
     fp64_peak = fp64_gemm_peak(4096)
     nnz = s.nnzb
-    # algorithmic work per launch (blocks 8x8 / 8x2 / 2x2, FP64): the block-product
-    # triples of each gather, counted from the structural patterns
     TRIPLES = sparse_triples(sysm, rp, col, wrp, wcol)
     d = s.diag()
     rows = {
@@ -615,10 +619,12 @@ def run_c3(args, quiet=False):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": (f"linear-scaling OMM-CG, 4096 atoms (16x16x16 jittered grid), m={sysm.m}, "
                                     f"n={sysm.n}, R_C={C3['radius']} A, BSR 8x8 / 8x2, filter 1e-8"),
-                       "tol": tol, "max_iter": max_iter, "screen_eps": args.screen_eps, "nnzb": nnz},
+                       "tol": tol, "max_iter": max_iter, "screen_eps": args.screen_eps, "nnzb": nnz,
+                       "precision": args.c3_precision},
+            "iters_mixed": int(d.iters_mixed), "iters_refine": int(d.iters_refine),
             "time_to_converge_ms": t_ms, "iters": int(iters), "status": int(st), "E": E, "eta": d.eta,
             "ms_per_iteration": t_ms / max(1, int(iters)),
-            "stages_ms_per_solve": {n_: ms[i] for i, n_ in enumerate(STAGES)},
+            "stages_ms_20_steps": {n_: ms[i] for i, n_ in enumerate(STAGES)},
             "roofline": roof, "fp64_peak_tflops": fp64_peak,
             "gpu_launches": int(launches), "clocks": clk.summary()}
     if not quiet:
@@ -1023,6 +1029,8 @@ def main():
     ap.add_argument("--batch", type=int, default=64, help="c4: number of systems")
     ap.add_argument("--tile-mode", type=int, default=-1, choices=[-1, 0, 1],
                     help="c4: grouped launch tile mode (-1 autotune, 0 single CTA, 1 CTA pair)")
+    ap.add_argument("--c3-precision", default="fp64", choices=["fp64", "mixed"],
+                    help="c3: FP64 throughout, or FP32 increments on FP64 state with an FP64 refinement")
     ap.add_argument("--screen-eps", type=float, default=0.0,
                     help="c3: norm-based screening threshold of the sparse block products (0: off)")
     ap.add_argument("--md-steps", type=int, default=5, help="md: snapshots per chain")

@@ -100,7 +100,7 @@ struct omm_handle {
     int cur_dig = 3;          // digits of the split products of the current phase
     // one CUDA graph per phase for the chunk of CG steps, captured after one
     // eager chunk of that phase (modules loaded, kernel attributes set)
-    static constexpr int kPhases = 6;
+    static constexpr int kPhases = 7;
     cudaGraphExec_t graph[kPhases] = {};
     int64_t graph_kernels[kPhases] = {};
     int graph_eager[kPhases] = {};
@@ -877,8 +877,22 @@ int sparse_iteration(omm_handle *h) {
     return OMM_OK;
 }
 
+// One first-phase step of the mixed sparse form (FP32 increments on FP64 state).
+int sparse_mixed_iteration(omm_handle *h) {
+    omm::sp::Dev &d = h->sd;
+    cudaStream_t st = h->stream;
+    omm::DevState *s = h->dstate;
+    { StageTimer t(h, OMM_STAGE_PRODUCTS); TRY(omm::sp::mixed_products(d, s, st)); }
+    { StageTimer t(h, OMM_STAGE_CONTRACT); TRY(omm::sp::mixed_contract(d, s, st)); }
+    { StageTimer t(h, OMM_STAGE_LINESEARCH); TRY(omm::sp::mixed_coeffs(d, scr(h, 0), ctr(h, 0), s, st)); }
+    { StageTimer t(h, OMM_STAGE_UPDATE); TRY(omm::sp::mixed_update(d, scr(h, 1), ctr(h, 1), s, st)); }
+    { StageTimer t(h, OMM_STAGE_GRADIENT); TRY(omm::sp::mixed_gradient(d, s, st)); }
+    { StageTimer t(h, OMM_STAGE_DIRECTION); TRY(omm::sp::mixed_direction(d, scr(h, 2), ctr(h, 2), s, st)); }
+    return OMM_OK;
+}
+
 // Solve phases of the asynchronous driver (omm_solve_begin / _progress / _end)
-enum { PH_IDLE = 0, PH_MIXED = 1, PH_REFINE = 2, PH_FP64 = 3, PH_SPARSE = 4, PH_FINISHED = 5 };
+enum { PH_IDLE = 0, PH_MIXED = 1, PH_REFINE = 2, PH_FP64 = 3, PH_SPARSE = 4, PH_FINISHED = 5, PH_SPARSE_MIXED = 6 };
 
 double *w_dev(omm_handle *h) { return h->sparse ? h->sd.W : h->WD; }
 int64_t w_len(omm_handle *h) { return h->sparse ? h->sd.nnzW * h->sd.bm * h->sd.bn : h->m * h->n; }
@@ -892,6 +906,7 @@ int chunk_body(omm_handle *h) {
             case PH_REFINE: TRY(mixed_iteration(h, true)); break;
             case PH_FP64: TRY(dense_iteration(h)); break;
             case PH_SPARSE: TRY(sparse_iteration(h)); break;
+            case PH_SPARSE_MIXED: TRY(sparse_mixed_iteration(h)); break;
             default: return OMM_ERR_STATE;
         }
     }
@@ -1150,7 +1165,8 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
             pattern->W_rowptr == nullptr || pattern->W_col == nullptr)
             return OMM_ERR_PATTERN;
         if (pattern->bm != 8 || pattern->bn != 2) return OMM_ERR_UNSUPPORTED;
-        if (opt != nullptr && (opt->precision != OMM_PREC_FP64 || opt->cholesky != 0 || opt->precon != 0))
+        if (opt != nullptr && (opt->cholesky != 0 || opt->precon != 0 ||
+                               (opt->precision == OMM_PREC_MIXED && opt->screen_eps > 0.0)))
             return OMM_ERR_UNSUPPORTED;
     }
     omm_handle *h = new (std::nothrow) omm_handle();
@@ -1219,7 +1235,7 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         free_handle(h);
         return rc;
     }
-    if (h->opt.precision == OMM_PREC_MIXED && (rc = mixed_alloc(h))) {
+    if (h->opt.precision == OMM_PREC_MIXED && (rc = h->sparse ? omm::sp::mixed_alloc(h->sd) : mixed_alloc(h))) {
         free_handle(h);
         return rc;
     }
@@ -1234,7 +1250,8 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
             return rc;
         }
     }
-    if (h->opt.precision == OMM_PREC_MIXED && h->opt.refine == OMM_REFINE_EXACT && (rc = exact_alloc(h))) {
+    if (!h->sparse && h->opt.precision == OMM_PREC_MIXED && h->opt.refine == OMM_REFINE_EXACT &&
+        (rc = exact_alloc(h))) {
         free_handle(h);
         return rc;
     }
@@ -1278,6 +1295,7 @@ int omm_set_HS(omm_handle *h, const double *H, const double *S, int32_t on_devic
             StageTimer t(h, OMM_STAGE_SETUP);
             TRY(omm::sp::set_HS(h->sd, H, S, on_device != 0, h->opt.filter_eps, h->opt.eta_auto != 0, scr(h, 3),
                                 ctr(h, 3), h->dstate, st));
+            if (h->sd.mixed) TRY(omm::sp::mixed_shadow_HS(h->sd, st));
         }
         OMM_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(omm::DevState), cudaMemcpyDeviceToHost, st));
         OMM_CUDA_TRY(cudaEventRecord(h->ev1, st));
@@ -1418,7 +1436,20 @@ int begin_setup(omm_handle *h, const double *W0, int32_t W0_on_device, double to
     h->tol_target = tol;
     h->k_mixed = 0;
     h->status = OMM_OK;
-    if (h->sparse) {
+    if (h->sparse && h->sd.mixed) {
+        // first phase with FP32 increments: from the FP64 start, to RelTol
+        // max(0.1 tol, 1e-12) or until the FP32 increments' noise makes the energy
+        // rise; an FP64 refinement, re-anchored from W, takes it to tol
+        h->phase = PH_SPARSE_MIXED;
+        omm::DevState ph = init;
+        ph.tol = fmax(0.1 * tol, 1e-12);
+        ph.orth_tol = 0.0;
+        *h->hstate = ph;
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
+        { StageTimer t(h, OMM_STAGE_START);
+          TRY(sparse_start(h));
+          TRY(omm::sp::mixed_begin(h->sd, h->dstate, st)); }
+    } else if (h->sparse) {
         h->phase = PH_SPARSE;
         *h->hstate = init;
         OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, st));
@@ -1475,6 +1506,23 @@ int omm_solve_progress(omm_handle *h, int32_t blocking, int32_t *done) {
         return OMM_OK;
     }
     if (!h->hstate->done) return enqueue_chunk(h);
+    if (h->phase == PH_SPARSE_MIXED && h->hstate->status == OMM_OK) {
+        // refinement of the sparse form: FP64 steps, re-anchored from W
+        h->k_mixed = h->hstate->k;
+        omm::DevState rf{};
+        rf.eta = h->diag.eta;
+        rf.e_shift = 2.0 * h->diag.eta * (double)n_occ(h);
+        rf.tol = h->tol_target;
+        rf.orth_tol = h->opt.orth_tol;
+        rf.max_iter = h->opt.max_iter;
+        rf.n = (int)h->n;
+        rf.k = h->k_mixed;
+        *h->hstate = rf;
+        OMM_CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(omm::DevState), cudaMemcpyHostToDevice, h->stream));
+        { StageTimer t(h, OMM_STAGE_ANCHOR); TRY(sparse_start(h)); }
+        h->phase = PH_SPARSE;
+        return enqueue_chunk(h);
+    }
     if (h->phase == PH_MIXED && h->hstate->status == OMM_OK) {
         // phase 2: refinement sweep -- accurate re-anchoring of H'W, SW, H_W,
         // S_W and G, then CG steps with an accurate gradient

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "fp_convert.cuh"
 #include "linemin.cuh"
 #include "omm_internal.cuh"
 #include "sparse.cuh"
@@ -490,11 +491,11 @@ __global__ void __launch_bounds__(NT) gershgorin_kernel(int64_t nbr, int bm, con
 // Screening (SCREEN): the block product H'_(I,K) D_(K,J) (or S_(I,K) D_(K,J)) is
 // skipped when ||H'_(I,K)||^2 ||D_(K,J)||^2 < eps^2, from the squared block norms
 // nHS ([nnzH][2]: H', S) and nB (one per D block).
-template <int BM, int BN, bool SCREEN>
+template <int BM, int BN, bool SCREEN, typename T = double>
 __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64_t *__restrict__ Prp,
                                                        const int32_t *__restrict__ Ph, const int32_t *__restrict__ Pw,
-                                                       const double *__restrict__ HS, const double *__restrict__ D,
-                                                       double *HD, double *SD, const double *__restrict__ nHS,
+                                                       const T *__restrict__ HS, const T *__restrict__ D,
+                                                       T *HD, T *SD, const double *__restrict__ nHS,
                                                        const double *__restrict__ nB, double eps2,
                                                        const DevState *state) {
     if (done(state)) return;
@@ -505,11 +506,11 @@ __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64
     const int r = e / BN, c = e % BN;
     const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
     for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; o < nnzHW; o += nwarps) {
-        double acc = 0.0;
+        T acc = T(0);
         for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
             if (SCREEN && nHS[(int64_t)Ph[t] * 2 + which] * nB[Pw[t]] < eps2) continue;
-            const double *A = HS + ((int64_t)Ph[t] * 2 + which) * BM * BM + r * BM;
-            const double *B = D + (int64_t)Pw[t] * BM * BN + c;
+            const T *A = HS + ((int64_t)Ph[t] * 2 + which) * BM * BM + r * BM;
+            const T *B = D + (int64_t)Pw[t] * BM * BN + c;
             if (active) {
 #pragma unroll
                 for (int k = 0; k < BM; ++k) acc = fma(A[k], B[k * BN], acc);
@@ -523,12 +524,12 @@ __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64
 // with two lanes each splitting the basis index k.
 // Screening: the pair (L block a, R block b) is skipped when ||L_a||^2 ||R_b||^2 < eps^2,
 // with L = W or D and R = H'D or SD as the output matrix takes them.
-template <int BM, int BN, bool SCREEN>
+template <int BM, int BN, bool SCREEN, typename T = double>
 __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_t *__restrict__ Crp,
                                                        const int32_t *__restrict__ Ca, const int32_t *__restrict__ Cb,
-                                                       const double *__restrict__ W, const double *__restrict__ D,
-                                                       const double *__restrict__ HD, const double *__restrict__ SD,
-                                                       double *X, double *Y, double *h2, double *s2,
+                                                       const T *__restrict__ W, const T *__restrict__ D,
+                                                       const T *__restrict__ HD, const T *__restrict__ SD,
+                                                       T *X, T *Y, T *h2, T *s2,
                                                        const double *__restrict__ nW, const double *__restrict__ nD,
                                                        const double *__restrict__ nHD, const double *__restrict__ nSD,
                                                        double eps2, const int32_t *__restrict__ Ntr,
@@ -538,9 +539,9 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
     static_assert(BN == 2, "contraction lanes assume 2 orbitals per W block");
     const int v = lane >> 1, half = lane & 1;
     const int mat = v >> 2, a = (v >> 1) & 1, b = v & 1;   // mat: 0 X, 1 Y, 2 h2, 3 s2
-    const double *L = (mat < 2) ? W : D;
-    const double *R = (mat == 0 || mat == 2) ? HD : SD;
-    double *out = mat == 0 ? X : mat == 1 ? Y : mat == 2 ? h2 : s2;
+    const T *L = (mat < 2) ? W : D;
+    const T *R = (mat == 0 || mat == 2) ? HD : SD;
+    T *out = mat == 0 ? X : mat == 1 ? Y : mat == 2 ? h2 : s2;
     const double *nL = SCREEN ? ((mat < 2) ? nW : nD) : nullptr;
     const double *nR = SCREEN ? ((mat == 0 || mat == 2) ? nHD : nSD) : nullptr;
     // lower-triangle blocks with `Ntr` given: D^T H'D and D^T S D are symmetric, so
@@ -548,15 +549,15 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
     // output by four lanes splitting the basis index k
     const int v4 = lane >> 2, quarter = lane & 3;
     const int mat4 = v4 >> 2, a4 = (v4 >> 1) & 1, b4 = v4 & 1;   // mat4: 0 X, 1 Y
-    const double *R4 = mat4 == 0 ? HD : SD;
-    double *out4 = mat4 == 0 ? X : Y;
+    const T *R4 = mat4 == 0 ? HD : SD;
+    T *out4 = mat4 == 0 ? X : Y;
     const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
     for (int64_t q = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; q < nnzN; q += nwarps) {
         if (!SCREEN && Ntr != nullptr && Ntr[q] < q) {
-            double acc = 0.0;
+            T acc = T(0);
             for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
-                const double *l = W + (int64_t)Ca[t] * BM * BN + a4;
-                const double *rr = R4 + (int64_t)Cb[t] * BM * BN + b4;
+                const T *l = W + (int64_t)Ca[t] * BM * BN + a4;
+                const T *rr = R4 + (int64_t)Cb[t] * BM * BN + b4;
 #pragma unroll
                 for (int kk = 0; kk < BM / 4; ++kk) {
                     const int k = quarter * (BM / 4) + kk;
@@ -568,11 +569,11 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
             if (quarter == 0) out4[q * 4 + a4 * 2 + b4] = acc;
             continue;
         }
-        double acc = 0.0;
+        T acc = T(0);
         for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
             if (SCREEN && nL[Ca[t]] * nR[Cb[t]] < eps2) continue;
-            const double *l = L + (int64_t)Ca[t] * BM * BN + a;
-            const double *rr = R + (int64_t)Cb[t] * BM * BN + b;
+            const T *l = L + (int64_t)Ca[t] * BM * BN + a;
+            const T *rr = R + (int64_t)Cb[t] * BM * BN + b;
 #pragma unroll
             for (int kk = 0; kk < BM / 2; ++kk) {
                 const int k = half * (BM / 2) + kk;
@@ -585,8 +586,8 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
 }
 
 // h2, s2 on the lower-triangle blocks of P_N from their transposes' blocks
-__global__ void mirror_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr, double *h2, double *s2,
-                              const DevState *state) {
+template <typename T>
+__global__ void mirror_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr, T *h2, T *s2, const DevState *state) {
     if (done(state)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnzN * 4;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -603,12 +604,12 @@ __global__ void mirror_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr, dou
 // half-warp per W block, one lane per element (r, c).
 // Screening: SW_(I,K) h0_(K,J) and H'W_(I,K) s0_(K,J) are skipped separately when
 // the product of their squared block norms is below eps^2.
-template <int BM, int BN, bool SCREEN>
+template <int BM, int BN, bool SCREEN, typename T = double>
 __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_t *__restrict__ Grp,
                                                        const int32_t *__restrict__ Gb, const int32_t *__restrict__ Gq,
-                                                       const int32_t *__restrict__ WtoHW, const double *__restrict__ HW,
-                                                       const double *__restrict__ SW, const double *__restrict__ h0,
-                                                       const double *__restrict__ s0, double *G,
+                                                       const int32_t *__restrict__ WtoHW, const T *__restrict__ HW,
+                                                       const T *__restrict__ SW, const T *__restrict__ h0,
+                                                       const T *__restrict__ s0, T *G,
                                                        const double *__restrict__ nHW, const double *__restrict__ nSW,
                                                        const double *__restrict__ nh0, const double *__restrict__ ns0,
                                                        double eps2, const DevState *state) {
@@ -618,12 +619,12 @@ __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_
     const int r = e / BN, c = e % BN;
     const int64_t ngroups = ((int64_t)gridDim.x * NT) >> 4;
     for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 4; o < nnzW; o += ngroups) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int64_t t = Grp[o]; t < Grp[o + 1]; ++t) {
-        const double *sw = SW + (int64_t)Gb[t] * BM * BN + r * BN;
-        const double *hw = HW + (int64_t)Gb[t] * BM * BN + r * BN;
-        const double *hq = h0 + (int64_t)Gq[t] * BN * BN + c;
-        const double *sq = s0 + (int64_t)Gq[t] * BN * BN + c;
+        const T *sw = SW + (int64_t)Gb[t] * BM * BN + r * BN;
+        const T *hw = HW + (int64_t)Gb[t] * BM * BN + r * BN;
+        const T *hq = h0 + (int64_t)Gq[t] * BN * BN + c;
+        const T *sq = s0 + (int64_t)Gq[t] * BN * BN + c;
         if (SCREEN) {
             const bool use_s = !(nSW[Gb[t]] * nh0[Gq[t]] < eps2), use_h = !(nHW[Gb[t]] * ns0[Gq[t]] < eps2);
 #pragma unroll
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_
             acc = fma(hw[k], sq[k * BN], acc);
         }
     }
-    G[o * BM * BN + e] = 2.0 * (2.0 * HW[(int64_t)WtoHW[o] * BM * BN + e] - acc);
+    G[o * BM * BN + e] = T(2) * (T(2) * HW[(int64_t)WtoHW[o] * BM * BN + e] - acc);
     }
 }
 
@@ -781,8 +782,9 @@ __global__ void axpy_kernel(int64_t nW, double *W, const double *__restrict__ D,
 }
 
 constexpr int ND = 3;
-__global__ void __launch_bounds__(NT) dots_kernel(int64_t len, const double *__restrict__ G,
-                                                   const double *__restrict__ Gp, const double *__restrict__ D,
+template <typename T>
+__global__ void __launch_bounds__(NT) dots_kernel(int64_t len, const T *__restrict__ G,
+                                                   const T *__restrict__ Gp, const T *__restrict__ D,
                                                    double *partials, unsigned int *counter, DevState *state, int first) {
     if (done(state)) return;
     __shared__ double red[(NT / 32) * ND];
@@ -819,15 +821,178 @@ __global__ void __launch_bounds__(NT) dots_kernel(int64_t len, const double *__r
     state->restart = restart;
 }
 
-__global__ void direction_kernel(int64_t len, const double *__restrict__ G, double *Gp, double *D,
-                                 const DevState *state) {
+template <typename T>
+__global__ void direction_kernel(int64_t len, const T *__restrict__ G, T *Gp, T *D, const DevState *state) {
     if (done(state)) return;
-    const double beta = state->beta;
+    const T beta = (T)state->beta;
     const bool restart = state->restart != 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-        const double g = G[i];
+        const T g = G[i];
         D[i] = restart ? -g : fma(beta, D[i], -g);
         Gp[i] = g;
+    }
+}
+
+// ======================================================================== mixed form
+// FP32 increments on FP64 state: the first phase of a mixed-precision sparse solve
+// forms H'D, SD, the contractions and the gradient in FP32 (the GB300 FP32 pipe is
+// ~60x the FP64 one) from FP32 copies ("shadows") of H', S, W, H'W, SW, H_W, S_W,
+// and adds each FP32 increment to the FP64 state; energies and the stop test stay
+// FP64.  A refinement in FP64, re-anchored from W, finishes the solve.
+struct ConvJob {
+    const double *src;
+    float *dst;
+    int64_t n;
+};
+struct ConvJobs {
+    ConvJob j[8];
+    int n;
+};
+
+__global__ void shadow_kernel(ConvJobs jobs, const DevState *state) {
+    if (done(state)) return;
+    for (int q = 0; q < jobs.n; ++q) {
+        const ConvJob J = jobs.j[q];
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < J.n; i += (int64_t)gridDim.x * blockDim.x)
+            J.dst[i] = sw_d2f(J.src[i]);
+    }
+}
+
+// quartic coefficients from FP32 shadows and increments, FP32 per-thread sums
+// combined in FP64; c0 is the FP64 energy of the current state
+__global__ void __launch_bounds__(NT) mx_coeffs_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr,
+                                                        const unsigned char *__restrict__ Ndiag,
+                                                        const float *__restrict__ h0, const float *__restrict__ s0,
+                                                        const float *__restrict__ X, const float *__restrict__ Y,
+                                                        const float *__restrict__ h2, const float *__restrict__ s2,
+                                                        double *partials, unsigned int *counter, DevState *state) {
+    if (done(state)) return;
+    __shared__ double red[(NT / 32) * NC];
+    float f[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) f[q] = 0.f;
+    const int64_t total = nnzN * 4;
+    for (int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x; t < total; t += (int64_t)gridDim.x * NT) {
+        const int64_t q = t >> 2;
+        const int e = (int)(t & 3), a = e >> 1, b = e & 1;
+        const int64_t tt = (int64_t)Ntr[q] * 4 + b * 2 + a;
+        const float vh0 = h0[t], vs0 = s0[t], vx = X[t], vy = Y[t], vh2 = h2[t], vs2 = s2[t], vxt = X[tt];
+        if (Ndiag[q] && a == b) { f[0] += vh0; f[2] += vx; f[5] += vh2; }
+        f[1] = fmaf(vs0, vh0, f[1]);
+        f[3] = fmaf(vs0, vx, f[3]);
+        f[4] = fmaf(vy, vh0, f[4]);
+        f[6] = fmaf(vs0, vh2, f[6]);
+        f[7] = fmaf(vy, vx, f[7]);
+        f[8] = fmaf(vy, vxt, f[8]);
+        f[9] = fmaf(vs2, vh0, f[9]);
+        f[10] = fmaf(vy, vh2, f[10]);
+        f[11] = fmaf(vs2, vx, f[11]);
+        f[12] = fmaf(vs2, vh2, f[12]);
+    }
+    double v[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) v[q] = sw_f2d(f[q]);
+    block_sum<NC>(v, red);
+    double tot[NC] = {};
+    if (!publish_and_collect<NC>(v, partials, counter, tot, red)) return;
+    if (threadIdx.x >= 32) return;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) tot[q] = __shfl_sync(0xffffffffu, tot[q], 0);
+    double c[5];
+    c[0] = state->E - state->e_shift;
+    c[1] = 2.0 * (4.0 * tot[2] - 2.0 * tot[3] - 2.0 * tot[4]);
+    c[2] = 2.0 * (2.0 * tot[5] - tot[6] - 2.0 * (tot[7] + tot[8]) - tot[9]);
+    c[3] = 2.0 * (-2.0 * tot[10] - 2.0 * tot[11]);
+    c[4] = -2.0 * tot[12];
+    double x = 0.0;
+    const int st = lm::quartic_min_warp(c, &x);
+    if (threadIdx.x != 0) return;
+    for (int q = 0; q < 5; ++q) state->c[q] = c[q];
+    state->x = x;
+    state->x_f = (float)x;
+    if (st != OMM_OK) {
+        state->status = st;
+        state->done = 1;
+    }
+}
+
+// W += x D, H'W += x H'D, SW += x SD (FP64 state, FP32 increments) and their shadows
+__global__ void mx_axpy_kernel(int64_t nW, double *W, const float *__restrict__ D, float *Ws, int64_t nHW, double *HW,
+                               const float *__restrict__ HD, float *HWs, double *SW, const float *__restrict__ SD,
+                               float *SWs, const DevState *state) {
+    if (done(state)) return;
+    const double x = state->x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nHW; i += (int64_t)gridDim.x * blockDim.x) {
+        const double hw = fma(x, sw_f2d(HD[i]), HW[i]);
+        const double sw = fma(x, sw_f2d(SD[i]), SW[i]);
+        HW[i] = hw;
+        SW[i] = sw;
+        HWs[i] = sw_d2f(hw);
+        SWs[i] = sw_d2f(sw);
+        if (i < nW) {
+            const double w = fma(x, sw_f2d(D[i]), W[i]);
+            W[i] = w;
+            Ws[i] = sw_d2f(w);
+        }
+    }
+}
+
+// h0, s0 += x (X + X^T) + x^2 sym(h2 / s2) in FP64 from FP32 increments, their shadows,
+// energy, ||S_W - I||, and the first phase's stop: RelTol, or an energy that rose
+// (the FP32 increments' noise floor), or max_iter
+__global__ void __launch_bounds__(NT) mx_nn_update_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr,
+                                                           const unsigned char *__restrict__ Ndiag, double *h0,
+                                                           double *s0, const float *__restrict__ X,
+                                                           const float *__restrict__ Y, const float *__restrict__ h2,
+                                                           const float *__restrict__ s2, float *h0s, float *s0s,
+                                                           double *partials, unsigned int *counter, DevState *state) {
+    if (done(state)) return;
+    __shared__ double red[(NT / 32) * NE3];
+    const double x = state->x;
+    double v[NE3] = {0.0, 0.0, 0.0};
+    const int64_t total = nnzN * 4;
+    for (int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x; t < total; t += (int64_t)gridDim.x * NT) {
+        const int64_t q = t >> 2;
+        const int e = (int)(t & 3), a = e >> 1, b = e & 1;
+        const int64_t tt = (int64_t)Ntr[q] * 4 + b * 2 + a;
+        const float fx = (float)x;
+        const float dh = fx * fmaf(fx, 0.5f * (h2[t] + h2[tt]), X[t] + X[tt]);
+        const float ds = fx * fmaf(fx, 0.5f * (s2[t] + s2[tt]), Y[t] + Y[tt]);
+        const double vh = h0[t] + sw_f2d(dh), vs = s0[t] + sw_f2d(ds);
+        h0[t] = vh;
+        s0[t] = vs;
+        h0s[t] = sw_d2f(vh);
+        s0s[t] = sw_d2f(vs);
+        const bool dg = Ndiag[q] && a == b;
+        if (dg) v[0] += vh;
+        v[1] = fma(vs, vh, v[1]);
+        const double ee = vs - (dg ? 1.0 : 0.0);
+        v[2] = fma(ee, ee, v[2]);
+    }
+    block_sum<NE3>(v, red);
+    double tot[NE3];
+    if (!publish_and_collect<NE3>(v, partials, counter, tot, red)) return;
+    if (threadIdx.x != 0) return;
+    const double E = 2.0 * (2.0 * tot[0] - tot[1]) + state->e_shift;
+    state->orth2 = tot[2];
+    if (!isfinite(E)) {
+        state->status = OMM_ERR_NONFINITE;
+        state->done = 1;
+        state->E = E;
+        return;
+    }
+    const double Ep = state->E;
+    const double rel = fabs(2.0 * (E - Ep) / (E + Ep));
+    state->E_prev = Ep;
+    state->E = E;
+    state->rel = rel;
+    state->k += 1;
+    if (rel < state->tol || E > Ep) {
+        state->status = OMM_OK;
+        state->done = 1;
+    } else if (state->k >= state->max_iter) {
+        state->status = OMM_ERR_MAXITER;
+        state->done = 1;
     }
 }
 
@@ -984,7 +1149,7 @@ void release(Dev &d) {
     void *ptrs[] = {d.Trp, d.Rrp, d.Tw, d.Tq, d.Rt, d.Rw, d.K, d.T,
                     d.Hrp, d.Hcol, d.Prp, d.Ph, d.Pw, d.Crp, d.Ca, d.Cb, d.Grp, d.Gb, d.Gq, d.WtoHW, d.Ntr,
                     d.Ndiag, d.HS, d.Hin, d.W, d.D, d.G, d.Gp, d.HW, d.SW, d.HD, d.SD, d.h0, d.s0, d.X,
-                    d.Y, d.h2, d.s2, d.keep, d.nrm};
+                    d.Y, d.h2, d.s2, d.keep, d.nrm, d.fbuf};
     for (void *p : ptrs) cudaFree(p);
     d = Dev{};
 }
@@ -1092,7 +1257,7 @@ int contract(Dev &d, const double *Wl, const double *Dl, const double *HDr, cons
                                      nullptr, nullptr, nullptr, 0.0, sym ? d.Ntr : nullptr, state)));
     LAUNCHED();
     if (sym) {
-        mirror_kernel<<<blocks_for(d.nnzN * 4, 256), 256, 0, st>>>(d.nnzN, d.Ntr, h2o, s2o, state);
+        mirror_kernel<double><<<blocks_for(d.nnzN * 4, 256), 256, 0, st>>>(d.nnzN, d.Ntr, h2o, s2o, state);
         LAUNCHED();
     }
     return OMM_OK;
@@ -1151,6 +1316,120 @@ int gradient(Dev &d, const DevState *state, cudaStream_t st) {
     return OMM_OK;
 }
 
+int mixed_alloc(Dev &d) {
+    const int64_t bb = (int64_t)d.bm * d.bm, bw = (int64_t)d.bm * d.bn, bq = (int64_t)d.bn * d.bn;
+    const int64_t nHS = 2 * d.nnzH * bb, nW = d.nnzW * bw, nHW = d.nnzHW * bw, nN = d.nnzN * bq;
+    const int64_t total = nHS + 4 * nW + 4 * nHW + 6 * nN;
+    if (cudaMalloc((void **)&d.fbuf, (size_t)(total > 0 ? total : 1) * sizeof(float)) != cudaSuccess)
+        return OMM_ERR_NOMEM;
+    float *p = d.fbuf;
+    auto take = [&](float **dst, int64_t n) { *dst = p; p += n; };
+    take(&d.HS32, nHS);
+    take(&d.W32, nW);
+    take(&d.D32, nW);
+    take(&d.G32, nW);
+    take(&d.Gp32, nW);
+    take(&d.HW32, nHW);
+    take(&d.SW32, nHW);
+    take(&d.HD32, nHW);
+    take(&d.SD32, nHW);
+    take(&d.h032, nN);
+    take(&d.s032, nN);
+    take(&d.X32, nN);
+    take(&d.Y32, nN);
+    take(&d.h232, nN);
+    take(&d.s232, nN);
+    d.mixed = true;
+    return OMM_OK;
+}
+
+namespace {
+int convert(ConvJobs &jobs, const DevState *state, cudaStream_t st) {
+    if (jobs.n == 0) return OMM_OK;
+    int64_t most = 0;
+    for (int q = 0; q < jobs.n; ++q) most = std::max(most, jobs.j[q].n);
+    shadow_kernel<<<blocks_for(most, 256), 256, 0, st>>>(jobs, state);
+    LAUNCHED();
+    jobs.n = 0;
+    return OMM_OK;
+}
+}  // namespace
+
+int mixed_shadow_HS(Dev &d, cudaStream_t st) {
+    ConvJobs jobs{};
+    jobs.j[jobs.n++] = ConvJob{d.HS, d.HS32, 2 * d.nnzH * d.bm * d.bm};
+    return convert(jobs, nullptr, st);
+}
+
+int mixed_begin(Dev &d, const DevState *state, cudaStream_t st) {
+    const int64_t bw = (int64_t)d.bm * d.bn, bq = (int64_t)d.bn * d.bn;
+    ConvJobs jobs{};
+    jobs.j[jobs.n++] = ConvJob{d.W, d.W32, d.nnzW * bw};
+    jobs.j[jobs.n++] = ConvJob{d.D, d.D32, d.nnzW * bw};
+    jobs.j[jobs.n++] = ConvJob{d.G, d.G32, d.nnzW * bw};
+    jobs.j[jobs.n++] = ConvJob{d.Gp, d.Gp32, d.nnzW * bw};
+    jobs.j[jobs.n++] = ConvJob{d.HW, d.HW32, d.nnzHW * bw};
+    jobs.j[jobs.n++] = ConvJob{d.SW, d.SW32, d.nnzHW * bw};
+    jobs.j[jobs.n++] = ConvJob{d.h0, d.h032, d.nnzN * bq};
+    jobs.j[jobs.n++] = ConvJob{d.s0, d.s032, d.nnzN * bq};
+    return convert(jobs, state, st);
+}
+
+int mixed_products(Dev &d, const DevState *state, cudaStream_t st) {
+    DISPATCH_BLOCKS(d.bm, d.bn, (products_kernel<BM, BN, false, float><<<blocks_for(d.nnzHW * 32, NT), NT, 0, st>>>(
+                                     d.nnzHW, d.Prp, d.Ph, d.Pw, d.HS32, d.D32, d.HD32, d.SD32, nullptr, nullptr, 0.0,
+                                     state)));
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int mixed_contract(Dev &d, const DevState *state, cudaStream_t st) {
+    DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, false, float><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
+                                     d.nnzN, d.Crp, d.Ca, d.Cb, d.W32, d.D32, d.HD32, d.SD32, d.X32, d.Y32, d.h232,
+                                     d.s232, nullptr, nullptr, nullptr, nullptr, 0.0, d.Ntr, state)));
+    LAUNCHED();
+    mirror_kernel<float><<<blocks_for(d.nnzN * 4, 256), 256, 0, st>>>(d.nnzN, d.Ntr, d.h232, d.s232, state);
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int mixed_coeffs(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
+    mx_coeffs_kernel<<<red_blocks(d.nnzN * 4), NT, 0, st>>>(d.nnzN, d.Ntr, d.Ndiag, d.h032, d.s032, d.X32, d.Y32,
+                                                              d.h232, d.s232, scratch, counter, state);
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int mixed_update(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
+    const int64_t bw = (int64_t)d.bm * d.bn;
+    mx_axpy_kernel<<<blocks_for(d.nnzHW * bw, 256 * 4), 256, 0, st>>>(d.nnzW * bw, d.W, d.D32, d.W32, d.nnzHW * bw,
+                                                                         d.HW, d.HD32, d.HW32, d.SW, d.SD32, d.SW32,
+                                                                         state);
+    LAUNCHED();
+    mx_nn_update_kernel<<<red_blocks(d.nnzN * 4), NT, 0, st>>>(d.nnzN, d.Ntr, d.Ndiag, d.h0, d.s0, d.X32, d.Y32,
+                                                                 d.h232, d.s232, d.h032, d.s032, scratch, counter,
+                                                                 state);
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int mixed_gradient(Dev &d, const DevState *state, cudaStream_t st) {
+    DISPATCH_BLOCKS(d.bm, d.bn, (gradient_kernel<BM, BN, false, float><<<blocks_for(d.nnzW * 16, NT), NT, 0, st>>>(
+                                     d.nnzW, d.Grp, d.Gb, d.Gq, d.WtoHW, d.HW32, d.SW32, d.h032, d.s032, d.G32,
+                                     nullptr, nullptr, nullptr, nullptr, 0.0, state)));
+    LAUNCHED();
+    return OMM_OK;
+}
+
+int mixed_direction(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
+    const int64_t len = d.nnzW * d.bm * d.bn;
+    dots_kernel<float><<<red_blocks(len), NT, 0, st>>>(len, d.G32, d.Gp32, d.D32, scratch, counter, state, 0);
+    LAUNCHED();
+    direction_kernel<float><<<blocks_for(len, 256 * 4), 256, 0, st>>>(len, d.G32, d.Gp32, d.D32, state);
+    LAUNCHED();
+    return OMM_OK;
+}
+
 int coeffs(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
     coeffs_kernel<<<red_blocks(d.nnzN * 4), NT, 0, st>>>(d.nnzN, d.Ntr, d.Ndiag, d.h0, d.s0, d.X, d.Y, d.h2,
                                                            d.s2, scratch, counter, state);
@@ -1175,14 +1454,14 @@ int axpy(Dev &d, const DevState *state, cudaStream_t st) {
 
 int dots(Dev &d, int first, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
     const int64_t len = d.nnzW * d.bm * d.bn;
-    dots_kernel<<<red_blocks(len), NT, 0, st>>>(len, d.G, d.Gp, d.D, scratch, counter, state, first);
+    dots_kernel<double><<<red_blocks(len), NT, 0, st>>>(len, d.G, d.Gp, d.D, scratch, counter, state, first);
     LAUNCHED();
     return OMM_OK;
 }
 
 int direction(Dev &d, const DevState *state, cudaStream_t st) {
     const int64_t len = d.nnzW * d.bm * d.bn;
-    direction_kernel<<<blocks_for(len, 256 * 4), 256, 0, st>>>(len, d.G, d.Gp, d.D, state);
+    direction_kernel<double><<<blocks_for(len, 256 * 4), 256, 0, st>>>(len, d.G, d.Gp, d.D, state);
     LAUNCHED();
     return OMM_OK;
 }

@@ -68,6 +68,13 @@ struct Dev {
     double *nHS = nullptr, *nW = nullptr, *nD = nullptr, *nHW = nullptr, *nSW = nullptr, *nHD = nullptr,
            *nSD = nullptr, *nh0 = nullptr, *ns0 = nullptr;
     bool screening() const { return screen_eps2 > 0.0; }
+    // mixed form (allocated by mixed_alloc): FP32 shadows of H' and S ([nnzH][2]), W,
+    // H'W, SW, H_W, S_W, and the FP32 increments D, G, Gp, H'D, SD, X, Y, h2, s2
+    bool mixed = false;
+    float *fbuf = nullptr;
+    float *HS32 = nullptr, *W32 = nullptr, *D32 = nullptr, *G32 = nullptr, *Gp32 = nullptr, *HW32 = nullptr,
+          *SW32 = nullptr, *HD32 = nullptr, *SD32 = nullptr, *h032 = nullptr, *s032 = nullptr, *X32 = nullptr,
+          *Y32 = nullptr, *h232 = nullptr, *s232 = nullptr;
 };
 
 // which block norms to refresh (norms())
@@ -104,6 +111,23 @@ int contract(Dev &d, const double *Wl, const double *Dl, const double *HDr, cons
              double *Yo, double *h2o, double *s2o, const double *nWl, const double *nDl, const double *nHDr,
              const double *nSDr, const DevState *state, cudaStream_t st);
 int gradient(Dev &d, const DevState *state, cudaStream_t st);
+
+// Mixed form.  mixed_alloc: the FP32 arrays (about 60% of the FP64 ones).
+// mixed_shadow_HS: FP32 copies of H' and S (after set_HS).  mixed_begin: FP32
+// shadows and increments from the FP64 start (W, H'W, SW, H_W, S_W, G, Gp, D).
+// One first-phase CG step, in order: mixed_products (H'D, SD), mixed_contract
+// (X, Y, h2, s2), mixed_coeffs (quartic and line minimum), mixed_update (FP64
+// W, H'W, SW, H_W, S_W from FP32 increments, shadows, energy and stop test),
+// mixed_gradient, mixed_direction.
+int mixed_alloc(Dev &d);
+int mixed_shadow_HS(Dev &d, cudaStream_t st);
+int mixed_begin(Dev &d, const DevState *state, cudaStream_t st);
+int mixed_products(Dev &d, const DevState *state, cudaStream_t st);
+int mixed_contract(Dev &d, const DevState *state, cudaStream_t st);
+int mixed_coeffs(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
+int mixed_update(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
+int mixed_gradient(Dev &d, const DevState *state, cudaStream_t st);
+int mixed_direction(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
 int coeffs(Dev &d, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
 int nn_update(Dev &d, int64_t n, int mode, double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
 int axpy(Dev &d, const DevState *state, cudaStream_t st);

@@ -388,8 +388,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                 const int cls = (ncls == 2 && (args.pa[pr] != 0 || args.pb[pr] != 0)) ? 1 : 0;
                 const int acc = slot * ncls + cls;
                 const uint32_t tacc = tmem + (uint32_t)(acc * BN);
-                const uint64_t da = sdesc_sw128(st + args.pa[pr] * TILE_A);
-                const uint64_t db = sdesc_sw128(st + nA * TILE_A + args.pb[pr] * TILE_B);
+                const uint32_t sa = st + args.pa[pr] * TILE_A, sb = st + nA * TILE_A + args.pb[pr] * TILE_B;
+                const uint64_t da = BKT == 64 ? sdesc_sw128(sa) : sdesc_sw64(sa);
+                const uint64_t db = BKT == 64 ? sdesc_sw128(sb) : sdesc_sw64(sb);
 #pragma unroll
                 for (int kk = 0; kk < BKT / 16; ++kk) {
                     umma_bf16_pair(tacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,

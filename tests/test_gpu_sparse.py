@@ -284,3 +284,35 @@ def test_screen_eps_rejected_when_invalid(omm):
         with pytest.raises(omm.OmmError) as e:
             _setup(omm, sysm, 4.5, screen_eps=bad)
         assert e.value.status == omm.ERR_ARG
+
+
+@pytest.mark.parametrize("dims,radius,seed", [((3, 3, 2), 3.6, 2), ((4, 4, 4), 4.5, 0)])
+def test_mixed_sparse_converges_to_oracle(omm, dims, radius, seed):
+    """The mixed sparse form (FP32 increments on FP64 state, then an FP64
+    refinement re-anchored from W) reaches the FP64 oracle's localised minimum
+    within the mixed-precision bar, with both phases taking steps."""
+    import synth
+    sysm = synth.make_system(*dims, seed=seed)
+    s, (rp, col, Hv, Sv), _ = _setup(omm, sysm, radius, precision=omm.PREC_MIXED)
+    s.set_HS(Hv, Sv)
+    eta = s.diag().eta
+    E, iters, st = s.solve(sysm.W0_bsr_values(radius), tol=1e-11)
+    d = s.diag()
+    ref = O.omm_cg(sysm.dense_H(), sysm.dense_S(), sysm.W0_local(radius), tol=1e-12, eta=eta,
+                   mask=sysm.w_mask(radius), max_iter=20000)
+    assert st == omm.OK and ref.status == O.OK
+    assert abs(E - ref.E) / abs(ref.E) < 1e-8
+    assert d.iters_mixed > 0 and d.iters_refine > 0
+    W = _w_blocks_to_dense(sysm, radius, s.get_array(omm.ARRAY_W).reshape(-1, 8, 2))
+    Hs = O.shift(sysm.dense_H(), sysm.dense_S(), eta)
+    e_w = O.functional(W, Hs, sysm.dense_S()) + 2 * eta * sysm.n
+    assert abs(e_w - E) / abs(E) < 1e-10
+    s.close()
+
+
+def test_mixed_sparse_rejects_screening(omm):
+    import synth
+    sysm = synth.make_system(2, 2, 2, seed=1)
+    with pytest.raises(omm.OmmError) as e:
+        _setup(omm, sysm, 4.5, precision=omm.PREC_MIXED, screen_eps=1e-3)
+    assert e.value.status == omm.ERR_UNSUPPORTED
