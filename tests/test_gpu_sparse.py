@@ -289,8 +289,16 @@ def test_screen_eps_rejected_when_invalid(omm):
 @pytest.mark.parametrize("dims,radius,seed", [((3, 3, 2), 3.6, 2), ((4, 4, 4), 4.5, 0)])
 def test_mixed_sparse_converges_to_oracle(omm, dims, radius, seed):
     """The mixed sparse form (FP32 increments on FP64 state, then an FP64
-    refinement re-anchored from W) reaches the FP64 oracle's localised minimum
-    within the mixed-precision bar, with both phases taking steps."""
+    refinement re-anchored from W) ends at a minimum of the localised functional
+    at least as low as the FP64 oracle's, within the mixed-precision bar, with
+    both phases taking steps: its energy is at most the oracle's + 1e-8 relative,
+    its W is stationary on the pattern (the masked gradient, formed by the oracle,
+    below 1e-5 of |4 H'W|, against 0.5 at W0), and the oracle's functional at that
+    W is the reported energy.  The truncated functional has several local minima
+    (the paper's reason for the Kim functional), and a CG path in other
+    arithmetic may end in a lower one: on the 64-atom case the mixed form ends
+    1.2e-4 below the FP64 minimum, which the oracle itself keeps after 60,000
+    steps."""
     import synth
     sysm = synth.make_system(*dims, seed=seed)
     s, (rp, col, Hv, Sv), _ = _setup(omm, sysm, radius, precision=omm.PREC_MIXED)
@@ -301,12 +309,14 @@ def test_mixed_sparse_converges_to_oracle(omm, dims, radius, seed):
     ref = O.omm_cg(sysm.dense_H(), sysm.dense_S(), sysm.W0_local(radius), tol=1e-12, eta=eta,
                    mask=sysm.w_mask(radius), max_iter=20000)
     assert st == omm.OK and ref.status == O.OK
-    assert abs(E - ref.E) / abs(ref.E) < 1e-8
+    assert E <= ref.E + 1e-8 * abs(ref.E)
     assert d.iters_mixed > 0 and d.iters_refine > 0
     W = _w_blocks_to_dense(sysm, radius, s.get_array(omm.ARRAY_W).reshape(-1, 8, 2))
     Hs = O.shift(sysm.dense_H(), sysm.dense_S(), eta)
     e_w = O.functional(W, Hs, sysm.dense_S()) + 2 * eta * sysm.n
     assert abs(e_w - E) / abs(E) < 1e-10
+    G = O.gradient(W, Hs, sysm.dense_S(), sysm.w_mask(radius))
+    assert np.linalg.norm(G) < 1e-5 * np.linalg.norm(4.0 * Hs @ W)
     s.close()
 
 
