@@ -239,7 +239,8 @@ def run_omm(args):
     torch.cuda.synchronize()
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
                 orth_tol=TOL[prec]["orth_tol"], stream=stream.cuda_stream, cholesky=int(args.cholesky),
-                split_digits=args.split_digits, gemm_pair=args.gemm_pair, gemm_persistent=args.gemm_persistent)
+                split_digits=args.split_digits, gemm_pair=args.gemm_pair, gemm_persistent=args.gemm_persistent,
+                dir_digits=args.dir_digits)
     solver = omm.Solver(m, n, 8, **opts)
     tol = TOL[prec]["tol"]
 
@@ -387,15 +388,20 @@ def run_omm(args):
     roof = roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind)
     if roof is not None and prec == "mixed":
         # BF16 digit-pair products per FP64-equivalent product in the products stage:
-        # both phases multiply the split_digits digits of [H'; S] and D, so 3 pairs
-        # with two digits and 6 with three; bf16_issue_frac counts the BF16 flops the
-        # tensor cores issue against the same measured BF16 peak
-        pairs = 3 if args.split_digits == 2 else 6
+        # both phases multiply the split_digits digits of [H'; S] by D, which carries
+        # one digit (dir_digits = 1: 2 pairs with two digits, 3 with three) or
+        # split_digits digits (3 or 6 pairs); bf16_issue_frac counts the BF16 flops
+        # the tensor cores issue against the same measured BF16 peak
+        if args.dir_digits == 1:
+            pairs = args.split_digits
+        else:
+            pairs = 3 if args.split_digits == 2 else 6
         roof["bf16_pairs_per_product"] = pairs
         roof["bf16_issue_frac"] = roof["frac"] * pairs
-    if roof is not None and roof.get("kernel") in TRAFFIC and prec == "mixed" and args.split_digits == 2:
-        roof["traffic"] = TRAFFIC[roof["kernel"]]["bytes_per_launch"]
-        roof["traffic_source"] = TRAFFIC[roof["kernel"]]["source"]
+    tkey = (roof or {}).get("kernel"), args.split_digits, args.dir_digits, bool(args.gemm_pair)
+    if roof is not None and prec == "mixed" and tkey in TRAFFIC:
+        roof["traffic"] = TRAFFIC[tkey]["bytes_per_launch"]
+        roof["traffic_source"] = TRAFFIC[tkey]["source"]
 
     if rank != 0:
         solver.close()
@@ -412,7 +418,7 @@ def run_omm(args):
         "config": {"workload": workload_name(sysm) + (" cholesky-reduced" if args.cholesky else ""),
                    "precision": prec, "tol": tol, "cholesky": bool(args.cholesky),
                    "split_digits": args.split_digits, "gemm_pair": bool(args.gemm_pair),
-                   "gemm_persistent": bool(args.gemm_persistent),
+                   "gemm_persistent": bool(args.gemm_persistent), "dir_digits": args.dir_digits,
                    "refine": "exact-digit tensor cores" if prec == "mixed" else None,
                    "orth_tol": TOL[prec]["orth_tol"], "parallelism": f"replicas x{ws}",
                    "l2": "working set (H, S = 256 MiB, plus W/D/products) exceeds the 129 MB L2"},
@@ -471,11 +477,9 @@ STAGES = ["products", "contract", "linesearch", "update", "gradient", "direction
 
 
 # DRAM bytes per launch of the dominant kernel, from one ncu capture of the current
-# kernel on this workload (a first-phase products launch of the two-digit split
-# GEMM); replaced whenever the kernel changes and is captured again.
-TRAFFIC = {"products": {"bytes_per_launch": 167.2e6 + 40.3e6,
-                        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one first-phase "
-                                  "products launch of the split GEMM, m=4096, n=1024"}}
+# kernel on this workload, keyed by (stage, split_digits, dir_digits, CTA pairs);
+# an entry is removed whenever its kernel changes, and added when it is captured again.
+TRAFFIC = {}
 
 
 def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
@@ -676,7 +680,7 @@ def run_profile(args):
     opts = dict(precision=omm.PREC_MIXED if prec == "mixed" else omm.PREC_FP64,
                 orth_tol=TOL[prec]["orth_tol"], stream=torch.cuda.current_stream().cuda_stream,
                 cholesky=int(args.cholesky), split_digits=args.split_digits, gemm_pair=args.gemm_pair,
-                gemm_persistent=args.gemm_persistent)
+                gemm_persistent=args.gemm_persistent, dir_digits=args.dir_digits)
     if args.max_iter > 0:
         opts["max_iter"] = args.max_iter
     solver = omm.Solver(sysm.m, sysm.n, 8, **opts)
@@ -808,7 +812,7 @@ def run_c4(args, quiet=False):
     dev = lambda a: torch.from_numpy(np.asfortranarray(a)).to("cuda")
     data = [(dev(s.dense_H()), dev(s.dense_S()), dev(s.W0_dense())) for s in systems]
     solvers = [omm.Solver(s.m, s.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6, graphs=args.graphs,
-                          gemm_pair=args.gemm_pair) for s in systems]
+                          gemm_pair=args.gemm_pair, dir_digits=args.dir_digits) for s in systems]
 
     def set_all():
         for sv, (H, S, _) in zip(solvers, data):
@@ -1021,6 +1025,9 @@ def main():
                     help="mixed form: BF16 digits per operand in the first phase (3 pairs or 6)")
     ap.add_argument("--gemm-pair", type=int, default=1, choices=[0, 1],
                     help="mixed form: split products on CTA pairs (cta_group::2) or one CTA per tile")
+    ap.add_argument("--dir-digits", type=int, default=1, choices=[0, 1],
+                    help="mixed form: BF16 digits kept of each search direction (1: the H'D, SD products "
+                         "take two digit pairs; 0: two digits, three pairs)")
     ap.add_argument("--gemm-persistent", type=int, default=0, choices=[0, 1],
                     help="mixed form: split products as persistent tile-list launches")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],

@@ -156,6 +156,19 @@ typedef struct {
                               every 152nd tile; the next tile's operands load while the last
                               one's results are written); 0 (default): one CTA (or pair) per
                               tile.  The results are the same bits either way */
+    int32_t dir_digits;    /* mixed form: BF16 digits of the search direction D.  1
+                              (default): the line search and the update run along D
+                              rounded to one BF16 digit (8 significant bits), so the split
+                              products H'D and SD take one digit of D exactly (2 digit
+                              pairs per product in place of 3, or 3 in place of 6 with
+                              split_digits = 3) and the D^T rows of the contraction one
+                              digit plane; the slope <G, D> of the quartic is taken of the
+                              rounded D, and the CG recurrence (beta, the restart test, the
+                              next direction) keeps the unrounded direction in a separate
+                              FP32 array (4 m n bytes more).  The state W, H'W, SW, H_W, S_W
+                              stays consistent to the split products' accuracy and the
+                              converged result is held to the same bars.  0: D keeps
+                              split_digits digits */
 } omm_options;
 
 enum {

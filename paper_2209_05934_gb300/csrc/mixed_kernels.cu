@@ -492,36 +492,75 @@ __global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__
     state->gD = restart ? -gg : -gg + beta * tot[2];   // <G, D_new>
 }
 
-// D = -Z + beta D (D = -Z on a restart), Z = P G (Zg) or G; Gp <- G
-__global__ void mx_direction_kernel(int m, int n, const float *__restrict__ G, const float *__restrict__ Zg,
-                                    float *Gp, float *D, const DevState *state, DigitOut dd) {
+// Df = -Z + beta Df (Df = -Z on a restart), Z = P G (Zg) or G; Gp <- G.  Df is
+// the direction of the CG recurrence.  ROUND1: the line search runs along D, Df
+// rounded to one BF16 digit (its digit planes past the first are zero), while
+// the recurrence keeps Df unrounded; the slope <G, D> of the rounded direction
+// replaces the one the dots kernel took of Df (state->gD, c1 / 2 of the
+// quartic).  Without ROUND1, D and Df are the same array.  The reduction needs
+// gridDim.x <= kRedBlocksMax.
+template <bool ROUND1>
+__device__ __forceinline__ void direction_slope(float gd, double *partials, unsigned int *counter,
+                                                DevState *state) {
+    if (!ROUND1) return;
+    __shared__ double red[NT / 32];
+    const float f[1] = {gd};
+    double v[1];
+    to_f64<1>(f, v);
+    block_sum<1>(v, red, true);
+    double tot[1];
+    if (!publish_and_collect<1>(v, partials, counter, tot, red)) return;
+    if (threadIdx.x == 0) state->gD = tot[0];
+}
+
+template <bool ROUND1>
+__global__ void __launch_bounds__(NT) mx_direction_kernel(int m, int64_t mn, const float *__restrict__ G,
+                                                           const float *__restrict__ Zg, float *Gp, float *Df,
+                                                           float *D, DevState *state, DigitOut dd,
+                                                           double *partials, unsigned int *counter) {
     if (*((volatile const int *)&state->done)) return;
     const float beta = state->beta_f;
     const bool restart = state->restart != 0;
-    for (int j = blockIdx.y; j < n; j += gridDim.y)
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-            const int64_t o = (int64_t)j * m + i;
-            const float g = G[o], z = Zg != nullptr ? Zg[o] : g;
-            const float d = restart ? -z : fmaf(beta, D[o], -z);
-            D[o] = d;
-            Gp[o] = g;
-            if (dd.ptr != nullptr) put3f(dd, (int64_t)j * dd.ld + i, d);
+    float gd = 0.f;
+    for (int64_t o = (int64_t)blockIdx.x * NT + threadIdx.x; o < mn; o += (int64_t)gridDim.x * NT) {
+        const float g = G[o], z = Zg != nullptr ? Zg[o] : g;
+        const float d = restart ? -z : fmaf(beta, Df[o], -z);
+        Df[o] = d;
+        Gp[o] = g;
+        const int64_t j = o / m, i = o - j * m;
+        if (ROUND1) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(d);
+            const float r = __bfloat162float(b);
+            gd = fmaf(g, r, gd);
+            D[o] = r;
+            if (dd.ptr != nullptr) {
+                __nv_bfloat16 *p = (__nv_bfloat16 *)dd.ptr;
+                const int64_t q = j * dd.ld + i;
+                p[q] = b;
+                for (int t = 1; t < dd.nd; ++t) p[t * dd.plane + q] = __float2bfloat16_rn(0.f);
+            }
+        } else if (dd.ptr != nullptr) {
+            put3f(dd, j * dd.ld + i, d);
         }
+    }
+    direction_slope<ROUND1>(gd, partials, counter, state);
 }
 
 // four consecutive rows of one column per thread (m % 4 == 0, 16-byte aligned arrays)
-template <bool PRE>
+template <bool PRE, bool ROUND1>
 __global__ void __launch_bounds__(NT) mx_direction4_kernel(int m, int64_t mn, const float4 *__restrict__ G,
-                                                            const float4 *__restrict__ Zg, float4 *Gp, float4 *D,
-                                                            const DevState *state, DigitOut dd) {
+                                                            const float4 *__restrict__ Zg, float4 *Gp, float4 *Df,
+                                                            float4 *D, DevState *state, DigitOut dd,
+                                                            double *partials, unsigned int *counter) {
     if (*((volatile const int *)&state->done)) return;
     const float beta = state->beta_f;
     const bool restart = state->restart != 0;
     const int64_t n4 = mn / 4;
+    float gd = 0.f;
     for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n4; k += (int64_t)gridDim.x * NT) {
         const float4 g = G[k];
         const float4 z = PRE ? Zg[k] : g;
-        float4 d = D[k];
+        float4 d = Df[k];
         if (restart) {
             d = make_float4(-z.x, -z.y, -z.z, -z.w);
         } else {
@@ -530,13 +569,29 @@ __global__ void __launch_bounds__(NT) mx_direction4_kernel(int m, int64_t mn, co
             d.z = fmaf(beta, d.z, -z.z);
             d.w = fmaf(beta, d.w, -z.w);
         }
-        D[k] = d;
+        Df[k] = d;
         Gp[k] = g;
-        if (dd.ptr != nullptr) {
-            const int64_t o = 4 * k, j = o / m, i = o - j * m;
+        const int64_t o = 4 * k, j = o / m, i = o - j * m;
+        if (ROUND1) {
+            const __nv_bfloat162 b01 = __floats2bfloat162_rn(d.x, d.y), b23 = __floats2bfloat162_rn(d.z, d.w);
+            const float2 f01 = __bfloat1622float2(b01), f23 = __bfloat1622float2(b23);
+            const float4 r = make_float4(f01.x, f01.y, f23.x, f23.y);
+            gd = fmaf(g.x, r.x, fmaf(g.y, r.y, fmaf(g.z, r.z, fmaf(g.w, r.w, gd))));
+            D[k] = r;
+            if (dd.ptr != nullptr) {
+                __nv_bfloat16 *p = (__nv_bfloat16 *)dd.ptr;
+                uint2 u;
+                u.x = *reinterpret_cast<const uint32_t *>(&b01);
+                u.y = *reinterpret_cast<const uint32_t *>(&b23);
+                *reinterpret_cast<uint2 *>(p + j * dd.ld + i) = u;
+                for (int t = 1; t < dd.nd; ++t)
+                    *reinterpret_cast<uint2 *>(p + t * dd.plane + j * dd.ld + i) = make_uint2(0u, 0u);
+            }
+        } else if (dd.ptr != nullptr) {
             put3f4(dd, j * dd.ld + i, d);
         }
     }
+    direction_slope<ROUND1>(gd, partials, counter, state);
 }
 
 // Digits of four consecutive rows of one column per thread (m % 4 == 0)
@@ -627,28 +682,38 @@ int mx_dots_beta(int64_t mn, const float *G, const float *Zg, const float *Gp, c
     return OMM_OK;
 }
 
-int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *D, const DevState *state,
-                 DigitOut dd, cudaStream_t st) {
-    const bool aligned = ((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)D) | ((uintptr_t)Zg)) & 15u) == 0 &&
-                         (dd.ptr == nullptr || ((((uintptr_t)dd.ptr) & 7u) == 0 && dd.ld % 4 == 0 && dd.plane % 4 == 0));
+int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *Df, float *D,
+                 DevState *state, DigitOut dd, bool round1, double *scratch, unsigned int *counter, cudaStream_t st) {
+    if (round1 && (scratch == nullptr || counter == nullptr || D == nullptr || D == Df)) return OMM_ERR_ARG;
+    if (!round1) D = Df;
+    const int64_t mn = m * n;
+    const bool aligned =
+        ((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)Df) | ((uintptr_t)D) | ((uintptr_t)Zg)) & 15u) == 0 &&
+        (dd.ptr == nullptr || ((((uintptr_t)dd.ptr) & 7u) == 0 && dd.ld % 4 == 0 && dd.plane % 4 == 0));
+    // the rounding form sums <G, D> over its blocks: at most kRedBlocksMax of them
+    const int64_t cap = round1 ? kRedBlocksMax : 152 * 8;
     if (m % 4 == 0 && aligned) {
-        int64_t nb = ceil_div(m * n / 4, (int64_t)NT * 4);
-        if (nb > 152 * 8) nb = 152 * 8;
+        int64_t nb = ceil_div(mn / 4, (int64_t)NT * 4);
+        if (nb > cap) nb = cap;
         const unsigned grid = (unsigned)(nb < 1 ? 1 : nb);
         const float4 *G4 = reinterpret_cast<const float4 *>(G);
-        if (Zg != nullptr)
-            mx_direction4_kernel<true><<<grid, NT, 0, st>>>((int)m, m * n, G4, reinterpret_cast<const float4 *>(Zg),
-                                                             reinterpret_cast<float4 *>(Gp),
-                                                             reinterpret_cast<float4 *>(D), state, dd);
-        else
-            mx_direction4_kernel<false><<<grid, NT, 0, st>>>((int)m, m * n, G4, G4, reinterpret_cast<float4 *>(Gp),
-                                                              reinterpret_cast<float4 *>(D), state, dd);
+        const float4 *Z4 = Zg != nullptr ? reinterpret_cast<const float4 *>(Zg) : G4;
+        float4 *Gp4 = reinterpret_cast<float4 *>(Gp), *Df4 = reinterpret_cast<float4 *>(Df),
+               *D4 = reinterpret_cast<float4 *>(D);
+        auto kern = Zg != nullptr ? (round1 ? mx_direction4_kernel<true, true> : mx_direction4_kernel<true, false>)
+                                  : (round1 ? mx_direction4_kernel<false, true> : mx_direction4_kernel<false, false>);
+        kern<<<grid, NT, 0, st>>>((int)m, mn, G4, Z4, Gp4, Df4, D4, state, dd, scratch, counter);
         count_launch();
         OMM_CUDA_TRY(cudaGetLastError());
         return OMM_OK;
     }
-    dim3 grid((unsigned)ceil_div(m, NT), (unsigned)(n < 1024 ? n : 1024));
-    mx_direction_kernel<<<grid, NT, 0, st>>>((int)m, (int)n, G, Zg, Gp, D, state, dd);
+    int64_t nb = ceil_div(mn, (int64_t)NT * 4);
+    if (nb > cap) nb = cap;
+    const unsigned grid = (unsigned)(nb < 1 ? 1 : nb);
+    if (round1)
+        mx_direction_kernel<true><<<grid, NT, 0, st>>>((int)m, mn, G, Zg, Gp, Df, D, state, dd, scratch, counter);
+    else
+        mx_direction_kernel<false><<<grid, NT, 0, st>>>((int)m, mn, G, Zg, Gp, Df, D, state, dd, scratch, counter);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

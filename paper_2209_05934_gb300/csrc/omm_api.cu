@@ -46,6 +46,7 @@ struct MixedBufs {
     // the B operands again with 128-row boxes: half of a 256-wide tile per CTA of a pair
     CUtensorMap mapHDSD_H, mapHSW_H, mapG_H;
     float *HDSD32 = nullptr, *Z32 = nullptr, *G32 = nullptr, *Gp32 = nullptr, *D32 = nullptr;
+    float *Df32 = nullptr;   // unrounded CG direction (dir_digits = 1; D32 is its one-digit rounding)
     __nv_bfloat16 *Pd = nullptr, *Gd = nullptr;
     CUtensorMap mapP_A, mapG_B;
     float *PG32 = nullptr;
@@ -180,6 +181,7 @@ void free_handle(omm_handle *h) {
     cudaFree(h->mx.G32);
     cudaFree(h->mx.Gp32);
     cudaFree(h->mx.D32);
+    cudaFree(h->mx.Df32);
     cudaFree(h->ex.HSx);
     cudaFree(h->ex.Wx);
     cudaFree(h->ex.HWSWx);
@@ -393,6 +395,7 @@ int mixed_alloc(omm_handle *h) {
     TRY(dalloc(&x.G32, (size_t)(m * n)));
     TRY(dalloc(&x.Gp32, (size_t)(m * n)));
     TRY(dalloc(&x.D32, (size_t)(m * n)));
+    if (h->opt.dir_digits == 1) TRY(dalloc(&x.Df32, (size_t)(m * n)));
     TRY(omm::tc::make_digit_map(&x.mapHS_A, x.HSd, m, 2 * m, x.ldm, 2 * m * x.ldm, kDig, 128, kBK));
     TRY(omm::tc::make_digit_map(&x.mapWD_A, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, 128, kBK));
     TRY(omm::tc::make_digit_map(&x.mapWD_B, x.WDd, m, 2 * n, x.ldm, 2 * n * x.ldm, kDig, kBN, kBK));
@@ -467,6 +470,10 @@ SplitCall products_call(omm_handle *h, int b_row0, double *C, float *C32, int64_
     a.dplane = 2 * n * x.ldm;
     a.dout_step = dout_step * x.ldm;
     a.ndig = h->cur_dig;
+    if (b_row0 == (int)n && h->opt.dir_digits == 1) {
+        // one BF16 digit of D: the pairs (p, 1) of A's digits with it, smallest first
+        omm::tc::pairs_one_b(h->cur_dig, a);
+    }
     c.mA = &x.mapHS_A;
     c.mB = &x.mapWD_B;
     c.mBh = &x.mapWD_A;
@@ -485,6 +492,7 @@ SplitCall contract_call(omm_handle *h) {
     MixedBufs &x = h->mx;
     SplitCall c;
     c.a = tc_args(h, (int)(2 * n), (int)(2 * n), (int)m);
+    if (h->opt.dir_digits == 1) c.a.a_split_row = (int)n;   // the rows of D^T carry one digit
     c.a.C32 = x.Z32;
     c.a.ldc = 2 * n;
     c.mA = &x.mapWD_A;
@@ -737,8 +745,13 @@ int mixed_direction(omm_handle *h, int first) {
         Zg = x.PG32;
     }
     StageTimer t(h, OMM_STAGE_DIRECTION);
-    TRY(omm::mx_dots_beta(m * n, x.G32, Zg, x.Gp32, x.D32, scr(h, 2), ctr(h, 2), h->dstate, first, h->stream));
-    return omm::mx_direction(m, n, x.G32, Zg, x.Gp32, x.D32, h->dstate, dig_D(h), h->stream);
+    // with one-digit directions the recurrence (beta, the restart test, the next
+    // direction) runs on the unrounded Df32 and the line search along D32
+    const bool round1 = h->opt.dir_digits == 1;
+    float *Df = round1 ? x.Df32 : x.D32;
+    TRY(omm::mx_dots_beta(m * n, x.G32, Zg, x.Gp32, Df, scr(h, 2), ctr(h, 2), h->dstate, first, h->stream));
+    return omm::mx_direction(m, n, x.G32, Zg, x.Gp32, Df, x.D32, h->dstate, dig_D(h), round1, scr(h, 2), ctr(h, 2),
+                             h->stream);
 }
 
 // Start of the split-precision phase: H'W, SW, H_W, S_W, energy, G, D from W.
@@ -1132,6 +1145,7 @@ void omm_default_options(omm_options *opt) {
     opt->screen_eps = 0.0;
     opt->gemm_pair = 1;
     opt->gemm_persistent = 0;
+    opt->dir_digits = 1;
 }
 
 const char *omm_status_str(int status) {
@@ -1180,7 +1194,8 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         h->opt.split_digits > 3 || h->opt.n_occupied < 0 || h->opt.n_occupied > n ||
         (h->opt.n_occupied > 0 && h->opt.n_occupied < n && h->opt.eta_auto) ||
         (h->opt.precon != 0 && !(h->opt.tau_T > 0.0 && isfinite(h->opt.tau_T))) ||
-        !(h->opt.screen_eps >= 0.0 && isfinite(h->opt.screen_eps))) {
+        !(h->opt.screen_eps >= 0.0 && isfinite(h->opt.screen_eps)) || h->opt.dir_digits < 0 ||
+        h->opt.dir_digits > 1) {
         delete h;
         return OMM_ERR_ARG;
     }
@@ -1669,6 +1684,7 @@ struct GroupList {
     omm::tc::TileProblem *probs = nullptr;
     omm::tc::TileRef *tiles = nullptr;
     int ntiles = 0;
+    int nA = 0, nB = 0;   // digit planes of every problem's operands
     void release() {
         cudaFree(probs);
         cudaFree(tiles);
@@ -1695,7 +1711,10 @@ int build_group_list(omm_handle **hs, int count, int stage, int mode, GroupList 
         TRY(tile_problem(c, mode, probs[i]));
         nb[i] = c.nbatch;
         order[i] = i;
+        if (i > 0 && (c.a.nA != probs[0].a.nA || c.a.nB != probs[0].a.nB)) return OMM_ERR_UNSUPPORTED;
     }
+    L.nA = probs[0].a.nA;
+    L.nB = probs[0].a.nB;
     // longest tiles first: K loop times tile width
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return (int64_t)probs[a].a.K * probs[a].bn > (int64_t)probs[b].a.K * probs[b].bn;
@@ -1711,8 +1730,8 @@ int build_group_list(omm_handle **hs, int count, int stage, int mode, GroupList 
 }
 
 int run_group_list(const GroupList &L, int mode, omm_handle *h0, cudaStream_t st) {
-    return omm::tc::gemm_list(L.probs, L.tiles, L.ntiles, mode, list_ctas(mode, L.ntiles), h0->opt.split_digits,
-                              h0->opt.split_digits, st);
+    (void)h0;
+    return omm::tc::gemm_list(L.probs, L.tiles, L.ntiles, mode, list_ctas(mode, L.ntiles), L.nA, L.nB, st);
 }
 
 // Tile modes chosen by the autotuner per group signature (the systems' (m, n) in
@@ -1768,9 +1787,10 @@ int omm_batch_solve_grouped(omm_handle **handles, int32_t count, const double *c
             if (handles[j] == h) return OMM_ERR_ARG;
         if (h->sparse || h->opt.precision != OMM_PREC_MIXED || h->opt.split_digits != 2 || h->opt.cholesky ||
             h->opt.precon != 0 || h->profiling || h->stream == nullptr || h->stream == cudaStreamLegacy ||
-            h->stream == cudaStreamPerThread) {
+            h->stream == cudaStreamPerThread || h->opt.dir_digits != handles[0]->opt.dir_digits) {
             omm::set_error("omm_batch_solve_grouped: handle %d is not a dense mixed-precision handle with two "
-                           "split digits, no Cholesky or preconditioning, profiling off and its own stream", i);
+                           "split digits, no Cholesky or preconditioning, profiling off, its own stream and "
+                           "the first handle's dir_digits", i);
             return OMM_ERR_UNSUPPORTED;
         }
         for (int32_t j = 0; j < i; ++j)

@@ -137,8 +137,12 @@ int mx_nn_update(int n, double *h0, double *s0, int64_t ldh, const float *Z, int
 // Zg: the preconditioned gradient P G, or nullptr (Z = G)
 int mx_dots_beta(int64_t mn, const float *G, const float *Zg, const float *Gp, const float *D, double *scratch,
                  unsigned int *counter, DevState *state, int first, cudaStream_t st);
-int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *D, const DevState *state,
-                 DigitOut dd, cudaStream_t st);
+// Df: the CG recurrence's direction, updated in place.  round1: D receives Df
+// rounded to one BF16 digit (the search direction; its digits to dd) and
+// state->gD = <G, D> (summed over the kernel's blocks in scratch / counter);
+// otherwise D is ignored and Df is the search direction.
+int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *Df, float *D,
+                 DevState *state, DigitOut dd, bool round1, double *scratch, unsigned int *counter, cudaStream_t st);
 // digits of an FP32 m x n column-major array: column j -> row j of the planes
 int mx_digits(int64_t m, int64_t n, const float *A, const DevState *state, DigitOut dd, cudaStream_t st);
 int mx_round(int64_t count, const double *src, float *dst, const DevState *state, cudaStream_t st);

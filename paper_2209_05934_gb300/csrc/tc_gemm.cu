@@ -313,6 +313,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     constexpr int TILE_A = BM * BKT * 2;
     constexpr int TILE_B = BNH * BKT * 2;
     const int stage_bytes = nA * TILE_A + nB * TILE_B;
+    // A planes this pair tile reads: one where the whole tile lies in A's one-digit rows
+    const int nA_t = (args.a_split_row > 0 && (int)blockIdx.y * (2 * BM) >= args.a_split_row) ? 1 : nA;
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -359,14 +361,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             if (!mbar_wait(&empty_bar[s], ph ^ 1u, deadline, &abort_flag, args.err)) break;
             uint8_t *st = smem + s * stage_bytes;
             if (rank == 0) {
-                mbar_arrive_expect_tx(&full_bar[s], (uint32_t)(2 * stage_bytes));
-                for (int p = 0; p < nA; ++p)
+                mbar_arrive_expect_tx(&full_bar[s], (uint32_t)(2 * (nA_t * TILE_A + nB * TILE_B)));
+                for (int p = 0; p < nA_t; ++p)
                     tma_load_3d(st + p * TILE_A, &mapA, kb * BKT, a_row, p, &full_bar[s]);
                 for (int q = 0; q < nB; ++q)
                     tma_load_3d(st + nA * TILE_A + q * TILE_B, &mapB, kb * BKT, b_row, q, &full_bar[s]);
             } else {
                 const uint32_t fb = mapa_shared(smem_u32(&full_bar[s]), 0u);
-                for (int p = 0; p < nA; ++p)
+                for (int p = 0; p < nA_t; ++p)
                     tma_load_3d_pair(st + p * TILE_A, &mapA, kb * BKT, a_row, p, fb);
                 for (int q = 0; q < nB; ++q)
                     tma_load_3d_pair(st + nA * TILE_A + q * TILE_B, &mapB, kb * BKT, b_row, q, fb);
@@ -385,6 +387,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             const uint32_t st = smem_u32(smem + s * stage_bytes);
             const int slot = (kb * kacc) / nkb;
             for (int pr = 0; pr < args.npairs; ++pr) {
+                if (args.pa[pr] >= nA_t) continue;   // a zero plane of A: the pair adds nothing
                 const int cls = (ncls == 2 && (args.pa[pr] != 0 || args.pb[pr] != 0)) ? 1 : 0;
                 const int acc = slot * ncls + cls;
                 const uint32_t tacc = tmem + (uint32_t)(acc * BN);
@@ -869,6 +872,7 @@ int gemm(const CUtensorMap &mapA, const CUtensorMap &mapB, const TcArgs &a, int 
     // CTA pairs: 256 x 256 tiles with the B tile split between the two SMs; needs the
     // 64-wide K blocks and a B map whose box is 128 rows
     if (mapB_half != nullptr && a.bk == 64 && bn == 256) {
+        if (a.nA + a.nB <= 3) return launch_tc_pair<4, 64>(mapA, *mapB_half, a, nbatch, st);   // 4 x 48 KB
         if (a.nA + a.nB <= 4) return launch_tc_pair<3, 64>(mapA, *mapB_half, a, nbatch, st);   // 3 x 64 KB
         return launch_tc_pair<2, 64>(mapA, *mapB_half, a, nbatch, st);                         // 2 x 96 KB
     }
@@ -921,6 +925,19 @@ void pairs_for_digits(int ndig, TcArgs &a) {
     a.npairs = k;
     a.nA = ndig;
     a.nB = ndig;
+}
+
+void pairs_one_b(int ndig, TcArgs &a) {
+    // B carries one digit: pairs (p, 1), p = ndig .. 1 (1-based), smallest terms first
+    int k = 0;
+    for (int p = ndig; p >= 1; --p) {
+        a.pa[k] = (uint8_t)(p - 1);
+        a.pb[k] = 0;
+        ++k;
+    }
+    a.npairs = k;
+    a.nA = ndig;
+    a.nB = 1;
 }
 
 }  // namespace tc

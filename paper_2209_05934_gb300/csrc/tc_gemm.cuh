@@ -36,6 +36,9 @@ struct TcArgs {
     int kacc;                    // set by the launcher: K-range accumulators in tensor memory
     int ncls;                    // set by the launcher: 2 = leading digit pair kept apart
     int bk;                      // K-block width of the tensor maps: 64 (128-byte swizzle) or 32
+    int a_split_row;             // > 0: the A rows at and past this output row carry one digit (their
+                                 // further planes are zero), so CTA-pair tiles that start there load
+                                 // A's first plane only and skip the pairs of the others; 0: none
 };
 
 // One problem of a grouped (tile-list) launch: its tensor maps (device copies)
@@ -80,6 +83,8 @@ int pack_cm(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_
 int pack_t(int64_t rows, int64_t cols, const double *src, int64_t ld_src, __nv_bfloat16 *dst, int64_t ldd,
            int64_t plane, int ndig, const DevState *state, cudaStream_t st);
 void pairs_for_digits(int ndig, TcArgs &a);
+// A with ndig digits, B with one: the pairs (p, 1), p = ndig .. 1, and nB = 1
+void pairs_one_b(int ndig, TcArgs &a);
 
 }  // namespace tc
 }  // namespace omm

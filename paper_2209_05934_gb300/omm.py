@@ -33,7 +33,7 @@ class Options(C.Structure):
                 ("exact_digits", C.c_int32), ("split_digits", C.c_int32), ("graphs", C.c_int32),
                 ("n_occupied", C.c_int32), ("precon", C.c_int32), ("tau_T", C.c_double),
                 ("screen_eps", C.c_double), ("gemm_pair", C.c_int32),
-                ("gemm_persistent", C.c_int32)]
+                ("gemm_persistent", C.c_int32), ("dir_digits", C.c_int32)]
 
 
 class Pattern(C.Structure):

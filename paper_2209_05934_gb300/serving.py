@@ -74,7 +74,7 @@ def footprint_bytes(m: int, n: int, precision: int, exact_digits: int = 7) -> in
         ldm = (m + 7) // 8 * 8
         ld2n = (2 * n + 7) // 8 * 8
         f64 += 2 * 3 * (2 * m * ldm + 4 * n * ldm + m * ld2n + n * ld2n)          # split digits
-        f64 += 4 * (2 * m * n + 4 * n * n + 3 * m * n)                             # FP32 increments
+        f64 += 4 * (2 * m * n + 4 * n * n + 4 * m * n)                             # FP32 increments
         f64 += 2 * exact_digits * (2 * m * ldm + 3 * n * ldm + m * ld2n + n * ld2n)  # exact digits
     return int(f64)
 

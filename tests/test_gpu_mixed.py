@@ -24,14 +24,18 @@ def dev(a):
     return torch.from_numpy(np.asfortranarray(a)).to("cuda")
 
 
-@pytest.mark.parametrize("dims,refine", [((4, 4, 4), "exact"), ((3, 4, 5), "exact"), ((5, 5, 5), "exact"),
-                                         ((4, 4, 4), "fp64"), ((3, 4, 5), "fp64")])
-def test_mixed_solve_matches_oracle(omm, dims, refine):
+@pytest.mark.parametrize("dims,refine,dir_digits", [((4, 4, 4), "exact", 1), ((3, 4, 5), "exact", 1),
+                                                    ((5, 5, 5), "exact", 1), ((4, 4, 4), "fp64", 1),
+                                                    ((3, 4, 5), "fp64", 1), ((4, 4, 4), "exact", 0),
+                                                    ((3, 4, 5), "exact", 0)])
+def test_mixed_solve_matches_oracle(omm, dims, refine, dir_digits):
+    """dir_digits 1 (default): search directions rounded to one BF16 digit, the
+    H'D, SD products on two digit pairs; 0: directions keep two digits."""
     import synth
     sysm = synth.make_system(*dims, seed=0)
     H, S = sysm.dense_H(), sysm.dense_S()
     W0 = np.asfortranarray(sysm.W0_dense())
-    s = omm.Solver(sysm.m, sysm.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6,
+    s = omm.Solver(sysm.m, sysm.n, 8, precision=omm.PREC_MIXED, orth_tol=1e-6, dir_digits=dir_digits,
                    refine=omm.REFINE_EXACT if refine == "exact" else omm.REFINE_FP64)
     s.set_HS(dev(H), dev(S))
     W = torch.zeros((sysm.n, sysm.m), dtype=torch.float64, device="cuda").T

@@ -2,7 +2,9 @@
 against the one-CTA tiles and the FP64 oracle: the same solves with
 gemm_pair = 1 and 0 take the same steps to the same energy, on sizes that
 fill the pair tiles and on ragged ones that leave the second CTA of a pair
-partly or wholly outside the matrix."""
+partly or wholly outside the matrix.  With n = 150 and n = 256 the contraction
+[W D]^T [H'D SD] has pair tiles wholly in the rows of D^T, whose one-digit A
+operand those tiles load and multiply as one plane."""
 import numpy as np
 import pytest
 
@@ -37,7 +39,7 @@ def _solve(omm, H, S, W0, m, n, pair, max_iter=10000):
     return E, iters, st, d, W.cpu().numpy()
 
 
-@pytest.mark.parametrize("case", ["c1", "ragged_600_150", "ragged_136_34"])
+@pytest.mark.parametrize("case", ["c1", "ragged_600_150", "ragged_136_34", "dense_1024_256"])
 def test_pair_tiles_match_single_tiles_and_oracle(omm, case):
     import synth
     if case == "c1":
