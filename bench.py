@@ -78,6 +78,11 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.file, stderr=subprocess.DEVNULL)
+            # the timed region starts once nvidia-smi has taken its first sample: its
+            # start-up (NVML initialisation) competes with the host driving the GPU
+            t_end = time.perf_counter() + 1.0
+            while time.perf_counter() < t_end and self.proc.poll() is None and os.path.getsize(self.file.name) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -455,7 +460,7 @@ def run_omm(args):
                              "fp64_peak_tflops": r3["fp64_peak_tflops"], "nnzb": r3["config"]["nnzb"],
                              "note": "20 CG steps from W0 (the converged solve is bench.py --config c3)"}
         a4 = copy.copy(args)
-        a4.steps, a4.warmup, a4.tile_mode = 1, 1, -1
+        a4.steps, a4.warmup, a4.tile_mode = 2, 2, -1
         r4 = run_c4(a4, quiet=True)
         ex["c4"] = {k: r4[k] for k in ("value", "unit", "ms_per_step", "tuning", "streams", "one_by_one",
                                        "results_equal_alone", "all_ok", "iters")}
@@ -479,7 +484,10 @@ STAGES = ["products", "contract", "linesearch", "update", "gradient", "direction
 # DRAM bytes per launch of the dominant kernel, from one ncu capture of the current
 # kernel on this workload, keyed by (stage, split_digits, dir_digits, CTA pairs);
 # an entry is removed whenever its kernel changes, and added when it is captured again.
-TRAFFIC = {}
+TRAFFIC = {("products", 2, 1, True): {
+    "bytes_per_launch": 150.83392e6 + 39.697152e6,
+    "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one first-phase products launch "
+              "(tc_gemm_pair_kernel, two digits of [H'; S], one digit of D), m=4096, n=1024"}}
 
 
 def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
@@ -1000,9 +1008,56 @@ def run_c5(args, quiet=False):
         for name in ("mixed", "fp64"):
             del cmp[name]["E_last"]
         out["mixed_vs_fp64"] = cmp
+    if args.c5_sparse_steps > 0:
+        out["sparse_sequence"] = run_c5_sparse(args)
     if not quiet:
         print(json.dumps(out), flush=True)
     return out
+
+
+def run_c5_sparse(args):
+    """One SCF-like sequence of the linear-scaling workload (C3 system, m = 32768,
+    mixed form): a cold solve from W0, then c5_sparse_steps - 1 solves each after an
+    onsite update of H (every diagonal block B <- B + sym(N(0, 1e-3 eV)), drawn per
+    step), warm-started from the resident W.  Solves run back to back (one
+    sequence, no queueing); each time-to-converge is the device time of
+    omm_set_HS + omm_solve."""
+    import torch
+    from paper_2209_05934_gb300 import omm
+
+    sysm = synth.make_system(*C3["dims"], seed=C3["seed"])
+    rp, col, Hv, Sv = sysm.bsr()
+    wrp, wcol = sysm.w_pattern(C3["radius"])
+    stream = torch.cuda.Stream()
+    s = omm.SparseSolver(sysm.m, sysm.n, 8, 2, rp, col, wrp, wcol, max_iter=40000, stream=stream.cuda_stream,
+                         precision=omm.PREC_MIXED)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    Sd, W0d = dev(Sv), dev(sysm.W0_bsr_values(C3["radius"]))
+    diag_blocks = np.array([k for i in range(len(rp) - 1) for k in range(rp[i], rp[i + 1]) if col[k] == i])
+    solves = []
+    for k in range(args.c5_sparse_steps):
+        Hk = Hv.copy()
+        if k > 0:
+            g = np.random.Generator(np.random.PCG64(7000 + k))
+            nz = g.normal(0.0, 1e-3, size=(len(diag_blocks), 8, 8))
+            Hk[diag_blocks] += 0.5 * (nz + nz.transpose(0, 2, 1))
+        Hd = dev(Hk)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.set_HS(Hd, Sd)
+        E, iters, st = s.solve(W0d if k == 0 else None, tol=1e-10, raise_on_error=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d = s.diag()
+        solves.append({"step": k, "ms": e0.elapsed_time(e1), "iters": int(iters), "iters_mixed": int(d.iters_mixed),
+                       "iters_refine": int(d.iters_refine), "status": int(st), "E": E})
+    s.close()
+    warm = [r["ms"] for r in solves[1:]]
+    return {"workload": (f"C3 system (4096 atoms, m={sysm.m}, n={sysm.n}, R_C={C3['radius']} A), mixed form, "
+                         "1 cold + onsite-perturbed warm-started solves, tol 1e-10"),
+            "cold_ms": solves[0]["ms"], "warm_ms_median": float(np.median(warm)) if warm else None,
+            "all_ok": all(r["status"] == omm.OK for r in solves), "solves": solves}
 
 
 def main():
@@ -1055,6 +1110,8 @@ def main():
     ap.add_argument("--sequences", type=int, default=91,
                     help="c5: sequences served at each arrival rate (91 x 11 solves = 1001 per rate)")
     ap.add_argument("--scf-steps", type=int, default=11, help="c5: solves per sequence (1 + perturbations)")
+    ap.add_argument("--c5-sparse-steps", type=int, default=0,
+                    help="c5: also serve one linear-scaling sequence (m = 32768) of this many solves")
     ap.add_argument("--rates", type=float, nargs="+", default=[10.0, 20.0, 50.0, 100.0, 200.0, 500.0],
                     help="c5: sequence arrivals per second")
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0, help="c5: admission budget")

@@ -233,6 +233,17 @@ struct StageTimer {
     int slot = -1;
     StageTimer(omm_handle *h_, int stage_) : h(h_), stage(stage_) {
         if (!h->profiling || h->nev + 2 > omm_handle::kMaxEv) return;
+        // a CG-step stage enqueued after the solve finished (the rest of a chunk)
+        // returns at once on the device: it is neither timed nor counted, so the
+        // per-launch averages hold real launches only (profiling waits on the
+        // stream here; its stage times are device events)
+        if (stage <= OMM_STAGE_DIRECTION || stage == OMM_STAGE_PRECON) {
+            int dn = 0;
+            if (cudaMemcpyAsync(&dn, &h->dstate->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream) ==
+                    cudaSuccess &&
+                cudaStreamSynchronize(h->stream) == cudaSuccess && dn != 0)
+                return;
+        }
         slot = h->nev;
         h->nev += 2;
         for (int i = 0; i < 2; ++i)

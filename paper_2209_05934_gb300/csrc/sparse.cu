@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "fp_convert.cuh"
@@ -486,6 +487,17 @@ __global__ void __launch_bounds__(NT) gershgorin_kernel(int64_t nbr, int bm, con
     state->eta = (g >= 0.0) ? g / lo : g / hi;
 }
 
+// FP32 gathers of the mixed form (8x2 blocks, no screening) in the products and
+// gradient kernels load whole block rows and blocks as 8- and 16-byte vectors
+// (every FP32 block array is 16-byte aligned: its blocks hold 64, 16 or 4 floats)
+// instead of one scalar per element; the FMAs run in the scalar paths' order, so
+// the results are the same bits.
+template <typename T, int BM, int BN, bool SCREEN>
+struct VecGather {
+    static constexpr bool on = std::is_same<T, float>::value && BM == 8 && BN == 2 && !SCREEN;
+};
+__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
 // ---- products: HD_o = sum H'_(I,K) D_(K,J), SD_o likewise; warp per P_HW block,
 // lanes 0..15 -> H'D element (r, c), lanes 16..31 -> SD element.
 // Screening (SCREEN): the block product H'_(I,K) D_(K,J) (or S_(I,K) D_(K,J)) is
@@ -507,13 +519,30 @@ __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64
     const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
     for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; o < nnzHW; o += nwarps) {
         T acc = T(0);
-        for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
-            if (SCREEN && nHS[(int64_t)Ph[t] * 2 + which] * nB[Pw[t]] < eps2) continue;
-            const T *A = HS + ((int64_t)Ph[t] * 2 + which) * BM * BM + r * BM;
-            const T *B = D + (int64_t)Pw[t] * BM * BN + c;
-            if (active) {
+        if constexpr (VecGather<T, BM, BN, SCREEN>::on) {
+            // A row r (two vectors), the whole 8x2 D block (four), column c picked
+#pragma unroll 2
+            for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
+                const float *A = HS + ((int64_t)Ph[t] * 2 + which) * 64 + r * 8;
+                const float *B = D + (int64_t)Pw[t] * 16;
+                const float4 a0 = ld4(A), a1 = ld4(A + 4);
+                const float4 b0 = ld4(B), b1 = ld4(B + 4), b2 = ld4(B + 8), b3 = ld4(B + 12);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[8] = {c ? b0.y : b0.x, c ? b0.w : b0.z, c ? b1.y : b1.x, c ? b1.w : b1.z,
+                                     c ? b2.y : b2.x, c ? b2.w : b2.z, c ? b3.y : b3.x, c ? b3.w : b3.z};
 #pragma unroll
-                for (int k = 0; k < BM; ++k) acc = fma(A[k], B[k * BN], acc);
+                for (int k = 0; k < 8; ++k) acc = fmaf(av[k], bv[k], acc);
+            }
+        } else {
+#pragma unroll 4
+            for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
+                if (SCREEN && nHS[(int64_t)Ph[t] * 2 + which] * nB[Pw[t]] < eps2) continue;
+                const T *A = HS + ((int64_t)Ph[t] * 2 + which) * BM * BM + r * BM;
+                const T *B = D + (int64_t)Pw[t] * BM * BN + c;
+                if (active) {
+#pragma unroll
+                    for (int k = 0; k < BM; ++k) acc = fma(A[k], B[k * BN], acc);
+                }
             }
         }
         if (active) (which ? SD : HD)[o * NE + e] = acc;
@@ -555,6 +584,7 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
     for (int64_t q = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; q < nnzN; q += nwarps) {
         if (!SCREEN && Ntr != nullptr && Ntr[q] < q) {
             T acc = T(0);
+#pragma unroll 4
             for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
                 const T *l = W + (int64_t)Ca[t] * BM * BN + a4;
                 const T *rr = R4 + (int64_t)Cb[t] * BM * BN + b4;
@@ -569,7 +599,10 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
             if (quarter == 0) out4[q * 4 + a4 * 2 + b4] = acc;
             continue;
         }
+        // (16-byte vector loads measured slower here than these scalar ones: each
+        // lane needs every other element of its block rows)
         T acc = T(0);
+#pragma unroll 4
         for (int64_t t = Crp[q]; t < Crp[q + 1]; ++t) {
             if (SCREEN && nL[Ca[t]] * nR[Cb[t]] < eps2) continue;
             const T *l = L + (int64_t)Ca[t] * BM * BN + a;
@@ -619,28 +652,45 @@ __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_
     const int r = e / BN, c = e % BN;
     const int64_t ngroups = ((int64_t)gridDim.x * NT) >> 4;
     for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 4; o < nnzW; o += ngroups) {
-    T acc = T(0);
-    for (int64_t t = Grp[o]; t < Grp[o + 1]; ++t) {
-        const T *sw = SW + (int64_t)Gb[t] * BM * BN + r * BN;
-        const T *hw = HW + (int64_t)Gb[t] * BM * BN + r * BN;
-        const T *hq = h0 + (int64_t)Gq[t] * BN * BN + c;
-        const T *sq = s0 + (int64_t)Gq[t] * BN * BN + c;
-        if (SCREEN) {
-            const bool use_s = !(nSW[Gb[t]] * nh0[Gq[t]] < eps2), use_h = !(nHW[Gb[t]] * ns0[Gq[t]] < eps2);
-#pragma unroll
-            for (int k = 0; k < BN; ++k) {
-                if (use_s) acc = fma(sw[k], hq[k * BN], acc);
-                if (use_h) acc = fma(hw[k], sq[k * BN], acc);
+        T acc = T(0);
+        if constexpr (VecGather<T, BM, BN, SCREEN>::on) {
+            // row r of the SW and H'W blocks (two floats each), the whole 2x2 h0, s0 blocks
+#pragma unroll 2
+            for (int64_t t = Grp[o]; t < Grp[o + 1]; ++t) {
+                const int64_t gb = (int64_t)Gb[t] * 16 + r * 2, gq = (int64_t)Gq[t] * 4;
+                const float2 sw = __ldg(reinterpret_cast<const float2 *>(SW + gb));
+                const float2 hw = __ldg(reinterpret_cast<const float2 *>(HW + gb));
+                const float4 hq = ld4(h0 + gq), sq = ld4(s0 + gq);
+                acc = fmaf(sw.x, c ? hq.y : hq.x, acc);
+                acc = fmaf(hw.x, c ? sq.y : sq.x, acc);
+                acc = fmaf(sw.y, c ? hq.w : hq.z, acc);
+                acc = fmaf(hw.y, c ? sq.w : sq.z, acc);
             }
-            continue;
-        }
+        } else {
+#pragma unroll 4
+            for (int64_t t = Grp[o]; t < Grp[o + 1]; ++t) {
+                const T *sw = SW + (int64_t)Gb[t] * BM * BN + r * BN;
+                const T *hw = HW + (int64_t)Gb[t] * BM * BN + r * BN;
+                const T *hq = h0 + (int64_t)Gq[t] * BN * BN + c;
+                const T *sq = s0 + (int64_t)Gq[t] * BN * BN + c;
+                if constexpr (SCREEN) {
+                    const bool use_s = !(nSW[Gb[t]] * nh0[Gq[t]] < eps2),
+                               use_h = !(nHW[Gb[t]] * ns0[Gq[t]] < eps2);
 #pragma unroll
-        for (int k = 0; k < BN; ++k) {
-            acc = fma(sw[k], hq[k * BN], acc);
-            acc = fma(hw[k], sq[k * BN], acc);
+                    for (int k = 0; k < BN; ++k) {
+                        if (use_s) acc = fma(sw[k], hq[k * BN], acc);
+                        if (use_h) acc = fma(hw[k], sq[k * BN], acc);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < BN; ++k) {
+                        acc = fma(sw[k], hq[k * BN], acc);
+                        acc = fma(hw[k], sq[k * BN], acc);
+                    }
+                }
+            }
         }
-    }
-    G[o * BM * BN + e] = T(2) * (T(2) * HW[(int64_t)WtoHW[o] * BM * BN + e] - acc);
+        G[o * BM * BN + e] = T(2) * (T(2) * HW[(int64_t)WtoHW[o] * BM * BN + e] - acc);
     }
 }
 
