@@ -45,10 +45,9 @@ __device__ void block_sum(double (&v)[NV], double *red /* smem NV*8 */) {
 }
 
 // Publish this block's NV partials; returns true in the last block to finish,
-// whose thread 0 then holds the totals in `tot`.  The last block reads the
-// partials with all its threads (thread t takes blocks t, t + NT, ... in order)
-// and combines them with the same fixed tree as block_sum, so the result does
-// not depend on which block finished last.
+// whose threads then all hold the totals in `tot`.  The last block sums the
+// partials in a fixed order (warp per value, lane-strided blocks, shuffle tree),
+// so the result does not depend on which block finished last.
 template <int NV>
 __device__ bool publish_and_collect(const double (&v)[NV], double *partials, unsigned int *counter,
                                     double (&tot)[NV], double *red) {
@@ -63,18 +62,21 @@ __device__ bool publish_and_collect(const double (&v)[NV], double *partials, uns
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
-    double w[NV];
+    // warp w sums values w, w + NT/32, ...: its lanes take blocks lane, lane + 32,
+    // ... in order, then a fixed shuffle tree (one dependent chain per value on
+    // the long-latency FP64 unit, instead of a block-wide tree per value)
+    for (int q = threadIdx.x >> 5; q < NV; q += NT / 32) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x & 31; b < gridDim.x; b += 32) s += __ldcg(&partials[b * NV + q]);
 #pragma unroll
-    for (int q = 0; q < NV; ++q) w[q] = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += NT)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) w[q] += __ldcg(&partials[b * NV + q]);
-    block_sum<NV>(w, red);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) tot[q] = w[q];
-        *counter = 0u;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) red[q] = s;
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = red[q];
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();   // red is free again for the caller
     return true;
 }
 

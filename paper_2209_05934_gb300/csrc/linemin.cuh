@@ -13,10 +13,13 @@
 // evaluate the cubic at 32 interior points and keep the first sign change, so
 // the bracket shrinks 33-fold without a division -- then deflation, a stable
 // quadratic formula for the other two roots and Newton polishing, one root per
-// lane.  FP64 latency on this part is long and FP64 division is a long
-// sequence, so a single thread's Newton iteration from a poor start costs
-// microseconds in the serial tail of every CG step; the warp form takes a few
-// hundred cycles.
+// lane.  A dependent FP64 operation takes ~64 cycles on this part (FP32: ~4),
+// so the bracketing and the deflation run in FP32 on the cubic scaled to
+// t = x / R with coefficients of magnitude <= 1, and only the polishing runs in
+// FP64: Newton steps whose reciprocal of E'' is taken in FP32 (each step then
+// shrinks the error by ~1e-7, so two or three reach FP64 precision from the
+// FP32 root).  Where the scaling leaves the FP32 range the FP64 multisection
+// runs instead.
 #pragma once
 
 #include <math.h>
@@ -117,9 +120,31 @@ __device__ __forceinline__ double polish(double a, double b, double c, double d,
     return x;
 }
 
-// Warp form: all 32 lanes of one warp call it with the same c; every lane
-// gets the same status and x.
-__device__ inline int quartic_min_warp(const double *c, double *xout) {
+// FP64 Newton polish of a root of a x^3 + b x^2 + c x + d; the step's
+// reciprocal derivative is taken in FP32 where it is representable.
+__device__ __forceinline__ double polish_fast(double a, double b, double c, double d, double x) {
+    auto f = [&](double t) { return ((a * t + b) * t + c) * t + d; };
+    auto fp = [&](double t) { return (3.0 * a * t + 2.0 * b) * t + c; };
+    double fx = f(x);
+    for (int it = 0; it < 6; ++it) {
+        if (fx == 0.0) break;
+        const double dx = fp(x);
+        if (dx == 0.0) break;
+        const float rf = 1.0f / (float)dx;
+        const double step = (isfinite(rf) && rf != 0.0f) ? fx * (double)rf : fx / dx;
+        const double xn = x - step;
+        if (!isfinite(xn)) break;
+        const double fn = f(xn);
+        if (!(fabs(fn) < fabs(fx))) break;
+        x = xn;
+        fx = fn;
+        if (fabs(step) <= 1e-17 * fabs(x)) break;
+    }
+    return x;
+}
+
+// FP64 multisection (the form used where the scaled cubic leaves the FP32 range).
+__device__ inline int quartic_min_warp64(const double *c, double *xout) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     double r[3];
@@ -151,6 +176,69 @@ __device__ inline int quartic_min_warp(const double *c, double *xout) {
     nr = deflate(a, b, cc, 0.5 * (lo + hi), r);
     // one root per lane for the polishing, then everyone takes all of them
     double mine = lane < nr ? polish(a, b, cc, d, r[lane]) : 0.0;
+    for (int i = 0; i < nr; ++i) r[i] = __shfl_sync(full, mine, i);
+    return select_min(c, r, nr, xout);
+}
+
+// Warp form: all 32 lanes of one warp call it with the same c; every lane
+// gets the same status and x.
+__device__ inline int quartic_min_warp(const double *c, double *xout) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    double r[3];
+    int nr = 0;
+    bool done;
+    const int st = trivial_cases(c, r, &nr, xout, &done);
+    if (done) return st;
+    const double sg = c[4] > 0.0 ? 1.0 : -1.0;
+    const double a = sg * 4.0 * c[4], b = sg * 3.0 * c[3], cc = sg * 2.0 * c[2], d = sg * c[1];
+    // Cauchy bound R = 1 + max(|b|, |cc|, |d|) / a, kept an upper bound of the FP32 quotient
+    const float qf = (float)fmax(fabs(b), fmax(fabs(cc), fabs(d))) / (float)a;
+    if (!(qf >= 0.0f) || !isfinite(qf) || qf > 1e30f) return quartic_min_warp64(c, xout);
+    const double R = 1.0 + (double)qf * (1.0 + 1e-5);
+    // the cubic in t = x / R, scaled so that its largest coefficient is 1
+    const double A = a * R * R * R, B = b * R * R, C = cc * R, D = d;
+    const float inv = 1.0f / (float)fmax(fmax(fabs(A), fabs(B)), fmax(fabs(C), fabs(D)));
+    if (!isfinite(inv) || inv == 0.0f) return quartic_min_warp64(c, xout);
+    const float Af = (float)A * inv, Bf = (float)B * inv, Cf = (float)C * inv, Df = (float)D * inv;
+    auto g = [&](float t) { return fmaf(fmaf(fmaf(Af, t, Bf), t, Cf), t, Df); };
+    float lo = -1.0f, hi = 1.0f;   // g(-1) < 0 < g(1): every root lies inside
+    const float step = 1.0f / 33.0f;
+    for (int round = 0; round < 24; ++round) {
+        const float w = hi - lo;
+        if (!(w > 2e-7f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f)) break;
+        const float tl = fmaf(w, (float)(lane + 1) * step, lo);
+        const float gl = g(tl);
+        const unsigned nonneg = __ballot_sync(full, !(gl < 0.0f));   // first lane with g >= 0 closes the bracket
+        const int j = nonneg ? __ffs(nonneg) - 1 : 32;
+        const float tprev = __shfl_sync(full, tl, j > 0 ? j - 1 : 0);
+        const float tj = __shfl_sync(full, tl, j < 32 ? j : 31);
+        const float nlo = j > 0 ? tprev : lo, nhi = j < 32 ? tj : hi;
+        if (nlo == lo && nhi == hi) break;
+        lo = nlo;
+        hi = nhi;
+    }
+    // deflate in FP32: (t - t1)(Af t^2 + p t + q)
+    const float t1 = 0.5f * (lo + hi);
+    float tr[3] = {t1, 0.0f, 0.0f};
+    nr = 1;
+    const float p = fmaf(Af, t1, Bf), q = fmaf(p, t1, Cf);
+    const float disc = fmaf(p, p, -4.0f * Af * q);
+    if (disc >= 0.0f) {
+        const float sq = sqrtf(disc);
+        const float t = -0.5f * (p + (p >= 0.0f ? sq : -sq));
+        if (t != 0.0f) {
+            tr[nr++] = t / Af;
+            tr[nr++] = q / t;
+        } else {
+            tr[nr++] = 0.0f;
+        }
+    } else if (disc > -1e-5f * p * p) {
+        tr[nr++] = -0.5f * p / Af;   // a double root within the FP32 rounding
+    }
+    // one root per lane for the FP64 polishing, then everyone takes all of them
+    const float tmine = lane == 0 ? tr[0] : lane == 1 ? tr[1] : tr[2];
+    const double mine = lane < nr ? polish_fast(a, b, cc, d, (double)tmine * R) : 0.0;
     for (int i = 0; i < nr; ++i) r[i] = __shfl_sync(full, mine, i);
     return select_min(c, r, nr, xout);
 }

@@ -131,18 +131,21 @@ __device__ bool publish_and_collect(const double (&v)[NV], double *partials, uns
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
-    double w[NV];
+    // warp w sums values w, w + NT/32, ...: its lanes take blocks lane, lane + 32,
+    // ... in order, then a fixed shuffle tree (one dependent chain per value on
+    // the long-latency FP64 unit, instead of a block-wide tree per value)
+    for (int q = threadIdx.x >> 5; q < NV; q += NT / 32) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x & 31; b < gridDim.x; b += 32) s += __ldcg(&partials[b * NV + q]);
 #pragma unroll
-    for (int q = 0; q < NV; ++q) w[q] = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += NT)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) w[q] += __ldcg(&partials[b * NV + q]);
-    block_sum<NV>(w, red);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) tot[q] = w[q];
-        *counter = 0u;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) red[q] = s;
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = red[q];
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();   // red is free again for the caller
     return true;
 }
 
@@ -154,7 +157,8 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
                                                         const double *__restrict__ s0, int64_t ldh,
                                                         const float *__restrict__ Z, int64_t ldz,
                                                         double *partials, unsigned int *counter,
-                                                        DevState *state) {
+                                                        DevState *state, const double *__restrict__ slope,
+                                                        int nslope) {
     if (*((volatile int *)&state->done)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) state->done_upd = 1;
         return;
@@ -210,18 +214,27 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
     block_sum<NC>(v, red, true);
     double tot[NC] = {};
     if (!publish_and_collect<NC>(v, partials, counter, tot, red)) return;
+    // the slope <G, D>: the direction kernel's per-block parts (one-digit
+    // directions), else the dots kernel's value
+    double gd[1] = {0.0};
+    if (nslope > 0) {
+        for (int b = threadIdx.x; b < nslope; b += NT) gd[0] += __ldcg(&slope[b]);
+        block_sum<1>(gd, red);
+    }
     if (threadIdx.x >= 32) return;   // warp 0: the line minimum
 #pragma unroll
     for (int q = 0; q < NC; ++q) tot[q] = __shfl_sync(0xffffffffu, tot[q], 0);
+    const double gD = nslope > 0 ? __shfl_sync(0xffffffffu, gd[0], 0) : state->gD;
     double c[5];
     c[0] = state->E - state->e_shift;   // the shifted functional at x = 0
-    c[1] = 2.0 * state->gD;
+    c[1] = 2.0 * gD;
     c[2] = 2.0 * (2.0 * tot[0] - tot[1] - 2.0 * (tot[2] + tot[3]) - tot[4]);
     c[3] = 2.0 * (-2.0 * tot[5] - 2.0 * tot[6]);
     c[4] = -2.0 * tot[7];
     double x = 0.0;
     const int st = lm::quartic_min_warp(c, &x);
     if (threadIdx.x != 0) return;
+    state->gD = gD;
     for (int q = 0; q < 5; ++q) state->c[q] = c[q];
     state->x = x;
     state->x_f = (float)x;
@@ -236,7 +249,7 @@ __global__ void __launch_bounds__(NT) mx_coeffs_kernel(int n, const double *__re
 // ---------------------------------------------------------------- H_W, S_W update
 // h0 += x (X + X^T) + x^2 sym(h2), s0 likewise (FP32 increments, FP64 sums);
 // ||s0 - I||_F^2 for the orthonormality test; digits of [H_W ; S_W] columns.
-__global__ void __launch_bounds__(NT, 3) mx_nn_update_kernel(int n, double *h0, double *s0, int64_t ldh,
+__global__ void __launch_bounds__(NT, 4) mx_nn_update_kernel(int n, double *h0, double *s0, int64_t ldh,
                                                            const float *__restrict__ Z, int64_t ldz,
                                                            double *partials, unsigned int *counter,
                                                            DevState *state, DigitOut hsw) {
@@ -495,29 +508,25 @@ __global__ void __launch_bounds__(NT) mx_dots_kernel(int64_t mn, const float *__
 // Df = -Z + beta Df (Df = -Z on a restart), Z = P G (Zg) or G; Gp <- G.  Df is
 // the direction of the CG recurrence.  ROUND1: the line search runs along D, Df
 // rounded to one BF16 digit (its digit planes past the first are zero), while
-// the recurrence keeps Df unrounded; the slope <G, D> of the rounded direction
-// replaces the one the dots kernel took of Df (state->gD, c1 / 2 of the
-// quartic).  Without ROUND1, D and Df are the same array.  The reduction needs
-// gridDim.x <= kRedBlocksMax.
+// the recurrence keeps Df unrounded; each block leaves its part of the slope
+// <G, D> of the rounded direction in slope[blockIdx.x], which the coefficients
+// kernel sums (c1 / 2 of the quartic; no serial tail here).  Without ROUND1, D
+// and Df are the same array.
 template <bool ROUND1>
-__device__ __forceinline__ void direction_slope(float gd, double *partials, unsigned int *counter,
-                                                DevState *state) {
+__device__ __forceinline__ void direction_slope(float gd, double *slope) {
     if (!ROUND1) return;
     __shared__ double red[NT / 32];
     const float f[1] = {gd};
     double v[1];
     to_f64<1>(f, v);
     block_sum<1>(v, red, true);
-    double tot[1];
-    if (!publish_and_collect<1>(v, partials, counter, tot, red)) return;
-    if (threadIdx.x == 0) state->gD = tot[0];
+    if (threadIdx.x == 0) slope[blockIdx.x] = v[0];
 }
 
 template <bool ROUND1>
 __global__ void __launch_bounds__(NT) mx_direction_kernel(int m, int64_t mn, const float *__restrict__ G,
                                                            const float *__restrict__ Zg, float *Gp, float *Df,
-                                                           float *D, DevState *state, DigitOut dd,
-                                                           double *partials, unsigned int *counter) {
+                                                           float *D, DevState *state, DigitOut dd, double *slope) {
     if (*((volatile const int *)&state->done)) return;
     const float beta = state->beta_f;
     const bool restart = state->restart != 0;
@@ -543,7 +552,7 @@ __global__ void __launch_bounds__(NT) mx_direction_kernel(int m, int64_t mn, con
             put3f(dd, j * dd.ld + i, d);
         }
     }
-    direction_slope<ROUND1>(gd, partials, counter, state);
+    direction_slope<ROUND1>(gd, slope);
 }
 
 // four consecutive rows of one column per thread (m % 4 == 0, 16-byte aligned arrays)
@@ -551,7 +560,7 @@ template <bool PRE, bool ROUND1>
 __global__ void __launch_bounds__(NT) mx_direction4_kernel(int m, int64_t mn, const float4 *__restrict__ G,
                                                             const float4 *__restrict__ Zg, float4 *Gp, float4 *Df,
                                                             float4 *D, DevState *state, DigitOut dd,
-                                                            double *partials, unsigned int *counter) {
+                                                            double *slope) {
     if (*((volatile const int *)&state->done)) return;
     const float beta = state->beta_f;
     const bool restart = state->restart != 0;
@@ -591,7 +600,7 @@ __global__ void __launch_bounds__(NT) mx_direction4_kernel(int m, int64_t mn, co
             put3f4(dd, j * dd.ld + i, d);
         }
     }
-    direction_slope<ROUND1>(gd, partials, counter, state);
+    direction_slope<ROUND1>(gd, slope);
 }
 
 // Digits of four consecutive rows of one column per thread (m % 4 == 0)
@@ -626,8 +635,11 @@ int tiles_blocks(int64_t a, int64_t b) {
 }  // namespace
 
 int mx_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh, const float *Z, int64_t ldz,
-                      double *scratch, unsigned int *counter, DevState *state, cudaStream_t st) {
-    mx_coeffs_kernel<<<tiles_blocks(n, n), NT, 0, st>>>(n, h0, s0, ldh, Z, ldz, scratch, counter, state);
+                      double *scratch, unsigned int *counter, DevState *state, const double *slope, int nslope,
+                      cudaStream_t st) {
+    if (nslope < 0 || nslope > kRedBlocksMax || (nslope > 0 && slope == nullptr)) return OMM_ERR_ARG;
+    mx_coeffs_kernel<<<tiles_blocks(n, n), NT, 0, st>>>(n, h0, s0, ldh, Z, ldz, scratch, counter, state, slope,
+                                                        nslope);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
@@ -683,37 +695,36 @@ int mx_dots_beta(int64_t mn, const float *G, const float *Zg, const float *Gp, c
 }
 
 int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *Df, float *D,
-                 DevState *state, DigitOut dd, bool round1, double *scratch, unsigned int *counter, cudaStream_t st) {
-    if (round1 && (scratch == nullptr || counter == nullptr || D == nullptr || D == Df)) return OMM_ERR_ARG;
+                 DevState *state, DigitOut dd, bool round1, double *slope, int *slope_blocks, cudaStream_t st) {
+    if (round1 && (slope == nullptr || D == nullptr || D == Df)) return OMM_ERR_ARG;
     if (!round1) D = Df;
     const int64_t mn = m * n;
     const bool aligned =
         ((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)Df) | ((uintptr_t)D) | ((uintptr_t)Zg)) & 15u) == 0 &&
         (dd.ptr == nullptr || ((((uintptr_t)dd.ptr) & 7u) == 0 && dd.ld % 4 == 0 && dd.plane % 4 == 0));
-    // the rounding form sums <G, D> over its blocks: at most kRedBlocksMax of them
+    // the rounding form leaves one slope partial per block: at most kRedBlocksMax
     const int64_t cap = round1 ? kRedBlocksMax : 152 * 8;
-    if (m % 4 == 0 && aligned) {
-        int64_t nb = ceil_div(mn / 4, (int64_t)NT * 4);
-        if (nb > cap) nb = cap;
-        const unsigned grid = (unsigned)(nb < 1 ? 1 : nb);
+    const bool vec = m % 4 == 0 && aligned;
+    int64_t nb = vec ? ceil_div(mn / 4, (int64_t)NT * 4) : ceil_div(mn, (int64_t)NT * 4);
+    if (nb > cap) nb = cap;
+    const unsigned grid = (unsigned)(nb < 1 ? 1 : nb);
+    if (slope_blocks != nullptr) *slope_blocks = round1 ? (int)grid : 0;
+    if (vec) {
         const float4 *G4 = reinterpret_cast<const float4 *>(G);
         const float4 *Z4 = Zg != nullptr ? reinterpret_cast<const float4 *>(Zg) : G4;
         float4 *Gp4 = reinterpret_cast<float4 *>(Gp), *Df4 = reinterpret_cast<float4 *>(Df),
                *D4 = reinterpret_cast<float4 *>(D);
         auto kern = Zg != nullptr ? (round1 ? mx_direction4_kernel<true, true> : mx_direction4_kernel<true, false>)
                                   : (round1 ? mx_direction4_kernel<false, true> : mx_direction4_kernel<false, false>);
-        kern<<<grid, NT, 0, st>>>((int)m, mn, G4, Z4, Gp4, Df4, D4, state, dd, scratch, counter);
+        kern<<<grid, NT, 0, st>>>((int)m, mn, G4, Z4, Gp4, Df4, D4, state, dd, slope);
         count_launch();
         OMM_CUDA_TRY(cudaGetLastError());
         return OMM_OK;
     }
-    int64_t nb = ceil_div(mn, (int64_t)NT * 4);
-    if (nb > cap) nb = cap;
-    const unsigned grid = (unsigned)(nb < 1 ? 1 : nb);
     if (round1)
-        mx_direction_kernel<true><<<grid, NT, 0, st>>>((int)m, mn, G, Zg, Gp, Df, D, state, dd, scratch, counter);
+        mx_direction_kernel<true><<<grid, NT, 0, st>>>((int)m, mn, G, Zg, Gp, Df, D, state, dd, slope);
     else
-        mx_direction_kernel<false><<<grid, NT, 0, st>>>((int)m, mn, G, Zg, Gp, Df, D, state, dd, scratch, counter);
+        mx_direction_kernel<false><<<grid, NT, 0, st>>>((int)m, mn, G, Zg, Gp, Df, D, state, dd, slope);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;

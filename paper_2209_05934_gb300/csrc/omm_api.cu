@@ -99,6 +99,7 @@ struct omm_handle {
     omm_diag diag{};
     int chunk = 8;
     int cur_dig = 3;          // digits of the split products of the current phase
+    int slope_blocks = 0;     // per-block slope parts the last mixed direction left in slot 3
     // one CUDA graph per phase for the chunk of CG steps, captured after one
     // eager chunk of that phase (modules loaded, kernel attributes set)
     static constexpr int kPhases = 7;
@@ -761,8 +762,9 @@ int mixed_direction(omm_handle *h, int first) {
     const bool round1 = h->opt.dir_digits == 1;
     float *Df = round1 ? x.Df32 : x.D32;
     TRY(omm::mx_dots_beta(m * n, x.G32, Zg, x.Gp32, Df, scr(h, 2), ctr(h, 2), h->dstate, first, h->stream));
-    return omm::mx_direction(m, n, x.G32, Zg, x.Gp32, Df, x.D32, h->dstate, dig_D(h), round1, scr(h, 2), ctr(h, 2),
-                             h->stream);
+    // the slope parts go to reduction slot 3 (otherwise used by omm_set_HS only)
+    return omm::mx_direction(m, n, x.G32, Zg, x.Gp32, Df, x.D32, h->dstate, dig_D(h), round1, scr(h, 3),
+                             &h->slope_blocks, h->stream);
 }
 
 // Start of the split-precision phase: H'W, SW, H_W, S_W, energy, G, D from W.
@@ -797,7 +799,8 @@ int mixed_glue1(omm_handle *h, bool accurate_gradient) {
     omm::DevState *s = h->dstate;
     MixedBufs &x = h->mx;
     { StageTimer t(h, OMM_STAGE_LINESEARCH);
-      TRY(omm::mx_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 0), ctr(h, 0), s, st)); }
+      TRY(omm::mx_coeffs_linemin((int)n, h->h0s0, h->h0s0 + n, 2 * n, x.Z32, 2 * n, scr(h, 0), ctr(h, 0), s,
+                                 scr(h, 3), h->slope_blocks, st)); }
     { StageTimer t(h, OMM_STAGE_UPDATE);
       // the n x n update (H_W, S_W, energy, stop test) reads and writes nothing the
       // m x n update touches: for large systems it runs beside it on the handle's
@@ -1578,6 +1581,9 @@ int omm_solve_progress(omm_handle *h, int32_t blocking, int32_t *done) {
         h->phase = PH_REFINE;
         return enqueue_chunk(h);
     }
+    // a first phase that ended without reaching its tolerance (step limit, line
+    // search, non-finite data) ends the solve: its steps are first-phase steps
+    if (h->phase == PH_MIXED || h->phase == PH_SPARSE_MIXED) h->k_mixed = h->hstate->k;
     h->status = h->hstate->status;
     h->phase = PH_FINISHED;
     OMM_CUDA_TRY(cudaEventRecord(h->ev1, h->stream));

@@ -128,8 +128,11 @@ int launch_gershgorin(int64_t m, const double *H, const double *S, double *scrat
 // -------- FP32-glue kernels of the mixed form (mixed_kernels.cu).  The FP64
 // state (W, H'W, SW, H_W, S_W) is updated from FP32 increments; the search
 // direction, gradient and products are FP32 (see mixed_kernels.cu).
+// slope / nslope: the per-block parts of <G, D> left by mx_direction (round1),
+// summed for c1; nslope = 0 takes state->gD from the dots kernel
 int mx_coeffs_linemin(int n, const double *h0, const double *s0, int64_t ldh, const float *Z, int64_t ldz,
-                      double *scratch, unsigned int *counter, DevState *state, cudaStream_t st);
+                      double *scratch, unsigned int *counter, DevState *state, const double *slope, int nslope,
+                      cudaStream_t st);
 int mx_update(int64_t m, int64_t n, double *W, const float *D, double *HW, const float *HD, double *SW,
               const float *SD, const DevState *state, DigitOut wd, DigitOut swhw, cudaStream_t st);
 int mx_nn_update(int n, double *h0, double *s0, int64_t ldh, const float *Z, int64_t ldz, double *scratch,
@@ -138,11 +141,12 @@ int mx_nn_update(int n, double *h0, double *s0, int64_t ldh, const float *Z, int
 int mx_dots_beta(int64_t mn, const float *G, const float *Zg, const float *Gp, const float *D, double *scratch,
                  unsigned int *counter, DevState *state, int first, cudaStream_t st);
 // Df: the CG recurrence's direction, updated in place.  round1: D receives Df
-// rounded to one BF16 digit (the search direction; its digits to dd) and
-// state->gD = <G, D> (summed over the kernel's blocks in scratch / counter);
-// otherwise D is ignored and Df is the search direction.
+// rounded to one BF16 digit (the search direction; its digits to dd) and each
+// block's part of <G, D> goes to slope[block] (*slope_blocks of them, at most
+// kRedBlocksMax), for mx_coeffs_linemin; otherwise D is ignored, Df is the
+// search direction and *slope_blocks = 0.
 int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *Df, float *D,
-                 DevState *state, DigitOut dd, bool round1, double *scratch, unsigned int *counter, cudaStream_t st);
+                 DevState *state, DigitOut dd, bool round1, double *slope, int *slope_blocks, cudaStream_t st);
 // digits of an FP32 m x n column-major array: column j -> row j of the planes
 int mx_digits(int64_t m, int64_t n, const float *A, const DevState *state, DigitOut dd, cudaStream_t st);
 int mx_round(int64_t count, const double *src, float *dst, const DevState *state, cudaStream_t st);
