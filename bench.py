@@ -407,6 +407,7 @@ def run_omm(args):
     if roof is not None and prec == "mixed" and tkey in TRAFFIC:
         roof["traffic"] = TRAFFIC[tkey]["bytes_per_launch"]
         roof["traffic_source"] = TRAFFIC[tkey]["source"]
+        roof["tensor_pipe_active_ncu"] = TRAFFIC[tkey]["tensor_pipe_active"]
 
     if rank != 0:
         solver.close()
@@ -487,7 +488,9 @@ STAGES = ["products", "contract", "linesearch", "update", "gradient", "direction
 TRAFFIC = {("products", 2, 1, True): {
     "bytes_per_launch": 150.83392e6 + 39.697152e6,
     "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one first-phase products launch "
-              "(tc_gemm_pair_kernel, two digits of [H'; S], one digit of D), m=4096, n=1024"}}
+              "(tc_gemm_pair_kernel, two digits of [H'; S], one digit of D), m=4096, n=1024",
+    # the same capture's sm__pipe_tensor_cycles_active (of the SMs' active and of elapsed cycles)
+    "tensor_pipe_active": {"of_active_cycles": 0.495, "of_elapsed_cycles": 0.404}}}
 
 
 def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):

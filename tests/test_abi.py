@@ -68,5 +68,7 @@ def test_options_reject_unknown_names(built):
     from paper_2209_05934_gb300 import omm
     o = omm.default_options(precon=-1, tau_T=5.0, split_digits=3)
     assert (o.precon, o.tau_T, o.split_digits, o.graphs) == (-1, 5.0, 3, 1)
+    # the C defaults of the last fields land where the binding reads them (same layout)
+    assert (o.screen_eps, o.gemm_pair, o.gemm_persistent, o.dir_digits) == (0.0, 1, 0, 1)
     with pytest.raises(TypeError):
         omm.default_options(precond=-1)

@@ -95,5 +95,12 @@ def test_grouped_rejects_unsupported_handles(omm):
     W0 = dev(sysm.W0_dense())
     E, it, st, rc = omm.batch_solve_grouped([a, b], [W0, W0], tol=1e-10)
     assert rc == omm.ERR_UNSUPPORTED
+    # one grouped launch holds one operand layout: every handle's search directions
+    # must carry the same number of digits
+    c = omm.Solver(sysm.m, sysm.n, 8, precision=omm.PREC_MIXED, dir_digits=0)
+    c.set_HS(dev(sysm.dense_H()), dev(sysm.dense_S()))
+    E, it, st, rc = omm.batch_solve_grouped([a, c], [W0, W0], tol=1e-10)
+    assert rc == omm.ERR_UNSUPPORTED
     a.close()
     b.close()
+    c.close()
