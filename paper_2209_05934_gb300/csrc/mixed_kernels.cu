@@ -37,7 +37,7 @@ __device__ __forceinline__ void put3f(const DigitOut &d, int64_t o, float v) {
     const __nv_bfloat16 d3 = __float2bfloat16_rn(r1 - __bfloat162float(d2));
     __nv_bfloat16 *p = (__nv_bfloat16 *)d.ptr;
     p[o] = d1;
-    p[d.plane + o] = d2;
+    if (d.nd > 1) p[d.plane + o] = d2;
     if (d.nd > 2) p[2 * d.plane + o] = d3;
 }
 
@@ -59,7 +59,7 @@ __device__ __forceinline__ void put3f4(const DigitOut &d, int64_t o, float4 v) {
         return u;
     };
     *reinterpret_cast<uint2 *>(p + o) = pack(a1, b1);
-    *reinterpret_cast<uint2 *>(p + d.plane + o) = pack(a2, b2);
+    if (d.nd > 1) *reinterpret_cast<uint2 *>(p + d.plane + o) = pack(a2, b2);
     if (d.nd > 2) *reinterpret_cast<uint2 *>(p + 2 * d.plane + o) = pack(a3, b3);
 }
 
@@ -73,7 +73,7 @@ __device__ __forceinline__ void put3f2(const DigitOut &d, int64_t o, float v0, f
     const __nv_bfloat162 a3 = __floats2bfloat162_rn(r0 - f2.x, r1 - f2.y);
     __nv_bfloat16 *p = (__nv_bfloat16 *)d.ptr;
     *reinterpret_cast<__nv_bfloat162 *>(p + o) = a1;
-    *reinterpret_cast<__nv_bfloat162 *>(p + d.plane + o) = a2;
+    if (d.nd > 1) *reinterpret_cast<__nv_bfloat162 *>(p + d.plane + o) = a2;
     if (d.nd > 2) *reinterpret_cast<__nv_bfloat162 *>(p + 2 * d.plane + o) = a3;
 }
 

@@ -748,9 +748,17 @@ int mixed_direction(omm_handle *h, int first) {
     MixedBufs &x = h->mx;
     const float *Zg = nullptr;
     if (h->precon_on) {
+        // Z = P G only shapes the search direction (the line search is exact along
+        // any direction, and beta and the restart test take the same Z), so it is
+        // formed from the leading BF16 digit of P and of G: one pair product
         StageTimer t(h, OMM_STAGE_PRECON);
-        TRY(omm::mx_digits(m, n, x.G32, h->dstate, omm::DigitOut{x.Gd, x.ldm, n * x.ldm, h->cur_dig}, h->stream));
+        TRY(omm::mx_digits(m, n, x.G32, h->dstate, omm::DigitOut{x.Gd, x.ldm, n * x.ldm, 1}, h->stream));
         omm::tc::TcArgs a = tc_args(h, (int)m, (int)n, (int)m);
+        a.npairs = 1;
+        a.pa[0] = 0;
+        a.pb[0] = 0;
+        a.nA = 1;
+        a.nB = 1;
         a.C32 = x.PG32;
         a.ldc = m;
         TRY(omm::tc::gemm(x.mapP_A, x.mapG_B, a, 1, kBN, h->stream, pair_map(h, x.mapG_H)));
