@@ -521,13 +521,14 @@ def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):
 C3 = dict(dims=(16, 16, 16), seed=0, radius=6.0)
 
 
-def sparse_setup(omm, max_iter):
+def sparse_setup(omm, max_iter, precision=None):
     sysm = synth.make_system(*C3["dims"], seed=C3["seed"])
     rp, col, Hv, Sv = sysm.bsr()
     wrp, wcol = sysm.w_pattern(C3["radius"])
     import torch
     s = omm.SparseSolver(sysm.m, sysm.n, 8, 2, rp, col, wrp, wcol, max_iter=max_iter,
-                         stream=torch.cuda.current_stream().cuda_stream)
+                         stream=torch.cuda.current_stream().cuda_stream,
+                         precision=omm.PREC_FP64 if precision is None else precision)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
     return sysm, s, dev(Hv), dev(Sv), dev(sysm.W0_bsr_values(C3["radius"]))
 
@@ -537,7 +538,8 @@ def run_profile_c3(args):
     from paper_2209_05934_gb300 import omm
 
     omm.lib()
-    sysm, s, Hd, Sd, W0d = sparse_setup(omm, args.max_iter if args.max_iter > 0 else 10)
+    prec = omm.PREC_MIXED if args.c3_precision == "mixed" else omm.PREC_FP64
+    sysm, s, Hd, Sd, W0d = sparse_setup(omm, args.max_iter if args.max_iter > 0 else 10, prec)
     s.set_profiling(True)
     s.set_HS(Hd, Sd)
     E, iters, st = s.solve(W0d, tol=0.0, raise_on_error=False)
