@@ -514,29 +514,50 @@ __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64
                                                        const double *__restrict__ nB, double eps2,
                                                        const DevState *state) {
     if (done(state)) return;
-    const int lane = threadIdx.x & 31;
-    constexpr int NE = BM * BN;          // outputs per block
-    const int which = lane / 16, e = lane % 16;   // which: 0 = H', 1 = S
-    const bool active = e < NE;
-    const int r = e / BN, c = e % BN;
-    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
-    for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; o < nnzHW; o += nwarps) {
-        T acc = T(0);
-        if constexpr (VecGather<T, BM, BN, SCREEN>::on) {
-            // A row r (two vectors), the whole 8x2 D block (four), column c picked
+    if constexpr (VecGather<T, BM, BN, SCREEN>::on) {
+        // FP32 (8x2 blocks): lane (which, r) computes both columns of row r from
+        // its A row (two 16-byte loads) and the whole D block (four): two P_HW
+        // blocks per warp, half the L1 bytes of a lane per output element; the
+        // FMAs of each output run in k order, as in the scalar form
+        const int lane = threadIdx.x & 31;
+        const int r = lane & 7, which = (lane >> 3) & 1;
+        const int64_t ngroups = ((int64_t)gridDim.x * NT) >> 4;
+        for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 4; o < nnzHW; o += ngroups) {
+            float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll 2
             for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
                 const float *A = HS + ((int64_t)Ph[t] * 2 + which) * 64 + r * 8;
                 const float *B = D + (int64_t)Pw[t] * 16;
                 const float4 a0 = ld4(A), a1 = ld4(A + 4);
                 const float4 b0 = ld4(B), b1 = ld4(B + 4), b2 = ld4(B + 8), b3 = ld4(B + 12);
-                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const float bv[8] = {c ? b0.y : b0.x, c ? b0.w : b0.z, c ? b1.y : b1.x, c ? b1.w : b1.z,
-                                     c ? b2.y : b2.x, c ? b2.w : b2.z, c ? b3.y : b3.x, c ? b3.w : b3.z};
-#pragma unroll
-                for (int k = 0; k < 8; ++k) acc = fmaf(av[k], bv[k], acc);
+                acc0 = fmaf(a0.x, b0.x, acc0);
+                acc1 = fmaf(a0.x, b0.y, acc1);
+                acc0 = fmaf(a0.y, b0.z, acc0);
+                acc1 = fmaf(a0.y, b0.w, acc1);
+                acc0 = fmaf(a0.z, b1.x, acc0);
+                acc1 = fmaf(a0.z, b1.y, acc1);
+                acc0 = fmaf(a0.w, b1.z, acc0);
+                acc1 = fmaf(a0.w, b1.w, acc1);
+                acc0 = fmaf(a1.x, b2.x, acc0);
+                acc1 = fmaf(a1.x, b2.y, acc1);
+                acc0 = fmaf(a1.y, b2.z, acc0);
+                acc1 = fmaf(a1.y, b2.w, acc1);
+                acc0 = fmaf(a1.z, b3.x, acc0);
+                acc1 = fmaf(a1.z, b3.y, acc1);
+                acc0 = fmaf(a1.w, b3.z, acc0);
+                acc1 = fmaf(a1.w, b3.w, acc1);
             }
-        } else {
+            *reinterpret_cast<float2 *>((which ? SD : HD) + o * 16 + r * 2) = make_float2(acc0, acc1);
+        }
+    } else {
+        const int lane = threadIdx.x & 31;
+        constexpr int NE = BM * BN;          // outputs per block
+        const int which = lane / 16, e = lane % 16;   // which: 0 = H', 1 = S
+        const bool active = e < NE;
+        const int r = e / BN, c = e % BN;
+        const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+        for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; o < nnzHW; o += nwarps) {
+            T acc = T(0);
 #pragma unroll 4
             for (int64_t t = Prp[o]; t < Prp[o + 1]; ++t) {
                 if (SCREEN && nHS[(int64_t)Ph[t] * 2 + which] * nB[Pw[t]] < eps2) continue;
@@ -547,8 +568,8 @@ __global__ void __launch_bounds__(NT) products_kernel(int64_t nnzHW, const int64
                     for (int k = 0; k < BM; ++k) acc = fma(A[k], B[k * BN], acc);
                 }
             }
+            if (active) (which ? SD : HD)[o * NE + e] = acc;
         }
-        if (active) (which ? SD : HD)[o * NE + e] = acc;
     }
 }
 
@@ -584,6 +605,66 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
     const T *R4 = mat4 == 0 ? HD : SD;
     T *out4 = mat4 == 0 ? X : Y;
     const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+    if constexpr (VecGather<T, BM, BN, SCREEN>::on) {
+        // FP32 (8x2 blocks): each eight-lane group of a warp takes one P_N block,
+        // lane k of the group basis row k: per block triple it loads row k of the
+        // W, D, H'D and SD blocks once (the L1's return bandwidth bounds these
+        // gathers: 256 bytes per triple, each byte fetched once) and updates all
+        // sixteen outputs (2x2 each of X, Y, h2, s2; X and Y only on the lower-
+        // triangle blocks), which the group then sums over k.
+        const int k = lane & 7, grp = lane >> 3;
+        // warp-uniform loop: the four groups of a warp take blocks qb .. qb + 3, and
+        // every lane runs the sums (a group past the end accumulates nothing)
+        for (int64_t qb = (((int64_t)blockIdx.x * NT + threadIdx.x) >> 5) * 4; qb < nnzN; qb += nwarps * 4) {
+            const int64_t q = qb + grp;
+            const bool valid = q < nnzN;
+            const bool lower = valid && Ntr != nullptr && Ntr[q] < q;
+            float acc[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+            const int64_t t1 = valid ? Crp[q + 1] : 0;
+#pragma unroll 2
+            for (int64_t t = valid ? Crp[q] : 0; t < t1; ++t) {
+                const int64_t ia = (int64_t)Ca[t] * 16 + 2 * k, ib = (int64_t)Cb[t] * 16 + 2 * k;
+                const float2 w = __ldg(reinterpret_cast<const float2 *>(W + ia));
+                const float2 hd = __ldg(reinterpret_cast<const float2 *>(HD + ib));
+                const float2 sd = __ldg(reinterpret_cast<const float2 *>(SD + ib));
+                acc[0] = fmaf(w.x, hd.x, acc[0]);
+                acc[1] = fmaf(w.x, hd.y, acc[1]);
+                acc[2] = fmaf(w.y, hd.x, acc[2]);
+                acc[3] = fmaf(w.y, hd.y, acc[3]);
+                acc[4] = fmaf(w.x, sd.x, acc[4]);
+                acc[5] = fmaf(w.x, sd.y, acc[5]);
+                acc[6] = fmaf(w.y, sd.x, acc[6]);
+                acc[7] = fmaf(w.y, sd.y, acc[7]);
+                if (!lower) {
+                    const float2 dd = __ldg(reinterpret_cast<const float2 *>(D + ia));
+                    acc[8] = fmaf(dd.x, hd.x, acc[8]);
+                    acc[9] = fmaf(dd.x, hd.y, acc[9]);
+                    acc[10] = fmaf(dd.y, hd.x, acc[10]);
+                    acc[11] = fmaf(dd.y, hd.y, acc[11]);
+                    acc[12] = fmaf(dd.x, sd.x, acc[12]);
+                    acc[13] = fmaf(dd.x, sd.y, acc[13]);
+                    acc[14] = fmaf(dd.y, sd.x, acc[14]);
+                    acc[15] = fmaf(dd.y, sd.y, acc[15]);
+                }
+            }
+            // sums over the group's eight lanes (xor 1, 2, 4 stay inside the group)
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+            // lanes 0..3 of the group store X, Y, h2, s2 (X and Y on lower blocks)
+            if (valid && k < (lower ? 2 : 4)) {
+                float *o = k == 0 ? X : k == 1 ? Y : k == 2 ? h2 : s2;
+                const float4 v = k == 0   ? make_float4(acc[0], acc[1], acc[2], acc[3])
+                                 : k == 1 ? make_float4(acc[4], acc[5], acc[6], acc[7])
+                                 : k == 2 ? make_float4(acc[8], acc[9], acc[10], acc[11])
+                                          : make_float4(acc[12], acc[13], acc[14], acc[15]);
+                *reinterpret_cast<float4 *>(o + q * 4) = v;
+            }
+        }
+    } else {
     for (int64_t q = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; q < nnzN; q += nwarps) {
         if (!SCREEN && Ntr != nullptr && Ntr[q] < q) {
             T acc = T(0);
@@ -619,6 +700,7 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         if (half == 0) out[q * 4 + a * 2 + b] = acc;
     }
+    }
 }
 
 // h2, s2 on the lower-triangle blocks of P_N from their transposes' blocks
@@ -650,26 +732,41 @@ __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_
                                                        const double *__restrict__ nh0, const double *__restrict__ ns0,
                                                        double eps2, const DevState *state) {
     if (done(state)) return;
-    const int e = threadIdx.x & 15;
-    if (e >= BM * BN) return;
-    const int r = e / BN, c = e % BN;
-    const int64_t ngroups = ((int64_t)gridDim.x * NT) >> 4;
-    for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 4; o < nnzW; o += ngroups) {
-        T acc = T(0);
-        if constexpr (VecGather<T, BM, BN, SCREEN>::on) {
-            // row r of the SW and H'W blocks (two floats each), the whole 2x2 h0, s0 blocks
+    if constexpr (VecGather<T, BM, BN, SCREEN>::on) {
+        // FP32 (8x2 blocks): lane per block row r computing both columns from one
+        // row of the SW and H'W blocks and the whole 2x2 h0, s0 blocks (half the
+        // L1 bytes of a lane per output element), four W blocks per warp; the
+        // FMAs of each output run in the same order as the scalar form's
+        const int r = threadIdx.x & 7;
+        const int64_t ngroups = ((int64_t)gridDim.x * NT) >> 3;
+        for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 3; o < nnzW; o += ngroups) {
+            float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll 2
             for (int64_t t = Grp[o]; t < Grp[o + 1]; ++t) {
                 const int64_t gb = (int64_t)Gb[t] * 16 + r * 2, gq = (int64_t)Gq[t] * 4;
                 const float2 sw = __ldg(reinterpret_cast<const float2 *>(SW + gb));
                 const float2 hw = __ldg(reinterpret_cast<const float2 *>(HW + gb));
                 const float4 hq = ld4(h0 + gq), sq = ld4(s0 + gq);
-                acc = fmaf(sw.x, c ? hq.y : hq.x, acc);
-                acc = fmaf(hw.x, c ? sq.y : sq.x, acc);
-                acc = fmaf(sw.y, c ? hq.w : hq.z, acc);
-                acc = fmaf(hw.y, c ? sq.w : sq.z, acc);
+                acc0 = fmaf(sw.x, hq.x, acc0);
+                acc0 = fmaf(hw.x, sq.x, acc0);
+                acc0 = fmaf(sw.y, hq.z, acc0);
+                acc0 = fmaf(hw.y, sq.z, acc0);
+                acc1 = fmaf(sw.x, hq.y, acc1);
+                acc1 = fmaf(hw.x, sq.y, acc1);
+                acc1 = fmaf(sw.y, hq.w, acc1);
+                acc1 = fmaf(hw.y, sq.w, acc1);
             }
-        } else {
+            const float2 hwo = *reinterpret_cast<const float2 *>(HW + (int64_t)WtoHW[o] * 16 + r * 2);
+            *reinterpret_cast<float2 *>(G + o * 16 + r * 2) =
+                make_float2(2.0f * (2.0f * hwo.x - acc0), 2.0f * (2.0f * hwo.y - acc1));
+        }
+    } else {
+        const int e = threadIdx.x & 15;
+        if (e >= BM * BN) return;
+        const int r = e / BN, c = e % BN;
+        const int64_t ngroups = ((int64_t)gridDim.x * NT) >> 4;
+        for (int64_t o = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 4; o < nnzW; o += ngroups) {
+            T acc = T(0);
 #pragma unroll 4
             for (int64_t t = Grp[o]; t < Grp[o + 1]; ++t) {
                 const T *sw = SW + (int64_t)Gb[t] * BM * BN + r * BN;
@@ -692,8 +789,8 @@ __global__ void __launch_bounds__(NT) gradient_kernel(int64_t nnzW, const int64_
                     }
                 }
             }
+            G[o * BM * BN + e] = T(2) * (T(2) * HW[(int64_t)WtoHW[o] * BM * BN + e] - acc);
         }
-        G[o * BM * BN + e] = T(2) * (T(2) * HW[(int64_t)WtoHW[o] * BM * BN + e] - acc);
     }
 }
 
@@ -1429,7 +1526,7 @@ int mixed_begin(Dev &d, const DevState *state, cudaStream_t st) {
 }
 
 int mixed_products(Dev &d, const DevState *state, cudaStream_t st) {
-    DISPATCH_BLOCKS(d.bm, d.bn, (products_kernel<BM, BN, false, float><<<blocks_for(d.nnzHW * 32, NT), NT, 0, st>>>(
+    DISPATCH_BLOCKS(d.bm, d.bn, (products_kernel<BM, BN, false, float><<<blocks_for(d.nnzHW * 16, NT), NT, 0, st>>>(
                                      d.nnzHW, d.Prp, d.Ph, d.Pw, d.HS32, d.D32, d.HD32, d.SD32, nullptr, nullptr, 0.0,
                                      state)));
     LAUNCHED();
@@ -1437,7 +1534,7 @@ int mixed_products(Dev &d, const DevState *state, cudaStream_t st) {
 }
 
 int mixed_contract(Dev &d, const DevState *state, cudaStream_t st) {
-    DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, false, float><<<blocks_for(d.nnzN * 32, NT), NT, 0, st>>>(
+    DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, false, float><<<blocks_for(d.nnzN * 8, NT), NT, 0, st>>>(
                                      d.nnzN, d.Crp, d.Ca, d.Cb, d.W32, d.D32, d.HD32, d.SD32, d.X32, d.Y32, d.h232,
                                      d.s232, nullptr, nullptr, nullptr, nullptr, 0.0, d.Ntr, state)));
     LAUNCHED();
@@ -1467,7 +1564,7 @@ int mixed_update(Dev &d, double *scratch, unsigned int *counter, DevState *state
 }
 
 int mixed_gradient(Dev &d, const DevState *state, cudaStream_t st) {
-    DISPATCH_BLOCKS(d.bm, d.bn, (gradient_kernel<BM, BN, false, float><<<blocks_for(d.nnzW * 16, NT), NT, 0, st>>>(
+    DISPATCH_BLOCKS(d.bm, d.bn, (gradient_kernel<BM, BN, false, float><<<blocks_for(d.nnzW * 8, NT), NT, 0, st>>>(
                                      d.nnzW, d.Grp, d.Gb, d.Gq, d.WtoHW, d.HW32, d.SW32, d.h032, d.s032, d.G32,
                                      nullptr, nullptr, nullptr, nullptr, 0.0, state)));
     LAUNCHED();
