@@ -1272,7 +1272,7 @@ int omm_create(int64_t m, int64_t n, int32_t block_size, const omm_pattern *patt
         free_handle(h);
         return rc;
     }
-    if (h->opt.precision == OMM_PREC_MIXED && (rc = h->sparse ? omm::sp::mixed_alloc(h->sd) : mixed_alloc(h))) {
+    if (h->opt.precision == OMM_PREC_MIXED && (rc = h->sparse ? omm::sp::mixed_alloc(h->sh, h->sd) : mixed_alloc(h))) {
         free_handle(h);
         return rc;
     }

@@ -703,6 +703,89 @@ __global__ void __launch_bounds__(NT) contract_kernel(int64_t nnzN, const int64_
     }
 }
 
+// The FP32 contraction by P_N rows: a CTA takes row J (outputs (J, J2)); the
+// W and D blocks of W's column J (every triple of the row draws its left block
+// from them) are staged in shared memory once, so per triple only the H'D and
+// SD rows come from the L1 and L2; CaSlot names the left block's slot in the
+// column.  Lanes as in contract_kernel's FP32 form: an eight-lane group per
+// output block, lane k holding all sixteen outputs for basis row k.
+__global__ void __launch_bounds__(NT) contract_rows_kernel(int64_t nbc, const int64_t *__restrict__ Nrp,
+                                                            const int64_t *__restrict__ WcolRp,
+                                                            const int32_t *__restrict__ WcolIdx,
+                                                            const int64_t *__restrict__ Crp,
+                                                            const uint16_t *__restrict__ CaSlot,
+                                                            const int32_t *__restrict__ Cb, const float *__restrict__ W,
+                                                            const float *__restrict__ D, const float *__restrict__ HD,
+                                                            const float *__restrict__ SD, float *X, float *Y, float *h2,
+                                                            float *s2, const int32_t *__restrict__ Ntr,
+                                                            const DevState *state) {
+    if (done(state)) return;
+    extern __shared__ float4 stage4[];   // W rows of the column, then D rows (nc x 16 floats each)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, k = lane & 7, grp = lane >> 3;
+    for (int64_t J = blockIdx.x; J < nbc; J += gridDim.x) {
+        const int64_t c0 = WcolRp[J];
+        const int nc = (int)(WcolRp[J + 1] - c0);
+        float *sW = reinterpret_cast<float *>(stage4), *sD = sW + (int64_t)nc * 16;
+        __syncthreads();   // the previous row's readers are done with the stage
+        for (int e = threadIdx.x; e < nc * 4; e += NT) {   // one float4 per thread and step
+            const int64_t a = WcolIdx[c0 + (e >> 2)];
+            reinterpret_cast<float4 *>(sW)[e] = __ldg(reinterpret_cast<const float4 *>(W + a * 16) + (e & 3));
+            reinterpret_cast<float4 *>(sD)[e] = __ldg(reinterpret_cast<const float4 *>(D + a * 16) + (e & 3));
+        }
+        __syncthreads();
+        const int64_t q1 = Nrp[J + 1];
+        // warp-uniform loop: the four groups of a warp take blocks qb .. qb + 3
+        for (int64_t qb = Nrp[J] + 4 * warp; qb < q1; qb += 4 * (NT / 32)) {
+            const int64_t q = qb + grp;
+            const bool valid = q < q1;
+            const bool lower = valid && Ntr[q] < q;
+            float acc[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+            const int64_t t1 = valid ? Crp[q + 1] : 0;
+#pragma unroll 2
+            for (int64_t t = valid ? Crp[q] : 0; t < t1; ++t) {
+                const int ia = (int)CaSlot[t] * 16 + 2 * k;
+                const int64_t ib = (int64_t)Cb[t] * 16 + 2 * k;
+                const float2 w = *reinterpret_cast<const float2 *>(sW + ia);
+                const float2 hd = __ldg(reinterpret_cast<const float2 *>(HD + ib));
+                const float2 sd = __ldg(reinterpret_cast<const float2 *>(SD + ib));
+                acc[0] = fmaf(w.x, hd.x, acc[0]);
+                acc[1] = fmaf(w.x, hd.y, acc[1]);
+                acc[2] = fmaf(w.y, hd.x, acc[2]);
+                acc[3] = fmaf(w.y, hd.y, acc[3]);
+                acc[4] = fmaf(w.x, sd.x, acc[4]);
+                acc[5] = fmaf(w.x, sd.y, acc[5]);
+                acc[6] = fmaf(w.y, sd.x, acc[6]);
+                acc[7] = fmaf(w.y, sd.y, acc[7]);
+                if (!lower) {
+                    const float2 dd = *reinterpret_cast<const float2 *>(sD + ia);
+                    acc[8] = fmaf(dd.x, hd.x, acc[8]);
+                    acc[9] = fmaf(dd.x, hd.y, acc[9]);
+                    acc[10] = fmaf(dd.y, hd.x, acc[10]);
+                    acc[11] = fmaf(dd.y, hd.y, acc[11]);
+                    acc[12] = fmaf(dd.x, sd.x, acc[12]);
+                    acc[13] = fmaf(dd.x, sd.y, acc[13]);
+                    acc[14] = fmaf(dd.y, sd.x, acc[14]);
+                    acc[15] = fmaf(dd.y, sd.y, acc[15]);
+                }
+            }
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+            if (valid && k < (lower ? 2 : 4)) {
+                float *o = k == 0 ? X : k == 1 ? Y : k == 2 ? h2 : s2;
+                const float4 v = k == 0   ? make_float4(acc[0], acc[1], acc[2], acc[3])
+                                 : k == 1 ? make_float4(acc[4], acc[5], acc[6], acc[7])
+                                 : k == 2 ? make_float4(acc[8], acc[9], acc[10], acc[11])
+                                          : make_float4(acc[12], acc[13], acc[14], acc[15]);
+                *reinterpret_cast<float4 *>(o + q * 4) = v;
+            }
+        }
+    }
+}
+
 // h2, s2 on the lower-triangle blocks of P_N from their transposes' blocks
 template <typename T>
 __global__ void mirror_kernel(int64_t nnzN, const int32_t *__restrict__ Ntr, T *h2, T *s2, const DevState *state) {
@@ -1299,7 +1382,7 @@ void release(Dev &d) {
     void *ptrs[] = {d.Trp, d.Rrp, d.Tw, d.Tq, d.Rt, d.Rw, d.K, d.T,
                     d.Hrp, d.Hcol, d.Prp, d.Ph, d.Pw, d.Crp, d.Ca, d.Cb, d.Grp, d.Gb, d.Gq, d.WtoHW, d.Ntr,
                     d.Ndiag, d.HS, d.Hin, d.W, d.D, d.G, d.Gp, d.HW, d.SW, d.HD, d.SD, d.h0, d.s0, d.X,
-                    d.Y, d.h2, d.s2, d.keep, d.nrm, d.fbuf};
+                    d.Y, d.h2, d.s2, d.keep, d.nrm, d.fbuf, d.Nrp, d.WcolRp, d.WcolIdx, d.CaSlot};
     for (void *p : ptrs) cudaFree(p);
     d = Dev{};
 }
@@ -1466,7 +1549,42 @@ int gradient(Dev &d, const DevState *state, cudaStream_t st) {
     return OMM_OK;
 }
 
-int mixed_alloc(Dev &d) {
+namespace {
+// Shared-memory budget of the row-staged contraction: W and D rows of one
+// column of W (16 floats each per block)
+constexpr int kRowStageMaxCol = 256;   // 32 KB
+}
+
+int mixed_alloc(const Host &hs, Dev &d) {
+    // row-staged FP32 contraction: slot of every W block in its column, per triple
+    {
+        const int64_t nbc = hs.P.nbc, nnzW = (int64_t)hs.WcolIdx.size();
+        int64_t maxcol = 0;
+        for (int64_t J = 0; J < nbc; ++J) maxcol = std::max(maxcol, hs.WcolRp[J + 1] - hs.WcolRp[J]);
+        if (maxcol > 0 && maxcol <= kRowStageMaxCol) {
+            std::vector<uint16_t> wslot(nnzW);
+            std::vector<int32_t> widx(nnzW);
+            for (int64_t J = 0; J < nbc; ++J)
+                for (int64_t c = hs.WcolRp[J]; c < hs.WcolRp[J + 1]; ++c) {
+                    wslot[hs.WcolIdx[c]] = (uint16_t)(c - hs.WcolRp[J]);
+                    widx[c] = (int32_t)hs.WcolIdx[c];
+                }
+            std::vector<uint16_t> slot(hs.Ca.size());
+            for (size_t t = 0; t < hs.Ca.size(); ++t) slot[t] = wslot[hs.Ca[t]];
+            auto up = [](auto **dst, const auto &v) -> int {
+                const size_t bytes = (v.empty() ? 1 : v.size()) * sizeof(v[0]);
+                if (cudaMalloc((void **)dst, bytes) != cudaSuccess) return OMM_ERR_NOMEM;
+                if (!v.empty() && cudaMemcpy(*dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice) != cudaSuccess)
+                    return OMM_ERR_CUDA;
+                return OMM_OK;
+            };
+            int rc;
+            if ((rc = up(&d.Nrp, hs.Nrp)) || (rc = up(&d.WcolRp, hs.WcolRp)) || (rc = up(&d.WcolIdx, widx)) ||
+                (rc = up(&d.CaSlot, slot)))
+                return rc;
+            d.maxcol = (int)maxcol;
+        }
+    }
     const int64_t bb = (int64_t)d.bm * d.bm, bw = (int64_t)d.bm * d.bn, bq = (int64_t)d.bn * d.bn;
     const int64_t nHS = 2 * d.nnzH * bb, nW = d.nnzW * bw, nHW = d.nnzHW * bw, nN = d.nnzN * bq;
     const int64_t total = nHS + 4 * nW + 4 * nHW + 6 * nN;
@@ -1534,10 +1652,19 @@ int mixed_products(Dev &d, const DevState *state, cudaStream_t st) {
 }
 
 int mixed_contract(Dev &d, const DevState *state, cudaStream_t st) {
-    DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, false, float><<<blocks_for(d.nnzN * 8, NT), NT, 0, st>>>(
-                                     d.nnzN, d.Crp, d.Ca, d.Cb, d.W32, d.D32, d.HD32, d.SD32, d.X32, d.Y32, d.h232,
-                                     d.s232, nullptr, nullptr, nullptr, nullptr, 0.0, d.Ntr, state)));
-    LAUNCHED();
+    if (d.maxcol > 0 && d.bm == 8 && d.bn == 2) {
+        const size_t smem = (size_t)d.maxcol * 16 * 2 * sizeof(float);
+        const int64_t nb = d.nbc < 152 * 8 ? d.nbc : 152 * 8;
+        contract_rows_kernel<<<(unsigned)(nb < 1 ? 1 : nb), NT, smem, st>>>(
+            d.nbc, d.Nrp, d.WcolRp, d.WcolIdx, d.Crp, d.CaSlot, d.Cb, d.W32, d.D32, d.HD32, d.SD32, d.X32, d.Y32,
+            d.h232, d.s232, d.Ntr, state);
+        LAUNCHED();
+    } else {
+        DISPATCH_BLOCKS(d.bm, d.bn, (contract_kernel<BM, BN, false, float><<<blocks_for(d.nnzN * 8, NT), NT, 0, st>>>(
+                                         d.nnzN, d.Crp, d.Ca, d.Cb, d.W32, d.D32, d.HD32, d.SD32, d.X32, d.Y32,
+                                         d.h232, d.s232, nullptr, nullptr, nullptr, nullptr, 0.0, d.Ntr, state)));
+        LAUNCHED();
+    }
     mirror_kernel<float><<<blocks_for(d.nnzN * 4, 256), 256, 0, st>>>(d.nnzN, d.Ntr, d.h232, d.s232, state);
     LAUNCHED();
     return OMM_OK;

@@ -75,6 +75,14 @@ struct Dev {
     float *HS32 = nullptr, *W32 = nullptr, *D32 = nullptr, *G32 = nullptr, *Gp32 = nullptr, *HW32 = nullptr,
           *SW32 = nullptr, *HD32 = nullptr, *SD32 = nullptr, *h032 = nullptr, *s032 = nullptr, *X32 = nullptr,
           *Y32 = nullptr, *h232 = nullptr, *s232 = nullptr;
+    // the FP32 contraction by P_N rows (mixed form): row J's W and D blocks (W's
+    // column J, WcolRp / WcolIdx) staged in shared memory, each triple's W block
+    // named by its slot in that column (CaSlot); maxcol = 0: not built (a column
+    // longer than the staging allows), the per-block kernel runs instead
+    int64_t *Nrp = nullptr, *WcolRp = nullptr;
+    int32_t *WcolIdx = nullptr;
+    uint16_t *CaSlot = nullptr;
+    int maxcol = 0;
 };
 
 // which block norms to refresh (norms())
@@ -119,7 +127,7 @@ int gradient(Dev &d, const DevState *state, cudaStream_t st);
 // (X, Y, h2, s2), mixed_coeffs (quartic and line minimum), mixed_update (FP64
 // W, H'W, SW, H_W, S_W from FP32 increments, shadows, energy and stop test),
 // mixed_gradient, mixed_direction.
-int mixed_alloc(Dev &d);
+int mixed_alloc(const Host &hs, Dev &d);
 int mixed_shadow_HS(Dev &d, cudaStream_t st);
 int mixed_begin(Dev &d, const DevState *state, cudaStream_t st);
 int mixed_products(Dev &d, const DevState *state, cudaStream_t st);
