@@ -341,11 +341,23 @@ __global__ void exp_cm_kernel(int64_t K, int64_t R, const double *__restrict__ X
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t *Xb = (const uint64_t *)X;
     for (int64_t r = w; r < R; r += nw) {
-        unsigned long long mx = 0;
-        for (int64_t k = lane; k < K; k += 32) {
+        // four independent maxima: four loads of each lane in flight (with one warp
+        // per column the grid holds few warps, so each must keep several loads going)
+        unsigned long long m4[4] = {0, 0, 0, 0};
+        int64_t k = lane;
+        for (; k + 96 < K; k += 128)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned long long a = Xb[k + 32 * u + r * ld] & 0x7FFFFFFFFFFFFFFFull;
+                m4[u] = a > m4[u] ? a : m4[u];
+            }
+        for (; k < K; k += 32) {
             const unsigned long long a = Xb[k + r * ld] & 0x7FFFFFFFFFFFFFFFull;
-            mx = a > mx ? a : mx;
+            m4[0] = a > m4[0] ? a : m4[0];
         }
+        unsigned long long mx = m4[0] > m4[1] ? m4[0] : m4[1];
+        const unsigned long long m23 = m4[2] > m4[3] ? m4[2] : m4[3];
+        mx = m23 > mx ? m23 : mx;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
