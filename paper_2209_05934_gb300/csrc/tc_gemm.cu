@@ -61,12 +61,14 @@ __device__ __forceinline__ void split3_i(double v, __nv_bfloat16 &d1, __nv_bfloa
 
 // ------------------------------------------------------------------ epilogue
 // One epilogue warp: TMEM lanes 32q..32q+31 (rows `row` = m0 + 32q + lane of the
-// tile) x BN columns from n0 -> C = alpha acc + beta Cin (FP32 or FP64,
-// column-major), optionally with the result's BF16 digits.  nacc accumulators
-// (K ranges x pair classes) are summed; have_acc false writes beta Cin only.
+// tile) x the tile columns [c_lo, c_hi) from n0 -> C = alpha acc + beta Cin (FP32
+// or FP64, column-major), optionally with the result's BF16 digits.  nacc
+// accumulators (K ranges x pair classes) are summed; have_acc false writes beta
+// Cin only.  This is the general form; tc_epilogue_part takes the specialised one
+// below where it applies.
 template <int BN>
 __device__ __forceinline__ void tc_epilogue(const TcArgs &args, uint32_t tmem, int q, int row, int n0, int z,
-                                            int nacc, bool have_acc, int bn = BN) {
+                                            int nacc, bool have_acc, int c_lo, int c_hi) {
     double *C = args.C != nullptr ? args.C + (int64_t)z * args.c_step : nullptr;
     const double *Cin = args.Cin ? args.Cin + (int64_t)z * args.cin_step : nullptr;
     __nv_bfloat16 *Dd = args.Dout ? args.Dout + (int64_t)z * args.dout_step : nullptr;
@@ -87,9 +89,9 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs &args, uint32_t tmem, i
             }
         };
         double cin[16], cin_next[16];
-        load_cin(0, cin);
-        for (int c0 = 0; c0 < bn; c0 += 16) {
-            if (c0 + 16 < bn) load_cin(c0 + 16, cin_next);
+        load_cin(c_lo, cin);
+        for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
+            if (c0 + 16 < c_hi) load_cin(c0 + 16, cin_next);
             float v[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = 0.f;
@@ -134,9 +136,9 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs &args, uint32_t tmem, i
             }
         };
         double cin[16], cin_next[16];
-        load_cin(0, cin);
-        for (int c0 = 0; c0 < bn; c0 += 16) {
-            if (c0 + 16 < bn) load_cin(c0 + 16, cin_next);
+        load_cin(c_lo, cin);
+        for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
+            if (c0 + 16 < c_hi) load_cin(c0 + 16, cin_next);
             double v[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = 0.0;
@@ -171,6 +173,130 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs &args, uint32_t tmem, i
         }
     }
 }
+
+// The FP32 epilogue specialised at compile time on the launch's options: CIN (an
+// FP64 Cin is read) and NDIG (BF16 digit planes written).  Same arithmetic and
+// rounding as the FP32 branch of tc_epilogue, element for element (the sum of
+// the accumulators starts from +0 there too), but every option test and every
+// 64-bit index product leaves the per-element loop: the outputs advance by
+// pointer steps, and only a chunk that crosses column N tests its columns.  The
+// general form spent about 60 instructions per element on one warp per
+// scheduler, which made the epilogue of a 128 x 256 tile longer than half of
+// its MMAs.  Up to two accumulators (nacc <= 2).
+template <int BN, bool CIN, int NDIG>
+__device__ __forceinline__ void tc_epilogue_fast(const TcArgs &args, uint32_t lane_base, int row, int n0, int z,
+                                                 int nacc, bool have_acc, int c_lo, int c_hi) {
+    const bool row_ok = row < args.M;
+    const int nlim = args.N - n0;   // tile columns inside N
+    const float alpha = (float)args.alpha, beta = (float)args.beta;
+    const int64_t ldc = args.ldc, ldd = NDIG > 0 ? args.ldd : 0, ldi = CIN ? args.ldcin : 0;
+    const int64_t dpl = NDIG > 1 ? args.dplane : 0;
+    float *pc = args.C32 + (int64_t)z * args.c_step + row + (int64_t)(n0 + c_lo) * ldc;
+    __nv_bfloat16 *pd =
+        NDIG > 0 ? args.Dout + (int64_t)z * args.dout_step + row + (int64_t)(n0 + c_lo) * ldd : nullptr;
+    const double *pi = CIN ? args.Cin + (int64_t)z * args.cin_step + row + (int64_t)(n0 + c_lo) * ldi : nullptr;
+    double cin[16], cin_next[16];
+    // Cin of the 16 columns from tile column c0 (p points at column c0), zero past N
+    auto load_cin = [&](const double *p, int c0, double (&dst)[16]) {
+        if (c0 + 16 <= nlim) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) dst[i] = __ldg(p + i * ldi);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) dst[i] = c0 + i < nlim ? __ldg(p + i * ldi) : 0.0;
+        }
+    };
+    // one output element: column i of the chunk at pc / pd
+    auto put = [&](int i, float acc, double cin_i) {
+        float out = alpha * acc;
+        if (CIN) out = fmaf(beta, sw_d2f(cin_i), out);
+        pc[i * ldc] = out;
+        if (NDIG > 0) {
+            const __nv_bfloat16 d1 = __float2bfloat16_rn(out);
+            pd[i * ldd] = d1;
+            if (NDIG > 1) {
+                const float r1 = out - __bfloat162float(d1);
+                const __nv_bfloat16 d2 = __float2bfloat16_rn(r1);
+                pd[dpl + i * ldd] = d2;
+                if (NDIG > 2) pd[2 * dpl + i * ldd] = __float2bfloat16_rn(r1 - __bfloat162float(d2));
+            }
+        }
+    };
+    if (CIN && row_ok && c_lo < nlim) load_cin(pi, c_lo, cin);
+    for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
+        if (c0 >= nlim) break;   // the rest of the tile lies past N (uniform over the warp)
+        if (CIN && row_ok && c0 + 16 < c_hi && c0 + 16 < nlim) load_cin(pi + 16 * ldi, c0 + 16, cin_next);
+        uint32_t r0[16], r1[16];
+        if (have_acc) {
+            tmem_ld16_async(lane_base + (uint32_t)c0, r0);
+            if (nacc > 1) tmem_ld16_async(lane_base + (uint32_t)(BN + c0), r1);
+            tmem_wait_ld(r0);
+            tmem_pin16(r1);
+        }
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            v[i] = 0.f;
+            if (have_acc) {
+                v[i] += __uint_as_float(r0[i]);
+                if (nacc > 1) v[i] += __uint_as_float(r1[i]);
+            }
+        }
+        if (row_ok) {
+            if (c0 + 16 <= nlim) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) put(i, v[i], CIN ? cin[i] : 0.0);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (c0 + i < nlim) put(i, v[i], CIN ? cin[i] : 0.0);
+            }
+        }
+        pc += 16 * ldc;
+        if (NDIG > 0) pd += 16 * ldd;
+        if (CIN) {
+            pi += 16 * ldi;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) cin[i] = cin_next[i];
+        }
+    }
+}
+
+// The epilogue of columns [c_lo, c_hi) of a tile: the specialised FP32 form for
+// FP32 outputs from at most two accumulators, the general form otherwise.
+template <int BN>
+__device__ __forceinline__ void tc_epilogue_part(const TcArgs &args, uint32_t tmem, int q, int row, int n0, int z,
+                                                 int nacc, bool have_acc, int c_lo, int c_hi) {
+    if (args.C32 != nullptr && nacc <= 2) {
+        const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16);
+        const int ndig = args.Dout != nullptr ? args.ndig : 0;
+        if (args.Cin != nullptr) {
+            switch (ndig) {
+            case 0: tc_epilogue_fast<BN, true, 0>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi); return;
+            case 1: tc_epilogue_fast<BN, true, 1>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi); return;
+            case 2: tc_epilogue_fast<BN, true, 2>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi); return;
+            case 3: tc_epilogue_fast<BN, true, 3>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi); return;
+            default: break;
+            }
+        } else {
+            switch (ndig) {
+            case 0: tc_epilogue_fast<BN, false, 0>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi); return;
+            case 1: tc_epilogue_fast<BN, false, 1>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi); return;
+            case 2: tc_epilogue_fast<BN, false, 2>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi); return;
+            case 3: tc_epilogue_fast<BN, false, 3>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi); return;
+            default: break;
+            }
+        }
+    }
+    tc_epilogue<BN>(args, tmem, q, row, n0, z, nacc, have_acc, c_lo, c_hi);
+}
+
+// Epilogue warps per tensor-memory lane quarter in the CTA-pair kernel: two, each
+// taking half of the tile's columns, so that every scheduler runs two epilogue
+// warps and hides the latency of the other's chain (10 warps: at most 168
+// registers a thread).
+constexpr int kEpiWarpsPerQuarter = 2;
+constexpr int kPairThreads = 64 + 128 * kEpiWarpsPerQuarter;
 
 // ------------------------------------------------------------------ the GEMM kernel
 template <int BN, int STAGES, int BKT>
@@ -273,7 +399,7 @@ __global__ void __launch_bounds__(192, 1)
         const bool have_acc = __all_sync(0xffffffffu, got);   // tcgen05.ld is warp-collective
         tc_fence_after();
         const int nacc = (nkb < kacc ? nkb : kacc) * ncls;   // accumulators that were written
-        tc_epilogue<BN>(args, tmem, q, row, n0, z, nacc, have_acc);
+        tc_epilogue_part<BN>(args, tmem, q, row, n0, z, nacc, have_acc, 0, BN);
     }
     tc_fence_before();
     __syncthreads();
@@ -297,11 +423,12 @@ __global__ void __launch_bounds__(192, 1)
 //   warp 1, CTA 0: waits for the stage, issues the pair MMAs and commits to
 //     the empty barriers of both CTAs (multicast), finally to both
 //     accumulator barriers;
-//   warps 2..5 (both CTAs): the epilogue of the CTA's 128 rows.
+//   warps 2..9 (both CTAs): the epilogue of the CTA's 128 rows, two warps per
+//     tensor-memory lane quarter, each writing half of the tile's columns.
 // All waits are bounded; the pair meets at cluster barriers only after every
 // role's loop has ended, and tensor memory is released by both CTAs together.
 template <int STAGES, int BKT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                         const TcArgs args) {
     // state->done only changes between launches, so both CTAs of a pair return here together
@@ -412,7 +539,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         const bool have_acc = __all_sync(0xffffffffu, got);
         tc_fence_after();
         const int nacc = (nkb < kacc ? nkb : kacc) * ncls;
-        tc_epilogue<BN>(args, tmem, q, row, n0, z, nacc, have_acc);
+        const int c_lo = (warp - 2) < 4 ? 0 : BN / 2;   // two warps per lane quarter, half the columns each
+        tc_epilogue_part<BN>(args, tmem, q, row, n0, z, nacc, have_acc, c_lo, c_lo + BN / 2);
     }
     if (warp == 0 && lane == 0 && abort_flag) {
         // an aborted pipeline: let the issued copies land before the CTA can exit.  CTA 0
@@ -600,7 +728,9 @@ __global__ void __launch_bounds__(192, 1)
             tc_fence_after();
             const int m0 = tr.mi * (PAIR ? 2 * BM : BM) + BM * (int)rank;
             const int row = m0 + 32 * q + lane;
-            tc_epilogue<BN>(a, tmem, q, row, tr.ni * bn, tr.z, a.ncls, true, bn);
+            // the general epilogue: with the specialised forms inlined as well, this
+            // kernel's roles no longer fit in a thread's registers
+            tc_epilogue<BN>(a, tmem, q, row, tr.ni * bn, tr.z, a.ncls, true, 0, bn);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
@@ -765,7 +895,7 @@ int launch_tc_pair(const CUtensorMap &ma, const CUtensorMap &mb_half, const TcAr
     while (kacc > 1 && kacc > nkb) kacc >>= 1;
     b.kacc = kacc;
     dim3 grid((unsigned)(2 * ceil_div(a.N, 256)), (unsigned)ceil_div(a.M, 2 * BM), (unsigned)nbatch);
-    tc_gemm_pair_kernel<STAGES, BKT><<<grid, 192, smem, st>>>(ma, mb_half, b);
+    tc_gemm_pair_kernel<STAGES, BKT><<<grid, kPairThreads, smem, st>>>(ma, mb_half, b);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
     return OMM_OK;
