@@ -486,11 +486,12 @@ STAGES = ["products", "contract", "linesearch", "update", "gradient", "direction
 # kernel on this workload, keyed by (stage, split_digits, dir_digits, CTA pairs);
 # an entry is removed whenever its kernel changes, and added when it is captured again.
 TRAFFIC = {("products", 2, 1, True): {
-    "bytes_per_launch": 150.83392e6 + 39.697152e6,
+    "bytes_per_launch": 150.687488e6 + 36.777728e6,
     "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one first-phase products launch "
-              "(tc_gemm_pair_kernel, two digits of [H'; S], one digit of D), m=4096, n=1024",
+              "(tc_gemm_pair_kernel with the specialised FP32 epilogue, two digits of [H'; S], one digit "
+              "of D), m=4096, n=1024",
     # the same capture's sm__pipe_tensor_cycles_active (of the SMs' active and of elapsed cycles)
-    "tensor_pipe_active": {"of_active_cycles": 0.495, "of_elapsed_cycles": 0.404}}}
+    "tensor_pipe_active": {"of_active_cycles": 0.663, "of_elapsed_cycles": 0.542}}}
 
 
 def roofline_entry(prec, dom, ms_stage, n_stage, m, n, pk, pk_kind):

@@ -381,7 +381,16 @@ __device__ bool publish_and_collect(const double (&v)[NV], double *partials, uns
     // the long-latency FP64 unit, instead of a block-wide tree per value)
     for (int q = threadIdx.x >> 5; q < NV; q += NT / 32) {
         double s = 0.0;
-        for (unsigned b = threadIdx.x & 31; b < gridDim.x; b += 32) s += __ldcg(&partials[b * NV + q]);
+        // the lane's blocks in order, eight loads in flight at a time
+        unsigned b = threadIdx.x & 31;
+        for (; b + 224 < gridDim.x; b += 256) {
+            double p[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) p[k] = __ldcg(&partials[(b + 32 * k) * NV + q]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s += p[k];
+        }
+        for (; b < gridDim.x; b += 32) s += __ldcg(&partials[b * NV + q]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         if ((threadIdx.x & 31) == 0) red[q] = s;

@@ -291,6 +291,31 @@ __device__ __forceinline__ void tc_epilogue_part(const TcArgs &args, uint32_t tm
     tc_epilogue<BN>(args, tmem, q, row, n0, z, nacc, have_acc, c_lo, c_hi);
 }
 
+// The same with only the three forms the solver's split products take (digits of
+// the products with two planes, the contraction without, the gradient with Cin),
+// for the tile-list kernel, whose roles leave less room for inlined code.
+template <int BN>
+__device__ __forceinline__ void tc_epilogue_part3(const TcArgs &args, uint32_t tmem, int q, int row, int n0, int z,
+                                                  int nacc, bool have_acc, int c_lo, int c_hi) {
+    if (args.C32 != nullptr && nacc <= 2) {
+        const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16);
+        const int ndig = args.Dout != nullptr ? args.ndig : 0;
+        if (args.Cin != nullptr && ndig == 0) {
+            tc_epilogue_fast<BN, true, 0>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi);
+            return;
+        }
+        if (args.Cin == nullptr && ndig == 0) {
+            tc_epilogue_fast<BN, false, 0>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi);
+            return;
+        }
+        if (args.Cin == nullptr && ndig == 2) {
+            tc_epilogue_fast<BN, false, 2>(args, lb, row, n0, z, nacc, have_acc, c_lo, c_hi);
+            return;
+        }
+    }
+    tc_epilogue<BN>(args, tmem, q, row, n0, z, nacc, have_acc, c_lo, c_hi);
+}
+
 // Epilogue warps per tensor-memory lane quarter in the CTA-pair kernel: two, each
 // taking half of the tile's columns, so that every scheduler runs two epilogue
 // warps and hides the latency of the other's chain (10 warps: at most 168
@@ -728,9 +753,7 @@ __global__ void __launch_bounds__(192, 1)
             tc_fence_after();
             const int m0 = tr.mi * (PAIR ? 2 * BM : BM) + BM * (int)rank;
             const int row = m0 + 32 * q + lane;
-            // the general epilogue: with the specialised forms inlined as well, this
-            // kernel's roles no longer fit in a thread's registers
-            tc_epilogue<BN>(a, tmem, q, row, tr.ni * bn, tr.z, a.ncls, true, 0, bn);
+            tc_epilogue_part3<BN>(a, tmem, q, row, tr.ni * bn, tr.z, a.ncls, true, 0, bn);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
