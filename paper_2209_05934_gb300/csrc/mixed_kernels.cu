@@ -612,6 +612,172 @@ __global__ void __launch_bounds__(NT) mx_direction4_kernel(int m, int64_t mn, co
     direction_slope<ROUND1>(gd, slope);
 }
 
+// Grid-wide barrier of a cooperative launch (every block of the grid is
+// resident).  Blocks arrive on a 64-bit counter that only grows; a launch waits
+// for the next multiple of gridDim.x, so the counter needs no reset as long as
+// every launch on it has the same grid.  The wait is bounded: past ~1 s (far
+// beyond any skew between resident blocks) it records the error and the block
+// goes on.
+__device__ __forceinline__ void grid_barrier(unsigned long long *count, int *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long old = atomicAdd(count, 1ull);
+        const unsigned long long target = (old / gridDim.x + 1ull) * gridDim.x;
+        uint64_t t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        for (uint32_t i = 0;; ++i) {
+            unsigned long long c;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(count) : "memory");
+            if (c >= target) break;
+            if ((i & 255u) == 255u) {
+                uint64_t t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                if (t - t0 > 1000000000ull) {
+                    atomicExch(err, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// The CG dots and the direction in one cooperative launch (m % 4 == 0, 16-byte
+// aligned arrays): each block sums its part of <Z,G>, <Z,Gp>, <G,Df> exactly as
+// mx_dots_kernel does, the grid meets at a barrier, every block then forms the
+// three totals from the per-block parts in the same fixed order (so every block
+// holds the same beta and restart flag; block 0 writes them to the state), and
+// the grid runs the direction pass of mx_direction4_kernel.  This replaces a
+// second launch and the last block's serial pass of the dots kernel; G, Gp and
+// Df are read twice, the second time mostly from L2.
+template <bool PRE, bool ROUND1>
+__global__ void __launch_bounds__(NT, 4) mx_dots_direction4_kernel(int m, int64_t mn, const float4 *__restrict__ G,
+                                                                 const float4 *__restrict__ Zg, float4 *Gp,
+                                                                 float4 *Df, float4 *D, DevState *state, DigitOut dd,
+                                                                 double *slope, double *partials,
+                                                                 unsigned long long *bar, int first) {
+    if (*((volatile const int *)&state->done)) return;
+    __shared__ double red[(NT / 32) * ND];
+    __shared__ float s_beta;
+    __shared__ int s_restart, s_bad;
+    // read before the barrier: block 0 overwrites it after
+    const double gpgp = state->gg_prev;
+    const int64_t n4 = mn / 4, stride = (int64_t)gridDim.x * NT;
+    {
+        float f[ND] = {0.f, 0.f, 0.f};
+#pragma unroll 4
+        for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n4; k += stride) {
+            const float4 g = G[k];
+            const float4 z = PRE ? Zg[k] : g;
+            f[0] = fmaf(z.x, g.x, fmaf(z.y, g.y, fmaf(z.z, g.z, fmaf(z.w, g.w, f[0]))));
+            if (!first) {
+                const float4 p = Gp[k], d = Df[k];
+                f[1] = fmaf(z.x, p.x, fmaf(z.y, p.y, fmaf(z.z, p.z, fmaf(z.w, p.w, f[1]))));
+                f[2] = fmaf(g.x, d.x, fmaf(g.y, d.y, fmaf(g.z, d.z, fmaf(g.w, d.w, f[2]))));
+            }
+        }
+        double v[ND];
+        to_f64<ND>(f, v);
+        block_sum<ND>(v, red, true);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < ND; ++q) partials[blockIdx.x * ND + q] = v[q];
+        }
+    }
+    grid_barrier(bar, &state->wait_timeout);
+    // the totals, warp q for value q, lanes over the blocks in order (as the
+    // last block of a reduction kernel sums them)
+    if ((threadIdx.x >> 5) < ND) {
+        const int q = threadIdx.x >> 5;
+        double s = 0.0;
+        unsigned b = threadIdx.x & 31;
+        for (; b + 224 < gridDim.x; b += 256) {
+            double p[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) p[k] = __ldcg(&partials[(b + 32 * k) * ND + q]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s += p[k];
+        }
+        for (; b < gridDim.x; b += 32) s += __ldcg(&partials[b * ND + q]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) red[q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double gg = red[0], ggp = red[1], gdot = red[2];
+        double beta = 0.0;
+        int restart = 1;
+        if (!first) {
+            beta = (gpgp > 0.0) ? fmax(0.0, (gg - ggp) / gpgp) : 0.0;
+            restart = (-gg + beta * gdot >= 0.0) ? 1 : 0;
+            if (restart) beta = 0.0;
+        }
+        const bool bad = !isfinite(gg) || !isfinite(beta);
+        s_beta = (float)beta;
+        s_restart = restart;
+        s_bad = bad ? 1 : 0;
+        if (blockIdx.x == 0) {
+            if (bad) {
+                state->status = OMM_ERR_NONFINITE;
+                state->done = 1;
+            } else {
+                state->gg = gg;
+                state->ggp = ggp;
+                state->gd = gdot;
+                state->gg_prev = gg;
+                state->beta = beta;
+                state->beta_f = (float)beta;
+                state->restart = restart;
+                state->gD = restart ? -gg : -gg + beta * gdot;   // <G, D_new>
+            }
+        }
+    }
+    __syncthreads();
+    if (s_bad) return;
+    // the direction pass (mx_direction4_kernel)
+    const float beta = s_beta;
+    const bool restart = s_restart != 0;
+    float gd = 0.f;
+    for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n4; k += stride) {
+        const float4 g = G[k];
+        const float4 z = PRE ? Zg[k] : g;
+        float4 d = Df[k];
+        if (restart) {
+            d = make_float4(-z.x, -z.y, -z.z, -z.w);
+        } else {
+            d.x = fmaf(beta, d.x, -z.x);
+            d.y = fmaf(beta, d.y, -z.y);
+            d.z = fmaf(beta, d.z, -z.z);
+            d.w = fmaf(beta, d.w, -z.w);
+        }
+        Df[k] = d;
+        Gp[k] = g;
+        const int64_t o = 4 * k, j = o / m, i = o - j * m;
+        if (ROUND1) {
+            const __nv_bfloat162 b01 = __floats2bfloat162_rn(d.x, d.y), b23 = __floats2bfloat162_rn(d.z, d.w);
+            const float2 f01 = __bfloat1622float2(b01), f23 = __bfloat1622float2(b23);
+            const float4 r = make_float4(f01.x, f01.y, f23.x, f23.y);
+            gd = fmaf(g.x, r.x, fmaf(g.y, r.y, fmaf(g.z, r.z, fmaf(g.w, r.w, gd))));
+            D[k] = r;
+            if (dd.ptr != nullptr) {
+                __nv_bfloat16 *p = (__nv_bfloat16 *)dd.ptr;
+                uint2 u;
+                u.x = *reinterpret_cast<const uint32_t *>(&b01);
+                u.y = *reinterpret_cast<const uint32_t *>(&b23);
+                *reinterpret_cast<uint2 *>(p + j * dd.ld + i) = u;
+                for (int t = 1; t < dd.nd; ++t)
+                    *reinterpret_cast<uint2 *>(p + t * dd.plane + j * dd.ld + i) = make_uint2(0u, 0u);
+            }
+        } else if (dd.ptr != nullptr) {
+            put3f4(dd, j * dd.ld + i, d);
+        }
+    }
+    direction_slope<ROUND1>(gd, slope);
+}
+
 // Digits of four consecutive rows of one column per thread (m % 4 == 0)
 __global__ void __launch_bounds__(NT) mx_digits4_kernel(int m, int64_t mn, const float4 *__restrict__ A,
                                                          const DevState *state, DigitOut dd) {
@@ -736,6 +902,60 @@ int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *G
         mx_direction_kernel<false><<<grid, NT, 0, st>>>((int)m, mn, G, Zg, Gp, Df, D, state, dd, slope);
     count_launch();
     OMM_CUDA_TRY(cudaGetLastError());
+    return OMM_OK;
+}
+
+int mx_dots_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *Df, float *D,
+                      DevState *state, DigitOut dd, bool round1, double *slope, int *slope_blocks, double *scratch,
+                      unsigned long long *bar, int first, cudaStream_t st) {
+    if (round1 && (slope == nullptr || D == nullptr || D == Df)) return OMM_ERR_ARG;
+    if (!round1) D = Df;
+    const int64_t mn = m * n;
+    const bool aligned =
+        ((((uintptr_t)G) | ((uintptr_t)Gp) | ((uintptr_t)Df) | ((uintptr_t)D) | ((uintptr_t)Zg)) & 15u) == 0 &&
+        (dd.ptr == nullptr || ((((uintptr_t)dd.ptr) & 7u) == 0 && dd.ld % 4 == 0 && dd.plane % 4 == 0));
+    if (m % 4 != 0 || !aligned || bar == nullptr || (((uintptr_t)bar) & 7u) != 0) return OMM_ERR_UNSUPPORTED;
+    const int variant = (Zg != nullptr ? 2 : 0) + (round1 ? 1 : 0);
+    auto kern = Zg != nullptr
+                    ? (round1 ? mx_dots_direction4_kernel<true, true> : mx_dots_direction4_kernel<true, false>)
+                    : (round1 ? mx_dots_direction4_kernel<false, true> : mx_dots_direction4_kernel<false, false>);
+    // every block must be resident at once: the grid is capped by the occupancy
+    // (the same for every launch of a handle, as the barrier's counter needs)
+    static int coop = -1, sms = 0;
+    if (coop < 0) {
+        int dev = 0, c = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return OMM_ERR_CUDA;
+        coop = c;
+    }
+    if (!coop) return OMM_ERR_UNSUPPORTED;
+    static int occupancy[4] = {0, 0, 0, 0};
+    if (occupancy[variant] == 0) OMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occupancy[variant], kern, NT, 0));
+    const int per_sm = occupancy[variant];
+    int64_t nb = ceil_div(mn, (int64_t)NT * 8);
+    if (nb > kRedBlocksMax) nb = kRedBlocksMax;
+    if (nb > (int64_t)per_sm * sms) nb = (int64_t)per_sm * sms;
+    if (nb < 1) return OMM_ERR_UNSUPPORTED;
+    if (slope_blocks != nullptr) *slope_blocks = round1 ? (int)nb : 0;
+    const float4 *G4 = reinterpret_cast<const float4 *>(G);
+    const float4 *Z4 = Zg != nullptr ? reinterpret_cast<const float4 *>(Zg) : G4;
+    float4 *Gp4 = reinterpret_cast<float4 *>(Gp), *Df4 = reinterpret_cast<float4 *>(Df),
+           *D4 = reinterpret_cast<float4 *>(D);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nb, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    OMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, (int)m, mn, G4, Z4, Gp4, Df4, D4, state, dd, slope, scratch, bar,
+                                    first));
+    count_launch();
     return OMM_OK;
 }
 

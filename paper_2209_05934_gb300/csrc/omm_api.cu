@@ -268,8 +268,9 @@ void harvest_stage_times(omm_handle *h) {
     h->nev = 0;
 }
 
-// counters: 0 coeffs, 1 nn update, 2 dots, 3 gershgorin
+// counters: 0 coeffs, 1 nn update, 2 dots, 3 gershgorin, 4 grid barrier (64-bit)
 unsigned int *ctr(omm_handle *h, int i) { return h->counters + 64 * i; }
+unsigned long long *grid_bar(omm_handle *h) { return reinterpret_cast<unsigned long long *>(ctr(h, 4)); }
 double *scr(omm_handle *h, int i) {
     return h->scratch + (int64_t)i * omm::kRedBlocksMax * omm::kRedSlots;
 }
@@ -769,8 +770,12 @@ int mixed_direction(omm_handle *h, int first) {
     // direction) runs on the unrounded Df32 and the line search along D32
     const bool round1 = h->opt.dir_digits == 1;
     float *Df = round1 ? x.Df32 : x.D32;
+    // the slope parts go to reduction slot 3 (otherwise used by omm_set_HS only);
+    // one cooperative launch where it applies, else the dots and direction kernels
+    const int rc = omm::mx_dots_direction(m, n, x.G32, Zg, x.Gp32, Df, x.D32, h->dstate, dig_D(h), round1,
+                                          scr(h, 3), &h->slope_blocks, scr(h, 2), grid_bar(h), first, h->stream);
+    if (rc != OMM_ERR_UNSUPPORTED) return rc;
     TRY(omm::mx_dots_beta(m * n, x.G32, Zg, x.Gp32, Df, scr(h, 2), ctr(h, 2), h->dstate, first, h->stream));
-    // the slope parts go to reduction slot 3 (otherwise used by omm_set_HS only)
     return omm::mx_direction(m, n, x.G32, Zg, x.Gp32, Df, x.D32, h->dstate, dig_D(h), round1, scr(h, 3),
                              &h->slope_blocks, h->stream);
 }
