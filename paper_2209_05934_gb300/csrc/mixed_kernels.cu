@@ -613,29 +613,37 @@ __global__ void __launch_bounds__(NT) mx_direction4_kernel(int m, int64_t mn, co
 }
 
 // Grid-wide barrier of a cooperative launch (every block of the grid is
-// resident).  Blocks arrive on a 64-bit counter that only grows; a launch waits
-// for the next multiple of gridDim.x, so the counter needs no reset as long as
-// every launch on it has the same grid.  The wait is bounded: past ~1 s (far
-// beyond any skew between resident blocks) it records the error and the block
-// goes on.
-__device__ __forceinline__ void grid_barrier(unsigned long long *count, int *err) {
+// resident), on two words kept for the handle: bar[0] counts the blocks that
+// have arrived, bar[1] is the generation.  Each block reads the generation,
+// then arrives; the last to arrive resets the count and advances the
+// generation, which releases the others.  Nothing depends on the grid size of
+// earlier launches.  The wait is bounded: past ~1 s (far beyond any skew
+// between resident blocks) it records the error and the block goes on.
+__device__ __forceinline__ void grid_barrier(unsigned int *bar, int *err) {
     __syncthreads();
     if (threadIdx.x == 0) {
+        unsigned int gen;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
         __threadfence();
-        const unsigned long long old = atomicAdd(count, 1ull);
-        const unsigned long long target = (old / gridDim.x + 1ull) * gridDim.x;
-        uint64_t t0;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-        for (uint32_t i = 0;; ++i) {
-            unsigned long long c;
-            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(count) : "memory");
-            if (c >= target) break;
-            if ((i & 255u) == 255u) {
-                uint64_t t;
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                if (t - t0 > 1000000000ull) {
-                    atomicExch(err, 1);
-                    break;
+        const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            bar[0] = 0u;
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(gen + 1u) : "memory");
+        } else {
+            uint64_t t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            for (uint32_t i = 0;; ++i) {
+                unsigned int g;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+                if (g != gen) break;
+                if ((i & 255u) == 255u) {
+                    uint64_t t;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                    if (t - t0 > 1000000000ull) {
+                        atomicExch(err, 1);
+                        break;
+                    }
                 }
             }
         }
@@ -657,7 +665,7 @@ __global__ void __launch_bounds__(NT, 4) mx_dots_direction4_kernel(int m, int64_
                                                                  const float4 *__restrict__ Zg, float4 *Gp,
                                                                  float4 *Df, float4 *D, DevState *state, DigitOut dd,
                                                                  double *slope, double *partials,
-                                                                 unsigned long long *bar, int first) {
+                                                                 unsigned int *bar, int first) {
     if (*((volatile const int *)&state->done)) return;
     __shared__ double red[(NT / 32) * ND];
     __shared__ float s_beta;
@@ -907,7 +915,7 @@ int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *G
 
 int mx_dots_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *Df, float *D,
                       DevState *state, DigitOut dd, bool round1, double *slope, int *slope_blocks, double *scratch,
-                      unsigned long long *bar, int first, cudaStream_t st) {
+                      unsigned int *bar, int first, cudaStream_t st) {
     if (round1 && (slope == nullptr || D == nullptr || D == Df)) return OMM_ERR_ARG;
     if (!round1) D = Df;
     const int64_t mn = m * n;
@@ -920,7 +928,6 @@ int mx_dots_direction(int64_t m, int64_t n, const float *G, const float *Zg, flo
                     ? (round1 ? mx_dots_direction4_kernel<true, true> : mx_dots_direction4_kernel<true, false>)
                     : (round1 ? mx_dots_direction4_kernel<false, true> : mx_dots_direction4_kernel<false, false>);
     // every block must be resident at once: the grid is capped by the occupancy
-    // (the same for every launch of a handle, as the barrier's counter needs)
     static int coop = -1, sms = 0;
     if (coop < 0) {
         int dev = 0, c = 0;

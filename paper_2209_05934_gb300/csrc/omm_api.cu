@@ -268,9 +268,9 @@ void harvest_stage_times(omm_handle *h) {
     h->nev = 0;
 }
 
-// counters: 0 coeffs, 1 nn update, 2 dots, 3 gershgorin, 4 grid barrier (64-bit)
+// counters: 0 coeffs, 1 nn update, 2 dots, 3 gershgorin, 4 grid barrier (count, generation)
 unsigned int *ctr(omm_handle *h, int i) { return h->counters + 64 * i; }
-unsigned long long *grid_bar(omm_handle *h) { return reinterpret_cast<unsigned long long *>(ctr(h, 4)); }
+unsigned int *grid_bar(omm_handle *h) { return ctr(h, 4); }
 double *scr(omm_handle *h, int i) {
     return h->scratch + (int64_t)i * omm::kRedBlocksMax * omm::kRedSlots;
 }

@@ -149,12 +149,12 @@ int mx_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *G
                  DevState *state, DigitOut dd, bool round1, double *slope, int *slope_blocks, cudaStream_t st);
 // mx_dots_beta and mx_direction in one cooperative launch with a grid barrier
 // (m % 4 == 0, 16-byte aligned arrays): the same dots, beta, restart test and
-// direction.  bar: a zeroed 64-bit counter kept for the handle (every launch on
-// it has the same grid).  OMM_ERR_UNSUPPORTED when the form does not apply (the
-// caller then launches the two kernels).
+// direction.  bar: two zeroed words kept for the handle (arrival count and
+// generation of the grid barrier).  OMM_ERR_UNSUPPORTED when the form does not
+// apply (the caller then launches the two kernels).
 int mx_dots_direction(int64_t m, int64_t n, const float *G, const float *Zg, float *Gp, float *Df, float *D,
                       DevState *state, DigitOut dd, bool round1, double *slope, int *slope_blocks, double *scratch,
-                      unsigned long long *bar, int first, cudaStream_t st);
+                      unsigned int *bar, int first, cudaStream_t st);
 // digits of an FP32 m x n column-major array: column j -> row j of the planes
 int mx_digits(int64_t m, int64_t n, const float *A, const DevState *state, DigitOut dd, cudaStream_t st);
 int mx_round(int64_t count, const double *src, float *dst, const DevState *state, cudaStream_t st);
